@@ -1,0 +1,140 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the smoke check.
+
+This module holds no arithmetic of the method: it only fixes the workload
+shapes and draws random numbers (flow weights, test fields).  Both the FP64
+oracle (``oracle/``) and the CUDA library receive the arrays produced here as
+plain data, so neither depends on the other.
+
+Canonical weight layout (FP64, flat, one block per coupling layer ``l`` in the
+order the layers are applied to the prior sample):
+
+    W1[c1][1][T]  b1[c1]  W2[c2][c1][T]  b2[c2]  W3[2][c2][T]  b3[2]
+
+with ``T = 3**nd`` taps ordered (kz, ky, kx) in 3D and (ky, kx) in 2D, offset
+``k - 1`` along each axis.  Output channel 0 of conv3 is s, channel 1 is t.
+The s/t network shape (three 3^d convolutions, hidden sizes [c1, c2], one
+input channel, two output channels) is the paper's model section (Sec. 3,
+the example parameter file: n_layers, hidden_sizes, kernel_size, inC, outC).
+
+Initialisation: Kaiming-uniform with negative slope sqrt(5) (the default of
+PyTorch convolution layers, which the paper's software mirrors), i.e.
+W, b ~ U(-1/sqrt(fan_in), +1/sqrt(fan_in)), fan_in = C_in * T, drawn in FP64
+with numpy's Philox bit generator keyed by ``seed`` in the layout order above.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+
+@dataclasses.dataclass(frozen=True)
+class FlowShape:
+    nd: int                 # lattice dimension, 2 or 3
+    L: int                  # sites per axis (periodic)
+    n_layers: int           # affine coupling layers
+    c1: int = 8             # hidden width after conv1
+    c2: int = 8             # hidden width after conv2
+    use_final_tanh: bool = True
+    leaky_slope: float = 0.01
+
+    @property
+    def V(self) -> int:
+        return self.L ** self.nd
+
+    @property
+    def taps(self) -> int:
+        return 3 ** self.nd
+
+    def layer_params(self) -> int:
+        T = self.taps
+        return (self.c1 * T + self.c1 + self.c2 * self.c1 * T + self.c2
+                + 2 * self.c2 * T + 2)
+
+    def n_params(self) -> int:
+        return self.n_layers * self.layer_params()
+
+    def layer_blocks(self):
+        """(name, shape) of the six tensors of one layer, in layout order."""
+        T = self.taps
+        return [("W1", (self.c1, 1, T)), ("b1", (self.c1,)),
+                ("W2", (self.c2, self.c1, T)), ("b2", (self.c2,)),
+                ("W3", (2, self.c2, T)), ("b3", (2,))]
+
+
+@dataclasses.dataclass(frozen=True)
+class Phi4:
+    m2: float
+    lam: float
+
+
+def init_weights(shape: FlowShape, seed: int = 0) -> np.ndarray:
+    """Flat FP64 weights in the canonical layout, Kaiming-uniform from ``seed``."""
+    gen = np.random.Generator(np.random.Philox(key=seed))
+    T = shape.taps
+    fan_in = {"W1": T, "b1": T, "W2": shape.c1 * T, "b2": shape.c1 * T,
+              "W3": shape.c2 * T, "b3": shape.c2 * T}
+    out = []
+    for _ in range(shape.n_layers):
+        for name, shp in shape.layer_blocks():
+            a = 1.0 / math.sqrt(fan_in[name])
+            out.append(gen.uniform(-a, a, size=int(np.prod(shp))))
+    w = np.concatenate(out).astype(np.float64)
+    assert w.size == shape.n_params()
+    return w
+
+
+def split_layer(shape: FlowShape, w: np.ndarray, layer: int) -> dict:
+    """Views of the six tensors of one layer of a canonical weight array."""
+    P = shape.layer_params()
+    blk = w[layer * P:(layer + 1) * P]
+    out, off = {}, 0
+    for name, shp in shape.layer_blocks():
+        n = int(np.prod(shp))
+        out[name] = blk[off:off + n].reshape(shp)
+        off += n
+    return out
+
+
+def zero_head(shape: FlowShape, w: np.ndarray) -> np.ndarray:
+    """Copy of ``w`` with every conv3 weight and bias set to zero (s = t = 0)."""
+    w = w.copy()
+    for l in range(shape.n_layers):
+        d = split_layer(shape, w, l)
+        d["W3"][...] = 0.0
+        d["b3"][...] = 0.0
+    return w
+
+
+def scale_head(shape: FlowShape, w: np.ndarray, factor: float) -> np.ndarray:
+    """Copy of ``w`` with conv3 weights and bias multiplied by ``factor``."""
+    w = w.copy()
+    for l in range(shape.n_layers):
+        d = split_layer(shape, w, l)
+        d["W3"][...] *= factor
+        d["b3"][...] *= factor
+    return w
+
+
+def random_field(nd: int, L: int, B: int, seed: int, scale: float = 1.0) -> np.ndarray:
+    """[B][L^nd] FP64 Gaussian test fields (numpy Philox, independent of the method)."""
+    gen = np.random.Generator(np.random.Philox(key=seed + 7919))
+    return scale * gen.standard_normal((B, L ** nd))
+
+
+# ---------------------------------------------------------------------------
+# Workloads.  c1 is the paper's printed example (Sec. 3, example parameter
+# file: 2D, L=8, m^2=-4, lambda=8, 16 layers, hidden [8, 8], batch 64);
+# c2..c5 are the larger synthetic workloads the build is measured on.
+# ---------------------------------------------------------------------------
+WORKLOADS = {
+    "c1": dict(shape=FlowShape(nd=2, L=8, n_layers=16, c1=8, c2=8),
+               phi4=Phi4(m2=-4.0, lam=8.0), batch=64, chain=1024),
+    "c2": dict(shape=FlowShape(nd=2, L=32, n_layers=24, c1=32, c2=32),
+               phi4=Phi4(m2=-4.0, lam=8.0), batch=1024, chain=0),
+    "c3": dict(shape=FlowShape(nd=3, L=16, n_layers=16, c1=32, c2=32),
+               phi4=Phi4(m2=-6.0, lam=5.0), batch=4096, chain=100000),
+    "c4": dict(nd=3, L=16, phi4=Phi4(m2=-6.0, lam=5.0), chains=512,
+               n_steps=20, eps=0.05, trajectories=1000),
+}

@@ -1,0 +1,638 @@
+/*
+ * gf_oracle.c -- plain FP64 CPU oracle (TEST INFRASTRUCTURE ONLY; see
+ * gf_oracle.h for the scope and the paper sections each routine follows).
+ *
+ * Deliberately slow and literal: direct periodic cross-correlation with a
+ * neighbour table, the action with both neighbour terms, a serial MH loop and
+ * a textbook leapfrog.  OpenMP (when enabled) only splits independent
+ * configurations / chains across threads.
+ */
+#include "gf_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x64-10 (Salmon et al., SC'11): two 64x64->128 multiplies per round,
+ * Weyl key schedule, ten rounds.                                            */
+/* ------------------------------------------------------------------------ */
+#define PHILOX_M0 0xD2E7470EE14C6C93ULL
+#define PHILOX_M1 0xCA5A826395121157ULL
+#define PHILOX_W0 0x9E3779B97F4A7C15ULL
+#define PHILOX_W1 0xBB67AE8584CAA73BULL
+
+void gfo_philox4x64_10(const uint64_t key[2], const uint64_t ctr[4], uint64_t out[4]) {
+    uint64_t k0 = key[0], k1 = key[1];
+    uint64_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) { k0 += PHILOX_W0; k1 += PHILOX_W1; }
+        unsigned __int128 p0 = (unsigned __int128)PHILOX_M0 * x0;
+        unsigned __int128 p1 = (unsigned __int128)PHILOX_M1 * x2;
+        uint64_t hi0 = (uint64_t)(p0 >> 64), lo0 = (uint64_t)p0;
+        uint64_t hi1 = (uint64_t)(p1 >> 64), lo1 = (uint64_t)p1;
+        uint64_t y0 = hi1 ^ x1 ^ k0;
+        uint64_t y2 = hi0 ^ x3 ^ k1;
+        x0 = y0; x1 = lo1; x2 = y2; x3 = lo0;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* Stream tags in the last counter word (reading: the paper does not specify
+ * its generator; each random purpose gets its own counter sub-space). */
+enum { TAG_PRIOR = 1, TAG_MH = 2, TAG_HMC_P = 3, TAG_HMC_U = 4 };
+
+/* Uniform in (0,1) with 23 random bits: (2k+1) * 2^-24, exact in fp32. */
+static double u24(uint64_t w) { return (double)(2 * (w >> 41) + 1) * 0x1p-24; }
+/* Uniform in (0,1) with 52 random bits: (2k+1) * 2^-53, exact in fp64. */
+static double u53(uint64_t w) { return (double)(2 * (w >> 12) + 1) * 0x1p-53; }
+
+static const double TWO_PI = 6.283185307179586476925286766559;
+
+void gfo_prior(int64_t V, int64_t B, uint64_t seed, uint64_t counter0, int32_t f32, double* z) {
+    /* Sites 4j..4j+3 of configuration b use philox(key=(seed,0),
+     * ctr=(counter0+b, j, 0, TAG_PRIOR)); words (0,1) and (2,3) feed two
+     * Box-Muller pairs (cos, sin) in that order. */
+    for (int64_t b = 0; b < B; ++b) {
+        for (int64_t j = 0; 4 * j < V; ++j) {
+            uint64_t key[2] = {seed, 0};
+            uint64_t ctr[4] = {counter0 + (uint64_t)b, (uint64_t)j, 0, TAG_PRIOR};
+            uint64_t w[4];
+            gfo_philox4x64_10(key, ctr, w);
+            double zz[4];
+            for (int p = 0; p < 2; ++p) {
+                double r = sqrt(-2.0 * log(u24(w[2 * p])));
+                double th = TWO_PI * u24(w[2 * p + 1]);
+                zz[2 * p] = r * cos(th);
+                zz[2 * p + 1] = r * sin(th);
+            }
+            for (int q = 0; q < 4 && 4 * j + q < V; ++q) {
+                double v = zz[q];
+                if (f32) v = (double)(float)v;
+                z[b * V + 4 * j + q] = v;
+            }
+        }
+    }
+}
+
+void gfo_log_prior(int64_t V, int64_t B, const double* z, double* logr) {
+    for (int64_t b = 0; b < B; ++b) {
+        double s = 0.0;
+        for (int64_t n = 0; n < V; ++n) s += z[b * V + n] * z[b * V + n];
+        logr[b] = -0.5 * s - 0.5 * (double)V * log(TWO_PI);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Lattice geometry: site index n = x + L*(y + L*z) (x fastest).            */
+/* ------------------------------------------------------------------------ */
+static int64_t ipow(int64_t a, int e) { int64_t r = 1; while (e--) r *= a; return r; }
+
+static void coords(int nd, int L, int64_t n, int c[3]) {
+    c[0] = c[1] = c[2] = 0;
+    for (int a = 0; a < nd; ++a) { c[a] = (int)(n % L); n /= L; }   /* c[0]=x, c[1]=y, c[2]=z */
+}
+static int64_t site(int nd, int L, const int c[3]) {
+    int64_t n = 0;
+    for (int a = nd - 1; a >= 0; --a) n = n * L + (((c[a] % L) + L) % L);
+    return n;
+}
+static int parity(int nd, int L, int64_t n) {
+    int c[3]; coords(nd, L, n, c);
+    return (c[0] + c[1] + c[2]) & 1;
+}
+/* nbr[n*T + t] = index of n + delta(t); taps ordered (kz,ky,kx) / (ky,kx),
+ * delta = k - 1 along each axis. */
+static int64_t* make_nbr(int nd, int L) {
+    int64_t V = ipow(L, nd); int T = (int)ipow(3, nd);
+    int64_t* nbr = (int64_t*)malloc(sizeof(int64_t) * V * T);
+    for (int64_t n = 0; n < V; ++n) {
+        int c[3]; coords(nd, L, n, c);
+        for (int t = 0; t < T; ++t) {
+            int k[3] = {0, 0, 0}; int tt = t;
+            for (int a = 0; a < nd; ++a) { k[a] = tt % 3; tt /= 3; } /* k[0]=kx (fastest) */
+            int d[3] = {c[0] + k[0] - 1, c[1] + k[1] - 1, c[2] + k[2] - 1};
+            nbr[n * T + t] = site(nd, L, d);
+        }
+    }
+    return nbr;
+}
+
+/* phi^4 action (Sec. 1): S = sum_n [ -phi(n) Lap phi(n) + m2 phi^2 + lam phi^4 ],
+ * Lap phi(n) = sum_mu [phi(n+mu) + phi(n-mu) - 2 phi(n)], periodic.
+ * Reading: the printed summand phi(n_o) d^2 phi(n_o) uses the summation index n. */
+static double action_one(int nd, int L, double m2, double lam, const double* phi) {
+    int64_t V = ipow(L, nd);
+    double S = 0.0;
+    for (int64_t n = 0; n < V; ++n) {
+        int c[3]; coords(nd, L, n, c);
+        double p = phi[n], lap = 0.0;
+        for (int mu = 0; mu < nd; ++mu) {
+            int cp[3] = {c[0], c[1], c[2]}, cm[3] = {c[0], c[1], c[2]};
+            cp[mu] += 1; cm[mu] -= 1;
+            lap += phi[site(nd, L, cp)] + phi[site(nd, L, cm)] - 2.0 * p;
+        }
+        S += -p * lap + m2 * p * p + lam * p * p * p * p;
+    }
+    return S;
+}
+
+void gfo_action(int32_t nd, int32_t L, double m2, double lam, int64_t B, const double* phi, double* S) {
+    int64_t V = ipow(L, nd);
+    for (int64_t b = 0; b < B; ++b) S[b] = action_one(nd, L, m2, lam, phi + b * V);
+}
+
+/* dS/dphi(n) = 2 sum_mu (2 phi(n) - phi(n+mu) - phi(n-mu)) + 2 m2 phi + 4 lam phi^3 */
+static void force_one(int nd, int L, double m2, double lam, const double* phi, double* F) {
+    int64_t V = ipow(L, nd);
+    for (int64_t n = 0; n < V; ++n) {
+        int c[3]; coords(nd, L, n, c);
+        double p = phi[n], k = 0.0;
+        for (int mu = 0; mu < nd; ++mu) {
+            int cp[3] = {c[0], c[1], c[2]}, cm[3] = {c[0], c[1], c[2]};
+            cp[mu] += 1; cm[mu] -= 1;
+            k += 2.0 * p - phi[site(nd, L, cp)] - phi[site(nd, L, cm)];
+        }
+        F[n] = 2.0 * k + 2.0 * m2 * p + 4.0 * lam * p * p * p;
+    }
+}
+
+void gfo_force(int32_t nd, int32_t L, double m2, double lam, int64_t B, const double* phi, double* F) {
+    int64_t V = ipow(L, nd);
+    for (int64_t b = 0; b < B; ++b) force_one(nd, L, m2, lam, phi + b * V, F + b * V);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Coupling network: conv(1->c1) LReLU conv(c1->c2) LReLU conv(c2->2),       */
+/* periodic 3^d cross-correlation out[n][o] = b[o] + sum_{i,t} W[o][i][t] in[nbr(n,t)][i]. */
+/* ------------------------------------------------------------------------ */
+static double bf16_round(double x) {
+    /* Round to the nearest value with 8 significant bits, ties to even. */
+    if (x == 0.0 || !isfinite(x)) return x;
+    int e; double m = frexp(x, &e);               /* x = m * 2^e, 0.5 <= |m| < 1 */
+    double r = nearbyint(ldexp(m, 8));            /* default mode: ties to even */
+    return ldexp(r, e - 8);
+}
+
+typedef struct {
+    const double *W1, *b1, *W2, *b2, *W3, *b3;
+} layer_w;
+
+static int64_t layer_size(const gfo_shape* sh) {
+    int64_t T = ipow(3, sh->nd);
+    return sh->c1 * T + sh->c1 + (int64_t)sh->c2 * sh->c1 * T + sh->c2 + 2 * sh->c2 * T + 2;
+}
+
+static layer_w layer_ptrs(const gfo_shape* sh, const double* w, int layer) {
+    int64_t T = ipow(3, sh->nd);
+    const double* p = w + layer * layer_size(sh);
+    layer_w lw;
+    lw.W1 = p; p += sh->c1 * T;
+    lw.b1 = p; p += sh->c1;
+    lw.W2 = p; p += (int64_t)sh->c2 * sh->c1 * T;
+    lw.b2 = p; p += sh->c2;
+    lw.W3 = p; p += 2 * sh->c2 * T;
+    lw.b3 = p;
+    return lw;
+}
+
+static double lrelu(double v, double a) { return v > 0.0 ? v : a * v; }
+
+/* Periodic cross-correlation: in [V][Cin] -> out [V][Cout], W [Cout][Cin][T]. */
+static void conv(int64_t V, int T, const int64_t* nbr, int Cin, int Cout,
+                 const double* W, const double* b, int round_w, const double* in, double* out) {
+    for (int64_t n = 0; n < V; ++n) {
+        for (int o = 0; o < Cout; ++o) {
+            double acc = b[o];
+            for (int i = 0; i < Cin; ++i) {
+                for (int t = 0; t < T; ++t) {
+                    double wv = W[((int64_t)o * Cin + i) * T + t];
+                    if (round_w) wv = bf16_round(wv);
+                    acc += wv * in[nbr[n * T + t] * Cin + i];
+                }
+            }
+            out[n * Cout + o] = acc;
+        }
+    }
+}
+
+/* Network intermediates of one layer on one configuration. */
+typedef struct { double *h1pre, *h1, *h2pre, *h2, *spre, *s, *t; } net_buf;
+
+static net_buf net_alloc(const gfo_shape* sh, int64_t V) {
+    net_buf nb;
+    nb.h1pre = (double*)malloc(sizeof(double) * V * sh->c1);
+    nb.h1 = (double*)malloc(sizeof(double) * V * sh->c1);
+    nb.h2pre = (double*)malloc(sizeof(double) * V * sh->c2);
+    nb.h2 = (double*)malloc(sizeof(double) * V * sh->c2);
+    nb.spre = (double*)malloc(sizeof(double) * V * 2);
+    nb.s = (double*)malloc(sizeof(double) * V);
+    nb.t = (double*)malloc(sizeof(double) * V);
+    return nb;
+}
+static void net_free(net_buf* nb) {
+    free(nb->h1pre); free(nb->h1); free(nb->h2pre); free(nb->h2);
+    free(nb->spre); free(nb->s); free(nb->t);
+}
+
+/* s, t = net(y) where y is the layer input with its updated (active) sites zeroed.
+ * Readings: LeakyReLU after conv1 and conv2, none after conv3; tanh on channel 0
+ * (s) only when use_final_tanh; channel 1 is t. */
+static void net_forward(const gfo_shape* sh, layer_w lw, int32_t bf16, int64_t V, int T,
+                        const int64_t* nbr, const double* y, net_buf* nb) {
+    conv(V, T, nbr, 1, sh->c1, lw.W1, lw.b1, bf16 & GFO_BF16_W1, y, nb->h1pre);
+    for (int64_t k = 0; k < V * sh->c1; ++k) {
+        nb->h1[k] = lrelu(nb->h1pre[k], sh->leaky_slope);
+        if (bf16 & GFO_BF16_H1) nb->h1[k] = bf16_round(nb->h1[k]);
+    }
+    conv(V, T, nbr, sh->c1, sh->c2, lw.W2, lw.b2, bf16 & GFO_BF16_W2, nb->h1, nb->h2pre);
+    for (int64_t k = 0; k < V * sh->c2; ++k) {
+        nb->h2[k] = lrelu(nb->h2pre[k], sh->leaky_slope);
+        if (bf16 & GFO_BF16_H2) nb->h2[k] = bf16_round(nb->h2[k]);
+    }
+    conv(V, T, nbr, sh->c2, 2, lw.W3, lw.b3, bf16 & GFO_BF16_W3, nb->h2, nb->spre);
+    for (int64_t n = 0; n < V; ++n) {
+        nb->s[n] = sh->use_final_tanh ? tanh(nb->spre[2 * n]) : nb->spre[2 * n];
+        nb->t[n] = nb->spre[2 * n + 1];
+    }
+}
+
+static int shape_ok(const gfo_shape* sh) {
+    return sh && (sh->nd == 2 || sh->nd == 3) && sh->L >= 1 && sh->n_layers >= 0 &&
+           sh->c1 >= 1 && sh->c2 >= 1;
+}
+
+int gfo_coupling_net(const gfo_shape* sh, const double* w, int32_t layer, int32_t bf16_mask,
+                     const double* y, double* s, double* t) {
+    if (!shape_ok(sh) || layer < 0 || layer >= sh->n_layers) return -1;
+    int64_t V = ipow(sh->L, sh->nd); int T = (int)ipow(3, sh->nd);
+    int64_t* nbr = make_nbr(sh->nd, sh->L);
+    net_buf nb = net_alloc(sh, V);
+    net_forward(sh, layer_ptrs(sh, w, layer), bf16_mask, V, T, nbr, y, &nb);
+    memcpy(s, nb.s, sizeof(double) * V);
+    memcpy(t, nb.t, sizeof(double) * V);
+    net_free(&nb); free(nbr);
+    return 0;
+}
+
+/* Sampling direction for one configuration (Sec. 1, coupling layer and its
+ * composition).  Reading: layer l (0-based, in application order) keeps the
+ * sites with parity (x+y+z) mod 2 == l mod 2 fixed and maps the others by
+ * x -> x * exp(s) + t, s and t computed from the fixed sites only; the
+ * log-det of dphi/dz is the sum of s over the updated sites. */
+static void sample_one(const gfo_shape* sh, const double* w, int32_t bf16, int64_t V, int T,
+                       const int64_t* nbr, const int* par, const double* z, double* x,
+                       double* logdet_out, net_buf* nb, double* y) {
+    memcpy(x, z, sizeof(double) * V);
+    double logdet = 0.0;
+    for (int l = 0; l < sh->n_layers; ++l) {
+        int frozen = l & 1;
+        for (int64_t n = 0; n < V; ++n) y[n] = (par[n] == frozen) ? x[n] : 0.0;
+        net_forward(sh, layer_ptrs(sh, w, l), bf16, V, T, nbr, y, nb);
+        for (int64_t n = 0; n < V; ++n) {
+            if (par[n] != frozen) {
+                x[n] = x[n] * exp(nb->s[n]) + nb->t[n];
+                logdet += nb->s[n];
+            }
+        }
+    }
+    *logdet_out = logdet;
+}
+
+int gfo_flow_sample(const gfo_shape* sh, const double* w, int32_t bf16_mask, double m2, double lam,
+                    int64_t B, uint64_t seed, uint64_t counter0, const double* z_in,
+                    double* z_out, double* phi_out, double* logq_out, double* S_out,
+                    double* logw_out, int32_t nthreads) {
+    if (!shape_ok(sh) || B < 0 || !phi_out || !logq_out) return -1;
+    int64_t V = ipow(sh->L, sh->nd); int T = (int)ipow(3, sh->nd);
+    int64_t* nbr = make_nbr(sh->nd, sh->L);
+    int* par = (int*)malloc(sizeof(int) * V);
+    for (int64_t n = 0; n < V; ++n) par[n] = parity(sh->nd, sh->L, n);
+    double* zall = (double*)malloc(sizeof(double) * (B > 0 ? B : 1) * V);
+    if (z_in) memcpy(zall, z_in, sizeof(double) * B * V);
+    else gfo_prior(V, B, seed, counter0, (bf16_mask & GFO_F32_IO) ? 1 : 0, zall);
+    if (nthreads < 1) nthreads = 1;
+#pragma omp parallel num_threads(nthreads)
+    {
+        net_buf nb = net_alloc(sh, V);
+        double* y = (double*)malloc(sizeof(double) * V);
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t b = 0; b < B; ++b) {
+            const double* z = zall + b * V;
+            double* x = phi_out + b * V;
+            double logdet, logr, S;
+            sample_one(sh, w, bf16_mask, V, T, nbr, par, z, x, &logdet, &nb, y);
+            gfo_log_prior(V, 1, z, &logr);
+            S = action_one(sh->nd, sh->L, m2, lam, x);
+            logq_out[b] = logr - logdet;                 /* log q = log r(z) - log|det dphi/dz| */
+            if (S_out) S_out[b] = S;
+            if (logw_out) logw_out[b] = -S - logq_out[b]; /* log p - log q, p = exp(-S) unnormalised */
+        }
+        net_free(&nb); free(y);
+    }
+    if (z_out) memcpy(z_out, zall, sizeof(double) * B * V);
+    free(zall); free(par); free(nbr);
+    return 0;
+}
+
+int gfo_flow_logq(const gfo_shape* sh, const double* w, int32_t bf16_mask, int64_t B,
+                  const double* phi, double* z_out, double* logq_out, int32_t nthreads) {
+    if (!shape_ok(sh) || B < 0 || !phi || !logq_out) return -1;
+    int64_t V = ipow(sh->L, sh->nd); int T = (int)ipow(3, sh->nd);
+    int64_t* nbr = make_nbr(sh->nd, sh->L);
+    int* par = (int*)malloc(sizeof(int) * V);
+    for (int64_t n = 0; n < V; ++n) par[n] = parity(sh->nd, sh->L, n);
+    if (nthreads < 1) nthreads = 1;
+#pragma omp parallel num_threads(nthreads)
+    {
+        net_buf nb = net_alloc(sh, V);
+        double* y = (double*)malloc(sizeof(double) * V);
+        double* x = (double*)malloc(sizeof(double) * V);
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t b = 0; b < B; ++b) {
+            memcpy(x, phi + b * V, sizeof(double) * V);
+            double logdet = 0.0, logr;
+            /* Layers in reverse order; each inverts x = (x - t) * exp(-s) on its
+             * updated sites, with s, t from the fixed sites (unchanged by the layer). */
+            for (int l = sh->n_layers - 1; l >= 0; --l) {
+                int frozen = l & 1;
+                for (int64_t n = 0; n < V; ++n) y[n] = (par[n] == frozen) ? x[n] : 0.0;
+                net_forward(sh, layer_ptrs(sh, w, l), bf16_mask, V, T, nbr, y, &nb);
+                for (int64_t n = 0; n < V; ++n) {
+                    if (par[n] != frozen) {
+                        x[n] = (x[n] - nb.t[n]) * exp(-nb.s[n]);
+                        logdet += nb.s[n];
+                    }
+                }
+            }
+            gfo_log_prior(V, 1, x, &logr);
+            logq_out[b] = logr - logdet;
+            if (z_out) memcpy(z_out + b * V, x, sizeof(double) * V);
+        }
+        net_free(&nb); free(y); free(x);
+    }
+    free(par); free(nbr);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Metropolis-Hastings independence chain (Sec. 1: flow proposals made exact */
+/* by the MH test with the Jacobian).  Readings: accept proposal k when      */
+/* log w_k - log w_cur > log u_k (strict, ties reject), with                 */
+/* log w = log p - log q = -S - log q; the very first proposal of a chain is */
+/* accepted unconditionally; u_k from philox(key=(seed, stream_id),          */
+/* ctr=(step, 0, 0, TAG_MH)) word 0.                                         */
+/* ------------------------------------------------------------------------ */
+void gfo_mh_logu(uint64_t seed, uint64_t stream_id, int64_t step0, int64_t n, double* logu) {
+    for (int64_t k = 0; k < n; ++k) {
+        uint64_t key[2] = {seed, stream_id};
+        uint64_t ctr[4] = {(uint64_t)(step0 + k), 0, 0, TAG_MH};
+        uint64_t w[4];
+        gfo_philox4x64_10(key, ctr, w);
+        logu[k] = log(u53(w[0]));
+    }
+}
+
+void gfo_mh_scan(gfo_mh_state* st, int64_t n, const double* logw, const double* logu,
+                 int64_t* chain_idx, uint8_t* acc) {
+    for (int64_t k = 0; k < n; ++k) {
+        int64_t g = st->step;
+        int a;
+        if (g == 0) a = 1;
+        else a = (logw[k] - st->logw_cur) > logu[k];
+        if (a) {
+            st->logw_cur = logw[k];
+            st->idx_cur = g;
+            if (g > 0) st->n_acc += 1;
+        }
+        if (chain_idx) chain_idx[k] = st->idx_cur;
+        if (acc) acc[k] = (uint8_t)a;
+        st->step = g + 1;
+    }
+}
+
+void gfo_mh_chain(gfo_mh_state* st, int64_t n, const double* logw, int64_t* chain_idx, uint8_t* acc) {
+    double* logu = (double*)malloc(sizeof(double) * (n > 0 ? n : 1));
+    gfo_mh_logu(st->seed, st->stream_id, st->step, n, logu);
+    gfo_mh_scan(st, n, logw, logu, chain_idx, acc);
+    free(logu);
+}
+
+/* ------------------------------------------------------------------------ */
+/* HMC (Sec. 2.2) with H = 1/2 sum pi^2 + S.  Leapfrog: half kick, then       */
+/* n_steps x (drift, kick) with the last kick halved; accept iff             */
+/* -dH > log u.  Momenta: FP64 Box-Muller from philox(key=(seed,0),          */
+/* ctr=(chain, traj, j, TAG_HMC_P)); u from ctr=(chain, traj, 0, TAG_HMC_U). */
+/* ------------------------------------------------------------------------ */
+void gfo_hmc_momenta(int64_t V, uint64_t seed, uint64_t chain, uint64_t traj, double* pi) {
+    for (int64_t j = 0; 4 * j < V; ++j) {
+        uint64_t key[2] = {seed, 0};
+        uint64_t ctr[4] = {chain, traj, (uint64_t)j, TAG_HMC_P};
+        uint64_t w[4];
+        gfo_philox4x64_10(key, ctr, w);
+        double pp[4];
+        for (int p = 0; p < 2; ++p) {
+            double r = sqrt(-2.0 * log(u53(w[2 * p])));
+            double th = TWO_PI * u53(w[2 * p + 1]);
+            pp[2 * p] = r * cos(th);
+            pp[2 * p + 1] = r * sin(th);
+        }
+        for (int q = 0; q < 4 && 4 * j + q < V; ++q) pi[4 * j + q] = pp[q];
+    }
+}
+
+static double kinetic(int64_t V, const double* pi) {
+    double k = 0.0;
+    for (int64_t n = 0; n < V; ++n) k += 0.5 * pi[n] * pi[n];
+    return k;
+}
+
+double gfo_leapfrog(int32_t nd, int32_t L, double m2, double lam, double* phi, double* pi,
+                    int32_t n_steps, double eps) {
+    int64_t V = ipow(L, nd);
+    double* F = (double*)malloc(sizeof(double) * V);
+    double H0 = kinetic(V, pi) + action_one(nd, L, m2, lam, phi);
+    force_one(nd, L, m2, lam, phi, F);
+    for (int64_t n = 0; n < V; ++n) pi[n] -= 0.5 * eps * F[n];
+    for (int i = 1; i <= n_steps; ++i) {
+        for (int64_t n = 0; n < V; ++n) phi[n] += eps * pi[n];
+        force_one(nd, L, m2, lam, phi, F);
+        double h = (i < n_steps) ? eps : 0.5 * eps;
+        for (int64_t n = 0; n < V; ++n) pi[n] -= h * F[n];
+    }
+    double H1 = kinetic(V, pi) + action_one(nd, L, m2, lam, phi);
+    free(F);
+    return H1 - H0;
+}
+
+void gfo_hmc_trajectory(int32_t nd, int32_t L, double m2, double lam, int64_t n_chains,
+                        double* phi, int32_t n_steps, double eps, uint64_t seed,
+                        uint64_t traj_index, double* dH_out, uint8_t* acc_out,
+                        int32_t nthreads) {
+    int64_t V = ipow(L, nd);
+    if (nthreads < 1) nthreads = 1;
+#pragma omp parallel num_threads(nthreads)
+    {
+        double* pi = (double*)malloc(sizeof(double) * V);
+        double* old = (double*)malloc(sizeof(double) * V);
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t c = 0; c < n_chains; ++c) {
+            double* p = phi + c * V;
+            memcpy(old, p, sizeof(double) * V);
+            gfo_hmc_momenta(V, seed, (uint64_t)c, traj_index, pi);
+            double dH = gfo_leapfrog(nd, L, m2, lam, p, pi, n_steps, eps);
+            uint64_t key[2] = {seed, 0};
+            uint64_t ctr[4] = {(uint64_t)c, traj_index, 0, TAG_HMC_U};
+            uint64_t w[4];
+            gfo_philox4x64_10(key, ctr, w);
+            int a = (-dH) > log(u53(w[0]));
+            if (!a) memcpy(p, old, sizeof(double) * V);
+            if (dH_out) dH_out[c] = dH;
+            if (acc_out) acc_out[c] = (uint8_t)a;
+        }
+        free(pi); free(old);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Reverse-KL loss and its gradient (Sec. 1, shifted reverse KL divergence):  */
+/* L = (1/B) sum_b [log q(phi_b) + S(phi_b)], phi_b = F^{-1}(z_b), z fixed.  */
+/* The reverse pass is the chain rule written out by hand, layer by layer.   */
+/* ------------------------------------------------------------------------ */
+
+/* Adjoint of out = conv(in): gin += W^T gout (scatter form), gW += gout (x) in, gb += gout. */
+static void conv_backward(int64_t V, int T, const int64_t* nbr, int Cin, int Cout,
+                          const double* W, const double* in, const double* gout,
+                          double* gin, double* gW, double* gb) {
+    for (int64_t n = 0; n < V; ++n) {
+        for (int o = 0; o < Cout; ++o) {
+            double g = gout[n * Cout + o];
+            if (g == 0.0) continue;
+            gb[o] += g;
+            for (int i = 0; i < Cin; ++i) {
+                for (int t = 0; t < T; ++t) {
+                    int64_t m = nbr[n * T + t];
+                    gW[((int64_t)o * Cin + i) * T + t] += g * in[m * Cin + i];
+                    if (gin) gin[m * Cin + i] += W[((int64_t)o * Cin + i) * T + t] * g;
+                }
+            }
+        }
+    }
+}
+
+int gfo_flow_loss_grad(const gfo_shape* sh, const double* w, double m2, double lam, int64_t B,
+                       const double* z, double* loss_out, double* grad_out, int32_t nthreads) {
+    if (!shape_ok(sh) || B <= 0 || !z || !loss_out || !grad_out) return -1;
+    int64_t V = ipow(sh->L, sh->nd); int T = (int)ipow(3, sh->nd);
+    int64_t P = layer_size(sh) * sh->n_layers;
+    int64_t* nbr = make_nbr(sh->nd, sh->L);
+    int* par = (int*)malloc(sizeof(int) * V);
+    for (int64_t n = 0; n < V; ++n) par[n] = parity(sh->nd, sh->L, n);
+    double* loss_b = (double*)malloc(sizeof(double) * B);
+    if (nthreads < 1) nthreads = 1;
+    double* gpart = (double*)calloc((size_t)nthreads * P, sizeof(double));
+#pragma omp parallel num_threads(nthreads)
+    {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        double* G = gpart + (int64_t)tid * P;
+        net_buf nb = net_alloc(sh, V);
+        double* xs = (double*)malloc(sizeof(double) * V * (sh->n_layers + 1)); /* x_l, l=0..N */
+        double* y = (double*)malloc(sizeof(double) * V);
+        double* gx = (double*)malloc(sizeof(double) * V);
+        double* gy = (double*)malloc(sizeof(double) * V);
+        double* g3 = (double*)malloc(sizeof(double) * V * 2);
+        double* gh2 = (double*)malloc(sizeof(double) * V * sh->c2);
+        double* gh1 = (double*)malloc(sizeof(double) * V * sh->c1);
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t b = 0; b < B; ++b) {
+            /* forward, keeping each layer input x_l */
+            memcpy(xs, z + b * V, sizeof(double) * V);
+            double logdet = 0.0;
+            for (int l = 0; l < sh->n_layers; ++l) {
+                const double* xi = xs + (int64_t)l * V;
+                double* xo = xs + (int64_t)(l + 1) * V;
+                int frozen = l & 1;
+                for (int64_t n = 0; n < V; ++n) y[n] = (par[n] == frozen) ? xi[n] : 0.0;
+                net_forward(sh, layer_ptrs(sh, w, l), 0, V, T, nbr, y, &nb);
+                for (int64_t n = 0; n < V; ++n) {
+                    if (par[n] != frozen) { xo[n] = xi[n] * exp(nb.s[n]) + nb.t[n]; logdet += nb.s[n]; }
+                    else xo[n] = xi[n];
+                }
+            }
+            const double* phi = xs + (int64_t)sh->n_layers * V;
+            double logr;
+            gfo_log_prior(V, 1, z + b * V, &logr);
+            loss_b[b] = (logr - logdet) + action_one(sh->nd, sh->L, m2, lam, phi);
+
+            /* reverse pass: dL_b/dphi = force, dL_b/dlogdet = -1 */
+            force_one(sh->nd, sh->L, m2, lam, phi, gx);
+            for (int l = sh->n_layers - 1; l >= 0; --l) {
+                const double* xi = xs + (int64_t)l * V;
+                layer_w lw = layer_ptrs(sh, w, l);
+                double* Gl = G + (int64_t)l * layer_size(sh);
+                double* gW1 = Gl;
+                double* gb1 = gW1 + sh->c1 * T;
+                double* gW2 = gb1 + sh->c1;
+                double* gb2 = gW2 + (int64_t)sh->c2 * sh->c1 * T;
+                double* gW3 = gb2 + sh->c2;
+                double* gb3 = gW3 + 2 * sh->c2 * T;
+                int frozen = l & 1;
+                for (int64_t n = 0; n < V; ++n) y[n] = (par[n] == frozen) ? xi[n] : 0.0;
+                net_forward(sh, lw, 0, V, T, nbr, y, &nb);
+                for (int64_t n = 0; n < V; ++n) {
+                    if (par[n] != frozen) {
+                        double e = exp(nb.s[n]);
+                        double gs = gx[n] * xi[n] * e - 1.0;     /* d/ds of x*e^s + t, and of -logdet */
+                        double gspre = sh->use_final_tanh ? gs * (1.0 - nb.s[n] * nb.s[n]) : gs;
+                        g3[2 * n] = gspre;
+                        g3[2 * n + 1] = gx[n];                     /* d/dt */
+                        gx[n] = gx[n] * e;                          /* d/dx_in at updated sites */
+                    } else {
+                        g3[2 * n] = 0.0; g3[2 * n + 1] = 0.0;
+                    }
+                }
+                memset(gh2, 0, sizeof(double) * V * sh->c2);
+                conv_backward(V, T, nbr, sh->c2, 2, lw.W3, nb.h2, g3, gh2, gW3, gb3);
+                for (int64_t k = 0; k < V * sh->c2; ++k)
+                    gh2[k] *= (nb.h2pre[k] > 0.0) ? 1.0 : sh->leaky_slope;
+                memset(gh1, 0, sizeof(double) * V * sh->c1);
+                conv_backward(V, T, nbr, sh->c1, sh->c2, lw.W2, nb.h1, gh2, gh1, gW2, gb2);
+                for (int64_t k = 0; k < V * sh->c1; ++k)
+                    gh1[k] *= (nb.h1pre[k] > 0.0) ? 1.0 : sh->leaky_slope;
+                memset(gy, 0, sizeof(double) * V);
+                conv_backward(V, T, nbr, 1, sh->c1, lw.W1, y, gh1, gy, gW1, gb1);
+                for (int64_t n = 0; n < V; ++n)
+                    if (par[n] == frozen) gx[n] += gy[n];          /* y = x on fixed sites only */
+            }
+        }
+        net_free(&nb); free(xs); free(y); free(gx); free(gy); free(g3); free(gh2); free(gh1);
+    }
+    double loss = 0.0;
+    for (int64_t b = 0; b < B; ++b) loss += loss_b[b];
+    *loss_out = loss / (double)B;
+    for (int64_t p = 0; p < P; ++p) {
+        double s = 0.0;
+        for (int t = 0; t < nthreads; ++t) s += gpart[(int64_t)t * P + p];
+        grad_out[p] = s / (double)B;
+    }
+    free(gpart); free(loss_b); free(par); free(nbr);
+    return 0;
+}
+
+void gfo_adam(int64_t n, double* theta, const double* g, double* m, double* v, int64_t t,
+              double lr, double beta1, double beta2, double eps) {
+    double c1 = 1.0 - pow(beta1, (double)t), c2 = 1.0 - pow(beta2, (double)t);
+    for (int64_t i = 0; i < n; ++i) {
+        m[i] = beta1 * m[i] + (1.0 - beta1) * g[i];
+        v[i] = beta2 * v[i] + (1.0 - beta2) * g[i] * g[i];
+        double mh = m[i] / c1, vh = v[i] / c2;
+        theta[i] -= lr * mh / (sqrt(vh) + eps);
+    }
+}

@@ -1,0 +1,191 @@
+"""Pins of the oracle's coupling layers, flow composition and log-det (CPU only).
+
+arXiv:2208.08903 Sec. 1: the even/odd affine coupling layer, the composition
+of N_tri layers, the Jacobian of F^{-1} and the model density P^(ML).
+
+- one coupling network against scipy.ndimage.correlate (periodic, independent
+  library routine) with torch's bf16 rounding for the BF16-emulation flags;
+- the whole flow against a brute-force numpy composition of those layers;
+- log-det against log|det| of the brute-force Jacobian (central differences,
+  numpy slogdet) on L=2,3 lattices;
+- invertibility, identity flow, translation equivariance.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import ndimage, stats
+
+import gf_inputs as gi
+
+
+def lrelu(v, a):
+    return np.where(v > 0, v, a * v)
+
+
+def scipy_net(shape, w, layer, y, round_fn=None, flags=0):
+    """s, t of one coupling network with scipy's periodic correlate."""
+    d = gi.split_layer(shape, w, layer)
+    nd, L = shape.nd, shape.L
+    grid = [L] * nd
+    ker = lambda W: W.reshape(W.shape[0], W.shape[1], *([3] * nd))
+    rw = (lambda a: a) if round_fn is None else round_fn
+
+    def conv(inp, W, b):
+        K = ker(W)
+        out = np.zeros((K.shape[0],) + tuple(grid))
+        for o in range(K.shape[0]):
+            acc = np.full(grid, b[o])
+            for i in range(K.shape[1]):
+                acc = acc + ndimage.correlate(inp[i], K[o, i], mode="wrap")
+            out[o] = acc
+        return out
+
+    W1 = rw(d["W1"]) if flags & 16 else d["W1"]
+    W2 = rw(d["W2"]) if flags & 2 else d["W2"]
+    W3 = rw(d["W3"]) if flags & 8 else d["W3"]
+    h1 = lrelu(conv(y.reshape([1] + grid), W1, d["b1"]), shape.leaky_slope)
+    if flags & 1:
+        h1 = rw(h1)
+    h2 = lrelu(conv(h1, W2, d["b2"]), shape.leaky_slope)
+    if flags & 4:
+        h2 = rw(h2)
+    st = conv(h2, W3, d["b3"])
+    s = np.tanh(st[0]) if shape.use_final_tanh else st[0]
+    return s.ravel(), st[1].ravel()
+
+
+def parity(nd, L):
+    g = np.meshgrid(*([np.arange(L)] * nd), indexing="ij")
+    return (sum(g) % 2).ravel()
+
+
+def numpy_flow(shape, w, z):
+    """Brute-force composition: layer l keeps parity l%2 fixed, updates the rest."""
+    par = parity(shape.nd, shape.L)
+    x = z.copy()
+    logdet = 0.0
+    for l in range(shape.n_layers):
+        fz = par == (l % 2)
+        s, t = scipy_net(shape, w, l, np.where(fz, x, 0.0))
+        x = np.where(fz, x, x * np.exp(s) + t)
+        logdet += s[~fz].sum()
+    return x, logdet
+
+
+SHAPES = [gi.FlowShape(2, 4, 3, 4, 5), gi.FlowShape(2, 3, 2, 3, 2),
+          gi.FlowShape(3, 3, 2, 2, 3), gi.FlowShape(2, 5, 4, 8, 8, use_final_tanh=False),
+          gi.FlowShape(3, 2, 3, 4, 4)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_coupling_net_vs_scipy(orc, shape):
+    w = gi.init_weights(shape, seed=3)
+    y = gi.random_field(shape.nd, shape.L, 1, seed=4)[0]
+    for layer in range(shape.n_layers):
+        s, t = orc.coupling_net(shape, w, layer, y)
+        rs, rt = scipy_net(shape, w, layer, y)
+        assert np.allclose(s, rs, rtol=1e-12, atol=1e-13)
+        assert np.allclose(t, rt, rtol=1e-12, atol=1e-13)
+
+
+def test_bf16_rounding_points_vs_torch(orc):
+    torch = pytest.importorskip("torch")
+
+    def rnd(a):
+        a = np.asarray(a)
+        t = torch.from_numpy(a.astype(np.float32)).to(torch.bfloat16).to(torch.float64)
+        return t.numpy().reshape(a.shape)
+
+    shape = gi.FlowShape(3, 3, 1, 8, 8)
+    w = gi.init_weights(shape, seed=8)
+    y = gi.random_field(3, 3, 1, seed=2)[0]
+    for flags in (1, 2, 4, 8, 16, 1 | 2 | 4 | 8):
+        s, t = orc.coupling_net(shape, w, 0, y, bf16_mask=flags)
+        rs, rt = scipy_net(shape, w, 0, y, round_fn=rnd, flags=flags)
+        assert np.allclose(s, rs, rtol=1e-9, atol=1e-10), flags
+        assert np.allclose(t, rt, rtol=1e-9, atol=1e-10), flags
+    s0, _ = orc.coupling_net(shape, w, 0, y, bf16_mask=0)
+    s1, _ = orc.coupling_net(shape, w, 0, y, bf16_mask=1 | 2 | 4)
+    assert not np.allclose(s0, s1, rtol=1e-6)
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_flow_vs_bruteforce_composition(orc, shape):
+    w = gi.init_weights(shape, seed=5)
+    B = 3
+    z = gi.random_field(shape.nd, shape.L, B, seed=6)
+    m2, lam = -4.0, 8.0
+    o = orc.flow_sample(shape, w, m2, lam, B, z=z)
+    for b in range(B):
+        phi, logdet = numpy_flow(shape, w, z[b])
+        assert np.allclose(o["phi"][b], phi, rtol=1e-12, atol=1e-12)
+        logr = stats.norm.logpdf(z[b]).sum()
+        assert o["logq"][b] == pytest.approx(logr - logdet, rel=1e-12, abs=1e-11)
+    S = orc.action(shape.nd, shape.L, m2, lam, o["phi"])
+    assert np.allclose(o["S"], S, rtol=1e-14)
+    assert np.allclose(o["logw"], -S - o["logq"], rtol=1e-14)
+
+
+@pytest.mark.parametrize("shape", [gi.FlowShape(2, 2, 4, 4, 4), gi.FlowShape(2, 3, 3, 4, 4),
+                                   gi.FlowShape(3, 2, 4, 3, 3), gi.FlowShape(3, 3, 2, 2, 2)])
+def test_logdet_vs_bruteforce_jacobian(orc, shape):
+    """log|det dphi/dz| by central differences + LU must equal log r(z) - log q."""
+    w = gi.init_weights(shape, seed=2)
+    z = gi.random_field(shape.nd, shape.L, 1, seed=3)[0]
+    V = shape.V
+    eps = 1e-5
+    J = np.zeros((V, V))
+    for j in range(V):
+        zp, zm = z.copy(), z.copy()
+        zp[j] += eps
+        zm[j] -= eps
+        fp = orc.flow_sample(shape, w, 0.0, 0.0, 1, z=zp[None])["phi"][0]
+        fm = orc.flow_sample(shape, w, 0.0, 0.0, 1, z=zm[None])["phi"][0]
+        J[:, j] = (fp - fm) / (2 * eps)
+    sign, logabsdet = np.linalg.slogdet(J)
+    o = orc.flow_sample(shape, w, 0.0, 0.0, 1, z=z[None])
+    logdet = orc.log_prior(z[None])[0] - o["logq"][0]
+    assert sign > 0       # exp(s) > 0 on every updated site: orientation preserving
+    assert logabsdet == pytest.approx(logdet, rel=1e-7, abs=1e-7)
+
+
+@pytest.mark.parametrize("shape", SHAPES + [gi.WORKLOADS["c1"]["shape"]])
+def test_invertibility(orc, shape):
+    w = gi.init_weights(shape, seed=0)
+    o = orc.flow_sample(shape, w, -4.0, 8.0, 5, seed=9, counter0=3)
+    z, logq = orc.flow_logq(shape, w, o["phi"])
+    assert np.allclose(z, o["z"], rtol=0, atol=1e-12)
+    assert np.allclose(logq, o["logq"], rtol=1e-12, atol=1e-10)
+
+
+def test_identity_flow(orc):
+    shape = gi.WORKLOADS["c1"]["shape"]
+    w = gi.zero_head(shape, gi.init_weights(shape))
+    o = orc.flow_sample(shape, w, -4.0, 8.0, 4, seed=1)
+    assert np.array_equal(o["phi"], o["z"])
+    assert np.allclose(o["logq"], stats.norm.logpdf(o["z"]).sum(1), rtol=1e-13)
+
+
+@pytest.mark.parametrize("nd,L,shift", [(2, 4, (0, 2)), (2, 6, (1, 1)), (3, 4, (2, 0, 0)),
+                                        (3, 4, (1, 0, 1))])
+def test_translation_equivariance(orc, nd, L, shift):
+    """Parity-preserving periodic shifts commute with the flow."""
+    shape = gi.FlowShape(nd, L, 4, 4, 4)
+    w = gi.init_weights(shape, seed=1)
+    z = gi.random_field(nd, L, 1, seed=2)
+    o = orc.flow_sample(shape, w, -4.0, 8.0, 1, z=z)
+    zs = np.roll(z.reshape([L] * nd), shift, axis=tuple(range(nd))).reshape(1, -1)
+    os_ = orc.flow_sample(shape, w, -4.0, 8.0, 1, z=zs)
+    ref = np.roll(o["phi"].reshape([L] * nd), shift, axis=tuple(range(nd))).ravel()
+    assert np.allclose(os_["phi"][0], ref, rtol=1e-12, atol=1e-12)
+    assert os_["logq"][0] == pytest.approx(o["logq"][0], rel=1e-12)
+
+
+def test_prior_counter_selects_configuration(orc):
+    """Configuration b of a call with counter0=c equals configuration 0 of counter0=c+b."""
+    shape = gi.WORKLOADS["c1"]["shape"]
+    w = gi.init_weights(shape)
+    a = orc.flow_sample(shape, w, -4.0, 8.0, 6, seed=4, counter0=10)
+    b = orc.flow_sample(shape, w, -4.0, 8.0, 1, seed=4, counter0=14)
+    assert np.array_equal(a["phi"][4], b["phi"][0])
