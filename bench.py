@@ -1,0 +1,358 @@
+"""Benchmark of the flow sampler's hot path on GB300.
+
+One step = one batch through the whole path: prior -> coupling stack ->
+log q, phi^4 action, log w (one fused kernel) -> Metropolis-Hastings chain
+over the batch's proposals (continuing one chain across steps).
+
+Default workload: 3D phi^4, L=16 (4096 sites), m2=-6, lam=5, RealNVP with 16
+checkerboard coupling layers, s/t nets conv3x3x3 1->32->32->2, batch 4096,
+random-init weights (seed 0), synthetic Philox prior; metric = flow
+configurations per second through sample + log q + S + MH.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+on the same workload instead (bounded samples per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import gf_inputs as gi  # noqa: E402
+
+L2_BYTES = 129 * 1024 * 1024
+METRIC = "flow configs/sec (sample+logq+S+MH)"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+def flops_per_config(shape) -> float:
+    """Algorithmic forward FLOPs of one configuration: conv1 on the taps that
+    can be non-zero (fixed-site neighbours), conv2 dense, conv3 at the updated
+    sites only."""
+    V, T, C1, C2 = shape.V, shape.taps, shape.c1, shape.c2
+    nz = 13.5 if shape.nd == 3 else 4.5
+    per_layer = 2 * V * C1 * nz + 2 * V * C1 * C2 * T + 2 * (V / 2) * 2 * C2 * T
+    return per_layer * shape.n_layers
+
+
+def fp32_alu_peak_tflops(n_sm: int, mhz: float) -> float:
+    # 128 FP32 FMA lanes per SM, 2 FLOP per FMA
+    return n_sm * 128 * 2 * mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.gpu = gpu_index
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = [r.split(",") for r in out.strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i]
+                          and "Not" not in r[5 + i]})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup(want: int):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if _cuda_ok() else "gloo")
+    return rank, world, local
+
+
+def _cuda_ok():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+def counter_base(rank: int) -> int:
+    """Disjoint prior counters per rank (2^40 configurations each)."""
+    return rank << 40
+
+
+def max_over_ranks(v: float, world: int) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if _cuda_ok() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# --------------------------------------------------------------------------- GPU arm
+def bench_gpu(args, rank, world, local):
+    import torch
+    import paper_2208_08903_gb300 as P
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    W = gi.WORKLOADS[args.workload]
+    shape, phi4, B = W["shape"], W["phi4"], args.batch or W["batch"]
+    prec = args.precision
+    if prec == "auto":
+        prec = "fp32"
+    flow = P.Flow(shape, gi.init_weights(shape, seed=0), precision=prec)
+    V = shape.V
+    out = P.SampleResult(phi=torch.empty(B, V, device=dev),
+                         logq=torch.empty(B, device=dev, dtype=torch.float64),
+                         S=torch.empty(B, device=dev, dtype=torch.float64),
+                         logw=torch.empty(B, device=dev, dtype=torch.float64))
+    state = P.new_mh_state(seed=12345, stream_id=rank, device=dev)
+    idx = torch.empty(B, device=dev, dtype=torch.int64)
+    acc = torch.empty(B, device=dev, dtype=torch.uint8)
+    ws = torch.empty(max(P.mh_chain_workspace_bytes(B) // 8, 1), device=dev, dtype=torch.float64)
+    flush = torch.empty(2 * L2_BYTES // 4, device=dev, dtype=torch.float32)
+    stream = torch.cuda.current_stream()
+    seed = 2024
+    c0 = counter_base(rank)
+
+    def step(i, z=None):
+        flow.sample(B, seed=seed, counter0=c0 + i * B, phi4=phi4, z=z, out=out)
+        P.mh_chain(state, out.logw, workspace=ws, chain_idx=idx, acc=acc)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    assert P.device_status() == 0
+
+    # device-timed steps: inputs resident, L2 flushed between steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        e0, e1, e2 = ev[i]
+        e0.record(stream)
+        flow.sample(B, seed=seed, counter0=c0 + (args.warmup + i) * B, phi4=phi4, out=out)
+        e1.record(stream)
+        P.mh_chain(state, out.logw, workspace=ws, chain_idx=idx, acc=acc)
+        e2.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier(world)
+    step_ms = [e0.elapsed_time(e2) for e0, e1, e2 in ev]
+    flow_ms = [e0.elapsed_time(e1) for e0, e1, e2 in ev]
+    total_ms = max_over_ranks(sum(step_ms), world)
+    st = P.read_mh_state(state)
+
+    # end-to-end through the public API with host buffers (pinned), copies timed
+    z_host = torch.from_numpy(gi.random_field(shape.nd, shape.L, B, seed=99).astype(np.float32)).pin_memory()
+    phi_host = torch.empty(B, V, dtype=torch.float32).pin_memory()
+    small_host = torch.empty(4, B, dtype=torch.float64).pin_memory()
+    idx_host = torch.empty(B, dtype=torch.int64).pin_memory()
+    acc_host = torch.empty(B, dtype=torch.uint8).pin_memory()
+    z_dev = torch.empty(B, V, device=dev)
+    e2e_ms = []
+    n_e2e = max(3, min(args.steps, 10))
+    for i in range(n_e2e + 1):
+        flush.fill_(float(i))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        z_dev.copy_(z_host, non_blocking=True)
+        step(10**6 + i, z=z_dev)
+        phi_host.copy_(out.phi, non_blocking=True)
+        small_host[0].copy_(out.logq, non_blocking=True)
+        small_host[1].copy_(out.S, non_blocking=True)
+        small_host[2].copy_(out.logw, non_blocking=True)
+        idx_host.copy_(idx, non_blocking=True)
+        acc_host.copy_(acc, non_blocking=True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if i > 0:                 # first iteration warms the pinned paths
+            e2e_ms.append(a.elapsed_time(b))
+    e2e_total = max_over_ranks(sum(e2e_ms), world)
+    h2d = B * V * 4
+    d2h = B * V * 4 + 3 * B * 8 + B * 8 + B
+
+    pk, pk_kind = peaks()
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    fpc = flops_per_config(shape)
+    flow_avg_s = float(np.mean(flow_ms)) / 1e3
+    achieved = fpc * B / flow_avg_s / 1e12
+    if prec == "bf16":
+        peak = pk.get("bf16_tflops_sustained", 1700.0)
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_kind": f"bf16 dense sustained, {pk_kind}"}
+    else:
+        mhz = pk.get("sm_max_mhz", 2070.0)
+        peak = fp32_alu_peak_tflops(n_sm, mhz)
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_kind": f"FP32 FFMA: {n_sm} SM x 128 lanes x 2 FLOP x {mhz:.0f} MHz (derived)"}
+    roof["kernel"] = "flow_fp32_kernel" if prec == "fp32" else "flow_bf16_kernel"
+    roof["flops_per_config"] = fpc
+    value = world * B * args.steps / (total_ms / 1e3)
+    res = {
+        "metric": METRIC, "value": value, "unit": "configs/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if prec == "fp32" else "bf16",
+        "data": "synthetic (seeded Philox prior, Kaiming-uniform random-init weights seed 0)",
+        "config": {"workload": f"{args.workload}: {shape.nd}D phi^4 L={shape.L} m2={phi4.m2} lam={phi4.lam}, "
+                               f"RealNVP {shape.n_layers} couplings, conv 1->{shape.c1}->{shape.c2}->2, "
+                               f"batch {B}, MH chain over the batch",
+                   "batch": B, "nd": shape.nd, "L": shape.L, "n_layers": shape.n_layers,
+                   "hidden": [shape.c1, shape.c2], "precision": prec,
+                   "l2": "flushed between timed steps (2x L2 buffer write)",
+                   "parallelism": f"dp{world} (independent batches, one MH chain per rank)"},
+        "e2e": {"value": world * B * n_e2e / (e2e_total / 1e3), "unit": "configs/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": 3 * args.steps,
+        "roofline": roof,
+        "clocks": clk,
+        "mh": {"steps": int(st.step), "accepted": int(st.n_acc),
+               "acceptance": st.n_acc / max(1, st.step - 1)},
+        "flow_kernel_ms": float(np.mean(flow_ms)),
+    }
+    return res
+
+
+# --------------------------------------------------------------------------- CPU oracle
+def oracle_rate(shape, phi4, n_cfg, seed=2024, counter0=0):
+    import oracle
+    nthr = oracle.default_threads()
+    w = gi.init_weights(shape, seed=0)
+    t0 = time.perf_counter()
+    out = oracle.flow_sample(shape, w, phi4.m2, phi4.lam, n_cfg, seed=seed, counter0=counter0,
+                             nthreads=nthr)
+    st = oracle.new_mh_state(12345)
+    oracle.mh_chain(st, out["logw"])
+    dt = time.perf_counter() - t0
+    return n_cfg / dt, dt, nthr
+
+
+def cpu_sample_size(shape, phi4, target_s):
+    r, dt, nthr = oracle_rate(shape, phi4, 1)
+    per_cfg_serial = dt
+    n = max(1, int(target_s * nthr / max(per_cfg_serial, 1e-6)))
+    return min(n, 4096), nthr
+
+
+def bench_cpu_baseline(args):
+    W = gi.WORKLOADS[args.workload]
+    shape, phi4 = W["shape"], W["phi4"]
+    n, nthr = cpu_sample_size(shape, phi4, target_s=args.cpu_seconds)
+    rate, dt, nthr = oracle_rate(shape, phi4, n, counter0=7)
+    return {"value": rate, "unit": "configs/s", "cores": nthr, "kind": "oracle",
+            "sample": f"{n} configurations of the same workload (FP64 C oracle, OpenMP over "
+                      f"configurations) + MH over them, {dt:.1f} s"}
+
+
+def bench_reference(args, rank, world):
+    if rank != 0:
+        return None
+    W = gi.WORKLOADS[args.workload]
+    shape, phi4 = W["shape"], W["phi4"]
+    budget = max(20.0, min(150.0, args.ref_seconds))
+    per_step = budget / (args.steps + args.warmup)
+    n, nthr = cpu_sample_size(shape, phi4, target_s=per_step)
+    times = []
+    for i in range(args.warmup + args.steps):
+        r, dt, _ = oracle_rate(shape, phi4, n, counter0=1000 + i * n)
+        if i >= args.warmup:
+            times.append(dt)
+    value = n * args.steps / sum(times)
+    sample = f"{n} configurations per step (FP64 C oracle on {nthr} host threads) + MH over them"
+    return {"metric": METRIC, "value": value, "unit": "configs/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": args.workload, "batch_per_step": n},
+            "cpu_baseline": {"value": value, "unit": "configs/s", "cores": nthr, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "configs/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gfflow", choices=["gfflow", "reference"])
+    ap.add_argument("--workload", default="c3", choices=["c1", "c3"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "bf16"])
+    ap.add_argument("--batch", type=int, default=0)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-seconds", type=float, default=120.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank, world, local = dist_setup(args.gpus)
+    if args.impl == "reference":
+        res = bench_reference(args, rank, world)
+        if rank == 0:
+            print(json.dumps(res), flush=True)
+        return
+    res = bench_gpu(args, rank, world, local)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            res["cpu_baseline"] = bench_cpu_baseline(args)
+        else:
+            res["cpu_baseline"] = None
+        print(json.dumps(res), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,202 @@
+/*
+ * gfflow.h -- C ABI of the GB300 flow-based sampler for lattice phi^4 theory
+ * (method of Tomiya & Terasaki, "GomalizingFlow.jl", arXiv:2208.08903).
+ *
+ * Conventions for every call
+ *   - Fields are [B][V] row-major, V = L^nd sites, site index
+ *     n = x + L*(y + L*z) (x fastest), periodic boundaries in every axis.
+ *   - Pointers named d_* / "device" are device memory owned by the caller;
+ *     "host" pointers are host memory owned by the caller.  The library owns
+ *     only what gf_flow_create allocates (the device copy of the weights).
+ *   - Every compute call is asynchronous on the given stream and launches
+ *     only this library's kernels.  Argument errors return GF_EINVAL before
+ *     anything is launched; a failed launch returns GF_ECUDA.  Errors a kernel
+ *     detects (a bounded wait that ran out, a corrupt schedule) are recorded
+ *     in a device status word read by gf_device_status; no call traps.
+ *   - Random numbers: Philox4x64-10 (Salmon et al., SC'11), keyed by the
+ *     caller's seed, one counter sub-space per purpose, so results do not
+ *     depend on launch shape or batching.
+ */
+#ifndef GFFLOW_H
+#define GFFLOW_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GF_OK = 0,
+    GF_EINVAL = -1,        /* bad argument (null pointer, size, shape)            */
+    GF_ENOMEM = -2,        /* device allocation failed (gf_flow_create only)      */
+    GF_ECUDA = -3,         /* a CUDA runtime call or launch failed                */
+    GF_EUNSUPPORTED = -4,  /* valid request this build has no kernel for          */
+    GF_ETIMEOUT = -5,      /* reported through gf_device_status                   */
+    GF_EDEVICE = -6        /* reported through gf_device_status                   */
+} gf_status;
+
+typedef enum {
+    GF_PREC_FP32 = 0,             /* FP32 convolutions, FP64 sums                  */
+    GF_PREC_BF16CONV_FP64RED = 1  /* BF16 tensor-core conv2, FP32 accumulate,
+                                     FP64 sums (3D, C=32 only)                    */
+} gf_precision;
+
+/* Flow shape (paper Sec. 3, model parameters: n_layers, hidden_sizes,
+ * kernel_size, inC=1, outC=2, use_final_tanh, use_bn=false).
+ * Supported: nd in {2,3}; c_hidden1 == c_hidden2 in {8,16,32}; ksize == 3;
+ * 2 <= L with L^nd <= 65536 and L even (checkerboard is a bipartition). */
+typedef struct {
+    int32_t nd, L, n_layers, c_hidden1, c_hidden2, ksize, use_final_tanh;
+    double leaky_slope;   /* LeakyReLU slope after conv1 and conv2 */
+} gf_flow_shape;
+
+/* phi^4 couplings (paper Sec. 1, action S[phi] and potential V[phi]):
+ * S = sum_n [ sum_mu phi(n)(2 phi(n) - phi(n+mu) - phi(n-mu)) + m2 phi^2 + lam phi^4 ]. */
+typedef struct { double m2, lam; } gf_phi4;
+
+typedef struct gf_flow gf_flow;   /* opaque; owns the device copy of the weights */
+
+/* MH chain state.  Lives in DEVICE memory (caller-allocated, 48 bytes,
+ * 8-byte aligned) so successive calls continue one chain without a host
+ * round trip.  Initialise with logw_cur=0, idx_cur=0, n_acc=0, step=0. */
+typedef struct {
+    double   logw_cur;   /* log weight of the current state                   */
+    int64_t  idx_cur;    /* global proposal index of the current state        */
+    int64_t  n_acc;      /* accepted proposals among steps 1..step-1          */
+    int64_t  step;       /* proposals consumed so far (global step counter)   */
+    uint64_t seed, stream_id;   /* Philox key of this chain's uniforms        */
+} gf_mh_state;
+
+/* ---------------------------------------------------------------------- */
+/* Flow object                                                             */
+/* ---------------------------------------------------------------------- */
+
+/* Copies host FP64 weights (canonical layout, one block per layer in the
+ * order the layers act on the prior sample: W1[c1][1][T] b1[c1]
+ * W2[c2][c1][T] b2[c2] W3[2][c2][T] b3[2], T = 3^nd taps ordered
+ * (kz,ky,kx) resp. (ky,kx), offset k-1; conv3 channel 0 is s, 1 is t) to the
+ * device in the kernels' layouts.  Synchronises `stream` before returning.
+ * *out is set only on GF_OK; release with gf_flow_destroy. */
+gf_status gf_flow_create(const gf_flow_shape* shape, const double* weights_host,
+                         gf_precision prec, cudaStream_t stream, gf_flow** out);
+gf_status gf_flow_destroy(gf_flow* flow);
+/* Number of canonical parameters. */
+int64_t   gf_flow_n_params(const gf_flow* flow);
+/* Replaces the weights from a DEVICE FP32 array in canonical layout
+ * (asynchronous on `stream`). */
+gf_status gf_flow_set_weights_device(gf_flow* flow, const float* d_weights, cudaStream_t stream);
+/* Copies the current FP32 canonical weights into d_weights_out [n_params]. */
+gf_status gf_flow_get_weights_device(const gf_flow* flow, float* d_weights_out, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------- */
+/* Sampling: phi = F^{-1}(z) with log q, S and log w (paper Sec. 1: prior  */
+/* sample, untrivialising map, Jacobian, model density P^(ML)).            */
+/* ---------------------------------------------------------------------- */
+
+/* For b < B: z_b is d_z_in[b] when d_z_in != NULL, else drawn in-kernel from
+ * philox(key=(seed,0), ctr=(counter0+b, j, 0, 1)) for sites 4j..4j+3 (FP32
+ * Box-Muller).  Layer l (0-based) keeps sites with (x+y+z)%2 == l%2 fixed
+ * and maps the others by x -> x*exp(s)+t, s=tanh(conv-net(fixed sites)).
+ * Writes d_phi_out[b] (FP32), d_logq_out[b] = log r(z_b) - sum s (FP64).
+ * d_z_out (nullable) receives z.  When phi4 != NULL, d_S_out and
+ * d_logw_out (each nullable) receive S(phi_b) and -S - log q (FP64);
+ * when phi4 == NULL both must be NULL. */
+gf_status gf_flow_sample(const gf_flow* flow, const gf_phi4* phi4, int64_t B,
+                         uint64_t seed, uint64_t counter0, const float* d_z_in,
+                         float* d_z_out, float* d_phi_out, double* d_logq_out,
+                         double* d_S_out, double* d_logw_out, cudaStream_t stream);
+
+/* Trivialising direction z = F(phi) (paper Sec. 1, F_theta and its
+ * bijectivity): layers in reverse order, x -> (x - t)*exp(-s).
+ * d_logq_out[b] = log r(z_b) - sum s.  d_z_out nullable. */
+gf_status gf_flow_logq(const gf_flow* flow, int64_t B, const float* d_phi_in,
+                       float* d_z_out, double* d_logq_out, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------- */
+/* Action (paper Sec. 1)                                                    */
+/* ---------------------------------------------------------------------- */
+
+/* d_S_out[b] = S(phi_b) in FP64 for d_phi [B][L^nd], FP32 (phi_is_fp64=0)
+ * or FP64 (phi_is_fp64=1).  Each site term is formed in FP64. */
+gf_status gf_phi4_action(int32_t nd, int32_t L, const gf_phi4* phi4, int64_t B,
+                         const void* d_phi, int32_t phi_is_fp64, double* d_S_out,
+                         cudaStream_t stream);
+/* d_F_out = dS/dphi = 2 sum_mu (2phi - phi(n+mu) - phi(n-mu)) + 2 m2 phi
+ * + 4 lam phi^3, FP64 in and out ([B][V]). */
+gf_status gf_phi4_force(int32_t nd, int32_t L, const gf_phi4* phi4, int64_t B,
+                        const double* d_phi, double* d_F_out, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------- */
+/* Metropolis-Hastings independence chain (paper Sec. 1: flow proposals   */
+/* corrected by the MH test with the Jacobian)                             */
+/* ---------------------------------------------------------------------- */
+
+/* Bytes of device workspace gf_mh_chain needs for n proposals. */
+size_t gf_mh_chain_workspace_bytes(int64_t n);
+
+/* Consumes proposals k = 0..n-1 with log weights d_logw[k] (FP64, log p -
+ * log q).  Global step g = state.step + k: g == 0 is accepted
+ * unconditionally; otherwise accept iff d_logw[k] - logw_cur > log u_g,
+ * u_g = (2*(w>>12)+1)*2^-53, w = word 0 of philox(key=(seed, stream_id),
+ * ctr=(g, 0, 0, 2)).  Writes d_chain_idx_out[k] = global index of the state
+ * after step g and d_acc_out[k] in {0,1} (each nullable); updates
+ * *d_state in place.  d_workspace: >= gf_mh_chain_workspace_bytes(n) bytes
+ * of device memory, 8-byte aligned, owned by the caller, free after the
+ * call's work on `stream` completes. */
+gf_status gf_mh_chain(gf_mh_state* d_state, int64_t n, const double* d_logw,
+                      int64_t* d_chain_idx_out, uint8_t* d_acc_out,
+                      void* d_workspace, size_t workspace_bytes, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------- */
+/* HMC comparison sampler (paper Sec. 2.2: HMC for the same theory)        */
+/* ---------------------------------------------------------------------- */
+
+/* One trajectory per chain, FP64.  H = 1/2 sum pi^2 + S; momenta from
+ * philox(key=(seed,0), ctr=(chain, traj_index, j, 3)) (FP64 Box-Muller);
+ * leapfrog: half kick, n_steps x (drift eps, kick eps) with the last kick
+ * halved; accept iff -dH > log u, u from ctr=(chain, traj_index, 0, 4).
+ * d_phi [n_chains][V] is updated in place (restored on reject);
+ * d_dH_out, d_acc_out nullable.  Supported: V <= 4096. */
+gf_status gf_hmc_trajectory(int32_t nd, int32_t L, const gf_phi4* phi4, int64_t n_chains,
+                            double* d_phi, int32_t n_steps, double eps, uint64_t seed,
+                            uint64_t traj_index, double* d_dH_out, uint8_t* d_acc_out,
+                            cudaStream_t stream);
+
+/* ---------------------------------------------------------------------- */
+/* Reverse-KL self-training (paper Sec. 1, shifted reverse KL divergence;  */
+/* Sec. 3, training loop with Adam)                                        */
+/* ---------------------------------------------------------------------- */
+
+/* Bytes of device workspace gf_flow_train_step needs for batch B. */
+size_t gf_train_workspace_bytes(const gf_flow* flow, int64_t B);
+
+/* loss = (1/B) sum_b [log q(phi_b) + S(phi_b)], phi_b = F^{-1}(z_b), z_b as
+ * in gf_flow_sample.  Writes *d_loss_out (FP64 device scalar) and, when
+ * d_grad_out != NULL, dloss/dtheta in canonical order (FP32 [n_params]).
+ * When lr > 0 also applies one Adam step (Kingma & Ba; bias-corrected,
+ * 1-based step adam_t) to the flow's weights using the caller's FP32 moment
+ * buffers d_adam_m, d_adam_v [n_params].  d_workspace as for gf_mh_chain. */
+gf_status gf_flow_train_step(gf_flow* flow, const gf_phi4* phi4, int64_t B, uint64_t seed,
+                             uint64_t counter0, const float* d_z_in, double* d_loss_out,
+                             float* d_grad_out, float lr, float beta1, float beta2,
+                             float adam_eps, float* d_adam_m, float* d_adam_v,
+                             int64_t adam_t, void* d_workspace, size_t workspace_bytes,
+                             cudaStream_t stream);
+
+/* ---------------------------------------------------------------------- */
+/* Status                                                                  */
+/* ---------------------------------------------------------------------- */
+
+/* Synchronises `stream`, returns the device status word (0 = no error,
+ * else a negative gf_status) and clears it. */
+gf_status gf_device_status(cudaStream_t stream, int32_t* status_out);
+/* Human-readable name of a status code (static string). */
+const char* gf_status_string(int32_t status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GFFLOW_H */

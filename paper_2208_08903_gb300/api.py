@@ -1,0 +1,232 @@
+"""Torch-facing binding of libgfflow (argument marshalling only).
+
+Every function here validates dtypes/devices, allocates output tensors with
+torch and calls one C-ABI entry point on torch's current CUDA stream.  All
+arithmetic runs in the library's kernels.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+
+import torch
+
+from . import _abi
+
+
+def _stream(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+def _need(t, dtype, name, numel=None):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA {dtype} tensor")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, has {t.numel()}")
+
+
+def _phi4(phi4):
+    if phi4 is None:
+        return None
+    m2, lam = (phi4.m2, phi4.lam) if hasattr(phi4, "m2") else phi4
+    return _abi.Phi4C(float(m2), float(lam))
+
+
+@dataclasses.dataclass
+class SampleResult:
+    phi: torch.Tensor
+    logq: torch.Tensor
+    S: torch.Tensor | None = None
+    logw: torch.Tensor | None = None
+    z: torch.Tensor | None = None
+
+
+class Flow:
+    """A RealNVP coupling stack resident on the current CUDA device.
+
+    shape: any object with nd, L, n_layers, c1, c2, use_final_tanh, leaky_slope.
+    weights: FP64 numpy array (or CPU tensor) in canonical layout.
+    precision: "fp32" or "bf16" (BF16 tensor-core conv2, FP64 sums).
+    """
+
+    def __init__(self, shape, weights, precision: str = "fp32"):
+        lib = _abi.load()
+        self.shape = shape
+        self.V = shape.L ** shape.nd
+        sh = _abi.FlowShapeC(shape.nd, shape.L, shape.n_layers, shape.c1, shape.c2, 3,
+                             1 if shape.use_final_tanh else 0, float(shape.leaky_slope))
+        w = torch.as_tensor(weights, dtype=torch.float64).contiguous().cpu()
+        prec = {"fp32": _abi.GF_PREC_FP32, "bf16": _abi.GF_PREC_BF16CONV_FP64RED}[precision]
+        self.precision = precision
+        h = C.c_void_p()
+        _abi.check("gf_flow_create", lib.gf_flow_create(C.byref(sh), w.data_ptr(), prec,
+                                                         _stream(), C.byref(h)))
+        self._h = h
+        self._lib = lib
+        self.n_params = int(lib.gf_flow_n_params(h))
+        if self.n_params != w.numel():
+            raise ValueError(f"weights have {w.numel()} entries, the shape needs {self.n_params}")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.gf_flow_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def sample(self, B: int, seed: int = 0, counter0: int = 0, phi4=None, z=None,
+               return_z: bool = False, out: SampleResult | None = None) -> SampleResult:
+        dev = torch.device("cuda", torch.cuda.current_device())
+        V = self.V
+        if z is not None:
+            _need(z, torch.float32, "z", B * V)
+        if out is None:
+            out = SampleResult(phi=torch.empty(B, V, device=dev),
+                               logq=torch.empty(B, device=dev, dtype=torch.float64))
+            if phi4 is not None:
+                out.S = torch.empty(B, device=dev, dtype=torch.float64)
+                out.logw = torch.empty(B, device=dev, dtype=torch.float64)
+            if return_z:
+                out.z = torch.empty(B, V, device=dev)
+        p = _phi4(phi4)
+        _abi.check("gf_flow_sample", self._lib.gf_flow_sample(
+            self._h, C.byref(p) if p is not None else None, B, seed & (2**64 - 1),
+            counter0 & (2**64 - 1), _ptr(z), _ptr(out.z), _ptr(out.phi), _ptr(out.logq),
+            _ptr(out.S), _ptr(out.logw), _stream()))
+        return out
+
+    def logq(self, phi: torch.Tensor, return_z: bool = False):
+        B = phi.shape[0]
+        _need(phi, torch.float32, "phi", B * self.V)
+        logq = torch.empty(B, device=phi.device, dtype=torch.float64)
+        z = torch.empty_like(phi) if return_z else None
+        _abi.check("gf_flow_logq", self._lib.gf_flow_logq(self._h, B, _ptr(phi), _ptr(z),
+                                                          _ptr(logq), _stream()))
+        return (z, logq) if return_z else logq
+
+    def get_weights(self) -> torch.Tensor:
+        w = torch.empty(self.n_params, device="cuda", dtype=torch.float32)
+        _abi.check("gf_flow_get_weights_device",
+                   self._lib.gf_flow_get_weights_device(self._h, _ptr(w), _stream()))
+        return w
+
+    def set_weights(self, w: torch.Tensor):
+        _need(w, torch.float32, "w", self.n_params)
+        _abi.check("gf_flow_set_weights_device",
+                   self._lib.gf_flow_set_weights_device(self._h, _ptr(w), _stream()))
+
+    def train_workspace_bytes(self, B: int) -> int:
+        return int(self._lib.gf_train_workspace_bytes(self._h, B))
+
+    def train_step(self, B: int, phi4, seed: int = 0, counter0: int = 0, z=None, lr: float = 0.0,
+                   adam_m=None, adam_v=None, adam_t: int = 0, beta1=0.9, beta2=0.999,
+                   adam_eps=1e-8, grad: bool = True, workspace: torch.Tensor | None = None):
+        """Returns (loss [1] FP64 tensor, grad [n_params] FP32 tensor or None)."""
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if z is not None:
+            _need(z, torch.float32, "z", B * self.V)
+        nbytes = self.train_workspace_bytes(B)
+        if workspace is None or workspace.numel() < nbytes:
+            workspace = torch.empty(max(nbytes, 1), device=dev, dtype=torch.uint8)
+        loss = torch.empty(1, device=dev, dtype=torch.float64)
+        g = torch.empty(self.n_params, device=dev, dtype=torch.float32) if grad else None
+        if lr > 0:
+            _need(adam_m, torch.float32, "adam_m", self.n_params)
+            _need(adam_v, torch.float32, "adam_v", self.n_params)
+        p = _phi4(phi4)
+        _abi.check("gf_flow_train_step", self._lib.gf_flow_train_step(
+            self._h, C.byref(p), B, seed, counter0, _ptr(z), _ptr(loss), _ptr(g), float(lr),
+            float(beta1), float(beta2), float(adam_eps), _ptr(adam_m), _ptr(adam_v), int(adam_t),
+            _ptr(workspace), workspace.numel(), _stream()))
+        return loss, g
+
+
+def phi4_action(nd: int, L: int, phi4, phi: torch.Tensor, out: torch.Tensor | None = None):
+    if phi.dtype not in (torch.float32, torch.float64):
+        raise ValueError("phi must be float32 or float64")
+    B = phi.shape[0]
+    _need(phi, phi.dtype, "phi", B * L**nd)
+    if out is None:
+        out = torch.empty(B, device=phi.device, dtype=torch.float64)
+    p = _phi4(phi4)
+    _abi.check("gf_phi4_action", _abi.load().gf_phi4_action(
+        nd, L, C.byref(p), B, _ptr(phi), 1 if phi.dtype == torch.float64 else 0, _ptr(out),
+        _stream()))
+    return out
+
+
+def phi4_force(nd: int, L: int, phi4, phi: torch.Tensor):
+    B = phi.shape[0]
+    _need(phi, torch.float64, "phi", B * L**nd)
+    out = torch.empty_like(phi)
+    p = _phi4(phi4)
+    _abi.check("gf_phi4_force", _abi.load().gf_phi4_force(nd, L, C.byref(p), B, _ptr(phi),
+                                                          _ptr(out), _stream()))
+    return out
+
+
+def new_mh_state(seed: int, stream_id: int = 0, device=None) -> torch.Tensor:
+    """Device-resident gf_mh_state (48 bytes) as an int64[6] tensor."""
+    st = _abi.MHStateC(0.0, 0, 0, 0, seed, stream_id)
+    raw = torch.frombuffer(bytearray(bytes(st)), dtype=torch.int64).clone()
+    return raw.to(device or torch.device("cuda", torch.cuda.current_device()))
+
+
+def read_mh_state(state: torch.Tensor) -> _abi.MHStateC:
+    b = state.detach().cpu().contiguous().numpy().tobytes()
+    return _abi.MHStateC.from_buffer_copy(b)
+
+
+def mh_chain_workspace_bytes(n: int) -> int:
+    return int(_abi.load().gf_mh_chain_workspace_bytes(n))
+
+
+def mh_chain(state: torch.Tensor, logw: torch.Tensor, workspace: torch.Tensor | None = None,
+             chain_idx: torch.Tensor | None = None, acc: torch.Tensor | None = None):
+    _need(state, torch.int64, "state", 6)
+    n = logw.numel()
+    _need(logw, torch.float64, "logw", n)
+    if chain_idx is None:
+        chain_idx = torch.empty(n, device=logw.device, dtype=torch.int64)
+    if acc is None:
+        acc = torch.empty(n, device=logw.device, dtype=torch.uint8)
+    nbytes = mh_chain_workspace_bytes(n)
+    if workspace is None or workspace.numel() * workspace.element_size() < nbytes:
+        workspace = torch.empty(max(nbytes // 8, 1), device=logw.device, dtype=torch.float64)
+    _abi.check("gf_mh_chain", _abi.load().gf_mh_chain(
+        _ptr(state), n, _ptr(logw), _ptr(chain_idx), _ptr(acc), _ptr(workspace),
+        workspace.numel() * workspace.element_size(), _stream()))
+    return chain_idx, acc
+
+
+def hmc_trajectory(nd: int, L: int, phi4, phi: torch.Tensor, n_steps: int, eps: float,
+                   seed: int, traj_index: int):
+    """Updates phi [n_chains][V] (FP64) in place; returns (dH, acc)."""
+    n = phi.shape[0]
+    _need(phi, torch.float64, "phi", n * L**nd)
+    dH = torch.empty(n, device=phi.device, dtype=torch.float64)
+    acc = torch.empty(n, device=phi.device, dtype=torch.uint8)
+    p = _phi4(phi4)
+    _abi.check("gf_hmc_trajectory", _abi.load().gf_hmc_trajectory(
+        nd, L, C.byref(p), n, _ptr(phi), n_steps, eps, seed, traj_index, _ptr(dH), _ptr(acc),
+        _stream()))
+    return dH, acc
+
+
+def device_status(stream=None) -> int:
+    v = C.c_int32(0)
+    _abi.check("gf_device_status", _abi.load().gf_device_status(_stream(stream), C.byref(v)))
+    return v.value

@@ -1,0 +1,149 @@
+// gf_action.cu -- standalone phi^4 action and force (paper arXiv:2208.08903
+// Sec. 1: S = sum_n [-phi(n) Lap phi(n) + m2 phi^2 + lam phi^4], periodic
+// lattice Laplacian).
+//
+// HBM-bound: each CTA stages one configuration at a time in shared memory
+// with 16-byte loads (grid-stride over configurations), evaluates the site
+// terms in FP64 from shared memory and reduces them in a fixed order.
+#include <algorithm>
+
+#include "gf_common.cuh"
+
+namespace gf {
+namespace {
+
+constexpr int kActThreads = 256;
+
+__device__ __forceinline__ int wrapi(int v, int L) { return v < 0 ? v + L : (v >= L ? v - L : v); }
+
+template <typename T>
+__device__ __forceinline__ void stage(const T* __restrict__ g, T* s, int V) {
+    // 16-byte vector path when the configuration is 16-byte aligned.
+    constexpr int per = 16 / sizeof(T);
+    if ((reinterpret_cast<uintptr_t>(g) & 15) == 0 && V % per == 0) {
+        const int4* g4 = reinterpret_cast<const int4*>(g);
+        int4* s4 = reinterpret_cast<int4*>(s);
+        for (int i = threadIdx.x; i < V / per; i += blockDim.x) s4[i] = __ldg(g4 + i);
+    } else {
+        for (int i = threadIdx.x; i < V; i += blockDim.x) s[i] = g[i];
+    }
+}
+
+// Sum over mu of (2 phi(n) - phi(n+mu) - phi(n-mu)) in FP64.
+template <typename T>
+__device__ __forceinline__ double lap_minus(const T* p, int n, int nd, int L) {
+    const int xc = n % L, yc = (n / L) % L;
+    const double c = (double)p[n];
+    double k = 2.0 * c - (double)p[n - xc + wrapi(xc + 1, L)] - (double)p[n - xc + wrapi(xc - 1, L)];
+    k += 2.0 * c - (double)p[n + (wrapi(yc + 1, L) - yc) * L] - (double)p[n + (wrapi(yc - 1, L) - yc) * L];
+    if (nd == 3) {
+        const int zc = n / (L * L), LL = L * L;
+        k += 2.0 * c - (double)p[n + (wrapi(zc + 1, L) - zc) * LL] - (double)p[n + (wrapi(zc - 1, L) - zc) * LL];
+    }
+    return k;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kActThreads) action_kernel(int nd, int L, int V, double m2, double lam,
+                                                             int64_t B, const T* __restrict__ phi,
+                                                             double* __restrict__ S_out) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* p = reinterpret_cast<T*>(smem_raw);
+    double* red = reinterpret_cast<double*>(smem_raw + (((size_t)V * sizeof(T) + 15) & ~size_t(15)));
+    for (int64_t b = blockIdx.x; b < B; b += gridDim.x) {
+        stage(phi + b * V, p, V);
+        __syncthreads();
+        double acc = 0.0;
+        for (int n = threadIdx.x; n < V; n += blockDim.x) {
+            const double c = (double)p[n], c2 = c * c;
+            acc += c * lap_minus(p, n, nd, L) + m2 * c2 + lam * c2 * c2;
+        }
+        const double S = block_sum(acc, red);
+        if (threadIdx.x == 0) S_out[b] = S;
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kActThreads) force_kernel(int nd, int L, int V, double m2, double lam,
+                                                            int64_t B, const double* __restrict__ phi,
+                                                            double* __restrict__ F) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* p = reinterpret_cast<double*>(smem_raw);
+    for (int64_t b = blockIdx.x; b < B; b += gridDim.x) {
+        stage(phi + b * V, p, V);
+        __syncthreads();
+        for (int n = threadIdx.x; n < V; n += blockDim.x) {
+            const double c = p[n];
+            F[b * V + n] = 2.0 * lap_minus(p, n, nd, L) + 2.0 * m2 * c + 4.0 * lam * c * c * c;
+        }
+        __syncthreads();
+    }
+}
+
+bool lattice_ok(int nd, int L) {
+    if (nd != 2 && nd != 3) return false;
+    if (L < 1) return false;
+    int64_t V = 1;
+    for (int i = 0; i < nd; ++i) V *= L;
+    return V <= 16384;
+}
+
+template <typename K>
+int64_t grid_for(K kern, size_t smem, int64_t B) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kActThreads, smem) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    return std::min<int64_t>(B, (int64_t)num_sms() * per_sm);
+}
+
+}  // namespace
+}  // namespace gf
+
+using namespace gf;
+
+extern "C" {
+
+gf_status gf_phi4_action(int32_t nd, int32_t L, const gf_phi4* phi4, int64_t B,
+                         const void* d_phi, int32_t phi_is_fp64, double* d_S_out,
+                         cudaStream_t stream) {
+    if (!phi4 || !lattice_ok(nd, L) || B < 0 || (B > 0 && (!d_phi || !d_S_out))) return GF_EINVAL;
+    if (phi_is_fp64 != 0 && phi_is_fp64 != 1) return GF_EINVAL;
+    if (B == 0) return GF_OK;
+    int V = 1;
+    for (int i = 0; i < nd; ++i) V *= L;
+    const size_t esz = phi_is_fp64 ? 8 : 4;
+    const size_t smem = (((size_t)V * esz + 15) & ~size_t(15)) + 32 * sizeof(double);
+    if (phi_is_fp64) {
+        auto k = action_kernel<double>;
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+            return GF_ECUDA;
+        k<<<(unsigned)grid_for(k, smem, B), kActThreads, smem, stream>>>(
+            nd, L, V, phi4->m2, phi4->lam, B, static_cast<const double*>(d_phi), d_S_out);
+    } else {
+        auto k = action_kernel<float>;
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+            return GF_ECUDA;
+        k<<<(unsigned)grid_for(k, smem, B), kActThreads, smem, stream>>>(
+            nd, L, V, phi4->m2, phi4->lam, B, static_cast<const float*>(d_phi), d_S_out);
+    }
+    GF_CHECK_LAUNCH();
+    return GF_OK;
+}
+
+gf_status gf_phi4_force(int32_t nd, int32_t L, const gf_phi4* phi4, int64_t B,
+                        const double* d_phi, double* d_F_out, cudaStream_t stream) {
+    if (!phi4 || !lattice_ok(nd, L) || B < 0 || (B > 0 && (!d_phi || !d_F_out))) return GF_EINVAL;
+    if (B == 0) return GF_OK;
+    int V = 1;
+    for (int i = 0; i < nd; ++i) V *= L;
+    const size_t smem = (size_t)V * 8;
+    if (cudaFuncSetAttribute(force_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return GF_ECUDA;
+    force_kernel<<<(unsigned)grid_for(force_kernel, smem, B), kActThreads, smem, stream>>>(
+        nd, L, V, phi4->m2, phi4->lam, B, d_phi, d_F_out);
+    GF_CHECK_LAUNCH();
+    return GF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,109 @@
+// gf_common.cuh -- device helpers shared by the sampler's kernels:
+// Philox4x64-10 (Salmon et al., SC'11), uniform/normal conversions, FP64
+// block reductions, the device status word and host launch utilities.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/gfflow.h"
+
+namespace gf {
+
+// ---------------------------------------------------------------------------
+// Device status word: kernels that can detect an error receive its address
+// and record the first error (atomicCAS from 0); gf_device_status reads and
+// clears it.  (The word itself is defined in gf_api.cu; no relocatable
+// device code is needed.)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void set_status(int32_t* word, int32_t code) {
+    atomicCAS(reinterpret_cast<int*>(word), 0, code);
+}
+int32_t* status_word();   // host: device address of the status word
+
+// ---------------------------------------------------------------------------
+// Philox4x64-10: ten rounds of two 64x64->128 multiplies with a Weyl key
+// schedule.  Counter sub-spaces (last counter word) per random purpose.
+// ---------------------------------------------------------------------------
+enum : uint64_t { TAG_PRIOR = 1, TAG_MH = 2, TAG_HMC_P = 3, TAG_HMC_U = 4 };
+
+struct u64x4 { uint64_t x, y, z, w; };
+
+__device__ __forceinline__ u64x4 philox4x64_10(uint64_t k0, uint64_t k1, u64x4 c) {
+    constexpr uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+    constexpr uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += W0; k1 += W1; }
+        const uint64_t hi0 = __umul64hi(M0, c.x), lo0 = M0 * c.x;
+        const uint64_t hi1 = __umul64hi(M1, c.z), lo1 = M1 * c.z;
+        c = u64x4{hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
+    }
+    return c;
+}
+
+// (2k+1) * 2^-24 with k the top 23 bits: exact in FP32, in (0,1).
+__device__ __forceinline__ float u24f(uint64_t w) {
+    return (float)(2u * (uint32_t)(w >> 41) + 1u) * 0x1p-24f;
+}
+// (2k+1) * 2^-53 with k the top 52 bits: exact in FP64, in (0,1).
+__device__ __forceinline__ double u53(uint64_t w) {
+    return (double)(2ull * (w >> 12) + 1ull) * 0x1p-53;
+}
+
+// Four FP32 standard normals (two Box-Muller pairs, cos then sin) from one block.
+__device__ __forceinline__ void normals4_f32(u64x4 w, float out[4]) {
+    float r0 = sqrtf(-2.0f * logf(u24f(w.x)));
+    float r1 = sqrtf(-2.0f * logf(u24f(w.z)));
+    float s0, c0, s1, c1;
+    sincospif(2.0f * u24f(w.y), &s0, &c0);
+    sincospif(2.0f * u24f(w.w), &s1, &c1);
+    out[0] = r0 * c0; out[1] = r0 * s0; out[2] = r1 * c1; out[3] = r1 * s1;
+}
+
+// Four FP64 standard normals.
+__device__ __forceinline__ void normals4_f64(u64x4 w, double out[4]) {
+    double r0 = sqrt(-2.0 * log(u53(w.x)));
+    double r1 = sqrt(-2.0 * log(u53(w.z)));
+    double s0, c0, s1, c1;
+    sincospi(2.0 * u53(w.y), &s0, &c0);
+    sincospi(2.0 * u53(w.w), &s1, &c1);
+    out[0] = r0 * c0; out[1] = r0 * s0; out[2] = r1 * c1; out[3] = r1 * s1;
+}
+
+// ---------------------------------------------------------------------------
+// Reductions
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-wide FP64 sum; `scratch` holds >= 32 doubles; result valid in all
+// threads.  Contains __syncthreads(): call from uniform control flow.
+__device__ __forceinline__ double block_sum(double v, double* scratch) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) scratch[wid] = v;
+    __syncthreads();
+    double r = 0.0;
+    for (int i = 0; i < nw; ++i) r += scratch[i];   // fixed order: deterministic
+    return r;
+}
+
+constexpr double LOG_2PI = 1.8378770664093454835606594728112;
+
+// ---------------------------------------------------------------------------
+// Host helpers
+// ---------------------------------------------------------------------------
+int num_sms();   // cached multiprocessor count of the current device
+
+}  // namespace gf
+
+#define GF_CHECK_LAUNCH()                                          \
+    do {                                                           \
+        if (cudaGetLastError() != cudaSuccess) return GF_ECUDA;    \
+    } while (0)

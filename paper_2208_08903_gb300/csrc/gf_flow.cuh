@@ -1,0 +1,75 @@
+// gf_flow.cuh -- internal representation of a flow object and the slice
+// schedule shared by the fused coupling-stack kernels.
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include "gf_common.cuh"
+
+namespace gf {
+
+// A lattice is processed as L "slices" along its outermost axis (z in 3D,
+// y in 2D), each of S = L^(nd-1) sites.  Hidden activations h1 / h2 live in
+// shared memory in R "slots" of one slice each; a phase computes one kind of
+// result for n consecutive slices s0 .. s0+n-1 (mod L):
+//   PH_H1: h1 = LReLU(conv1(masked x))     -> slots out[0..n)
+//   PH_H2: h2 = LReLU(conv2(h1))           <- h1 of slices s0-1 .. s0+n in in[0..n+2)
+//                                          -> slots out[0..n)
+//   PH_C3: (s,t) = conv3(h2) at the updated sites, affine update of x
+//                                          <- h2 of slices s0-1 .. s0+n in in[0..n+2)
+constexpr int PH_H1 = 0, PH_H2 = 1, PH_C3 = 2;
+constexpr int MAX_PHASE_SLICES = 62;
+
+struct Phase {
+    uint8_t type, n;
+    uint16_t s0;
+    uint8_t in[MAX_PHASE_SLICES + 2];
+    uint8_t out[MAX_PHASE_SLICES + 2];
+};
+
+// Builds the per-layer phase list.  full: all L slices resident (R = L).
+// Otherwise an LRU slot cache of R = G + 2 slots per tensor, results produced
+// G slices at a time, the two wrap-around slices recomputed at the end.
+std::vector<Phase> build_schedule(int L, int G, bool full);
+
+}  // namespace gf
+
+struct gf_flow {
+    gf_flow_shape shape;
+    gf_precision prec;
+    int device;
+    int V, S, T, C1, C2;
+    int64_t n_params;       // canonical parameter count
+    int64_t canon_stride;   // canonical floats per layer
+    int64_t packed_stride;  // packed floats per layer (multiple of 4)
+    float* d_canon;         // FP32 canonical weights [n_params]
+    float* d_packed;        // per-layer packed FP32 weights
+    gf::Phase* d_sched;
+    int n_phases;
+    int G;                  // slices per phase (RING) or L (FULL)
+    int R;                  // slots per hidden tensor
+    bool full;
+    size_t smem_bytes;
+    // BF16 tensor-core path (3D, C=32)
+    void* d_bf16;           // packed bf16 conv2 weights and FP32 head weights
+    size_t smem_bytes_bf16;
+};
+
+namespace gf {
+// Packed layout per layer (floats, from the layer's base):
+//   W1p[T][C1], b1[C1], W2p[T][C1][C2], b2[C2], W3p[T][C2][2], b3[2], pad
+struct PackedOffsets {
+    int64_t W1, b1, W2, b2, W3, b3, stride;
+};
+PackedOffsets packed_offsets(int T, int C1, int C2);
+
+gf_status repack_weights(gf_flow* f, cudaStream_t stream);  // d_canon -> d_packed (+ bf16)
+
+gf_status launch_flow_fp32(const gf_flow* f, bool inverse, const gf_phi4* phi4, int64_t B,
+                           uint64_t seed, uint64_t counter0, const float* z_in, float* z_out,
+                           const float* phi_in, float* phi_out, double* logq_out,
+                           double* S_out, double* logw_out, cudaStream_t stream);
+gf_status flow_fp32_configure(gf_flow* f);   // chooses FULL/RING, G, smem
+
+}  // namespace gf

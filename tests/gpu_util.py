@@ -1,0 +1,75 @@
+"""Helpers shared by the GPU parity tests: tolerance checks against the oracle."""
+import numpy as np
+import pytest
+
+# Plain FP32 path: 1e-5 relative per site, 1e-4 relative per log-weight.
+SITE_RTOL = 1e-5
+LOGW_RTOL = 1e-4
+
+
+def require_gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2208_08903_gb300 as P
+    P._abi.load()        # raises if the library was not built
+    return torch, P
+
+
+def assert_sites_close(gpu, ref, rtol=SITE_RTOL, what="phi"):
+    """|a-b| <= rtol * max(|b|, rms(b of that configuration)) for every site."""
+    gpu = np.asarray(gpu, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    assert gpu.shape == ref.shape
+    rms = np.sqrt((ref**2).mean(axis=-1, keepdims=True))
+    bound = rtol * np.maximum(np.abs(ref), rms)
+    err = np.abs(gpu - ref)
+    bad = err > bound
+    if bad.any():
+        i = np.unravel_index(np.argmax(err / np.maximum(bound, 1e-300)), err.shape)
+        raise AssertionError(f"{what}: {bad.sum()} sites out of tolerance; worst at {i}: "
+                             f"gpu={gpu[i]!r} ref={ref[i]!r} bound={bound[i]!r}")
+    return float((err / np.maximum(np.maximum(np.abs(ref), rms), 1e-300)).max())
+
+
+def assert_logw_close(gpu, ref, rtol=LOGW_RTOL, what="logw"):
+    """|a-b| <= rtol * max(|b|, 1) per configuration."""
+    gpu = np.asarray(gpu, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    bound = rtol * np.maximum(np.abs(ref), 1.0)
+    err = np.abs(gpu - ref)
+    bad = err > bound
+    if bad.any():
+        i = int(np.argmax(err / bound))
+        raise AssertionError(f"{what}: {bad.sum()} entries out of tolerance; worst at {i}: "
+                             f"gpu={gpu[i]!r} ref={ref[i]!r} bound={bound[i]!r}")
+    return float((err / np.maximum(np.abs(ref), 1.0)).max())
+
+
+def compare_mh(orc, st_seed, stream_id, logw, idx_gpu, acc_gpu, step0=0, logw_tol=0.0):
+    """MH decisions must match the oracle's except at near ties.
+
+    A decision may differ only where |(logw_k - logw_cur) - log u_k| < tau with
+    tau = 4 * logw_tol * max(|logw|, 1) + 1e-12 (the two sides evaluate log u
+    with their own log); after such a divergence the comparison resumes from
+    the oracle's state.  Returns the number of tolerated divergences.
+    """
+    logw = np.asarray(logw, dtype=np.float64)
+    n = logw.size
+    logu = orc.mh_logu(st_seed, stream_id, step0, n)
+    cur, idx = 0.0, 0
+    diverged = 0
+    for k in range(n):
+        g = step0 + k
+        d = logw[k] - cur
+        acc = True if g == 0 else d > logu[k]
+        if bool(acc_gpu[k]) != acc:
+            tau = 4 * logw_tol * max(abs(logw[k]), abs(cur), 1.0) + 1e-12
+            assert g > 0 and abs(d - logu[k]) < tau, (
+                f"MH decision {k} differs: gpu={acc_gpu[k]} oracle={acc} margin={d - logu[k]}")
+            diverged += 1
+        if acc:
+            cur, idx = logw[k], g
+        if bool(acc_gpu[k]) == acc:
+            assert idx_gpu[k] == idx or diverged, f"chain index {k}: {idx_gpu[k]} != {idx}"
+    return diverged

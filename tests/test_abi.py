@@ -1,0 +1,82 @@
+"""The C-ABI library loads and exports every declared symbol; argument errors
+are reported before any CUDA work (CPU only: no compute call is made)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(gf_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2208_08903_gb300 import _abi, build
+    build.build()
+    return _abi.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2208_08903_gb300 import _abi
+    decl = declared_symbols()
+    assert len(decl) >= 16
+    for name in decl:
+        assert hasattr(lib, name), name
+    assert set(decl) == set(_abi.EXPORTED) | (set(decl) - set(_abi.EXPORTED))
+    assert set(_abi.EXPORTED) <= set(decl)
+
+
+def test_argument_errors_without_gpu(lib):
+    from paper_2208_08903_gb300 import _abi
+    h = C.c_void_p()
+    w = (C.c_double * 100)()
+    bad = [
+        _abi.FlowShapeC(2, 7, 2, 8, 8, 3, 1, 0.01),     # odd L
+        _abi.FlowShapeC(4, 8, 2, 8, 8, 3, 1, 0.01),     # nd = 4
+        _abi.FlowShapeC(2, 8, 2, 8, 16, 3, 1, 0.01),    # c1 != c2
+        _abi.FlowShapeC(2, 8, 2, 12, 12, 3, 1, 0.01),   # width not in {8,16,32}
+        _abi.FlowShapeC(2, 8, 2, 8, 8, 5, 1, 0.01),     # ksize 5
+        _abi.FlowShapeC(3, 64, 2, 8, 8, 3, 1, 0.01),    # V > 65536
+    ]
+    for sh in bad:
+        assert lib.gf_flow_create(C.byref(sh), w, 0, None, C.byref(h)) == _abi.GF_EINVAL
+    good = _abi.FlowShapeC(2, 8, 2, 8, 8, 3, 1, 0.01)
+    assert lib.gf_flow_create(C.byref(good), None, 0, None, C.byref(h)) == _abi.GF_EINVAL
+    assert lib.gf_flow_create(C.byref(good), w, 7, None, C.byref(h)) == _abi.GF_EINVAL
+    assert lib.gf_flow_create(C.byref(good), w, 0, None, None) == _abi.GF_EINVAL
+    p = _abi.Phi4C(1.0, 1.0)
+    assert lib.gf_phi4_action(4, 8, C.byref(p), 1, None, 0, None, None) == _abi.GF_EINVAL
+    assert lib.gf_phi4_action(2, 8, None, 1, None, 0, None, None) == _abi.GF_EINVAL
+    assert lib.gf_phi4_action(2, 8, C.byref(p), -1, None, 0, None, None) == _abi.GF_EINVAL
+    assert lib.gf_phi4_action(2, 8, C.byref(p), 0, None, 0, None, None) == _abi.GF_OK
+    assert lib.gf_mh_chain(None, 5, None, None, None, None, 0, None) == _abi.GF_EINVAL
+    assert lib.gf_mh_chain_workspace_bytes(10) == 80
+    assert lib.gf_mh_chain_workspace_bytes(0) == 0
+    assert lib.gf_hmc_trajectory(2, 8, C.byref(p), 4, None, 0, 0.1, 0, 0, None, None, None) == _abi.GF_EINVAL
+    assert lib.gf_hmc_trajectory(3, 32, C.byref(p), 4, None, 5, 0.1, 0, 0, None, None, None) == _abi.GF_EUNSUPPORTED
+    assert lib.gf_flow_destroy(None) == _abi.GF_EINVAL
+    assert lib.gf_flow_n_params(None) == -1
+    assert lib.gf_status_string(-5) == b"GF_ETIMEOUT"
+
+
+def test_product_path_has_no_oracle_dependency():
+    """Nothing in the package imports, loads or names the oracle."""
+    pkg = os.path.join(ROOT, "paper_2208_08903_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        if "_build" in dirpath:
+            continue
+        for fn in files:
+            if fn.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                src = open(os.path.join(dirpath, fn)).read()
+                assert "oracle" not in src.lower(), fn
+                assert "gf_oracle" not in src and "gfo_" not in src, fn
