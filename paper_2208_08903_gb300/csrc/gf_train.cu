@@ -1,11 +1,632 @@
-// gf_train.cu -- reverse-KL training step (in progress).
+// gf_train.cu -- reverse-KL self-training step of the coupling stack.
+//
+// Paper arXiv:2208.08903 Sec. 1 (shifted reverse Kullback-Leibler divergence
+// as the training objective) and Sec. 3 (training loop: sample z from the
+// prior, gradient of the loss, Adam update).  Loss per configuration:
+// log q(phi) + S(phi) = log r(z) - sum_l sum_{updated} s + S(F^{-1}(z)),
+// differentiated by a hand-written reverse pass:
+//   forward  : layer-wise batched kernels, saving only each layer's input x_l
+//   backward : per layer (last first) recompute h1, h2, s from x_l, then
+//              affine adjoint -> conv3^T -> LReLU' -> conv2^T -> LReLU'
+//              -> conv1^T onto the fixed sites, and the weight gradients.
+// Activations go through HBM ([B][V][C] FP32): the step is bound by FP32
+// FMA throughput, the extra traffic is a few percent of its time.  Weight
+// gradients: each CTA accumulates its configurations in registers and
+// writes a partial; a second kernel sums the partials in a fixed order
+// (deterministic, no atomics).
+#include <algorithm>
+#include <cstring>
+
 #include "gf_flow.cuh"
 
+namespace gf {
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ int wrapi(int v, int L) { return v < 0 ? v + L : (v >= L ? v - L : v); }
+__device__ __forceinline__ float lrelu(float v, float a) { return v > 0.f ? v : a * v; }
+
+template <int ND>
+__device__ __forceinline__ void tap_delta(int t, int& ds, int& dy, int& dx) {
+    if (ND == 3) { ds = t / 9 - 1; dy = (t / 3) % 3 - 1; dx = t % 3 - 1; }
+    else { ds = t / 3 - 1; dy = 0; dx = t % 3 - 1; }
+}
+
+// Site n + delta(t) on the periodic lattice (n = x + L*(y + L*z)).
+template <int ND>
+__device__ __forceinline__ int nbr(int n, int t, int L) {
+    int ds, dy, dx;
+    tap_delta<ND>(t, ds, dy, dx);
+    const int x = n % L;
+    if (ND == 3) {
+        const int y = (n / L) % L, z = n / (L * L);
+        return (wrapi(z + ds, L) * L + wrapi(y + dy, L)) * L + wrapi(x + dx, L);
+    }
+    const int y = n / L;
+    return wrapi(y + ds, L) * L + wrapi(x + dx, L);
+}
+
+template <int ND>
+__device__ __forceinline__ int parity(int n, int L) {
+    const int x = n % L, y = (n / L) % L;
+    return (ND == 3 ? (x + y + n / (L * L)) : (x + y)) & 1;
+}
+
+// ------------------------------------------------------------------ prior
+__global__ void k_prior(int V, int64_t B, uint64_t seed, uint64_t counter0, const float* __restrict__ zin,
+                        float* __restrict__ z) {
+    const int64_t groups = (int64_t)B * ((V + 3) / 4);
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < groups;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = g / ((V + 3) / 4);
+        const int j = (int)(g - b * ((V + 3) / 4));
+        if (zin) {
+            for (int q = 0; q < 4 && 4 * j + q < V; ++q) z[b * V + 4 * j + q] = zin[b * V + 4 * j + q];
+            continue;
+        }
+        const u64x4 w = philox4x64_10(seed, 0ull, u64x4{counter0 + (uint64_t)b, (uint64_t)j, 0ull, TAG_PRIOR});
+        float zz[4];
+        normals4_f32(w, zz);
+        for (int q = 0; q < 4 && 4 * j + q < V; ++q) z[b * V + 4 * j + q] = zz[q];
+    }
+}
+
+// ------------------------------------------------------------------ generic periodic conv
+// out[b][n][co..co+8) = epi( sum_t sum_ci W[t][ci][co] * in'[b][nbr(n,t)][ci] )
+// in' = in, or in masked to sites of parity `mask` (mask >= 0).
+// mode 0: + bias, LeakyReLU.  mode 1: * LReLU'(ref[b][n][co]) (ref = post-activation).
+// Warp task = (configuration, 128 sites, 8 output channels); lane owns sites
+// lane + 32k (k < 4), weights are warp-uniform.
+struct ConvArgs {
+    const float* in; int Cin; int mask;
+    const float* W; const float* bias; int Cout;
+    float* out; const float* ref; int mode; float slope;
+    int L, V; int64_t B;
+};
+
+template <int ND, int VEC>
+__global__ void __launch_bounds__(kThreads) k_conv(const ConvArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int nblk = (a.V + 127) >> 7, ngrp = a.Cout >> 3;
+    const int64_t tasks = a.B * nblk * ngrp;
+    const int T = ND == 3 ? 27 : 9;
+    for (int64_t task = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; task < tasks;
+         task += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int g = (int)(task % ngrp);
+        const int64_t rest = task / ngrp;
+        const int blk = (int)(rest % nblk);
+        const int64_t b = rest / nblk;
+        const int co = g << 3;
+        int n[4];
+        bool valid[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            n[k] = (blk << 7) + lane + 32 * k;
+            valid[k] = n[k] < a.V;
+            if (!valid[k]) n[k] = a.V - 1;
+        }
+        float acc[4][8];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) acc[k][c] = (a.mode == 0) ? __ldg(a.bias + co + c) : 0.f;
+        const float* inb = a.in + b * (int64_t)a.V * a.Cin;
+        for (int t = 0; t < T; ++t) {
+            int m[4];
+            float msk[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                m[k] = nbr<ND>(n[k], t, a.L);
+                msk[k] = (a.mask < 0 || parity<ND>(m[k], a.L) == a.mask) ? 1.f : 0.f;
+            }
+            const float* Wt = a.W + (int64_t)t * a.Cin * a.Cout + co;
+            for (int c0 = 0; c0 < a.Cin; c0 += VEC) {
+                float hv[4][VEC];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float* p = inb + (int64_t)m[k] * a.Cin + c0;
+                    if (VEC == 4) {
+                        const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+                        hv[k][0] = v.x; hv[k][VEC > 1 ? 1 : 0] = v.y;
+                        hv[k][VEC > 2 ? 2 : 0] = v.z; hv[k][VEC > 3 ? 3 : 0] = v.w;
+                    } else if (VEC == 2) {
+                        const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+                        hv[k][0] = v.x; hv[k][VEC > 1 ? 1 : 0] = v.y;
+                    } else {
+                        hv[k][0] = __ldg(p);
+                    }
+#pragma unroll
+                    for (int q = 0; q < VEC; ++q) hv[k][q] *= msk[k];
+                }
+#pragma unroll
+                for (int q = 0; q < VEC; ++q) {
+                    const float* wp = Wt + (int64_t)(c0 + q) * a.Cout;
+                    const float4 wa = __ldg(reinterpret_cast<const float4*>(wp));
+                    const float4 wb = __ldg(reinterpret_cast<const float4*>(wp + 4));
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const float h = hv[k][q];
+                        acc[k][0] = fmaf(h, wa.x, acc[k][0]); acc[k][1] = fmaf(h, wa.y, acc[k][1]);
+                        acc[k][2] = fmaf(h, wa.z, acc[k][2]); acc[k][3] = fmaf(h, wa.w, acc[k][3]);
+                        acc[k][4] = fmaf(h, wb.x, acc[k][4]); acc[k][5] = fmaf(h, wb.y, acc[k][5]);
+                        acc[k][6] = fmaf(h, wb.z, acc[k][6]); acc[k][7] = fmaf(h, wb.w, acc[k][7]);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (!valid[k]) continue;
+            float* o = a.out + (b * a.V + n[k]) * (int64_t)a.Cout + co;
+            float r[8];
+            if (a.mode == 0) {
+#pragma unroll
+                for (int c = 0; c < 8; ++c) r[c] = lrelu(acc[k][c], a.slope);
+            } else {
+                const float* rp = a.ref + (b * a.V + n[k]) * (int64_t)a.Cout + co;
+#pragma unroll
+                for (int c = 0; c < 8; ++c) r[c] = acc[k][c] * (__ldg(rp + c) > 0.f ? 1.f : a.slope);
+            }
+            reinterpret_cast<float4*>(o)[0] = make_float4(r[0], r[1], r[2], r[3]);
+            reinterpret_cast<float4*>(o)[1] = make_float4(r[4], r[5], r[6], r[7]);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ conv3 + affine (forward)
+// One CTA per configuration: (s, t) at the updated sites, x_out = x_in*e^s + t
+// there, x_out = x_in on fixed sites; s saved for the reverse pass;
+// logdet[b] += sum s (FP64, fixed-order block reduction).
+template <int ND>
+__global__ void __launch_bounds__(kThreads) k_couple_fwd(const float* __restrict__ h2, int C2,
+                                                        const float* __restrict__ W3, const float* __restrict__ b3,
+                                                        int use_tanh, int frozen, int L, int V, int64_t B,
+                                                        const float* __restrict__ xin, float* __restrict__ xout,
+                                                        float* __restrict__ s_save, double* __restrict__ logdet) {
+    __shared__ double red[32];
+    const int T = ND == 3 ? 27 : 9;
+    for (int64_t b = blockIdx.x; b < B; b += gridDim.x) {
+        double ld = 0.0;
+        for (int n = threadIdx.x; n < V; n += blockDim.x) {
+            const float xv = xin[b * V + n];
+            if (parity<ND>(n, L) == frozen) { xout[b * V + n] = xv; s_save[b * V + n] = 0.f; continue; }
+            float ps = __ldg(b3), pt = __ldg(b3 + 1);
+            for (int t = 0; t < T; ++t) {
+                const float* hp = h2 + ((b * V) + nbr<ND>(n, t, L)) * (int64_t)C2;
+                const float* wp = W3 + (int64_t)t * C2 * 2;
+                for (int c = 0; c < C2; c += 4) {
+                    const float4 h = __ldg(reinterpret_cast<const float4*>(hp + c));
+                    const float4 w01 = __ldg(reinterpret_cast<const float4*>(wp + 2 * c));
+                    const float4 w23 = __ldg(reinterpret_cast<const float4*>(wp + 2 * c + 4));
+                    ps = fmaf(h.x, w01.x, ps); pt = fmaf(h.x, w01.y, pt);
+                    ps = fmaf(h.y, w01.z, ps); pt = fmaf(h.y, w01.w, pt);
+                    ps = fmaf(h.z, w23.x, ps); pt = fmaf(h.z, w23.y, pt);
+                    ps = fmaf(h.w, w23.z, ps); pt = fmaf(h.w, w23.w, pt);
+                }
+            }
+            const float s = use_tanh ? tanhf(ps) : ps;
+            xout[b * V + n] = fmaf(xv, expf(s), pt);
+            s_save[b * V + n] = s;
+            ld += (double)s;
+        }
+        const double tot = block_sum(ld, red);
+        if (threadIdx.x == 0) logdet[b] += tot;
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ affine adjoint
+// At updated sites: g3 = (dL/ds_pre, dL/dt), gx <- gx*e^s.  Fixed sites: g3 = 0.
+template <int ND>
+__global__ void k_couple_bwd(int frozen, int use_tanh, int L, int V, int64_t B, const float* __restrict__ xin,
+                             const float* __restrict__ s_save, float* __restrict__ gx, float* __restrict__ g3) {
+    const int64_t total = B * (int64_t)V;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int n = (int)(i % V);
+        float2 o = make_float2(0.f, 0.f);
+        if (parity<ND>(n, L) != frozen) {
+            const float s = s_save[i], e = expf(s), g = gx[i];
+            const float gs = g * xin[i] * e - 1.0f;           // d/ds of x*e^s and of -logdet
+            o.x = use_tanh ? gs * (1.f - s * s) : gs;
+            o.y = g;
+            gx[i] = g * e;
+        }
+        reinterpret_cast<float2*>(g3)[i] = o;
+    }
+}
+
+// ------------------------------------------------------------------ conv1^T onto fixed sites
+// gx[b][n] += sum_t sum_c W1b[t][c] * gh1[b][nbr(n,t)][c] at sites of parity `frozen`.
+template <int ND>
+__global__ void k_conv1_bwd(const float* __restrict__ gh1, int C1, const float* __restrict__ W1b, int frozen,
+                            int L, int V, int64_t B, float* __restrict__ gx) {
+    const int T = ND == 3 ? 27 : 9;
+    const int64_t total = B * (int64_t)V;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int n = (int)(i % V);
+        if (parity<ND>(n, L) != frozen) continue;
+        const int64_t b = i / V;
+        float acc = 0.f;
+        for (int t = 0; t < T; ++t) {
+            const float* hp = gh1 + (b * V + nbr<ND>(n, t, L)) * (int64_t)C1;
+            const float* wp = W1b + (int64_t)t * C1;
+            for (int c = 0; c < C1; c += 4) {
+                const float4 h = __ldg(reinterpret_cast<const float4*>(hp + c));
+                const float4 w = __ldg(reinterpret_cast<const float4*>(wp + c));
+                acc = fmaf(h.x, w.x, acc); acc = fmaf(h.y, w.y, acc);
+                acc = fmaf(h.z, w.z, acc); acc = fmaf(h.w, w.w, acc);
+            }
+        }
+        gx[i] += acc;
+    }
+}
+
+// ------------------------------------------------------------------ weight gradients
+// partial[cta][t][i][o] = sum over this CTA's configurations and all sites of
+//   gout[b][n][o] * in'[b][nbr(n,t)][i];  tap t == T is the bias (in' = 1, i = 0).
+// Thread task = (t, IB input channels, OB output channels).
+struct WgArgs {
+    const float* in; int Cin; int mask;
+    const float* gout; int Cout;
+    float* partial; int L, V; int64_t B;
+};
+
+template <int ND, int IB, int OB>
+__global__ void k_wgrad(const WgArgs a) {
+    const int T = ND == 3 ? 27 : 9;
+    const int nic = a.Cin / IB, noc = a.Cout / OB;
+    const int tasks = (T + 1) * nic * noc;
+    const int task = threadIdx.x;
+    const bool active = task < tasks;
+    const int oc = active ? task % noc : 0;
+    const int ic = active ? (task / noc) % nic : 0;
+    const int t = active ? task / (noc * nic) : 0;
+    const bool bias = t == T;
+    float acc[IB][OB];
+#pragma unroll
+    for (int i = 0; i < IB; ++i)
+#pragma unroll
+        for (int o = 0; o < OB; ++o) acc[i][o] = 0.f;
+    if (active && !(bias && ic != 0)) {
+        for (int64_t b = blockIdx.x; b < a.B; b += gridDim.x) {
+            const float* inb = a.in + b * (int64_t)a.V * a.Cin;
+            const float* gb = a.gout + b * (int64_t)a.V * a.Cout;
+            for (int n = 0; n < a.V; ++n) {
+                float iv[IB];
+                if (bias) {
+#pragma unroll
+                    for (int i = 0; i < IB; ++i) iv[i] = (i == 0) ? 1.f : 0.f;
+                } else {
+                    const int m = nbr<ND>(n, t, a.L);
+                    const float mk = (a.mask < 0 || parity<ND>(m, a.L) == a.mask) ? 1.f : 0.f;
+                    const float* p = inb + (int64_t)m * a.Cin + ic * IB;
+                    if (IB == 4) {
+                        const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+                        iv[0] = v.x * mk; iv[IB > 1 ? 1 : 0] = v.y * mk;
+                        iv[IB > 2 ? 2 : 0] = v.z * mk; iv[IB > 3 ? 3 : 0] = v.w * mk;
+                    } else {
+                        iv[0] = __ldg(p) * mk;
+                    }
+                }
+                float gv[OB];
+                const float* q = gb + (int64_t)n * a.Cout + oc * OB;
+                if (OB == 8) {
+                    const float4 g0 = __ldg(reinterpret_cast<const float4*>(q));
+                    const float4 g1 = __ldg(reinterpret_cast<const float4*>(q + 4));
+                    gv[0] = g0.x; gv[1 % OB] = g0.y; gv[2 % OB] = g0.z; gv[3 % OB] = g0.w;
+                    gv[4 % OB] = g1.x; gv[5 % OB] = g1.y; gv[6 % OB] = g1.z; gv[7 % OB] = g1.w;
+                } else {
+                    const float2 g0 = __ldg(reinterpret_cast<const float2*>(q));
+                    gv[0] = g0.x; gv[1 % OB] = g0.y;
+                }
+#pragma unroll
+                for (int i = 0; i < IB; ++i)
+#pragma unroll
+                    for (int o = 0; o < OB; ++o) acc[i][o] = fmaf(iv[i], gv[o], acc[i][o]);
+            }
+        }
+    }
+    if (active) {
+        float* P = a.partial + (int64_t)blockIdx.x * (T + 1) * a.Cin * a.Cout;
+#pragma unroll
+        for (int i = 0; i < IB; ++i)
+#pragma unroll
+            for (int o = 0; o < OB; ++o)
+                P[((int64_t)t * a.Cin + ic * IB + i) * a.Cout + oc * OB + o] = acc[i][o];
+    }
+}
+
+// grad (canonical, for one conv of one layer): W[o][i][t] and b[o], scaled by 1/B.
+__global__ void k_wgrad_reduce(const float* __restrict__ partial, int nparts, int T, int Cin, int Cout,
+                               float scale, float* __restrict__ gW, float* __restrict__ gb) {
+    const int per = (T + 1) * Cin * Cout;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < per; p += gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (int k = 0; k < nparts; ++k) s += partial[(int64_t)k * per + p];
+        const int o = p % Cout, i = (p / Cout) % Cin, t = p / (Cout * Cin);
+        if (t < T) gW[((int64_t)o * Cin + i) * T + t] = s * scale;
+        else if (i == 0) gb[o] = s * scale;
+    }
+}
+
+// ------------------------------------------------------------------ loss, force
+// loss_b = log r(z_b) - logdet_b + S(phi_b); gx = dS/dphi (FP64 terms, FP32 out).
+template <int ND>
+__global__ void __launch_bounds__(kThreads) k_loss_force(const float* __restrict__ z, const float* __restrict__ phi,
+                                                        const double* __restrict__ logdet, double m2, double lam,
+                                                        int L, int V, int64_t B, double* __restrict__ loss_b,
+                                                        float* __restrict__ gx) {
+    __shared__ double red[32];
+    for (int64_t b = blockIdx.x; b < B; b += gridDim.x) {
+        const float* p = phi + b * V;
+        double acc = 0.0, z2 = 0.0;
+        for (int n = threadIdx.x; n < V; n += blockDim.x) {
+            const double c = p[n];
+            double k = 0.0;
+            for (int mu = 0; mu < ND; ++mu) {
+                const int t_plus = (mu == 0) ? (ND == 3 ? 14 : 5) : (mu == 1) ? (ND == 3 ? 16 : 7) : 22;
+                const int t_minus = (ND == 3 ? 26 : 8) - t_plus;
+                k += 2.0 * c - (double)p[nbr<ND>(n, t_plus, L)] - (double)p[nbr<ND>(n, t_minus, L)];
+            }
+            acc += c * k + m2 * c * c + lam * c * c * c * c;
+            gx[b * V + n] = (float)(2.0 * k + 2.0 * m2 * c + 4.0 * lam * c * c * c);
+            const double zz = z[b * V + n];
+            z2 += zz * zz;
+        }
+        const double S = block_sum(acc, red);
+        const double Z2 = block_sum(z2, red);
+        if (threadIdx.x == 0) loss_b[b] = (-0.5 * Z2 - 0.5 * (double)V * LOG_2PI) - logdet[b] + S;
+        __syncthreads();
+    }
+}
+
+__global__ void k_mean(const double* __restrict__ v, int64_t n, double* __restrict__ out) {
+    __shared__ double red[32];
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += v[i];
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) *out = s / (double)n;
+}
+
+// ------------------------------------------------------------------ weights for the reverse pass
+// Transposed + tap-flipped copies: Wb[t][o][i] = W[o][i][T-1-t] (delta(T-1-t) = -delta(t)).
+__global__ void k_pack_bwd(const float* __restrict__ canon, int64_t cstride, int n_layers, int T, int C1, int C2,
+                           float* __restrict__ out, int64_t ostride) {
+    const int64_t total = (int64_t)n_layers * ostride;
+    const int64_t n1 = (int64_t)T * C1, n2 = (int64_t)T * C2 * C1, n3 = (int64_t)T * 2 * C2;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int l = (int)(i / ostride);
+        int64_t r = i - l * ostride;
+        const float* W = canon + l * cstride;
+        float v = 0.f;
+        if (r < n1) {                                    // W1b[t][c] = W1[c][0][T-1-t]
+            const int t = (int)(r / C1), c = (int)(r % C1);
+            v = W[(int64_t)c * T + (T - 1 - t)];
+        } else if ((r -= n1) < n2) {                     // W2b[t][o][i] = W2[o][i][T-1-t]
+            const int t = (int)(r / ((int64_t)C2 * C1));
+            const int o = (int)((r / C1) % C2), ii = (int)(r % C1);
+            v = W[n1 + C1 + ((int64_t)o * C1 + ii) * T + (T - 1 - t)];
+        } else if ((r -= n2) < n3) {                     // W3b[t][o][i] = W3[o][i][T-1-t]
+            const int t = (int)(r / (2 * C2));
+            const int o = (int)((r / C2) % 2), ii = (int)(r % C2);
+            v = W[n1 + C1 + n2 + C2 + ((int64_t)o * C2 + ii) * T + (T - 1 - t)];
+        }
+        out[i] = v;
+    }
+}
+
+// ------------------------------------------------------------------ Adam (Kingma & Ba)
+__global__ void k_adam(int64_t n, float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, float lr, float b1, float b2, float eps, float c1, float c2) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+// ------------------------------------------------------------------ workspace
+struct TrainWs {
+    float *xs, *h1, *h2, *s, *gx, *g3, *gh2, *gh1, *wb, *partial, *grad;
+    double *logdet, *loss_b;
+    size_t bytes;
+};
+
+int wgrad_grid() { return num_sms() * 2; }
+
+TrainWs carve(const gf_flow* f, int64_t B, char* base) {
+    TrainWs w;
+    std::memset(&w, 0, sizeof(w));
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> char* {
+        char* p = base ? base + off : nullptr;
+        off += (bytes + 255) & ~size_t(255);
+        return p;
+    };
+    const int64_t BV = B * (int64_t)f->V;
+    const int N = f->shape.n_layers, C = std::max(f->C1, f->C2);
+    const int64_t obstride = (int64_t)f->T * f->C1 + (int64_t)f->T * f->C2 * f->C1 + 2LL * f->T * f->C2;
+    w.xs = (float*)take(sizeof(float) * BV * (N + 1));
+    w.h1 = (float*)take(sizeof(float) * BV * f->C1);
+    w.h2 = (float*)take(sizeof(float) * BV * f->C2);
+    w.s = (float*)take(sizeof(float) * BV);
+    w.gx = (float*)take(sizeof(float) * BV);
+    w.g3 = (float*)take(sizeof(float) * BV * 2);
+    w.gh2 = (float*)take(sizeof(float) * BV * f->C2);
+    w.gh1 = (float*)take(sizeof(float) * BV * f->C1);
+    w.wb = (float*)take(sizeof(float) * obstride * std::max(N, 1));
+    w.partial = (float*)take(sizeof(float) * (size_t)wgrad_grid() * (f->T + 1) * C * C);
+    w.grad = (float*)take(sizeof(float) * std::max<int64_t>(f->n_params, 1));
+    w.logdet = (double*)take(sizeof(double) * std::max<int64_t>(B, 1));
+    w.loss_b = (double*)take(sizeof(double) * std::max<int64_t>(B, 1));
+    w.bytes = off;
+    return w;
+}
+
+int64_t grid1d(int64_t n) { return std::max<int64_t>(1, std::min<int64_t>((n + kThreads - 1) / kThreads, (int64_t)num_sms() * 16)); }
+
+template <int ND>
+gf_status conv(const ConvArgs& a, cudaStream_t st) {
+    const int64_t warps = a.B * ((a.V + 127) / 128) * (a.Cout / 8);
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((warps + 7) / 8, (int64_t)num_sms() * 8));
+    if (a.Cin % 4 == 0) k_conv<ND, 4><<<(unsigned)grid, kThreads, 0, st>>>(a);
+    else if (a.Cin % 2 == 0) k_conv<ND, 2><<<(unsigned)grid, kThreads, 0, st>>>(a);
+    else k_conv<ND, 1><<<(unsigned)grid, kThreads, 0, st>>>(a);
+    GF_CHECK_LAUNCH();
+    return GF_OK;
+}
+
+template <int ND>
+gf_status wgrad(const WgArgs& a, float* gW, float* gbias, float scale, cudaStream_t st) {
+    const int T = ND == 3 ? 27 : 9;
+    const int grid = (int)std::min<int64_t>(a.B, wgrad_grid());
+    int threads;
+    if (a.Cin == 1) {
+        threads = (T + 1) * (a.Cout / 8);
+        k_wgrad<ND, 1, 8><<<grid, (threads + 31) / 32 * 32, 0, st>>>(a);
+    } else if (a.Cout == 2) {
+        threads = (T + 1) * (a.Cin / 4);
+        k_wgrad<ND, 4, 2><<<grid, (threads + 31) / 32 * 32, 0, st>>>(a);
+    } else {
+        threads = (T + 1) * (a.Cin / 4) * (a.Cout / 8);
+        k_wgrad<ND, 4, 8><<<grid, (threads + 31) / 32 * 32, 0, st>>>(a);
+    }
+    GF_CHECK_LAUNCH();
+    const int per = (T + 1) * a.Cin * a.Cout;
+    k_wgrad_reduce<<<(per + 255) / 256, 256, 0, st>>>(a.partial, grid, T, a.Cin, a.Cout, scale, gW, gbias);
+    GF_CHECK_LAUNCH();
+    return GF_OK;
+}
+
+template <int ND>
+gf_status train_step(gf_flow* f, const gf_phi4* phi4, int64_t B, uint64_t seed, uint64_t counter0,
+                     const float* z_in, double* loss_out, float* grad_out, float lr, float beta1,
+                     float beta2, float adam_eps, float* adam_m, float* adam_v, int64_t adam_t,
+                     const TrainWs& w, cudaStream_t st) {
+    const int L = f->shape.L, V = f->V, N = f->shape.n_layers, T = f->T;
+    const int C1 = f->C1, C2 = f->C2;
+    const int64_t BV = B * (int64_t)V;
+    const float slope = (float)f->shape.leaky_slope;
+    const int use_tanh = f->shape.use_final_tanh;
+    const PackedOffsets po = packed_offsets(T, C1, C2);
+    const int64_t obstride = (int64_t)T * C1 + (int64_t)T * C2 * C1 + 2LL * T * C2;
+    float* grad = grad_out ? grad_out : w.grad;
+
+    k_prior<<<(unsigned)grid1d(BV / 4 + 1), kThreads, 0, st>>>(V, B, seed, counter0, z_in, w.xs);
+    GF_CHECK_LAUNCH();
+    if (cudaMemsetAsync(w.logdet, 0, sizeof(double) * B, st) != cudaSuccess) return GF_ECUDA;
+    if (N > 0) {
+        k_pack_bwd<<<(unsigned)grid1d(obstride * N), kThreads, 0, st>>>(f->d_canon, f->canon_stride, N, T, C1, C2,
+                                                                        w.wb, obstride);
+        GF_CHECK_LAUNCH();
+    }
+    const unsigned cfg_grid = (unsigned)std::min<int64_t>(B, (int64_t)num_sms() * 8);
+
+    auto net_fwd = [&](int l, const float* xl) -> gf_status {
+        const float* P = f->d_packed + (int64_t)l * f->packed_stride;
+        ConvArgs c1{xl, 1, l & 1, P + po.W1, P + po.b1, C1, w.h1, nullptr, 0, slope, L, V, B};
+        gf_status s = conv<ND>(c1, st);
+        if (s != GF_OK) return s;
+        ConvArgs c2{w.h1, C1, -1, P + po.W2, P + po.b2, C2, w.h2, nullptr, 0, slope, L, V, B};
+        return conv<ND>(c2, st);
+    };
+
+    // forward: save x_l, accumulate logdet
+    for (int l = 0; l < N; ++l) {
+        const float* xl = w.xs + (int64_t)l * BV;
+        gf_status s = net_fwd(l, xl);
+        if (s != GF_OK) return s;
+        const float* P = f->d_packed + (int64_t)l * f->packed_stride;
+        k_couple_fwd<ND><<<cfg_grid, kThreads, 0, st>>>(w.h2, C2, P + po.W3, P + po.b3, use_tanh, l & 1, L, V, B,
+                                                       xl, w.xs + (int64_t)(l + 1) * BV, w.s, w.logdet);
+        GF_CHECK_LAUNCH();
+    }
+    k_loss_force<ND><<<cfg_grid, kThreads, 0, st>>>(w.xs, w.xs + (int64_t)N * BV, w.logdet, phi4->m2, phi4->lam,
+                                                    L, V, B, w.loss_b, w.gx);
+    GF_CHECK_LAUNCH();
+    k_mean<<<1, kThreads, 0, st>>>(w.loss_b, B, loss_out);
+    GF_CHECK_LAUNCH();
+
+    // reverse pass
+    const float scale = 1.0f / (float)B;
+    for (int l = N - 1; l >= 0; --l) {
+        const float* xl = w.xs + (int64_t)l * BV;
+        const float* P = f->d_packed + (int64_t)l * f->packed_stride;
+        const float* Wb = w.wb + (int64_t)l * obstride;
+        float* G = grad + (int64_t)l * f->canon_stride;
+        float* gW1 = G;
+        float* gb1 = gW1 + (int64_t)C1 * T;
+        float* gW2 = gb1 + C1;
+        float* gb2 = gW2 + (int64_t)C2 * C1 * T;
+        float* gW3 = gb2 + C2;
+        float* gb3 = gW3 + 2LL * C2 * T;
+        gf_status s = net_fwd(l, xl);                                  // recompute h1, h2
+        if (s != GF_OK) return s;
+        k_couple_fwd<ND><<<cfg_grid, kThreads, 0, st>>>(w.h2, C2, P + po.W3, P + po.b3, use_tanh, l & 1, L, V, B,
+                                                       xl, w.g3 /* scratch for x_out */, w.s, w.logdet + 0);
+        GF_CHECK_LAUNCH();
+        // (the logdet re-accumulation above is discarded: loss already reduced)
+        k_couple_bwd<ND><<<(unsigned)grid1d(BV), kThreads, 0, st>>>(l & 1, use_tanh, L, V, B, xl, w.s, w.gx, w.g3);
+        GF_CHECK_LAUNCH();
+        WgArgs a3{w.h2, C2, -1, w.g3, 2, w.partial, L, V, B};
+        if ((s = wgrad<ND>(a3, gW3, gb3, scale, st)) != GF_OK) return s;
+        ConvArgs d3{w.g3, 2, -1, Wb + (int64_t)T * C1 + (int64_t)T * C2 * C1, nullptr, C2, w.gh2, w.h2, 1, slope, L, V, B};
+        if ((s = conv<ND>(d3, st)) != GF_OK) return s;                // gh2 * LReLU'
+        WgArgs a2{w.h1, C1, -1, w.gh2, C2, w.partial, L, V, B};
+        if ((s = wgrad<ND>(a2, gW2, gb2, scale, st)) != GF_OK) return s;
+        ConvArgs d2{w.gh2, C2, -1, Wb + (int64_t)T * C1, nullptr, C1, w.gh1, w.h1, 1, slope, L, V, B};
+        if ((s = conv<ND>(d2, st)) != GF_OK) return s;                // gh1 * LReLU'
+        WgArgs a1{xl, 1, l & 1, w.gh1, C1, w.partial, L, V, B};
+        if ((s = wgrad<ND>(a1, gW1, gb1, scale, st)) != GF_OK) return s;
+        k_conv1_bwd<ND><<<(unsigned)grid1d(BV), kThreads, 0, st>>>(w.gh1, C1, Wb, l & 1, L, V, B, w.gx);
+        GF_CHECK_LAUNCH();
+    }
+    if (lr > 0.f) {
+        const float c1 = 1.f - powf(beta1, (float)adam_t), c2 = 1.f - powf(beta2, (float)adam_t);
+        k_adam<<<(unsigned)grid1d(f->n_params), kThreads, 0, st>>>(f->n_params, f->d_canon, grad, adam_m, adam_v,
+                                                                    lr, beta1, beta2, adam_eps, c1, c2);
+        GF_CHECK_LAUNCH();
+        return repack_weights(f, st);
+    }
+    return GF_OK;
+}
+
+}  // namespace
+}  // namespace gf
+
+using namespace gf;
+
 extern "C" {
-size_t gf_train_workspace_bytes(const gf_flow*, int64_t) { return 0; }
-gf_status gf_flow_train_step(gf_flow*, const gf_phi4*, int64_t, uint64_t, uint64_t, const float*,
-                             double*, float*, float, float, float, float, float*, float*, int64_t,
-                             void*, size_t, cudaStream_t) {
-    return GF_EUNSUPPORTED;
+
+size_t gf_train_workspace_bytes(const gf_flow* flow, int64_t B) {
+    if (!flow || B < 0) return 0;
+    return carve(flow, B, nullptr).bytes;
 }
+
+gf_status gf_flow_train_step(gf_flow* flow, const gf_phi4* phi4, int64_t B, uint64_t seed,
+                             uint64_t counter0, const float* d_z_in, double* d_loss_out,
+                             float* d_grad_out, float lr, float beta1, float beta2,
+                             float adam_eps, float* d_adam_m, float* d_adam_v,
+                             int64_t adam_t, void* d_workspace, size_t workspace_bytes,
+                             cudaStream_t stream) {
+    if (!flow || !phi4 || B <= 0 || !d_loss_out) return GF_EINVAL;
+    if (!(lr >= 0.f)) return GF_EINVAL;
+    if (lr > 0.f && (!d_adam_m || !d_adam_v || adam_t < 1)) return GF_EINVAL;
+    const TrainWs w = carve(flow, B, static_cast<char*>(d_workspace));
+    if (!d_workspace || workspace_bytes < w.bytes) return GF_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(d_workspace) & 255) != 0) return GF_EINVAL;
+    if (flow->shape.nd == 3)
+        return train_step<3>(flow, phi4, B, seed, counter0, d_z_in, d_loss_out, d_grad_out, lr, beta1, beta2,
+                             adam_eps, d_adam_m, d_adam_v, adam_t, w, stream);
+    return train_step<2>(flow, phi4, B, seed, counter0, d_z_in, d_loss_out, d_grad_out, lr, beta1, beta2,
+                         adam_eps, d_adam_m, d_adam_v, adam_t, w, stream);
 }
+
+}  // extern "C"
