@@ -1,17 +1,503 @@
-// gf_flow_bf16.cu -- BF16 tensor-core variant of the fused coupling stack.
-// Not built yet: flows requested with GF_PREC_BF16CONV_FP64RED are refused
-// with GF_EUNSUPPORTED at creation.
+// gf_flow_bf16.cu -- fused coupling stack with conv2 on the 5th-generation
+// tensor cores (tcgen05, BF16 operands, FP32 accumulation in TMEM), for 3D
+// lattices with L = 16 and hidden width 32.
+//
+// Paper arXiv:2208.08903 Sec. 1 (affine coupling layers, Jacobian, model
+// density, action); precision split of this variant: conv2 operands (h1 and
+// W2) in BF16, conv2 accumulation FP32, conv1/conv3/affine update in FP32,
+// h2 stored as BF16, the field x in FP32, and log-det, sum z^2, S, log q,
+// log w in FP64.
+//
+// Per CTA one configuration at a time (persistent), the same slice schedule
+// as the FP32 kernel with one z-slice (256 sites) per phase:
+//   H1: conv1 (FFMA, fixed-site taps only) -> h1 slot (BF16)
+//   H2: conv2 as implicit GEMM: per z-slice two M=128 tiles (8 y-rows x 16 x),
+//       N = 32 output channels, K = 9 (dz,dy) taps x 32 channels; one elected
+//       thread issues tcgen05.mma with shared-memory descriptors.
+//       Activations are stored channel-group major ([4][288 sites][8 ch],
+//       288 = 18 y-rows incl. one periodic halo row on each side), so each
+//       8-site core matrix is 128 contiguous bytes and a (dz,dy) shift is just
+//       a different start address.  The x-shift is not materialised: three
+//       accumulators P_dx (dx = -1, 0, +1) are kept in TMEM and the epilogue
+//       forms out(x) = sum_dx P_dx(x + dx) with width-16 warp shuffles (one
+//       x-row = one half-warp = 16 TMEM lanes).
+//   C3: conv3 at the updated sites (FFMA from BF16 h2) + affine update.
+#include <algorithm>
+#include <cstring>
+
+#include <cuda_bf16.h>
+
 #include "gf_flow.cuh"
 
 namespace gf {
 
-bool bf16_supported(const gf_flow_shape*) { return false; }
-gf_status bf16_configure(gf_flow*) { return GF_EUNSUPPORTED; }
-gf_status repack_bf16(gf_flow*, cudaStream_t) { return GF_EUNSUPPORTED; }
-gf_status launch_flow_bf16(const gf_flow*, bool, const gf_phi4*, int64_t, uint64_t, uint64_t,
-                           const float*, float*, const float*, float*, double*, double*, double*,
-                           cudaStream_t) {
-    return GF_EUNSUPPORTED;
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kL = 16, kS = 256, kC = 32, kT = 27;
+constexpr int kHaloSites = 18 * 16;                    // y = -1 .. 16
+constexpr int kSlotBytes = 4 * kHaloSites * 16;        // [cg][site][8] bf16 = 18432
+constexpr int kW2Bytes = kT * 4 * 32 * 16;             // [t][kg][n][8] bf16 = 55296
+// FP32 part of a layer block (floats): W1s[t][c], b1[c], b2[c], W3s[t][c][2], b3[2], pad
+constexpr int kF_W1 = 0, kF_b1 = kT * kC, kF_b2 = kF_b1 + kC, kF_W3 = kF_b2 + kC;
+constexpr int kF_b3 = kF_W3 + kT * kC * 2, kF_N = (kF_b3 + 2 + 3) & ~3;
+constexpr int kLayerBytes = kW2Bytes + kF_N * 4;
+constexpr int kTmemCols = 256;                         // 2 tiles x 3 dx x 32 columns, rounded up
+constexpr long long kWaitLimit = 1ll << 26;            // bounded mbarrier wait (iterations)
+
+// ---------------------------------------------------------------- PTX wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 :: "r"(smem_u32(dst)), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void fence_before_sync() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after_sync() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                 " selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+// D[tmem] (+)= A[smem] * B[smem]^T, kind::f16 (BF16 in, FP32 accumulate).
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                 :: "r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate) : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 :: "r"(smem_u32(bar)) : "memory");
+}
+// 32 lanes x 32 consecutive FP32 columns: thread i gets row (lane base + i).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                   "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                   "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+                   "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+                   "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                 : "r"(taddr) : "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Shared-memory matrix descriptor, no swizzle, K-major canonical layout:
+// core matrix = 8 rows x 16 bytes contiguous; LBO = byte distance between
+// core matrices adjacent in K, SBO = between 8-row groups.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;              // descriptor version for tcgen05
+    return d;                            // base offset 0, swizzle mode 0 (none)
+}
+// Instruction descriptor: D = F32, A = B = BF16, both K-major, N = 32, M = 128.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+
+struct Bf16Args {
+    const unsigned char* Wl;   // per-layer blocks of kLayerBytes
+    const Phase* sched;
+    int n_phases, n_layers;
+    float slope;
+    int use_tanh, has_phi4;
+    double m2, lam;
+    int64_t B;
+    uint64_t seed, counter0;
+    const float* z_in; float* z_out; const float* phi_in; float* phi_out;
+    double* logq_out; double* S_out; double* logw_out;
+    int32_t* status;
+};
+
+__device__ __forceinline__ int wrap16(int v) { return v & 15; }
+
+// halo-row site index of interior (y, x), y in -1..16
+__device__ __forceinline__ int hsite(int y, int x) { return (y + 1) * 16 + x; }
+
+// Stores 8 channels (one channel group) of a site row in BF16, plus the
+// periodic halo copy when the row is y = 0 or y = 15.
+__device__ __forceinline__ void store8(unsigned char* slot, int cg, int y, int x, const float* v) {
+    __align__(16) __nv_bfloat162 p[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) p[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+    const uint4 w = *reinterpret_cast<const uint4*>(p);
+    unsigned char* base = slot + (size_t)cg * kHaloSites * 16;
+    *reinterpret_cast<uint4*>(base + hsite(y, x) * 16) = w;
+    if (y == 0) *reinterpret_cast<uint4*>(base + hsite(16, x) * 16) = w;
+    if (y == 15) *reinterpret_cast<uint4*>(base + hsite(-1, x) * 16) = w;
+}
+
+template <bool INVERSE>
+__global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* w2s = smem;                                        // kW2Bytes
+    float* wf = reinterpret_cast<float*>(smem + kW2Bytes);            // kF_N floats
+    unsigned char* h1 = smem + kW2Bytes + kF_N * 4;                   // 3 slots
+    unsigned char* h2 = h1 + 3 * kSlotBytes;                          // 3 slots
+    float* x = reinterpret_cast<float*>(h2 + 3 * kSlotBytes);         // 4096 floats
+    double* red = reinterpret_cast<double*>(x + 4096);                // 32
+    Phase* ph = reinterpret_cast<Phase*>(red + 32);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(ph) + ((sizeof(Phase) + 7) & ~7));
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 1);
+    int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int V = 4096;
+    if (warp == 0) {
+        tmem_alloc(tmem_slot, kTmemCols);
+        tmem_relinquish();
+    }
+    if (tid == 0) {
+        mbar_init(mbar, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+    uint32_t phase_bit = 0;
+
+    for (int64_t b = blockIdx.x; b < a.B; b += gridDim.x) {
+        double sumz2 = 0.0;
+        if (!INVERSE) {
+            if (a.z_in) {
+                for (int n = tid; n < V; n += kThreads) {
+                    const float v = __ldg(a.z_in + b * V + n);
+                    x[n] = v;
+                    sumz2 += (double)v * v;
+                }
+            } else {
+                for (int j = tid; 4 * j < V; j += kThreads) {
+                    const u64x4 w = philox4x64_10(a.seed, 0ull,
+                                                  u64x4{a.counter0 + (uint64_t)b, (uint64_t)j, 0ull, TAG_PRIOR});
+                    float zz[4];
+                    normals4_f32(w, zz);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) { x[4 * j + q] = zz[q]; sumz2 += (double)zz[q] * zz[q]; }
+                }
+            }
+            __syncthreads();
+            if (a.z_out)
+                for (int n = tid; n < V; n += kThreads) a.z_out[b * V + n] = x[n];
+        } else {
+            for (int n = tid; n < V; n += kThreads) x[n] = __ldg(a.phi_in + b * V + n);
+        }
+        __syncthreads();
+
+        double logdet = 0.0;
+        for (int li = 0; li < a.n_layers; ++li) {
+            const int l = INVERSE ? a.n_layers - 1 - li : li;
+            const int frozen = l & 1;
+            // stage this layer's weights (W2 already in the MMA operand layout)
+            {
+                const uint4* src = reinterpret_cast<const uint4*>(a.Wl + (size_t)l * kLayerBytes);
+                uint4* dst = reinterpret_cast<uint4*>(smem);
+                for (int i = tid; i < kLayerBytes / 16; i += kThreads) dst[i] = __ldg(src + i);
+            }
+            fence_proxy_async();
+            __syncthreads();
+            const float slope = a.slope;
+            for (int p = 0; p < a.n_phases; ++p) {
+                if (tid < (int)(sizeof(Phase) / 4))
+                    reinterpret_cast<uint32_t*>(ph)[tid] =
+                        __ldg(reinterpret_cast<const uint32_t*>(a.sched + p) + tid);
+                __syncthreads();
+                const int type = ph->type;
+                const int s0 = ph->s0;
+                if (type == PH_H1) {
+                    // conv1: 256 sites x 4 channel groups; only fixed-site taps contribute
+                    unsigned char* slot = h1 + (size_t)ph->out[0] * kSlotBytes;
+                    for (int it = tid; it < kS * 4; it += kThreads) {
+                        const int j = it & (kS - 1), cg = it >> 8;
+                        const int y = j >> 4, xx = j & 15;
+                        float acc[8];
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) acc[c] = wf[kF_b1 + cg * 8 + c];
+                        for (int t = 0; t < kT; ++t) {
+                            const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
+                            const int z2 = wrap16(s0 + dz), y2 = wrap16(y + dy), x2 = wrap16(xx + dx);
+                            if (((z2 + y2 + x2) & 1) != frozen) continue;
+                            const float xv = x[(z2 * 16 + y2) * 16 + x2];
+                            const float* w = wf + kF_W1 + t * kC + cg * 8;
+#pragma unroll
+                            for (int c = 0; c < 8; ++c) acc[c] = fmaf(xv, w[c], acc[c]);
+                        }
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) acc[c] = acc[c] > 0.f ? acc[c] : slope * acc[c];
+                        store8(slot, cg, y, xx, acc);
+                    }
+                    fence_proxy_async();
+                } else if (type == PH_H2) {
+                    // conv2 on the tensor cores
+                    if (tid == 0) {
+                        fence_after_sync();
+                        const uint32_t w2a = smem_u32(w2s);
+#pragma unroll 1
+                        for (int mt = 0; mt < 2; ++mt) {
+#pragma unroll 1
+                            for (int dxi = 0; dxi < 3; ++dxi) {
+                                const uint32_t d = tmem + (uint32_t)((mt * 3 + dxi) * 32);
+                                uint32_t acc = 0;
+#pragma unroll 1
+                                for (int dzi = 0; dzi < 3; ++dzi) {
+                                    const uint32_t slot = smem_u32(h1 + (size_t)ph->in[dzi] * kSlotBytes);
+#pragma unroll 1
+                                    for (int dyi = 0; dyi < 3; ++dyi) {
+                                        const int t = (dzi * 3 + dyi) * 3 + dxi;
+#pragma unroll
+                                        for (int k = 0; k < 2; ++k) {
+                                            const uint32_t aaddr = slot + (uint32_t)(2 * k * kHaloSites * 16) +
+                                                                   (uint32_t)((mt * 8 + dyi) * 16 * 16);
+                                            const uint32_t baddr = w2a + (uint32_t)(t * 2048 + 2 * k * 512);
+                                            mma_bf16(d, smem_desc(aaddr, kHaloSites * 16, 128),
+                                                     smem_desc(baddr, 512, 128), kIdesc, acc);
+                                            acc = 1;
+                                        }
+                                    }
+                                }
+                            }
+                        }
+                        mma_commit(mbar);
+                    }
+                    // wait for the accumulators (bounded)
+                    long long spins = 0;
+                    while (!mbar_try_wait(mbar, phase_bit)) {
+                        if (++spins > kWaitLimit) { *abort_flag = 1; set_status(a.status, GF_ETIMEOUT); break; }
+                    }
+                    phase_bit ^= 1u;
+                    fence_after_sync();
+                    // epilogue: warp w -> tile w/4, TMEM lanes 32*(w%4) .. +31
+                    const int mt = warp >> 2, q = warp & 3;
+                    const int y = mt * 8 + q * 2 + (lane >> 4), xx = lane & 15;
+                    float pm[32], p0[32], pp[32];
+                    const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+                    tmem_ld32(tmem + lane_base + (uint32_t)((mt * 3 + 0) * 32), pm);
+                    tmem_ld32(tmem + lane_base + (uint32_t)((mt * 3 + 1) * 32), p0);
+                    tmem_ld32(tmem + lane_base + (uint32_t)((mt * 3 + 2) * 32), pp);
+                    tmem_ld_wait();
+                    const int src_m = (lane & 16) | ((xx + 15) & 15);   // x - 1
+                    const int src_p = (lane & 16) | ((xx + 1) & 15);    // x + 1
+                    unsigned char* slot = h2 + (size_t)ph->out[0] * kSlotBytes;
+#pragma unroll
+                    for (int cg = 0; cg < 4; ++cg) {
+                        float v[8];
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) {
+                            const int ch = cg * 8 + c;
+                            const float s = p0[ch] + __shfl_sync(0xffffffffu, pm[ch], src_m) +
+                                            __shfl_sync(0xffffffffu, pp[ch], src_p) + wf[kF_b2 + ch];
+                            v[c] = s > 0.f ? s : slope * s;
+                        }
+                        store8(slot, cg, y, xx, v);
+                    }
+                    fence_before_sync();
+                } else {
+                    // conv3 at the 128 updated sites of slice s0 (2 threads per site) + affine update
+                    const int ai = tid >> 1, half = tid & 1;
+                    const int y = ai >> 3, k = ai & 7;
+                    const int xx = 2 * k + ((frozen ^ 1 ^ s0 ^ y) & 1);
+                    float ps = 0.f, pt = 0.f;
+                    for (int t = 0; t < kT; ++t) {
+                        const int dzi = t / 9, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
+                        const unsigned char* slot = h2 + (size_t)ph->in[dzi] * kSlotBytes;
+                        const int hs = hsite(y + dy, wrap16(xx + dx));
+                        const float* w = wf + kF_W3 + t * kC * 2;
+#pragma unroll
+                        for (int g = 0; g < 2; ++g) {
+                            const int cg = half * 2 + g;
+                            const uint4 raw = *reinterpret_cast<const uint4*>(slot + ((size_t)cg * kHaloSites + hs) * 16);
+                            const __nv_bfloat162* hv = reinterpret_cast<const __nv_bfloat162*>(&raw);
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) {
+                                const float2 f = __bfloat1622float2(hv[i]);
+                                const int ch = cg * 8 + 2 * i;
+                                ps = fmaf(f.x, w[2 * ch], ps); pt = fmaf(f.x, w[2 * ch + 1], pt);
+                                ps = fmaf(f.y, w[2 * ch + 2], ps); pt = fmaf(f.y, w[2 * ch + 3], pt);
+                            }
+                        }
+                    }
+                    ps += __shfl_xor_sync(0xffffffffu, ps, 1);
+                    pt += __shfl_xor_sync(0xffffffffu, pt, 1);
+                    if (half == 0) {
+                        const float spre = ps + wf[kF_b3], tt = pt + wf[kF_b3 + 1];
+                        const float s = a.use_tanh ? tanhf(spre) : spre;
+                        float& xv = x[(s0 * 16 + y) * 16 + xx];
+                        if (!INVERSE) xv = fmaf(xv, expf(s), tt);
+                        else xv = (xv - tt) * expf(-s);
+                        logdet += (double)s;
+                    }
+                }
+                __syncthreads();
+                if (*abort_flag) break;
+            }
+            if (*abort_flag) break;
+        }
+        if (*abort_flag) break;
+
+        if (INVERSE) {
+            for (int n = tid; n < V; n += kThreads) {
+                const float v = x[n];
+                sumz2 += (double)v * v;
+                if (a.z_out) a.z_out[b * V + n] = v;
+            }
+        } else {
+            for (int n = tid; n < V; n += kThreads) a.phi_out[b * V + n] = x[n];
+        }
+        const double ld = block_sum(logdet, red);
+        const double z2 = block_sum(sumz2, red);
+        double S = 0.0;
+        if (!INVERSE && a.has_phi4) {
+            double acc = 0.0;
+            for (int n = tid; n < V; n += kThreads) {
+                const int xc = n & 15, yc = (n >> 4) & 15, zc = n >> 8;
+                const double p = x[n];
+                double kk = 6.0 * p;
+                kk -= (double)x[(n & ~15) | wrap16(xc + 1)] + (double)x[(n & ~15) | wrap16(xc - 1)];
+                kk -= (double)x[(zc << 8) | (wrap16(yc + 1) << 4) | xc] + (double)x[(zc << 8) | (wrap16(yc - 1) << 4) | xc];
+                kk -= (double)x[(wrap16(zc + 1) << 8) | (yc << 4) | xc] + (double)x[(wrap16(zc - 1) << 8) | (yc << 4) | xc];
+                const double p2 = p * p;
+                acc += p * kk + a.m2 * p2 + a.lam * p2 * p2;
+            }
+            S = block_sum(acc, red);
+        }
+        if (tid == 0) {
+            const double logr = -0.5 * z2 - 0.5 * (double)V * LOG_2PI;
+            const double logq = logr - ld;
+            a.logq_out[b] = logq;
+            if (!INVERSE && a.has_phi4) {
+                if (a.S_out) a.S_out[b] = S;
+                if (a.logw_out) a.logw_out[b] = -S - logq;
+            }
+        }
+        __syncthreads();
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after_sync();
+        tmem_dealloc(tmem, kTmemCols);
+    }
+}
+
+constexpr size_t kSmemBytes = (size_t)kW2Bytes + kF_N * 4 + 6 * (size_t)kSlotBytes + 4096 * 4 + 32 * 8 +
+                              ((sizeof(Phase) + 7) & ~size_t(7)) + 8 + 4 + 4;
+
+// canonical FP32 -> per-layer BF16 block (W2 in [t][kg][n][8]) + FP32 block
+__global__ void repack_bf16_kernel(const float* __restrict__ canon, int64_t cstride, int n_layers,
+                                   unsigned char* __restrict__ out) {
+    const int64_t per = kT * 4 * 32 * 8 + kF_N;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < per * n_layers;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int l = (int)(i / per);
+        const int64_t r = i - l * per;
+        const float* W = canon + l * cstride;
+        const float* W1 = W;                    // [c][0][t]
+        const float* b1 = W1 + kC * kT;
+        const float* W2 = b1 + kC;              // [o][i][t]
+        const float* b2 = W2 + kC * kC * kT;
+        const float* W3 = b2 + kC;              // [o][i][t]
+        const float* b3 = W3 + 2 * kC * kT;
+        unsigned char* blk = out + (size_t)l * kLayerBytes;
+        if (r < kT * 4 * 32 * 8) {
+            const int e = (int)(r & 7), n = (int)((r >> 3) & 31), kg = (int)((r >> 8) & 3), t = (int)(r >> 10);
+            const float v = W2[((int64_t)n * kC + kg * 8 + e) * kT + t];
+            reinterpret_cast<__nv_bfloat16*>(blk)[r] = __float2bfloat16_rn(v);
+        } else {
+            const int f = (int)(r - kT * 4 * 32 * 8);
+            float v = 0.f;
+            if (f < kF_b1) v = W1[(f % kC) * kT + f / kC];
+            else if (f < kF_b2) v = b1[f - kF_b1];
+            else if (f < kF_W3) v = b2[f - kF_b2];
+            else if (f < kF_b3) {
+                const int g = f - kF_W3, o = g & 1, c = (g >> 1) % kC, t = g / (2 * kC);
+                v = W3[((int64_t)o * kC + c) * kT + t];
+            } else if (f < kF_b3 + 2) v = b3[f - kF_b3];
+            reinterpret_cast<float*>(blk + kW2Bytes)[f] = v;
+        }
+    }
+}
+
+}  // namespace
+
+bool bf16_supported(const gf_flow_shape* s) {
+    return s && s->nd == 3 && s->L == kL && s->c_hidden1 == kC && s->c_hidden2 == kC && s->ksize == 3;
+}
+
+gf_status bf16_configure(gf_flow* f) {
+    if (!bf16_supported(&f->shape)) return GF_EUNSUPPORTED;
+    // the BF16 kernel uses the one-slice ring schedule
+    f->full = false;
+    f->G = 1;
+    f->R = 3;
+    f->smem_bytes_bf16 = kSmemBytes;
+    if (cudaMalloc(&f->d_bf16, (size_t)kLayerBytes * std::max(1, f->shape.n_layers)) != cudaSuccess)
+        return GF_ENOMEM;
+    return GF_OK;
+}
+
+gf_status repack_bf16(gf_flow* f, cudaStream_t stream) {
+    const int64_t total = (int64_t)(kT * 4 * 32 * 8 + kF_N) * f->shape.n_layers;
+    const int grid = (int)std::min<int64_t>((total + 255) / 256, 4096);
+    if (total == 0) return GF_OK;
+    repack_bf16_kernel<<<grid, 256, 0, stream>>>(f->d_canon, f->canon_stride, f->shape.n_layers,
+                                                 static_cast<unsigned char*>(f->d_bf16));
+    GF_CHECK_LAUNCH();
+    return GF_OK;
+}
+
+gf_status launch_flow_bf16(const gf_flow* f, bool inverse, const gf_phi4* phi4, int64_t B,
+                           uint64_t seed, uint64_t counter0, const float* z_in, float* z_out,
+                           const float* phi_in, float* phi_out, double* logq_out,
+                           double* S_out, double* logw_out, cudaStream_t stream) {
+    Bf16Args a;
+    std::memset(&a, 0, sizeof(a));
+    a.Wl = static_cast<const unsigned char*>(f->d_bf16);
+    a.sched = f->d_sched;
+    a.n_phases = f->n_phases;
+    a.n_layers = f->shape.n_layers;
+    a.slope = (float)f->shape.leaky_slope;
+    a.use_tanh = f->shape.use_final_tanh;
+    a.has_phi4 = phi4 != nullptr;
+    a.m2 = phi4 ? phi4->m2 : 0.0;
+    a.lam = phi4 ? phi4->lam : 0.0;
+    a.B = B; a.seed = seed; a.counter0 = counter0;
+    a.z_in = z_in; a.z_out = z_out; a.phi_in = phi_in; a.phi_out = phi_out;
+    a.logq_out = logq_out; a.S_out = S_out; a.logw_out = logw_out;
+    a.status = status_word();
+    if (!a.status) return GF_ECUDA;
+    auto kern = inverse ? flow_bf16_kernel<true> : flow_bf16_kernel<false>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes) != cudaSuccess)
+        return GF_ECUDA;
+    const int64_t grid = std::min<int64_t>(B, (int64_t)num_sms());
+    kern<<<(unsigned)grid, kThreads, kSmemBytes, stream>>>(a);
+    GF_CHECK_LAUNCH();
+    return GF_OK;
 }
 
 }  // namespace gf
