@@ -150,6 +150,30 @@ gf_status gf_mh_chain(gf_mh_state* d_state, int64_t n, const double* d_logw,
                       int64_t* d_chain_idx_out, uint8_t* d_acc_out,
                       void* d_workspace, size_t workspace_bytes, cudaStream_t stream);
 
+/* Largest n accepted by gf_mh_chain_noalloc (1 MiB of device scratch). */
+#define GF_MH_NOALLOC_MAX_N 131072
+
+/* Same chain as gf_mh_chain, for callers that cannot allocate device memory
+ * where they run the chain: for example a serving loop that owns a fixed
+ * memory budget handed out by its own allocator, or a latency-critical
+ * thread that must not risk the device-wide synchronisation a cudaMalloc can
+ * cause.  The paper has no counterpart; this is an interface convenience.
+ *
+ * The log-u scratch lives in a fixed device array inside the library
+ * (GF_MH_NOALLOC_MAX_N doubles, held on every device that loads the
+ * library until the process exits).  The caller still passes the state,
+ * log weights and outputs (same meaning as for gf_mh_chain).  No memory is
+ * allocated.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  n > GF_MH_NOALLOC_MAX_N returns GF_EINVAL.
+ * Every call on a device shares the one array and leaves its contents
+ * behind; each call writes every entry it reads before reading it, so
+ * nothing needs clearing, but calls that overlap on the GPU (different
+ * streams, no ordering between them) race on it and must not be issued. */
+gf_status gf_mh_chain_noalloc(gf_mh_state* d_state, int64_t n, const double* d_logw,
+                              int64_t* d_chain_idx_out, uint8_t* d_acc_out,
+                              cudaStream_t stream);
+
 /* ---------------------------------------------------------------------- */
 /* HMC comparison sampler (paper Sec. 2.2: HMC for the same theory)        */
 /* ---------------------------------------------------------------------- */

@@ -7,5 +7,6 @@ library libgfflow.so (C ABI: include/gfflow.h) does all the arithmetic; this
 package is its ctypes/torch binding.
 """
 from .api import (Flow, SampleResult, device_status, hmc_trajectory, mh_chain,  # noqa: F401
+                  mh_chain_noalloc,
                   mh_chain_workspace_bytes, new_mh_state, phi4_action, phi4_force,
                   read_mh_state)

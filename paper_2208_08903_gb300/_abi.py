@@ -12,11 +12,13 @@ from . import build as _build
 
 GF_OK, GF_EINVAL, GF_ENOMEM, GF_ECUDA, GF_EUNSUPPORTED, GF_ETIMEOUT, GF_EDEVICE = 0, -1, -2, -3, -4, -5, -6
 GF_PREC_FP32, GF_PREC_BF16CONV_FP64RED = 0, 1
+GF_MH_NOALLOC_MAX_N = 131072     # include/gfflow.h
 
 EXPORTED = [
     "gf_flow_create", "gf_flow_destroy", "gf_flow_n_params", "gf_flow_set_weights_device",
     "gf_flow_get_weights_device", "gf_flow_sample", "gf_flow_logq", "gf_phi4_action",
-    "gf_phi4_force", "gf_mh_chain_workspace_bytes", "gf_mh_chain", "gf_hmc_trajectory",
+    "gf_phi4_force", "gf_mh_chain_workspace_bytes", "gf_mh_chain", "gf_mh_chain_noalloc",
+    "gf_hmc_trajectory",
     "gf_train_workspace_bytes", "gf_flow_train_step", "gf_device_status", "gf_status_string",
 ]
 
@@ -75,6 +77,7 @@ def load():
         "gf_phi4_force": ([_I32, _I32, C.POINTER(Phi4C), _I64, _VP, _VP, _VP], _I32),
         "gf_mh_chain_workspace_bytes": ([_I64], _SZ),
         "gf_mh_chain": ([_VP, _I64, _VP, _VP, _VP, _VP, _SZ, _VP], _I32),
+        "gf_mh_chain_noalloc": ([_VP, _I64, _VP, _VP, _VP, _VP], _I32),
         "gf_hmc_trajectory": ([_I32, _I32, C.POINTER(Phi4C), _I64, _VP, _I32, _F64, _U64, _U64,
                                _VP, _VP, _VP], _I32),
         "gf_train_workspace_bytes": ([_VP, _I64], _SZ),

@@ -212,6 +212,23 @@ def mh_chain(state: torch.Tensor, logw: torch.Tensor, workspace: torch.Tensor | 
     return chain_idx, acc
 
 
+def mh_chain_noalloc(state: torch.Tensor, logw: torch.Tensor,
+                     chain_idx: torch.Tensor | None = None, acc: torch.Tensor | None = None):
+    """gf_mh_chain without caller workspace: the library's fixed device scratch
+    holds log u (at most GF_MH_NOALLOC_MAX_N proposals per call; calls that
+    overlap on the GPU must not be issued)."""
+    _need(state, torch.int64, "state", 6)
+    n = logw.numel()
+    _need(logw, torch.float64, "logw", n)
+    if chain_idx is None:
+        chain_idx = torch.empty(n, device=logw.device, dtype=torch.int64)
+    if acc is None:
+        acc = torch.empty(n, device=logw.device, dtype=torch.uint8)
+    _abi.check("gf_mh_chain_noalloc", _abi.load().gf_mh_chain_noalloc(
+        _ptr(state), n, _ptr(logw), _ptr(chain_idx), _ptr(acc), _stream()))
+    return chain_idx, acc
+
+
 def hmc_trajectory(nd: int, L: int, phi4, phi: torch.Tensor, n_steps: int, eps: float,
                    seed: int, traj_index: int):
     """Updates phi [n_chains][V] (FP64) in place; returns (dH, acc)."""

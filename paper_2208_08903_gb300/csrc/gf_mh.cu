@@ -12,6 +12,7 @@
 //     after it are re-tested.  A chunk costs 1 + (accepts in it) rounds of
 //     ballot instead of 32 dependent steps.  The state stays in device memory.
 #include <algorithm>
+#include <mutex>
 
 #include "gf_common.cuh"
 
@@ -84,6 +85,33 @@ gf_status mh_launch(gf_mh_state* d_state, int64_t n, const double* d_logw, int64
     return GF_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free variant: log u goes to a fixed device array owned by the
+// library instead of caller workspace.  Host code cannot use the array's
+// name as a device address, so its address is looked up once per device.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) double g_mh_noalloc_logu[GF_MH_NOALLOC_MAX_N];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[kMaxDevices] = {};
+
+gf_status noalloc_scratch(double** out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GF_ECUDA;
+    if (dev < 0 || dev >= kMaxDevices) return GF_EUNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (g_noalloc_ptr[dev] == nullptr) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_mh_noalloc_logu) != cudaSuccess || p == nullptr) return GF_ECUDA;
+        g_noalloc_ptr[dev] = static_cast<double*>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return GF_OK;
+}
+}  // namespace
+
 }  // namespace gf
 
 using namespace gf;
@@ -102,6 +130,19 @@ gf_status gf_mh_chain(gf_mh_state* d_state, int64_t n, const double* d_logw,
     if ((reinterpret_cast<uintptr_t>(d_workspace) & 7) != 0) return GF_EINVAL;
     return mh_launch(d_state, n, d_logw, d_chain_idx_out, d_acc_out,
                      static_cast<double*>(d_workspace), stream);
+}
+
+gf_status gf_mh_chain_noalloc(gf_mh_state* d_state, int64_t n, const double* d_logw,
+                              int64_t* d_chain_idx_out, uint8_t* d_acc_out, cudaStream_t stream) {
+    if (!d_state || n < 0) return GF_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(d_state) & 7) != 0) return GF_EINVAL;
+    if (n > GF_MH_NOALLOC_MAX_N) return GF_EINVAL;
+    if (n == 0) return GF_OK;
+    if (!d_logw) return GF_EINVAL;
+    double* scratch = nullptr;
+    const gf_status st = noalloc_scratch(&scratch);
+    if (st != GF_OK) return st;
+    return mh_launch(d_state, n, d_logw, d_chain_idx_out, d_acc_out, scratch, stream);
 }
 
 }  // extern "C"
