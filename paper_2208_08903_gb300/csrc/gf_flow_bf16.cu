@@ -43,7 +43,7 @@ constexpr int kF_W1 = 0, kF_b1 = kT * kC, kF_b2 = kF_b1 + kC, kF_W3 = kF_b2 + kC
 constexpr int kF_b3 = kF_W3 + kT * kC * 2, kF_N = (kF_b3 + 2 + 3) & ~3;
 constexpr int kLayerBytes = kW2Bytes + kF_N * 4;
 constexpr int kTmemCols = 256;                         // 2 tiles x 3 dx x 32 columns, rounded up
-constexpr long long kWaitLimit = 1ll << 26;            // bounded mbarrier wait (iterations)
+constexpr long long kWaitLimit = 1ll << 22;            // bounded mbarrier wait (iterations)
 
 // ---------------------------------------------------------------- PTX wrappers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {

@@ -1,0 +1,95 @@
+"""GPU parity of the BF16 tensor-core variant (3D L=16, hidden 32).
+
+The kernel rounds h1 (after LeakyReLU), the conv2 weights and h2 (after
+LeakyReLU) to bf16 and accumulates conv2 in FP32 on the tensor cores; all sums
+over the lattice are FP64.  It is compared with the oracle in the matching
+BF16-emulation mode (same rounding points, FP64 elsewhere) with
+    |a-b| <= 1e-4 * max(|b|, rms(b))  per site,  1e-4 * max(|b|, 1) per log-weight,
+and its error against the pure FP64 oracle is reported (max and p99 per result).
+"""
+import numpy as np
+import pytest
+
+import gf_inputs as gi
+from gpu_util import assert_logw_close, assert_sites_close, require_gpu
+
+pytestmark = pytest.mark.gpu
+BF16_MODE = 1 | 2 | 4 | 32          # H1 | W2 | H2 | FP32 prior
+RTOL = 1e-4
+
+
+def _report(name, gpu, ref):
+    gpu = np.asarray(gpu, np.float64)
+    ref = np.asarray(ref, np.float64)
+    if gpu.ndim == 2:
+        scale = np.maximum(np.abs(ref), np.sqrt((ref**2).mean(1, keepdims=True)))
+    else:
+        scale = np.maximum(np.abs(ref), 1.0)
+    e = np.abs(gpu - ref) / scale
+    print(f"{name}: max {e.max():.3e} p99 {np.percentile(e, 99):.3e}")
+    return e
+
+
+@pytest.mark.parametrize("n_layers,B", [(2, 3), (16, 3)])
+def test_bf16_sample_matches_emulated_oracle(orc, n_layers, B):
+    torch, P = require_gpu()
+    shape = gi.FlowShape(3, 16, n_layers, 32, 32)
+    m2, lam = -6.0, 5.0
+    w = gi.init_weights(shape, seed=0)
+    flow = P.Flow(shape, w, precision="bf16")
+    out = flow.sample(B, seed=21, counter0=5, phi4=(m2, lam), return_z=True)
+    torch.cuda.synchronize()
+    assert P.device_status() == 0
+    ref = orc.flow_sample(shape, w, m2, lam, B, seed=21, counter0=5, bf16_mask=BF16_MODE)
+    assert_sites_close(out.z.cpu().numpy(), ref["z"], rtol=1e-6, what="z")
+    assert_sites_close(out.phi.cpu().numpy(), ref["phi"], rtol=RTOL)
+    for k in ("logq", "S", "logw"):
+        assert_logw_close(getattr(out, k).cpu().numpy(), ref[k], rtol=RTOL, what=k)
+    # error of the BF16 path against the pure FP64 oracle, stated per result
+    f64 = orc.flow_sample(shape, w, m2, lam, B, seed=21, counter0=5)
+    _report("phi vs FP64", out.phi.cpu().numpy(), f64["phi"])
+    for k in ("logq", "S", "logw"):
+        _report(f"{k} vs FP64", getattr(out, k).cpu().numpy(), f64[k])
+
+
+def test_bf16_given_z_and_inverse(orc):
+    torch, P = require_gpu()
+    shape = gi.FlowShape(3, 16, 4, 32, 32, use_final_tanh=False)
+    w = gi.init_weights(shape, seed=4)
+    flow = P.Flow(shape, w, precision="bf16")
+    z = orc.prior(shape.V, 2, seed=8, counter0=0, f32=True)
+    zt = torch.tensor(z, dtype=torch.float32, device="cuda")
+    out = flow.sample(2, phi4=(-6.0, 5.0), z=zt)
+    ref = orc.flow_sample(shape, w, -6.0, 5.0, 2, z=z, bf16_mask=BF16_MODE)
+    assert_sites_close(out.phi.cpu().numpy(), ref["phi"], rtol=RTOL)
+    zb, lq = flow.logq(out.phi, return_z=True)
+    zr, lqr = orc.flow_logq(shape, w, out.phi.cpu().numpy().astype(np.float64), bf16_mask=BF16_MODE)
+    assert_sites_close(zb.cpu().numpy(), zr, rtol=RTOL, what="z(inverse)")
+    assert_logw_close(lq.cpu().numpy(), lqr, rtol=RTOL, what="logq(inverse)")
+    assert P.device_status() == 0
+
+
+def test_bf16_full_batch_sampled(orc):
+    """Batch 4096 at the benchmark's launch configuration, sampled configurations."""
+    torch, P = require_gpu()
+    W = gi.WORKLOADS["c3"]
+    shape, phi4, B = W["shape"], W["phi4"], W["batch"]
+    w = gi.init_weights(shape)
+    flow = P.Flow(shape, w, precision="bf16")
+    out = flow.sample(B, seed=2024, counter0=0, phi4=phi4)
+    torch.cuda.synchronize()
+    for b in (0, 1, 2047, B - 1):
+        ref = orc.flow_sample(shape, w, phi4.m2, phi4.lam, 1, seed=2024, counter0=b, bf16_mask=BF16_MODE)
+        assert_sites_close(out.phi[b:b + 1].cpu().numpy(), ref["phi"], rtol=RTOL, what=f"phi[{b}]")
+        assert_logw_close(out.logw[b:b + 1].cpu().numpy(), ref["logw"], rtol=RTOL, what=f"logw[{b}]")
+    assert torch.isfinite(out.phi).all()
+    S = P.phi4_action(3, 16, phi4, out.phi)
+    assert_logw_close(S.cpu().numpy(), out.S.cpu().numpy(), rtol=1e-12, what="fused vs standalone S")
+    assert P.device_status() == 0
+
+
+def test_bf16_rejects_other_shapes():
+    torch, P = require_gpu()
+    shape = gi.FlowShape(3, 8, 2, 32, 32)
+    with pytest.raises(P._abi.GFError):
+        P.Flow(shape, gi.init_weights(shape), precision="bf16")
