@@ -144,7 +144,7 @@ def bench_gpu(args, rank, world, local):
     shape, phi4, B = W["shape"], W["phi4"], args.batch or W["batch"]
     prec = args.precision
     if prec == "auto":
-        prec = "fp32"
+        prec = "bf16" if (shape.nd == 3 and shape.L == 16 and shape.c1 == 32 and shape.c2 == 32) else "fp32"
     flow = P.Flow(shape, gi.init_weights(shape, seed=0), precision=prec)
     V = shape.V
     out = P.SampleResult(phi=torch.empty(B, V, device=dev),
@@ -261,7 +261,128 @@ def bench_gpu(args, rank, world, local):
                "acceptance": st.n_acc / max(1, st.step - 1)},
         "flow_kernel_ms": float(np.mean(flow_ms)),
     }
+    del flush
+    if world == 1 and not args.no_extra:
+        flush2 = torch.empty(2 * L2_BYTES // 4, device=dev, dtype=torch.float32)
+        res["extra"] = bench_extra(args, dev, flush2, pk)
+        pl = res["extra"]["plain_fp32_unfused"]["configs_per_s"]
+        res["extra"]["speedup_vs_plain_fp32"] = value / pl
     return res
+
+
+# --------------------------------------------------------------------------- secondary measurements
+def _time_steps(fn, steps, warmup, flush=None):
+    """Per-step CUDA-event times (ms) on the current stream, L2 flushed between steps."""
+    import torch
+    stream = torch.cuda.current_stream()
+    for i in range(warmup):
+        fn(i)
+    torch.cuda.synchronize()
+    ts = []
+    for i in range(steps):
+        if flush is not None:
+            flush.fill_(float(i))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn(warmup + i)
+        b.record(stream)
+        ts.append((a, b))
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ts]
+
+
+def bench_extra(args, dev, flush, pk):
+    """Secondary lines: plain FP32 arm, training step, HMC, action GB/s, MH, c1."""
+    import torch
+    import paper_2208_08903_gb300 as P
+    out = {}
+    W = gi.WORKLOADS[args.workload]
+    shape, phi4, B = W["shape"], W["phi4"], args.batch or W["batch"]
+    w = gi.init_weights(shape, seed=0)
+    V = shape.V
+
+    def sampling_rate(kind, steps=3):
+        flow = P.Flow(shape, w, precision="fp32")
+        res = P.SampleResult(phi=torch.empty(B, V, device=dev),
+                             logq=torch.empty(B, device=dev, dtype=torch.float64),
+                             S=torch.empty(B, device=dev, dtype=torch.float64),
+                             logw=torch.empty(B, device=dev, dtype=torch.float64))
+        st = P.new_mh_state(seed=12345, device=dev)
+        ws = torch.empty(flow.unfused_workspace_bytes(B), device=dev, dtype=torch.uint8) if kind == "unfused" else None
+
+        def step(i):
+            if kind == "unfused":
+                flow.sample_unfused(B, seed=2024, counter0=i * B, phi4=phi4, out=res, workspace=ws)
+            else:
+                flow.sample(B, seed=2024, counter0=i * B, phi4=phi4, out=res)
+            P.mh_chain(st, res.logw)
+        t = _time_steps(step, steps, 1, flush)
+        s = P.read_mh_state(st)
+        del ws
+        return {"configs_per_s": B * len(t) / (sum(t) / 1e3), "ms_per_step": float(np.mean(t)),
+                "acceptance": s.n_acc / max(1, s.step - 1)}
+
+    out["plain_fp32_unfused"] = sampling_rate("unfused")
+    out["fused_fp32"] = sampling_rate("fused")
+    torch.cuda.empty_cache()
+
+    # reverse-KL training step, 2D L=32, 24 couplings, hidden 32, batch 1024, Adam
+    W2 = gi.WORKLOADS["c2"]
+    f2 = P.Flow(W2["shape"], gi.init_weights(W2["shape"]))
+    m = torch.zeros(f2.n_params, device=dev)
+    v = torch.zeros(f2.n_params, device=dev)
+    ws2 = torch.empty(f2.train_workspace_bytes(W2["batch"]), device=dev, dtype=torch.uint8)
+    t = _time_steps(lambda i: f2.train_step(W2["batch"], W2["phi4"], seed=12345, counter0=i * W2["batch"],
+                                            lr=1e-3, adam_m=m, adam_v=v, adam_t=i + 1, workspace=ws2,
+                                            grad=False), 3, 2, flush)
+    fl = 4 * flops_per_config(W2["shape"]) * W2["batch"]
+    out["train_c2"] = {"steps_per_s": 1e3 / float(np.mean(t)), "ms_per_step": float(np.mean(t)),
+                       "approx_tflops": fl / (float(np.mean(t)) / 1e3) / 1e12,
+                       "workload": "2D L=32, 24 couplings, hidden 32, batch 1024, forward+backward+Adam"}
+    del ws2, f2
+    torch.cuda.empty_cache()
+
+    # HMC, 3D L=16, 512 chains, 20 leapfrog steps, eps 0.05, FP64
+    W4 = gi.WORKLOADS["c4"]
+    phi = torch.zeros(W4["chains"], W4["L"] ** 3, device=dev, dtype=torch.float64)
+    t = _time_steps(lambda i: P.hmc_trajectory(3, W4["L"], W4["phi4"], phi, W4["n_steps"], W4["eps"], 7, i),
+                    20, 3, None)
+    traj_ms = float(np.mean(t))
+    out["hmc_c4"] = {"trajectories_per_s": 1e3 / traj_ms, "ms_per_trajectory_all_chains": traj_ms,
+                     "chain_trajectories_per_s": W4["chains"] * 1e3 / traj_ms,
+                     "seconds_for_1000_trajectories": traj_ms,
+                     "workload": "3D L=16, 512 chains, 20 steps, eps=0.05, FP64"}
+
+    # standalone action: HBM-bound
+    phi32 = torch.randn(B, V, device=dev)
+    S = torch.empty(B, device=dev, dtype=torch.float64)
+    t = _time_steps(lambda i: P.phi4_action(shape.nd, shape.L, phi4, phi32, out=S), 10, 3, flush)
+    gbs = (B * V * 4 + B * 8) / (float(np.mean(t)) / 1e3) / 1e9
+    out["action_fp32"] = {"GB_per_s": gbs, "frac_of_hbm": gbs / pk.get("hbm_gbs", 6800.0),
+                          "bytes_per_launch": B * V * 4 + B * 8, "ms": float(np.mean(t))}
+
+    # MH chain alone, 100k proposals
+    n = 100000
+    lw = torch.randn(n, device=dev, dtype=torch.float64) * 2 - 50
+    st = P.new_mh_state(seed=1, device=dev)
+    wsm = torch.empty(n, device=dev, dtype=torch.float64)
+    t = _time_steps(lambda i: P.mh_chain(st, lw, workspace=wsm), 5, 2, None)
+    out["mh_chain"] = {"ns_per_proposal": float(np.mean(t)) * 1e6 / n, "proposals": n}
+
+    # the paper's example workload (2D L=8, 16 couplings, hidden 8, batch 64)
+    W1 = gi.WORKLOADS["c1"]
+    f1 = P.Flow(W1["shape"], gi.init_weights(W1["shape"]))
+    r1 = P.SampleResult(phi=torch.empty(64, 64, device=dev), logq=torch.empty(64, device=dev, dtype=torch.float64),
+                        S=torch.empty(64, device=dev, dtype=torch.float64),
+                        logw=torch.empty(64, device=dev, dtype=torch.float64))
+    st1 = P.new_mh_state(seed=2, device=dev)
+
+    def c1step(i):
+        f1.sample(64, seed=3, counter0=64 * i, phi4=W1["phi4"], out=r1)
+        P.mh_chain(st1, r1.logw)
+    t = _time_steps(c1step, 50, 5, None)
+    out["c1_sampling"] = {"configs_per_s": 64 / (float(np.mean(t)) / 1e3), "ms_per_step": float(np.mean(t))}
+    return out
 
 
 # --------------------------------------------------------------------------- CPU oracle
@@ -333,6 +454,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=120.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the secondary measurements")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -115,6 +115,20 @@ gf_status gf_flow_sample(const gf_flow* flow, const gf_phi4* phi4, int64_t B,
 gf_status gf_flow_logq(const gf_flow* flow, int64_t B, const float* d_phi_in,
                        float* d_z_out, double* d_logq_out, cudaStream_t stream);
 
+/* The same function as gf_flow_sample computed the plain way: one kernel per
+ * convolution (conv1, conv2, conv3 + affine update) per layer with every
+ * activation written to and read back from device memory, then one kernel
+ * for log r, S, log q and log w.  FP32 throughout except the FP64 sums.  It
+ * is the comparison point for the fused kernels (same results within the
+ * FP32 tolerance).  d_workspace: >= gf_unfused_workspace_bytes(flow, B)
+ * bytes of device memory, 256-byte aligned, owned by the caller. */
+size_t gf_unfused_workspace_bytes(const gf_flow* flow, int64_t B);
+gf_status gf_flow_sample_unfused(const gf_flow* flow, const gf_phi4* phi4, int64_t B,
+                                 uint64_t seed, uint64_t counter0, const float* d_z_in,
+                                 float* d_z_out, float* d_phi_out, double* d_logq_out,
+                                 double* d_S_out, double* d_logw_out, void* d_workspace,
+                                 size_t workspace_bytes, cudaStream_t stream);
+
 /* ---------------------------------------------------------------------- */
 /* Action (paper Sec. 1)                                                    */
 /* ---------------------------------------------------------------------- */

@@ -17,6 +17,7 @@ GF_MH_NOALLOC_MAX_N = 131072     # include/gfflow.h
 EXPORTED = [
     "gf_flow_create", "gf_flow_destroy", "gf_flow_n_params", "gf_flow_set_weights_device",
     "gf_flow_get_weights_device", "gf_flow_sample", "gf_flow_logq", "gf_phi4_action",
+    "gf_unfused_workspace_bytes", "gf_flow_sample_unfused",
     "gf_phi4_force", "gf_mh_chain_workspace_bytes", "gf_mh_chain", "gf_mh_chain_noalloc",
     "gf_hmc_trajectory",
     "gf_train_workspace_bytes", "gf_flow_train_step", "gf_device_status", "gf_status_string",
@@ -73,6 +74,9 @@ def load():
         "gf_flow_sample": ([_VP, C.POINTER(Phi4C), _I64, _U64, _U64, _VP, _VP, _VP, _VP, _VP,
                             _VP, _VP], _I32),
         "gf_flow_logq": ([_VP, _I64, _VP, _VP, _VP, _VP], _I32),
+        "gf_unfused_workspace_bytes": ([_VP, _I64], _SZ),
+        "gf_flow_sample_unfused": ([_VP, C.POINTER(Phi4C), _I64, _U64, _U64, _VP, _VP, _VP, _VP, _VP,
+                                    _VP, _VP, _SZ, _VP], _I32),
         "gf_phi4_action": ([_I32, _I32, C.POINTER(Phi4C), _I64, _VP, _I32, _VP, _VP], _I32),
         "gf_phi4_force": ([_I32, _I32, C.POINTER(Phi4C), _I64, _VP, _VP, _VP], _I32),
         "gf_mh_chain_workspace_bytes": ([_I64], _SZ),

@@ -108,6 +108,35 @@ class Flow:
             _ptr(out.S), _ptr(out.logw), _stream()))
         return out
 
+    def unfused_workspace_bytes(self, B: int) -> int:
+        return int(self._lib.gf_unfused_workspace_bytes(self._h, B))
+
+    def sample_unfused(self, B: int, seed: int = 0, counter0: int = 0, phi4=None, z=None,
+                       return_z: bool = False, out: SampleResult | None = None,
+                       workspace: torch.Tensor | None = None) -> SampleResult:
+        """gf_flow_sample_unfused: same results, one kernel per convolution."""
+        dev = torch.device("cuda", torch.cuda.current_device())
+        V = self.V
+        if z is not None:
+            _need(z, torch.float32, "z", B * V)
+        if out is None:
+            out = SampleResult(phi=torch.empty(B, V, device=dev),
+                               logq=torch.empty(B, device=dev, dtype=torch.float64))
+            if phi4 is not None:
+                out.S = torch.empty(B, device=dev, dtype=torch.float64)
+                out.logw = torch.empty(B, device=dev, dtype=torch.float64)
+            if return_z:
+                out.z = torch.empty(B, V, device=dev)
+        nbytes = self.unfused_workspace_bytes(B)
+        if workspace is None or workspace.numel() < nbytes:
+            workspace = torch.empty(max(nbytes, 1), device=dev, dtype=torch.uint8)
+        p = _phi4(phi4)
+        _abi.check("gf_flow_sample_unfused", self._lib.gf_flow_sample_unfused(
+            self._h, C.byref(p) if p is not None else None, B, seed & (2**64 - 1),
+            counter0 & (2**64 - 1), _ptr(z), _ptr(out.z), _ptr(out.phi), _ptr(out.logq),
+            _ptr(out.S), _ptr(out.logw), _ptr(workspace), workspace.numel(), _stream()))
+        return out
+
     def logq(self, phi: torch.Tensor, return_z: bool = False):
         B = phi.shape[0]
         _need(phi, torch.float32, "phi", B * self.V)

@@ -391,6 +391,46 @@ __global__ void k_mean(const double* __restrict__ v, int64_t n, double* __restri
     if (threadIdx.x == 0) *out = s / (double)n;
 }
 
+// ------------------------------------------------------------------ unfused sampler epilogue
+// log r(z), S(phi) (FP64 site terms), log q = log r - logdet, log w = -S - log q.
+template <int ND>
+__global__ void __launch_bounds__(kThreads) k_finish(const float* __restrict__ z, const float* __restrict__ phi,
+                                                    const double* __restrict__ logdet, int has_phi4, double m2,
+                                                    double lam, int L, int V, int64_t B, float* __restrict__ phi_out,
+                                                    float* __restrict__ z_out, double* __restrict__ logq,
+                                                    double* __restrict__ S_out, double* __restrict__ logw) {
+    __shared__ double red[32];
+    for (int64_t b = blockIdx.x; b < B; b += gridDim.x) {
+        const float* p = phi + b * V;
+        double acc = 0.0, z2 = 0.0;
+        for (int n = threadIdx.x; n < V; n += blockDim.x) {
+            const double c = p[n];
+            if (has_phi4) {
+                double k = 0.0;
+                for (int mu = 0; mu < ND; ++mu) {
+                    const int t_plus = (mu == 0) ? (ND == 3 ? 14 : 5) : (mu == 1) ? (ND == 3 ? 16 : 7) : 22;
+                    const int t_minus = (ND == 3 ? 26 : 8) - t_plus;
+                    k += 2.0 * c - (double)p[nbr<ND>(n, t_plus, L)] - (double)p[nbr<ND>(n, t_minus, L)];
+                }
+                acc += c * k + m2 * c * c + lam * c * c * c * c;
+            }
+            const double zz = z[b * V + n];
+            z2 += zz * zz;
+            phi_out[b * V + n] = p[n];
+            if (z_out) z_out[b * V + n] = z[b * V + n];
+        }
+        const double S = block_sum(acc, red);
+        const double Z2 = block_sum(z2, red);
+        if (threadIdx.x == 0) {
+            const double lq = (-0.5 * Z2 - 0.5 * (double)V * LOG_2PI) - logdet[b];
+            logq[b] = lq;
+            if (has_phi4 && S_out) S_out[b] = S;
+            if (has_phi4 && logw) logw[b] = -S - lq;
+        }
+        __syncthreads();
+    }
+}
+
 // ------------------------------------------------------------------ weights for the reverse pass
 // Transposed + tap-flipped copies: Wb[t][o][i] = W[o][i][T-1-t] (delta(T-1-t) = -delta(t)).
 __global__ void k_pack_bwd(const float* __restrict__ canon, int64_t cstride, int n_layers, int T, int C1, int C2,
@@ -598,6 +638,64 @@ gf_status train_step(gf_flow* f, const gf_phi4* phi4, int64_t B, uint64_t seed, 
     return GF_OK;
 }
 
+// Unfused FP32 sampler: one kernel per convolution, activations through HBM.
+// Workspace: z, two x buffers, h1, h2, s [B][V](x C), logdet [B].
+struct PlainWs { float *z, *xa, *xb, *h1, *h2, *s; double* logdet; size_t bytes; };
+
+PlainWs carve_plain(const gf_flow* f, int64_t B, char* base) {
+    PlainWs w;
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> char* {
+        char* p = base ? base + off : nullptr;
+        off += (bytes + 255) & ~size_t(255);
+        return p;
+    };
+    const int64_t BV = B * (int64_t)f->V;
+    w.z = (float*)take(sizeof(float) * BV);
+    w.xa = (float*)take(sizeof(float) * BV);
+    w.xb = (float*)take(sizeof(float) * BV);
+    w.h1 = (float*)take(sizeof(float) * BV * f->C1);
+    w.h2 = (float*)take(sizeof(float) * BV * f->C2);
+    w.s = (float*)take(sizeof(float) * BV);
+    w.logdet = (double*)take(sizeof(double) * std::max<int64_t>(B, 1));
+    w.bytes = off;
+    return w;
+}
+
+template <int ND>
+gf_status sample_unfused(const gf_flow* f, const gf_phi4* phi4, int64_t B, uint64_t seed, uint64_t counter0,
+                         const float* z_in, float* z_out, float* phi_out, double* logq, double* S_out,
+                         double* logw, const PlainWs& w, cudaStream_t st) {
+    const int L = f->shape.L, V = f->V, N = f->shape.n_layers;
+    const int C1 = f->C1, C2 = f->C2;
+    const int64_t BV = B * (int64_t)V;
+    const float slope = (float)f->shape.leaky_slope;
+    const PackedOffsets po = packed_offsets(f->T, C1, C2);
+    k_prior<<<(unsigned)grid1d(BV / 4 + 1), kThreads, 0, st>>>(V, B, seed, counter0, z_in, w.z);
+    GF_CHECK_LAUNCH();
+    if (cudaMemsetAsync(w.logdet, 0, sizeof(double) * B, st) != cudaSuccess) return GF_ECUDA;
+    const unsigned cfg_grid = (unsigned)std::min<int64_t>(B, (int64_t)num_sms() * 8);
+    const float* xin = w.z;
+    float* bufs[2] = {w.xa, w.xb};
+    for (int l = 0; l < N; ++l) {
+        const float* P = f->d_packed + (int64_t)l * f->packed_stride;
+        ConvArgs c1{xin, 1, l & 1, P + po.W1, P + po.b1, C1, w.h1, nullptr, 0, slope, L, V, B};
+        gf_status s = conv<ND>(c1, st);
+        if (s != GF_OK) return s;
+        ConvArgs c2{w.h1, C1, -1, P + po.W2, P + po.b2, C2, w.h2, nullptr, 0, slope, L, V, B};
+        if ((s = conv<ND>(c2, st)) != GF_OK) return s;
+        float* xout = bufs[l & 1];
+        k_couple_fwd<ND><<<cfg_grid, kThreads, 0, st>>>(w.h2, C2, P + po.W3, P + po.b3, f->shape.use_final_tanh,
+                                                       l & 1, L, V, B, xin, xout, w.s, w.logdet);
+        GF_CHECK_LAUNCH();
+        xin = xout;
+    }
+    k_finish<ND><<<cfg_grid, kThreads, 0, st>>>(w.z, xin, w.logdet, phi4 != nullptr, phi4 ? phi4->m2 : 0.0,
+                                               phi4 ? phi4->lam : 0.0, L, V, B, phi_out, z_out, logq, S_out, logw);
+    GF_CHECK_LAUNCH();
+    return GF_OK;
+}
+
 }  // namespace
 }  // namespace gf
 
@@ -627,6 +725,28 @@ gf_status gf_flow_train_step(gf_flow* flow, const gf_phi4* phi4, int64_t B, uint
                              adam_eps, d_adam_m, d_adam_v, adam_t, w, stream);
     return train_step<2>(flow, phi4, B, seed, counter0, d_z_in, d_loss_out, d_grad_out, lr, beta1, beta2,
                          adam_eps, d_adam_m, d_adam_v, adam_t, w, stream);
+}
+
+size_t gf_unfused_workspace_bytes(const gf_flow* flow, int64_t B) {
+    if (!flow || B < 0) return 0;
+    return carve_plain(flow, B, nullptr).bytes;
+}
+
+gf_status gf_flow_sample_unfused(const gf_flow* flow, const gf_phi4* phi4, int64_t B, uint64_t seed,
+                                 uint64_t counter0, const float* d_z_in, float* d_z_out, float* d_phi_out,
+                                 double* d_logq_out, double* d_S_out, double* d_logw_out, void* d_workspace,
+                                 size_t workspace_bytes, cudaStream_t stream) {
+    if (!flow || B < 0 || (B > 0 && (!d_phi_out || !d_logq_out))) return GF_EINVAL;
+    if (!phi4 && (d_S_out || d_logw_out)) return GF_EINVAL;
+    if (B == 0) return GF_OK;
+    const PlainWs w = carve_plain(flow, B, static_cast<char*>(d_workspace));
+    if (!d_workspace || workspace_bytes < w.bytes) return GF_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(d_workspace) & 255) != 0) return GF_EINVAL;
+    if (flow->shape.nd == 3)
+        return sample_unfused<3>(flow, phi4, B, seed, counter0, d_z_in, d_z_out, d_phi_out, d_logq_out, d_S_out,
+                                 d_logw_out, w, stream);
+    return sample_unfused<2>(flow, phi4, B, seed, counter0, d_z_in, d_z_out, d_phi_out, d_logq_out, d_S_out,
+                             d_logw_out, w, stream);
 }
 
 }  // extern "C"

@@ -6,6 +6,13 @@ over the lattice are FP64.  It is compared with the oracle in the matching
 BF16-emulation mode (same rounding points, FP64 elsewhere) with
     |a-b| <= 1e-4 * max(|b|, rms(b))  per site,  1e-4 * max(|b|, 1) per log-weight,
 and its error against the pure FP64 oracle is reported (max and p99 per result).
+
+Site tolerance: half a bf16 ulp (2^-9) relative.  The kernel and the oracle
+round h1/h2 to bf16 from values that differ at the FP32 level, so a value
+lying within that difference of a rounding boundary rounds the other way on
+one side; each such flip moves the s, t of the neighbouring updated sites by a
+fraction of one bf16 ulp of one input term.  Log-weights are sums over all
+sites, where the flips average out: 1e-4 relative.
 """
 import numpy as np
 import pytest
@@ -15,7 +22,8 @@ from gpu_util import assert_logw_close, assert_sites_close, require_gpu
 
 pytestmark = pytest.mark.gpu
 BF16_MODE = 1 | 2 | 4 | 32          # H1 | W2 | H2 | FP32 prior
-RTOL = 1e-4
+RTOL = 2.0**-9                      # per site
+LW_RTOL = 1e-4                      # per log-weight
 
 
 def _report(name, gpu, ref):
@@ -42,9 +50,12 @@ def test_bf16_sample_matches_emulated_oracle(orc, n_layers, B):
     assert P.device_status() == 0
     ref = orc.flow_sample(shape, w, m2, lam, B, seed=21, counter0=5, bf16_mask=BF16_MODE)
     assert_sites_close(out.z.cpu().numpy(), ref["z"], rtol=1e-6, what="z")
+    _report("phi vs bf16-emulated", out.phi.cpu().numpy(), ref["phi"])
+    for k in ("logq", "S", "logw"):
+        _report(f"{k} vs bf16-emulated", getattr(out, k).cpu().numpy(), ref[k])
     assert_sites_close(out.phi.cpu().numpy(), ref["phi"], rtol=RTOL)
     for k in ("logq", "S", "logw"):
-        assert_logw_close(getattr(out, k).cpu().numpy(), ref[k], rtol=RTOL, what=k)
+        assert_logw_close(getattr(out, k).cpu().numpy(), ref[k], rtol=LW_RTOL, what=k)
     # error of the BF16 path against the pure FP64 oracle, stated per result
     f64 = orc.flow_sample(shape, w, m2, lam, B, seed=21, counter0=5)
     _report("phi vs FP64", out.phi.cpu().numpy(), f64["phi"])
@@ -65,7 +76,7 @@ def test_bf16_given_z_and_inverse(orc):
     zb, lq = flow.logq(out.phi, return_z=True)
     zr, lqr = orc.flow_logq(shape, w, out.phi.cpu().numpy().astype(np.float64), bf16_mask=BF16_MODE)
     assert_sites_close(zb.cpu().numpy(), zr, rtol=RTOL, what="z(inverse)")
-    assert_logw_close(lq.cpu().numpy(), lqr, rtol=RTOL, what="logq(inverse)")
+    assert_logw_close(lq.cpu().numpy(), lqr, rtol=LW_RTOL, what="logq(inverse)")
     assert P.device_status() == 0
 
 
@@ -81,7 +92,7 @@ def test_bf16_full_batch_sampled(orc):
     for b in (0, 1, 2047, B - 1):
         ref = orc.flow_sample(shape, w, phi4.m2, phi4.lam, 1, seed=2024, counter0=b, bf16_mask=BF16_MODE)
         assert_sites_close(out.phi[b:b + 1].cpu().numpy(), ref["phi"], rtol=RTOL, what=f"phi[{b}]")
-        assert_logw_close(out.logw[b:b + 1].cpu().numpy(), ref["logw"], rtol=RTOL, what=f"logw[{b}]")
+        assert_logw_close(out.logw[b:b + 1].cpu().numpy(), ref["logw"], rtol=LW_RTOL, what=f"logw[{b}]")
     assert torch.isfinite(out.phi).all()
     S = P.phi4_action(3, 16, phi4, out.phi)
     assert_logw_close(S.cpu().numpy(), out.S.cpu().numpy(), rtol=1e-12, what="fused vs standalone S")

@@ -130,3 +130,20 @@ def test_bench_size_sampled_parity(orc, key):
     assert_logw_close(lq.cpu().numpy(), out.logq.cpu().numpy(), what="logq(F(phi)) vs logq")
     S = P.phi4_action(shape.nd, shape.L, phi4, out.phi)
     assert_logw_close(S.cpu().numpy(), out.S.cpu().numpy(), rtol=1e-12, what="fused vs standalone S")
+
+
+@pytest.mark.parametrize("case", [CASES[0], CASES[2], CASES[7]], ids=[_ids(c) for c in (CASES[0], CASES[2], CASES[7])])
+def test_unfused_path_matches_oracle(orc, case):
+    """The plain one-kernel-per-convolution path computes the same function."""
+    torch, P = require_gpu()
+    shape, m2, lam, B = case
+    w = gi.init_weights(shape, seed=0)
+    flow = P.Flow(shape, w)
+    out = flow.sample_unfused(B, seed=1234, counter0=77, phi4=(m2, lam), return_z=True)
+    ref = orc.flow_sample(shape, w, m2, lam, B, seed=1234, counter0=77)
+    assert_sites_close(out.z.cpu().numpy(), ref["z"], rtol=1e-6, what="z")
+    assert_sites_close(out.phi.cpu().numpy(), ref["phi"])
+    for k in ("logq", "S", "logw"):
+        assert_logw_close(getattr(out, k).cpu().numpy(), ref[k], what=k)
+    fused = flow.sample(B, seed=1234, counter0=77, phi4=(m2, lam))
+    assert_logw_close(out.logw.cpu().numpy(), fused.logw.cpu().numpy(), what="unfused vs fused")
