@@ -369,6 +369,10 @@ def bench_extra(args, dev, flush, pk):
     t = _time_steps(lambda i: P.mh_chain(st, lw, workspace=wsm), 5, 2, None)
     out["mh_chain"] = {"ns_per_proposal": float(np.mean(t)) * 1e6 / n, "proposals": n}
 
+    # serving mix: resident random-init models, Poisson arrivals at 200 req/s
+    out["serving_c5"] = bench_serving(dev, n_requests=args.serving_requests)
+    torch.cuda.empty_cache()
+
     # the paper's example workload (2D L=8, 16 couplings, hidden 8, batch 64)
     W1 = gi.WORKLOADS["c1"]
     f1 = P.Flow(W1["shape"], gi.init_weights(W1["shape"]))
@@ -383,6 +387,28 @@ def bench_extra(args, dev, flush, pk):
     t = _time_steps(c1step, 50, 5, None)
     out["c1_sampling"] = {"configs_per_s": 64 / (float(np.mean(t)) / 1e3), "ms_per_step": float(np.mean(t))}
     return out
+
+
+def bench_serving(dev, n_requests=120, rate=200.0, n_models=16, seed=5):
+    """Continuous-batching loop on the serving mix; returns latency / throughput."""
+    import torch
+    import paper_2208_08903_gb300 as P
+    from paper_2208_08903_gb300 import serving
+    specs = gi.serving_models(n_models, seed)
+    models = {}
+    for name, shape, s in specs:
+        prec = "bf16" if (shape.nd == 3 and shape.L == 16 and shape.c1 == 32 and shape.c2 == 32) else "fp32"
+        models[name] = serving.Model(name, shape, P.Flow(shape, gi.init_weights(shape, seed=s), precision=prec))
+    arr = serving.poisson_arrivals(n_requests, rate, seed)
+    reqs = [serving.Request(i, name, m2, lam, b, sd, arrival=float(arr[i]))
+            for i, (name, m2, lam, b, sd) in enumerate(gi.serving_requests(n_requests, list(models), seed))]
+    srv = serving.Server(models, hbm_budget_bytes=16 << 30, max_active=16, chunk=2048, device=dev)
+    srv.run(reqs[:4], keep_results=False, realtime=False)          # warm-up (kernel attributes, streams)
+    _, stats = srv.run(reqs, keep_results=False, realtime=True)
+    stats.update({"offered_rate_req_per_s": rate, "models": n_models,
+                  "mix": "2D L in {8,16,32,64}, 3D L in {8,12,16}, 12-24 couplings, hidden {8,16,32}, "
+                         "batch 64-8192 log-uniform, BF16 conv2 for 3D L=16 hidden 32, FP32 otherwise"})
+    return stats
 
 
 # --------------------------------------------------------------------------- CPU oracle
@@ -455,6 +481,7 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=120.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the secondary measurements")
+    ap.add_argument("--serving-requests", type=int, default=120)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -138,3 +138,35 @@ WORKLOADS = {
     "c4": dict(nd=3, L=16, phi4=Phi4(m2=-6.0, lam=5.0), chains=512,
                n_steps=20, eps=0.05, trajectories=1000),
 }
+
+
+# ---------------------------------------------------------------------------
+# Serving mix: resident models drawn from 2D L in {8,16,32,64} and 3D L in
+# {8,12,16}, 12-24 couplings, hidden width in {8,16,32}; requests pick a model
+# uniformly, (m2, lam) uniform in [-6,-2] x [1,10], batch log-uniform in
+# [64, 8192], Poisson arrivals.
+# ---------------------------------------------------------------------------
+def serving_models(n_models: int, seed: int):
+    """[(name, FlowShape, init seed)] for the serving mix."""
+    rng = np.random.default_rng(seed)
+    lattices = [(2, 8), (2, 16), (2, 32), (2, 64), (3, 8), (3, 12), (3, 16)]
+    out = []
+    for i in range(n_models):
+        nd, L = lattices[int(rng.integers(len(lattices)))]
+        c = int(rng.choice([8, 16, 32]))
+        n_layers = int(rng.integers(12, 25))
+        out.append((f"m{i}", FlowShape(nd, L, n_layers, c, c), 1000 + i))
+    return out
+
+
+def serving_requests(n: int, model_names, seed: int, max_batch: int = 8192):
+    """[(model name, m2, lam, batch, seed)] for n requests."""
+    rng = np.random.default_rng(seed + 17)
+    out = []
+    for i in range(n):
+        name = model_names[int(rng.integers(len(model_names)))]
+        m2 = float(rng.uniform(-6.0, -2.0))
+        lam = float(rng.uniform(1.0, 10.0))
+        batch = int(round(float(np.exp(rng.uniform(np.log(64), np.log(max_batch))))))
+        out.append((name, m2, lam, batch, 50000 + i))
+    return out

@@ -2,9 +2,11 @@
 // Sec. 1: S = sum_n [-phi(n) Lap phi(n) + m2 phi^2 + lam phi^4], periodic
 // lattice Laplacian).
 //
-// HBM-bound: each CTA stages one configuration at a time in shared memory
-// with 16-byte loads (grid-stride over configurations), evaluates the site
-// terms in FP64 from shared memory and reduces them in a fixed order.
+// Each CTA stages one configuration at a time in shared memory with 16-byte
+// loads (grid-stride over configurations), evaluates the site terms in FP64
+// from shared memory and reduces them in a fixed order.  On GB300 the FP64
+// issue rate (about 1/64 of FP32), not HBM, bounds it: the site terms must be
+// FP64 because S enters the Metropolis-Hastings log weights.
 #include <algorithm>
 
 #include "gf_common.cuh"
@@ -43,6 +45,23 @@ __device__ __forceinline__ double lap_minus(const T* p, int n, int nd, int L) {
     return k;
 }
 
+// Site term in the forward-hop arrangement (equal to the two-neighbour form of
+// the action summed over the lattice): (2d + m2) phi^2 + lam phi^4
+// - 2 phi(n) sum_mu phi(n + mu).  It needs d neighbour reads and about half the
+// FP64 operations of the two-neighbour form; FP64 issue rate, not HBM, bounds
+// this kernel on GB300.
+template <typename T>
+__device__ __forceinline__ double site_term_fwd(const T* p, int n, int nd, int L, double c2d, double lam) {
+    const int xc = n % L, yc = (n / L) % L;
+    double hop = (double)p[n - xc + wrapi(xc + 1, L)] + (double)p[n + (wrapi(yc + 1, L) - yc) * L];
+    if (nd == 3) {
+        const int zc = n / (L * L);
+        hop += (double)p[n + (wrapi(zc + 1, L) - zc) * L * L];
+    }
+    const double c = (double)p[n], q = c * c;
+    return fma(q, fma(lam, q, c2d), -2.0 * c * hop);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kActThreads) action_kernel(int nd, int L, int V, double m2, double lam,
                                                              int64_t B, const T* __restrict__ phi,
@@ -50,14 +69,12 @@ __global__ void __launch_bounds__(kActThreads) action_kernel(int nd, int L, int 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* p = reinterpret_cast<T*>(smem_raw);
     double* red = reinterpret_cast<double*>(smem_raw + (((size_t)V * sizeof(T) + 15) & ~size_t(15)));
+    const double c2d = 2.0 * nd + m2;
     for (int64_t b = blockIdx.x; b < B; b += gridDim.x) {
         stage(phi + b * V, p, V);
         __syncthreads();
         double acc = 0.0;
-        for (int n = threadIdx.x; n < V; n += blockDim.x) {
-            const double c = (double)p[n], c2 = c * c;
-            acc += c * lap_minus(p, n, nd, L) + m2 * c2 + lam * c2 * c2;
-        }
+        for (int n = threadIdx.x; n < V; n += blockDim.x) acc += site_term_fwd(p, n, nd, L, c2d, lam);
         const double S = block_sum(acc, red);
         if (threadIdx.x == 0) S_out[b] = S;
         __syncthreads();

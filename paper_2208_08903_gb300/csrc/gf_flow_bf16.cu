@@ -152,13 +152,178 @@ __device__ __forceinline__ void store8(unsigned char* slot, int cg, int y, int x
     if (y == 15) *reinterpret_cast<uint4*>(base + hsite(-1, x) * 16) = w;
 }
 
+// Virtual slice v (may lie outside 0..L-1 by the wrap-around recomputation)
+// -> lattice slice v mod L; h1 slot v mod 4, h2 slot v mod 3.
+__device__ __forceinline__ int slice_of(int v) { return v & 15; }
+__device__ __forceinline__ int h1_slot(int v) { return (v + 16) & 3; }
+__device__ __forceinline__ int h2_slot(int v) { return (v + 15) % 3; }
+
+// conv1 + LReLU of virtual slice v into its h1 slot (BF16).  Work items:
+// (channel group, site parity class, 128 sites of that class); a warp holds
+// sites of one parity, so every lane takes the same 13 or 14 taps (those whose
+// neighbour has the fixed parity), selected by a warp-uniform test on a
+// compile-time tap offset.
+__device__ __forceinline__ void conv1_slice(unsigned char* h1, int v, const float* wf, const float* x, int frozen,
+                                            float slope, int tid) {
+    const int z = slice_of(v);
+    unsigned char* slot = h1 + (size_t)h1_slot(v) * kSlotBytes;
+#pragma unroll 1
+    for (int it = tid; it < kS * 4; it += kThreads) {
+        const int cg = it >> 8, rest = it & 255, pcls = rest >> 7, k = rest & 127;
+        const int y = k >> 3, xx = 2 * (k & 7) + ((pcls ^ z ^ y) & 1);    // (z+y+x) & 1 == pcls
+        const int need = (frozen ^ pcls) & 1;                              // tap parity reaching fixed sites
+        int zr[3], yr[3], xc[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            zr[d] = wrap16(z + d - 1) << 8;
+            yr[d] = wrap16(y + d - 1) << 4;
+            xc[d] = wrap16(xx + d - 1);
+        }
+        const float4 b0 = *reinterpret_cast<const float4*>(wf + kF_b1 + cg * 8);
+        const float4 b1 = *reinterpret_cast<const float4*>(wf + kF_b1 + cg * 8 + 4);
+        float acc[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+        for (int t = 0; t < kT; ++t) {
+            const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;             // compile-time after unrolling
+            if (((dz + dy + dx + 1) & 1) != need) continue;                 // |offset| parity, warp-uniform
+            const float xv = x[zr[dz] + yr[dy] + xc[dx]];
+            const float4 w0 = *reinterpret_cast<const float4*>(wf + kF_W1 + t * kC + cg * 8);
+            const float4 w1 = *reinterpret_cast<const float4*>(wf + kF_W1 + t * kC + cg * 8 + 4);
+            acc[0] = fmaf(xv, w0.x, acc[0]); acc[1] = fmaf(xv, w0.y, acc[1]);
+            acc[2] = fmaf(xv, w0.z, acc[2]); acc[3] = fmaf(xv, w0.w, acc[3]);
+            acc[4] = fmaf(xv, w1.x, acc[4]); acc[5] = fmaf(xv, w1.y, acc[5]);
+            acc[6] = fmaf(xv, w1.z, acc[6]); acc[7] = fmaf(xv, w1.w, acc[7]);
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[c] = acc[c] > 0.f ? acc[c] : slope * acc[c];
+        store8(slot, cg, y, xx, acc);
+    }
+}
+
+// One elected thread: conv2 of virtual slice v as 2 M-tiles x 3 dx accumulators
+// x 9 (dz,dy) taps x 2 K-steps of tcgen05.mma, then a commit to the mbarrier.
+__device__ __forceinline__ void issue_conv2(const unsigned char* h1, const unsigned char* w2s, uint32_t tmem,
+                                            int v, uint64_t* mbar) {
+    fence_after_sync();
+    const uint32_t w2a = smem_u32(w2s);
+    uint32_t slots[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) slots[d] = smem_u32(h1 + (size_t)h1_slot(v - 1 + d) * kSlotBytes);
+#pragma unroll 1
+    for (int mt = 0; mt < 2; ++mt) {
+#pragma unroll 1
+        for (int dxi = 0; dxi < 3; ++dxi) {
+            const uint32_t d = tmem + (uint32_t)((mt * 3 + dxi) * 32);
+            uint32_t acc = 0;
+#pragma unroll
+            for (int dzi = 0; dzi < 3; ++dzi) {
+#pragma unroll
+                for (int dyi = 0; dyi < 3; ++dyi) {
+                    const int t = (dzi * 3 + dyi) * 3 + dxi;
+#pragma unroll
+                    for (int k = 0; k < 2; ++k) {
+                        const uint32_t aaddr = slots[dzi] + (uint32_t)(2 * k * kHaloSites * 16) +
+                                               (uint32_t)((mt * 8 + dyi) * 16 * 16);
+                        const uint32_t baddr = w2a + (uint32_t)(t * 2048 + 2 * k * 512);
+                        mma_bf16(d, smem_desc(aaddr, kHaloSites * 16, 128), smem_desc(baddr, 512, 128), kIdesc, acc);
+                        acc = 1;
+                    }
+                }
+            }
+        }
+    }
+    mma_commit(mbar);
+}
+
+// Epilogue: out(x) = sum_dx P_dx(x + dx) + b2, LReLU, BF16 into the h2 slot of v.
+__device__ __forceinline__ void conv2_epilogue(unsigned char* h2, uint32_t tmem, int v, const float* wf, float slope,
+                                               int warp, int lane) {
+    const int mt = warp >> 2, q = warp & 3;
+    const int y = mt * 8 + q * 2 + (lane >> 4), xx = lane & 15;
+    float pm[32], p0[32], pp[32];
+    const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+    tmem_ld32(tmem + lane_base + (uint32_t)((mt * 3 + 0) * 32), pm);
+    tmem_ld32(tmem + lane_base + (uint32_t)((mt * 3 + 1) * 32), p0);
+    tmem_ld32(tmem + lane_base + (uint32_t)((mt * 3 + 2) * 32), pp);
+    tmem_ld_wait();
+    const int src_m = (lane & 16) | ((xx + 15) & 15);   // x - 1
+    const int src_p = (lane & 16) | ((xx + 1) & 15);    // x + 1
+    unsigned char* slot = h2 + (size_t)h2_slot(v) * kSlotBytes;
+#pragma unroll
+    for (int cg = 0; cg < 4; ++cg) {
+        float o[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int ch = cg * 8 + c;
+            const float s = p0[ch] + __shfl_sync(0xffffffffu, pm[ch], src_m) +
+                            __shfl_sync(0xffffffffu, pp[ch], src_p) + wf[kF_b2 + ch];
+            o[c] = s > 0.f ? s : slope * s;
+        }
+        store8(slot, cg, y, xx, o);
+    }
+}
+
+// conv3 at the 128 updated sites of slice z and the affine update of x.
+// Thread = (pair of updated sites of one y-row, channel group cg): 4 lanes
+// (the 4 channel groups) share a site pair and are combined by shuffles; the
+// conv3 weights of a tap and channel group (8 channels x (s,t)) are loaded once
+// for both sites.  Lane cg == 0 applies the update and accumulates the log-det.
+__device__ __forceinline__ void conv3_slice(const unsigned char* h2, int z, const float* wf, float* x, int frozen,
+                                            int use_tanh, bool inverse, double& logdet, int tid) {
+    const int cg = tid & 3, pair = tid >> 2;                   // 64 pairs
+    const int y = pair >> 2, kp = pair & 3;                    // 4 pairs per row: k = 2kp, 2kp+1
+    const int off = (frozen ^ 1 ^ z ^ y) & 1;
+    const int xa = 4 * kp + off, xb = xa + 2;
+    const unsigned char* sl[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) sl[d] = h2 + (size_t)h2_slot(z - 1 + d) * kSlotBytes + (size_t)cg * kHaloSites * 16;
+    float psa = 0.f, pta = 0.f, psb = 0.f, ptb = 0.f;
+#pragma unroll
+    for (int t = 0; t < kT; ++t) {
+        const int dzi = t / 9, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
+        const int row = (y + dy + 1) * 16;
+        const uint4 ra = *reinterpret_cast<const uint4*>(sl[dzi] + (row + wrap16(xa + dx)) * 16);
+        const uint4 rb = *reinterpret_cast<const uint4*>(sl[dzi] + (row + wrap16(xb + dx)) * 16);
+        const float4* w = reinterpret_cast<const float4*>(wf + kF_W3 + t * kC * 2 + cg * 16);
+        const __nv_bfloat162* ha = reinterpret_cast<const __nv_bfloat162*>(&ra);
+        const __nv_bfloat162* hb = reinterpret_cast<const __nv_bfloat162*>(&rb);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float4 wv = w[i];                            // (s,t) of channels 2i, 2i+1
+            const float2 fa = __bfloat1622float2(ha[i]);
+            const float2 fb = __bfloat1622float2(hb[i]);
+            psa = fmaf(fa.x, wv.x, psa); pta = fmaf(fa.x, wv.y, pta);
+            psa = fmaf(fa.y, wv.z, psa); pta = fmaf(fa.y, wv.w, pta);
+            psb = fmaf(fb.x, wv.x, psb); ptb = fmaf(fb.x, wv.y, ptb);
+            psb = fmaf(fb.y, wv.z, psb); ptb = fmaf(fb.y, wv.w, ptb);
+        }
+    }
+#pragma unroll
+    for (int o = 1; o < 4; o <<= 1) {
+        psa += __shfl_xor_sync(0xffffffffu, psa, o); pta += __shfl_xor_sync(0xffffffffu, pta, o);
+        psb += __shfl_xor_sync(0xffffffffu, psb, o); ptb += __shfl_xor_sync(0xffffffffu, ptb, o);
+    }
+    if (cg == 0) {
+        const float bs = wf[kF_b3], bt = wf[kF_b3 + 1];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const float spre = (q ? psb : psa) + bs, tt = (q ? ptb : pta) + bt;
+            const float s = use_tanh ? tanhf(spre) : spre;
+            float& xv = x[(z * 16 + y) * 16 + (q ? xb : xa)];
+            if (!inverse) xv = fmaf(xv, expf(s), tt);
+            else xv = (xv - tt) * expf(-s);
+            logdet += (double)s;
+        }
+    }
+}
+
 template <bool INVERSE>
 __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a) {
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* w2s = smem;                                        // kW2Bytes
     float* wf = reinterpret_cast<float*>(smem + kW2Bytes);            // kF_N floats
-    unsigned char* h1 = smem + kW2Bytes + kF_N * 4;                   // 3 slots
-    unsigned char* h2 = h1 + 3 * kSlotBytes;                          // 3 slots
+    unsigned char* h1 = smem + kW2Bytes + kF_N * 4;                   // 4 slots
+    unsigned char* h2 = h1 + 4 * kSlotBytes;                          // 3 slots
     float* x = reinterpret_cast<float*>(h2 + 3 * kSlotBytes);         // 4096 floats
     double* red = reinterpret_cast<double*>(x + 4096);                // 32
     Phase* ph = reinterpret_cast<Phase*>(red + 32);
@@ -211,7 +376,7 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
         __syncthreads();
 
         double logdet = 0.0;
-        for (int li = 0; li < a.n_layers; ++li) {
+        for (int li = 0; li < a.n_layers && !*abort_flag; ++li) {
             const int l = INVERSE ? a.n_layers - 1 - li : li;
             const int frozen = l & 1;
             // stage this layer's weights (W2 already in the MMA operand layout)
@@ -222,141 +387,34 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
             }
             fence_proxy_async();
             __syncthreads();
-            const float slope = a.slope;
-            for (int p = 0; p < a.n_phases; ++p) {
-                if (tid < (int)(sizeof(Phase) / 4))
-                    reinterpret_cast<uint32_t*>(ph)[tid] =
-                        __ldg(reinterpret_cast<const uint32_t*>(a.sched + p) + tid);
-                __syncthreads();
-                const int type = ph->type;
-                const int s0 = ph->s0;
-                if (type == PH_H1) {
-                    // conv1: 256 sites x 4 channel groups; only fixed-site taps contribute
-                    unsigned char* slot = h1 + (size_t)ph->out[0] * kSlotBytes;
-                    for (int it = tid; it < kS * 4; it += kThreads) {
-                        const int j = it & (kS - 1), cg = it >> 8;
-                        const int y = j >> 4, xx = j & 15;
-                        float acc[8];
-#pragma unroll
-                        for (int c = 0; c < 8; ++c) acc[c] = wf[kF_b1 + cg * 8 + c];
-                        for (int t = 0; t < kT; ++t) {
-                            const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
-                            const int z2 = wrap16(s0 + dz), y2 = wrap16(y + dy), x2 = wrap16(xx + dx);
-                            if (((z2 + y2 + x2) & 1) != frozen) continue;
-                            const float xv = x[(z2 * 16 + y2) * 16 + x2];
-                            const float* w = wf + kF_W1 + t * kC + cg * 8;
-#pragma unroll
-                            for (int c = 0; c < 8; ++c) acc[c] = fmaf(xv, w[c], acc[c]);
-                        }
-#pragma unroll
-                        for (int c = 0; c < 8; ++c) acc[c] = acc[c] > 0.f ? acc[c] : slope * acc[c];
-                        store8(slot, cg, y, xx, acc);
-                    }
+            // prologue: h1 of virtual slices -2, -1, 0
+            for (int v = -2; v <= 0; ++v) conv1_slice(h1, v, wf, x, frozen, a.slope, tid);
+            fence_proxy_async();
+            __syncthreads();
+            // pipeline over the virtual h2 slices v = -1 .. L (slice v mod L):
+            //   tensor cores: conv2 of h2[v]      FFMA: conv3 + update of slice v-2, conv1 of h1[v+2]
+            for (int v = -1; v <= kL; ++v) {
+                if (tid == 0) issue_conv2(h1, w2s, tmem, v, mbar);
+                if (v - 2 >= 0) conv3_slice(h2, v - 2, wf, x, frozen, a.use_tanh, INVERSE, logdet, tid);
+                if (v + 2 <= kL + 1) {
+                    conv1_slice(h1, v + 2, wf, x, frozen, a.slope, tid);
                     fence_proxy_async();
-                } else if (type == PH_H2) {
-                    // conv2 on the tensor cores
-                    if (tid == 0) {
-                        fence_after_sync();
-                        const uint32_t w2a = smem_u32(w2s);
-#pragma unroll 1
-                        for (int mt = 0; mt < 2; ++mt) {
-#pragma unroll 1
-                            for (int dxi = 0; dxi < 3; ++dxi) {
-                                const uint32_t d = tmem + (uint32_t)((mt * 3 + dxi) * 32);
-                                uint32_t acc = 0;
-#pragma unroll 1
-                                for (int dzi = 0; dzi < 3; ++dzi) {
-                                    const uint32_t slot = smem_u32(h1 + (size_t)ph->in[dzi] * kSlotBytes);
-#pragma unroll 1
-                                    for (int dyi = 0; dyi < 3; ++dyi) {
-                                        const int t = (dzi * 3 + dyi) * 3 + dxi;
-#pragma unroll
-                                        for (int k = 0; k < 2; ++k) {
-                                            const uint32_t aaddr = slot + (uint32_t)(2 * k * kHaloSites * 16) +
-                                                                   (uint32_t)((mt * 8 + dyi) * 16 * 16);
-                                            const uint32_t baddr = w2a + (uint32_t)(t * 2048 + 2 * k * 512);
-                                            mma_bf16(d, smem_desc(aaddr, kHaloSites * 16, 128),
-                                                     smem_desc(baddr, 512, 128), kIdesc, acc);
-                                            acc = 1;
-                                        }
-                                    }
-                                }
-                            }
-                        }
-                        mma_commit(mbar);
-                    }
-                    // wait for the accumulators (bounded)
-                    long long spins = 0;
-                    while (!mbar_try_wait(mbar, phase_bit)) {
-                        if (++spins > kWaitLimit) { *abort_flag = 1; set_status(a.status, GF_ETIMEOUT); break; }
-                    }
-                    phase_bit ^= 1u;
-                    fence_after_sync();
-                    // epilogue: warp w -> tile w/4, TMEM lanes 32*(w%4) .. +31
-                    const int mt = warp >> 2, q = warp & 3;
-                    const int y = mt * 8 + q * 2 + (lane >> 4), xx = lane & 15;
-                    float pm[32], p0[32], pp[32];
-                    const uint32_t lane_base = (uint32_t)(q * 32) << 16;
-                    tmem_ld32(tmem + lane_base + (uint32_t)((mt * 3 + 0) * 32), pm);
-                    tmem_ld32(tmem + lane_base + (uint32_t)((mt * 3 + 1) * 32), p0);
-                    tmem_ld32(tmem + lane_base + (uint32_t)((mt * 3 + 2) * 32), pp);
-                    tmem_ld_wait();
-                    const int src_m = (lane & 16) | ((xx + 15) & 15);   // x - 1
-                    const int src_p = (lane & 16) | ((xx + 1) & 15);    // x + 1
-                    unsigned char* slot = h2 + (size_t)ph->out[0] * kSlotBytes;
-#pragma unroll
-                    for (int cg = 0; cg < 4; ++cg) {
-                        float v[8];
-#pragma unroll
-                        for (int c = 0; c < 8; ++c) {
-                            const int ch = cg * 8 + c;
-                            const float s = p0[ch] + __shfl_sync(0xffffffffu, pm[ch], src_m) +
-                                            __shfl_sync(0xffffffffu, pp[ch], src_p) + wf[kF_b2 + ch];
-                            v[c] = s > 0.f ? s : slope * s;
-                        }
-                        store8(slot, cg, y, xx, v);
-                    }
-                    fence_before_sync();
-                } else {
-                    // conv3 at the 128 updated sites of slice s0 (2 threads per site) + affine update
-                    const int ai = tid >> 1, half = tid & 1;
-                    const int y = ai >> 3, k = ai & 7;
-                    const int xx = 2 * k + ((frozen ^ 1 ^ s0 ^ y) & 1);
-                    float ps = 0.f, pt = 0.f;
-                    for (int t = 0; t < kT; ++t) {
-                        const int dzi = t / 9, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
-                        const unsigned char* slot = h2 + (size_t)ph->in[dzi] * kSlotBytes;
-                        const int hs = hsite(y + dy, wrap16(xx + dx));
-                        const float* w = wf + kF_W3 + t * kC * 2;
-#pragma unroll
-                        for (int g = 0; g < 2; ++g) {
-                            const int cg = half * 2 + g;
-                            const uint4 raw = *reinterpret_cast<const uint4*>(slot + ((size_t)cg * kHaloSites + hs) * 16);
-                            const __nv_bfloat162* hv = reinterpret_cast<const __nv_bfloat162*>(&raw);
-#pragma unroll
-                            for (int i = 0; i < 4; ++i) {
-                                const float2 f = __bfloat1622float2(hv[i]);
-                                const int ch = cg * 8 + 2 * i;
-                                ps = fmaf(f.x, w[2 * ch], ps); pt = fmaf(f.x, w[2 * ch + 1], pt);
-                                ps = fmaf(f.y, w[2 * ch + 2], ps); pt = fmaf(f.y, w[2 * ch + 3], pt);
-                            }
-                        }
-                    }
-                    ps += __shfl_xor_sync(0xffffffffu, ps, 1);
-                    pt += __shfl_xor_sync(0xffffffffu, pt, 1);
-                    if (half == 0) {
-                        const float spre = ps + wf[kF_b3], tt = pt + wf[kF_b3 + 1];
-                        const float s = a.use_tanh ? tanhf(spre) : spre;
-                        float& xv = x[(s0 * 16 + y) * 16 + xx];
-                        if (!INVERSE) xv = fmaf(xv, expf(s), tt);
-                        else xv = (xv - tt) * expf(-s);
-                        logdet += (double)s;
-                    }
                 }
+                __syncthreads();                       // conv3 done reading the h2 slot about to be reused
+                long long spins = 0;
+                while (!mbar_try_wait(mbar, phase_bit)) {
+                    if (++spins > kWaitLimit) { *abort_flag = 1; set_status(a.status, GF_ETIMEOUT); break; }
+                }
+                phase_bit ^= 1u;
+                fence_after_sync();
+                conv2_epilogue(h2, tmem, v, wf, a.slope, warp, lane);
+                fence_before_sync();
                 __syncthreads();
                 if (*abort_flag) break;
             }
             if (*abort_flag) break;
+            conv3_slice(h2, kL - 1, wf, x, frozen, a.use_tanh, INVERSE, logdet, tid);
+            __syncthreads();
         }
         if (*abort_flag) break;
 
@@ -405,7 +463,7 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
     }
 }
 
-constexpr size_t kSmemBytes = (size_t)kW2Bytes + kF_N * 4 + 6 * (size_t)kSlotBytes + 4096 * 4 + 32 * 8 +
+constexpr size_t kSmemBytes = (size_t)kW2Bytes + kF_N * 4 + 7 * (size_t)kSlotBytes + 4096 * 4 + 32 * 8 +
                               ((sizeof(Phase) + 7) & ~size_t(7)) + 8 + 4 + 4;
 
 // canonical FP32 -> per-layer BF16 block (W2 in [t][kg][n][8]) + FP32 block

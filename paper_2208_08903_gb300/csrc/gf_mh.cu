@@ -33,39 +33,51 @@ __global__ void __launch_bounds__(32) mh_scan_kernel(gf_mh_state* __restrict__ s
                                                      const double* __restrict__ logu,
                                                      int64_t* __restrict__ chain_idx,
                                                      uint8_t* __restrict__ acc_out) {
+    constexpr int kChunks = 8;                 // 256 proposals loaded per round trip to memory
     const int lane = threadIdx.x;
     double cur = st->logw_cur;
     int64_t idx = st->idx_cur, nacc = st->n_acc;
     const int64_t g0 = st->step;
-    for (int64_t base = 0; base < n; base += 32) {
-        const int64_t k = base + lane;
-        const bool valid = k < n;
-        const double lw = valid ? logw[k] : 0.0;
-        const double lu = valid ? logu[k] : 0.0;
-        const int64_t g = g0 + k;
-        const int64_t idx_before = idx;
-        unsigned remaining = __ballot_sync(0xffffffffu, valid);
-        unsigned accm = 0u;
-        while (remaining) {
-            const bool mine = (remaining >> lane) & 1u;
-            const bool test = mine && (g == 0 || (lw - cur) > lu);
-            const unsigned m = __ballot_sync(0xffffffffu, test);
-            if (m == 0u) break;
-            const int j = __ffs(m) - 1;
-            accm |= 1u << j;
-            cur = __shfl_sync(0xffffffffu, lw, j);
-            idx = g0 + base + j;
-            remaining &= (j == 31) ? 0u : ~((2u << j) - 1u);
+    for (int64_t blk = 0; blk < n; blk += 32 * kChunks) {
+        double lwv[kChunks], luv[kChunks];
+#pragma unroll
+        for (int c = 0; c < kChunks; ++c) {
+            const int64_t k = blk + 32 * c + lane;
+            lwv[c] = k < n ? __ldg(logw + k) : 0.0;
+            luv[c] = k < n ? __ldg(logu + k) : 0.0;
         }
-        // state after this lane's step: the last accept at or before it
-        const unsigned le = (lane == 31) ? accm : (accm & ((2u << lane) - 1u));
-        if (valid) {
-            if (chain_idx) chain_idx[k] = le ? (g0 + base + (31 - __clz(le))) : idx_before;
-            if (acc_out) acc_out[k] = (uint8_t)((accm >> lane) & 1u);
+#pragma unroll
+        for (int c = 0; c < kChunks; ++c) {
+            const int64_t base = blk + 32 * c;
+            if (base >= n) break;
+            const int64_t k = base + lane;
+            const bool valid = k < n;
+            const double lw = lwv[c], lu = luv[c];
+            const int64_t g = g0 + k;
+            const int64_t idx_before = idx;
+            unsigned remaining = __ballot_sync(0xffffffffu, valid);
+            unsigned accm = 0u;
+            while (remaining) {
+                const bool mine = (remaining >> lane) & 1u;
+                const bool test = mine && (g == 0 || (lw - cur) > lu);
+                const unsigned m = __ballot_sync(0xffffffffu, test);
+                if (m == 0u) break;
+                const int j = __ffs(m) - 1;
+                accm |= 1u << j;
+                cur = __shfl_sync(0xffffffffu, lw, j);
+                idx = g0 + base + j;
+                remaining &= (j == 31) ? 0u : ~((2u << j) - 1u);
+            }
+            // state after this lane's step: the last accept at or before it
+            const unsigned le = (lane == 31) ? accm : (accm & ((2u << lane) - 1u));
+            if (valid) {
+                if (chain_idx) chain_idx[k] = le ? (g0 + base + (31 - __clz(le))) : idx_before;
+                if (acc_out) acc_out[k] = (uint8_t)((accm >> lane) & 1u);
+            }
+            int cnt = __popc(accm);
+            if (g0 + base == 0 && (accm & 1u)) cnt -= 1;   // step 0 is not counted
+            nacc += cnt;
         }
-        int cnt = __popc(accm);
-        if (g0 + base == 0 && (accm & 1u)) cnt -= 1;   // step 0 is not counted
-        nacc += cnt;
     }
     if (lane == 0) {
         st->logw_cur = cur;

@@ -1,0 +1,70 @@
+"""Continuous-batching request loop: each result is the same alone and in the mix.
+
+Requests of different lattice sizes, dimensions and couplings are admitted as
+slots and HBM budget free up; their chunks overlap on the GPU on separate
+streams.  Every request's phi, log q, S, log w, chain indices, accept flags and
+final chain state must be bit-identical to the same request served alone, and
+one request is checked against the FP64 oracle.
+"""
+import numpy as np
+import pytest
+
+import gf_inputs as gi
+from gpu_util import assert_logw_close, assert_sites_close, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def _models(P):
+    specs = [("a", gi.FlowShape(2, 8, 4, 8, 8), 1), ("b", gi.FlowShape(3, 4, 3, 16, 16), 2),
+             ("c", gi.FlowShape(2, 16, 6, 16, 16), 3), ("d", gi.FlowShape(3, 16, 2, 32, 32), 4)]
+    from paper_2208_08903_gb300 import serving
+    models = {}
+    for name, shape, s in specs:
+        prec = "bf16" if (shape.nd == 3 and shape.L == 16 and shape.c1 == 32) else "fp32"
+        models[name] = serving.Model(name, shape, P.Flow(shape, gi.init_weights(shape, seed=s), precision=prec))
+    return models, {n: (sh, s) for n, sh, s in specs}
+
+
+def test_results_same_alone_and_in_mix(orc):
+    torch, P = require_gpu()
+    from paper_2208_08903_gb300 import serving
+    models, specs = _models(P)
+    rng = np.random.default_rng(0)
+    names = list(models)
+    reqs = [serving.Request(i, names[i % 4], float(rng.uniform(-6, -2)), float(rng.uniform(1, 10)),
+                            int(rng.integers(5, 300)), 900 + i, arrival=0.0) for i in range(14)]
+    budget = 6 << 20
+    srv = serving.Server(models, hbm_budget_bytes=budget, max_active=4, chunk=64)
+    mix, stats = srv.run(reqs, realtime=False)
+    assert stats["requests"] == len(reqs)
+    assert stats["max_concurrent_requests"] > 1
+    assert stats["peak_budget_bytes"] <= budget
+    for r in reqs:
+        alone, _ = serving.Server(models, hbm_budget_bytes=budget, max_active=1, chunk=64).run([r], realtime=False)
+        a, m = alone[r.rid], mix[r.rid]
+        for k in ("phi", "logq", "S", "logw", "chain_idx", "accepted", "mh_state"):
+            assert torch.equal(getattr(a, k), getattr(m, k)), (r.rid, k)
+    # one request against the oracle
+    r = reqs[2]
+    shape, s = specs[r.model]
+    w = gi.init_weights(shape, seed=s)
+    ref = orc.flow_sample(shape, w, r.m2, r.lam, r.batch, seed=r.seed, counter0=0)
+    assert_sites_close(mix[r.rid].phi.cpu().numpy(), ref["phi"])
+    assert_logw_close(mix[r.rid].logw.cpu().numpy(), ref["logw"])
+    assert P.device_status() == 0
+
+
+def test_realtime_poisson_loop_reports_latency():
+    torch, P = require_gpu()
+    from paper_2208_08903_gb300 import serving
+    models, _ = _models(P)
+    arr = serving.poisson_arrivals(40, 400.0, seed=1)
+    rng = np.random.default_rng(1)
+    names = list(models)
+    reqs = [serving.Request(i, names[int(rng.integers(4))], -4.0, 5.0, int(rng.integers(64, 512)), i,
+                            arrival=float(arr[i])) for i in range(40)]
+    res, stats = serving.Server(models, hbm_budget_bytes=64 << 20, max_active=8, chunk=256).run(reqs)
+    assert stats["requests"] == 40
+    assert 0 < stats["p50_latency_ms"] <= stats["p99_latency_ms"]
+    assert all(r.done >= r.arrival for r in res.values())
