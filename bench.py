@@ -52,6 +52,23 @@ def flops_per_config(shape) -> float:
     return per_layer * shape.n_layers
 
 
+def measured_traffic(kernel: str, batch: int):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary
+    (profiles/roofline_traffic.json), or None when the kernel's source changed
+    since the counters were taken or the capture was at another batch size."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "roofline_traffic.json")) as f:
+            ent = json.load(f)[kernel]
+        src = os.path.join(ROOT, "paper_2208_08903_gb300", "csrc", ent["source"])
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        if sha != ent["source_sha256"] or int(ent["batch"]) != int(batch):
+            return None
+        return float(ent["dram_bytes_read"]) + float(ent["dram_bytes_write"])
+    except Exception:
+        return None
+
+
 def fp32_alu_peak_tflops(n_sm: int, mhz: float) -> float:
     # 128 FP32 FMA lanes per SM, 2 FLOP per FMA
     return n_sm * 128 * 2 * mhz * 1e6 / 1e12
@@ -237,6 +254,7 @@ def bench_gpu(args, rank, world, local):
                 "frac": achieved / peak, "traffic": None,
                 "peak_kind": f"FP32 FFMA: {n_sm} SM x 128 lanes x 2 FLOP x {mhz:.0f} MHz (derived)"}
     roof["kernel"] = "flow_fp32_kernel" if prec == "fp32" else "flow_bf16_kernel"
+    roof["traffic"] = measured_traffic(roof["kernel"], B)
     roof["flops_per_config"] = fpc
     value = world * B * args.steps / (total_ms / 1e3)
     res = {

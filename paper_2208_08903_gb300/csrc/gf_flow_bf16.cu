@@ -38,7 +38,8 @@ constexpr int kL = 16, kS = 256, kC = 32, kT = 27;
 constexpr int kHaloSites = 18 * 16;                    // y = -1 .. 16
 constexpr int kSlotBytes = 4 * kHaloSites * 16;        // [cg][site][8] bf16 = 18432
 constexpr int kW2Bytes = kT * 4 * 32 * 16;             // [t][kg][n][8] bf16 = 55296
-// FP32 part of a layer block (floats): W1s[t][c], b1[c], b2[c], W3s[t][c][2], b3[2], pad
+// FP32 part of a layer block (floats): W1s[t][c], b1[c], b2[c],
+// W3s[t][i][cg][4] = (s, t weights of channel cg*8+2i, then of channel cg*8+2i+1), b3[2], pad
 constexpr int kF_W1 = 0, kF_b1 = kT * kC, kF_b2 = kF_b1 + kC, kF_W3 = kF_b2 + kC;
 constexpr int kF_b3 = kF_W3 + kT * kC * 2, kF_N = (kF_b3 + 2 + 3) & ~3;
 constexpr int kLayerBytes = kW2Bytes + kF_N * 4;
@@ -152,6 +153,31 @@ __device__ __forceinline__ void store8(unsigned char* slot, int cg, int y, int x
     if (y == 15) *reinterpret_cast<uint4*>(base + hsite(-1, x) * 16) = w;
 }
 
+// h2 (conv3 input only) is stored site-major: 288 halo sites x 64 bytes (32
+// channels), the four 16-byte channel-group chunks of a site permuted by
+// (site >> 1) & 3.  Readers and writers whose lanes touch sites an odd number
+// of sites apart then hit disjoint banks.
+__device__ __forceinline__ int h2_chunk(int hs, int cg) { return hs * 64 + ((cg ^ ((hs >> 1) & 3)) << 4); }
+
+__device__ __forceinline__ void store_h2(unsigned char* slot, int y, int x, const float (&v)[32]) {
+    uint4 w[4];
+#pragma unroll
+    for (int cg = 0; cg < 4; ++cg) {
+        __align__(16) __nv_bfloat162 p[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) p[i] = __floats2bfloat162_rn(v[cg * 8 + 2 * i], v[cg * 8 + 2 * i + 1]);
+        w[cg] = *reinterpret_cast<const uint4*>(p);
+    }
+    const int hs = hsite(y, x);
+#pragma unroll
+    for (int cg = 0; cg < 4; ++cg) *reinterpret_cast<uint4*>(slot + h2_chunk(hs, cg)) = w[cg];
+    if (y == 0 || y == 15) {
+        const int hh = hsite(y == 0 ? 16 : -1, x);
+#pragma unroll
+        for (int cg = 0; cg < 4; ++cg) *reinterpret_cast<uint4*>(slot + h2_chunk(hh, cg)) = w[cg];
+    }
+}
+
 // Virtual slice v (may lie outside 0..L-1 by the wrap-around recomputation)
 // -> lattice slice v mod L; h1 slot v mod 4, h2 slot v mod 3.
 __device__ __forceinline__ int slice_of(int v) { return v & 15; }
@@ -170,7 +196,8 @@ __device__ __forceinline__ void conv1_slice(unsigned char* h1, int v, const floa
 #pragma unroll 1
     for (int it = tid; it < kS * 4; it += kThreads) {
         const int cg = it >> 8, rest = it & 255, pcls = rest >> 7, k = rest & 127;
-        const int y = k >> 3, xx = 2 * (k & 7) + ((pcls ^ z ^ y) & 1);    // (z+y+x) & 1 == pcls
+        // neighbouring lanes alternate between rows y and y+1 (conflict-free stores)
+        const int y = 2 * (k >> 4) + (k & 1), xx = 2 * ((k >> 1) & 7) + ((pcls ^ z ^ y) & 1);  // parity pcls
         const int need = (frozen ^ pcls) & 1;                              // tap parity reaching fixed sites
         int zr[3], yr[3], xc[3];
 #pragma unroll
@@ -249,18 +276,14 @@ __device__ __forceinline__ void conv2_epilogue(unsigned char* h2, uint32_t tmem,
     const int src_m = (lane & 16) | ((xx + 15) & 15);   // x - 1
     const int src_p = (lane & 16) | ((xx + 1) & 15);    // x + 1
     unsigned char* slot = h2 + (size_t)h2_slot(v) * kSlotBytes;
+    float o[32];
 #pragma unroll
-    for (int cg = 0; cg < 4; ++cg) {
-        float o[8];
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const int ch = cg * 8 + c;
-            const float s = p0[ch] + __shfl_sync(0xffffffffu, pm[ch], src_m) +
-                            __shfl_sync(0xffffffffu, pp[ch], src_p) + wf[kF_b2 + ch];
-            o[c] = s > 0.f ? s : slope * s;
-        }
-        store8(slot, cg, y, xx, o);
+    for (int ch = 0; ch < 32; ++ch) {
+        const float sum = p0[ch] + __shfl_sync(0xffffffffu, pm[ch], src_m) +
+                          __shfl_sync(0xffffffffu, pp[ch], src_p) + wf[kF_b2 + ch];
+        o[ch] = sum > 0.f ? sum : slope * sum;
     }
+    store_h2(slot, y, xx, o);
 }
 
 // conv3 at the 128 updated sites of slice z and the affine update of x.
@@ -271,25 +294,25 @@ __device__ __forceinline__ void conv2_epilogue(unsigned char* h2, uint32_t tmem,
 __device__ __forceinline__ void conv3_slice(const unsigned char* h2, int z, const float* wf, float* x, int frozen,
                                             int use_tanh, bool inverse, double& logdet, int tid) {
     const int cg = tid & 3, pair = tid >> 2;                   // 64 pairs
-    const int y = pair >> 2, kp = pair & 3;                    // 4 pairs per row: k = 2kp, 2kp+1
+    const int y = 2 * (pair >> 3) + (pair & 1), kp = (pair >> 1) & 3;   // lanes 4-7 take row y+1
     const int off = (frozen ^ 1 ^ z ^ y) & 1;
     const int xa = 4 * kp + off, xb = xa + 2;
     const unsigned char* sl[3];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) sl[d] = h2 + (size_t)h2_slot(z - 1 + d) * kSlotBytes + (size_t)cg * kHaloSites * 16;
+    for (int d = 0; d < 3; ++d) sl[d] = h2 + (size_t)h2_slot(z - 1 + d) * kSlotBytes;
     float psa = 0.f, pta = 0.f, psb = 0.f, ptb = 0.f;
 #pragma unroll
     for (int t = 0; t < kT; ++t) {
         const int dzi = t / 9, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
         const int row = (y + dy + 1) * 16;
-        const uint4 ra = *reinterpret_cast<const uint4*>(sl[dzi] + (row + wrap16(xa + dx)) * 16);
-        const uint4 rb = *reinterpret_cast<const uint4*>(sl[dzi] + (row + wrap16(xb + dx)) * 16);
-        const float4* w = reinterpret_cast<const float4*>(wf + kF_W3 + t * kC * 2 + cg * 16);
+        const uint4 ra = *reinterpret_cast<const uint4*>(sl[dzi] + h2_chunk(row + wrap16(xa + dx), cg));
+        const uint4 rb = *reinterpret_cast<const uint4*>(sl[dzi] + h2_chunk(row + wrap16(xb + dx), cg));
+        const float4* w = reinterpret_cast<const float4*>(wf + kF_W3 + t * kC * 2) + cg;   // [i][cg][4]
         const __nv_bfloat162* ha = reinterpret_cast<const __nv_bfloat162*>(&ra);
         const __nv_bfloat162* hb = reinterpret_cast<const __nv_bfloat162*>(&rb);
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            const float4 wv = w[i];                            // (s,t) of channels 2i, 2i+1
+            const float4 wv = w[4 * i];                        // (s,t) of channels cg*8+2i, cg*8+2i+1
             const float2 fa = __bfloat1622float2(ha[i]);
             const float2 fb = __bfloat1622float2(hb[i]);
             psa = fmaf(fa.x, wv.x, psa); pta = fmaf(fa.x, wv.y, pta);
@@ -493,7 +516,9 @@ __global__ void repack_bf16_kernel(const float* __restrict__ canon, int64_t cstr
             else if (f < kF_b2) v = b1[f - kF_b1];
             else if (f < kF_W3) v = b2[f - kF_b2];
             else if (f < kF_b3) {
-                const int g = f - kF_W3, o = g & 1, c = (g >> 1) % kC, t = g / (2 * kC);
+                const int g = f - kF_W3, t = g / (2 * kC), r = g % (2 * kC);
+                const int i = r >> 4, cgi = (r >> 2) & 3, e = r & 3;
+                const int c = cgi * 8 + 2 * i + (e >> 1), o = e & 1;
                 v = W3[((int64_t)o * kC + c) * kT + t];
             } else if (f < kF_b3 + 2) v = b3[f - kF_b3];
             reinterpret_cast<float*>(blk + kW2Bytes)[f] = v;
