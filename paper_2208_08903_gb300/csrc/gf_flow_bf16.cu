@@ -1,27 +1,30 @@
-// gf_flow_bf16.cu -- fused coupling stack with conv2 on the 5th-generation
-// tensor cores (tcgen05, BF16 operands, FP32 accumulation in TMEM), for 3D
-// lattices with L = 16 and hidden width 32.
+// gf_flow_bf16.cu -- fused coupling stack with conv2 and conv3 on the
+// 5th-generation tensor cores (tcgen05, BF16 operands, FP32 accumulation in
+// TMEM), for 3D lattices with L = 16 and hidden width 32.
 //
 // Paper arXiv:2208.08903 Sec. 1 (affine coupling layers, Jacobian, model
-// density, action); precision split of this variant: conv2 operands (h1 and
-// W2) in BF16, conv2 accumulation FP32, conv1/conv3/affine update in FP32,
-// h2 stored as BF16, the field x in FP32, and log-det, sum z^2, S, log q,
+// density, action); precision split of this variant: conv2 and conv3 operands
+// (h1, h2 and their weights) in BF16 with FP32 accumulation, conv1 and the
+// affine update in FP32, the field x in FP32, and log-det, sum z^2, S, log q,
 // log w in FP64.
 //
-// Per CTA one configuration at a time (persistent), the same slice schedule
-// as the FP32 kernel with one z-slice (256 sites) per phase:
-//   H1: conv1 (FFMA, fixed-site taps only) -> h1 slot (BF16)
-//   H2: conv2 as implicit GEMM: per z-slice two M=128 tiles (8 y-rows x 16 x),
-//       N = 32 output channels, K = 9 (dz,dy) taps x 32 channels; one elected
-//       thread issues tcgen05.mma with shared-memory descriptors.
-//       Activations are stored channel-group major ([4][288 sites][8 ch],
-//       288 = 18 y-rows incl. one periodic halo row on each side), so each
-//       8-site core matrix is 128 contiguous bytes and a (dz,dy) shift is just
-//       a different start address.  The x-shift is not materialised: three
-//       accumulators P_dx (dx = -1, 0, +1) are kept in TMEM and the epilogue
-//       forms out(x) = sum_dx P_dx(x + dx) with width-16 warp shuffles (one
-//       x-row = one half-warp = 16 TMEM lanes).
-//   C3: conv3 at the updated sites (FFMA from BF16 h2) + affine update.
+// Per CTA one configuration at a time (persistent).  Within a layer the
+// lattice is walked along z one 256-site slice at a time:
+//   conv1 (FFMA, only the 13/14 taps that reach fixed sites) -> h1 slice (BF16)
+//   conv2 as an implicit GEMM on the tensor cores -> h2 slice (BF16)
+//   conv3 as an implicit GEMM (N = 16, rows s and t) -> affine update of x
+// Implicit GEMM: per z-slice two M = 128 tiles (8 y-rows x 16 x); K = the 9
+// (dz,dy) taps x 32 channels in steps of 16.  Activations are stored channel-
+// group major ([4][288 sites][8 ch], 288 = 18 y-rows with one periodic halo row
+// on each side), so each 8-site core matrix is 128 contiguous bytes and a
+// (dz,dy) shift is only a different start address.  The periodic x-shift is
+// not gathered: three accumulators P_dx (dx = -1, 0, +1) stay in TMEM and the
+// epilogues form out(x) = sum_dx P_dx(x + dx) with width-16 shuffles (one
+// x-row = one half-warp = 16 TMEM lanes).
+// Pipeline, per virtual slice v: one thread issues conv3 of slice v-2 and
+// conv2 of slice v; meanwhile all warps run conv1 of slice v+2 on the FMA
+// pipes; then the conv3 epilogue updates slice v-2 and the conv2 epilogue
+// writes h2[v].
 #include <algorithm>
 #include <cstring>
 
@@ -36,15 +39,18 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kL = 16, kS = 256, kC = 32, kT = 27;
 constexpr int kHaloSites = 18 * 16;                    // y = -1 .. 16
-constexpr int kSlotBytes = 4 * kHaloSites * 16;        // [cg][site][8] bf16 = 18432
+constexpr int kCgStride = kHaloSites * 16;             // bytes between channel groups
+constexpr int kSlotBytes = 4 * kCgStride;              // [cg][site][8] bf16 = 18432
 constexpr int kW2Bytes = kT * 4 * 32 * 16;             // [t][kg][n][8] bf16 = 55296
-// FP32 part of a layer block (floats): W1s[t][c], b1[c], b2[c],
-// W3s[t][i][cg][4] = (s, t weights of channel cg*8+2i, then of channel cg*8+2i+1), b3[2], pad
-constexpr int kF_W1 = 0, kF_b1 = kT * kC, kF_b2 = kF_b1 + kC, kF_W3 = kF_b2 + kC;
-constexpr int kF_b3 = kF_W3 + kT * kC * 2, kF_N = (kF_b3 + 2 + 3) & ~3;
-constexpr int kLayerBytes = kW2Bytes + kF_N * 4;
-constexpr int kTmemCols = 256;                         // 2 tiles x 3 dx x 32 columns, rounded up
-constexpr long long kWaitLimit = 1ll << 22;            // bounded mbarrier wait (iterations)
+constexpr int kW3Bytes = kT * 4 * 8 * 16;              // [t][kg][n<8][8] bf16 = 13824 (rows s, t, zeros)
+// FP32 part of a layer block (floats): W1s[t][c], b1[c], b2[c], b3[2], pad
+constexpr int kF_W1 = 0, kF_b1 = kT * kC, kF_b2 = kF_b1 + kC, kF_b3 = kF_b2 + kC;
+constexpr int kF_N = (kF_b3 + 2 + 3) & ~3;
+constexpr int kLayerBytes = kW2Bytes + kW3Bytes + kF_N * 4;
+constexpr int kZeroBytes = 256;                         // two zero core matrices (B rows 8..15 of conv3)
+constexpr int kTmem3 = 192;                             // conv3 accumulators start here
+constexpr int kTmemCols = 512;                          // conv2: 2 x 3 x 32, conv3: 2 x 3 x 16
+constexpr long long kWaitLimit = 1ll << 22;             // bounded mbarrier wait (iterations)
 
 // ---------------------------------------------------------------- PTX wrappers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -105,11 +111,21 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 #pragma unroll
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
+// 32 lanes x 2 consecutive FP32 columns.
+__device__ __forceinline__ void tmem_ld2(uint32_t taddr, float& a, float& b) {
+    uint32_t r0, r1;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];" : "=r"(r0), "=r"(r1) : "r"(taddr) : "memory");
+    a = __uint_as_float(r0);
+    b = __uint_as_float(r1);
+}
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Shared-memory matrix descriptor, no swizzle, K-major canonical layout:
 // core matrix = 8 rows x 16 bytes contiguous; LBO = byte distance between
-// core matrices adjacent in K, SBO = between 8-row groups.
+// core matrices adjacent in K, SBO = between 8-row groups.  The start address
+// occupies the low 14 bits (in 16-byte units): adding (bytes >> 4) to a
+// descriptor moves its start; every shared address here is below 256 KB, so
+// the field never carries into LBO.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
     uint64_t d = 0;
     d |= (uint64_t)((addr >> 4) & 0x3FFFu);
@@ -118,13 +134,13 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
     d |= (uint64_t)1 << 46;              // descriptor version for tcgen05
     return d;                            // base offset 0, swizzle mode 0 (none)
 }
-// Instruction descriptor: D = F32, A = B = BF16, both K-major, N = 32, M = 128.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+// Instruction descriptors: D = F32, A = B = BF16, both K-major, M = 128, N = 32 / 16.
+constexpr uint32_t kIdesc32 = (1u << 4) | (1u << 7) | (1u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+constexpr uint32_t kIdesc16 = (1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
 
 struct Bf16Args {
     const unsigned char* Wl;   // per-layer blocks of kLayerBytes
-    const Phase* sched;
-    int n_phases, n_layers;
+    int n_layers;
     float slope;
     int use_tanh, has_phi4;
     double m2, lam;
@@ -140,42 +156,17 @@ __device__ __forceinline__ int wrap16(int v) { return v & 15; }
 // halo-row site index of interior (y, x), y in -1..16
 __device__ __forceinline__ int hsite(int y, int x) { return (y + 1) * 16 + x; }
 
-// Stores 8 channels (one channel group) of a site row in BF16, plus the
-// periodic halo copy when the row is y = 0 or y = 15.
+// Stores 8 channels (one channel group) of a site in BF16, plus the periodic
+// halo copy when the row is y = 0 or y = 15.
 __device__ __forceinline__ void store8(unsigned char* slot, int cg, int y, int x, const float* v) {
     __align__(16) __nv_bfloat162 p[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) p[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
     const uint4 w = *reinterpret_cast<const uint4*>(p);
-    unsigned char* base = slot + (size_t)cg * kHaloSites * 16;
+    unsigned char* base = slot + (size_t)cg * kCgStride;
     *reinterpret_cast<uint4*>(base + hsite(y, x) * 16) = w;
     if (y == 0) *reinterpret_cast<uint4*>(base + hsite(16, x) * 16) = w;
     if (y == 15) *reinterpret_cast<uint4*>(base + hsite(-1, x) * 16) = w;
-}
-
-// h2 (conv3 input only) is stored site-major: 288 halo sites x 64 bytes (32
-// channels), the four 16-byte channel-group chunks of a site permuted by
-// (site >> 1) & 3.  Readers and writers whose lanes touch sites an odd number
-// of sites apart then hit disjoint banks.
-__device__ __forceinline__ int h2_chunk(int hs, int cg) { return hs * 64 + ((cg ^ ((hs >> 1) & 3)) << 4); }
-
-__device__ __forceinline__ void store_h2(unsigned char* slot, int y, int x, const float (&v)[32]) {
-    uint4 w[4];
-#pragma unroll
-    for (int cg = 0; cg < 4; ++cg) {
-        __align__(16) __nv_bfloat162 p[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) p[i] = __floats2bfloat162_rn(v[cg * 8 + 2 * i], v[cg * 8 + 2 * i + 1]);
-        w[cg] = *reinterpret_cast<const uint4*>(p);
-    }
-    const int hs = hsite(y, x);
-#pragma unroll
-    for (int cg = 0; cg < 4; ++cg) *reinterpret_cast<uint4*>(slot + h2_chunk(hs, cg)) = w[cg];
-    if (y == 0 || y == 15) {
-        const int hh = hsite(y == 0 ? 16 : -1, x);
-#pragma unroll
-        for (int cg = 0; cg < 4; ++cg) *reinterpret_cast<uint4*>(slot + h2_chunk(hh, cg)) = w[cg];
-    }
 }
 
 // Virtual slice v (may lie outside 0..L-1 by the wrap-around recomputation)
@@ -188,7 +179,8 @@ __device__ __forceinline__ int h2_slot(int v) { return (v + 15) % 3; }
 // (channel group, site parity class, 128 sites of that class); a warp holds
 // sites of one parity, so every lane takes the same 13 or 14 taps (those whose
 // neighbour has the fixed parity), selected by a warp-uniform test on a
-// compile-time tap offset.
+// compile-time tap offset.  Neighbouring lanes alternate between rows y and
+// y+1, which keeps the 16-byte stores free of bank conflicts.
 __device__ __forceinline__ void conv1_slice(unsigned char* h1, int v, const float* wf, const float* x, int frozen,
                                             float slope, int tid) {
     const int z = slice_of(v);
@@ -196,7 +188,6 @@ __device__ __forceinline__ void conv1_slice(unsigned char* h1, int v, const floa
 #pragma unroll 1
     for (int it = tid; it < kS * 4; it += kThreads) {
         const int cg = it >> 8, rest = it & 255, pcls = rest >> 7, k = rest & 127;
-        // neighbouring lanes alternate between rows y and y+1 (conflict-free stores)
         const int y = 2 * (k >> 4) + (k & 1), xx = 2 * ((k >> 1) & 7) + ((pcls ^ z ^ y) & 1);  // parity pcls
         const int need = (frozen ^ pcls) & 1;                              // tap parity reaching fixed sites
         int zr[3], yr[3], xc[3];
@@ -227,21 +218,18 @@ __device__ __forceinline__ void conv1_slice(unsigned char* h1, int v, const floa
     }
 }
 
-// One elected thread: conv2 of virtual slice v as 2 M-tiles x 3 dx accumulators
-// x 9 (dz,dy) taps x 2 K-steps of tcgen05.mma, then a commit to the mbarrier.
-__device__ __forceinline__ void issue_conv2(const unsigned char* h1, const unsigned char* w2s, uint32_t tmem,
-                                            int v, uint64_t* mbar) {
-    fence_after_sync();
-    const uint32_t w2a = smem_u32(w2s);
-    uint32_t slots[3];
+// One elected thread: an implicit-GEMM convolution of a slice.  For each of
+// the 2 M-tiles and 3 dx accumulators (N columns each, from TMEM column d0):
+// 9 (dz,dy) taps x 2 K-steps of tcgen05.mma.  a_slot[dzi] = A descriptors of
+// the three input slices; the B descriptor of tap t, K-step k is
+// bdesc(t, k) (a functor, so conv3 can give each one its own SBO).
+template <int N, typename BDesc>
+__device__ __forceinline__ void issue_conv(const uint64_t (&a_slot)[3], BDesc bdesc, uint32_t d0, uint32_t idesc) {
 #pragma unroll
-    for (int d = 0; d < 3; ++d) slots[d] = smem_u32(h1 + (size_t)h1_slot(v - 1 + d) * kSlotBytes);
-#pragma unroll 1
     for (int mt = 0; mt < 2; ++mt) {
-#pragma unroll 1
+#pragma unroll
         for (int dxi = 0; dxi < 3; ++dxi) {
-            const uint32_t d = tmem + (uint32_t)((mt * 3 + dxi) * 32);
-            uint32_t acc = 0;
+            const uint32_t d = d0 + (uint32_t)((mt * 3 + dxi) * N);
 #pragma unroll
             for (int dzi = 0; dzi < 3; ++dzi) {
 #pragma unroll
@@ -249,20 +237,16 @@ __device__ __forceinline__ void issue_conv2(const unsigned char* h1, const unsig
                     const int t = (dzi * 3 + dyi) * 3 + dxi;
 #pragma unroll
                     for (int k = 0; k < 2; ++k) {
-                        const uint32_t aaddr = slots[dzi] + (uint32_t)(2 * k * kHaloSites * 16) +
-                                               (uint32_t)((mt * 8 + dyi) * 16 * 16);
-                        const uint32_t baddr = w2a + (uint32_t)(t * 2048 + 2 * k * 512);
-                        mma_bf16(d, smem_desc(aaddr, kHaloSites * 16, 128), smem_desc(baddr, 512, 128), kIdesc, acc);
-                        acc = 1;
+                        const uint64_t ad = a_slot[dzi] + (uint64_t)((2 * k * kCgStride + (mt * 8 + dyi) * 256) >> 4);
+                        mma_bf16(d, ad, bdesc(t, k), idesc, (dzi | dyi | k) ? 1u : 0u);
                     }
                 }
             }
         }
     }
-    mma_commit(mbar);
 }
 
-// Epilogue: out(x) = sum_dx P_dx(x + dx) + b2, LReLU, BF16 into the h2 slot of v.
+// conv2 epilogue: out(x) = sum_dx P_dx(x + dx) + b2, LReLU, BF16 into the h2 slot of v.
 __device__ __forceinline__ void conv2_epilogue(unsigned char* h2, uint32_t tmem, int v, const float* wf, float slope,
                                                int warp, int lane) {
     const int mt = warp >> 2, q = warp & 3;
@@ -276,82 +260,70 @@ __device__ __forceinline__ void conv2_epilogue(unsigned char* h2, uint32_t tmem,
     const int src_m = (lane & 16) | ((xx + 15) & 15);   // x - 1
     const int src_p = (lane & 16) | ((xx + 1) & 15);    // x + 1
     unsigned char* slot = h2 + (size_t)h2_slot(v) * kSlotBytes;
-    float o[32];
 #pragma unroll
-    for (int ch = 0; ch < 32; ++ch) {
-        const float sum = p0[ch] + __shfl_sync(0xffffffffu, pm[ch], src_m) +
-                          __shfl_sync(0xffffffffu, pp[ch], src_p) + wf[kF_b2 + ch];
-        o[ch] = sum > 0.f ? sum : slope * sum;
+    for (int cg = 0; cg < 4; ++cg) {
+        float o[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int ch = cg * 8 + c;
+            const float s = p0[ch] + __shfl_sync(0xffffffffu, pm[ch], src_m) +
+                            __shfl_sync(0xffffffffu, pp[ch], src_p) + wf[kF_b2 + ch];
+            o[c] = s > 0.f ? s : slope * s;
+        }
+        store8(slot, cg, y, xx, o);
     }
-    store_h2(slot, y, xx, o);
 }
 
-// conv3 at the 128 updated sites of slice z and the affine update of x.
-// Thread = (pair of updated sites of one y-row, channel group cg): 4 lanes
-// (the 4 channel groups) share a site pair and are combined by shuffles; the
-// conv3 weights of a tap and channel group (8 channels x (s,t)) are loaded once
-// for both sites.  Lane cg == 0 applies the update and accumulates the log-det.
-__device__ __forceinline__ void conv3_slice(const unsigned char* h2, int z, const float* wf, float* x, int frozen,
-                                            int use_tanh, bool inverse, double& logdet, int tid) {
-    const int cg = tid & 3, pair = tid >> 2;                   // 64 pairs
-    const int y = 2 * (pair >> 3) + (pair & 1), kp = (pair >> 1) & 3;   // lanes 4-7 take row y+1
-    const int off = (frozen ^ 1 ^ z ^ y) & 1;
-    const int xa = 4 * kp + off, xb = xa + 2;
-    const unsigned char* sl[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) sl[d] = h2 + (size_t)h2_slot(z - 1 + d) * kSlotBytes;
-    float psa = 0.f, pta = 0.f, psb = 0.f, ptb = 0.f;
-#pragma unroll
-    for (int t = 0; t < kT; ++t) {
-        const int dzi = t / 9, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
-        const int row = (y + dy + 1) * 16;
-        const uint4 ra = *reinterpret_cast<const uint4*>(sl[dzi] + h2_chunk(row + wrap16(xa + dx), cg));
-        const uint4 rb = *reinterpret_cast<const uint4*>(sl[dzi] + h2_chunk(row + wrap16(xb + dx), cg));
-        const float4* w = reinterpret_cast<const float4*>(wf + kF_W3 + t * kC * 2) + cg;   // [i][cg][4]
-        const __nv_bfloat162* ha = reinterpret_cast<const __nv_bfloat162*>(&ra);
-        const __nv_bfloat162* hb = reinterpret_cast<const __nv_bfloat162*>(&rb);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const float4 wv = w[4 * i];                        // (s,t) of channels cg*8+2i, cg*8+2i+1
-            const float2 fa = __bfloat1622float2(ha[i]);
-            const float2 fb = __bfloat1622float2(hb[i]);
-            psa = fmaf(fa.x, wv.x, psa); pta = fmaf(fa.x, wv.y, pta);
-            psa = fmaf(fa.y, wv.z, psa); pta = fmaf(fa.y, wv.w, pta);
-            psb = fmaf(fb.x, wv.x, psb); ptb = fmaf(fb.x, wv.y, ptb);
-            psb = fmaf(fb.y, wv.z, psb); ptb = fmaf(fb.y, wv.w, ptb);
-        }
+// conv3 epilogue of slice z: (s, t) = sum_dx P3_dx(x + dx) + b3 for every
+// site; the updated sites apply the affine map and accumulate the log-det.
+__device__ __forceinline__ void conv3_epilogue(uint32_t tmem, int z, const float* wf, float* x, int frozen,
+                                               int use_tanh, bool inverse, double& logdet, int warp, int lane) {
+    const int mt = warp >> 2, q = warp & 3;
+    const int y = mt * 8 + q * 2 + (lane >> 4), xx = lane & 15;
+    const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+    float sm, tm, s0, t0, sp, tp;
+    tmem_ld2(tmem + lane_base + (uint32_t)(kTmem3 + (mt * 3 + 0) * 16), sm, tm);
+    tmem_ld2(tmem + lane_base + (uint32_t)(kTmem3 + (mt * 3 + 1) * 16), s0, t0);
+    tmem_ld2(tmem + lane_base + (uint32_t)(kTmem3 + (mt * 3 + 2) * 16), sp, tp);
+    tmem_ld_wait();
+    const int src_m = (lane & 16) | ((xx + 15) & 15);
+    const int src_p = (lane & 16) | ((xx + 1) & 15);
+    const float spre = s0 + __shfl_sync(0xffffffffu, sm, src_m) + __shfl_sync(0xffffffffu, sp, src_p) + wf[kF_b3];
+    const float tt = t0 + __shfl_sync(0xffffffffu, tm, src_m) + __shfl_sync(0xffffffffu, tp, src_p) + wf[kF_b3 + 1];
+    if (((z + y + xx) & 1) != frozen) {
+        const float s = use_tanh ? tanhf(spre) : spre;
+        float& xv = x[(z * 16 + y) * 16 + xx];
+        if (!inverse) xv = fmaf(xv, expf(s), tt);
+        else xv = (xv - tt) * expf(-s);
+        logdet += (double)s;
     }
-#pragma unroll
-    for (int o = 1; o < 4; o <<= 1) {
-        psa += __shfl_xor_sync(0xffffffffu, psa, o); pta += __shfl_xor_sync(0xffffffffu, pta, o);
-        psb += __shfl_xor_sync(0xffffffffu, psb, o); ptb += __shfl_xor_sync(0xffffffffu, ptb, o);
+}
+
+// Bounded wait on an mbarrier phase; on expiry records GF_ETIMEOUT and raises
+// the CTA's abort flag (the caller leaves its loops, frees TMEM and returns).
+__device__ __forceinline__ void wait_bar(uint64_t* bar, uint32_t& phase, int* abort_flag, int32_t* status) {
+    long long spins = 0;
+    while (!mbar_try_wait(bar, phase)) {
+        if (++spins > kWaitLimit) { *abort_flag = 1; set_status(status, GF_ETIMEOUT); break; }
     }
-    if (cg == 0) {
-        const float bs = wf[kF_b3], bt = wf[kF_b3 + 1];
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const float spre = (q ? psb : psa) + bs, tt = (q ? ptb : pta) + bt;
-            const float s = use_tanh ? tanhf(spre) : spre;
-            float& xv = x[(z * 16 + y) * 16 + (q ? xb : xa)];
-            if (!inverse) xv = fmaf(xv, expf(s), tt);
-            else xv = (xv - tt) * expf(-s);
-            logdet += (double)s;
-        }
-    }
+    phase ^= 1u;
+    fence_after_sync();
 }
 
 template <bool INVERSE>
 __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char* w2s = smem;                                        // kW2Bytes
-    float* wf = reinterpret_cast<float*>(smem + kW2Bytes);            // kF_N floats
-    unsigned char* h1 = smem + kW2Bytes + kF_N * 4;                   // 4 slots
-    unsigned char* h2 = h1 + 4 * kSlotBytes;                          // 3 slots
-    float* x = reinterpret_cast<float*>(h2 + 3 * kSlotBytes);         // 4096 floats
-    double* red = reinterpret_cast<double*>(x + 4096);                // 32
-    Phase* ph = reinterpret_cast<Phase*>(red + 32);
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(ph) + ((sizeof(Phase) + 7) & ~7));
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 1);
+    unsigned char* w2s = smem;                                                 // kW2Bytes
+    unsigned char* w3s = smem + kW2Bytes;                                      // kW3Bytes
+    float* wf = reinterpret_cast<float*>(smem + kW2Bytes + kW3Bytes);          // kF_N floats
+    unsigned char* zero = smem + kLayerBytes;                                  // kZeroBytes
+    unsigned char* h1 = zero + kZeroBytes;                                     // 4 slots
+    unsigned char* h2 = h1 + 4 * kSlotBytes;                                   // 3 slots
+    float* x = reinterpret_cast<float*>(h2 + 3 * kSlotBytes);                  // 4096 floats
+    double* red = reinterpret_cast<double*>(x + 4096);                         // 32
+    uint64_t* bar2 = reinterpret_cast<uint64_t*>(red + 32);
+    uint64_t* bar3 = bar2 + 1;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar3 + 1);
     int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -361,15 +333,34 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
         tmem_relinquish();
     }
     if (tid == 0) {
-        mbar_init(mbar, 1);
+        mbar_init(bar2, 1);
+        mbar_init(bar3, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    for (int i = tid; i < kZeroBytes / 16; i += kThreads) reinterpret_cast<uint4*>(zero)[i] = make_uint4(0, 0, 0, 0);
+    fence_proxy_async();
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
     const uint32_t tmem = *tmem_slot;
-    uint32_t phase_bit = 0;
+    uint32_t ph2 = 0, ph3 = 0;
+
+    // A descriptors of every h1 / h2 slot (LBO = channel-group stride, SBO = 8 sites);
+    // conv2 B: LBO = 512 between K groups, SBO = 128 between 8-row N groups;
+    // conv3 B: LBO = 128, and its second 8-row N group (rows 8..15) is read from the
+    // zero block, so its SBO is (zero block - start) for each (tap, K-step).
+    const uint64_t a1_0 = smem_desc(smem_u32(h1), kCgStride, 128);
+    const uint64_t a2_0 = smem_desc(smem_u32(h2), kCgStride, 128);
+    const auto a1 = [a1_0](int slot) { return a1_0 + (uint64_t)(slot * (kSlotBytes >> 4)); };
+    const auto a2 = [a2_0](int slot) { return a2_0 + (uint64_t)(slot * (kSlotBytes >> 4)); };
+    const uint64_t b2d = smem_desc(smem_u32(w2s), 512, 128);
+    const uint32_t w3a = smem_u32(w3s), za = smem_u32(zero);
+    const auto bdesc2 = [b2d](int t, int k) { return b2d + (uint64_t)((t * 2048 + k * 1024) >> 4); };
+    const auto bdesc3 = [w3a, za](int t, int k) {
+        const uint32_t start = w3a + (uint32_t)(t * 512 + k * 256);
+        return smem_desc(start, 128, za - start);
+    };
 
     for (int64_t b = blockIdx.x; b < a.B; b += gridDim.x) {
         double sumz2 = 0.0;
@@ -402,8 +393,7 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
         for (int li = 0; li < a.n_layers && !*abort_flag; ++li) {
             const int l = INVERSE ? a.n_layers - 1 - li : li;
             const int frozen = l & 1;
-            // stage this layer's weights (W2 already in the MMA operand layout)
-            {
+            {   // stage this layer's weights (W2, W3 already in the MMA operand layouts)
                 const uint4* src = reinterpret_cast<const uint4*>(a.Wl + (size_t)l * kLayerBytes);
                 uint4* dst = reinterpret_cast<uint4*>(smem);
                 for (int i = tid; i < kLayerBytes / 16; i += kThreads) dst[i] = __ldg(src + i);
@@ -414,30 +404,42 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
             for (int v = -2; v <= 0; ++v) conv1_slice(h1, v, wf, x, frozen, a.slope, tid);
             fence_proxy_async();
             __syncthreads();
-            // pipeline over the virtual h2 slices v = -1 .. L (slice v mod L):
-            //   tensor cores: conv2 of h2[v]      FFMA: conv3 + update of slice v-2, conv1 of h1[v+2]
-            for (int v = -1; v <= kL; ++v) {
-                if (tid == 0) issue_conv2(h1, w2s, tmem, v, mbar);
-                if (v - 2 >= 0) conv3_slice(h2, v - 2, wf, x, frozen, a.use_tanh, INVERSE, logdet, tid);
+            // v = -1 .. L+1: conv2 of h2[v] (v <= L), conv3 + update of slice v-2 (v >= 2),
+            // conv1 of h1[v+2] (v+2 <= L+1) on the FMA pipes meanwhile.
+            for (int v = -1; v <= kL + 1; ++v) {
+                const bool do2 = v <= kL, do3 = v >= 2;
+                if (tid == 0) {
+                    fence_after_sync();
+                    if (do3) {
+                        const uint64_t as[3] = {a2(h2_slot(v - 3)), a2(h2_slot(v - 2)), a2(h2_slot(v - 1))};
+                        issue_conv<16>(as, bdesc3, tmem + kTmem3, kIdesc16);
+                        mma_commit(bar3);
+                    }
+                    if (do2) {
+                        const uint64_t as[3] = {a1(h1_slot(v - 1)), a1(h1_slot(v)), a1(h1_slot(v + 1))};
+                        issue_conv<32>(as, bdesc2, tmem, kIdesc32);
+                        mma_commit(bar2);
+                    }
+                }
                 if (v + 2 <= kL + 1) {
                     conv1_slice(h1, v + 2, wf, x, frozen, a.slope, tid);
                     fence_proxy_async();
                 }
-                __syncthreads();                       // conv3 done reading the h2 slot about to be reused
-                long long spins = 0;
-                while (!mbar_try_wait(mbar, phase_bit)) {
-                    if (++spins > kWaitLimit) { *abort_flag = 1; set_status(a.status, GF_ETIMEOUT); break; }
+                __syncthreads();
+                if (do3) {
+                    // conv3 of slice v-2 has finished reading all three h2 slots after this wait
+                    wait_bar(bar3, ph3, abort_flag, a.status);
+                    conv3_epilogue(tmem, slice_of(v - 2), wf, x, frozen, a.use_tanh, INVERSE, logdet, warp, lane);
                 }
-                phase_bit ^= 1u;
-                fence_after_sync();
-                conv2_epilogue(h2, tmem, v, wf, a.slope, warp, lane);
+                if (do2) {
+                    wait_bar(bar2, ph2, abort_flag, a.status);
+                    conv2_epilogue(h2, tmem, v, wf, a.slope, warp, lane);
+                    fence_proxy_async();
+                }
                 fence_before_sync();
                 __syncthreads();
                 if (*abort_flag) break;
             }
-            if (*abort_flag) break;
-            conv3_slice(h2, kL - 1, wf, x, frozen, a.use_tanh, INVERSE, logdet, tid);
-            __syncthreads();
         }
         if (*abort_flag) break;
 
@@ -454,16 +456,16 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
         const double z2 = block_sum(sumz2, red);
         double S = 0.0;
         if (!INVERSE && a.has_phi4) {
+            // forward-hop arrangement of the action: (2d + m2) phi^2 + lam phi^4 - 2 phi sum_mu phi(n + mu)
+            const double c2d = 6.0 + a.m2;
             double acc = 0.0;
             for (int n = tid; n < V; n += kThreads) {
                 const int xc = n & 15, yc = (n >> 4) & 15, zc = n >> 8;
-                const double p = x[n];
-                double kk = 6.0 * p;
-                kk -= (double)x[(n & ~15) | wrap16(xc + 1)] + (double)x[(n & ~15) | wrap16(xc - 1)];
-                kk -= (double)x[(zc << 8) | (wrap16(yc + 1) << 4) | xc] + (double)x[(zc << 8) | (wrap16(yc - 1) << 4) | xc];
-                kk -= (double)x[(wrap16(zc + 1) << 8) | (yc << 4) | xc] + (double)x[(wrap16(zc - 1) << 8) | (yc << 4) | xc];
-                const double p2 = p * p;
-                acc += p * kk + a.m2 * p2 + a.lam * p2 * p2;
+                const double hop = (double)x[(n & ~15) | wrap16(xc + 1)] +
+                                   (double)x[(zc << 8) | (wrap16(yc + 1) << 4) | xc] +
+                                   (double)x[(wrap16(zc + 1) << 8) | (yc << 4) | xc];
+                const double c = x[n], qq = c * c;
+                acc += fma(qq, fma(a.lam, qq, c2d), -2.0 * c * hop);
             }
             S = block_sum(acc, red);
         }
@@ -486,13 +488,15 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
     }
 }
 
-constexpr size_t kSmemBytes = (size_t)kW2Bytes + kF_N * 4 + 7 * (size_t)kSlotBytes + 4096 * 4 + 32 * 8 +
-                              ((sizeof(Phase) + 7) & ~size_t(7)) + 8 + 4 + 4;
+constexpr size_t kSmemBytes = (size_t)kLayerBytes + kZeroBytes + 7 * (size_t)kSlotBytes + 4096 * 4 + 32 * 8 +
+                              2 * 8 + 4 + 4;
 
-// canonical FP32 -> per-layer BF16 block (W2 in [t][kg][n][8]) + FP32 block
+// canonical FP32 -> per-layer block: W2 [t][kg][n][8] bf16, W3 [t][kg][n<8][8] bf16
+// (row 0 = s, row 1 = t, rows 2..7 zero), then FP32 W1s[t][c], b1, b2, b3.
 __global__ void repack_bf16_kernel(const float* __restrict__ canon, int64_t cstride, int n_layers,
                                    unsigned char* __restrict__ out) {
-    const int64_t per = kT * 4 * 32 * 8 + kF_N;
+    constexpr int n2 = kT * 4 * 32 * 8, n3 = kT * 4 * 8 * 8;
+    const int64_t per = n2 + n3 + kF_N;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < per * n_layers;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int l = (int)(i / per);
@@ -505,23 +509,23 @@ __global__ void repack_bf16_kernel(const float* __restrict__ canon, int64_t cstr
         const float* W3 = b2 + kC;              // [o][i][t]
         const float* b3 = W3 + 2 * kC * kT;
         unsigned char* blk = out + (size_t)l * kLayerBytes;
-        if (r < kT * 4 * 32 * 8) {
+        if (r < n2) {
             const int e = (int)(r & 7), n = (int)((r >> 3) & 31), kg = (int)((r >> 8) & 3), t = (int)(r >> 10);
             const float v = W2[((int64_t)n * kC + kg * 8 + e) * kT + t];
             reinterpret_cast<__nv_bfloat16*>(blk)[r] = __float2bfloat16_rn(v);
+        } else if (r < n2 + n3) {
+            const int r3 = (int)(r - n2);
+            const int e = r3 & 7, n = (r3 >> 3) & 7, kg = (r3 >> 6) & 3, t = r3 >> 8;
+            const float v = n < 2 ? W3[((int64_t)n * kC + kg * 8 + e) * kT + t] : 0.f;
+            reinterpret_cast<__nv_bfloat16*>(blk + kW2Bytes)[r3] = __float2bfloat16_rn(v);
         } else {
-            const int f = (int)(r - kT * 4 * 32 * 8);
+            const int f = (int)(r - n2 - n3);
             float v = 0.f;
             if (f < kF_b1) v = W1[(f % kC) * kT + f / kC];
             else if (f < kF_b2) v = b1[f - kF_b1];
-            else if (f < kF_W3) v = b2[f - kF_b2];
-            else if (f < kF_b3) {
-                const int g = f - kF_W3, t = g / (2 * kC), r = g % (2 * kC);
-                const int i = r >> 4, cgi = (r >> 2) & 3, e = r & 3;
-                const int c = cgi * 8 + 2 * i + (e >> 1), o = e & 1;
-                v = W3[((int64_t)o * kC + c) * kT + t];
-            } else if (f < kF_b3 + 2) v = b3[f - kF_b3];
-            reinterpret_cast<float*>(blk + kW2Bytes)[f] = v;
+            else if (f < kF_b3) v = b2[f - kF_b2];
+            else if (f < kF_b3 + 2) v = b3[f - kF_b3];
+            reinterpret_cast<float*>(blk + kW2Bytes + kW3Bytes)[f] = v;
         }
     }
 }
@@ -534,10 +538,6 @@ bool bf16_supported(const gf_flow_shape* s) {
 
 gf_status bf16_configure(gf_flow* f) {
     if (!bf16_supported(&f->shape)) return GF_EUNSUPPORTED;
-    // the BF16 kernel uses the one-slice ring schedule
-    f->full = false;
-    f->G = 1;
-    f->R = 3;
     f->smem_bytes_bf16 = kSmemBytes;
     if (cudaMalloc(&f->d_bf16, (size_t)kLayerBytes * std::max(1, f->shape.n_layers)) != cudaSuccess)
         return GF_ENOMEM;
@@ -545,7 +545,7 @@ gf_status bf16_configure(gf_flow* f) {
 }
 
 gf_status repack_bf16(gf_flow* f, cudaStream_t stream) {
-    const int64_t total = (int64_t)(kT * 4 * 32 * 8 + kF_N) * f->shape.n_layers;
+    const int64_t total = (int64_t)(kT * 4 * 32 * 8 + kT * 4 * 8 * 8 + kF_N) * f->shape.n_layers;
     const int grid = (int)std::min<int64_t>((total + 255) / 256, 4096);
     if (total == 0) return GF_OK;
     repack_bf16_kernel<<<grid, 256, 0, stream>>>(f->d_canon, f->canon_stride, f->shape.n_layers,
@@ -561,8 +561,6 @@ gf_status launch_flow_bf16(const gf_flow* f, bool inverse, const gf_phi4* phi4, 
     Bf16Args a;
     std::memset(&a, 0, sizeof(a));
     a.Wl = static_cast<const unsigned char*>(f->d_bf16);
-    a.sched = f->d_sched;
-    a.n_phases = f->n_phases;
     a.n_layers = f->shape.n_layers;
     a.slope = (float)f->shape.leaky_slope;
     a.use_tanh = f->shape.use_final_tanh;
