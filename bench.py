@@ -150,6 +150,76 @@ def barrier(world: int):
         dist.barrier()
 
 
+# --------------------------------------------------------------------------- training-step arm
+def bench_train(args, rank, world, local):
+    """One step = one reverse-KL training step (forward with saved layer inputs,
+    hand-written backward, Adam) on 2D L=32, 24 couplings, hidden 32, batch 1024."""
+    import torch
+    import paper_2208_08903_gb300 as P
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    W = gi.WORKLOADS["c2"]
+    shape, phi4, B = W["shape"], W["phi4"], args.batch or W["batch"]
+    flow = P.Flow(shape, gi.init_weights(shape, seed=0))
+    m = torch.zeros(flow.n_params, device=dev)
+    v = torch.zeros(flow.n_params, device=dev)
+    ws = torch.empty(flow.train_workspace_bytes(B), device=dev, dtype=torch.uint8)
+    loss = None
+    c0 = counter_base(rank)
+
+    def step(i):
+        nonlocal loss
+        loss, _ = flow.train_step(B, phi4, seed=12345, counter0=c0 + i * B, lr=1e-3, adam_m=m, adam_v=v,
+                                  adam_t=i + 1, workspace=ws, grad=False)
+
+    flush = torch.empty(2 * L2_BYTES // 4, device=dev, dtype=torch.float32)
+    barrier(world)
+    clocks = ClockSampler(local)
+    t = _time_steps(step, args.steps, args.warmup, flush)
+    clk = clocks.stop()
+    total_ms = max_over_ranks(sum(t), world)
+    # end to end: z from pinned host memory, loss back to the host, every step
+    z_host = torch.from_numpy(gi.random_field(2, shape.L, B, seed=5).astype(np.float32)).pin_memory()
+    z_dev = torch.empty(B, shape.V, device=dev)
+    loss_host = torch.empty(1, dtype=torch.float64).pin_memory()
+    stream = torch.cuda.current_stream()
+    e2e = []
+    for i in range(max(3, min(args.steps, 10)) + 1):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        z_dev.copy_(z_host, non_blocking=True)
+        lo, _ = flow.train_step(B, phi4, z=z_dev, lr=1e-3, adam_m=m, adam_v=v, adam_t=args.warmup + args.steps + i + 1,
+                                workspace=ws, grad=False)
+        loss_host.copy_(lo, non_blocking=True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if i > 0:
+            e2e.append(a.elapsed_time(b))
+    e2e_total = max_over_ranks(sum(e2e), world)
+    fl = 4 * flops_per_config(shape) * B
+    pk, pk_kind = peaks()
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = fp32_alu_peak_tflops(n_sm, pk.get("sm_max_mhz", 2070.0))
+    ach = fl / (float(np.mean(t)) / 1e3) / 1e12
+    return {"metric": "train steps/s (reverse-KL step: forward + backward + Adam)",
+            "value": world * args.steps / (total_ms / 1e3), "unit": "steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded Philox prior, random-init weights seed 0)",
+            "config": {"workload": "c2: 2D L=32 m2=-4 lam=8, 24 couplings, hidden 32, batch 1024, Adam lr 1e-3",
+                       "batch": B, "l2": "flushed between timed steps"},
+            "e2e": {"value": world * len(e2e) / (e2e_total / 1e3), "unit": "steps/s",
+                    "h2d_bytes_per_step": B * shape.V * 4, "d2h_bytes_per_step": 8},
+            # per step: prior + reverse-pass weight packing, 3 per layer forward, loss + mean,
+            # 13 per layer backward, Adam + repack
+            "gpu_launches": args.steps * (16 * shape.n_layers + 6),
+            "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                         "traffic": None, "note": "algorithmic FLOP = 4 x forward (forward, recompute, "
+                                                  "data and weight gradients)"},
+            "clocks": clk, "loss": float(loss.item())}
+
+
 # --------------------------------------------------------------------------- GPU arm
 def bench_gpu(args, rank, world, local):
     import torch
@@ -492,7 +562,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gfflow", choices=["gfflow", "reference"])
-    ap.add_argument("--workload", default="c3", choices=["c1", "c3"])
+    ap.add_argument("--workload", default="c3", choices=["c1", "c2", "c3"])
     ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "bf16"])
     ap.add_argument("--batch", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -506,6 +576,11 @@ def main():
     rank, world, local = dist_setup(args.gpus)
     if args.impl == "reference":
         res = bench_reference(args, rank, world)
+        if rank == 0:
+            print(json.dumps(res), flush=True)
+        return
+    if args.workload == "c2":
+        res = bench_train(args, rank, world, local)
         if rank == 0:
             print(json.dumps(res), flush=True)
         return

@@ -14,7 +14,9 @@
 //   conv2 as an implicit GEMM on the tensor cores -> h2 slice (BF16)
 //   conv3 as an implicit GEMM (N = 16, rows s and t) -> affine update of x
 // Implicit GEMM: per z-slice two M = 128 tiles (8 y-rows x 16 x); K = the 9
-// (dz,dy) taps x 32 channels in steps of 16.  Activations are stored channel-
+// (dz,dy) taps x 32 channels in steps of 16; the three dx weight sets are
+// stacked along N (conv2: N = 96, conv3: N = 32), so one instruction yields
+// the three dx partial sums.  Activations are stored channel-
 // group major ([4][288 sites][8 ch], 288 = 18 y-rows with one periodic halo row
 // on each side), so each 8-site core matrix is 128 contiguous bytes and a
 // (dz,dy) shift is only a different start address.  The periodic x-shift is
@@ -41,15 +43,17 @@ constexpr int kL = 16, kS = 256, kC = 32, kT = 27;
 constexpr int kHaloSites = 18 * 16;                    // y = -1 .. 16
 constexpr int kCgStride = kHaloSites * 16;             // bytes between channel groups
 constexpr int kSlotBytes = 4 * kCgStride;              // [cg][site][8] bf16 = 18432
-constexpr int kW2Bytes = kT * 4 * 32 * 16;             // [t][kg][n][8] bf16 = 55296
-constexpr int kW3Bytes = kT * 4 * 8 * 16;              // [t][kg][n<8][8] bf16 = 13824 (rows s, t, zeros)
+// conv2 B operand per (dz,dy) tap pair: the three dx weight sets stacked along N
+// (N = 96: row dxi*32 + o); conv3 B: rows dxi*8 + {s, t, 6 zeros} for dxi < 3 and
+// 8 zero rows (N = 32).  Layout [tap9][kg][n][8] bf16 (K-major core matrices).
+constexpr int kW2Bytes = 9 * 4 * 96 * 16;              // 55296
+constexpr int kW3Bytes = 9 * 4 * 32 * 16;              // 18432
 // FP32 part of a layer block (floats): W1s[t][c], b1[c], b2[c], b3[2], pad
 constexpr int kF_W1 = 0, kF_b1 = kT * kC, kF_b2 = kF_b1 + kC, kF_b3 = kF_b2 + kC;
 constexpr int kF_N = (kF_b3 + 2 + 3) & ~3;
 constexpr int kLayerBytes = kW2Bytes + kW3Bytes + kF_N * 4;
-constexpr int kZeroBytes = 256;                         // two zero core matrices (B rows 8..15 of conv3)
 constexpr int kTmem3 = 192;                             // conv3 accumulators start here
-constexpr int kTmemCols = 512;                          // conv2: 2 x 3 x 32, conv3: 2 x 3 x 16
+constexpr int kTmemCols = 256;                          // conv2: 2 tiles x 96, conv3: 2 tiles x 32
 constexpr long long kWaitLimit = 1ll << 22;             // bounded mbarrier wait (iterations)
 
 // ---------------------------------------------------------------- PTX wrappers
@@ -134,9 +138,9 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
     d |= (uint64_t)1 << 46;              // descriptor version for tcgen05
     return d;                            // base offset 0, swizzle mode 0 (none)
 }
-// Instruction descriptors: D = F32, A = B = BF16, both K-major, M = 128, N = 32 / 16.
+// Instruction descriptors: D = F32, A = B = BF16, both K-major, M = 128, N = 96 / 32.
+constexpr uint32_t kIdesc96 = (1u << 4) | (1u << 7) | (1u << 10) | ((96u >> 3) << 17) | ((128u >> 4) << 24);
 constexpr uint32_t kIdesc32 = (1u << 4) | (1u << 7) | (1u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
-constexpr uint32_t kIdesc16 = (1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
 
 struct Bf16Args {
     const unsigned char* Wl;   // per-layer blocks of kLayerBytes
@@ -218,28 +222,25 @@ __device__ __forceinline__ void conv1_slice(unsigned char* h1, int v, const floa
     }
 }
 
-// One elected thread: an implicit-GEMM convolution of a slice.  For each of
-// the 2 M-tiles and 3 dx accumulators (N columns each, from TMEM column d0):
-// 9 (dz,dy) taps x 2 K-steps of tcgen05.mma.  a_slot[dzi] = A descriptors of
-// the three input slices; the B descriptor of tap t, K-step k is
-// bdesc(t, k) (a functor, so conv3 can give each one its own SBO).
-template <int N, typename BDesc>
-__device__ __forceinline__ void issue_conv(const uint64_t (&a_slot)[3], BDesc bdesc, uint32_t d0, uint32_t idesc) {
+// One elected thread: an implicit-GEMM convolution of a slice: for each of the
+// 2 M-tiles, 9 (dz,dy) taps x 2 K-steps of tcgen05.mma, each producing the three
+// dx partial sums at once (B holds the dx weight sets stacked along N).
+// a_slot[dzi] = A descriptors of the three input slices; b0 = B descriptor of
+// tap pair 0, K-step 0; tap pair p, K-step k adds p * b_tap + k * b_k (16-byte units).
+__device__ __forceinline__ void issue_conv(const uint64_t (&a_slot)[3], uint64_t b0, uint32_t b_tap, uint32_t b_k,
+                                           uint32_t d0, uint32_t d_tile, uint32_t idesc) {
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt) {
+        const uint32_t d = d0 + (uint32_t)mt * d_tile;
 #pragma unroll
-        for (int dxi = 0; dxi < 3; ++dxi) {
-            const uint32_t d = d0 + (uint32_t)((mt * 3 + dxi) * N);
+        for (int dzi = 0; dzi < 3; ++dzi) {
 #pragma unroll
-            for (int dzi = 0; dzi < 3; ++dzi) {
+            for (int dyi = 0; dyi < 3; ++dyi) {
 #pragma unroll
-                for (int dyi = 0; dyi < 3; ++dyi) {
-                    const int t = (dzi * 3 + dyi) * 3 + dxi;
-#pragma unroll
-                    for (int k = 0; k < 2; ++k) {
-                        const uint64_t ad = a_slot[dzi] + (uint64_t)((2 * k * kCgStride + (mt * 8 + dyi) * 256) >> 4);
-                        mma_bf16(d, ad, bdesc(t, k), idesc, (dzi | dyi | k) ? 1u : 0u);
-                    }
+                for (int k = 0; k < 2; ++k) {
+                    const uint64_t ad = a_slot[dzi] + (uint64_t)((2 * k * kCgStride + (mt * 8 + dyi) * 256) >> 4);
+                    const uint64_t bd = b0 + (uint64_t)((dzi * 3 + dyi) * b_tap + k * b_k);
+                    mma_bf16(d, ad, bd, idesc, (dzi | dyi | k) ? 1u : 0u);
                 }
             }
         }
@@ -282,9 +283,9 @@ __device__ __forceinline__ void conv3_epilogue(uint32_t tmem, int z, const float
     const int y = mt * 8 + q * 2 + (lane >> 4), xx = lane & 15;
     const uint32_t lane_base = (uint32_t)(q * 32) << 16;
     float sm, tm, s0, t0, sp, tp;
-    tmem_ld2(tmem + lane_base + (uint32_t)(kTmem3 + (mt * 3 + 0) * 16), sm, tm);
-    tmem_ld2(tmem + lane_base + (uint32_t)(kTmem3 + (mt * 3 + 1) * 16), s0, t0);
-    tmem_ld2(tmem + lane_base + (uint32_t)(kTmem3 + (mt * 3 + 2) * 16), sp, tp);
+    tmem_ld2(tmem + lane_base + (uint32_t)(kTmem3 + mt * 32 + 0), sm, tm);
+    tmem_ld2(tmem + lane_base + (uint32_t)(kTmem3 + mt * 32 + 8), s0, t0);
+    tmem_ld2(tmem + lane_base + (uint32_t)(kTmem3 + mt * 32 + 16), sp, tp);
     tmem_ld_wait();
     const int src_m = (lane & 16) | ((xx + 15) & 15);
     const int src_p = (lane & 16) | ((xx + 1) & 15);
@@ -316,8 +317,7 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
     unsigned char* w2s = smem;                                                 // kW2Bytes
     unsigned char* w3s = smem + kW2Bytes;                                      // kW3Bytes
     float* wf = reinterpret_cast<float*>(smem + kW2Bytes + kW3Bytes);          // kF_N floats
-    unsigned char* zero = smem + kLayerBytes;                                  // kZeroBytes
-    unsigned char* h1 = zero + kZeroBytes;                                     // 4 slots
+    unsigned char* h1 = smem + kLayerBytes;                                    // 4 slots
     unsigned char* h2 = h1 + 4 * kSlotBytes;                                   // 3 slots
     float* x = reinterpret_cast<float*>(h2 + 3 * kSlotBytes);                  // 4096 floats
     double* red = reinterpret_cast<double*>(x + 4096);                         // 32
@@ -338,8 +338,6 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    for (int i = tid; i < kZeroBytes / 16; i += kThreads) reinterpret_cast<uint4*>(zero)[i] = make_uint4(0, 0, 0, 0);
-    fence_proxy_async();
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
@@ -347,20 +345,13 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
     uint32_t ph2 = 0, ph3 = 0;
 
     // A descriptors of every h1 / h2 slot (LBO = channel-group stride, SBO = 8 sites);
-    // conv2 B: LBO = 512 between K groups, SBO = 128 between 8-row N groups;
-    // conv3 B: LBO = 128, and its second 8-row N group (rows 8..15) is read from the
-    // zero block, so its SBO is (zero block - start) for each (tap, K-step).
+    // B: conv2 LBO = 96 rows x 16 B between K groups, conv3 LBO = 32 rows x 16 B, SBO = 128.
     const uint64_t a1_0 = smem_desc(smem_u32(h1), kCgStride, 128);
     const uint64_t a2_0 = smem_desc(smem_u32(h2), kCgStride, 128);
     const auto a1 = [a1_0](int slot) { return a1_0 + (uint64_t)(slot * (kSlotBytes >> 4)); };
     const auto a2 = [a2_0](int slot) { return a2_0 + (uint64_t)(slot * (kSlotBytes >> 4)); };
-    const uint64_t b2d = smem_desc(smem_u32(w2s), 512, 128);
-    const uint32_t w3a = smem_u32(w3s), za = smem_u32(zero);
-    const auto bdesc2 = [b2d](int t, int k) { return b2d + (uint64_t)((t * 2048 + k * 1024) >> 4); };
-    const auto bdesc3 = [w3a, za](int t, int k) {
-        const uint32_t start = w3a + (uint32_t)(t * 512 + k * 256);
-        return smem_desc(start, 128, za - start);
-    };
+    const uint64_t b2d = smem_desc(smem_u32(w2s), 96 * 16, 128);
+    const uint64_t b3d = smem_desc(smem_u32(w3s), 32 * 16, 128);
 
     for (int64_t b = blockIdx.x; b < a.B; b += gridDim.x) {
         double sumz2 = 0.0;
@@ -412,12 +403,12 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
                     fence_after_sync();
                     if (do3) {
                         const uint64_t as[3] = {a2(h2_slot(v - 3)), a2(h2_slot(v - 2)), a2(h2_slot(v - 1))};
-                        issue_conv<16>(as, bdesc3, tmem + kTmem3, kIdesc16);
+                        issue_conv(as, b3d, (4 * 32 * 16) >> 4, (2 * 32 * 16) >> 4, tmem + kTmem3, 32, kIdesc32);
                         mma_commit(bar3);
                     }
                     if (do2) {
                         const uint64_t as[3] = {a1(h1_slot(v - 1)), a1(h1_slot(v)), a1(h1_slot(v + 1))};
-                        issue_conv<32>(as, bdesc2, tmem, kIdesc32);
+                        issue_conv(as, b2d, (4 * 96 * 16) >> 4, (2 * 96 * 16) >> 4, tmem, 96, kIdesc96);
                         mma_commit(bar2);
                     }
                 }
@@ -488,14 +479,15 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
     }
 }
 
-constexpr size_t kSmemBytes = (size_t)kLayerBytes + kZeroBytes + 7 * (size_t)kSlotBytes + 4096 * 4 + 32 * 8 +
+constexpr size_t kSmemBytes = (size_t)kLayerBytes + 7 * (size_t)kSlotBytes + 4096 * 4 + 32 * 8 +
                               2 * 8 + 4 + 4;
 
-// canonical FP32 -> per-layer block: W2 [t][kg][n][8] bf16, W3 [t][kg][n<8][8] bf16
-// (row 0 = s, row 1 = t, rows 2..7 zero), then FP32 W1s[t][c], b1, b2, b3.
+// canonical FP32 -> per-layer block: W2 [tap9][kg][dxi*32 + o][8] bf16,
+// W3 [tap9][kg][dxi*8 + j][8] bf16 (j = 0: s, 1: t, else 0; rows 24..31 zero),
+// then FP32 W1s[t][c], b1, b2, b3.
 __global__ void repack_bf16_kernel(const float* __restrict__ canon, int64_t cstride, int n_layers,
                                    unsigned char* __restrict__ out) {
-    constexpr int n2 = kT * 4 * 32 * 8, n3 = kT * 4 * 8 * 8;
+    constexpr int n2 = 9 * 4 * 96 * 8, n3 = 9 * 4 * 32 * 8;
     const int64_t per = n2 + n3 + kF_N;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < per * n_layers;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -510,13 +502,15 @@ __global__ void repack_bf16_kernel(const float* __restrict__ canon, int64_t cstr
         const float* b3 = W3 + 2 * kC * kT;
         unsigned char* blk = out + (size_t)l * kLayerBytes;
         if (r < n2) {
-            const int e = (int)(r & 7), n = (int)((r >> 3) & 31), kg = (int)((r >> 8) & 3), t = (int)(r >> 10);
-            const float v = W2[((int64_t)n * kC + kg * 8 + e) * kT + t];
+            const int e = (int)(r & 7), row = (int)((r >> 3) % 96), kg = (int)((r / 768) & 3), tp = (int)(r / 3072);
+            const int dxi = row >> 5, o = row & 31, t = tp * 3 + dxi;
+            const float v = W2[((int64_t)o * kC + kg * 8 + e) * kT + t];
             reinterpret_cast<__nv_bfloat16*>(blk)[r] = __float2bfloat16_rn(v);
         } else if (r < n2 + n3) {
             const int r3 = (int)(r - n2);
-            const int e = r3 & 7, n = (r3 >> 3) & 7, kg = (r3 >> 6) & 3, t = r3 >> 8;
-            const float v = n < 2 ? W3[((int64_t)n * kC + kg * 8 + e) * kT + t] : 0.f;
+            const int e = r3 & 7, row = (r3 >> 3) & 31, kg = (r3 >> 8) & 3, tp = r3 >> 10;
+            const int dxi = row >> 3, j = row & 7, t = tp * 3 + dxi;
+            const float v = (dxi < 3 && j < 2) ? W3[((int64_t)j * kC + kg * 8 + e) * kT + t] : 0.f;
             reinterpret_cast<__nv_bfloat16*>(blk + kW2Bytes)[r3] = __float2bfloat16_rn(v);
         } else {
             const int f = (int)(r - n2 - n3);
@@ -545,7 +539,7 @@ gf_status bf16_configure(gf_flow* f) {
 }
 
 gf_status repack_bf16(gf_flow* f, cudaStream_t stream) {
-    const int64_t total = (int64_t)(kT * 4 * 32 * 8 + kT * 4 * 8 * 8 + kF_N) * f->shape.n_layers;
+    const int64_t total = (int64_t)(9 * 4 * 96 * 8 + 9 * 4 * 32 * 8 + kF_N) * f->shape.n_layers;
     const int grid = (int)std::min<int64_t>((total + 255) / 256, 4096);
     if (total == 0) return GF_OK;
     repack_bf16_kernel<<<grid, 256, 0, stream>>>(f->d_canon, f->canon_stride, f->shape.n_layers,

@@ -20,7 +20,7 @@ import gf_inputs as gi
 from gpu_util import assert_logw_close, assert_sites_close, require_gpu
 
 pytestmark = pytest.mark.gpu
-BF16_MODE = 1 | 2 | 4 | 32          # H1 | W2 | H2 | FP32 prior
+BF16_MODE = 1 | 2 | 4 | 8 | 32      # H1 | W2 | H2 | W3 | FP32 prior
 RTOL = 2.0**-7                      # per site
 LW_RTOL = 1e-3                      # per log-weight
 
