@@ -23,10 +23,11 @@
 // not gathered: three accumulators P_dx (dx = -1, 0, +1) stay in TMEM and the
 // epilogues form out(x) = sum_dx P_dx(x + dx) with width-16 shuffles (one
 // x-row = one half-warp = 16 TMEM lanes).
-// Pipeline, per virtual slice v: one thread issues conv3 of slice v-2 and
-// conv2 of slice v; meanwhile all warps run conv1 of slice v+2 on the FMA
-// pipes; then the conv3 epilogue updates slice v-2 and the conv2 epilogue
-// writes h2[v].
+// Pipeline, per virtual slice v: one thread issues conv3 of slice v-2; all
+// warps run conv1 of slice v+2 on the FMA pipes; the thread then queues conv2
+// of slice v+1 into the other of two TMEM buffers, so the tensor cores stay
+// busy while the conv3 epilogue updates slice v-2 and the conv2 epilogue
+// (issued one iteration earlier) writes h2[v].
 #include <algorithm>
 #include <cstring>
 
@@ -52,8 +53,9 @@ constexpr int kW3Bytes = 9 * 4 * 32 * 16;              // 18432
 constexpr int kF_W1 = 0, kF_b1 = kT * kC, kF_b2 = kF_b1 + kC, kF_b3 = kF_b2 + kC;
 constexpr int kF_N = (kF_b3 + 2 + 3) & ~3;
 constexpr int kLayerBytes = kW2Bytes + kW3Bytes + kF_N * 4;
-constexpr int kTmem3 = 192;                             // conv3 accumulators start here
-constexpr int kTmemCols = 256;                          // conv2: 2 tiles x 96, conv3: 2 tiles x 32
+constexpr int kTmem3 = 192;                             // conv3 accumulators (2 tiles x 32 columns)
+constexpr int kTmem2B = 256;                            // second conv2 buffer (2 tiles x 96 columns)
+constexpr int kTmemCols = 512;
 constexpr long long kWaitLimit = 1ll << 22;             // bounded mbarrier wait (iterations)
 
 // ---------------------------------------------------------------- PTX wrappers
@@ -321,8 +323,8 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
     unsigned char* h2 = h1 + 4 * kSlotBytes;                                   // 3 slots
     float* x = reinterpret_cast<float*>(h2 + 3 * kSlotBytes);                  // 4096 floats
     double* red = reinterpret_cast<double*>(x + 4096);                         // 32
-    uint64_t* bar2 = reinterpret_cast<uint64_t*>(red + 32);
-    uint64_t* bar3 = bar2 + 1;
+    uint64_t* bar2 = reinterpret_cast<uint64_t*>(red + 32);   // one per conv2 TMEM buffer
+    uint64_t* bar3 = bar2 + 2;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar3 + 1);
     int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
 
@@ -334,6 +336,7 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
     }
     if (tid == 0) {
         mbar_init(bar2, 1);
+        mbar_init(bar2 + 1, 1);
         mbar_init(bar3, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -342,7 +345,7 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
     __syncthreads();
     fence_after_sync();
     const uint32_t tmem = *tmem_slot;
-    uint32_t ph2 = 0, ph3 = 0;
+    uint32_t ph2a = 0, ph2b = 0, ph3 = 0;      // phase bits of the two conv2 barriers and conv3
 
     // A descriptors of every h1 / h2 slot (LBO = channel-group stride, SBO = 8 sites);
     // B: conv2 LBO = 96 rows x 16 B between K groups, conv3 LBO = 32 rows x 16 B, SBO = 128.
@@ -391,40 +394,52 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
             }
             fence_proxy_async();
             __syncthreads();
-            // prologue: h1 of virtual slices -2, -1, 0
+            // prologue: h1 of virtual slices -2, -1, 0, and conv2 of h2[-1] into TMEM buffer 1
             for (int v = -2; v <= 0; ++v) conv1_slice(h1, v, wf, x, frozen, a.slope, tid);
             fence_proxy_async();
             __syncthreads();
-            // v = -1 .. L+1: conv2 of h2[v] (v <= L), conv3 + update of slice v-2 (v >= 2),
-            // conv1 of h1[v+2] (v+2 <= L+1) on the FMA pipes meanwhile.
+            if (tid == 0) {
+                fence_after_sync();
+                const uint64_t as[3] = {a1(h1_slot(-2)), a1(h1_slot(-1)), a1(h1_slot(0))};
+                issue_conv(as, b2d, (4 * 96 * 16) >> 4, (2 * 96 * 16) >> 4, tmem + kTmem2B, 96, kIdesc96);
+                mma_commit(bar2 + 1);
+            }
+            // v = -1 .. L+1.  Tensor-core queue per iteration: conv3 of slice v-2 (v >= 2), then
+            // conv2 of h2[v+1] (v+1 <= L) into TMEM buffer (v+1)&1, issued before the epilogues
+            // of this iteration so the tensor cores never wait for them; FMA pipes: conv1 of
+            // h1[v+2]; then the conv3 epilogue (update of slice v-2) and the conv2 epilogue of
+            // h2[v] (buffer v&1, issued one iteration earlier).
             for (int v = -1; v <= kL + 1; ++v) {
-                const bool do2 = v <= kL, do3 = v >= 2;
-                if (tid == 0) {
+                const bool do3 = v >= 2, do2 = v <= kL, next2 = v + 1 <= kL;
+                if (tid == 0 && do3) {
                     fence_after_sync();
-                    if (do3) {
-                        const uint64_t as[3] = {a2(h2_slot(v - 3)), a2(h2_slot(v - 2)), a2(h2_slot(v - 1))};
-                        issue_conv(as, b3d, (4 * 32 * 16) >> 4, (2 * 32 * 16) >> 4, tmem + kTmem3, 32, kIdesc32);
-                        mma_commit(bar3);
-                    }
-                    if (do2) {
-                        const uint64_t as[3] = {a1(h1_slot(v - 1)), a1(h1_slot(v)), a1(h1_slot(v + 1))};
-                        issue_conv(as, b2d, (4 * 96 * 16) >> 4, (2 * 96 * 16) >> 4, tmem, 96, kIdesc96);
-                        mma_commit(bar2);
-                    }
+                    const uint64_t as[3] = {a2(h2_slot(v - 3)), a2(h2_slot(v - 2)), a2(h2_slot(v - 1))};
+                    issue_conv(as, b3d, (4 * 32 * 16) >> 4, (2 * 32 * 16) >> 4, tmem + kTmem3, 32, kIdesc32);
+                    mma_commit(bar3);
                 }
                 if (v + 2 <= kL + 1) {
                     conv1_slice(h1, v + 2, wf, x, frozen, a.slope, tid);
                     fence_proxy_async();
                 }
                 __syncthreads();
+                if (tid == 0 && next2) {
+                    fence_after_sync();
+                    const int bn = (v + 1) & 1;
+                    const uint64_t as[3] = {a1(h1_slot(v)), a1(h1_slot(v + 1)), a1(h1_slot(v + 2))};
+                    issue_conv(as, b2d, (4 * 96 * 16) >> 4, (2 * 96 * 16) >> 4, tmem + (bn ? kTmem2B : 0u), 96,
+                               kIdesc96);
+                    mma_commit(bar2 + bn);
+                }
                 if (do3) {
                     // conv3 of slice v-2 has finished reading all three h2 slots after this wait
                     wait_bar(bar3, ph3, abort_flag, a.status);
                     conv3_epilogue(tmem, slice_of(v - 2), wf, x, frozen, a.use_tanh, INVERSE, logdet, warp, lane);
                 }
                 if (do2) {
-                    wait_bar(bar2, ph2, abort_flag, a.status);
-                    conv2_epilogue(h2, tmem, v, wf, a.slope, warp, lane);
+                    const int bc = v & 1;
+                    if (bc) wait_bar(bar2 + 1, ph2b, abort_flag, a.status);
+                    else wait_bar(bar2, ph2a, abort_flag, a.status);
+                    conv2_epilogue(h2, tmem + (bc ? kTmem2B : 0u), v, wf, a.slope, warp, lane);
                     fence_proxy_async();
                 }
                 fence_before_sync();
@@ -480,7 +495,7 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
 }
 
 constexpr size_t kSmemBytes = (size_t)kLayerBytes + 7 * (size_t)kSlotBytes + 4096 * 4 + 32 * 8 +
-                              2 * 8 + 4 + 4;
+                              3 * 8 + 4 + 4;
 
 // canonical FP32 -> per-layer block: W2 [tap9][kg][dxi*32 + o][8] bf16,
 // W3 [tap9][kg][dxi*8 + j][8] bf16 (j = 0: s, 1: t, else 0; rows 24..31 zero),

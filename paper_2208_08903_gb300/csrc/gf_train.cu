@@ -275,11 +275,13 @@ struct WgArgs {
 };
 
 template <int ND, int IB, int OB>
-__global__ void k_wgrad(const WgArgs a) {
+__global__ void k_wgrad(const WgArgs a, int nsplit) {
+    // Thread = (task, split): the nsplit lanes of a task (adjacent lanes of one
+    // warp) take every nsplit-th site and are combined by a fixed shuffle tree.
     const int T = ND == 3 ? 27 : 9;
     const int nic = a.Cin / IB, noc = a.Cout / OB;
     const int tasks = (T + 1) * nic * noc;
-    const int task = threadIdx.x;
+    const int task = threadIdx.x / nsplit, split = threadIdx.x % nsplit;
     const bool active = task < tasks;
     const int oc = active ? task % noc : 0;
     const int ic = active ? (task / noc) % nic : 0;
@@ -294,7 +296,7 @@ __global__ void k_wgrad(const WgArgs a) {
         for (int64_t b = blockIdx.x; b < a.B; b += gridDim.x) {
             const float* inb = a.in + b * (int64_t)a.V * a.Cin;
             const float* gb = a.gout + b * (int64_t)a.V * a.Cout;
-            for (int n = 0; n < a.V; ++n) {
+            for (int n = split; n < a.V; n += nsplit) {
                 float iv[IB];
                 if (bias) {
 #pragma unroll
@@ -329,7 +331,13 @@ __global__ void k_wgrad(const WgArgs a) {
             }
         }
     }
-    if (active) {
+    // combine the nsplit lanes of each task (fixed order: deterministic)
+    for (int off = 1; off < nsplit; off <<= 1)
+#pragma unroll
+        for (int i = 0; i < IB; ++i)
+#pragma unroll
+            for (int o = 0; o < OB; ++o) acc[i][o] += __shfl_xor_sync(0xffffffffu, acc[i][o], off);
+    if (active && split == 0) {
         float* P = a.partial + (int64_t)blockIdx.x * (T + 1) * a.Cin * a.Cout;
 #pragma unroll
         for (int i = 0; i < IB; ++i)
@@ -527,17 +535,16 @@ template <int ND>
 gf_status wgrad(const WgArgs& a, float* gW, float* gbias, float scale, cudaStream_t st) {
     const int T = ND == 3 ? 27 : 9;
     const int grid = (int)std::min<int64_t>(a.B, wgrad_grid());
-    int threads;
-    if (a.Cin == 1) {
-        threads = (T + 1) * (a.Cout / 8);
-        k_wgrad<ND, 1, 8><<<grid, (threads + 31) / 32 * 32, 0, st>>>(a);
-    } else if (a.Cout == 2) {
-        threads = (T + 1) * (a.Cin / 4);
-        k_wgrad<ND, 4, 2><<<grid, (threads + 31) / 32 * 32, 0, st>>>(a);
-    } else {
-        threads = (T + 1) * (a.Cin / 4) * (a.Cout / 8);
-        k_wgrad<ND, 4, 8><<<grid, (threads + 31) / 32 * 32, 0, st>>>(a);
-    }
+    // lanes per task: enough threads per CTA for the small (conv1, conv3) gradients
+    auto launch = [&](auto kern, int tasks) {
+        int nsplit = 1;
+        while (nsplit < 8 && tasks * nsplit * 2 <= 512) nsplit *= 2;
+        const int threads = (tasks * nsplit + 31) / 32 * 32;
+        kern<<<grid, threads, 0, st>>>(a, nsplit);
+    };
+    if (a.Cin == 1) launch(k_wgrad<ND, 1, 8>, (T + 1) * (a.Cout / 8));
+    else if (a.Cout == 2) launch(k_wgrad<ND, 4, 2>, (T + 1) * (a.Cin / 4));
+    else launch(k_wgrad<ND, 4, 8>, (T + 1) * (a.Cin / 4) * (a.Cout / 8));
     GF_CHECK_LAUNCH();
     const int per = (T + 1) * a.Cin * a.Cout;
     k_wgrad_reduce<<<(per + 255) / 256, 256, 0, st>>>(a.partial, grid, T, a.Cin, a.Cout, scale, gW, gbias);
