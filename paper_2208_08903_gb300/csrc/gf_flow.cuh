@@ -51,6 +51,7 @@ struct gf_flow {
     int R;                  // slots per hidden tensor
     bool full;
     size_t smem_bytes;
+    bool wsmem;             // FP32 kernel keeps all packed weights in shared memory
     // BF16 tensor-core path (3D, C=32)
     void* d_bf16;           // packed bf16 conv2 weights and FP32 head weights
     size_t smem_bytes_bf16;

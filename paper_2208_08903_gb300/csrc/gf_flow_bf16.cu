@@ -39,7 +39,7 @@ namespace gf {
 
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;
 constexpr int kL = 16, kS = 256, kC = 32, kT = 27;
 constexpr int kHaloSites = 18 * 16;                    // y = -1 .. 16
 constexpr int kCgStride = kHaloSites * 16;             // bytes between channel groups
@@ -117,6 +117,18 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 #pragma unroll
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
+// 32 lanes x 16 consecutive FP32 columns.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                   "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                   "=r"(r[14]), "=r"(r[15])
+                 : "r"(taddr) : "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
 // 32 lanes x 2 consecutive FP32 columns.
 __device__ __forceinline__ void tmem_ld2(uint32_t taddr, float& a, float& b) {
     uint32_t r0, r1;
@@ -181,12 +193,31 @@ __device__ __forceinline__ int slice_of(int v) { return v & 15; }
 __device__ __forceinline__ int h1_slot(int v) { return (v + 16) & 3; }
 __device__ __forceinline__ int h2_slot(int v) { return (v + 15) % 3; }
 
+// The taps of conv1 that reach fixed sites from an output site of parity p are
+// those whose offset parity (|dz|+|dy|+|dx|) mod 2 equals NEED = frozen ^ p; the
+// tap set is chosen at compile time, so the loop has no branches.
+template <int NEED>
+__device__ __forceinline__ void conv1_taps(float (&acc)[8], const float* wf, const float* x, const int (&zr)[3],
+                                           const int (&yr)[3], const int (&xc)[3], int cg) {
+#pragma unroll
+    for (int t = 0; t < kT; ++t) {
+        const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;
+        if (((dz + dy + dx + 1) & 1) != NEED) continue;                     // resolved at compile time
+        const float xv = x[zr[dz] + yr[dy] + xc[dx]];
+        const float4 w0 = *reinterpret_cast<const float4*>(wf + kF_W1 + t * kC + cg * 8);
+        const float4 w1 = *reinterpret_cast<const float4*>(wf + kF_W1 + t * kC + cg * 8 + 4);
+        acc[0] = fmaf(xv, w0.x, acc[0]); acc[1] = fmaf(xv, w0.y, acc[1]);
+        acc[2] = fmaf(xv, w0.z, acc[2]); acc[3] = fmaf(xv, w0.w, acc[3]);
+        acc[4] = fmaf(xv, w1.x, acc[4]); acc[5] = fmaf(xv, w1.y, acc[5]);
+        acc[6] = fmaf(xv, w1.z, acc[6]); acc[7] = fmaf(xv, w1.w, acc[7]);
+    }
+}
+
 // conv1 + LReLU of virtual slice v into its h1 slot (BF16).  Work items:
 // (channel group, site parity class, 128 sites of that class); a warp holds
-// sites of one parity, so every lane takes the same 13 or 14 taps (those whose
-// neighbour has the fixed parity), selected by a warp-uniform test on a
-// compile-time tap offset.  Neighbouring lanes alternate between rows y and
-// y+1, which keeps the 16-byte stores free of bank conflicts.
+// sites of one parity, so all its lanes take the same 13 or 14 taps.
+// Neighbouring lanes alternate between rows y and y+1, which keeps the
+// 16-byte stores free of bank conflicts.
 __device__ __forceinline__ void conv1_slice(unsigned char* h1, int v, const float* wf, const float* x, int frozen,
                                             float slope, int tid) {
     const int z = slice_of(v);
@@ -195,7 +226,6 @@ __device__ __forceinline__ void conv1_slice(unsigned char* h1, int v, const floa
     for (int it = tid; it < kS * 4; it += kThreads) {
         const int cg = it >> 8, rest = it & 255, pcls = rest >> 7, k = rest & 127;
         const int y = 2 * (k >> 4) + (k & 1), xx = 2 * ((k >> 1) & 7) + ((pcls ^ z ^ y) & 1);  // parity pcls
-        const int need = (frozen ^ pcls) & 1;                              // tap parity reaching fixed sites
         int zr[3], yr[3], xc[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
@@ -206,18 +236,8 @@ __device__ __forceinline__ void conv1_slice(unsigned char* h1, int v, const floa
         const float4 b0 = *reinterpret_cast<const float4*>(wf + kF_b1 + cg * 8);
         const float4 b1 = *reinterpret_cast<const float4*>(wf + kF_b1 + cg * 8 + 4);
         float acc[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
-        for (int t = 0; t < kT; ++t) {
-            const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;             // compile-time after unrolling
-            if (((dz + dy + dx + 1) & 1) != need) continue;                 // |offset| parity, warp-uniform
-            const float xv = x[zr[dz] + yr[dy] + xc[dx]];
-            const float4 w0 = *reinterpret_cast<const float4*>(wf + kF_W1 + t * kC + cg * 8);
-            const float4 w1 = *reinterpret_cast<const float4*>(wf + kF_W1 + t * kC + cg * 8 + 4);
-            acc[0] = fmaf(xv, w0.x, acc[0]); acc[1] = fmaf(xv, w0.y, acc[1]);
-            acc[2] = fmaf(xv, w0.z, acc[2]); acc[3] = fmaf(xv, w0.w, acc[3]);
-            acc[4] = fmaf(xv, w1.x, acc[4]); acc[5] = fmaf(xv, w1.y, acc[5]);
-            acc[6] = fmaf(xv, w1.z, acc[6]); acc[7] = fmaf(xv, w1.w, acc[7]);
-        }
+        if ((frozen ^ pcls) & 1) conv1_taps<1>(acc, wf, x, zr, yr, xc, cg);
+        else conv1_taps<0>(acc, wf, x, zr, yr, xc, cg);
 #pragma unroll
         for (int c = 0; c < 8; ++c) acc[c] = acc[c] > 0.f ? acc[c] : slope * acc[c];
         store8(slot, cg, y, xx, acc);
@@ -249,31 +269,36 @@ __device__ __forceinline__ void issue_conv(const uint64_t (&a_slot)[3], uint64_t
     }
 }
 
-// conv2 epilogue: out(x) = sum_dx P_dx(x + dx) + b2, LReLU, BF16 into the h2 slot of v.
+// conv2 epilogue: out(x) = sum_dx P_dx(x + dx) + b2, LReLU, BF16 into the h2
+// slot of v.  16 warps: warp w covers tile (w>>2)&1, TMEM lane quarter w&3 and
+// output channels 16*(w>>3) .. +15.
 __device__ __forceinline__ void conv2_epilogue(unsigned char* h2, uint32_t tmem, int v, const float* wf, float slope,
                                                int warp, int lane) {
-    const int mt = warp >> 2, q = warp & 3;
+    const int mt = (warp >> 2) & 1, q = warp & 3, hf = warp >> 3;
     const int y = mt * 8 + q * 2 + (lane >> 4), xx = lane & 15;
-    float pm[32], p0[32], pp[32];
-    const uint32_t lane_base = (uint32_t)(q * 32) << 16;
-    tmem_ld32(tmem + lane_base + (uint32_t)((mt * 3 + 0) * 32), pm);
-    tmem_ld32(tmem + lane_base + (uint32_t)((mt * 3 + 1) * 32), p0);
-    tmem_ld32(tmem + lane_base + (uint32_t)((mt * 3 + 2) * 32), pp);
+    float pm[16], p0[16], pp[16];
+    const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(hf * 16);
+    tmem_ld16(base + (uint32_t)((mt * 3 + 0) * 32), pm);
+    tmem_ld16(base + (uint32_t)((mt * 3 + 1) * 32), p0);
+    tmem_ld16(base + (uint32_t)((mt * 3 + 2) * 32), pp);
     tmem_ld_wait();
     const int src_m = (lane & 16) | ((xx + 15) & 15);   // x - 1
     const int src_p = (lane & 16) | ((xx + 1) & 15);    // x + 1
     unsigned char* slot = h2 + (size_t)h2_slot(v) * kSlotBytes;
 #pragma unroll
-    for (int cg = 0; cg < 4; ++cg) {
+    for (int g = 0; g < 2; ++g) {
+        const float4 bA = *reinterpret_cast<const float4*>(wf + kF_b2 + hf * 16 + g * 8);
+        const float4 bB = *reinterpret_cast<const float4*>(wf + kF_b2 + hf * 16 + g * 8 + 4);
+        const float bias[8] = {bA.x, bA.y, bA.z, bA.w, bB.x, bB.y, bB.z, bB.w};
         float o[8];
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-            const int ch = cg * 8 + c;
+            const int ch = g * 8 + c;
             const float s = p0[ch] + __shfl_sync(0xffffffffu, pm[ch], src_m) +
-                            __shfl_sync(0xffffffffu, pp[ch], src_p) + wf[kF_b2 + ch];
+                            __shfl_sync(0xffffffffu, pp[ch], src_p) + bias[c];
             o[c] = s > 0.f ? s : slope * s;
         }
-        store8(slot, cg, y, xx, o);
+        store8(slot, hf * 2 + g, y, xx, o);
     }
 }
 
@@ -433,7 +458,8 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
                 if (do3) {
                     // conv3 of slice v-2 has finished reading all three h2 slots after this wait
                     wait_bar(bar3, ph3, abort_flag, a.status);
-                    conv3_epilogue(tmem, slice_of(v - 2), wf, x, frozen, a.use_tanh, INVERSE, logdet, warp, lane);
+                    if (warp < 8)
+                        conv3_epilogue(tmem, slice_of(v - 2), wf, x, frozen, a.use_tanh, INVERSE, logdet, warp, lane);
                 }
                 if (do2) {
                     const int bc = v & 1;

@@ -9,8 +9,10 @@
 // the field x stays in shared memory through every layer, the hidden
 // activations h1/h2 live in a slot cache of slices (see gf_flow.cuh), the
 // log-det, sum z^2 and action are reduced in FP64.  Nothing but the inputs
-// and the per-configuration results touches global memory (weights are read
-// through the read-only path and stay in L1/L2).
+// and the per-configuration results touches global memory: weights are read
+// through the read-only path (L1/L2), or, when every layer's packed weights
+// fit beside the activations (small flows such as the paper's 2D L=8 example),
+// staged once per CTA in shared memory.
 #include <algorithm>
 #include <cstring>
 
@@ -74,8 +76,21 @@ __device__ __forceinline__ int swz(int chunk, int j, int C) { return chunk ^ (j 
 
 __device__ __forceinline__ float lrelu(float v, float a) { return v > 0.f ? v : a * v; }
 
+// Weight reads: through the read-only cache from global memory, or plain loads
+// when the whole flow's packed weights were staged in shared memory (WS).
+template <bool WS>
+__device__ __forceinline__ float4 ldw4(const float* p) {
+    if (WS) return *reinterpret_cast<const float4*>(p);
+    return __ldg(reinterpret_cast<const float4*>(p));
+}
+template <bool WS>
+__device__ __forceinline__ float ldw(const float* p) {
+    if (WS) return *p;
+    return __ldg(p);
+}
+
 // ---------------------------------------------------------------- conv1
-template <int ND>
+template <int ND, bool WS>
 __device__ void phase_h1(const FlowArgs& a, const float* __restrict__ Wl, const Phase& ph,
                          const float* x, float* h1, int frozen) {
     const int L = a.L, S = a.S, C1 = a.C1, T = (ND == 3) ? 27 : 9;
@@ -88,8 +103,8 @@ __device__ void phase_h1(const FlowArgs& a, const float* __restrict__ Wl, const 
         const int sl = wrap(ph.s0 + r, L);
         const int co = g << 3;
         float acc[8];
-        const float4 bb0 = __ldg(reinterpret_cast<const float4*>(b1 + co));
-        const float4 bb1 = __ldg(reinterpret_cast<const float4*>(b1 + co + 4));
+        const float4 bb0 = ldw4<WS>(b1 + co);
+        const float4 bb1 = ldw4<WS>(b1 + co + 4);
         acc[0] = bb0.x; acc[1] = bb0.y; acc[2] = bb0.z; acc[3] = bb0.w;
         acc[4] = bb1.x; acc[5] = bb1.y; acc[6] = bb1.z; acc[7] = bb1.w;
         for (int t = 0; t < T; ++t) {
@@ -99,8 +114,8 @@ __device__ void phase_h1(const FlowArgs& a, const float* __restrict__ Wl, const 
             const int j2 = shift_in_slice<ND>(j, dy, dx, L);
             const int par = (sl2 + coord_sum_in_slice<ND>(j2, L)) & 1;
             const float xv = (par == frozen) ? x[sl2 * S + j2] : 0.f;
-            const float4 w0 = __ldg(reinterpret_cast<const float4*>(W1 + t * C1 + co));
-            const float4 w1 = __ldg(reinterpret_cast<const float4*>(W1 + t * C1 + co + 4));
+            const float4 w0 = ldw4<WS>(W1 + t * C1 + co);
+            const float4 w1 = ldw4<WS>(W1 + t * C1 + co + 4);
             acc[0] = fmaf(xv, w0.x, acc[0]); acc[1] = fmaf(xv, w0.y, acc[1]);
             acc[2] = fmaf(xv, w0.z, acc[2]); acc[3] = fmaf(xv, w0.w, acc[3]);
             acc[4] = fmaf(xv, w1.x, acc[4]); acc[5] = fmaf(xv, w1.y, acc[5]);
@@ -119,7 +134,7 @@ __device__ void phase_h1(const FlowArgs& a, const float* __restrict__ Wl, const 
 // ---------------------------------------------------------------- conv2
 // Warp task = 128 consecutive chunk sites x 8 output channels; lane i owns
 // sites i, i+32, i+64, i+96 (register tile 4 x 8), weights are warp-uniform.
-template <int ND>
+template <int ND, bool WS>
 __device__ void phase_h2(const FlowArgs& a, const float* __restrict__ Wl, const Phase& ph,
                          const float* h1, float* h2) {
     const int L = a.L, S = a.S, C1 = a.C1, C2 = a.C2, T = (ND == 3) ? 27 : 9;
@@ -142,8 +157,8 @@ __device__ void phase_h2(const FlowArgs& a, const float* __restrict__ Wl, const 
         }
         float acc[4][8];
         {
-            const float4 bb0 = __ldg(reinterpret_cast<const float4*>(b2 + co));
-            const float4 bb1 = __ldg(reinterpret_cast<const float4*>(b2 + co + 4));
+            const float4 bb0 = ldw4<WS>(b2 + co);
+            const float4 bb1 = ldw4<WS>(b2 + co + 4);
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 acc[k][0] = bb0.x; acc[k][1] = bb0.y; acc[k][2] = bb0.z; acc[k][3] = bb0.w;
@@ -170,8 +185,8 @@ __device__ void phase_h2(const FlowArgs& a, const float* __restrict__ Wl, const 
 #pragma unroll
                 for (int cc = 0; cc < 4; ++cc) {
                     const float* wp = Wt + (size_t)(4 * c4 + cc) * C2;
-                    const float4 wa = __ldg(reinterpret_cast<const float4*>(wp));
-                    const float4 wb = __ldg(reinterpret_cast<const float4*>(wp + 4));
+                    const float4 wa = ldw4<WS>(wp);
+                    const float4 wb = ldw4<WS>(wp + 4);
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
                         const float h = cc == 0 ? hv[k].x : cc == 1 ? hv[k].y : cc == 2 ? hv[k].z : hv[k].w;
@@ -200,7 +215,7 @@ __device__ void phase_h2(const FlowArgs& a, const float* __restrict__ Wl, const 
 // ---------------------------------------------------------------- conv3 + affine update
 // (s, t) at the updated sites only; `tps` lanes share a site, each summing
 // C2/tps channels, combined with xor-shuffles.
-template <int ND, bool INVERSE>
+template <int ND, bool INVERSE, bool WS>
 __device__ void phase_c3(const FlowArgs& a, const float* __restrict__ Wl, const Phase& ph,
                          const float* h2, float* x, int frozen, double& logdet) {
     const int L = a.L, S = a.S, C2 = a.C2, T = (ND == 3) ? 27 : 9;
@@ -210,7 +225,7 @@ __device__ void phase_c3(const FlowArgs& a, const float* __restrict__ Wl, const 
     const int nchunk = (C2 >> 2) / tps;
     const int total = nact * tps;
     const float* W3 = Wl + a.off.W3;
-    const float bs = __ldg(Wl + a.off.b3), bt = __ldg(Wl + a.off.b3 + 1);
+    const float bs = ldw<WS>(Wl + a.off.b3), bt = ldw<WS>(Wl + a.off.b3 + 1);
     const size_t slot_sz = (size_t)S * C2;
     const int iters = (total + blockDim.x - 1) / blockDim.x;
     for (int i = 0; i < iters; ++i) {
@@ -238,8 +253,8 @@ __device__ void phase_c3(const FlowArgs& a, const float* __restrict__ Wl, const 
                 for (int c = 0; c < nchunk; ++c) {
                     const int c4 = rk * nchunk + c;
                     const float4 hv = *reinterpret_cast<const float4*>(row + ((c4 ^ key) << 2));
-                    const float4 w01 = __ldg(reinterpret_cast<const float4*>(Wt + 8 * c4));
-                    const float4 w23 = __ldg(reinterpret_cast<const float4*>(Wt + 8 * c4 + 4));
+                    const float4 w01 = ldw4<WS>(Wt + 8 * c4);
+                    const float4 w23 = ldw4<WS>(Wt + 8 * c4 + 4);
                     ps = fmaf(hv.x, w01.x, ps); pt = fmaf(hv.x, w01.y, pt);
                     ps = fmaf(hv.y, w01.z, ps); pt = fmaf(hv.y, w01.w, pt);
                     ps = fmaf(hv.z, w23.x, ps); pt = fmaf(hv.z, w23.y, pt);
@@ -281,7 +296,7 @@ __device__ double action_part(const float* x, int L, int V, double m2, double la
     return acc;
 }
 
-template <int ND, bool INVERSE>
+template <int ND, bool INVERSE, bool WS>
 __global__ void __launch_bounds__(kThreads) flow_fp32_kernel(const FlowArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int V = a.V;
@@ -291,6 +306,16 @@ __global__ void __launch_bounds__(kThreads) flow_fp32_kernel(const FlowArgs a) {
     float* h2 = h1 + (size_t)a.R * a.S * a.C1;
     double* red = reinterpret_cast<double*>(h2 + (size_t)a.R * a.S * a.C2);   // 32 doubles
     Phase* ph = reinterpret_cast<Phase*>(red + 32);
+    // optional copy of every layer's packed weights (16-byte aligned after the phase header)
+    float* wsm = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(ph) + ((sizeof(Phase) + 15) & ~size_t(15)));
+    if (WS) {
+        const float4* src = reinterpret_cast<const float4*>(a.W);
+        float4* dst = reinterpret_cast<float4*>(wsm);
+        const int64_t n4 = (int64_t)a.n_layers * a.stride / 4;
+        for (int64_t i = threadIdx.x; i < n4; i += blockDim.x) dst[i] = __ldg(src + i);
+        __syncthreads();
+    }
+    const float* Wbase = WS ? wsm : a.W;
 
     for (int64_t b = blockIdx.x; b < a.B; b += gridDim.x) {
         double sumz2 = 0.0;
@@ -328,15 +353,15 @@ __global__ void __launch_bounds__(kThreads) flow_fp32_kernel(const FlowArgs a) {
         for (int li = 0; li < a.n_layers; ++li) {
             const int l = INVERSE ? a.n_layers - 1 - li : li;
             const int frozen = l & 1;
-            const float* Wl = a.W + (size_t)l * a.stride;
+            const float* Wl = Wbase + (size_t)l * a.stride;
             for (int p = 0; p < a.n_phases; ++p) {
                 if (threadIdx.x < (int)(sizeof(Phase) / 4))
                     reinterpret_cast<uint32_t*>(ph)[threadIdx.x] =
                         __ldg(reinterpret_cast<const uint32_t*>(a.sched + p) + threadIdx.x);
                 __syncthreads();
-                if (ph->type == PH_H1) phase_h1<ND>(a, Wl, *ph, x, h1, frozen);
-                else if (ph->type == PH_H2) phase_h2<ND>(a, Wl, *ph, h1, h2);
-                else phase_c3<ND, INVERSE>(a, Wl, *ph, h2, x, frozen, logdet);
+                if (ph->type == PH_H1) phase_h1<ND, WS>(a, Wl, *ph, x, h1, frozen);
+                else if (ph->type == PH_H2) phase_h2<ND, WS>(a, Wl, *ph, h1, h2);
+                else phase_c3<ND, INVERSE, WS>(a, Wl, *ph, h2, x, frozen, logdet);
                 __syncthreads();
             }
         }
@@ -367,9 +392,9 @@ __global__ void __launch_bounds__(kThreads) flow_fp32_kernel(const FlowArgs a) {
     }
 }
 
-template <int ND, bool INV>
+template <int ND, bool INV, bool WS>
 gf_status launch_t(const gf_flow* f, const FlowArgs& a, cudaStream_t stream) {
-    auto kern = flow_fp32_kernel<ND, INV>;
+    auto kern = flow_fp32_kernel<ND, INV, WS>;
     static int configured_bytes[2] = {0, 0};   // per-instantiation attribute cache
     (void)configured_bytes;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -390,7 +415,7 @@ gf_status launch_t(const gf_flow* f, const FlowArgs& a, cudaStream_t stream) {
 
 size_t flow_fp32_smem(const gf_flow* f, int R) {
     const size_t Vpad = (f->V + 3) & ~3;
-    return Vpad * 4 + (size_t)R * f->S * (f->C1 + f->C2) * 4 + 32 * 8 + sizeof(Phase);
+    return Vpad * 4 + (size_t)R * f->S * (f->C1 + f->C2) * 4 + 32 * 8 + ((sizeof(Phase) + 15) & ~size_t(15));
 }
 
 gf_status flow_fp32_configure(gf_flow* f) {
@@ -405,6 +430,10 @@ gf_status flow_fp32_configure(gf_flow* f) {
         f->full = false; f->G = G; f->R = G + 2;
     }
     f->smem_bytes = flow_fp32_smem(f, f->R);
+    // small flows: keep every layer's packed weights in shared memory as well
+    const size_t wbytes = (size_t)f->shape.n_layers * (size_t)f->packed_stride * 4;
+    f->wsmem = f->smem_bytes + wbytes <= kBudget && wbytes > 0;
+    if (f->wsmem) f->smem_bytes += wbytes;
     return GF_OK;
 }
 
@@ -429,9 +458,14 @@ gf_status launch_flow_fp32(const gf_flow* f, bool inverse, const gf_phi4* phi4, 
     a.B = B; a.seed = seed; a.counter0 = counter0;
     a.z_in = z_in; a.z_out = z_out; a.phi_in = phi_in; a.phi_out = phi_out;
     a.logq_out = logq_out; a.S_out = S_out; a.logw_out = logw_out;
+    if (f->wsmem) {
+        if (f->shape.nd == 3)
+            return inverse ? launch_t<3, true, true>(f, a, stream) : launch_t<3, false, true>(f, a, stream);
+        return inverse ? launch_t<2, true, true>(f, a, stream) : launch_t<2, false, true>(f, a, stream);
+    }
     if (f->shape.nd == 3)
-        return inverse ? launch_t<3, true>(f, a, stream) : launch_t<3, false>(f, a, stream);
-    return inverse ? launch_t<2, true>(f, a, stream) : launch_t<2, false>(f, a, stream);
+        return inverse ? launch_t<3, true, false>(f, a, stream) : launch_t<3, false, false>(f, a, stream);
+    return inverse ? launch_t<2, true, false>(f, a, stream) : launch_t<2, false, false>(f, a, stream);
 }
 
 }  // namespace gf
