@@ -153,7 +153,8 @@ size_t gf_mh_chain_workspace_bytes(int64_t n);
 
 /* Consumes proposals k = 0..n-1 with log weights d_logw[k] (FP64, log p -
  * log q).  Global step g = state.step + k: g == 0 is accepted
- * unconditionally; otherwise accept iff d_logw[k] - logw_cur > log u_g,
+ * unconditionally; otherwise accept iff (d_logw[k] - log u_g) > logw_cur
+ * (w_k / w_cur > u_g, the proposal-only term formed first in FP64),
  * u_g = (2*(w>>12)+1)*2^-53, w = word 0 of philox(key=(seed, stream_id),
  * ctr=(g, 0, 0, 2)).  Writes d_chain_idx_out[k] = global index of the state
  * after step g and d_acc_out[k] in {0,1} (each nullable); updates
@@ -173,9 +174,9 @@ gf_status gf_mh_chain(gf_mh_state* d_state, int64_t n, const double* d_logw,
  * thread that must not risk the device-wide synchronisation a cudaMalloc can
  * cause.  The paper has no counterpart; this is an interface convenience.
  *
- * The log-u scratch lives in a fixed device array inside the library
- * (GF_MH_NOALLOC_MAX_N doubles, held on every device that loads the
- * library until the process exits).  The caller still passes the state,
+ * The per-proposal scratch (one 8-byte key per proposal) lives in a fixed
+ * device array inside the library (GF_MH_NOALLOC_MAX_N entries = 1 MiB,
+ * held on every device that loads the library until the process exits).  The caller still passes the state,
  * log weights and outputs (same meaning as for gf_mh_chain).  No memory is
  * allocated.  The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call

@@ -382,7 +382,8 @@ int gfo_flow_logq(const gfo_shape* sh, const double* w, int32_t bf16_mask, int64
 /* ------------------------------------------------------------------------ */
 /* Metropolis-Hastings independence chain (Sec. 1: flow proposals made exact */
 /* by the MH test with the Jacobian).  Readings: accept proposal k when      */
-/* log w_k - log w_cur > log u_k (strict, ties reject), with                 */
+/* w_k / w_cur > u_k, evaluated as (log w_k - log u_k) > log w_cur in FP64   */
+/* (strict, ties reject; the proposal-only term is formed first), with       */
 /* log w = log p - log q = -S - log q; the very first proposal of a chain is */
 /* accepted unconditionally; u_k from philox(key=(seed, stream_id),          */
 /* ctr=(step, 0, 0, TAG_MH)) word 0.                                         */
@@ -403,7 +404,7 @@ void gfo_mh_scan(gfo_mh_state* st, int64_t n, const double* logw, const double* 
         int64_t g = st->step;
         int a;
         if (g == 0) a = 1;
-        else a = (logw[k] - st->logw_cur) > logu[k];
+        else a = (logw[k] - logu[k]) > st->logw_cur;
         if (a) {
             st->logw_cur = logw[k];
             st->idx_cur = g;

@@ -99,7 +99,8 @@ int gfo_flow_logq(const gfo_shape* sh, const double* w, int32_t bf16_mask, int64
 
 /* MH: uniforms log u_k for steps step0 .. step0+n-1 of stream (seed, stream_id). */
 void gfo_mh_logu(uint64_t seed, uint64_t stream_id, int64_t step0, int64_t n, double* logu);
-/* MH decisions given log u (logu[k] is ignored on global step 0). */
+/* MH decisions given log u: step 0 accepts, step k > 0 accepts iff
+ * (logw[k] - logu[k]) > logw_cur (logu[k] is ignored on global step 0). */
 void gfo_mh_scan(gfo_mh_state* st, int64_t n, const double* logw, const double* logu,
                  int64_t* chain_idx, uint8_t* acc);
 /* MH chain with its own uniforms (gfo_mh_logu + gfo_mh_scan). */

@@ -9,8 +9,10 @@
 //   backward : per layer (last first) recompute h1, h2, s from x_l, then
 //              affine adjoint -> conv3^T -> LReLU' -> conv2^T -> LReLU'
 //              -> conv1^T onto the fixed sites, and the weight gradients.
-// Activations go through HBM ([B][V][C] FP32): the step is bound by FP32
-// FMA throughput, the extra traffic is a few percent of its time.  Weight
+// Activations go through HBM in a channel-chunk-major layout,
+// [B][C/4][V][4] FP32 (chunk width min(C, 4)), so that lanes working on
+// consecutive sites load consecutive 16-byte words; the step is bound by FP32
+// FMA throughput and the extra traffic is a few percent of its time.  Weight
 // gradients: each CTA accumulates its configurations in registers and
 // writes a partial; a second kernel sums the partials in a fixed order
 // (deterministic, no atomics).
@@ -53,6 +55,14 @@ __device__ __forceinline__ int parity(int n, int L) {
     return (ND == 3 ? (x + y + n / (L * L)) : (x + y)) & 1;
 }
 
+// Element (b, n, c) of a C-channel activation tensor: chunk width W = min(C, 4),
+// offset ((b * (C / W) + c / W) * V + n) * W + c % W.  This returns the start of
+// chunk c / W (c a multiple of W).
+__device__ __forceinline__ int64_t chunk_at(int64_t b, int n, int c, int C, int V) {
+    const int W = C < 4 ? C : 4;
+    return ((b * (C / W) + c / W) * (int64_t)V + n) * W;
+}
+
 // ------------------------------------------------------------------ prior
 __global__ void k_prior(int V, int64_t B, uint64_t seed, uint64_t counter0, const float* __restrict__ zin,
                         float* __restrict__ z) {
@@ -73,11 +83,12 @@ __global__ void k_prior(int V, int64_t B, uint64_t seed, uint64_t counter0, cons
 }
 
 // ------------------------------------------------------------------ generic periodic conv
-// out[b][n][co..co+8) = epi( sum_t sum_ci W[t][ci][co] * in'[b][nbr(n,t)][ci] )
+// out(b, n, co..co+8) = epi( sum_t sum_ci W[t][ci][co] * in'(b, nbr(n,t), ci) )
 // in' = in, or in masked to sites of parity `mask` (mask >= 0).
-// mode 0: + bias, LeakyReLU.  mode 1: * LReLU'(ref[b][n][co]) (ref = post-activation).
+// mode 0: + bias, LeakyReLU.  mode 1: * LReLU'(ref(b, n, co)) (ref = post-activation).
 // Warp task = (configuration, 128 sites, 8 output channels); lane owns sites
-// lane + 32k (k < 4), weights are warp-uniform.
+// lane + 32k (k < 4).  The conv's weights [T][Cin][Cout] are staged in shared
+// memory once per CTA (warp-uniform broadcast reads).
 struct ConvArgs {
     const float* in; int Cin; int mask;
     const float* W; const float* bias; int Cout;
@@ -87,10 +98,18 @@ struct ConvArgs {
 
 template <int ND, int VEC>
 __global__ void __launch_bounds__(kThreads) k_conv(const ConvArgs a) {
+    extern __shared__ __align__(16) float wsm[];
+    const int T = ND == 3 ? 27 : 9;
+    {
+        const int n4 = T * a.Cin * a.Cout / 4;
+        for (int i = threadIdx.x; i < n4; i += blockDim.x)
+            reinterpret_cast<float4*>(wsm)[i] = __ldg(reinterpret_cast<const float4*>(a.W) + i);
+        __syncthreads();
+    }
     const int lane = threadIdx.x & 31;
     const int nblk = (a.V + 127) >> 7, ngrp = a.Cout >> 3;
     const int64_t tasks = a.B * nblk * ngrp;
-    const int T = ND == 3 ? 27 : 9;
+    const int64_t cstride = (int64_t)a.V * VEC;            // floats between input chunks
     for (int64_t task = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; task < tasks;
          task += ((int64_t)gridDim.x * blockDim.x) >> 5) {
         const int g = (int)(task % ngrp);
@@ -111,7 +130,7 @@ __global__ void __launch_bounds__(kThreads) k_conv(const ConvArgs a) {
         for (int k = 0; k < 4; ++k)
 #pragma unroll
             for (int c = 0; c < 8; ++c) acc[k][c] = (a.mode == 0) ? __ldg(a.bias + co + c) : 0.f;
-        const float* inb = a.in + b * (int64_t)a.V * a.Cin;
+        const float* inb = a.in + chunk_at(b, 0, 0, a.Cin, a.V);
         for (int t = 0; t < T; ++t) {
             int m[4];
             float msk[4];
@@ -120,12 +139,13 @@ __global__ void __launch_bounds__(kThreads) k_conv(const ConvArgs a) {
                 m[k] = nbr<ND>(n[k], t, a.L);
                 msk[k] = (a.mask < 0 || parity<ND>(m[k], a.L) == a.mask) ? 1.f : 0.f;
             }
-            const float* Wt = a.W + (int64_t)t * a.Cin * a.Cout + co;
+            const float* Wt = wsm + t * a.Cin * a.Cout + co;
             for (int c0 = 0; c0 < a.Cin; c0 += VEC) {
                 float hv[4][VEC];
+                const float* pc = inb + (int64_t)(c0 / VEC) * cstride;
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    const float* p = inb + (int64_t)m[k] * a.Cin + c0;
+                    const float* p = pc + (int64_t)m[k] * VEC;
                     if (VEC == 4) {
                         const float4 v = __ldg(reinterpret_cast<const float4*>(p));
                         hv[k][0] = v.x; hv[k][VEC > 1 ? 1 : 0] = v.y;
@@ -141,9 +161,9 @@ __global__ void __launch_bounds__(kThreads) k_conv(const ConvArgs a) {
                 }
 #pragma unroll
                 for (int q = 0; q < VEC; ++q) {
-                    const float* wp = Wt + (int64_t)(c0 + q) * a.Cout;
-                    const float4 wa = __ldg(reinterpret_cast<const float4*>(wp));
-                    const float4 wb = __ldg(reinterpret_cast<const float4*>(wp + 4));
+                    const float* wp = Wt + (c0 + q) * a.Cout;
+                    const float4 wa = *reinterpret_cast<const float4*>(wp);
+                    const float4 wb = *reinterpret_cast<const float4*>(wp + 4);
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
                         const float h = hv[k][q];
@@ -158,18 +178,21 @@ __global__ void __launch_bounds__(kThreads) k_conv(const ConvArgs a) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             if (!valid[k]) continue;
-            float* o = a.out + (b * a.V + n[k]) * (int64_t)a.Cout + co;
+            float* o0 = a.out + chunk_at(b, n[k], co, a.Cout, a.V);
+            float* o1 = a.out + chunk_at(b, n[k], co + 4, a.Cout, a.V);
             float r[8];
             if (a.mode == 0) {
 #pragma unroll
                 for (int c = 0; c < 8; ++c) r[c] = lrelu(acc[k][c], a.slope);
             } else {
-                const float* rp = a.ref + (b * a.V + n[k]) * (int64_t)a.Cout + co;
+                const float4 q0 = __ldg(reinterpret_cast<const float4*>(a.ref + chunk_at(b, n[k], co, a.Cout, a.V)));
+                const float4 q1 = __ldg(reinterpret_cast<const float4*>(a.ref + chunk_at(b, n[k], co + 4, a.Cout, a.V)));
+                const float rv[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
 #pragma unroll
-                for (int c = 0; c < 8; ++c) r[c] = acc[k][c] * (__ldg(rp + c) > 0.f ? 1.f : a.slope);
+                for (int c = 0; c < 8; ++c) r[c] = acc[k][c] * (rv[c] > 0.f ? 1.f : a.slope);
             }
-            reinterpret_cast<float4*>(o)[0] = make_float4(r[0], r[1], r[2], r[3]);
-            reinterpret_cast<float4*>(o)[1] = make_float4(r[4], r[5], r[6], r[7]);
+            *reinterpret_cast<float4*>(o0) = make_float4(r[0], r[1], r[2], r[3]);
+            *reinterpret_cast<float4*>(o1) = make_float4(r[4], r[5], r[6], r[7]);
         }
     }
 }
@@ -193,10 +216,10 @@ __global__ void __launch_bounds__(kThreads) k_couple_fwd(const float* __restrict
             if (parity<ND>(n, L) == frozen) { xout[b * V + n] = xv; s_save[b * V + n] = 0.f; continue; }
             float ps = __ldg(b3), pt = __ldg(b3 + 1);
             for (int t = 0; t < T; ++t) {
-                const float* hp = h2 + ((b * V) + nbr<ND>(n, t, L)) * (int64_t)C2;
+                const int m = nbr<ND>(n, t, L);
                 const float* wp = W3 + (int64_t)t * C2 * 2;
                 for (int c = 0; c < C2; c += 4) {
-                    const float4 h = __ldg(reinterpret_cast<const float4*>(hp + c));
+                    const float4 h = __ldg(reinterpret_cast<const float4*>(h2 + chunk_at(b, m, c, C2, V)));
                     const float4 w01 = __ldg(reinterpret_cast<const float4*>(wp + 2 * c));
                     const float4 w23 = __ldg(reinterpret_cast<const float4*>(wp + 2 * c + 4));
                     ps = fmaf(h.x, w01.x, ps); pt = fmaf(h.x, w01.y, pt);
@@ -251,10 +274,10 @@ __global__ void k_conv1_bwd(const float* __restrict__ gh1, int C1, const float* 
         const int64_t b = i / V;
         float acc = 0.f;
         for (int t = 0; t < T; ++t) {
-            const float* hp = gh1 + (b * V + nbr<ND>(n, t, L)) * (int64_t)C1;
+            const int m = nbr<ND>(n, t, L);
             const float* wp = W1b + (int64_t)t * C1;
             for (int c = 0; c < C1; c += 4) {
-                const float4 h = __ldg(reinterpret_cast<const float4*>(hp + c));
+                const float4 h = __ldg(reinterpret_cast<const float4*>(gh1 + chunk_at(b, m, c, C1, V)));
                 const float4 w = __ldg(reinterpret_cast<const float4*>(wp + c));
                 acc = fmaf(h.x, w.x, acc); acc = fmaf(h.y, w.y, acc);
                 acc = fmaf(h.z, w.z, acc); acc = fmaf(h.w, w.w, acc);
@@ -294,8 +317,6 @@ __global__ void k_wgrad(const WgArgs a, int nsplit) {
         for (int o = 0; o < OB; ++o) acc[i][o] = 0.f;
     if (active && !(bias && ic != 0)) {
         for (int64_t b = blockIdx.x; b < a.B; b += gridDim.x) {
-            const float* inb = a.in + b * (int64_t)a.V * a.Cin;
-            const float* gb = a.gout + b * (int64_t)a.V * a.Cout;
             for (int n = split; n < a.V; n += nsplit) {
                 float iv[IB];
                 if (bias) {
@@ -304,7 +325,7 @@ __global__ void k_wgrad(const WgArgs a, int nsplit) {
                 } else {
                     const int m = nbr<ND>(n, t, a.L);
                     const float mk = (a.mask < 0 || parity<ND>(m, a.L) == a.mask) ? 1.f : 0.f;
-                    const float* p = inb + (int64_t)m * a.Cin + ic * IB;
+                    const float* p = a.in + chunk_at(b, m, ic * IB, a.Cin, a.V);
                     if (IB == 4) {
                         const float4 v = __ldg(reinterpret_cast<const float4*>(p));
                         iv[0] = v.x * mk; iv[IB > 1 ? 1 : 0] = v.y * mk;
@@ -314,10 +335,10 @@ __global__ void k_wgrad(const WgArgs a, int nsplit) {
                     }
                 }
                 float gv[OB];
-                const float* q = gb + (int64_t)n * a.Cout + oc * OB;
+                const float* q = a.gout + chunk_at(b, n, oc * OB, a.Cout, a.V);
                 if (OB == 8) {
                     const float4 g0 = __ldg(reinterpret_cast<const float4*>(q));
-                    const float4 g1 = __ldg(reinterpret_cast<const float4*>(q + 4));
+                    const float4 g1 = __ldg(reinterpret_cast<const float4*>(a.gout + chunk_at(b, n, oc * OB + 4, a.Cout, a.V)));
                     gv[0] = g0.x; gv[1 % OB] = g0.y; gv[2 % OB] = g0.z; gv[3 % OB] = g0.w;
                     gv[4 % OB] = g1.x; gv[5 % OB] = g1.y; gv[6 % OB] = g1.z; gv[7 % OB] = g1.w;
                 } else {
@@ -524,9 +545,19 @@ template <int ND>
 gf_status conv(const ConvArgs& a, cudaStream_t st) {
     const int64_t warps = a.B * ((a.V + 127) / 128) * (a.Cout / 8);
     const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((warps + 7) / 8, (int64_t)num_sms() * 8));
-    if (a.Cin % 4 == 0) k_conv<ND, 4><<<(unsigned)grid, kThreads, 0, st>>>(a);
-    else if (a.Cin % 2 == 0) k_conv<ND, 2><<<(unsigned)grid, kThreads, 0, st>>>(a);
-    else k_conv<ND, 1><<<(unsigned)grid, kThreads, 0, st>>>(a);
+    const int T = ND == 3 ? 27 : 9;
+    const size_t smem = (size_t)T * a.Cin * a.Cout * sizeof(float);
+    auto go = [&](auto kern) -> bool {
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+            return false;
+        kern<<<(unsigned)grid, kThreads, smem, st>>>(a);
+        return true;
+    };
+    bool ok;
+    if (a.Cin % 4 == 0) ok = go(k_conv<ND, 4>);
+    else if (a.Cin % 2 == 0) ok = go(k_conv<ND, 2>);
+    else ok = go(k_conv<ND, 1>);
+    if (!ok) return GF_ECUDA;
     GF_CHECK_LAUNCH();
     return GF_OK;
 }

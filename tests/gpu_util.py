@@ -49,7 +49,7 @@ def assert_logw_close(gpu, ref, rtol=LOGW_RTOL, what="logw"):
 def compare_mh(orc, st_seed, stream_id, logw, idx_gpu, acc_gpu, step0=0, logw_tol=0.0):
     """MH decisions must match the oracle's except at near ties.
 
-    A decision may differ only where |(logw_k - logw_cur) - log u_k| < tau with
+    A decision may differ only where |(logw_k - log u_k) - logw_cur| < tau with
     tau = 4 * logw_tol * max(|logw|, 1) + 1e-12 (the two sides evaluate log u
     with their own log); after such a divergence the comparison resumes from
     the oracle's state.  Returns the number of tolerated divergences.
@@ -61,12 +61,12 @@ def compare_mh(orc, st_seed, stream_id, logw, idx_gpu, acc_gpu, step0=0, logw_to
     diverged = 0
     for k in range(n):
         g = step0 + k
-        d = logw[k] - cur
-        acc = True if g == 0 else d > logu[k]
+        d = logw[k] - logu[k]
+        acc = True if g == 0 else d > cur
         if bool(acc_gpu[k]) != acc:
             tau = 4 * logw_tol * max(abs(logw[k]), abs(cur), 1.0) + 1e-12
-            assert g > 0 and abs(d - logu[k]) < tau, (
-                f"MH decision {k} differs: gpu={acc_gpu[k]} oracle={acc} margin={d - logu[k]}")
+            assert g > 0 and abs(d - cur) < tau, (
+                f"MH decision {k} differs: gpu={acc_gpu[k]} oracle={acc} margin={d - cur}")
             diverged += 1
         if acc:
             cur, idx = logw[k], g
