@@ -549,7 +549,12 @@ def bench_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": args.workload, "batch_per_step": n},
+            "config": {"workload": f"{args.workload}: {shape.nd}D phi^4 L={shape.L} m2={phi4.m2} "
+                                   f"lam={phi4.lam}, RealNVP {shape.n_layers} couplings, conv "
+                                   f"1->{shape.c1}->{shape.c2}->2, MH chain over the batch",
+                       "batch_per_step": n, "nd": shape.nd, "L": shape.L, "n_layers": shape.n_layers,
+                       "hidden": [shape.c1, shape.c2], "precision": "f64",
+                       "parallelism": "rank 0 host cores (OpenMP over configurations)"},
             "cpu_baseline": {"value": value, "unit": "configs/s", "cores": nthr, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "configs/s", "h2d_bytes_per_step": 0,
@@ -571,14 +576,17 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the secondary measurements")
     ap.add_argument("--serving-requests", type=int, default=120)
     args = ap.parse_args()
-    if args.warmup < 3:
-        ap.error("--warmup must be >= 3")
-    rank, world, local = dist_setup(args.gpus)
     if args.impl == "reference":
+        # The oracle runs on the host cores of rank 0 only: no process group, no GPU.
+        rank = int(os.environ.get("RANK", "0"))
+        world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))
         res = bench_reference(args, rank, world)
         if rank == 0:
             print(json.dumps(res), flush=True)
         return
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank, world, local = dist_setup(args.gpus)
     if args.workload == "c2":
         res = bench_train(args, rank, world, local)
         if rank == 0:

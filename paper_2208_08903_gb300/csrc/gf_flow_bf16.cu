@@ -195,52 +195,72 @@ __device__ __forceinline__ int h2_slot(int v) { return (v + 15) % 3; }
 
 // The taps of conv1 that reach fixed sites from an output site of parity p are
 // those whose offset parity (|dz|+|dy|+|dx|) mod 2 equals NEED = frozen ^ p; the
-// tap set is chosen at compile time, so the loop has no branches.
+// tap set is chosen at compile time, so the loop has no branches.  Two sites
+// (rows y and y + 8, same parity) share each tap's weight loads.
 template <int NEED>
-__device__ __forceinline__ void conv1_taps(float (&acc)[8], const float* wf, const float* x, const int (&zr)[3],
-                                           const int (&yr)[3], const int (&xc)[3], int cg) {
+__device__ __forceinline__ void conv1_taps2(float (&acc)[2][8], const float* wf, const float* x, const int (&zr)[3],
+                                            const int (&yr)[2][3], const int (&xc)[2][3], int cg) {
 #pragma unroll
     for (int t = 0; t < kT; ++t) {
         const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;
         if (((dz + dy + dx + 1) & 1) != NEED) continue;                     // resolved at compile time
-        const float xv = x[zr[dz] + yr[dy] + xc[dx]];
+        const float x0 = x[zr[dz] + yr[0][dy] + xc[0][dx]];
+        const float x1 = x[zr[dz] + yr[1][dy] + xc[1][dx]];
         const float4 w0 = *reinterpret_cast<const float4*>(wf + kF_W1 + t * kC + cg * 8);
         const float4 w1 = *reinterpret_cast<const float4*>(wf + kF_W1 + t * kC + cg * 8 + 4);
-        acc[0] = fmaf(xv, w0.x, acc[0]); acc[1] = fmaf(xv, w0.y, acc[1]);
-        acc[2] = fmaf(xv, w0.z, acc[2]); acc[3] = fmaf(xv, w0.w, acc[3]);
-        acc[4] = fmaf(xv, w1.x, acc[4]); acc[5] = fmaf(xv, w1.y, acc[5]);
-        acc[6] = fmaf(xv, w1.z, acc[6]); acc[7] = fmaf(xv, w1.w, acc[7]);
+        const float w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            acc[0][c] = fmaf(x0, w[c], acc[0][c]);
+            acc[1][c] = fmaf(x1, w[c], acc[1][c]);
+        }
     }
 }
 
-// conv1 + LReLU of virtual slice v into its h1 slot (BF16).  Work items:
-// (channel group, site parity class, 128 sites of that class); a warp holds
-// sites of one parity, so all its lanes take the same 13 or 14 taps.
-// Neighbouring lanes alternate between rows y and y+1, which keeps the
-// 16-byte stores free of bank conflicts.
+// conv1 + LReLU of virtual slice v into its h1 slot (BF16).  512 work items:
+// (channel group, site parity class, 64 site pairs); a warp holds sites of one
+// parity, so all its lanes take the same 13 or 14 taps.  Neighbouring lanes
+// alternate between rows y and y+1, which keeps the 16-byte stores free of
+// bank conflicts.
 __device__ __forceinline__ void conv1_slice(unsigned char* h1, int v, const float* wf, const float* x, int frozen,
                                             float slope, int tid) {
     const int z = slice_of(v);
     unsigned char* slot = h1 + (size_t)h1_slot(v) * kSlotBytes;
 #pragma unroll 1
-    for (int it = tid; it < kS * 4; it += kThreads) {
-        const int cg = it >> 8, rest = it & 255, pcls = rest >> 7, k = rest & 127;
-        const int y = 2 * (k >> 4) + (k & 1), xx = 2 * ((k >> 1) & 7) + ((pcls ^ z ^ y) & 1);  // parity pcls
-        int zr[3], yr[3], xc[3];
+    for (int it = tid; it < kS * 2; it += kThreads) {
+        const int cg = it >> 7, rest = it & 127, pcls = rest >> 6, k = rest & 63;
+        int ys[2], xs[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            ys[q] = 2 * (k >> 4) + (k & 1) + 8 * q;
+            xs[q] = 2 * ((k >> 1) & 7) + ((pcls ^ z ^ ys[q]) & 1);        // parity pcls
+        }
+        int zr[3], yr[2][3], xc[2][3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             zr[d] = wrap16(z + d - 1) << 8;
-            yr[d] = wrap16(y + d - 1) << 4;
-            xc[d] = wrap16(xx + d - 1);
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                yr[q][d] = wrap16(ys[q] + d - 1) << 4;
+                xc[q][d] = wrap16(xs[q] + d - 1);
+            }
         }
         const float4 b0 = *reinterpret_cast<const float4*>(wf + kF_b1 + cg * 8);
         const float4 b1 = *reinterpret_cast<const float4*>(wf + kF_b1 + cg * 8 + 4);
-        float acc[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-        if ((frozen ^ pcls) & 1) conv1_taps<1>(acc, wf, x, zr, yr, xc, cg);
-        else conv1_taps<0>(acc, wf, x, zr, yr, xc, cg);
+        float acc[2][8];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) acc[c] = acc[c] > 0.f ? acc[c] : slope * acc[c];
-        store8(slot, cg, y, xx, acc);
+        for (int q = 0; q < 2; ++q) {
+            acc[q][0] = b0.x; acc[q][1] = b0.y; acc[q][2] = b0.z; acc[q][3] = b0.w;
+            acc[q][4] = b1.x; acc[q][5] = b1.y; acc[q][6] = b1.z; acc[q][7] = b1.w;
+        }
+        if ((frozen ^ pcls) & 1) conv1_taps2<1>(acc, wf, x, zr, yr, xc, cg);
+        else conv1_taps2<0>(acc, wf, x, zr, yr, xc, cg);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) acc[q][c] = acc[q][c] > 0.f ? acc[q][c] : slope * acc[q][c];
+            store8(slot, cg, ys[q], xs[q], acc[q]);
+        }
     }
 }
 

@@ -368,6 +368,93 @@ __global__ void k_wgrad(const WgArgs a, int nsplit) {
     }
 }
 
+// Weight gradient of a C -> C convolution (conv2), tiled through shared memory.
+// A work unit is G consecutive slices (outermost axis) of one configuration:
+// its gout rows and its input rows plus one halo slice on each side are staged
+// site-major ([site][C], bank-conflict-free for the 8 input / 8 output chunks a
+// warp reads per site), then thread (tap t, input chunk ic, 8 outputs oc)
+// accumulates over the unit's sites from shared memory.  Tap t == T is the bias.
+template <int ND>
+__global__ void k_wgrad_tiled(const WgArgs a, int G) {
+    extern __shared__ __align__(16) float sm[];
+    const int T = ND == 3 ? 27 : 9;
+    const int L = a.L, V = a.V, C = a.Cin, CO = a.Cout;
+    const int S = V / L;                                   // sites per slice
+    const int nic = C / 4, noc = CO / 8;
+    const int tasks = (T + 1) * nic * noc;
+    const int task = threadIdx.x;
+    const bool active = task < tasks;
+    const int oc = active ? task % noc : 0;
+    const int ic = active ? (task / noc) % nic : 0;
+    const int t = active ? task / (noc * nic) : T;
+    const bool bias = t == T;
+    int ds = 0, dy = 0, dx = 0;
+    if (!bias) tap_delta<ND>(t, ds, dy, dx);
+    float* g_s = sm;                                       // [G*S][CO]
+    float* x_s = sm + (size_t)G * S * CO;                  // [(G+2)*S][C]
+    float acc[4][8];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int o = 0; o < 8; ++o) acc[i][o] = 0.f;
+    const int units_per_cfg = L / G;
+    const int64_t units = a.B * units_per_cfg;
+    for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
+        const int64_t b = u / units_per_cfg;
+        const int s0 = (int)(u % units_per_cfg) * G;
+        __syncthreads();
+        // stage gout for slices s0 .. s0+G-1 and the input for s0-1 .. s0+G
+        for (int e = threadIdx.x; e < G * S * (CO / 4); e += blockDim.x) {
+            const int site = e / (CO / 4), c4 = e % (CO / 4);
+            const int n = s0 * S + site;
+            *reinterpret_cast<float4*>(g_s + (size_t)site * CO + c4 * 4) =
+                __ldg(reinterpret_cast<const float4*>(a.gout + chunk_at(b, n, c4 * 4, CO, V)));
+        }
+        for (int e = threadIdx.x; e < (G + 2) * S * (C / 4); e += blockDim.x) {
+            const int site = e / (C / 4), c4 = e % (C / 4);
+            const int sl = s0 - 1 + site / S;
+            const int n = ((sl % L + L) % L) * S + site % S;
+            *reinterpret_cast<float4*>(x_s + (size_t)site * C + c4 * 4) =
+                __ldg(reinterpret_cast<const float4*>(a.in + chunk_at(b, n, c4 * 4, C, V)));
+        }
+        __syncthreads();
+        if (active && !(bias && ic != 0)) {
+            for (int r = 0; r < G * S; ++r) {
+                const int j = r % S, rs = r / S;               // slice offset within the unit, in-slice site
+                const float4 g0 = *reinterpret_cast<const float4*>(g_s + (size_t)r * CO + oc * 8);
+                const float4 g1 = *reinterpret_cast<const float4*>(g_s + (size_t)r * CO + oc * 8 + 4);
+                const float gv[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+                float iv[4];
+                if (bias) {
+                    iv[0] = 1.f; iv[1] = iv[2] = iv[3] = 0.f;
+                } else {
+                    int j2;
+                    if (ND == 3) {
+                        const int y = j / L, x = j - y * L;
+                        j2 = wrapi(y + dy, L) * L + wrapi(x + dx, L);
+                    } else {
+                        j2 = wrapi(j + dx, L);
+                    }
+                    const float4 v = *reinterpret_cast<const float4*>(x_s + (size_t)((rs + 1 + ds) * S + j2) * C + ic * 4);
+                    iv[0] = v.x; iv[1] = v.y; iv[2] = v.z; iv[3] = v.w;
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int o = 0; o < 8; ++o) acc[i][o] = fmaf(iv[i], gv[o], acc[i][o]);
+            }
+        }
+    }
+    if (active) {
+        float* P = a.partial + (int64_t)blockIdx.x * (T + 1) * C * CO;
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int o = 0; o < 8; ++o)
+                P[((int64_t)t * C + ic * 4 + i) * CO + oc * 8 + o] = acc[i][o];
+    }
+}
+
 // grad (canonical, for one conv of one layer): W[o][i][t] and b[o], scaled by 1/B.
 __global__ void k_wgrad_reduce(const float* __restrict__ partial, int nparts, int T, int Cin, int Cout,
                                float scale, float* __restrict__ gW, float* __restrict__ gb) {
@@ -575,7 +662,20 @@ gf_status wgrad(const WgArgs& a, float* gW, float* gbias, float scale, cudaStrea
     };
     if (a.Cin == 1) launch(k_wgrad<ND, 1, 8>, (T + 1) * (a.Cout / 8));
     else if (a.Cout == 2) launch(k_wgrad<ND, 4, 2>, (T + 1) * (a.Cin / 4));
-    else launch(k_wgrad<ND, 4, 8>, (T + 1) * (a.Cin / 4) * (a.Cout / 8));
+    else {
+        // C -> C (unmasked input): shared-memory tiled; G = the largest divisor of
+        // L whose staged rows fit in 96 KB, else 1
+        if (a.mask >= 0) return GF_EINVAL;
+        const int S = a.V / a.L;
+        int G = a.L;
+        auto bytes = [&](int g) { return (size_t)(g * S * a.Cout + (g + 2) * S * a.Cin) * sizeof(float); };
+        while (G > 1 && (bytes(G) > 96 * 1024 || a.L % G != 0)) --G;
+        const int threads = ((T + 1) * (a.Cin / 4) * (a.Cout / 8) + 31) / 32 * 32;
+        if (cudaFuncSetAttribute(k_wgrad_tiled<ND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)bytes(G)) != cudaSuccess)
+            return GF_ECUDA;
+        k_wgrad_tiled<ND><<<grid, threads, bytes(G), st>>>(a, G);
+    }
     GF_CHECK_LAUNCH();
     const int per = (T + 1) * a.Cin * a.Cout;
     k_wgrad_reduce<<<(per + 255) / 256, 256, 0, st>>>(a.partial, grid, T, a.Cin, a.Cout, scale, gW, gbias);
