@@ -375,7 +375,7 @@ __global__ void k_wgrad(const WgArgs a, int nsplit) {
 // warp reads per site), then thread (tap t, input chunk ic, 8 outputs oc)
 // accumulates over the unit's sites from shared memory.  Tap t == T is the bias.
 template <int ND>
-__global__ void k_wgrad_tiled(const WgArgs a, int G) {
+__global__ void __launch_bounds__(1024) k_wgrad_tiled(const WgArgs a, int G) {
     extern __shared__ __align__(16) float sm[];
     const int T = ND == 3 ? 27 : 9;
     const int L = a.L, V = a.V, C = a.Cin, CO = a.Cout;
