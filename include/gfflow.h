@@ -143,6 +143,14 @@ gf_status gf_phi4_action(int32_t nd, int32_t L, const gf_phi4* phi4, int64_t B,
 gf_status gf_phi4_force(int32_t nd, int32_t L, const gf_phi4* phi4, int64_t B,
                         const double* d_phi, double* d_F_out, cudaStream_t stream);
 
+/* Vector-Jacobian product for FP32 fields: d_gphi_out[b][n] = d_gS[b] *
+ * dS/dphi_b(n), each product formed in FP64 and rounded once to FP32.  With
+ * d_gS[b] = dLoss/dS_b it gives dLoss/dphi for a loss built on S (the
+ * reverse-KL loss of Sec. 1 uses d_gS[b] = 1/B). */
+gf_status gf_phi4_action_vjp(int32_t nd, int32_t L, const gf_phi4* phi4, int64_t B,
+                             const float* d_phi, const double* d_gS, float* d_gphi_out,
+                             cudaStream_t stream);
+
 /* ---------------------------------------------------------------------- */
 /* Metropolis-Hastings independence chain (paper Sec. 1: flow proposals   */
 /* corrected by the MH test with the Jacobian)                             */
@@ -224,6 +232,27 @@ gf_status gf_flow_train_step(gf_flow* flow, const gf_phi4* phi4, int64_t B, uint
                              float adam_eps, float* d_adam_m, float* d_adam_v,
                              int64_t adam_t, void* d_workspace, size_t workspace_bytes,
                              cudaStream_t stream);
+
+/* The training step in two halves, for a loss assembled by the caller
+ * (e.g. through torch.autograd).  Both take the workspace of
+ * gf_train_workspace_bytes(flow, B).
+ *
+ * Forward half: phi_b = F^{-1}(z_b) and log q(phi_b) = log r(z_b) - log det
+ * (Sec. 1), z_b as in gf_flow_sample.  Writes d_phi_out [B][V] FP32 and
+ * d_logq_out [B] FP64, and keeps every layer's input in the workspace. */
+gf_status gf_flow_forward_train(const gf_flow* flow, int64_t B, uint64_t seed, uint64_t counter0,
+                                const float* d_z_in, float* d_phi_out, double* d_logq_out,
+                                void* d_workspace, size_t workspace_bytes, cudaStream_t stream);
+/* Backward half: given dLoss/dphi (d_gphi [B][V] FP32, NULL = 0) and
+ * dLoss/dlog q (d_glogq [B] FP64, NULL = 0), writes dLoss/dtheta to
+ * d_grad_out [n_params] FP32 in canonical order.  The workspace must hold the
+ * state left by the latest gf_flow_forward_train with the same B and the
+ * same weights; it is overwritten (a second backward needs a new forward).
+ * With d_gphi = dS/dphi / B and d_glogq = 1/B it equals the gradient of
+ * gf_flow_train_step up to FP32 rounding order. */
+gf_status gf_flow_backward(const gf_flow* flow, int64_t B, const float* d_gphi, const double* d_glogq,
+                           float* d_grad_out, void* d_workspace, size_t workspace_bytes,
+                           cudaStream_t stream);
 
 /* ---------------------------------------------------------------------- */
 /* Status                                                                  */

@@ -8,5 +8,6 @@ package is its ctypes/torch binding.
 """
 from .api import (Flow, SampleResult, device_status, hmc_trajectory, mh_chain,  # noqa: F401
                   mh_chain_noalloc,
-                  mh_chain_workspace_bytes, new_mh_state, phi4_action, phi4_force,
-                  read_mh_state)
+                  mh_chain_workspace_bytes, new_mh_state, phi4_action, phi4_action_vjp,
+                  phi4_force, read_mh_state)
+from . import autograd  # noqa: F401

@@ -68,6 +68,7 @@ class Flow:
                                                          _stream(), C.byref(h)))
         self._h = h
         self._lib = lib
+        self.weights_version = 0      # bumped whenever the resident weights change
         self.n_params = int(lib.gf_flow_n_params(h))
         if self.n_params != w.numel():
             raise ValueError(f"weights have {w.numel()} entries, the shape needs {self.n_params}")
@@ -156,6 +157,7 @@ class Flow:
         _need(w, torch.float32, "w", self.n_params)
         _abi.check("gf_flow_set_weights_device",
                    self._lib.gf_flow_set_weights_device(self._h, _ptr(w), _stream()))
+        self.weights_version += 1
 
     def train_workspace_bytes(self, B: int) -> int:
         return int(self._lib.gf_train_workspace_bytes(self._h, B))
@@ -180,7 +182,54 @@ class Flow:
             self._h, C.byref(p), B, seed, counter0, _ptr(z), _ptr(loss), _ptr(g), float(lr),
             float(beta1), float(beta2), float(adam_eps), _ptr(adam_m), _ptr(adam_v), int(adam_t),
             _ptr(workspace), workspace.numel(), _stream()))
+        if lr > 0:
+            self.weights_version += 1
         return loss, g
+
+
+    def forward_train(self, B: int, seed: int = 0, counter0: int = 0, z=None,
+                      workspace: torch.Tensor | None = None):
+        """Forward half of training: (phi [B][V] FP32, log q [B] FP64, workspace).
+
+        The workspace keeps every layer's input for `backward`."""
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if z is not None:
+            _need(z, torch.float32, "z", B * self.V)
+        nbytes = self.train_workspace_bytes(B)
+        if workspace is None or workspace.numel() < nbytes:
+            workspace = torch.empty(max(nbytes, 1), device=dev, dtype=torch.uint8)
+        phi = torch.empty(B, self.V, device=dev, dtype=torch.float32)
+        logq = torch.empty(B, device=dev, dtype=torch.float64)
+        _abi.check("gf_flow_forward_train", self._lib.gf_flow_forward_train(
+            self._h, B, seed, counter0, _ptr(z), _ptr(phi), _ptr(logq), _ptr(workspace),
+            workspace.numel(), _stream()))
+        return phi, logq, workspace
+
+    def backward(self, B: int, gphi, glogq, workspace: torch.Tensor) -> torch.Tensor:
+        """dLoss/dtheta [n_params] FP32 from dLoss/dphi (FP32 [B][V] or None) and
+        dLoss/dlog q (FP64 [B] or None); `workspace` from the matching forward_train."""
+        if gphi is not None:
+            _need(gphi, torch.float32, "gphi", B * self.V)
+        if glogq is not None:
+            _need(glogq, torch.float64, "glogq", B)
+        _need(workspace, torch.uint8, "workspace")
+        g = torch.empty(self.n_params, device=workspace.device, dtype=torch.float32)
+        _abi.check("gf_flow_backward", self._lib.gf_flow_backward(
+            self._h, B, _ptr(gphi), _ptr(glogq), _ptr(g), _ptr(workspace), workspace.numel(),
+            _stream()))
+        return g
+
+
+def phi4_action_vjp(nd: int, L: int, phi4, phi: torch.Tensor, gS: torch.Tensor) -> torch.Tensor:
+    """gS[b] * dS/dphi_b for an FP32 field [B][V] (FP64 arithmetic, FP32 out)."""
+    B = phi.shape[0]
+    _need(phi, torch.float32, "phi", B * L**nd)
+    _need(gS, torch.float64, "gS", B)
+    out = torch.empty_like(phi)
+    p = _phi4(phi4)
+    _abi.check("gf_phi4_action_vjp", _abi.load().gf_phi4_action_vjp(
+        nd, L, C.byref(p), B, _ptr(phi), _ptr(gS), _ptr(out), _stream()))
+    return out
 
 
 def phi4_action(nd: int, L: int, phi4, phi: torch.Tensor, out: torch.Tensor | None = None):

@@ -97,6 +97,27 @@ __global__ void __launch_bounds__(kActThreads) force_kernel(int nd, int L, int V
     }
 }
 
+// Vector-Jacobian product of the action for FP32 fields: gphi = gS[b] dS/dphi,
+// formed in FP64 from the exactly widened field, rounded once to FP32.
+__global__ void __launch_bounds__(kActThreads) action_vjp_kernel(int nd, int L, int V, double m2, double lam,
+                                                                 int64_t B, const float* __restrict__ phi,
+                                                                 const double* __restrict__ gS,
+                                                                 float* __restrict__ gphi) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* p = reinterpret_cast<float*>(smem_raw);
+    for (int64_t b = blockIdx.x; b < B; b += gridDim.x) {
+        stage(phi + b * V, p, V);
+        __syncthreads();
+        const double g = gS[b];
+        for (int n = threadIdx.x; n < V; n += blockDim.x) {
+            const double c = p[n];
+            const double F = 2.0 * lap_minus(p, n, nd, L) + 2.0 * m2 * c + 4.0 * lam * c * c * c;
+            gphi[b * V + n] = (float)(g * F);
+        }
+        __syncthreads();
+    }
+}
+
 bool lattice_ok(int nd, int L) {
     if (nd != 2 && nd != 3) return false;
     if (L < 1) return false;
@@ -159,6 +180,22 @@ gf_status gf_phi4_force(int32_t nd, int32_t L, const gf_phi4* phi4, int64_t B,
         return GF_ECUDA;
     force_kernel<<<(unsigned)grid_for(force_kernel, smem, B), kActThreads, smem, stream>>>(
         nd, L, V, phi4->m2, phi4->lam, B, d_phi, d_F_out);
+    GF_CHECK_LAUNCH();
+    return GF_OK;
+}
+
+gf_status gf_phi4_action_vjp(int32_t nd, int32_t L, const gf_phi4* phi4, int64_t B, const float* d_phi,
+                             const double* d_gS, float* d_gphi_out, cudaStream_t stream) {
+    if (!phi4 || !lattice_ok(nd, L) || B < 0 || (B > 0 && (!d_phi || !d_gS || !d_gphi_out))) return GF_EINVAL;
+    if (B == 0) return GF_OK;
+    int V = 1;
+    for (int i = 0; i < nd; ++i) V *= L;
+    const size_t smem = (size_t)V * 4;
+    if (cudaFuncSetAttribute(action_vjp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return GF_ECUDA;
+    action_vjp_kernel<<<(unsigned)grid_for(action_vjp_kernel, smem, B), kActThreads, smem, stream>>>(
+        nd, L, V, phi4->m2, phi4->lam, B, d_phi, d_gS, d_gphi_out);
     GF_CHECK_LAUNCH();
     return GF_OK;
 }

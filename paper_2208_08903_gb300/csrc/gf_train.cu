@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(kThreads) k_conv(const ConvArgs a) {
 // ------------------------------------------------------------------ conv3 + affine (forward)
 // One CTA per configuration: (s, t) at the updated sites, x_out = x_in*e^s + t
 // there, x_out = x_in on fixed sites; s saved for the reverse pass;
-// logdet[b] += sum s (FP64, fixed-order block reduction).
+// logdet[b] += sum s (FP64, fixed-order block reduction) unless logdet is null.
 template <int ND>
 __global__ void __launch_bounds__(kThreads) k_couple_fwd(const float* __restrict__ h2, int C2,
                                                         const float* __restrict__ W3, const float* __restrict__ b3,
@@ -233,8 +233,10 @@ __global__ void __launch_bounds__(kThreads) k_couple_fwd(const float* __restrict
             s_save[b * V + n] = s;
             ld += (double)s;
         }
-        const double tot = block_sum(ld, red);
-        if (threadIdx.x == 0) logdet[b] += tot;
+        if (logdet) {                                   // uniform over the block
+            const double tot = block_sum(ld, red);
+            if (threadIdx.x == 0) logdet[b] += tot;
+        }
         __syncthreads();
     }
 }
@@ -243,7 +245,8 @@ __global__ void __launch_bounds__(kThreads) k_couple_fwd(const float* __restrict
 // At updated sites: g3 = (dL/ds_pre, dL/dt), gx <- gx*e^s.  Fixed sites: g3 = 0.
 template <int ND>
 __global__ void k_couple_bwd(int frozen, int use_tanh, int L, int V, int64_t B, const float* __restrict__ xin,
-                             const float* __restrict__ s_save, float* __restrict__ gx, float* __restrict__ g3) {
+                             const float* __restrict__ s_save, const double* __restrict__ glq, float glq_const,
+                             float* __restrict__ gx, float* __restrict__ g3) {
     const int64_t total = B * (int64_t)V;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -251,7 +254,9 @@ __global__ void k_couple_bwd(int frozen, int use_tanh, int L, int V, int64_t B, 
         float2 o = make_float2(0.f, 0.f);
         if (parity<ND>(n, L) != frozen) {
             const float s = s_save[i], e = expf(s), g = gx[i];
-            const float gs = g * xin[i] * e - 1.0f;           // d/ds of x*e^s and of -logdet
+            // d/ds of x*e^s, and of log q = log r - logdet (dLoss/dlog q per configuration)
+            const float gq = glq ? (float)glq[i / V] : glq_const;
+            const float gs = g * xin[i] * e - gq;
             o.x = use_tanh ? gs * (1.f - s * s) : gs;
             o.y = g;
             gx[i] = g * e;
@@ -649,6 +654,19 @@ gf_status conv(const ConvArgs& a, cudaStream_t st) {
     return GF_OK;
 }
 
+// conv1 + LReLU and conv2 + LReLU of layer l on x_l (FP32, activations in the workspace).
+template <int ND>
+gf_status net_fwd(const gf_flow* f, int l, const float* xl, int64_t B, const TrainWs& w, cudaStream_t st) {
+    const PackedOffsets po = packed_offsets(f->T, f->C1, f->C2);
+    const float slope = (float)f->shape.leaky_slope;
+    const float* P = f->d_packed + (int64_t)l * f->packed_stride;
+    ConvArgs c1{xl, 1, l & 1, P + po.W1, P + po.b1, f->C1, w.h1, nullptr, 0, slope, f->shape.L, f->V, B};
+    gf_status s = conv<ND>(c1, st);
+    if (s != GF_OK) return s;
+    ConvArgs c2{w.h1, f->C1, -1, P + po.W2, P + po.b2, f->C2, w.h2, nullptr, 0, slope, f->shape.L, f->V, B};
+    return conv<ND>(c2, st);
+}
+
 template <int ND>
 gf_status wgrad(const WgArgs& a, float* gW, float* gbias, float scale, cudaStream_t st) {
     const int T = ND == 3 ? 27 : 9;
@@ -683,11 +701,39 @@ gf_status wgrad(const WgArgs& a, float* gW, float* gbias, float scale, cudaStrea
     return GF_OK;
 }
 
+// Forward pass of training: z -> x_1 .. x_N saved in the workspace, logdet per
+// configuration.  Leaves the last layer's h1 / h2 / s in the workspace.
 template <int ND>
-gf_status train_step(gf_flow* f, const gf_phi4* phi4, int64_t B, uint64_t seed, uint64_t counter0,
-                     const float* z_in, double* loss_out, float* grad_out, float lr, float beta1,
-                     float beta2, float adam_eps, float* adam_m, float* adam_v, int64_t adam_t,
-                     const TrainWs& w, cudaStream_t st) {
+gf_status forward_pass(const gf_flow* f, int64_t B, uint64_t seed, uint64_t counter0, const float* z_in,
+                       const TrainWs& w, cudaStream_t st) {
+    const int L = f->shape.L, V = f->V, N = f->shape.n_layers, T = f->T;
+    const int C1 = f->C1, C2 = f->C2;
+    const int64_t BV = B * (int64_t)V;
+    const float slope = (float)f->shape.leaky_slope;
+    const PackedOffsets po = packed_offsets(T, C1, C2);
+    k_prior<<<(unsigned)grid1d(BV / 4 + 1), kThreads, 0, st>>>(V, B, seed, counter0, z_in, w.xs);
+    GF_CHECK_LAUNCH();
+    if (cudaMemsetAsync(w.logdet, 0, sizeof(double) * B, st) != cudaSuccess) return GF_ECUDA;
+    const unsigned cfg_grid = (unsigned)std::min<int64_t>(B, (int64_t)num_sms() * 8);
+    for (int l = 0; l < N; ++l) {
+        const float* xl = w.xs + (int64_t)l * BV;
+        gf_status s = net_fwd<ND>(f, l, xl, B, w, st);
+        if (s != GF_OK) return s;
+        const float* P = f->d_packed + (int64_t)l * f->packed_stride;
+        k_couple_fwd<ND><<<cfg_grid, kThreads, 0, st>>>(w.h2, C2, P + po.W3, P + po.b3, f->shape.use_final_tanh,
+                                                       l & 1, L, V, B, xl, w.xs + (int64_t)(l + 1) * BV, w.s,
+                                                       w.logdet);
+        GF_CHECK_LAUNCH();
+    }
+    return GF_OK;
+}
+
+// Reverse pass: with w.gx = dLoss/dphi seeded and dLoss/dlog q = glq[b] (or
+// glq_const when glq is null), writes dLoss/dtheta * scale to grad (canonical
+// order).  Needs the x_l saved by forward_pass with the same weights.
+template <int ND>
+gf_status reverse_pass(const gf_flow* f, int64_t B, const double* glq, float glq_const, float scale, float* grad,
+                       const TrainWs& w, cudaStream_t st) {
     const int L = f->shape.L, V = f->V, N = f->shape.n_layers, T = f->T;
     const int C1 = f->C1, C2 = f->C2;
     const int64_t BV = B * (int64_t)V;
@@ -695,45 +741,12 @@ gf_status train_step(gf_flow* f, const gf_phi4* phi4, int64_t B, uint64_t seed, 
     const int use_tanh = f->shape.use_final_tanh;
     const PackedOffsets po = packed_offsets(T, C1, C2);
     const int64_t obstride = (int64_t)T * C1 + (int64_t)T * C2 * C1 + 2LL * T * C2;
-    float* grad = grad_out ? grad_out : w.grad;
-
-    k_prior<<<(unsigned)grid1d(BV / 4 + 1), kThreads, 0, st>>>(V, B, seed, counter0, z_in, w.xs);
-    GF_CHECK_LAUNCH();
-    if (cudaMemsetAsync(w.logdet, 0, sizeof(double) * B, st) != cudaSuccess) return GF_ECUDA;
     if (N > 0) {
         k_pack_bwd<<<(unsigned)grid1d(obstride * N), kThreads, 0, st>>>(f->d_canon, f->canon_stride, N, T, C1, C2,
                                                                         w.wb, obstride);
         GF_CHECK_LAUNCH();
     }
     const unsigned cfg_grid = (unsigned)std::min<int64_t>(B, (int64_t)num_sms() * 8);
-
-    auto net_fwd = [&](int l, const float* xl) -> gf_status {
-        const float* P = f->d_packed + (int64_t)l * f->packed_stride;
-        ConvArgs c1{xl, 1, l & 1, P + po.W1, P + po.b1, C1, w.h1, nullptr, 0, slope, L, V, B};
-        gf_status s = conv<ND>(c1, st);
-        if (s != GF_OK) return s;
-        ConvArgs c2{w.h1, C1, -1, P + po.W2, P + po.b2, C2, w.h2, nullptr, 0, slope, L, V, B};
-        return conv<ND>(c2, st);
-    };
-
-    // forward: save x_l, accumulate logdet
-    for (int l = 0; l < N; ++l) {
-        const float* xl = w.xs + (int64_t)l * BV;
-        gf_status s = net_fwd(l, xl);
-        if (s != GF_OK) return s;
-        const float* P = f->d_packed + (int64_t)l * f->packed_stride;
-        k_couple_fwd<ND><<<cfg_grid, kThreads, 0, st>>>(w.h2, C2, P + po.W3, P + po.b3, use_tanh, l & 1, L, V, B,
-                                                       xl, w.xs + (int64_t)(l + 1) * BV, w.s, w.logdet);
-        GF_CHECK_LAUNCH();
-    }
-    k_loss_force<ND><<<cfg_grid, kThreads, 0, st>>>(w.xs, w.xs + (int64_t)N * BV, w.logdet, phi4->m2, phi4->lam,
-                                                    L, V, B, w.loss_b, w.gx);
-    GF_CHECK_LAUNCH();
-    k_mean<<<1, kThreads, 0, st>>>(w.loss_b, B, loss_out);
-    GF_CHECK_LAUNCH();
-
-    // reverse pass
-    const float scale = 1.0f / (float)B;
     for (int l = N - 1; l >= 0; --l) {
         const float* xl = w.xs + (int64_t)l * BV;
         const float* P = f->d_packed + (int64_t)l * f->packed_stride;
@@ -745,13 +758,13 @@ gf_status train_step(gf_flow* f, const gf_phi4* phi4, int64_t B, uint64_t seed, 
         float* gb2 = gW2 + (int64_t)C2 * C1 * T;
         float* gW3 = gb2 + C2;
         float* gb3 = gW3 + 2LL * C2 * T;
-        gf_status s = net_fwd(l, xl);                                  // recompute h1, h2
+        gf_status s = net_fwd<ND>(f, l, xl, B, w, st);               // recompute h1, h2
         if (s != GF_OK) return s;
         k_couple_fwd<ND><<<cfg_grid, kThreads, 0, st>>>(w.h2, C2, P + po.W3, P + po.b3, use_tanh, l & 1, L, V, B,
-                                                       xl, w.g3 /* scratch for x_out */, w.s, w.logdet + 0);
+                                                       xl, w.g3 /* scratch for x_out */, w.s, nullptr);
         GF_CHECK_LAUNCH();
-        // (the logdet re-accumulation above is discarded: loss already reduced)
-        k_couple_bwd<ND><<<(unsigned)grid1d(BV), kThreads, 0, st>>>(l & 1, use_tanh, L, V, B, xl, w.s, w.gx, w.g3);
+        k_couple_bwd<ND><<<(unsigned)grid1d(BV), kThreads, 0, st>>>(l & 1, use_tanh, L, V, B, xl, w.s, glq,
+                                                                   glq_const, w.gx, w.g3);
         GF_CHECK_LAUNCH();
         WgArgs a3{w.h2, C2, -1, w.g3, 2, w.partial, L, V, B};
         if ((s = wgrad<ND>(a3, gW3, gb3, scale, st)) != GF_OK) return s;
@@ -766,6 +779,28 @@ gf_status train_step(gf_flow* f, const gf_phi4* phi4, int64_t B, uint64_t seed, 
         k_conv1_bwd<ND><<<(unsigned)grid1d(BV), kThreads, 0, st>>>(w.gh1, C1, Wb, l & 1, L, V, B, w.gx);
         GF_CHECK_LAUNCH();
     }
+    return GF_OK;
+}
+
+template <int ND>
+gf_status train_step(gf_flow* f, const gf_phi4* phi4, int64_t B, uint64_t seed, uint64_t counter0,
+                     const float* z_in, double* loss_out, float* grad_out, float lr, float beta1,
+                     float beta2, float adam_eps, float* adam_m, float* adam_v, int64_t adam_t,
+                     const TrainWs& w, cudaStream_t st) {
+    const int L = f->shape.L, V = f->V, N = f->shape.n_layers;
+    const int64_t BV = B * (int64_t)V;
+    float* grad = grad_out ? grad_out : w.grad;
+    gf_status s = forward_pass<ND>(f, B, seed, counter0, z_in, w, st);
+    if (s != GF_OK) return s;
+    const unsigned cfg_grid = (unsigned)std::min<int64_t>(B, (int64_t)num_sms() * 8);
+    // per-configuration loss log r - logdet + S and the seed dS/dphi; the loss
+    // is the mean, so every configuration's gradient is scaled by 1/B
+    k_loss_force<ND><<<cfg_grid, kThreads, 0, st>>>(w.xs, w.xs + (int64_t)N * BV, w.logdet, phi4->m2, phi4->lam,
+                                                    L, V, B, w.loss_b, w.gx);
+    GF_CHECK_LAUNCH();
+    k_mean<<<1, kThreads, 0, st>>>(w.loss_b, B, loss_out);
+    GF_CHECK_LAUNCH();
+    if ((s = reverse_pass<ND>(f, B, nullptr, 1.0f, 1.0f / (float)B, grad, w, st)) != GF_OK) return s;
     if (lr > 0.f) {
         const float c1 = 1.f - powf(beta1, (float)adam_t), c2 = 1.f - powf(beta2, (float)adam_t);
         k_adam<<<(unsigned)grid1d(f->n_params), kThreads, 0, st>>>(f->n_params, f->d_canon, grad, adam_m, adam_v,
@@ -774,6 +809,32 @@ gf_status train_step(gf_flow* f, const gf_phi4* phi4, int64_t B, uint64_t seed, 
         return repack_weights(f, st);
     }
     return GF_OK;
+}
+
+// Forward half for autograd: phi = x_N and log q = log r(z) - logdet.
+template <int ND>
+gf_status forward_train(const gf_flow* f, int64_t B, uint64_t seed, uint64_t counter0, const float* z_in,
+                        float* phi_out, double* logq_out, const TrainWs& w, cudaStream_t st) {
+    gf_status s = forward_pass<ND>(f, B, seed, counter0, z_in, w, st);
+    if (s != GF_OK) return s;
+    const int64_t BV = B * (int64_t)f->V;
+    const unsigned cfg_grid = (unsigned)std::min<int64_t>(B, (int64_t)num_sms() * 8);
+    k_finish<ND><<<cfg_grid, kThreads, 0, st>>>(w.xs, w.xs + (int64_t)f->shape.n_layers * BV, w.logdet, 0, 0.0,
+                                               0.0, f->shape.L, f->V, B, phi_out, nullptr, logq_out, nullptr,
+                                               nullptr);
+    GF_CHECK_LAUNCH();
+    return GF_OK;
+}
+
+// Backward half: gx <- dLoss/dphi (zero when null), then the reverse pass.
+template <int ND>
+gf_status backward(const gf_flow* f, int64_t B, const float* gphi, const double* glogq, float* grad,
+                   const TrainWs& w, cudaStream_t st) {
+    const size_t bytes = sizeof(float) * (size_t)B * f->V;
+    const cudaError_t e = gphi ? cudaMemcpyAsync(w.gx, gphi, bytes, cudaMemcpyDeviceToDevice, st)
+                               : cudaMemsetAsync(w.gx, 0, bytes, st);
+    if (e != cudaSuccess) return GF_ECUDA;
+    return reverse_pass<ND>(f, B, glogq, 0.0f, 1.0f, grad, w, st);
 }
 
 // Unfused FP32 sampler: one kernel per convolution, activations through HBM.
@@ -863,6 +924,28 @@ gf_status gf_flow_train_step(gf_flow* flow, const gf_phi4* phi4, int64_t B, uint
                              adam_eps, d_adam_m, d_adam_v, adam_t, w, stream);
     return train_step<2>(flow, phi4, B, seed, counter0, d_z_in, d_loss_out, d_grad_out, lr, beta1, beta2,
                          adam_eps, d_adam_m, d_adam_v, adam_t, w, stream);
+}
+
+gf_status gf_flow_forward_train(const gf_flow* flow, int64_t B, uint64_t seed, uint64_t counter0,
+                                const float* d_z_in, float* d_phi_out, double* d_logq_out, void* d_workspace,
+                                size_t workspace_bytes, cudaStream_t stream) {
+    if (!flow || B <= 0 || !d_phi_out || !d_logq_out) return GF_EINVAL;
+    const TrainWs w = carve(flow, B, static_cast<char*>(d_workspace));
+    if (!d_workspace || workspace_bytes < w.bytes) return GF_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(d_workspace) & 255) != 0) return GF_EINVAL;
+    if (flow->shape.nd == 3)
+        return forward_train<3>(flow, B, seed, counter0, d_z_in, d_phi_out, d_logq_out, w, stream);
+    return forward_train<2>(flow, B, seed, counter0, d_z_in, d_phi_out, d_logq_out, w, stream);
+}
+
+gf_status gf_flow_backward(const gf_flow* flow, int64_t B, const float* d_gphi, const double* d_glogq,
+                           float* d_grad_out, void* d_workspace, size_t workspace_bytes, cudaStream_t stream) {
+    if (!flow || B <= 0 || !d_grad_out) return GF_EINVAL;
+    const TrainWs w = carve(flow, B, static_cast<char*>(d_workspace));
+    if (!d_workspace || workspace_bytes < w.bytes) return GF_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(d_workspace) & 255) != 0) return GF_EINVAL;
+    if (flow->shape.nd == 3) return backward<3>(flow, B, d_gphi, d_glogq, d_grad_out, w, stream);
+    return backward<2>(flow, B, d_gphi, d_glogq, d_grad_out, w, stream);
 }
 
 size_t gf_unfused_workspace_bytes(const gf_flow* flow, int64_t B) {

@@ -7,29 +7,9 @@ import numpy as np
 import pytest
 
 import gf_inputs as gi
-from gpu_util import assert_logw_close, require_gpu
+from gpu_util import assert_grad_close, assert_logw_close, require_gpu
 
 pytestmark = pytest.mark.gpu
-
-
-def assert_grad_close(g, ref):
-    """Relative L2 error <= 1e-3, and per entry |a-b| <= max(1e-2 |b|, 1e-4 max|b|).
-
-    The absolute floor is a fraction of the largest gradient entry because the
-    reverse pass runs in FP32 through every coupling layer: the rounding error
-    carried by the adjoint of x grows with the gradient's overall scale, so an
-    entry that is small only through cancellation keeps an error of that scale.
-    """
-    g = np.asarray(g, dtype=np.float64)
-    ref = np.asarray(ref, dtype=np.float64)
-    rel = np.linalg.norm(g - ref) / max(np.linalg.norm(ref), 1e-300)
-    assert rel <= 1e-3, f"relative L2 gradient error {rel:.3e}"
-    bound = np.maximum(1e-2 * np.abs(ref), 1e-4 * np.abs(ref).max())
-    ratio = np.abs(g - ref) / bound
-    i = int(np.argmax(ratio))
-    assert ratio[i] <= 1.0, (f"{(ratio > 1).sum()} gradient entries out of tolerance; worst {i}: "
-                             f"gpu={g[i]!r} ref={ref[i]!r} bound={bound[i]!r}")
-    return rel
 
 
 CASES = [
