@@ -88,6 +88,11 @@ def lib():
                                          _D, _D, _D, C.c_int32]
         L.gfo_adam.argtypes = [C.c_int64, _D, _D, _D, _D, C.c_int64, C.c_double, C.c_double,
                                C.c_double, C.c_double]
+        L.gfo_observables.argtypes = [C.c_int32, C.c_int32, C.c_int64, _D, _D, _D]
+        L.gfo_autocorr.argtypes = [C.c_int64, _D, C.c_int32, _D]
+        L.gfo_tau_int.argtypes = [C.c_int64, _D, C.c_int32, C.c_double, _D]
+        L.gfo_ess.argtypes = [C.c_int64, _D]
+        L.gfo_ess.restype = C.c_double
         _lib = L
     return _lib
 
@@ -252,3 +257,33 @@ def adam(theta, g, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
     for a in (theta, g, m, v):
         assert a.dtype == np.float64 and a.flags.c_contiguous
     lib().gfo_adam(theta.size, _p(theta), _p(g), _p(m), _p(v), t, lr, beta1, beta2, eps)
+
+
+def observables(nd, L, phi):
+    """(M [B], C [B][L]) of fields phi [B][V] (see gfo_observables)."""
+    phi = _f64(np.atleast_2d(phi))
+    B = phi.shape[0]
+    M = np.zeros(B)
+    Cc = np.zeros((B, L))
+    lib().gfo_observables(nd, L, B, _p(phi), _p(M), _p(Cc))
+    return M, Cc
+
+
+def autocorr(y, t_max):
+    y = _f64(y)
+    g = np.zeros(t_max + 1)
+    lib().gfo_autocorr(y.size, _p(y), t_max, _p(g))
+    return g
+
+
+def tau_int(n, gamma, c=5.0):
+    """(tau_int, W, error) from Gamma(0..t_max) of a series of length n."""
+    gamma = _f64(gamma)
+    out = np.zeros(3)
+    lib().gfo_tau_int(n, _p(gamma), gamma.size - 1, c, _p(out))
+    return float(out[0]), int(out[1]), float(out[2])
+
+
+def ess(logw):
+    logw = _f64(logw)
+    return float(lib().gfo_ess(logw.size, _p(logw)))

@@ -637,3 +637,87 @@ void gfo_adam(int64_t n, double* theta, const double* g, double* m, double* v, i
         theta[i] -= lr * mh / (sqrt(vh) + eps);
     }
 }
+
+/* ------------------------------------------------------------------------ */
+/* Observables of the Markov chain (Sec. 1: expectation values as chain     */
+/* averages, the autocorrelation time tau_ac with N_indep = N_conf/(2 tau); */
+/* Sec. 3: condensate, zero-momentum two-point function, ESS).              */
+/* ------------------------------------------------------------------------ */
+
+/* Per configuration b: M[b] = (1/V) sum_n phi(n) and, for t = 0..L-1,
+ * C[b][t] = (1/V) sum_tau Phi(tau) Phi(tau + t mod L), where Phi(tau) is the
+ * sum of phi over the sites whose outermost coordinate (y in 2D, z in 3D) is
+ * tau.  Either output may be NULL. */
+void gfo_observables(int32_t nd, int32_t L, int64_t B, const double* phi, double* M, double* C) {
+    int64_t V = ipow(L, nd);
+    double* Phi = (double*)malloc(sizeof(double) * L);
+    for (int64_t b = 0; b < B; ++b) {
+        const double* p = phi + b * V;
+        double m = 0.0;
+        for (int tau = 0; tau < L; ++tau) Phi[tau] = 0.0;
+        for (int64_t n = 0; n < V; ++n) {
+            int c[3]; coords(nd, L, n, c);
+            Phi[c[nd - 1]] += p[n];
+            m += p[n];
+        }
+        if (M) M[b] = m / (double)V;
+        if (C) {
+            for (int t = 0; t < L; ++t) {
+                double acc = 0.0;
+                for (int tau = 0; tau < L; ++tau) acc += Phi[tau] * Phi[(tau + t) % L];
+                C[b * L + t] = acc / (double)V;
+            }
+        }
+    }
+    free(Phi);
+}
+
+/* Gamma(t) = 1/(n-t) sum_{k=0}^{n-t-1} (y_k - ybar)(y_{k+t} - ybar) for
+ * t = 0..t_max (t_max < n), ybar the mean of y.  Evaluated on d_k = y_k - y_0
+ * (the same deviations from the mean), so that a constant series gives
+ * exactly zero. */
+void gfo_autocorr(int64_t n, const double* y, int32_t t_max, double* gamma) {
+    double dbar = 0.0;
+    for (int64_t k = 0; k < n; ++k) dbar += y[k] - y[0];
+    dbar /= (double)n;
+    for (int32_t t = 0; t <= t_max; ++t) {
+        double acc = 0.0;
+        for (int64_t k = 0; k + t < n; ++k) acc += ((y[k] - y[0]) - dbar) * ((y[k + t] - y[0]) - dbar);
+        gamma[t] = acc / (double)(n - t);
+    }
+}
+
+/* Integrated autocorrelation time with the automatic window of Madras and
+ * Sokal: tau(W) = 1/2 + sum_{t=1}^{W} Gamma(t)/Gamma(0); W is the smallest
+ * W >= 1 with W >= c * tau(W), else t_max.  out = {tau(W), W, tau(W) *
+ * sqrt((4W + 2)/n)} (the last is their error estimate).  A constant series
+ * (Gamma(0) = 0) gives {1/2, 0, 0}. */
+void gfo_tau_int(int64_t n, const double* gamma, int32_t t_max, double c, double out[3]) {
+    if (!(gamma[0] > 0.0)) { out[0] = 0.5; out[1] = 0.0; out[2] = 0.0; return; }
+    double tau = 0.5;
+    int32_t W = t_max;
+    for (int32_t w = 1; w <= t_max; ++w) {
+        tau += gamma[w] / gamma[0];
+        if ((double)w >= c * tau) { W = w; break; }
+    }
+    out[0] = tau;
+    out[1] = (double)W;
+    out[2] = tau * sqrt((4.0 * W + 2.0) / (double)n);
+}
+
+/* Effective sample size fraction of importance weights w_k = exp(logw_k):
+ * (sum w)^2 / (n sum w^2), evaluated with the largest log w factored out.
+ * Returns 0 when n == 0 or every weight is zero. */
+double gfo_ess(int64_t n, const double* logw) {
+    if (n <= 0) return 0.0;
+    double mx = -INFINITY;
+    for (int64_t k = 0; k < n; ++k) if (logw[k] > mx) mx = logw[k];
+    if (!(mx > -INFINITY)) return 0.0;
+    double s1 = 0.0, s2 = 0.0;
+    for (int64_t k = 0; k < n; ++k) {
+        const double w = exp(logw[k] - mx);
+        s1 += w;
+        s2 += w * w;
+    }
+    return s1 * s1 / ((double)n * s2);
+}

@@ -19,6 +19,9 @@
  *   - Metropolis-Hastings test   : Sec. 1, the flow proposals corrected by the
  *                                   MH test with the Jacobian
  *   - HMC                        : Sec. 2.2 (HMC for the same theory)
+ *   - chain observables          : Sec. 1 (chain averages, tau_ac, N_indep)
+ *                                   and Sec. 3 (condensate, zero-momentum
+ *                                   two-point function, ESS)
  *
  * Readings where the paper is silent (sign convention, parity order, tap
  * order, activation, uniform construction, MH tie rule, leapfrog form) are
@@ -126,6 +129,18 @@ int gfo_flow_loss_grad(const gfo_shape* sh, const double* w, double m2, double l
 /* Adam (Kingma & Ba), in place; t is the 1-based step count. */
 void gfo_adam(int64_t n, double* theta, const double* g, double* m, double* v, int64_t t,
               double lr, double beta1, double beta2, double eps);
+
+/* Chain observables (Sec. 1: chain averages and tau_ac; Sec. 3: condensate,
+ * zero-momentum two-point function, ESS).  Per configuration:
+ * M[b] = mean of phi; C[b][t] = (1/V) sum_tau Phi(tau) Phi(tau+t), Phi(tau) =
+ * sum of phi over the slice at outermost coordinate tau.  Outputs nullable. */
+void gfo_observables(int32_t nd, int32_t L, int64_t B, const double* phi, double* M, double* C);
+/* Gamma(t), t = 0..t_max, of the series y (mean subtracted, 1/(n-t) normalised). */
+void gfo_autocorr(int64_t n, const double* y, int32_t t_max, double* gamma);
+/* out = {tau_int, W, error}: Madras-Sokal automatic window with constant c. */
+void gfo_tau_int(int64_t n, const double* gamma, int32_t t_max, double c, double out[3]);
+/* ESS fraction (sum w)^2 / (n sum w^2) of w = exp(logw). */
+double gfo_ess(int64_t n, const double* logw);
 
 #ifdef __cplusplus
 }
