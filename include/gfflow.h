@@ -255,6 +255,47 @@ gf_status gf_flow_backward(const gf_flow* flow, int64_t B, const float* d_gphi, 
                            cudaStream_t stream);
 
 /* ---------------------------------------------------------------------- */
+/* Observables of the chain (Sec. 1: expectation values as chain averages, */
+/* the autocorrelation time tau_ac and N_indep = N_conf / (2 tau_ac);      */
+/* Sec. 3: condensate, zero-momentum two-point function, ESS)              */
+/* ---------------------------------------------------------------------- */
+
+#define GF_OBS_MAX_L 4096
+
+/* Per configuration of d_phi [B][L^nd] FP32: d_M_out[b] = (1/V) sum_n
+ * phi_b(n) (the magnetisation; the condensate is the chain average of |M|)
+ * and d_C_out[b][t], t < L: (1/V) sum_tau Phi_b(tau) Phi_b(tau + t mod L),
+ * Phi_b(tau) = sum of phi_b over the sites whose outermost coordinate (y in
+ * 2D, z in 3D) is tau -- the zero-momentum two-point function of one
+ * configuration.  FP64 outputs; either may be NULL (not both).  L <=
+ * GF_OBS_MAX_L. */
+gf_status gf_observables(int32_t nd, int32_t L, int64_t B, const float* d_phi, double* d_M_out,
+                         double* d_C_out, cudaStream_t stream);
+
+/* The chain's series of a per-proposal observable: d_out[k][j] =
+ * d_values[(d_chain_idx[k] - idx0) * width + j] for k < n, j < width, where
+ * d_chain_idx is gf_mh_chain's output and row r of d_values belongs to
+ * proposal idx0 + r (n_values rows).  An index outside the rows writes NaN
+ * and records GF_EINVAL in the device status word. */
+gf_status gf_chain_gather(int64_t n, const int64_t* d_chain_idx, int64_t idx0, int64_t n_values,
+                          const double* d_values, int32_t width, double* d_out, cudaStream_t stream);
+
+/* Autocorrelation of the series d_y [n] FP64: d_gamma_out[t] = 1/(n-t)
+ * sum_{k<n-t} (y_k - ybar)(y_{k+t} - ybar) for t = 0..t_max (t_max < n),
+ * and d_tau_out[4] = {tau_int, W, error, ybar}: tau_int = 1/2 +
+ * sum_{t=1}^{W} Gamma(t)/Gamma(0) with the automatic window of Madras and
+ * Sokal (the smallest W >= 1 with W >= c_window * tau_int(W), else t_max),
+ * error = tau_int sqrt((4W+2)/n).  A constant series gives {1/2, 0, 0, y0}.
+ * N_indep = n / (2 tau_int). */
+gf_status gf_autocorr(int64_t n, const double* d_y, int32_t t_max, double c_window,
+                      double* d_gamma_out, double* d_tau_out, cudaStream_t stream);
+
+/* Effective sample size fraction of the importance weights w = exp(logw)
+ * of d_logw [n]: *d_ess_out = (sum w)^2 / (n sum w^2), 0 when n == 0 or all
+ * weights vanish.  FP64. */
+gf_status gf_ess(int64_t n, const double* d_logw, double* d_ess_out, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------- */
 /* Status                                                                  */
 /* ---------------------------------------------------------------------- */
 

@@ -6,7 +6,8 @@ reverse-KL training step and the FP64 HMC comparison sampler.  The CUDA
 library libgfflow.so (C ABI: include/gfflow.h) does all the arithmetic; this
 package is its ctypes/torch binding.
 """
-from .api import (Flow, SampleResult, device_status, hmc_trajectory, mh_chain,  # noqa: F401
+from .api import (Flow, SampleResult, autocorr, chain_gather, device_status, ess,  # noqa: F401
+                  hmc_trajectory, mh_chain, observables,
                   mh_chain_noalloc,
                   mh_chain_workspace_bytes, new_mh_state, phi4_action, phi4_action_vjp,
                   phi4_force, read_mh_state)

@@ -12,6 +12,7 @@ from . import build as _build
 
 GF_OK, GF_EINVAL, GF_ENOMEM, GF_ECUDA, GF_EUNSUPPORTED, GF_ETIMEOUT, GF_EDEVICE = 0, -1, -2, -3, -4, -5, -6
 GF_PREC_FP32, GF_PREC_BF16CONV_FP64RED = 0, 1
+GF_OBS_MAX_L = 4096
 GF_MH_NOALLOC_MAX_N = 131072     # include/gfflow.h
 
 EXPORTED = [
@@ -21,7 +22,8 @@ EXPORTED = [
     "gf_phi4_force", "gf_mh_chain_workspace_bytes", "gf_mh_chain", "gf_mh_chain_noalloc",
     "gf_hmc_trajectory",
     "gf_train_workspace_bytes", "gf_flow_train_step", "gf_flow_forward_train", "gf_flow_backward",
-    "gf_phi4_action_vjp", "gf_device_status", "gf_status_string",
+    "gf_phi4_action_vjp", "gf_observables", "gf_chain_gather", "gf_autocorr", "gf_ess",
+    "gf_device_status", "gf_status_string",
 ]
 
 
@@ -91,6 +93,10 @@ def load():
         "gf_flow_forward_train": ([_VP, _I64, _U64, _U64, _VP, _VP, _VP, _VP, _SZ, _VP], _I32),
         "gf_flow_backward": ([_VP, _I64, _VP, _VP, _VP, _VP, _SZ, _VP], _I32),
         "gf_phi4_action_vjp": ([_I32, _I32, C.POINTER(Phi4C), _I64, _VP, _VP, _VP, _VP], _I32),
+        "gf_observables": ([_I32, _I32, _I64, _VP, _VP, _VP, _VP], _I32),
+        "gf_chain_gather": ([_I64, _VP, _I64, _I64, _VP, _I32, _VP, _VP], _I32),
+        "gf_autocorr": ([_I64, _VP, _I32, _F64, _VP, _VP, _VP], _I32),
+        "gf_ess": ([_I64, _VP, _VP, _VP], _I32),
         "gf_device_status": ([_VP, C.POINTER(_I32)], _I32),
         "gf_status_string": ([_I32], C.c_char_p),
     }

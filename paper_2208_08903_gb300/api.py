@@ -321,6 +321,48 @@ def hmc_trajectory(nd: int, L: int, phi4, phi: torch.Tensor, n_steps: int, eps: 
     return dH, acc
 
 
+def observables(nd: int, L: int, phi: torch.Tensor, magnetisation: bool = True,
+                two_point: bool = True):
+    """(M [B] FP64 or None, C [B][L] FP64 or None) of FP32 fields phi [B][V]."""
+    B = phi.shape[0]
+    _need(phi, torch.float32, "phi", B * L**nd)
+    M = torch.empty(B, device=phi.device, dtype=torch.float64) if magnetisation else None
+    Cc = torch.empty(B, L, device=phi.device, dtype=torch.float64) if two_point else None
+    _abi.check("gf_observables", _abi.load().gf_observables(nd, L, B, _ptr(phi), _ptr(M), _ptr(Cc),
+                                                            _stream()))
+    return M, Cc
+
+
+def chain_gather(chain_idx: torch.Tensor, values: torch.Tensor, idx0: int = 0) -> torch.Tensor:
+    """values[chain_idx - idx0] (rows of an FP64 [n_values] or [n_values][width] tensor)."""
+    _need(chain_idx, torch.int64, "chain_idx")
+    _need(values, torch.float64, "values")
+    n = chain_idx.numel()
+    width = 1 if values.dim() == 1 else values.shape[1]
+    out = torch.empty((n,) + tuple(values.shape[1:]), device=values.device, dtype=torch.float64)
+    _abi.check("gf_chain_gather", _abi.load().gf_chain_gather(
+        n, _ptr(chain_idx), idx0, values.shape[0], _ptr(values), width, _ptr(out), _stream()))
+    return out
+
+
+def autocorr(y: torch.Tensor, t_max: int, c_window: float = 5.0):
+    """(Gamma [t_max+1], summary [4] = {tau_int, W, error, mean}) of an FP64 series."""
+    _need(y, torch.float64, "y")
+    gamma = torch.empty(t_max + 1, device=y.device, dtype=torch.float64)
+    summ = torch.empty(4, device=y.device, dtype=torch.float64)
+    _abi.check("gf_autocorr", _abi.load().gf_autocorr(y.numel(), _ptr(y), t_max, float(c_window),
+                                                      _ptr(gamma), _ptr(summ), _stream()))
+    return gamma, summ
+
+
+def ess(logw: torch.Tensor) -> torch.Tensor:
+    """ESS fraction (sum w)^2 / (n sum w^2) of w = exp(logw), as an FP64 [1] tensor."""
+    _need(logw, torch.float64, "logw")
+    out = torch.empty(1, device=logw.device, dtype=torch.float64)
+    _abi.check("gf_ess", _abi.load().gf_ess(logw.numel(), _ptr(logw), _ptr(out), _stream()))
+    return out
+
+
 def device_status(stream=None) -> int:
     v = C.c_int32(0)
     _abi.check("gf_device_status", _abi.load().gf_device_status(_stream(stream), C.byref(v)))

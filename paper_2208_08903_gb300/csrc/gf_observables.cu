@@ -1,0 +1,236 @@
+// gf_observables.cu -- observables of the flow / MH chain on the device
+// (paper arXiv:2208.08903 Sec. 1: expectation values as chain averages, the
+// autocorrelation time tau_ac with N_indep = N_conf / (2 tau_ac); Sec. 3: the
+// condensate, the zero-momentum two-point function and the effective sample
+// size of the analysis tools).
+//
+//  - per configuration: M = mean of phi and C(t) = (1/V) sum_tau Phi(tau)
+//    Phi(tau + t), Phi(tau) = sum of phi over the slice at outermost
+//    coordinate tau.  A slice is V/L contiguous sites, so one warp sums one
+//    slice with coalesced 16-byte loads (FP64 accumulation); the kernel reads
+//    each field once and is HBM-bound.
+//  - chain gather: the chain's series O[chain_idx[k]] of a per-proposal
+//    observable.
+//  - Gamma(t) of a series (one CTA per lag, fixed-order FP64 reduction), then
+//    the Madras-Sokal automatic window for tau_int in one thread.
+//  - ESS fraction (sum w)^2 / (n sum w^2) of w = exp(log w), the largest
+//    log w factored out.
+#include <algorithm>
+#include <cmath>
+
+#include "gf_common.cuh"
+
+namespace gf {
+namespace {
+
+constexpr int kObsThreads = 256;
+constexpr int kRedThreads = 1024;
+
+// One CTA per configuration (grid-stride).  Dynamic shared memory: L doubles.
+__global__ void __launch_bounds__(kObsThreads) obs_kernel(int L, int64_t V, int64_t B, const float* __restrict__ phi,
+                                                         double* __restrict__ M, double* __restrict__ C) {
+    extern __shared__ double Phi[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int64_t S = V / L;
+    for (int64_t b = blockIdx.x; b < B; b += gridDim.x) {
+        const float* p = phi + b * V;
+        const bool vec = (S % 4 == 0) && ((reinterpret_cast<uintptr_t>(p) & 15) == 0);
+        for (int tau = wid; tau < L; tau += nw) {
+            const float* q = p + (int64_t)tau * S;
+            double acc = 0.0;
+            if (vec) {
+                const float4* q4 = reinterpret_cast<const float4*>(q);
+                for (int64_t i = lane; i < S / 4; i += 32) {
+                    const float4 v = __ldg(q4 + i);
+                    acc += ((double)v.x + (double)v.y) + ((double)v.z + (double)v.w);
+                }
+            } else {
+                for (int64_t i = lane; i < S; i += 32) acc += (double)__ldg(q + i);
+            }
+            acc = warp_sum(acc);
+            if (lane == 0) Phi[tau] = acc;
+        }
+        __syncthreads();
+        if (M && threadIdx.x == 0) {
+            double m = 0.0;
+            for (int tau = 0; tau < L; ++tau) m += Phi[tau];
+            M[b] = m / (double)V;
+        }
+        if (C) {
+            for (int t = threadIdx.x; t < L; t += blockDim.x) {
+                double acc = 0.0;
+                for (int tau = 0, u = t; tau < L; ++tau, u = (u + 1 == L) ? 0 : u + 1) acc += Phi[tau] * Phi[u];
+                C[b * L + t] = acc / (double)V;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// out[k][j] = values[(chain_idx[k] - idx0) * width + j]; an index outside
+// [0, n_values) writes NaN and records GF_EINVAL in the status word.
+__global__ void gather_kernel(int64_t n, const int64_t* __restrict__ chain_idx, int64_t idx0, int64_t n_values,
+                              const double* __restrict__ values, int width, double* __restrict__ out,
+                              int32_t* status) {
+    const int64_t total = n * width;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = i / width;
+        const int j = (int)(i - k * width);
+        const int64_t r = chain_idx[k] - idx0;
+        if (r < 0 || r >= n_values) {
+            out[i] = __longlong_as_double(0x7ff8000000000000ll);
+            set_status(status, GF_EINVAL);
+        } else {
+            out[i] = values[r * width + j];
+        }
+    }
+}
+
+// dbar = mean of (y_k - y_0), one block, fixed order.  Stored in out[3].
+__global__ void __launch_bounds__(kRedThreads) mean_dev_kernel(int64_t n, const double* __restrict__ y,
+                                                              double* __restrict__ out) {
+    __shared__ double red[32];
+    const double y0 = y[0];
+    double acc = 0.0;
+    for (int64_t k = threadIdx.x; k < n; k += blockDim.x) acc += y[k] - y0;
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0) out[3] = acc / (double)n;
+}
+
+// Gamma(t) for t = blockIdx.x (grid-stride over lags).
+__global__ void __launch_bounds__(kObsThreads) gamma_kernel(int64_t n, const double* __restrict__ y, int t_max,
+                                                           const double* __restrict__ stats,
+                                                           double* __restrict__ gamma) {
+    __shared__ double red[32];
+    const double y0 = y[0], dbar = stats[3];
+    for (int t = blockIdx.x; t <= t_max; t += gridDim.x) {
+        double acc = 0.0;
+        for (int64_t k = threadIdx.x; k + t < n; k += blockDim.x)
+            acc += ((y[k] - y0) - dbar) * ((y[k + t] - y0) - dbar);
+        acc = block_sum(acc, red);
+        if (threadIdx.x == 0) gamma[t] = acc / (double)(n - t);
+        __syncthreads();
+    }
+}
+
+// Madras-Sokal window and the summary {tau, W, error, mean}; one thread.
+__global__ void window_kernel(int64_t n, const double* __restrict__ y, const double* __restrict__ gamma, int t_max,
+                              double c, double* __restrict__ out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const double mean = y[0] + out[3];
+    if (!(gamma[0] > 0.0)) {
+        out[0] = 0.5; out[1] = 0.0; out[2] = 0.0; out[3] = mean;
+        return;
+    }
+    double tau = 0.5;
+    int W = t_max;
+    for (int w = 1; w <= t_max; ++w) {
+        tau += gamma[w] / gamma[0];
+        if ((double)w >= c * tau) { W = w; break; }
+    }
+    out[0] = tau;
+    out[1] = (double)W;
+    out[2] = tau * sqrt((4.0 * W + 2.0) / (double)n);
+    out[3] = mean;
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// ESS fraction in one block: max, then sum w and sum w^2 in a fixed order.
+__global__ void __launch_bounds__(kRedThreads) ess_kernel(int64_t n, const double* __restrict__ logw,
+                                                         double* __restrict__ out) {
+    __shared__ double red[32];
+    __shared__ double mx_s;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    double mx = -INFINITY;
+    for (int64_t k = threadIdx.x; k < n; k += blockDim.x) mx = fmax(mx, logw[k]);
+    mx = warp_max(mx);
+    if (lane == 0) red[wid] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = -INFINITY;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) m = fmax(m, red[i]);
+        mx_s = m;
+    }
+    __syncthreads();
+    mx = mx_s;
+    if (!(mx > -INFINITY)) {                       // n == 0 or all weights zero
+        if (threadIdx.x == 0) *out = 0.0;
+        return;
+    }
+    double s1 = 0.0, s2 = 0.0;
+    for (int64_t k = threadIdx.x; k < n; k += blockDim.x) {
+        const double w = exp(logw[k] - mx);
+        s1 += w;
+        s2 += w * w;
+    }
+    s1 = block_sum(s1, red);
+    s2 = block_sum(s2, red);
+    if (threadIdx.x == 0) *out = s1 * s1 / ((double)n * s2);
+}
+
+int64_t ipow(int64_t a, int e) {
+    int64_t r = 1;
+    while (e-- > 0) r *= a;
+    return r;
+}
+
+}  // namespace
+}  // namespace gf
+
+using namespace gf;
+
+extern "C" {
+
+gf_status gf_observables(int32_t nd, int32_t L, int64_t B, const float* d_phi, double* d_M_out, double* d_C_out,
+                         cudaStream_t stream) {
+    if ((nd != 2 && nd != 3) || L < 1 || L > GF_OBS_MAX_L || B < 0) return GF_EINVAL;
+    if (B > 0 && (!d_phi || (!d_M_out && !d_C_out))) return GF_EINVAL;
+    if (B == 0) return GF_OK;
+    const int64_t V = ipow(L, nd);
+    const size_t smem = sizeof(double) * (size_t)L;
+    const unsigned grid = (unsigned)std::min<int64_t>(B, (int64_t)num_sms() * 8);
+    obs_kernel<<<grid, kObsThreads, smem, stream>>>(L, V, B, d_phi, d_M_out, d_C_out);
+    GF_CHECK_LAUNCH();
+    return GF_OK;
+}
+
+gf_status gf_chain_gather(int64_t n, const int64_t* d_chain_idx, int64_t idx0, int64_t n_values,
+                          const double* d_values, int32_t width, double* d_out, cudaStream_t stream) {
+    if (n < 0 || width < 1 || n_values < 0) return GF_EINVAL;
+    if (n > 0 && (!d_chain_idx || !d_values || !d_out)) return GF_EINVAL;
+    if (n == 0) return GF_OK;
+    const int64_t total = n * width;
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, num_sms() * 16LL));
+    gather_kernel<<<grid, 256, 0, stream>>>(n, d_chain_idx, idx0, n_values, d_values, width, d_out, status_word());
+    GF_CHECK_LAUNCH();
+    return GF_OK;
+}
+
+gf_status gf_autocorr(int64_t n, const double* d_y, int32_t t_max, double c_window, double* d_gamma_out,
+                      double* d_tau_out, cudaStream_t stream) {
+    if (n < 1 || t_max < 0 || t_max >= n || !(c_window > 0.0)) return GF_EINVAL;
+    if (!d_y || !d_gamma_out || !d_tau_out) return GF_EINVAL;
+    mean_dev_kernel<<<1, kRedThreads, 0, stream>>>(n, d_y, d_tau_out);
+    GF_CHECK_LAUNCH();
+    const unsigned grid = (unsigned)std::min<int64_t>((int64_t)t_max + 1, (int64_t)num_sms() * 8);
+    gamma_kernel<<<grid, kObsThreads, 0, stream>>>(n, d_y, t_max, d_tau_out, d_gamma_out);
+    GF_CHECK_LAUNCH();
+    window_kernel<<<1, 32, 0, stream>>>(n, d_y, d_gamma_out, t_max, c_window, d_tau_out);
+    GF_CHECK_LAUNCH();
+    return GF_OK;
+}
+
+gf_status gf_ess(int64_t n, const double* d_logw, double* d_ess_out, cudaStream_t stream) {
+    if (n < 0 || !d_ess_out || (n > 0 && !d_logw)) return GF_EINVAL;
+    ess_kernel<<<1, kRedThreads, 0, stream>>>(n, d_logw, d_ess_out);
+    GF_CHECK_LAUNCH();
+    return GF_OK;
+}
+
+}  // extern "C"
