@@ -4,12 +4,25 @@ for epoch in epochs: for it in iterations: draw a batch from the prior, take
 the gradient of the shifted reverse KL loss, apply Adam -- each iteration is
 one gf_flow_train_step call (forward with saved layer inputs, hand-written
 backward, Adam on the device).  Prior counters advance with every iteration,
-so a run is reproducible from (seed, epochs, iterations, batch).
+so a run is reproducible from (seed, epochs, iterations, batch), and a run
+resumed from a checkpoint continues bit for bit where it stopped.
+
+The paper's training settings (Sec. 3, the example configuration) map to:
+seed -> `seed`, batchsize -> `batch`, epochs / iterations, base_lr -> `lr`,
+opt = Adam, lr_scheduler -> `lr_schedule` (a function of the 1-based step;
+None = constant), pretrained -> `load_checkpoint` + `state=`.
+
+Command line (trains, checkpoints, evaluates acceptance and ESS per epoch):
+    python -m paper_2208_08903_gb300.train --workload c1 --epochs 200 --iterations 100
 """
 from __future__ import annotations
 
+import argparse
 import dataclasses
+import json
+import time
 
+import numpy as np
 import torch
 
 from . import api
@@ -30,9 +43,10 @@ def new_state(flow: api.Flow) -> TrainState:
 
 def train(flow: api.Flow, phi4, epochs: int, iterations: int, batch: int, lr: float = 1e-3,
           seed: int = 12345, state: TrainState | None = None, record_every: int = 1,
-          betas=(0.9, 0.999), eps: float = 1e-8) -> TrainState:
+          betas=(0.9, 0.999), eps: float = 1e-8, lr_schedule=None) -> TrainState:
     """Runs epochs x iterations Adam steps of the reverse-KL loss; returns the
-    state (step count, Adam moments, recorded losses) so training can resume."""
+    state (step count, Adam moments, recorded losses) so training can resume.
+    lr_schedule(step) -> learning rate overrides `lr` when given."""
     st = state or new_state(flow)
     dev = st.adam_m.device
     ws = torch.empty(max(flow.train_workspace_bytes(batch), 1), device=dev, dtype=torch.uint8)
@@ -40,7 +54,8 @@ def train(flow: api.Flow, phi4, epochs: int, iterations: int, batch: int, lr: fl
     for _ in range(epochs):
         for _ in range(iterations):
             st.step += 1
-            loss, _ = flow.train_step(batch, phi4, seed=seed, counter0=st.step * batch, lr=lr,
+            step_lr = lr if lr_schedule is None else float(lr_schedule(st.step))
+            loss, _ = flow.train_step(batch, phi4, seed=seed, counter0=st.step * batch, lr=step_lr,
                                       adam_m=st.adam_m, adam_v=st.adam_v, adam_t=st.step,
                                       beta1=betas[0], beta2=betas[1], adam_eps=eps, grad=False,
                                       workspace=ws)
@@ -49,3 +64,112 @@ def train(flow: api.Flow, phi4, epochs: int, iterations: int, batch: int, lr: fl
     if pending:
         st.losses.extend(torch.cat(pending).cpu().tolist())
     return st
+
+
+def save_checkpoint(path: str, flow: api.Flow, state: TrainState, **meta) -> None:
+    """Writes the flow's FP32 weights, the Adam moments, the step count, the
+    recorded losses, the flow shape and any extra metadata to an .npz file."""
+    sh = flow.shape
+    np.savez(path,
+             weights=flow.get_weights().cpu().numpy(),
+             adam_m=state.adam_m.cpu().numpy(), adam_v=state.adam_v.cpu().numpy(),
+             step=np.int64(state.step), losses=np.asarray(state.losses, dtype=np.float64),
+             shape=np.array([sh.nd, sh.L, sh.n_layers, sh.c1, sh.c2, int(bool(sh.use_final_tanh))],
+                            dtype=np.int64),
+             leaky_slope=np.float64(sh.leaky_slope),
+             meta=json.dumps(meta))
+
+
+def load_checkpoint(path: str, flow: api.Flow) -> tuple[TrainState, dict]:
+    """Loads a checkpoint into `flow` (shapes must match) and returns the
+    training state to pass to `train(state=...)` and the stored metadata."""
+    z = np.load(path)
+    sh = flow.shape
+    want = [sh.nd, sh.L, sh.n_layers, sh.c1, sh.c2, int(bool(sh.use_final_tanh))]
+    if z["shape"].tolist() != want or float(z["leaky_slope"]) != float(sh.leaky_slope):
+        raise ValueError(f"checkpoint shape {z['shape'].tolist()} does not match the flow {want}")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    flow.set_weights(torch.tensor(z["weights"], dtype=torch.float32, device=dev))
+    st = TrainState(int(z["step"]), torch.tensor(z["adam_m"], device=dev), torch.tensor(z["adam_v"], device=dev),
+                    z["losses"].tolist())
+    return st, json.loads(str(z["meta"]))
+
+
+def evaluate(flow: api.Flow, phi4, n_proposals: int, batch: int, seed: int, counter0: int = 0,
+             mh_seed: int = 1, sampler: str = "fused") -> dict:
+    """Acceptance of an MH independence chain over n_proposals flow samples,
+    the ESS fraction of their importance weights and the chain average of
+    |M| with its integrated autocorrelation time (all on the device).
+    sampler: "fused" (gf_flow_sample) or "unfused" (one kernel per conv)."""
+    st = api.new_mh_state(mh_seed)
+    lws, Ms, idxs = [], [], []
+    ws = None
+    for i in range(0, n_proposals, batch):
+        b = min(batch, n_proposals - i)
+        if sampler == "fused":
+            r = flow.sample(b, seed=seed, counter0=counter0 + i, phi4=phi4)
+        else:
+            if ws is None:
+                ws = torch.empty(flow.unfused_workspace_bytes(batch), device="cuda", dtype=torch.uint8)
+            r = flow.sample_unfused(b, seed=seed, counter0=counter0 + i, phi4=phi4, workspace=ws)
+        idx, _ = api.mh_chain(st, r.logw)
+        M, _ = api.observables(flow.shape.nd, flow.shape.L, r.phi, two_point=False)
+        lws.append(r.logw)
+        Ms.append(M)
+        idxs.append(idx)
+    logw = torch.cat(lws)
+    series = api.chain_gather(torch.cat(idxs), torch.cat(Ms)).abs().contiguous()
+    t_max = int(min(1000, max(0, n_proposals - 1)))
+    _, summ = api.autocorr(series, t_max)
+    ess = api.ess(logw)
+    s = api.read_mh_state(st)
+    summ = summ.cpu().tolist()
+    return {"acceptance": s.n_acc / max(1, s.step - 1), "ess": float(ess.item()),
+            "abs_M": summ[3], "tau_int_abs_M": summ[0], "window": int(summ[1]),
+            "proposals": n_proposals}
+
+
+def main(argv=None):
+    import gf_inputs as gi
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--workload", default="c1", choices=["c1", "c2"])
+    ap.add_argument("--epochs", type=int, default=200)
+    ap.add_argument("--iterations", type=int, default=100)
+    ap.add_argument("--batch", type=int, default=0)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--seed", type=int, default=12345)
+    ap.add_argument("--model-seed", type=int, default=2021)
+    ap.add_argument("--checkpoint", default="")
+    ap.add_argument("--resume", default="")
+    ap.add_argument("--eval-proposals", type=int, default=16384)
+    ap.add_argument("--eval-every", type=int, default=20)
+    args = ap.parse_args(argv)
+    W = gi.WORKLOADS[args.workload]
+    shape, phi4 = W["shape"], W["phi4"]
+    batch = args.batch or W["batch"]
+    flow = api.Flow(shape, gi.init_weights(shape, seed=args.model_seed))
+    state = None
+    if args.resume:
+        state, _ = load_checkpoint(args.resume, flow)
+    t0 = time.perf_counter()
+    for ep in range(args.epochs):
+        state = train(flow, phi4, 1, args.iterations, batch, lr=args.lr, seed=args.seed, state=state)
+        if (ep + 1) % args.eval_every == 0 or ep + 1 == args.epochs:
+            ev = evaluate(flow, phi4, args.eval_proposals, 4096, seed=args.seed + 1, counter0=state.step << 20)
+            line = {"epoch": ep + 1, "step": state.step, "loss": float(np.mean(state.losses[-args.iterations:])),
+                    "seconds": time.perf_counter() - t0, **ev}
+            print(json.dumps(line), flush=True)
+            if args.checkpoint:
+                save_checkpoint(args.checkpoint, flow, state, workload=args.workload, seed=args.seed,
+                                batch=batch, lr=args.lr)
+    # the fused and the plain (one kernel per convolution) samplers on the same
+    # proposals: the MH decisions, hence the acceptance, must agree
+    same = {}
+    for kind in ("fused", "unfused"):
+        same[kind] = evaluate(flow, phi4, args.eval_proposals, 4096, seed=args.seed + 2, sampler=kind)
+    print(json.dumps({"final": True, "step": state.step, "fused": same["fused"], "unfused": same["unfused"]}),
+          flush=True)
+
+
+if __name__ == "__main__":
+    main()
