@@ -88,7 +88,7 @@ def test_backward_half_is_linear_in_upstream_gradients(orc):
 def test_action_vjp_matches_oracle_force(orc, nd, L):
     torch, P = require_gpu()
     V, B, m2, lam = L**nd, 5, -4.0, 8.0
-    phi = orc.prior(V, B, seed=8, counter0=0, f32=True) * 0.7
+    phi = (orc.prior(V, B, seed=8, counter0=0, f32=True) * 0.7).astype(np.float32).astype(np.float64)
     gS = np.linspace(-1.5, 2.0, B)
     out = P.phi4_action_vjp(nd, L, (m2, lam), torch.tensor(phi, dtype=torch.float32, device="cuda"),
                             torch.tensor(gS, device="cuda"))

@@ -22,7 +22,7 @@ RTOL = 1e-12
 def test_observables_match_oracle(orc, nd, L, B):
     torch, P = require_gpu()
     V = L**nd
-    phi = orc.prior(V, B, seed=21, counter0=0, f32=True) + 0.3
+    phi = (orc.prior(V, B, seed=21, counter0=0, f32=True) + 0.3).astype(np.float32).astype(np.float64)
     M, Cc = P.observables(nd, L, torch.tensor(phi, dtype=torch.float32, device="cuda"))
     torch.cuda.synchronize()
     rM, rC = orc.observables(nd, L, phi)
