@@ -471,6 +471,10 @@ def bench_extra(args, dev, flush, pk):
     t = _time_steps(lambda i: P.ess(y), 5, 2, None)
     out["ess"] = {"ms": float(np.mean(t)), "n": 100000}
 
+    # context: the same flow in eager PyTorch (cuDNN FP32 convolutions, TF32 off)
+    out["torch_eager_fp32_context"] = torch_eager_rate(shape, phi4, w, min(B, 1024), dev, flush)
+    torch.cuda.empty_cache()
+
     # MH chain alone, 100k proposals
     n = 100000
     lw = torch.randn(n, device=dev, dtype=torch.float64) * 2 - 50
@@ -496,7 +500,74 @@ def bench_extra(args, dev, flush, pk):
         P.mh_chain(st1, r1.logw)
     t = _time_steps(c1step, 50, 5, None)
     out["c1_sampling"] = {"configs_per_s": 64 / (float(np.mean(t)) / 1e3), "ms_per_step": float(np.mean(t))}
+    # batch sweep of the c1 flow (fused FP32 sampler + MH): 64 configurations cannot fill 152 SMs
+    sweep = {}
+    for Bs in (64, 1024, 16384, 65536):
+        rs = P.SampleResult(phi=torch.empty(Bs, 64, device=dev), logq=torch.empty(Bs, device=dev, dtype=torch.float64),
+                            S=torch.empty(Bs, device=dev, dtype=torch.float64),
+                            logw=torch.empty(Bs, device=dev, dtype=torch.float64))
+        sts = P.new_mh_state(seed=3, device=dev)
+
+        def sstep(i, Bs=Bs, rs=rs, sts=sts):
+            f1.sample(Bs, seed=4, counter0=Bs * i, phi4=W1["phi4"], out=rs)
+            P.mh_chain(sts, rs.logw)
+        t = _time_steps(sstep, 10, 3, None)
+        sweep[str(Bs)] = Bs / (float(np.mean(t)) / 1e3)
+    out["c1_batch_sweep_configs_per_s"] = sweep
     return out
+
+
+def torch_eager_flow(shape, phi4, w, dev):
+    """The flow (sampling direction, log q, S) written with eager torch ops:
+    circular padding + cuDNN convolutions in FP32.  Returns run(z) -> (phi,
+    log q, S).  A context baseline only; it shares nothing with the library."""
+    import torch
+    import torch.nn.functional as F
+    nd, L, V = shape.nd, shape.L, shape.V
+    conv = F.conv3d if nd == 3 else F.conv2d
+    k = (3,) * nd
+    layers = []
+    for l in range(shape.n_layers):
+        d = gi.split_layer(shape, w, l)
+        t = lambda a, shp: torch.tensor(a, dtype=torch.float32, device=dev).reshape(shp)
+        layers.append((t(d["W1"], (shape.c1, 1) + k), t(d["b1"], (-1,)), t(d["W2"], (shape.c2, shape.c1) + k),
+                       t(d["b2"], (-1,)), t(d["W3"], (2, shape.c2) + k), t(d["b3"], (-1,))))
+    coords = torch.stack(torch.meshgrid(*[torch.arange(L, device=dev)] * nd, indexing="ij"))
+    par = (coords.sum(0) % 2).reshape((1, 1) + (L,) * nd)
+    pad = (1, 1) * nd
+
+    def run(z):
+        x = z.reshape((z.shape[0], 1) + (L,) * nd)
+        logdet = torch.zeros(z.shape[0], device=dev, dtype=torch.float64)
+        for l, (W1, b1, W2, b2, W3, b3) in enumerate(layers):
+            frozen = (par == (l & 1)).float()
+            h = F.leaky_relu(conv(F.pad(x * frozen, pad, mode="circular"), W1, b1), shape.leaky_slope)
+            h = F.leaky_relu(conv(F.pad(h, pad, mode="circular"), W2, b2), shape.leaky_slope)
+            st = conv(F.pad(h, pad, mode="circular"), W3, b3)
+            s = torch.tanh(st[:, :1]) if shape.use_final_tanh else st[:, :1]
+            act = 1.0 - frozen
+            x = x * frozen + act * (x * torch.exp(s) + st[:, 1:])
+            logdet += (s * act).flatten(1).double().sum(1)
+        phi = x.flatten(1)
+        logr = -0.5 * (z.double() ** 2).sum(1) - 0.5 * V * math.log(2 * math.pi)
+        hop = sum(torch.roll(x, -1, dims=2 + a) for a in range(nd)).flatten(1).double()
+        pd = phi.double()
+        S = ((2 * nd + phi4.m2) * pd * pd + phi4.lam * pd ** 4 - 2 * pd * hop).sum(1)
+        return phi, logr - logdet, S
+    return run
+
+
+def torch_eager_rate(shape, phi4, w, B, dev, flush):
+    """Configs/s of torch_eager_flow with TF32 disabled (context figure)."""
+    import torch
+    torch.backends.cudnn.allow_tf32 = False
+    torch.backends.cuda.matmul.allow_tf32 = False
+    run = torch_eager_flow(shape, phi4, w, dev)
+    gen = torch.Generator(device=dev).manual_seed(1)
+    z = torch.randn(B, shape.V, device=dev, generator=gen)
+    t = _time_steps(lambda i: run(z), 3, 1, flush)
+    return {"configs_per_s": B / (float(np.mean(t)) / 1e3), "batch": B, "ms_per_step": float(np.mean(t)),
+            "note": "eager torch, cuDNN FP32 (TF32 off), no MH; context only"}
 
 
 def bench_serving(dev, n_requests=120, rate=200.0, n_models=16, seed=5):
@@ -522,9 +593,9 @@ def bench_serving(dev, n_requests=120, rate=200.0, n_models=16, seed=5):
 
 
 # --------------------------------------------------------------------------- CPU oracle
-def oracle_rate(shape, phi4, n_cfg, seed=2024, counter0=0):
+def oracle_rate(shape, phi4, n_cfg, seed=2024, counter0=0, nthreads=None):
     import oracle
-    nthr = oracle.default_threads()
+    nthr = nthreads or oracle.default_threads()
     w = gi.init_weights(shape, seed=0)
     t0 = time.perf_counter()
     out = oracle.flow_sample(shape, w, phi4.m2, phi4.lam, n_cfg, seed=seed, counter0=counter0,
@@ -547,9 +618,13 @@ def bench_cpu_baseline(args):
     shape, phi4 = W["shape"], W["phi4"]
     n, nthr = cpu_sample_size(shape, phi4, target_s=args.cpu_seconds)
     rate, dt, nthr = oracle_rate(shape, phi4, n, counter0=7)
+    n1 = max(1, n // max(nthr, 1))
+    rate1, dt1, _ = oracle_rate(shape, phi4, n1, counter0=7, nthreads=1)
     return {"value": rate, "unit": "configs/s", "cores": nthr, "kind": "oracle",
+            "single_thread_value": rate1,
             "sample": f"{n} configurations of the same workload (FP64 C oracle, OpenMP over "
-                      f"configurations) + MH over them, {dt:.1f} s"}
+                      f"configurations) + MH over them, {dt:.1f} s; single thread: {n1} "
+                      f"configurations, {dt1:.1f} s"}
 
 
 def bench_reference(args, rank, world):

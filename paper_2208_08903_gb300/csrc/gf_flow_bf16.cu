@@ -23,11 +23,14 @@
 // not gathered: three accumulators P_dx (dx = -1, 0, +1) stay in TMEM and the
 // epilogues form out(x) = sum_dx P_dx(x + dx) with width-16 shuffles (one
 // x-row = one half-warp = 16 TMEM lanes).
-// Pipeline, per virtual slice v: one thread issues conv3 of slice v-2; all
-// warps run conv1 of slice v+2 on the FMA pipes; the thread then queues conv2
-// of slice v+1 into the other of two TMEM buffers, so the tensor cores stay
-// busy while the conv3 epilogue updates slice v-2 and the conv2 epilogue
-// (issued one iteration earlier) writes h2[v].
+// Warp-specialised pipeline within a layer (mbarriers only, no CTA barrier):
+// producer warps run conv1 on the FMA pipes up to four slices ahead (four h1
+// slots); one thread of warp 0 queues conv2 of slice u (into one of two TMEM
+// buffers) and then conv3 of slice u-2 (two TMEM buffers) on the tensor cores;
+// four epilogue warps turn conv2 accumulators into h2 (three slots) and conv3
+// accumulators into the affine update of x.  conv1 reads only fixed sites of
+// x and the update writes only the other parity, so x needs no ordering within
+// a layer; the CTA meets at a barrier between layers.
 #include <algorithm>
 #include <cstring>
 
@@ -57,6 +60,8 @@ constexpr int kTmem3 = 192;                             // conv3 accumulators (2
 constexpr int kTmem2B = 256;                            // second conv2 buffer (2 tiles x 96 columns)
 constexpr int kTmemCols = 512;
 constexpr long long kWaitLimit = 1ll << 22;             // bounded mbarrier wait (iterations)
+constexpr int kProdWarp0 = 4, kProdWarps = 8, kProdThreads = kProdWarps * 32;   // conv1 producers
+constexpr int kEpiWarp0 = 12, kEpiThreads = 4 * 32;                            // epilogue warps 12..15
 
 // ---------------------------------------------------------------- PTX wrappers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -101,21 +106,6 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                  :: "r"(smem_u32(bar)) : "memory");
-}
-// 32 lanes x 32 consecutive FP32 columns: thread i gets row (lane base + i).
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-    uint32_t r[32];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                   "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-                   "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-                   "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-                   "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-                 : "r"(taddr) : "memory");
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 // 32 lanes x 16 consecutive FP32 columns.
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
@@ -218,16 +208,16 @@ __device__ __forceinline__ void conv1_taps2(float (&acc)[2][8], const float* wf,
 }
 
 // conv1 + LReLU of virtual slice v into its h1 slot (BF16).  512 work items:
-// (channel group, site parity class, 64 site pairs); a warp holds sites of one
-// parity, so all its lanes take the same 13 or 14 taps.  Neighbouring lanes
-// alternate between rows y and y+1, which keeps the 16-byte stores free of
-// bank conflicts.
+// (channel group, site parity class, 64 site pairs) spread over the producer
+// threads (ptid < kProdThreads); a warp holds sites of one parity, so all its
+// lanes take the same 13 or 14 taps.  Neighbouring lanes alternate between
+// rows y and y+1, which keeps the 16-byte stores free of bank conflicts.
 __device__ __forceinline__ void conv1_slice(unsigned char* h1, int v, const float* wf, const float* x, int frozen,
-                                            float slope, int tid) {
+                                            float slope, int ptid) {
     const int z = slice_of(v);
     unsigned char* slot = h1 + (size_t)h1_slot(v) * kSlotBytes;
 #pragma unroll 1
-    for (int it = tid; it < kS * 2; it += kThreads) {
+    for (int it = ptid; it < kS * 2; it += kProdThreads) {
         const int cg = it >> 7, rest = it & 127, pcls = rest >> 6, k = rest & 63;
         int ys[2], xs[2];
 #pragma unroll
@@ -289,12 +279,10 @@ __device__ __forceinline__ void issue_conv(const uint64_t (&a_slot)[3], uint64_t
     }
 }
 
-// conv2 epilogue: out(x) = sum_dx P_dx(x + dx) + b2, LReLU, BF16 into the h2
-// slot of v.  16 warps: warp w covers tile (w>>2)&1, TMEM lane quarter w&3 and
-// output channels 16*(w>>3) .. +15.
-__device__ __forceinline__ void conv2_epilogue(unsigned char* h2, uint32_t tmem, int v, const float* wf, float slope,
-                                               int warp, int lane) {
-    const int mt = (warp >> 2) & 1, q = warp & 3, hf = warp >> 3;
+// conv2 epilogue, one (tile mt, TMEM lane quarter q, channel half hf) part:
+// out(x) = sum_dx P_dx(x + dx) + b2, LReLU, BF16 into the h2 slot of v.
+__device__ __forceinline__ void conv2_epilogue_part(unsigned char* h2, uint32_t tmem, int v, const float* wf,
+                                                    float slope, int mt, int q, int hf, int lane) {
     const int y = mt * 8 + q * 2 + (lane >> 4), xx = lane & 15;
     float pm[16], p0[16], pp[16];
     const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(hf * 16);
@@ -322,17 +310,18 @@ __device__ __forceinline__ void conv2_epilogue(unsigned char* h2, uint32_t tmem,
     }
 }
 
-// conv3 epilogue of slice z: (s, t) = sum_dx P3_dx(x + dx) + b3 for every
-// site; the updated sites apply the affine map and accumulate the log-det.
-__device__ __forceinline__ void conv3_epilogue(uint32_t tmem, int z, const float* wf, float* x, int frozen,
-                                               int use_tanh, bool inverse, double& logdet, int warp, int lane) {
-    const int mt = warp >> 2, q = warp & 3;
+// conv3 epilogue of slice z, tile mt, lane quarter q: (s, t) = sum_dx P3_dx(x + dx)
+// + b3 for every site; the updated sites apply the affine map and accumulate
+// the log-det.  tmem3 = the conv3 accumulator buffer (2 tiles x 32 columns).
+__device__ __forceinline__ void conv3_epilogue_part(uint32_t tmem3, int z, const float* wf, float* x, int frozen,
+                                                    int use_tanh, bool inverse, double& logdet, int mt, int q,
+                                                    int lane) {
     const int y = mt * 8 + q * 2 + (lane >> 4), xx = lane & 15;
     const uint32_t lane_base = (uint32_t)(q * 32) << 16;
     float sm, tm, s0, t0, sp, tp;
-    tmem_ld2(tmem + lane_base + (uint32_t)(kTmem3 + mt * 32 + 0), sm, tm);
-    tmem_ld2(tmem + lane_base + (uint32_t)(kTmem3 + mt * 32 + 8), s0, t0);
-    tmem_ld2(tmem + lane_base + (uint32_t)(kTmem3 + mt * 32 + 16), sp, tp);
+    tmem_ld2(tmem3 + lane_base + (uint32_t)(mt * 32 + 0), sm, tm);
+    tmem_ld2(tmem3 + lane_base + (uint32_t)(mt * 32 + 8), s0, t0);
+    tmem_ld2(tmem3 + lane_base + (uint32_t)(mt * 32 + 16), sp, tp);
     tmem_ld_wait();
     const int src_m = (lane & 16) | ((xx + 15) & 15);
     const int src_p = (lane & 16) | ((xx + 1) & 15);
@@ -347,17 +336,39 @@ __device__ __forceinline__ void conv3_epilogue(uint32_t tmem, int z, const float
     }
 }
 
-// Bounded wait on an mbarrier phase; on expiry records GF_ETIMEOUT and raises
-// the CTA's abort flag (the caller leaves its loops, frees TMEM and returns).
-__device__ __forceinline__ void wait_bar(uint64_t* bar, uint32_t& phase, int* abort_flag, int32_t* status) {
+// Bounded wait for completion number `n` (0-based) of an mbarrier: parity of
+// n.  Returns false (and raises the CTA's abort flag, recording GF_ETIMEOUT)
+// when the limit runs out, or at once when another thread already aborted.
+// Every waiter is at most one completion behind the barrier (the pipeline's
+// dependencies guarantee it), so the parity identifies the completion.
+__device__ __forceinline__ bool wait_n(uint64_t* bar, int n, volatile int* abort_flag, int32_t* status) {
     long long spins = 0;
-    while (!mbar_try_wait(bar, phase)) {
-        if (++spins > kWaitLimit) { *abort_flag = 1; set_status(status, GF_ETIMEOUT); break; }
+    while (!mbar_try_wait(bar, (uint32_t)n & 1u)) {
+        if (*abort_flag) return false;
+        if (++spins > kWaitLimit) { *abort_flag = 1; set_status(status, GF_ETIMEOUT); return false; }
     }
-    phase ^= 1u;
-    fence_after_sync();
+    return true;
+}
+__device__ __forceinline__ uint64_t mbar_arrive(uint64_t* bar) {
+    uint64_t state;
+    asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(state) : "r"(smem_u32(bar)) : "memory");
+    return state;
 }
 
+// Per layer and CTA: 20 conv1 slices (virtual v = -2..17), 18 conv2 slices
+// (u = -1..16) and 16 conv3 slices (w = 0..15).  With seq = the CTA's running
+// layer count, the global numbers c = 20 seq + v + 2, g2 = 18 seq + u + 1 and
+// g3 = 16 seq + w index the barrier completions:
+//   h1 slot c % 4 (barrier bar_h1[c % 4], completion c / 4),
+//   conv2 TMEM buffer g2 & 1 (bar_m2 / bar_t2 completion g2 >> 1), h2 slot g2 % 3
+//   (bar_h2, completion g2 / 3), conv3 TMEM buffer g3 & 1 (bar_m3 / bar_t3, g3 >> 1).
+constexpr int kConv1PerLayer = 20, kConv2PerLayer = 18, kConv3PerLayer = kL;
+
+// Warp roles: warp 0 (one lane) issues every tcgen05.mma; warps 4..11 compute
+// conv1 (FFMA) into the h1 slots; warps 12..15 (TMEM lane quarter = warp & 3)
+// run the conv2 and conv3 epilogues.  They synchronise through mbarriers only,
+// so the tensor cores, the FMA pipes and the epilogues overlap; the CTA meets
+// at a barrier only between layers.
 template <bool INVERSE>
 __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a) {
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -368,10 +379,15 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
     unsigned char* h2 = h1 + 4 * kSlotBytes;                                   // 3 slots
     float* x = reinterpret_cast<float*>(h2 + 3 * kSlotBytes);                  // 4096 floats
     double* red = reinterpret_cast<double*>(x + 4096);                         // 32
-    uint64_t* bar2 = reinterpret_cast<uint64_t*>(red + 32);   // one per conv2 TMEM buffer
-    uint64_t* bar3 = bar2 + 2;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar3 + 1);
-    int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+    uint64_t* bar_h1 = reinterpret_cast<uint64_t*>(red + 32);  // 4: h1 slot written (producers)
+    uint64_t* bar_h2 = bar_h1 + 4;                             // 3: h2 slot written (epilogue)
+    uint64_t* bar_m2 = bar_h2 + 3;                             // 2: conv2 MMAs done (commit)
+    uint64_t* bar_m3 = bar_m2 + 2;                             // 2: conv3 MMAs done (commit)
+    uint64_t* bar_t2 = bar_m3 + 2;                             // 2: conv2 TMEM buffer drained
+    uint64_t* bar_t3 = bar_t2 + 2;                             // 2: conv3 TMEM buffer drained
+    uint64_t* bar_fin = bar_t3 + 2;                            // 1: every queued MMA done (exit)
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar_fin + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int V = 4096;
@@ -380,9 +396,15 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
         tmem_relinquish();
     }
     if (tid == 0) {
-        mbar_init(bar2, 1);
-        mbar_init(bar2 + 1, 1);
-        mbar_init(bar3, 1);
+        for (int i = 0; i < 4; ++i) mbar_init(bar_h1 + i, kProdThreads);
+        for (int i = 0; i < 3; ++i) mbar_init(bar_h2 + i, kEpiThreads);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(bar_m2 + i, 1);
+            mbar_init(bar_m3 + i, 1);
+            mbar_init(bar_t2 + i, kEpiThreads);
+            mbar_init(bar_t3 + i, kEpiThreads);
+        }
+        mbar_init(bar_fin, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -390,7 +412,9 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
     __syncthreads();
     fence_after_sync();
     const uint32_t tmem = *tmem_slot;
-    uint32_t ph2a = 0, ph2b = 0, ph3 = 0;      // phase bits of the two conv2 barriers and conv3
+    // conv2 buffers at columns 0 and 256 (2 tiles x 96), conv3 buffers at 192 and 448 (2 tiles x 32)
+    const auto t2buf = [tmem](int b) { return tmem + (b ? kTmem2B : 0u); };
+    const auto t3buf = [tmem](int b) { return tmem + (uint32_t)kTmem3 + (b ? kTmem2B : 0u); };
 
     // A descriptors of every h1 / h2 slot (LBO = channel-group stride, SBO = 8 sites);
     // B: conv2 LBO = 96 rows x 16 B between K groups, conv3 LBO = 32 rows x 16 B, SBO = 128.
@@ -401,6 +425,7 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
     const uint64_t b2d = smem_desc(smem_u32(w2s), 96 * 16, 128);
     const uint64_t b3d = smem_desc(smem_u32(w3s), 32 * 16, 128);
 
+    int seq = 0;                                   // layers processed by this CTA so far
     for (int64_t b = blockIdx.x; b < a.B; b += gridDim.x) {
         double sumz2 = 0.0;
         if (!INVERSE) {
@@ -429,7 +454,7 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
         __syncthreads();
 
         double logdet = 0.0;
-        for (int li = 0; li < a.n_layers && !*abort_flag; ++li) {
+        for (int li = 0; li < a.n_layers; ++li, ++seq) {
             const int l = INVERSE ? a.n_layers - 1 - li : li;
             const int frozen = l & 1;
             {   // stage this layer's weights (W2, W3 already in the MMA operand layouts)
@@ -439,59 +464,98 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
             }
             fence_proxy_async();
             __syncthreads();
-            // prologue: h1 of virtual slices -2, -1, 0, and conv2 of h2[-1] into TMEM buffer 1
-            for (int v = -2; v <= 0; ++v) conv1_slice(h1, v, wf, x, frozen, a.slope, tid);
-            fence_proxy_async();
+            const int c0 = seq * kConv1PerLayer, g20 = seq * kConv2PerLayer, g30 = seq * kConv3PerLayer;
+
+            if (warp == 0) {
+                // ---------------- tensor-core issue (one thread)
+                if (lane == 0) {
+                    auto wait_h1 = [&](int v) {
+                        const int c = c0 + v + 2;
+                        return wait_n(bar_h1 + (c & 3), c >> 2, abort_flag, a.status);
+                    };
+                    auto wait_h2 = [&](int u) {
+                        const int g = g20 + u + 1;
+                        return wait_n(bar_h2 + g % 3, g / 3, abort_flag, a.status);
+                    };
+                    auto issue3 = [&](int w) {
+                        const int g3 = g30 + w;
+                        if (g3 >= 2 && !wait_n(bar_t3 + (g3 & 1), (g3 - 2) >> 1, abort_flag, a.status)) return;
+                        fence_after_sync();
+                        const uint64_t as[3] = {a2(h2_slot(w - 1)), a2(h2_slot(w)), a2(h2_slot(w + 1))};
+                        issue_conv(as, b3d, (4 * 32 * 16) >> 4, (2 * 32 * 16) >> 4, t3buf(g3 & 1), 32, kIdesc32);
+                        mma_commit(bar_m3 + (g3 & 1));
+                    };
+                    for (int u = -1; u <= kL && !*abort_flag; ++u) {
+                        if (u == -1) {
+                            if (!wait_h1(-2) || !wait_h1(-1) || !wait_h1(0)) break;
+                        } else if (!wait_h1(u + 1)) {
+                            break;
+                        }
+                        const int g2 = g20 + u + 1;
+                        if (g2 >= 2 && !wait_n(bar_t2 + (g2 & 1), (g2 - 2) >> 1, abort_flag, a.status)) break;
+                        fence_after_sync();
+                        const uint64_t as[3] = {a1(h1_slot(u - 1)), a1(h1_slot(u)), a1(h1_slot(u + 1))};
+                        issue_conv(as, b2d, (4 * 96 * 16) >> 4, (2 * 96 * 16) >> 4, t2buf(g2 & 1), 96, kIdesc96);
+                        mma_commit(bar_m2 + (g2 & 1));
+                        if (u >= 2) {                    // conv3 of slice u - 2 reads h2[u-3 .. u-1]
+                            if (u == 2 && (!wait_h2(-1) || !wait_h2(0))) break;
+                            if (!wait_h2(u - 1)) break;
+                            issue3(u - 2);
+                        }
+                    }
+                    // the loop issued conv3 of slices 0 .. L-2; slice L-1 reads h2[L-2 .. L]
+                    if (!*abort_flag && wait_h2(kL)) issue3(kL - 1);
+                }
+                __syncwarp();
+            } else if (warp >= kProdWarp0 && warp < kProdWarp0 + kProdWarps) {
+                // ---------------- conv1 producers
+                const int ptid = tid - kProdWarp0 * 32;
+                for (int v = -2; v <= kL + 1 && !*abort_flag; ++v) {
+                    if (v >= 2) {                        // slot of h1[v-4] is free once conv2 of slice v-3 is done
+                        const int g2 = g20 + v - 2;
+                        if (!wait_n(bar_m2 + (g2 & 1), g2 >> 1, abort_flag, a.status)) break;
+                    }
+                    conv1_slice(h1, v, wf, x, frozen, a.slope, ptid);
+                    fence_proxy_async();
+                    mbar_arrive(bar_h1 + ((c0 + v + 2) & 3));
+                }
+            } else if (warp >= kEpiWarp0) {
+                // ---------------- epilogues (TMEM lane quarter q)
+                const int q = warp & 3;
+                auto epi3 = [&](int w) {
+                    const int g3 = g30 + w;
+                    if (!wait_n(bar_m3 + (g3 & 1), g3 >> 1, abort_flag, a.status)) return false;
+                    fence_after_sync();
+                    for (int mt = 0; mt < 2; ++mt)
+                        conv3_epilogue_part(t3buf(g3 & 1), slice_of(w), wf, x, frozen, a.use_tanh, INVERSE, logdet,
+                                            mt, q, lane);
+                    fence_before_sync();
+                    mbar_arrive(bar_t3 + (g3 & 1));
+                    return true;
+                };
+                for (int u = -1; u <= kL && !*abort_flag; ++u) {
+                    const int g2 = g20 + u + 1;
+                    if (u >= 2) {                        // h2 slot of u held h2[u-3], last read by conv3 of u-2
+                        const int g3 = g30 + u - 2;
+                        if (!wait_n(bar_m3 + (g3 & 1), g3 >> 1, abort_flag, a.status)) break;
+                    }
+                    if (!wait_n(bar_m2 + (g2 & 1), g2 >> 1, abort_flag, a.status)) break;
+                    fence_after_sync();
+                    for (int mt = 0; mt < 2; ++mt)
+                        for (int hf = 0; hf < 2; ++hf)
+                            conv2_epilogue_part(h2, t2buf(g2 & 1), u, wf, a.slope, mt, q, hf, lane);
+                    fence_before_sync();
+                    mbar_arrive(bar_t2 + (g2 & 1));
+                    fence_proxy_async();
+                    mbar_arrive(bar_h2 + g2 % 3);
+                    if (u >= 2 && !epi3(u - 2)) break;
+                }
+                if (!*abort_flag) epi3(kL - 1);     // the loop handled conv3 of slices 0 .. L-2
+            }
+            fence_before_sync();
             __syncthreads();
-            if (tid == 0) {
-                fence_after_sync();
-                const uint64_t as[3] = {a1(h1_slot(-2)), a1(h1_slot(-1)), a1(h1_slot(0))};
-                issue_conv(as, b2d, (4 * 96 * 16) >> 4, (2 * 96 * 16) >> 4, tmem + kTmem2B, 96, kIdesc96);
-                mma_commit(bar2 + 1);
-            }
-            // v = -1 .. L+1.  Tensor-core queue per iteration: conv3 of slice v-2 (v >= 2), then
-            // conv2 of h2[v+1] (v+1 <= L) into TMEM buffer (v+1)&1, issued before the epilogues
-            // of this iteration so the tensor cores never wait for them; FMA pipes: conv1 of
-            // h1[v+2]; then the conv3 epilogue (update of slice v-2) and the conv2 epilogue of
-            // h2[v] (buffer v&1, issued one iteration earlier).
-            for (int v = -1; v <= kL + 1; ++v) {
-                const bool do3 = v >= 2, do2 = v <= kL, next2 = v + 1 <= kL;
-                if (tid == 0 && do3) {
-                    fence_after_sync();
-                    const uint64_t as[3] = {a2(h2_slot(v - 3)), a2(h2_slot(v - 2)), a2(h2_slot(v - 1))};
-                    issue_conv(as, b3d, (4 * 32 * 16) >> 4, (2 * 32 * 16) >> 4, tmem + kTmem3, 32, kIdesc32);
-                    mma_commit(bar3);
-                }
-                if (v + 2 <= kL + 1) {
-                    conv1_slice(h1, v + 2, wf, x, frozen, a.slope, tid);
-                    fence_proxy_async();
-                }
-                __syncthreads();
-                if (tid == 0 && next2) {
-                    fence_after_sync();
-                    const int bn = (v + 1) & 1;
-                    const uint64_t as[3] = {a1(h1_slot(v)), a1(h1_slot(v + 1)), a1(h1_slot(v + 2))};
-                    issue_conv(as, b2d, (4 * 96 * 16) >> 4, (2 * 96 * 16) >> 4, tmem + (bn ? kTmem2B : 0u), 96,
-                               kIdesc96);
-                    mma_commit(bar2 + bn);
-                }
-                if (do3) {
-                    // conv3 of slice v-2 has finished reading all three h2 slots after this wait
-                    wait_bar(bar3, ph3, abort_flag, a.status);
-                    if (warp < 8)
-                        conv3_epilogue(tmem, slice_of(v - 2), wf, x, frozen, a.use_tanh, INVERSE, logdet, warp, lane);
-                }
-                if (do2) {
-                    const int bc = v & 1;
-                    if (bc) wait_bar(bar2 + 1, ph2b, abort_flag, a.status);
-                    else wait_bar(bar2, ph2a, abort_flag, a.status);
-                    conv2_epilogue(h2, tmem + (bc ? kTmem2B : 0u), v, wf, a.slope, warp, lane);
-                    fence_proxy_async();
-                }
-                fence_before_sync();
-                __syncthreads();
-                if (*abort_flag) break;
-            }
+            fence_after_sync();
+            if (*abort_flag) break;
         }
         if (*abort_flag) break;
 
@@ -532,6 +596,12 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
         }
         __syncthreads();
     }
+    if (tid == 0) {
+        // after an abort some MMAs may still be queued: wait (bounded) until all
+        // of this thread's tensor-core work is done before TMEM is freed
+        mma_commit(bar_fin);
+        for (long long spins = 0; !mbar_try_wait(bar_fin, 0u) && spins < kWaitLimit; ++spins) {}
+    }
     fence_before_sync();
     __syncthreads();
     if (warp == 0) {
@@ -541,7 +611,7 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
 }
 
 constexpr size_t kSmemBytes = (size_t)kLayerBytes + 7 * (size_t)kSlotBytes + 4096 * 4 + 32 * 8 +
-                              3 * 8 + 4 + 4;
+                              16 * 8 + 4 + 4;
 
 // canonical FP32 -> per-layer block: W2 [tap9][kg][dxi*32 + o][8] bf16,
 // W3 [tap9][kg][dxi*8 + j][8] bf16 (j = 0: s, 1: t, else 0; rows 24..31 zero),
