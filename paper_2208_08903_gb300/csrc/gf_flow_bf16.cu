@@ -24,11 +24,16 @@
 // epilogues form out(x) = sum_dx P_dx(x + dx) with width-16 shuffles (one
 // x-row = one half-warp = 16 TMEM lanes).
 // Warp-specialised pipeline within a layer (mbarriers only, no CTA barrier):
-// producer warps run conv1 on the FMA pipes up to four slices ahead (four h1
-// slots); one thread of warp 0 queues conv2 of slice u (into one of two TMEM
-// buffers) and then conv3 of slice u-2 (two TMEM buffers) on the tensor cores;
-// four epilogue warps turn conv2 accumulators into h2 (three slots) and conv3
-// accumulators into the affine update of x.  conv1 reads only fixed sites of
+// eight producer warps run conv1 on the FMA pipes (packed FP32x2 FMAs) up to
+// four slices ahead (four h1 slots); one thread of the MMA warp queues conv2 of
+// slice u tile by tile (one TMEM buffer per M-tile) and, once h2[u-1] exists,
+// one conv3 batch with every contribution of h2[u-1] (the three dz parts
+// stacked along N, so each h2 tile is read from shared memory three times
+// instead of nine; four TMEM batch regions); eight epilogue warps turn conv2
+// accumulators into h2 (three slots) and, from three batch regions, the conv3
+// result into the affine update of x.  The tensor cores read their operands
+// from shared memory at about 128 B per clock, so the number of operand bytes
+// per MMA, not the MMA count, bounds conv2 and conv3.  conv1 reads only fixed sites of
 // x and the update writes only the other parity, so x needs no ordering within
 // a layer; the CTA meets at a barrier between layers.
 #include <algorithm>
@@ -42,26 +47,33 @@ namespace gf {
 
 namespace {
 
-constexpr int kThreads = 512;
-constexpr int kL = 16, kS = 256, kC = 32, kT = 27;
+constexpr int kThreads = 17 * 32;                      // 8 epilogue + 8 producer warps + 1 MMA warp
+constexpr int kL = 16, kC = 32, kT = 27;
 constexpr int kHaloSites = 18 * 16;                    // y = -1 .. 16
 constexpr int kCgStride = kHaloSites * 16;             // bytes between channel groups
 constexpr int kSlotBytes = 4 * kCgStride;              // [cg][site][8] bf16 = 18432
 // conv2 B operand per (dz,dy) tap pair: the three dx weight sets stacked along N
-// (N = 96: row dxi*32 + o); conv3 B: rows dxi*8 + {s, t, 6 zeros} for dxi < 3 and
-// 8 zero rows (N = 32).  Layout [tap9][kg][n][8] bf16 (K-major core matrices).
+// (N = 96: row dxi*32 + o), layout [tap9][kg][n][8] bf16 (K-major core matrices).
+// conv3 B operand per dy tap: the three dz parts and three dx weight sets of s
+// and t stacked along N (N = 32: row d*8 + dxi*2 + {0: s, 1: t}, rows 6, 7, 14,
+// 15, 22..31 zero), layout [dy3][kg][n][8] bf16.
 constexpr int kW2Bytes = 9 * 4 * 96 * 16;              // 55296
-constexpr int kW3Bytes = 9 * 4 * 32 * 16;              // 18432
+constexpr int kW3Bytes = 3 * 4 * 32 * 16;              // 6144
+// The field x in shared memory: rows of 16 sites with a stride of 24 floats, so
+// the 32 lanes of a conv1 load (4 rows x 8 sites of one parity) hit 32 banks.
+constexpr int kXRow = 24, kXSlice = 16 * kXRow, kXFloats = 16 * kXSlice;
 // FP32 part of a layer block (floats): W1s[t][c], b1[c], b2[c], b3[2], pad
 constexpr int kF_W1 = 0, kF_b1 = kT * kC, kF_b2 = kF_b1 + kC, kF_b3 = kF_b2 + kC;
 constexpr int kF_N = (kF_b3 + 2 + 3) & ~3;
 constexpr int kLayerBytes = kW2Bytes + kW3Bytes + kF_N * 4;
-constexpr int kTmem3 = 192;                             // conv3 accumulators (2 tiles x 32 columns)
-constexpr int kTmem2B = 256;                            // second conv2 buffer (2 tiles x 96 columns)
+// TMEM columns: conv2 accumulators of tile 0 at 0 and tile 1 at 96 (N = 96 each);
+// four conv3 batch regions at 192 + 64 r (2 tiles x N = 32)
+constexpr int kTmemC3 = 192;
 constexpr int kTmemCols = 512;
 constexpr long long kWaitLimit = 1ll << 22;             // bounded mbarrier wait (iterations)
-constexpr int kProdWarp0 = 4, kProdWarps = 8, kProdThreads = kProdWarps * 32;   // conv1 producers
-constexpr int kEpiWarp0 = 12, kEpiThreads = 4 * 32;                            // epilogue warps 12..15
+constexpr int kEpiWarps = 8, kEpiThreads = kEpiWarps * 32;                     // epilogue: warps 0..7
+constexpr int kProdWarp0 = 8, kProdWarps = 8, kProdThreads = kProdWarps * 32;   // conv1 producers: 8..15
+constexpr int kMmaWarp = 16;                                                    // tensor-core issue
 
 // ---------------------------------------------------------------- PTX wrappers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -119,12 +131,15 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
-// 32 lanes x 2 consecutive FP32 columns.
-__device__ __forceinline__ void tmem_ld2(uint32_t taddr, float& a, float& b) {
-    uint32_t r0, r1;
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];" : "=r"(r0), "=r"(r1) : "r"(taddr) : "memory");
-    a = __uint_as_float(r0);
-    b = __uint_as_float(r1);
+// 32 lanes x 8 consecutive FP32 columns.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                   "=r"(r[7])
+                 : "r"(taddr) : "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
@@ -183,74 +198,77 @@ __device__ __forceinline__ int slice_of(int v) { return v & 15; }
 __device__ __forceinline__ int h1_slot(int v) { return (v + 16) & 3; }
 __device__ __forceinline__ int h2_slot(int v) { return (v + 15) % 3; }
 
+// Packed FP32 pairs for the conv1 FMAs: fma.rn.f32x2 rounds each half like fmaf.
+__device__ __forceinline__ unsigned long long f2pack(float lo, float hi) {
+    return ((unsigned long long)__float_as_uint(hi) << 32) | __float_as_uint(lo);
+}
+__device__ __forceinline__ void ffma2(unsigned long long& acc, unsigned long long a, unsigned long long b) {
+    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(a), "l"(b));
+}
+
 // The taps of conv1 that reach fixed sites from an output site of parity p are
 // those whose offset parity (|dz|+|dy|+|dx|) mod 2 equals NEED = frozen ^ p; the
-// tap set is chosen at compile time, so the loop has no branches.  Two sites
-// (rows y and y + 8, same parity) share each tap's weight loads.
+// tap set is chosen at compile time, so the loop has no branches.  Four sites
+// (rows y, y+4, y+8, y+12, same x and parity) share each tap's weight loads;
+// acc[q][j] holds channels (2j, 2j+1) of site q.
 template <int NEED>
-__device__ __forceinline__ void conv1_taps2(float (&acc)[2][8], const float* wf, const float* x, const int (&zr)[3],
-                                            const int (&yr)[2][3], const int (&xc)[2][3], int cg) {
+__device__ __forceinline__ void conv1_taps4(unsigned long long (&acc)[4][4], const float* wf, const float* x,
+                                            const int (&zr)[3], const int (&yr)[4][3], const int (&xc)[3], int cg) {
 #pragma unroll
     for (int t = 0; t < kT; ++t) {
         const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;
         if (((dz + dy + dx + 1) & 1) != NEED) continue;                     // resolved at compile time
-        const float x0 = x[zr[dz] + yr[0][dy] + xc[0][dx]];
-        const float x1 = x[zr[dz] + yr[1][dy] + xc[1][dx]];
-        const float4 w0 = *reinterpret_cast<const float4*>(wf + kF_W1 + t * kC + cg * 8);
-        const float4 w1 = *reinterpret_cast<const float4*>(wf + kF_W1 + t * kC + cg * 8 + 4);
-        const float w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+        const ulonglong2 wA = *reinterpret_cast<const ulonglong2*>(wf + kF_W1 + t * kC + cg * 8);
+        const ulonglong2 wB = *reinterpret_cast<const ulonglong2*>(wf + kF_W1 + t * kC + cg * 8 + 4);
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            acc[0][c] = fmaf(x0, w[c], acc[0][c]);
-            acc[1][c] = fmaf(x1, w[c], acc[1][c]);
+        for (int q = 0; q < 4; ++q) {
+            const float xv = x[zr[dz] + yr[q][dy] + xc[dx]];
+            const unsigned long long xx = f2pack(xv, xv);
+            ffma2(acc[q][0], xx, wA.x);
+            ffma2(acc[q][1], xx, wA.y);
+            ffma2(acc[q][2], xx, wB.x);
+            ffma2(acc[q][3], xx, wB.y);
         }
     }
 }
 
-// conv1 + LReLU of virtual slice v into its h1 slot (BF16).  512 work items:
-// (channel group, site parity class, 64 site pairs) spread over the producer
-// threads (ptid < kProdThreads); a warp holds sites of one parity, so all its
-// lanes take the same 13 or 14 taps.  Neighbouring lanes alternate between
-// rows y and y+1, which keeps the 16-byte stores free of bank conflicts.
+// conv1 + LReLU of virtual slice v into its h1 slot (BF16).  256 work items, one
+// per producer thread: (channel group, site parity class, 32 site quads).  A
+// warp holds sites of one parity, so all its lanes take the same 13 or 14 taps;
+// its 32 lanes cover rows y0..y0+3 x 8 sites, which with the padded x rows hits
+// 32 distinct banks, and their 16-byte stores cover all eight bank groups.
 __device__ __forceinline__ void conv1_slice(unsigned char* h1, int v, const float* wf, const float* x, int frozen,
                                             float slope, int ptid) {
     const int z = slice_of(v);
     unsigned char* slot = h1 + (size_t)h1_slot(v) * kSlotBytes;
-#pragma unroll 1
-    for (int it = ptid; it < kS * 2; it += kProdThreads) {
-        const int cg = it >> 7, rest = it & 127, pcls = rest >> 6, k = rest & 63;
-        int ys[2], xs[2];
+    const int cg = ptid >> 6, pcls = (ptid >> 5) & 1, k = ptid & 31;
+    const int y0 = k >> 3, xh = k & 7;
+    const int xs = 2 * xh + ((pcls ^ z ^ y0) & 1);                  // rows y0 + 4q share the parity
+    int zr[3], yr[4][3], xc[3];
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            ys[q] = 2 * (k >> 4) + (k & 1) + 8 * q;
-            xs[q] = 2 * ((k >> 1) & 7) + ((pcls ^ z ^ ys[q]) & 1);        // parity pcls
+    for (int d = 0; d < 3; ++d) {
+        zr[d] = wrap16(z + d - 1) * kXSlice;
+        xc[d] = wrap16(xs + d - 1);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) yr[q][d] = wrap16(y0 + 4 * q + d - 1) * kXRow;
+    }
+    const ulonglong2 bA = *reinterpret_cast<const ulonglong2*>(wf + kF_b1 + cg * 8);
+    const ulonglong2 bB = *reinterpret_cast<const ulonglong2*>(wf + kF_b1 + cg * 8 + 4);
+    unsigned long long acc[4][4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) { acc[q][0] = bA.x; acc[q][1] = bA.y; acc[q][2] = bB.x; acc[q][3] = bB.y; }
+    if ((frozen ^ pcls) & 1) conv1_taps4<1>(acc, wf, x, zr, yr, xc, cg);
+    else conv1_taps4<0>(acc, wf, x, zr, yr, xc, cg);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        float o[8];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float lo = __uint_as_float((unsigned)acc[q][j]), hi = __uint_as_float((unsigned)(acc[q][j] >> 32));
+            o[2 * j] = lo > 0.f ? lo : slope * lo;
+            o[2 * j + 1] = hi > 0.f ? hi : slope * hi;
         }
-        int zr[3], yr[2][3], xc[2][3];
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            zr[d] = wrap16(z + d - 1) << 8;
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                yr[q][d] = wrap16(ys[q] + d - 1) << 4;
-                xc[q][d] = wrap16(xs[q] + d - 1);
-            }
-        }
-        const float4 b0 = *reinterpret_cast<const float4*>(wf + kF_b1 + cg * 8);
-        const float4 b1 = *reinterpret_cast<const float4*>(wf + kF_b1 + cg * 8 + 4);
-        float acc[2][8];
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            acc[q][0] = b0.x; acc[q][1] = b0.y; acc[q][2] = b0.z; acc[q][3] = b0.w;
-            acc[q][4] = b1.x; acc[q][5] = b1.y; acc[q][6] = b1.z; acc[q][7] = b1.w;
-        }
-        if ((frozen ^ pcls) & 1) conv1_taps2<1>(acc, wf, x, zr, yr, xc, cg);
-        else conv1_taps2<0>(acc, wf, x, zr, yr, xc, cg);
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-#pragma unroll
-            for (int c = 0; c < 8; ++c) acc[q][c] = acc[q][c] > 0.f ? acc[q][c] : slope * acc[q][c];
-            store8(slot, cg, ys[q], xs[q], acc[q]);
-        }
+        store8(slot, cg, y0 + 4 * q, xs, o);
     }
 }
 
@@ -259,37 +277,61 @@ __device__ __forceinline__ void conv1_slice(unsigned char* h1, int v, const floa
 // dx partial sums at once (B holds the dx weight sets stacked along N).
 // a_slot[dzi] = A descriptors of the three input slices; b0 = B descriptor of
 // tap pair 0, K-step 0; tap pair p, K-step k adds p * b_tap + k * b_k (16-byte units).
-__device__ __forceinline__ void issue_conv(const uint64_t (&a_slot)[3], uint64_t b0, uint32_t b_tap, uint32_t b_k,
-                                           uint32_t d0, uint32_t d_tile, uint32_t idesc) {
+// One elected thread: conv2 of one M-tile (mt) of a slice as an implicit GEMM:
+// 9 (dz,dy) taps x 2 K-steps of tcgen05.mma, each producing the three dx
+// partial sums at once (B holds the dx weight sets stacked along N = 96).
+// a_slot[dzi] = A descriptors of the three input slices; b0 = B descriptor of
+// tap pair 0, K-step 0; tap pair p, K-step k adds p * b_tap + k * b_k (16-byte units).
+__device__ __forceinline__ void issue_conv2_tile(const uint64_t (&a_slot)[3], uint64_t b0, uint32_t d, int mt) {
+    constexpr uint32_t b_tap = (4 * 96 * 16) >> 4, b_k = (2 * 96 * 16) >> 4;
 #pragma unroll
-    for (int mt = 0; mt < 2; ++mt) {
-        const uint32_t d = d0 + (uint32_t)mt * d_tile;
+    for (int dzi = 0; dzi < 3; ++dzi) {
 #pragma unroll
-        for (int dzi = 0; dzi < 3; ++dzi) {
+        for (int dyi = 0; dyi < 3; ++dyi) {
 #pragma unroll
-            for (int dyi = 0; dyi < 3; ++dyi) {
-#pragma unroll
-                for (int k = 0; k < 2; ++k) {
-                    const uint64_t ad = a_slot[dzi] + (uint64_t)((2 * k * kCgStride + (mt * 8 + dyi) * 256) >> 4);
-                    const uint64_t bd = b0 + (uint64_t)((dzi * 3 + dyi) * b_tap + k * b_k);
-                    mma_bf16(d, ad, bd, idesc, (dzi | dyi | k) ? 1u : 0u);
-                }
+            for (int k = 0; k < 2; ++k) {
+                const uint64_t ad = a_slot[dzi] + (uint64_t)((2 * k * kCgStride + (mt * 8 + dyi) * 256) >> 4);
+                const uint64_t bd = b0 + (uint64_t)((dzi * 3 + dyi) * b_tap + k * b_k);
+                mma_bf16(d, ad, bd, kIdesc96, (dzi | dyi | k) ? 1u : 0u);
             }
         }
     }
 }
 
-// conv2 epilogue, one (tile mt, TMEM lane quarter q, channel half hf) part:
-// out(x) = sum_dx P_dx(x + dx) + b2, LReLU, BF16 into the h2 slot of v.
-__device__ __forceinline__ void conv2_epilogue_part(unsigned char* h2, uint32_t tmem, int v, const float* wf,
-                                                    float slope, int mt, int q, int hf, int lane) {
-    const int y = mt * 8 + q * 2 + (lane >> 4), xx = lane & 15;
-    float pm[16], p0[16], pp[16];
-    const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(hf * 16);
-    tmem_ld16(base + (uint32_t)((mt * 3 + 0) * 32), pm);
-    tmem_ld16(base + (uint32_t)((mt * 3 + 1) * 32), p0);
-    tmem_ld16(base + (uint32_t)((mt * 3 + 2) * 32), pp);
+// One elected thread: every conv3 contribution of one h2 slice (A descriptor a)
+// into a fresh batch region: 2 M-tiles x 3 dy taps x 2 K-steps with N = 32, the
+// three dz parts (for the slices after, at and before the h2 slice) and the dx
+// weight sets stacked along N.
+__device__ __forceinline__ void issue_conv3_batch(uint64_t a, uint64_t b0, uint32_t region) {
+    constexpr uint32_t b_tap = (4 * 32 * 16) >> 4, b_k = (2 * 32 * 16) >> 4;
+#pragma unroll
+    for (int dyi = 0; dyi < 3; ++dyi) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+                const uint64_t ad = a + (uint64_t)((2 * k * kCgStride + (mt * 8 + dyi) * 256) >> 4);
+                const uint64_t bd = b0 + (uint64_t)(dyi * b_tap + k * b_k);
+                mma_bf16(region + (uint32_t)mt * 32, ad, bd, kIdesc32, (dyi | k) ? 1u : 0u);
+            }
+        }
+    }
+}
+
+// conv2 epilogue of one M-tile mt, TMEM lane quarter q, channel half hf:
+// load the three dx partial sums (16 channels each) of the tile's TMEM buffer,
+// then out(x) = sum_dx P_dx(x + dx) + b2, LReLU, BF16 into the h2 slot of v.
+struct Conv2Parts { float pm[16], p0[16], pp[16]; };
+__device__ __forceinline__ void conv2_epi_load(Conv2Parts& P, uint32_t tile_buf, int q, int hf) {
+    const uint32_t base = tile_buf + ((uint32_t)(q * 32) << 16) + (uint32_t)(hf * 16);
+    tmem_ld16(base + 0u, P.pm);
+    tmem_ld16(base + 32u, P.p0);
+    tmem_ld16(base + 64u, P.pp);
     tmem_ld_wait();
+}
+__device__ __forceinline__ void conv2_epi_store(const Conv2Parts& P, unsigned char* h2, int v, const float* wf,
+                                                float slope, int mt, int q, int hf, int lane) {
+    const int y = mt * 8 + q * 2 + (lane >> 4), xx = lane & 15;
     const int src_m = (lane & 16) | ((xx + 15) & 15);   // x - 1
     const int src_p = (lane & 16) | ((xx + 1) & 15);    // x + 1
     unsigned char* slot = h2 + (size_t)h2_slot(v) * kSlotBytes;
@@ -302,34 +344,44 @@ __device__ __forceinline__ void conv2_epilogue_part(unsigned char* h2, uint32_t 
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
             const int ch = g * 8 + c;
-            const float s = p0[ch] + __shfl_sync(0xffffffffu, pm[ch], src_m) +
-                            __shfl_sync(0xffffffffu, pp[ch], src_p) + bias[c];
+            const float s = P.p0[ch] + __shfl_sync(0xffffffffu, P.pm[ch], src_m) +
+                            __shfl_sync(0xffffffffu, P.pp[ch], src_p) + bias[c];
             o[c] = s > 0.f ? s : slope * s;
         }
         store8(slot, hf * 2 + g, y, xx, o);
     }
 }
 
-// conv3 epilogue of slice z, tile mt, lane quarter q: (s, t) = sum_dx P3_dx(x + dx)
-// + b3 for every site; the updated sites apply the affine map and accumulate
-// the log-det.  tmem3 = the conv3 accumulator buffer (2 tiles x 32 columns).
-__device__ __forceinline__ void conv3_epilogue_part(uint32_t tmem3, int z, const float* wf, float* x, int frozen,
-                                                    int use_tanh, bool inverse, double& logdet, int mt, int q,
-                                                    int lane) {
-    const int y = mt * 8 + q * 2 + (lane >> 4), xx = lane & 15;
-    const uint32_t lane_base = (uint32_t)(q * 32) << 16;
-    float sm, tm, s0, t0, sp, tp;
-    tmem_ld2(tmem3 + lane_base + (uint32_t)(mt * 32 + 0), sm, tm);
-    tmem_ld2(tmem3 + lane_base + (uint32_t)(mt * 32 + 8), s0, t0);
-    tmem_ld2(tmem3 + lane_base + (uint32_t)(mt * 32 + 16), sp, tp);
+// conv3 epilogue of slice z, tile mt, lane quarter q.  The slice's (s, t)
+// partial sums lie in three batch regions: part 0 (dz = -1) in columns 0..5 of
+// the batch before it, part 1 in columns 8..13 of its own batch, part 2 in
+// columns 16..21 of the batch after it (columns 2*dxi + {0: s, 1: t}).
+// load: the three 8-column pieces; finish: (s, t) = sum_dx P_dx(x + dx) + b3 and,
+// at the updated sites, the affine map and the log-det.
+__device__ __forceinline__ void conv3_epi_load(float (&p)[3][8], uint32_t rm, uint32_t r0, uint32_t rp, int mt,
+                                               int q) {
+    const uint32_t lane_base = ((uint32_t)(q * 32) << 16) + (uint32_t)(mt * 32);
+    tmem_ld8(rm + lane_base + 0u, p[0]);
+    tmem_ld8(r0 + lane_base + 8u, p[1]);
+    tmem_ld8(rp + lane_base + 16u, p[2]);
     tmem_ld_wait();
+}
+__device__ __forceinline__ void conv3_epi_finish(const float (&p)[3][8], int z, const float* wf, float* x,
+                                                 int frozen, int use_tanh, bool inverse, double& logdet, int mt,
+                                                 int q, int lane) {
+    const int y = mt * 8 + q * 2 + (lane >> 4), xx = lane & 15;
+    float st[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) st[i] = p[0][i] + p[1][i] + p[2][i];
     const int src_m = (lane & 16) | ((xx + 15) & 15);
     const int src_p = (lane & 16) | ((xx + 1) & 15);
-    const float spre = s0 + __shfl_sync(0xffffffffu, sm, src_m) + __shfl_sync(0xffffffffu, sp, src_p) + wf[kF_b3];
-    const float tt = t0 + __shfl_sync(0xffffffffu, tm, src_m) + __shfl_sync(0xffffffffu, tp, src_p) + wf[kF_b3 + 1];
+    const float spre = st[2] + __shfl_sync(0xffffffffu, st[0], src_m) + __shfl_sync(0xffffffffu, st[4], src_p) +
+                       wf[kF_b3];
+    const float tt = st[3] + __shfl_sync(0xffffffffu, st[1], src_m) + __shfl_sync(0xffffffffu, st[5], src_p) +
+                     wf[kF_b3 + 1];
     if (((z + y + xx) & 1) != frozen) {
         const float s = use_tanh ? tanhf(spre) : spre;
-        float& xv = x[(z * 16 + y) * 16 + xx];
+        float& xv = x[(z * 16 + y) * kXRow + xx];
         if (!inverse) xv = fmaf(xv, expf(s), tt);
         else xv = (xv - tt) * expf(-s);
         logdet += (double)s;
@@ -356,17 +408,23 @@ __device__ __forceinline__ uint64_t mbar_arrive(uint64_t* bar) {
 }
 
 // Per layer and CTA: 20 conv1 slices (virtual v = -2..17), 18 conv2 slices
-// (u = -1..16) and 16 conv3 slices (w = 0..15).  With seq = the CTA's running
-// layer count, the global numbers c = 20 seq + v + 2, g2 = 18 seq + u + 1 and
-// g3 = 16 seq + w index the barrier completions:
-//   h1 slot c % 4 (barrier bar_h1[c % 4], completion c / 4),
-//   conv2 TMEM buffer g2 & 1 (bar_m2 / bar_t2 completion g2 >> 1), h2 slot g2 % 3
-//   (bar_h2, completion g2 / 3), conv3 TMEM buffer g3 & 1 (bar_m3 / bar_t3, g3 >> 1).
-constexpr int kConv1PerLayer = 20, kConv2PerLayer = 18, kConv3PerLayer = kL;
+// (u = -1..16), 18 conv3 batches and 16 conv3 slices (w = 0..15).  Batch u is
+// queued once h2[u] exists and computes every conv3 contribution of h2[u] (to
+// slices u+1, u and u-1, stacked along N) into its own TMEM region, so slice w
+// is complete after batch w+1; a region is released once the last existing
+// slice that reads it has been drained.  With seq = the CTA's running layer
+// count, the global numbers c = 20 seq + v + 2 and g2 = gb = 18 seq + u + 1
+// index the barrier completions:
+//   h1 slot: bar_h1[c % 4], completion c / 4;
+//   conv2 of tile t: bar_m2[2 t + (g2 & 1)] completion g2 >> 1; its TMEM drained:
+//   bar_t2[t] completion g2; h2 written: bar_h2[g2 % 3], completion g2 / 3;
+//   conv3 batch gb: bar_m3[gb & 1], completion gb >> 1; its region gb & 3
+//   released: bar_t3[gb & 3], completion gb >> 2.
+constexpr int kConv1PerLayer = 20, kConv2PerLayer = 18;
 
-// Warp roles: warp 0 (one lane) issues every tcgen05.mma; warps 4..11 compute
-// conv1 (FFMA) into the h1 slots; warps 12..15 (TMEM lane quarter = warp & 3)
-// run the conv2 and conv3 epilogues.  They synchronise through mbarriers only,
+// Warp roles: warps 0..7 run the conv2 and conv3 epilogues (warp w: M-tile
+// w >> 2, TMEM lane quarter w & 3); warps 8..15 compute conv1 (packed FFMA) into
+// the h1 slots; one lane of warp 16 issues every tcgen05.mma.  They synchronise through mbarriers only,
 // so the tensor cores, the FMA pipes and the epilogues overlap; the CTA meets
 // at a barrier only between layers.
 template <bool INVERSE>
@@ -377,21 +435,21 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
     float* wf = reinterpret_cast<float*>(smem + kW2Bytes + kW3Bytes);          // kF_N floats
     unsigned char* h1 = smem + kLayerBytes;                                    // 4 slots
     unsigned char* h2 = h1 + 4 * kSlotBytes;                                   // 3 slots
-    float* x = reinterpret_cast<float*>(h2 + 3 * kSlotBytes);                  // 4096 floats
-    double* red = reinterpret_cast<double*>(x + 4096);                         // 32
+    float* x = reinterpret_cast<float*>(h2 + 3 * kSlotBytes);                  // kXFloats (padded rows)
+    double* red = reinterpret_cast<double*>(x + kXFloats);                     // 32
     uint64_t* bar_h1 = reinterpret_cast<uint64_t*>(red + 32);  // 4: h1 slot written (producers)
     uint64_t* bar_h2 = bar_h1 + 4;                             // 3: h2 slot written (epilogue)
-    uint64_t* bar_m2 = bar_h2 + 3;                             // 2: conv2 MMAs done (commit)
-    uint64_t* bar_m3 = bar_m2 + 2;                             // 2: conv3 MMAs done (commit)
-    uint64_t* bar_t2 = bar_m3 + 2;                             // 2: conv2 TMEM buffer drained
-    uint64_t* bar_t3 = bar_t2 + 2;                             // 2: conv3 TMEM buffer drained
-    uint64_t* bar_fin = bar_t3 + 2;                            // 1: every queued MMA done (exit)
+    uint64_t* bar_m2 = bar_h2 + 3;                             // 4: conv2 of a tile done (commit)
+    uint64_t* bar_m3 = bar_m2 + 4;                             // 2: conv3 batch done (commit)
+    uint64_t* bar_t2 = bar_m3 + 2;                             // 2: conv2 tile buffer drained
+    uint64_t* bar_t3 = bar_t2 + 2;                             // 4: conv3 batch region released
+    uint64_t* bar_fin = bar_t3 + 4;                            // 1: every queued MMA done (exit)
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar_fin + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int V = 4096;
-    if (warp == 0) {
+    if (warp == kMmaWarp) {
         tmem_alloc(tmem_slot, kTmemCols);
         tmem_relinquish();
     }
@@ -399,9 +457,11 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
         for (int i = 0; i < 4; ++i) mbar_init(bar_h1 + i, kProdThreads);
         for (int i = 0; i < 3; ++i) mbar_init(bar_h2 + i, kEpiThreads);
         for (int i = 0; i < 2; ++i) {
-            mbar_init(bar_m2 + i, 1);
             mbar_init(bar_m3 + i, 1);
             mbar_init(bar_t2 + i, kEpiThreads);
+        }
+        for (int i = 0; i < 4; ++i) {
+            mbar_init(bar_m2 + i, 1);
             mbar_init(bar_t3 + i, kEpiThreads);
         }
         mbar_init(bar_fin, 1);
@@ -412,9 +472,9 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
     __syncthreads();
     fence_after_sync();
     const uint32_t tmem = *tmem_slot;
-    // conv2 buffers at columns 0 and 256 (2 tiles x 96), conv3 buffers at 192 and 448 (2 tiles x 32)
-    const auto t2buf = [tmem](int b) { return tmem + (b ? kTmem2B : 0u); };
-    const auto t3buf = [tmem](int b) { return tmem + (uint32_t)kTmem3 + (b ? kTmem2B : 0u); };
+    const auto t2tile = [tmem](int t) { return tmem + (uint32_t)(t * 96); };
+    const auto t3reg = [tmem](int r) { return tmem + (uint32_t)(kTmemC3 + (r & 3) * 64); };
+    const auto xi = [](int n) { return (n >> 4) * kXRow + (n & 15); };   // site -> padded x index
 
     // A descriptors of every h1 / h2 slot (LBO = channel-group stride, SBO = 8 sites);
     // B: conv2 LBO = 96 rows x 16 B between K groups, conv3 LBO = 32 rows x 16 B, SBO = 128.
@@ -432,7 +492,7 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
             if (a.z_in) {
                 for (int n = tid; n < V; n += kThreads) {
                     const float v = __ldg(a.z_in + b * V + n);
-                    x[n] = v;
+                    x[xi(n)] = v;
                     sumz2 += (double)v * v;
                 }
             } else {
@@ -442,14 +502,14 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
                     float zz[4];
                     normals4_f32(w, zz);
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) { x[4 * j + q] = zz[q]; sumz2 += (double)zz[q] * zz[q]; }
+                    for (int q = 0; q < 4; ++q) { x[xi(4 * j + q)] = zz[q]; sumz2 += (double)zz[q] * zz[q]; }
                 }
             }
             __syncthreads();
             if (a.z_out)
-                for (int n = tid; n < V; n += kThreads) a.z_out[b * V + n] = x[n];
+                for (int n = tid; n < V; n += kThreads) a.z_out[b * V + n] = x[xi(n)];
         } else {
-            for (int n = tid; n < V; n += kThreads) x[n] = __ldg(a.phi_in + b * V + n);
+            for (int n = tid; n < V; n += kThreads) x[xi(n)] = __ldg(a.phi_in + b * V + n);
         }
         __syncthreads();
 
@@ -458,32 +518,40 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
             const int l = INVERSE ? a.n_layers - 1 - li : li;
             const int frozen = l & 1;
             {   // stage this layer's weights (W2, W3 already in the MMA operand layouts)
+                // all of a thread's loads are issued before its stores (L2 latency once)
                 const uint4* src = reinterpret_cast<const uint4*>(a.Wl + (size_t)l * kLayerBytes);
                 uint4* dst = reinterpret_cast<uint4*>(smem);
-                for (int i = tid; i < kLayerBytes / 16; i += kThreads) dst[i] = __ldg(src + i);
+                constexpr int kN16 = kLayerBytes / 16, kPer = (kN16 + kThreads - 1) / kThreads;
+                uint4 tmp[kPer];
+#pragma unroll
+                for (int j = 0; j < kPer; ++j)
+                    if (tid + j * kThreads < kN16) tmp[j] = __ldg(src + tid + j * kThreads);
+#pragma unroll
+                for (int j = 0; j < kPer; ++j)
+                    if (tid + j * kThreads < kN16) dst[tid + j * kThreads] = tmp[j];
             }
             fence_proxy_async();
             __syncthreads();
-            const int c0 = seq * kConv1PerLayer, g20 = seq * kConv2PerLayer, g30 = seq * kConv3PerLayer;
+            const int c0 = seq * kConv1PerLayer, g20 = seq * kConv2PerLayer;
 
-            if (warp == 0) {
+            if (warp == kMmaWarp) {
                 // ---------------- tensor-core issue (one thread)
                 if (lane == 0) {
                     auto wait_h1 = [&](int v) {
                         const int c = c0 + v + 2;
                         return wait_n(bar_h1 + (c & 3), c >> 2, abort_flag, a.status);
                     };
-                    auto wait_h2 = [&](int u) {
-                        const int g = g20 + u + 1;
-                        return wait_n(bar_h2 + g % 3, g / 3, abort_flag, a.status);
-                    };
-                    auto issue3 = [&](int w) {
-                        const int g3 = g30 + w;
-                        if (g3 >= 2 && !wait_n(bar_t3 + (g3 & 1), (g3 - 2) >> 1, abort_flag, a.status)) return;
+                    // conv3 batch ub: every contribution of h2[ub] (needs h2[ub] written and
+                    // the batch region free: batch ub-4's readers drained)
+                    auto batch = [&](int ub) {
+                        const int gh = g20 + ub + 1;
+                        if (!wait_n(bar_h2 + gh % 3, gh / 3, abort_flag, a.status)) return false;
+                        if (gh >= 4 && !wait_n(bar_t3 + (gh & 3), (gh - 4) >> 2, abort_flag, a.status))
+                            return false;
                         fence_after_sync();
-                        const uint64_t as[3] = {a2(h2_slot(w - 1)), a2(h2_slot(w)), a2(h2_slot(w + 1))};
-                        issue_conv(as, b3d, (4 * 32 * 16) >> 4, (2 * 32 * 16) >> 4, t3buf(g3 & 1), 32, kIdesc32);
-                        mma_commit(bar_m3 + (g3 & 1));
+                        issue_conv3_batch(a2(h2_slot(ub)), b3d, t3reg(gh & 3));
+                        mma_commit(bar_m3 + (gh & 1));
+                        return true;
                     };
                     for (int u = -1; u <= kL && !*abort_flag; ++u) {
                         if (u == -1) {
@@ -492,19 +560,18 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
                             break;
                         }
                         const int g2 = g20 + u + 1;
-                        if (g2 >= 2 && !wait_n(bar_t2 + (g2 & 1), (g2 - 2) >> 1, abort_flag, a.status)) break;
-                        fence_after_sync();
                         const uint64_t as[3] = {a1(h1_slot(u - 1)), a1(h1_slot(u)), a1(h1_slot(u + 1))};
-                        issue_conv(as, b2d, (4 * 96 * 16) >> 4, (2 * 96 * 16) >> 4, t2buf(g2 & 1), 96, kIdesc96);
-                        mma_commit(bar_m2 + (g2 & 1));
-                        if (u >= 2) {                    // conv3 of slice u - 2 reads h2[u-3 .. u-1]
-                            if (u == 2 && (!wait_h2(-1) || !wait_h2(0))) break;
-                            if (!wait_h2(u - 1)) break;
-                            issue3(u - 2);
+                        bool ok = true;
+                        for (int t = 0; t < 2 && ok; ++t) {      // tile t's buffer: drained by epi2 of u-1
+                            if (g2 >= 1 && !wait_n(bar_t2 + t, g2 - 1, abort_flag, a.status)) { ok = false; break; }
+                            fence_after_sync();
+                            issue_conv2_tile(as, b2d, t2tile(t), t);
+                            mma_commit(bar_m2 + 2 * t + (g2 & 1));
                         }
+                        if (!ok) break;
+                        if (u >= 0 && !batch(u - 1)) break;
                     }
-                    // the loop issued conv3 of slices 0 .. L-2; slice L-1 reads h2[L-2 .. L]
-                    if (!*abort_flag && wait_h2(kL)) issue3(kL - 1);
+                    if (!*abort_flag) batch(kL);
                 }
                 __syncwarp();
             } else if (warp >= kProdWarp0 && warp < kProdWarp0 + kProdWarps) {
@@ -512,45 +579,63 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
                 const int ptid = tid - kProdWarp0 * 32;
                 for (int v = -2; v <= kL + 1 && !*abort_flag; ++v) {
                     if (v >= 2) {                        // slot of h1[v-4] is free once conv2 of slice v-3 is done
-                        const int g2 = g20 + v - 2;
-                        if (!wait_n(bar_m2 + (g2 & 1), g2 >> 1, abort_flag, a.status)) break;
+                        const int g2 = g20 + v - 2;          // (tile 1 is queued after tile 0)
+                        if (!wait_n(bar_m2 + 2 + (g2 & 1), g2 >> 1, abort_flag, a.status)) break;
                     }
                     conv1_slice(h1, v, wf, x, frozen, a.slope, ptid);
                     fence_proxy_async();
                     mbar_arrive(bar_h1 + ((c0 + v + 2) & 3));
                 }
-            } else if (warp >= kEpiWarp0) {
-                // ---------------- epilogues (TMEM lane quarter q)
-                const int q = warp & 3;
-                auto epi3 = [&](int w) {
-                    const int g3 = g30 + w;
-                    if (!wait_n(bar_m3 + (g3 & 1), g3 >> 1, abort_flag, a.status)) return false;
-                    fence_after_sync();
-                    for (int mt = 0; mt < 2; ++mt)
-                        conv3_epilogue_part(t3buf(g3 & 1), slice_of(w), wf, x, frozen, a.use_tanh, INVERSE, logdet,
-                                            mt, q, lane);
+            } else if (warp < kEpiWarps) {
+                // ---------------- epilogues.  conv2: lane quarter q, channel half hf of each
+                // tile in turn; conv3: tile mt, lane quarter q.
+                const int q = warp & 3, hf = warp >> 2, mt = warp >> 2;
+                auto wait_batch = [&](int ub) {
+                    const int gb = g20 + ub + 1;
+                    return wait_n(bar_m3 + (gb & 1), gb >> 1, abort_flag, a.status);
+                };
+                auto release = [&](int ub) { mbar_arrive(bar_t3 + ((g20 + ub + 1) & 3)); };
+                auto epi3 = [&](int w) {                 // batches w-1, w, w+1 are complete
+                    float p[3][8];
+                    conv3_epi_load(p, t3reg(g20 + w), t3reg(g20 + w + 1), t3reg(g20 + w + 2), mt, q);
                     fence_before_sync();
-                    mbar_arrive(bar_t3 + (g3 & 1));
-                    return true;
+                    release(w - 1);                      // slice w is the last reader of batch w-1
+                    if (w == kL - 1) { release(kL - 1); release(kL); }
+                    conv3_epi_finish(p, slice_of(w), wf, x, frozen, a.use_tanh, INVERSE, logdet, mt, q, lane);
                 };
                 for (int u = -1; u <= kL && !*abort_flag; ++u) {
                     const int g2 = g20 + u + 1;
-                    if (u >= 2) {                        // h2 slot of u held h2[u-3], last read by conv3 of u-2
-                        const int g3 = g30 + u - 2;
-                        if (!wait_n(bar_m3 + (g3 & 1), g3 >> 1, abort_flag, a.status)) break;
+                    // batch u-2 done: slice u-3 is complete and the h2 slot of u (last read by
+                    // batch u-3) is free.  Draining slice u-3 first keeps the epilogue two
+                    // batches behind the tensor cores, so they never wait for it.
+                    if (u >= 2) {
+                        if (!wait_batch(u - 2)) break;
+                        fence_after_sync();
+                        if (u >= 3) epi3(u - 3);
                     }
-                    if (!wait_n(bar_m2 + (g2 & 1), g2 >> 1, abort_flag, a.status)) break;
-                    fence_after_sync();
-                    for (int mt = 0; mt < 2; ++mt)
-                        for (int hf = 0; hf < 2; ++hf)
-                            conv2_epilogue_part(h2, t2buf(g2 & 1), u, wf, a.slope, mt, q, hf, lane);
-                    fence_before_sync();
-                    mbar_arrive(bar_t2 + (g2 & 1));
+                    bool ok = true;
+                    for (int t = 0; t < 2; ++t) {
+                        if (!wait_n(bar_m2 + 2 * t + (g2 & 1), g2 >> 1, abort_flag, a.status)) { ok = false; break; }
+                        fence_after_sync();
+                        Conv2Parts P;
+                        conv2_epi_load(P, t2tile(t), q, hf);
+                        fence_before_sync();
+                        mbar_arrive(bar_t2 + t);         // the tile's TMEM buffer may be refilled
+                        conv2_epi_store(P, h2, u, wf, a.slope, t, q, hf, lane);
+                    }
+                    if (!ok) break;
                     fence_proxy_async();
                     mbar_arrive(bar_h2 + g2 % 3);
-                    if (u >= 2 && !epi3(u - 2)) break;
                 }
-                if (!*abort_flag) epi3(kL - 1);     // the loop handled conv3 of slices 0 .. L-2
+                // slices L-2 and L-1 complete with batches L-1 and L
+                if (!*abort_flag && wait_batch(kL - 1)) {
+                    fence_after_sync();
+                    epi3(kL - 2);
+                    if (wait_batch(kL)) {
+                        fence_after_sync();
+                        epi3(kL - 1);
+                    }
+                }
             }
             fence_before_sync();
             __syncthreads();
@@ -561,12 +646,12 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
 
         if (INVERSE) {
             for (int n = tid; n < V; n += kThreads) {
-                const float v = x[n];
+                const float v = x[xi(n)];
                 sumz2 += (double)v * v;
                 if (a.z_out) a.z_out[b * V + n] = v;
             }
         } else {
-            for (int n = tid; n < V; n += kThreads) a.phi_out[b * V + n] = x[n];
+            for (int n = tid; n < V; n += kThreads) a.phi_out[b * V + n] = x[xi(n)];
         }
         const double ld = block_sum(logdet, red);
         const double z2 = block_sum(sumz2, red);
@@ -577,10 +662,10 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
             double acc = 0.0;
             for (int n = tid; n < V; n += kThreads) {
                 const int xc = n & 15, yc = (n >> 4) & 15, zc = n >> 8;
-                const double hop = (double)x[(n & ~15) | wrap16(xc + 1)] +
-                                   (double)x[(zc << 8) | (wrap16(yc + 1) << 4) | xc] +
-                                   (double)x[(wrap16(zc + 1) << 8) | (yc << 4) | xc];
-                const double c = x[n], qq = c * c;
+                const double hop = (double)x[xi((n & ~15) | wrap16(xc + 1))] +
+                                   (double)x[xi((zc << 8) | (wrap16(yc + 1) << 4) | xc)] +
+                                   (double)x[xi((wrap16(zc + 1) << 8) | (yc << 4) | xc)];
+                const double c = x[xi(n)], qq = c * c;
                 acc += fma(qq, fma(a.lam, qq, c2d), -2.0 * c * hop);
             }
             S = block_sum(acc, red);
@@ -596,7 +681,7 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
         }
         __syncthreads();
     }
-    if (tid == 0) {
+    if (warp == kMmaWarp && lane == 0) {
         // after an abort some MMAs may still be queued: wait (bounded) until all
         // of this thread's tensor-core work is done before TMEM is freed
         mma_commit(bar_fin);
@@ -604,21 +689,23 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
     }
     fence_before_sync();
     __syncthreads();
-    if (warp == 0) {
+    if (warp == kMmaWarp) {
         fence_after_sync();
         tmem_dealloc(tmem, kTmemCols);
     }
 }
 
-constexpr size_t kSmemBytes = (size_t)kLayerBytes + 7 * (size_t)kSlotBytes + 4096 * 4 + 32 * 8 +
-                              16 * 8 + 4 + 4;
+constexpr size_t kSmemBytes = (size_t)kLayerBytes + 7 * (size_t)kSlotBytes + (size_t)kXFloats * 4 + 32 * 8 +
+                              20 * 8 + 4 + 4;
+static_assert(kSmemBytes <= 227 * 1024, "shared memory budget");
 
 // canonical FP32 -> per-layer block: W2 [tap9][kg][dxi*32 + o][8] bf16,
-// W3 [tap9][kg][dxi*8 + j][8] bf16 (j = 0: s, 1: t, else 0; rows 24..31 zero),
+// W3 [dy3][kg][d*8 + dxi*2 + j][8] bf16 (tap (d, dy, dxi); j = 0: s, 1: t; rows
+// with (row & 7) >= 6 or row >= 24 zero),
 // then FP32 W1s[t][c], b1, b2, b3.
 __global__ void repack_bf16_kernel(const float* __restrict__ canon, int64_t cstride, int n_layers,
                                    unsigned char* __restrict__ out) {
-    constexpr int n2 = 9 * 4 * 96 * 8, n3 = 9 * 4 * 32 * 8;
+    constexpr int n2 = 9 * 4 * 96 * 8, n3 = 3 * 4 * 32 * 8;
     const int64_t per = n2 + n3 + kF_N;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < per * n_layers;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -639,9 +726,11 @@ __global__ void repack_bf16_kernel(const float* __restrict__ canon, int64_t cstr
             reinterpret_cast<__nv_bfloat16*>(blk)[r] = __float2bfloat16_rn(v);
         } else if (r < n2 + n3) {
             const int r3 = (int)(r - n2);
-            const int e = r3 & 7, row = (r3 >> 3) & 31, kg = (r3 >> 8) & 3, tp = r3 >> 10;
-            const int dxi = row >> 3, j = row & 7, t = tp * 3 + dxi;
-            const float v = (dxi < 3 && j < 2) ? W3[((int64_t)j * kC + kg * 8 + e) * kT + t] : 0.f;
+            const int e = r3 & 7, row = (r3 >> 3) & 31, kg = (r3 >> 8) & 3, dyi = r3 >> 10;
+            const int d = row >> 3, rr = row & 7, dxi = rr >> 1, j = rr & 1;
+            const bool live = d < 3 && rr < 6;
+            const int t = live ? d * 9 + dyi * 3 + dxi : 0;
+            const float v = live ? W3[((int64_t)j * kC + kg * 8 + e) * kT + t] : 0.f;
             reinterpret_cast<__nv_bfloat16*>(blk + kW2Bytes)[r3] = __float2bfloat16_rn(v);
         } else {
             const int f = (int)(r - n2 - n3);
@@ -670,7 +759,7 @@ gf_status bf16_configure(gf_flow* f) {
 }
 
 gf_status repack_bf16(gf_flow* f, cudaStream_t stream) {
-    const int64_t total = (int64_t)(9 * 4 * 96 * 8 + 9 * 4 * 32 * 8 + kF_N) * f->shape.n_layers;
+    const int64_t total = (int64_t)(9 * 4 * 96 * 8 + 3 * 4 * 32 * 8 + kF_N) * f->shape.n_layers;
     const int grid = (int)std::min<int64_t>((total + 255) / 256, 4096);
     if (total == 0) return GF_OK;
     repack_bf16_kernel<<<grid, 256, 0, stream>>>(f->d_canon, f->canon_stride, f->shape.n_layers,
