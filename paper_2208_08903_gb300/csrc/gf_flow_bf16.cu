@@ -47,7 +47,7 @@ namespace gf {
 
 namespace {
 
-constexpr int kThreads = 17 * 32;                      // 8 epilogue + 8 producer warps + 1 MMA warp
+constexpr int kThreads = 20 * 32;                      // MMA warp, 8 epilogue, 8 producer, 3 spare warps
 constexpr int kL = 16, kC = 32, kT = 27;
 constexpr int kHaloSites = 18 * 16;                    // y = -1 .. 16
 constexpr int kCgStride = kHaloSites * 16;             // bytes between channel groups
@@ -71,9 +71,18 @@ constexpr int kLayerBytes = kW2Bytes + kW3Bytes + kF_N * 4;
 constexpr int kTmemC3 = 192;
 constexpr int kTmemCols = 512;
 constexpr long long kWaitLimit = 1ll << 22;             // bounded mbarrier wait (iterations)
-constexpr int kEpiWarps = 8, kEpiThreads = kEpiWarps * 32;                     // epilogue: warps 0..7
-constexpr int kProdWarp0 = 8, kProdWarps = 8, kProdThreads = kProdWarps * 32;   // conv1 producers: 8..15
-constexpr int kMmaWarp = 16;                                                    // tensor-core issue
+// Warp w runs on sub-partition w % 4 and may read TMEM lane quarter w % 4.  The
+// MMA-issuing warp 0 shares sub-partition 0 only with two epilogue warps (4, 8)
+// and two spare warps, so its issue slots are not taken by the FMA-heavy conv1
+// producers, which live on sub-partitions 1..3.
+constexpr int kMmaWarp = 0;
+constexpr int kEpiWarps = 8, kEpiThreads = kEpiWarps * 32;      // epilogue: warps 1..8 (e = w - 1)
+constexpr int kProdWarps = 8, kProdThreads = kProdWarps * 32;   // producers: 9, 10, 11, 13, 14, 15, 17, 18
+__device__ __forceinline__ int producer_index(int w) {
+    if (w < 9 || w > 18 || (w & 3) == 0) return -1;              // 12 and 16 stay on sub-partition 0
+    const int p = w - 9 - ((w - 9) >> 2);                           // 9..11 -> 0..2, 13..15 -> 3..5, 17, 18 -> 6, 7
+    return p < kProdWarps ? p : -1;
+}
 
 // ---------------------------------------------------------------- PTX wrappers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -157,6 +166,12 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
     d |= (uint64_t)1 << 46;              // descriptor version for tcgen05
     return d;                            // base offset 0, swizzle mode 0 (none)
 }
+// Moves a descriptor's start address by off (16-byte units).  The start field
+// never carries out of the low word (shared addresses < 256 KB), so one 32-bit
+// add replaces a 64-bit one: the single MMA-issuing thread is issue-bound.
+__device__ __forceinline__ uint64_t desc_add(uint64_t d, uint32_t off) {
+    return ((d >> 32) << 32) | (uint32_t)((uint32_t)d + off);
+}
 // Instruction descriptors: D = F32, A = B = BF16, both K-major, M = 128, N = 96 / 32.
 constexpr uint32_t kIdesc96 = (1u << 4) | (1u << 7) | (1u << 10) | ((96u >> 3) << 17) | ((128u >> 4) << 24);
 constexpr uint32_t kIdesc32 = (1u << 4) | (1u << 7) | (1u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
@@ -238,7 +253,7 @@ __device__ __forceinline__ void conv1_taps4(unsigned long long (&acc)[4][4], con
 // its 32 lanes cover rows y0..y0+3 x 8 sites, which with the padded x rows hits
 // 32 distinct banks, and their 16-byte stores cover all eight bank groups.
 __device__ __forceinline__ void conv1_slice(unsigned char* h1, int v, const float* wf, const float* x, int frozen,
-                                            float slope, int ptid) {
+                                            float slope, int ptid, const unsigned long long (&b1)[4]) {
     const int z = slice_of(v);
     unsigned char* slot = h1 + (size_t)h1_slot(v) * kSlotBytes;
     const int cg = ptid >> 6, pcls = (ptid >> 5) & 1, k = ptid & 31;
@@ -252,11 +267,9 @@ __device__ __forceinline__ void conv1_slice(unsigned char* h1, int v, const floa
 #pragma unroll
         for (int q = 0; q < 4; ++q) yr[q][d] = wrap16(y0 + 4 * q + d - 1) * kXRow;
     }
-    const ulonglong2 bA = *reinterpret_cast<const ulonglong2*>(wf + kF_b1 + cg * 8);
-    const ulonglong2 bB = *reinterpret_cast<const ulonglong2*>(wf + kF_b1 + cg * 8 + 4);
     unsigned long long acc[4][4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) { acc[q][0] = bA.x; acc[q][1] = bA.y; acc[q][2] = bB.x; acc[q][3] = bB.y; }
+    for (int q = 0; q < 4; ++q) { acc[q][0] = b1[0]; acc[q][1] = b1[1]; acc[q][2] = b1[2]; acc[q][3] = b1[3]; }
     if ((frozen ^ pcls) & 1) conv1_taps4<1>(acc, wf, x, zr, yr, xc, cg);
     else conv1_taps4<0>(acc, wf, x, zr, yr, xc, cg);
 #pragma unroll
@@ -290,8 +303,8 @@ __device__ __forceinline__ void issue_conv2_tile(const uint64_t (&a_slot)[3], ui
         for (int dyi = 0; dyi < 3; ++dyi) {
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
-                const uint64_t ad = a_slot[dzi] + (uint64_t)((2 * k * kCgStride + (mt * 8 + dyi) * 256) >> 4);
-                const uint64_t bd = b0 + (uint64_t)((dzi * 3 + dyi) * b_tap + k * b_k);
+                const uint64_t ad = desc_add(a_slot[dzi], (uint32_t)((2 * k * kCgStride + (mt * 8 + dyi) * 256) >> 4));
+                const uint64_t bd = desc_add(b0, (uint32_t)((dzi * 3 + dyi) * b_tap + k * b_k));
                 mma_bf16(d, ad, bd, kIdesc96, (dzi | dyi | k) ? 1u : 0u);
             }
         }
@@ -310,8 +323,8 @@ __device__ __forceinline__ void issue_conv3_batch(uint64_t a, uint64_t b0, uint3
         for (int k = 0; k < 2; ++k) {
 #pragma unroll
             for (int mt = 0; mt < 2; ++mt) {
-                const uint64_t ad = a + (uint64_t)((2 * k * kCgStride + (mt * 8 + dyi) * 256) >> 4);
-                const uint64_t bd = b0 + (uint64_t)(dyi * b_tap + k * b_k);
+                const uint64_t ad = desc_add(a, (uint32_t)((2 * k * kCgStride + (mt * 8 + dyi) * 256) >> 4));
+                const uint64_t bd = desc_add(b0, (uint32_t)(dyi * b_tap + k * b_k));
                 mma_bf16(region + (uint32_t)mt * 32, ad, bd, kIdesc32, (dyi | k) ? 1u : 0u);
             }
         }
@@ -329,7 +342,7 @@ __device__ __forceinline__ void conv2_epi_load(Conv2Parts& P, uint32_t tile_buf,
     tmem_ld16(base + 64u, P.pp);
     tmem_ld_wait();
 }
-__device__ __forceinline__ void conv2_epi_store(const Conv2Parts& P, unsigned char* h2, int v, const float* wf,
+__device__ __forceinline__ void conv2_epi_store(const Conv2Parts& P, unsigned char* h2, int v, const float (&b2)[16],
                                                 float slope, int mt, int q, int hf, int lane) {
     const int y = mt * 8 + q * 2 + (lane >> 4), xx = lane & 15;
     const int src_m = (lane & 16) | ((xx + 15) & 15);   // x - 1
@@ -337,15 +350,12 @@ __device__ __forceinline__ void conv2_epi_store(const Conv2Parts& P, unsigned ch
     unsigned char* slot = h2 + (size_t)h2_slot(v) * kSlotBytes;
 #pragma unroll
     for (int g = 0; g < 2; ++g) {
-        const float4 bA = *reinterpret_cast<const float4*>(wf + kF_b2 + hf * 16 + g * 8);
-        const float4 bB = *reinterpret_cast<const float4*>(wf + kF_b2 + hf * 16 + g * 8 + 4);
-        const float bias[8] = {bA.x, bA.y, bA.z, bA.w, bB.x, bB.y, bB.z, bB.w};
         float o[8];
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
             const int ch = g * 8 + c;
             const float s = P.p0[ch] + __shfl_sync(0xffffffffu, P.pm[ch], src_m) +
-                            __shfl_sync(0xffffffffu, P.pp[ch], src_p) + bias[c];
+                            __shfl_sync(0xffffffffu, P.pp[ch], src_p) + b2[ch];
             o[c] = s > 0.f ? s : slope * s;
         }
         store8(slot, hf * 2 + g, y, xx, o);
@@ -366,7 +376,7 @@ __device__ __forceinline__ void conv3_epi_load(float (&p)[3][8], uint32_t rm, ui
     tmem_ld8(rp + lane_base + 16u, p[2]);
     tmem_ld_wait();
 }
-__device__ __forceinline__ void conv3_epi_finish(const float (&p)[3][8], int z, const float* wf, float* x,
+__device__ __forceinline__ void conv3_epi_finish(const float (&p)[3][8], int z, float b3s, float b3t, float* x,
                                                  int frozen, int use_tanh, bool inverse, double& logdet, int mt,
                                                  int q, int lane) {
     const int y = mt * 8 + q * 2 + (lane >> 4), xx = lane & 15;
@@ -376,9 +386,8 @@ __device__ __forceinline__ void conv3_epi_finish(const float (&p)[3][8], int z, 
     const int src_m = (lane & 16) | ((xx + 15) & 15);
     const int src_p = (lane & 16) | ((xx + 1) & 15);
     const float spre = st[2] + __shfl_sync(0xffffffffu, st[0], src_m) + __shfl_sync(0xffffffffu, st[4], src_p) +
-                       wf[kF_b3];
-    const float tt = st[3] + __shfl_sync(0xffffffffu, st[1], src_m) + __shfl_sync(0xffffffffu, st[5], src_p) +
-                     wf[kF_b3 + 1];
+                       b3s;
+    const float tt = st[3] + __shfl_sync(0xffffffffu, st[1], src_m) + __shfl_sync(0xffffffffu, st[5], src_p) + b3t;
     if (((z + y + xx) & 1) != frozen) {
         const float s = use_tanh ? tanhf(spre) : spre;
         float& xv = x[(z * 16 + y) * kXRow + xx];
@@ -396,8 +405,9 @@ __device__ __forceinline__ void conv3_epi_finish(const float (&p)[3][8], int z, 
 __device__ __forceinline__ bool wait_n(uint64_t* bar, int n, volatile int* abort_flag, int32_t* status) {
     long long spins = 0;
     while (!mbar_try_wait(bar, (uint32_t)n & 1u)) {
-        if (*abort_flag) return false;
-        if (++spins > kWaitLimit) { *abort_flag = 1; set_status(status, GF_ETIMEOUT); return false; }
+        ++spins;
+        if ((spins & 63) == 0 && *abort_flag) return false;      // another thread gave up
+        if (spins > kWaitLimit) { *abort_flag = 1; set_status(status, GF_ETIMEOUT); return false; }
     }
     return true;
 }
@@ -422,9 +432,10 @@ __device__ __forceinline__ uint64_t mbar_arrive(uint64_t* bar) {
 //   released: bar_t3[gb & 3], completion gb >> 2.
 constexpr int kConv1PerLayer = 20, kConv2PerLayer = 18;
 
-// Warp roles: warps 0..7 run the conv2 and conv3 epilogues (warp w: M-tile
-// w >> 2, TMEM lane quarter w & 3); warps 8..15 compute conv1 (packed FFMA) into
-// the h1 slots; one lane of warp 16 issues every tcgen05.mma.  They synchronise through mbarriers only,
+// Warp roles: one lane of warp 0 issues every tcgen05.mma; warps 1..8 run the
+// conv2 and conv3 epilogues (e = w - 1: M-tile or channel half e >> 2, TMEM lane
+// quarter w & 3); eight warps on sub-partitions 1..3 compute conv1 (packed FFMA)
+// into the h1 slots; warps 12, 16 and 19 have no role inside a layer.  They synchronise through mbarriers only,
 // so the tensor cores, the FMA pipes and the epilogues overlap; the CTA meets
 // at a barrier only between layers.
 template <bool INVERSE>
@@ -480,8 +491,8 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
     // B: conv2 LBO = 96 rows x 16 B between K groups, conv3 LBO = 32 rows x 16 B, SBO = 128.
     const uint64_t a1_0 = smem_desc(smem_u32(h1), kCgStride, 128);
     const uint64_t a2_0 = smem_desc(smem_u32(h2), kCgStride, 128);
-    const auto a1 = [a1_0](int slot) { return a1_0 + (uint64_t)(slot * (kSlotBytes >> 4)); };
-    const auto a2 = [a2_0](int slot) { return a2_0 + (uint64_t)(slot * (kSlotBytes >> 4)); };
+    const auto a1 = [a1_0](int slot) { return desc_add(a1_0, (uint32_t)(slot * (kSlotBytes >> 4))); };
+    const auto a2 = [a2_0](int slot) { return desc_add(a2_0, (uint32_t)(slot * (kSlotBytes >> 4))); };
     const uint64_t b2d = smem_desc(smem_u32(w2s), 96 * 16, 128);
     const uint64_t b3d = smem_desc(smem_u32(w3s), 32 * 16, 128);
 
@@ -574,22 +585,33 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
                     if (!*abort_flag) batch(kL);
                 }
                 __syncwarp();
-            } else if (warp >= kProdWarp0 && warp < kProdWarp0 + kProdWarps) {
+            } else if (producer_index(warp) >= 0) {
                 // ---------------- conv1 producers
-                const int ptid = tid - kProdWarp0 * 32;
+                const int ptid = producer_index(warp) * 32 + lane;
+                unsigned long long b1[4];                // this thread's 8 conv1 biases, for the layer
+                {
+                    const ulonglong2 bA = *reinterpret_cast<const ulonglong2*>(wf + kF_b1 + (ptid >> 6) * 8);
+                    const ulonglong2 bB = *reinterpret_cast<const ulonglong2*>(wf + kF_b1 + (ptid >> 6) * 8 + 4);
+                    b1[0] = bA.x; b1[1] = bA.y; b1[2] = bB.x; b1[3] = bB.y;
+                }
                 for (int v = -2; v <= kL + 1 && !*abort_flag; ++v) {
                     if (v >= 2) {                        // slot of h1[v-4] is free once conv2 of slice v-3 is done
                         const int g2 = g20 + v - 2;          // (tile 1 is queued after tile 0)
                         if (!wait_n(bar_m2 + 2 + (g2 & 1), g2 >> 1, abort_flag, a.status)) break;
                     }
-                    conv1_slice(h1, v, wf, x, frozen, a.slope, ptid);
+                    conv1_slice(h1, v, wf, x, frozen, a.slope, ptid, b1);
                     fence_proxy_async();
                     mbar_arrive(bar_h1 + ((c0 + v + 2) & 3));
                 }
-            } else if (warp < kEpiWarps) {
+            } else if (warp >= 1 && warp <= kEpiWarps) {
                 // ---------------- epilogues.  conv2: lane quarter q, channel half hf of each
                 // tile in turn; conv3: tile mt, lane quarter q.
-                const int q = warp & 3, hf = warp >> 2, mt = warp >> 2;
+                const int e = warp - 1;                  // 0..7: quarters 1, 2, 3, 0, 1, 2, 3, 0
+                const int q = warp & 3, hf = e >> 2, mt = e >> 2;
+                float b2[16];                            // this thread's conv2 biases and the conv3 biases
+#pragma unroll
+                for (int c = 0; c < 16; ++c) b2[c] = wf[kF_b2 + hf * 16 + c];
+                const float b3s = wf[kF_b3], b3t = wf[kF_b3 + 1];
                 auto wait_batch = [&](int ub) {
                     const int gb = g20 + ub + 1;
                     return wait_n(bar_m3 + (gb & 1), gb >> 1, abort_flag, a.status);
@@ -601,7 +623,7 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
                     fence_before_sync();
                     release(w - 1);                      // slice w is the last reader of batch w-1
                     if (w == kL - 1) { release(kL - 1); release(kL); }
-                    conv3_epi_finish(p, slice_of(w), wf, x, frozen, a.use_tanh, INVERSE, logdet, mt, q, lane);
+                    conv3_epi_finish(p, slice_of(w), b3s, b3t, x, frozen, a.use_tanh, INVERSE, logdet, mt, q, lane);
                 };
                 for (int u = -1; u <= kL && !*abort_flag; ++u) {
                     const int g2 = g20 + u + 1;
@@ -621,7 +643,7 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
                         conv2_epi_load(P, t2tile(t), q, hf);
                         fence_before_sync();
                         mbar_arrive(bar_t2 + t);         // the tile's TMEM buffer may be refilled
-                        conv2_epi_store(P, h2, u, wf, a.slope, t, q, hf, lane);
+                        conv2_epi_store(P, h2, u, b2, a.slope, t, q, hf, lane);
                     }
                     if (!ok) break;
                     fence_proxy_async();
