@@ -23,7 +23,7 @@ _HDR = os.path.join(_HERE, "gf_oracle.h")
 _OUT = os.path.join(_HERE, "_build", "libgforacle.so")
 _lib = None
 
-BF16_H1, BF16_W2, BF16_H2, BF16_W3, BF16_W1, F32_IO = 1, 2, 4, 8, 16, 32
+BF16_H1, BF16_W2, BF16_H2, BF16_W3, BF16_W1, F32_IO, BF16_X1 = 1, 2, 4, 8, 16, 32, 64
 
 
 def build(force: bool = False) -> str:

@@ -221,10 +221,11 @@ static void conv(int64_t V, int T, const int64_t* nbr, int Cin, int Cout,
 }
 
 /* Network intermediates of one layer on one configuration. */
-typedef struct { double *h1pre, *h1, *h2pre, *h2, *spre, *s, *t; } net_buf;
+typedef struct { double *yin, *h1pre, *h1, *h2pre, *h2, *spre, *s, *t; } net_buf;
 
 static net_buf net_alloc(const gfo_shape* sh, int64_t V) {
     net_buf nb;
+    nb.yin = (double*)malloc(sizeof(double) * V);
     nb.h1pre = (double*)malloc(sizeof(double) * V * sh->c1);
     nb.h1 = (double*)malloc(sizeof(double) * V * sh->c1);
     nb.h2pre = (double*)malloc(sizeof(double) * V * sh->c2);
@@ -235,7 +236,7 @@ static net_buf net_alloc(const gfo_shape* sh, int64_t V) {
     return nb;
 }
 static void net_free(net_buf* nb) {
-    free(nb->h1pre); free(nb->h1); free(nb->h2pre); free(nb->h2);
+    free(nb->yin); free(nb->h1pre); free(nb->h1); free(nb->h2pre); free(nb->h2);
     free(nb->spre); free(nb->s); free(nb->t);
 }
 
@@ -244,6 +245,10 @@ static void net_free(net_buf* nb) {
  * (s) only when use_final_tanh; channel 1 is t. */
 static void net_forward(const gfo_shape* sh, layer_w lw, int32_t bf16, int64_t V, int T,
                         const int64_t* nbr, const double* y, net_buf* nb) {
+    if (bf16 & GFO_BF16_X1) {          /* the BF16 variant's conv1 reads the field in bf16 */
+        for (int64_t n = 0; n < V; ++n) nb->yin[n] = bf16_round(y[n]);
+        y = nb->yin;
+    }
     conv(V, T, nbr, 1, sh->c1, lw.W1, lw.b1, bf16 & GFO_BF16_W1, y, nb->h1pre);
     for (int64_t k = 0; k < V * sh->c1; ++k) {
         nb->h1[k] = lrelu(nb->h1pre[k], sh->leaky_slope);

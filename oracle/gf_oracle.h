@@ -62,7 +62,8 @@ enum {
     GFO_BF16_H2 = 4,   /* round h2 (after LeakyReLU) to bf16 */
     GFO_BF16_W3 = 8,   /* round conv3 weights to bf16 */
     GFO_BF16_W1 = 16,  /* round conv1 weights to bf16 */
-    GFO_F32_IO  = 32   /* round the prior sample z to fp32 (the paper's Float32 prior) */
+    GFO_F32_IO  = 32,  /* round the prior sample z to fp32 (the paper's Float32 prior) */
+    GFO_BF16_X1 = 64   /* round conv1's input (the masked field) to bf16 */
 };
 
 typedef struct {

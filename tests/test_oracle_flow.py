@@ -42,6 +42,8 @@ def scipy_net(shape, w, layer, y, round_fn=None, flags=0):
         return out
 
     W1 = rw(d["W1"]) if flags & 16 else d["W1"]
+    if flags & 64:
+        y = rw(y)
     W2 = rw(d["W2"]) if flags & 2 else d["W2"]
     W3 = rw(d["W3"]) if flags & 8 else d["W3"]
     h1 = lrelu(conv(y.reshape([1] + grid), W1, d["b1"]), shape.leaky_slope)
@@ -100,7 +102,7 @@ def test_bf16_rounding_points_vs_torch(orc):
     shape = gi.FlowShape(3, 3, 1, 8, 8)
     w = gi.init_weights(shape, seed=8)
     y = gi.random_field(3, 3, 1, seed=2)[0]
-    for flags in (1, 2, 4, 8, 16, 1 | 2 | 4 | 8):
+    for flags in (1, 2, 4, 8, 16, 64, 1 | 2 | 4 | 8, 1 | 2 | 4 | 8 | 16 | 64):
         s, t = orc.coupling_net(shape, w, 0, y, bf16_mask=flags)
         rs, rt = scipy_net(shape, w, 0, y, round_fn=rnd, flags=flags)
         assert np.allclose(s, rs, rtol=1e-9, atol=1e-10), flags
