@@ -1,41 +1,43 @@
-// gf_flow_bf16.cu -- fused coupling stack with conv2 and conv3 on the
+// gf_flow_bf16.cu -- fused coupling stack with conv1, conv2 and conv3 on the
 // 5th-generation tensor cores (tcgen05, BF16 operands, FP32 accumulation in
 // TMEM), for 3D lattices with L = 16 and hidden width 32.
 //
 // Paper arXiv:2208.08903 Sec. 1 (affine coupling layers, Jacobian, model
-// density, action); precision split of this variant: conv2 and conv3 operands
-// (h1, h2 and their weights) in BF16 with FP32 accumulation, conv1 and the
-// affine update in FP32, the field x in FP32, and log-det, sum z^2, S, log q,
-// log w in FP64.
+// density, action); precision split of this variant: the convolutions read
+// BF16 operands (the masked field, h1, h2 and the weights) and accumulate in
+// FP32; the field x and the affine update stay FP32; log-det, sum z^2, S,
+// log q and log w are FP64.
 //
 // Per CTA one configuration at a time (persistent).  Within a layer the
 // lattice is walked along z one 256-site slice at a time:
-//   conv1 (FFMA, only the 13/14 taps that reach fixed sites) -> h1 slice (BF16)
-//   conv2 as an implicit GEMM on the tensor cores -> h2 slice (BF16)
-//   conv3 as an implicit GEMM (N = 16, rows s and t) -> affine update of x
+//   conv1: per parity tile (M = 128 sites of one parity, K = the 13 or 14 taps
+//   that reach fixed sites, padded to 16, N = 32) -> h1 slice (BF16)
+//   conv2 as an implicit GEMM -> h2 slice (BF16)
+//   conv3 as an implicit GEMM (rows s and t) -> affine update of x
 // Implicit GEMM: per z-slice two M = 128 tiles (8 y-rows x 16 x); K = the 9
 // (dz,dy) taps x 32 channels in steps of 16; the three dx weight sets are
-// stacked along N (conv2: N = 96, conv3: N = 32), so one instruction yields
-// the three dx partial sums.  Activations are stored channel-
-// group major ([4][288 sites][8 ch], 288 = 18 y-rows with one periodic halo row
-// on each side), so each 8-site core matrix is 128 contiguous bytes and a
-// (dz,dy) shift is only a different start address.  The periodic x-shift is
-// not gathered: three accumulators P_dx (dx = -1, 0, +1) stay in TMEM and the
-// epilogues form out(x) = sum_dx P_dx(x + dx) with width-16 shuffles (one
-// x-row = one half-warp = 16 TMEM lanes).
+// stacked along N (conv2: N = 96; conv3: N = 32 with its three dz parts
+// stacked too), so one instruction yields the three dx partial sums.
+// Activations are stored channel-group major ([4][288 sites][8 ch], 288 = 18
+// y-rows with one periodic halo row on each side), so each 8-site core matrix
+// is 128 contiguous bytes and a (dz,dy) shift is only a different start
+// address.  The periodic x-shift is not gathered: the epilogues form
+// out(x) = sum_dx P_dx(x + dx) with width-16 shuffles (one x-row = one
+// half-warp = 16 TMEM lanes).
 // Warp-specialised pipeline within a layer (mbarriers only, no CTA barrier):
-// eight producer warps run conv1 on the FMA pipes (packed FP32x2 FMAs) up to
-// four slices ahead (four h1 slots); one thread of the MMA warp queues conv2 of
-// slice u tile by tile (one TMEM buffer per M-tile) and, once h2[u-1] exists,
-// one conv3 batch with every contribution of h2[u-1] (the three dz parts
-// stacked along N, so each h2 tile is read from shared memory three times
-// instead of nine; four TMEM batch regions); eight epilogue warps turn conv2
-// accumulators into h2 (three slots) and, from three batch regions, the conv3
-// result into the affine update of x.  The tensor cores read their operands
-// from shared memory at about 128 B per clock, so the number of operand bytes
-// per MMA, not the MMA count, bounds conv2 and conv3.  conv1 reads only fixed sites of
-// x and the update writes only the other parity, so x needs no ordering within
-// a layer; the CTA meets at a barrier between layers.
+// eight conv1 worker warps gather each slice's conv1 operand (the field at the
+// live taps, BF16) two slices ahead and turn the conv1 accumulators into h1
+// (four h1 slots); one thread of warp 0 queues conv1, conv2 of M-tile 0 and,
+// once h2[u-1] exists, one conv3 batch with every contribution of h2[u-1] (the
+// three dz parts stacked along N, so each h2 tile is read from shared memory
+// three times instead of nine; three TMEM batch regions); one thread of warp 17
+// queues conv2 of M-tile 1 (one TMEM buffer per M-tile); eight epilogue warps
+// turn conv2 accumulators into h2 (three slots) and, from three batch regions,
+// the conv3 result into the affine update of x.  A single issuing thread that
+// shares its sub-partition with busy warps cannot keep the tensor cores fed,
+// hence two issuers on separate sub-partitions.  conv1 reads only fixed sites
+// of x and the update writes only the other parity, so x needs no ordering
+// within a layer; the CTA meets at a barrier between layers.
 #include <algorithm>
 #include <cstring>
 
@@ -47,7 +49,7 @@ namespace gf {
 
 namespace {
 
-constexpr int kThreads = 20 * 32;                      // MMA warp, 8 epilogue, 8 producer, 3 spare warps
+constexpr int kThreads = 20 * 32;                      // 2 MMA-issuing, 8 epilogue, 8 conv1, 2 spare warps
 constexpr int kL = 16, kC = 32, kT = 27;
 constexpr int kHaloSites = 18 * 16;                    // y = -1 .. 16
 constexpr int kCgStride = kHaloSites * 16;             // bytes between channel groups
@@ -59,30 +61,37 @@ constexpr int kSlotBytes = 4 * kCgStride;              // [cg][site][8] bf16 = 1
 // 15, 22..31 zero), layout [dy3][kg][n][8] bf16.
 constexpr int kW2Bytes = 9 * 4 * 96 * 16;              // 55296
 constexpr int kW3Bytes = 3 * 4 * 32 * 16;              // 6144
-// The field x in shared memory: rows of 16 sites with a stride of 24 floats, so
-// the 32 lanes of a conv1 load (4 rows x 8 sites of one parity) hit 32 banks.
-constexpr int kXRow = 24, kXSlice = 16 * kXRow, kXFloats = 16 * kXSlice;
-// FP32 part of a layer block (floats): W1s[t][c], b1[c], b2[c], b3[2], pad
-constexpr int kF_W1 = 0, kF_b1 = kT * kC, kF_b2 = kF_b1 + kC, kF_b3 = kF_b2 + kC;
+// The field x in shared memory, [z][y][x] (rows of 16 floats).
+constexpr int kXRow = 16, kXSlice = 16 * kXRow, kXFloats = 16 * kXSlice;
+// conv1 B operands: for each tap set (NEED = 0, 1: the 13 or 14 taps that reach
+// fixed sites from a site of one parity, in tap order, padded to K = 16 with
+// zeros), W1 as [need][kg][32 rows][8] bf16.
+constexpr int kW1Bytes = 2 * 2 * 32 * 16;              // 2048
+// FP32 part of a layer block (floats): b1[c], b2[c], b3[2], pad
+constexpr int kF_b1 = 0, kF_b2 = kC, kF_b3 = 2 * kC;
 constexpr int kF_N = (kF_b3 + 2 + 3) & ~3;
-constexpr int kLayerBytes = kW2Bytes + kW3Bytes + kF_N * 4;
+constexpr int kLayerBytes = kW2Bytes + kW3Bytes + kW1Bytes + kF_N * 4;
+static_assert(kLayerBytes % 16 == 0, "layer block staged in 16-byte pieces");
 // TMEM columns: conv2 accumulators of tile 0 at 0 and tile 1 at 96 (N = 96 each);
-// four conv3 batch regions at 192 + 64 r (2 tiles x N = 32)
+// three conv3 batch regions at 192 + 64 r (2 tiles x N = 32); two conv1
+// accumulators at 384 + 64 b (2 parity tiles x N = 32)
 constexpr int kTmemC3 = 192;
+constexpr int kTmemC1 = 384;
+// conv1 A operands, double-buffered: [buffer][tile][kg][128 rows][8] bf16
+constexpr int kIm2colBufBytes = 2 * 2 * 128 * 16, kIm2colBytes = 2 * kIm2colBufBytes;
 constexpr int kTmemCols = 512;
 constexpr long long kWaitLimit = 1ll << 22;             // bounded mbarrier wait (iterations)
-// Warp w runs on sub-partition w % 4 and may read TMEM lane quarter w % 4.  The
-// MMA-issuing warp 0 shares sub-partition 0 only with two epilogue warps (4, 8)
-// and two spare warps, so its issue slots are not taken by the FMA-heavy conv1
-// producers, which live on sub-partitions 1..3.
+// Warp w runs on sub-partition w % 4 and may read TMEM lane quarter w % 4.
+// One lane of warp 0 issues conv1, conv2 of M-tile 0 and the conv3 batches; one
+// lane of warp 17 (another sub-partition) issues conv2 of M-tile 1, which
+// doubles the MMA issue rate; warps 1..8 are the conv2/conv3 epilogue
+// (e = w - 1); warps 9..16 are the conv1 workers (tile = (w - 9) >> 2, TMEM
+// lane quarter w & 3), which build conv1's A operand and turn its accumulator
+// into h1; warps 18 and 19 have no role inside a layer.
 constexpr int kMmaWarp = 0;
-constexpr int kEpiWarps = 8, kEpiThreads = kEpiWarps * 32;      // epilogue: warps 1..8 (e = w - 1)
-constexpr int kProdWarps = 8, kProdThreads = kProdWarps * 32;   // producers: 9, 10, 11, 13, 14, 15, 17, 18
-__device__ __forceinline__ int producer_index(int w) {
-    if (w < 9 || w > 18 || (w & 3) == 0) return -1;              // 12 and 16 stay on sub-partition 0
-    const int p = w - 9 - ((w - 9) >> 2);                           // 9..11 -> 0..2, 13..15 -> 3..5, 17, 18 -> 6, 7
-    return p < kProdWarps ? p : -1;
-}
+constexpr int kEpiWarps = 8, kEpiThreads = kEpiWarps * 32;      // warps 1..8
+constexpr int kC1Warp0 = 9, kProdThreads = 8 * 32;              // warps 9..16
+constexpr int kMma2Warp = 17;                                   // issues conv2 of M-tile 1
 
 // ---------------------------------------------------------------- PTX wrappers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -113,6 +122,14 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
     asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                 " selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+// Non-blocking test of an mbarrier phase (try_wait may suspend the thread).
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
                  " selp.u32 %0, 1, 0, p;\n}\n"
                  : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
     return ok != 0;
@@ -213,83 +230,40 @@ __device__ __forceinline__ int slice_of(int v) { return v & 15; }
 __device__ __forceinline__ int h1_slot(int v) { return (v + 16) & 3; }
 __device__ __forceinline__ int h2_slot(int v) { return (v + 15) % 3; }
 
-// Packed FP32 pairs for the conv1 FMAs: fma.rn.f32x2 rounds each half like fmaf.
-__device__ __forceinline__ unsigned long long f2pack(float lo, float hi) {
-    return ((unsigned long long)__float_as_uint(hi) << 32) | __float_as_uint(lo);
-}
-__device__ __forceinline__ void ffma2(unsigned long long& acc, unsigned long long a, unsigned long long b) {
-    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(a), "l"(b));
-}
-
-// The taps of conv1 that reach fixed sites from an output site of parity p are
-// those whose offset parity (|dz|+|dy|+|dx|) mod 2 equals NEED = frozen ^ p; the
-// tap set is chosen at compile time, so the loop has no branches.  Four sites
-// (rows y, y+4, y+8, y+12, same x and parity) share each tap's weight loads;
-// acc[q][j] holds channels (2j, 2j+1) of site q.
-template <int NEED>
-__device__ __forceinline__ void conv1_taps4(unsigned long long (&acc)[4][4], const float* wf, const float* x,
-                                            const int (&zr)[3], const int (&yr)[4][3], const int (&xc)[3], int cg) {
-#pragma unroll
+// conv1 tap sets: from an output site of parity p, the taps reaching fixed sites
+// are those whose offset parity (|dz|+|dy|+|dx|) mod 2 equals NEED = frozen ^ p.
+// tap_of(need, k) = the k-th such tap in tap order, or -1 past the end.
+__host__ __device__ constexpr int tap_of(int need, int k) {
+    int n = 0;
     for (int t = 0; t < kT; ++t) {
-        const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;
-        if (((dz + dy + dx + 1) & 1) != NEED) continue;                     // resolved at compile time
-        const ulonglong2 wA = *reinterpret_cast<const ulonglong2*>(wf + kF_W1 + t * kC + cg * 8);
-        const ulonglong2 wB = *reinterpret_cast<const ulonglong2*>(wf + kF_W1 + t * kC + cg * 8 + 4);
+        if (((t / 9 + (t / 3) % 3 + t % 3 + 1) & 1) != need) continue;
+        if (n == k) return t;
+        ++n;
+    }
+    return -1;
+}
+
+// conv1 A operand row of one site: the masked field at its 13 or 14 live taps
+// (BF16), zero-padded to K = 16, stored as the row's two 16-byte core-matrix
+// pieces.
+template <int NEED>
+__device__ __forceinline__ void im2col_row(unsigned char* a_tile, int r, const float* x, const int (&zr)[3],
+                                           const int (&yr)[3], const int (&xc)[3]) {
+    float v[16];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const float xv = x[zr[dz] + yr[q][dy] + xc[dx]];
-            const unsigned long long xx = f2pack(xv, xv);
-            ffma2(acc[q][0], xx, wA.x);
-            ffma2(acc[q][1], xx, wA.y);
-            ffma2(acc[q][2], xx, wB.x);
-            ffma2(acc[q][3], xx, wB.y);
-        }
+    for (int k = 0; k < 16; ++k) {
+        const int t = tap_of(NEED, k);
+        v[k] = t < 0 ? 0.f : x[zr[t / 9] + yr[(t / 3) % 3] + xc[t % 3]];
+    }
+#pragma unroll
+    for (int kg = 0; kg < 2; ++kg) {
+        __align__(16) __nv_bfloat162 p[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) p[i] = __floats2bfloat162_rn(v[kg * 8 + 2 * i], v[kg * 8 + 2 * i + 1]);
+        *reinterpret_cast<uint4*>(a_tile + kg * 2048 + r * 16) = *reinterpret_cast<const uint4*>(p);
     }
 }
 
-// conv1 + LReLU of virtual slice v into its h1 slot (BF16).  256 work items, one
-// per producer thread: (channel group, site parity class, 32 site quads).  A
-// warp holds sites of one parity, so all its lanes take the same 13 or 14 taps;
-// its 32 lanes cover rows y0..y0+3 x 8 sites, which with the padded x rows hits
-// 32 distinct banks, and their 16-byte stores cover all eight bank groups.
-__device__ __forceinline__ void conv1_slice(unsigned char* h1, int v, const float* wf, const float* x, int frozen,
-                                            float slope, int ptid, const unsigned long long (&b1)[4]) {
-    const int z = slice_of(v);
-    unsigned char* slot = h1 + (size_t)h1_slot(v) * kSlotBytes;
-    const int cg = ptid >> 6, pcls = (ptid >> 5) & 1, k = ptid & 31;
-    const int y0 = k >> 3, xh = k & 7;
-    const int xs = 2 * xh + ((pcls ^ z ^ y0) & 1);                  // rows y0 + 4q share the parity
-    int zr[3], yr[4][3], xc[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        zr[d] = wrap16(z + d - 1) * kXSlice;
-        xc[d] = wrap16(xs + d - 1);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) yr[q][d] = wrap16(y0 + 4 * q + d - 1) * kXRow;
-    }
-    unsigned long long acc[4][4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) { acc[q][0] = b1[0]; acc[q][1] = b1[1]; acc[q][2] = b1[2]; acc[q][3] = b1[3]; }
-    if ((frozen ^ pcls) & 1) conv1_taps4<1>(acc, wf, x, zr, yr, xc, cg);
-    else conv1_taps4<0>(acc, wf, x, zr, yr, xc, cg);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        float o[8];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const float lo = __uint_as_float((unsigned)acc[q][j]), hi = __uint_as_float((unsigned)(acc[q][j] >> 32));
-            o[2 * j] = lo > 0.f ? lo : slope * lo;
-            o[2 * j + 1] = hi > 0.f ? hi : slope * hi;
-        }
-        store8(slot, cg, y0 + 4 * q, xs, o);
-    }
-}
-
-// One elected thread: an implicit-GEMM convolution of a slice: for each of the
-// 2 M-tiles, 9 (dz,dy) taps x 2 K-steps of tcgen05.mma, each producing the three
-// dx partial sums at once (B holds the dx weight sets stacked along N).
-// a_slot[dzi] = A descriptors of the three input slices; b0 = B descriptor of
-// tap pair 0, K-step 0; tap pair p, K-step k adds p * b_tap + k * b_k (16-byte units).
 // One elected thread: conv2 of one M-tile (mt) of a slice as an implicit GEMM:
 // 9 (dz,dy) taps x 2 K-steps of tcgen05.mma, each producing the three dx
 // partial sums at once (B holds the dx weight sets stacked along N = 96).
@@ -443,18 +417,22 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* w2s = smem;                                                 // kW2Bytes
     unsigned char* w3s = smem + kW2Bytes;                                      // kW3Bytes
-    float* wf = reinterpret_cast<float*>(smem + kW2Bytes + kW3Bytes);          // kF_N floats
+    unsigned char* w1s = smem + kW2Bytes + kW3Bytes;                           // kW1Bytes
+    float* wf = reinterpret_cast<float*>(smem + kW2Bytes + kW3Bytes + kW1Bytes);  // kF_N floats
     unsigned char* h1 = smem + kLayerBytes;                                    // 4 slots
     unsigned char* h2 = h1 + 4 * kSlotBytes;                                   // 3 slots
     float* x = reinterpret_cast<float*>(h2 + 3 * kSlotBytes);                  // kXFloats (padded rows)
-    double* red = reinterpret_cast<double*>(x + kXFloats);                     // 32
+    unsigned char* im2col = reinterpret_cast<unsigned char*>(x + kXFloats);  // kIm2colBytes
+    double* red = reinterpret_cast<double*>(im2col + kIm2colBytes);            // 32
     uint64_t* bar_h1 = reinterpret_cast<uint64_t*>(red + 32);  // 4: h1 slot written (producers)
     uint64_t* bar_h2 = bar_h1 + 4;                             // 3: h2 slot written (epilogue)
     uint64_t* bar_m2 = bar_h2 + 3;                             // 4: conv2 of a tile done (commit)
     uint64_t* bar_m3 = bar_m2 + 4;                             // 2: conv3 batch done (commit)
     uint64_t* bar_t2 = bar_m3 + 2;                             // 2: conv2 tile buffer drained
-    uint64_t* bar_t3 = bar_t2 + 2;                             // 4: conv3 batch region released
-    uint64_t* bar_fin = bar_t3 + 4;                            // 1: every queued MMA done (exit)
+    uint64_t* bar_t3 = bar_t2 + 2;                             // 3: conv3 batch region released
+    uint64_t* bar_b1 = bar_t3 + 3;                             // 2: conv1 A operand built (workers)
+    uint64_t* bar_c1 = bar_b1 + 2;                             // 2: conv1 MMAs done (commit)
+    uint64_t* bar_fin = bar_c1 + 2;                            // 1: every queued MMA done (exit)
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar_fin + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
@@ -471,11 +449,13 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
             mbar_init(bar_m3 + i, 1);
             mbar_init(bar_t2 + i, kEpiThreads);
         }
-        for (int i = 0; i < 4; ++i) {
-            mbar_init(bar_m2 + i, 1);
-            mbar_init(bar_t3 + i, kEpiThreads);
+        for (int i = 0; i < 4; ++i) mbar_init(bar_m2 + i, 1);
+        for (int i = 0; i < 3; ++i) mbar_init(bar_t3 + i, kEpiThreads);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(bar_b1 + i, kProdThreads);
+            mbar_init(bar_c1 + i, 1);
         }
-        mbar_init(bar_fin, 1);
+        mbar_init(bar_fin, 2);                                 // one commit per issuing thread
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -484,7 +464,7 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
     fence_after_sync();
     const uint32_t tmem = *tmem_slot;
     const auto t2tile = [tmem](int t) { return tmem + (uint32_t)(t * 96); };
-    const auto t3reg = [tmem](int r) { return tmem + (uint32_t)(kTmemC3 + (r & 3) * 64); };
+    const auto t3reg = [tmem](int r) { return tmem + (uint32_t)(kTmemC3 + (r % 3) * 64); };
     const auto xi = [](int n) { return (n >> 4) * kXRow + (n & 15); };   // site -> padded x index
 
     // A descriptors of every h1 / h2 slot (LBO = channel-group stride, SBO = 8 sites);
@@ -495,6 +475,8 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
     const auto a2 = [a2_0](int slot) { return desc_add(a2_0, (uint32_t)(slot * (kSlotBytes >> 4))); };
     const uint64_t b2d = smem_desc(smem_u32(w2s), 96 * 16, 128);
     const uint64_t b3d = smem_desc(smem_u32(w3s), 32 * 16, 128);
+    const uint64_t b1d = smem_desc(smem_u32(w1s), 32 * 16, 128);               // + need * 64
+    const uint64_t a1c = smem_desc(smem_u32(im2col), 128 * 16, 128);           // + (buffer, tile)
 
     int seq = 0;                                   // layers processed by this CTA so far
     for (int64_t b = blockIdx.x; b < a.B; b += gridDim.x) {
@@ -557,51 +539,143 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
                     auto batch = [&](int ub) {
                         const int gh = g20 + ub + 1;
                         if (!wait_n(bar_h2 + gh % 3, gh / 3, abort_flag, a.status)) return false;
-                        if (gh >= 4 && !wait_n(bar_t3 + (gh & 3), (gh - 4) >> 2, abort_flag, a.status))
+                        if (gh >= 3 && !wait_n(bar_t3 + gh % 3, (gh - 3) / 3, abort_flag, a.status))
                             return false;
                         fence_after_sync();
-                        issue_conv3_batch(a2(h2_slot(ub)), b3d, t3reg(gh & 3));
+                        issue_conv3_batch(a2(h2_slot(ub)), b3d, t3reg(gh));
                         mma_commit(bar_m3 + (gh & 1));
                         return true;
                     };
+                    // conv1 of virtual slice v: one MMA (K = 16) per parity tile, B = the tile's
+                    // tap set, into buffer b = c & 1 (c = c0 + v + 2) of the A operand and of
+                    // the accumulator.  Issued as soon as the workers have built the A operand
+                    // (they build slice v only after draining conv1 of slice v-2).
+                    int next1 = -2;
+                    auto issue1 = [&]() {
+                        const int b = (c0 + next1 + 2) & 1;
+                        fence_after_sync();
+#pragma unroll
+                        for (int pc = 0; pc < 2; ++pc)
+                            mma_bf16(tmem + (uint32_t)(kTmemC1 + 64 * b + 32 * pc),
+                                     desc_add(a1c, (uint32_t)((b * kIm2colBufBytes + pc * 4096) >> 4)),
+                                     desc_add(b1d, (uint32_t)(((frozen ^ pc) & 1) * 64)), kIdesc32, 0u);
+                        mma_commit(bar_c1 + b);
+                        ++next1;
+                    };
+                    auto pump1 = [&]() {                 // non-blocking
+                        while (next1 <= kL + 1) {
+                            const int c = c0 + next1 + 2;
+                            if (!mbar_test_wait(bar_b1 + (c & 1), (uint32_t)(c >> 1) & 1u)) break;
+                            issue1();
+                        }
+                    };
+                    auto need1 = [&](int v) {            // blocking, up to conv1 of slice v
+                        while (next1 <= v) {
+                            const int c = c0 + next1 + 2;
+                            if (!wait_n(bar_b1 + (c & 1), c >> 1, abort_flag, a.status)) return false;
+                            issue1();
+                        }
+                        return true;
+                    };
                     for (int u = -1; u <= kL && !*abort_flag; ++u) {
+                        pump1();
                         if (u == -1) {
-                            if (!wait_h1(-2) || !wait_h1(-1) || !wait_h1(0)) break;
-                        } else if (!wait_h1(u + 1)) {
+                            if (!need1(0) || !wait_h1(-2) || !wait_h1(-1) || !wait_h1(0)) break;
+                        } else if (!need1(u + 1) || !wait_h1(u + 1)) {
                             break;
                         }
                         const int g2 = g20 + u + 1;
                         const uint64_t as[3] = {a1(h1_slot(u - 1)), a1(h1_slot(u)), a1(h1_slot(u + 1))};
-                        bool ok = true;
-                        for (int t = 0; t < 2 && ok; ++t) {      // tile t's buffer: drained by epi2 of u-1
-                            if (g2 >= 1 && !wait_n(bar_t2 + t, g2 - 1, abort_flag, a.status)) { ok = false; break; }
-                            fence_after_sync();
-                            issue_conv2_tile(as, b2d, t2tile(t), t);
-                            mma_commit(bar_m2 + 2 * t + (g2 & 1));
-                        }
-                        if (!ok) break;
+                        // M-tile 0 (tile 1 is issued by the second MMA thread); its buffer is
+                        // drained by epi2 of u-1
+                        if (g2 >= 1 && !wait_n(bar_t2, g2 - 1, abort_flag, a.status)) break;
+                        fence_after_sync();
+                        issue_conv2_tile(as, b2d, t2tile(0), 0);
+                        mma_commit(bar_m2 + (g2 & 1));
+                        pump1();
                         if (u >= 0 && !batch(u - 1)) break;
                     }
                     if (!*abort_flag) batch(kL);
                 }
                 __syncwarp();
-            } else if (producer_index(warp) >= 0) {
-                // ---------------- conv1 producers
-                const int ptid = producer_index(warp) * 32 + lane;
-                unsigned long long b1[4];                // this thread's 8 conv1 biases, for the layer
-                {
-                    const ulonglong2 bA = *reinterpret_cast<const ulonglong2*>(wf + kF_b1 + (ptid >> 6) * 8);
-                    const ulonglong2 bB = *reinterpret_cast<const ulonglong2*>(wf + kF_b1 + (ptid >> 6) * 8 + 4);
-                    b1[0] = bA.x; b1[1] = bA.y; b1[2] = bB.x; b1[3] = bB.y;
-                }
-                for (int v = -2; v <= kL + 1 && !*abort_flag; ++v) {
-                    if (v >= 2) {                        // slot of h1[v-4] is free once conv2 of slice v-3 is done
-                        const int g2 = g20 + v - 2;          // (tile 1 is queued after tile 0)
-                        if (!wait_n(bar_m2 + 2 + (g2 & 1), g2 >> 1, abort_flag, a.status)) break;
+            } else if (warp == kMma2Warp) {
+                // ---------------- second tensor-core issue thread: conv2 of M-tile 1
+                if (lane == 0) {
+                    for (int u = -1; u <= kL && !*abort_flag; ++u) {
+                        bool ok = true;
+                        for (int v = (u == -1 ? -2 : u + 1); v <= u + 1 && ok; ++v) {
+                            const int c = c0 + v + 2;
+                            ok = wait_n(bar_h1 + (c & 3), c >> 2, abort_flag, a.status);
+                        }
+                        const int g2 = g20 + u + 1;
+                        if (!ok || (g2 >= 1 && !wait_n(bar_t2 + 1, g2 - 1, abort_flag, a.status))) break;
+                        fence_after_sync();
+                        const uint64_t as[3] = {a1(h1_slot(u - 1)), a1(h1_slot(u)), a1(h1_slot(u + 1))};
+                        issue_conv2_tile(as, b2d, t2tile(1), 1);
+                        mma_commit(bar_m2 + 2 + (g2 & 1));
                     }
-                    conv1_slice(h1, v, wf, x, frozen, a.slope, ptid, b1);
+                }
+                __syncwarp();
+            } else if (warp >= kC1Warp0 && warp < kC1Warp0 + 8) {
+                // ---------------- conv1 workers: thread = row r of parity tile pc.  Two A
+                // operand buffers and two accumulators (b = c & 1): the A operand of slice
+                // v+2 is built as soon as conv1 of slice v has been drained.
+                const int pc = (warp - kC1Warp0) >> 2, r = ((warp & 3) << 5) | lane;
+                const int y = r >> 3, xh = r & 7;
+                const int need = (frozen ^ pc) & 1;
+                const uint32_t t1lane = (uint32_t)((warp & 3) * 32) << 16;
+                auto build = [&](int v) {                // A operand of slice v, then signal it
+                    const int c = c0 + v + 2;
+                    const int z = slice_of(v);
+                    const int xs = 2 * xh + ((pc ^ z ^ y) & 1);
+                    int zr[3], yr[3], xc[3];
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        zr[d] = wrap16(z + d - 1) * kXSlice;
+                        yr[d] = wrap16(y + d - 1) * kXRow;
+                        xc[d] = wrap16(xs + d - 1);
+                    }
+                    unsigned char* a_tile = im2col + (c & 1) * kIm2colBufBytes + pc * 4096;
+                    if (need) im2col_row<1>(a_tile, r, x, zr, yr, xc);
+                    else im2col_row<0>(a_tile, r, x, zr, yr, xc);
                     fence_proxy_async();
-                    mbar_arrive(bar_h1 + ((c0 + v + 2) & 3));
+                    mbar_arrive(bar_b1 + (c & 1));
+                };
+                build(-2);
+                build(-1);
+                for (int v = -2; v <= kL + 1 && !*abort_flag; ++v) {
+                    const int c = c0 + v + 2;
+                    if (!wait_n(bar_c1 + (c & 1), c >> 1, abort_flag, a.status)) break;
+                    fence_after_sync();
+                    float d[32];
+                    const uint32_t acc = tmem + (uint32_t)(kTmemC1 + 64 * (c & 1) + 32 * pc) + t1lane;
+                    tmem_ld16(acc, *reinterpret_cast<float(*)[16]>(d));
+                    tmem_ld16(acc + 16u, *reinterpret_cast<float(*)[16]>(d + 16));
+                    tmem_ld_wait();
+                    fence_before_sync();
+                    // its arrival also says this accumulator (and A buffer) may be reused
+                    if (v + 2 <= kL + 1) build(v + 2);
+                    if (v >= 2) {                        // slot of h1[v-4] is free once conv2 of slice v-3 is done
+                        const int g2 = g20 + v - 2;
+                        if (!wait_n(bar_m2 + (g2 & 1), g2 >> 1, abort_flag, a.status) ||
+                            !wait_n(bar_m2 + 2 + (g2 & 1), g2 >> 1, abort_flag, a.status))
+                            break;
+                    }
+                    const int z = slice_of(v);
+                    const int xs = 2 * xh + ((pc ^ z ^ y) & 1);
+                    unsigned char* slot = h1 + (size_t)h1_slot(v) * kSlotBytes;
+#pragma unroll
+                    for (int cg = 0; cg < 4; ++cg) {
+                        float o[8];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            const float hv = d[cg * 8 + i] + wf[kF_b1 + cg * 8 + i];
+                            o[i] = hv > 0.f ? hv : a.slope * hv;
+                        }
+                        store8(slot, cg, y, xs, o);
+                    }
+                    fence_proxy_async();
+                    mbar_arrive(bar_h1 + (c & 3));
                 }
             } else if (warp >= 1 && warp <= kEpiWarps) {
                 // ---------------- epilogues.  conv2: lane quarter q, channel half hf of each
@@ -616,7 +690,7 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
                     const int gb = g20 + ub + 1;
                     return wait_n(bar_m3 + (gb & 1), gb >> 1, abort_flag, a.status);
                 };
-                auto release = [&](int ub) { mbar_arrive(bar_t3 + ((g20 + ub + 1) & 3)); };
+                auto release = [&](int ub) { mbar_arrive(bar_t3 + (g20 + ub + 1) % 3); };
                 auto epi3 = [&](int w) {                 // batches w-1, w, w+1 are complete
                     float p[3][8];
                     conv3_epi_load(p, t3reg(g20 + w), t3reg(g20 + w + 1), t3reg(g20 + w + 2), mt, q);
@@ -703,9 +777,10 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
         }
         __syncthreads();
     }
+    // after an abort some MMAs may still be queued: both issuing threads commit,
+    // and TMEM is freed only once all their tensor-core work is done (bounded wait)
+    if (warp == kMma2Warp && lane == 0) mma_commit(bar_fin);
     if (warp == kMmaWarp && lane == 0) {
-        // after an abort some MMAs may still be queued: wait (bounded) until all
-        // of this thread's tensor-core work is done before TMEM is freed
         mma_commit(bar_fin);
         for (long long spins = 0; !mbar_try_wait(bar_fin, 0u) && spins < kWaitLimit; ++spins) {}
     }
@@ -717,18 +792,19 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
     }
 }
 
-constexpr size_t kSmemBytes = (size_t)kLayerBytes + 7 * (size_t)kSlotBytes + (size_t)kXFloats * 4 + 32 * 8 +
-                              20 * 8 + 4 + 4;
+constexpr size_t kSmemBytes = (size_t)kLayerBytes + 7 * (size_t)kSlotBytes + (size_t)kXFloats * 4 + kIm2colBytes +
+                              32 * 8 + 24 * 8 + 4 + 4;
 static_assert(kSmemBytes <= 227 * 1024, "shared memory budget");
 
 // canonical FP32 -> per-layer block: W2 [tap9][kg][dxi*32 + o][8] bf16,
 // W3 [dy3][kg][d*8 + dxi*2 + j][8] bf16 (tap (d, dy, dxi); j = 0: s, 1: t; rows
 // with (row & 7) >= 6 or row >= 24 zero),
-// then FP32 W1s[t][c], b1, b2, b3.
+// then W1 as the two conv1 B operands [need][kg][o][8] bf16 (tap_of order), then
+// FP32 b1, b2, b3.
 __global__ void repack_bf16_kernel(const float* __restrict__ canon, int64_t cstride, int n_layers,
                                    unsigned char* __restrict__ out) {
-    constexpr int n2 = 9 * 4 * 96 * 8, n3 = 3 * 4 * 32 * 8;
-    const int64_t per = n2 + n3 + kF_N;
+    constexpr int n2 = 9 * 4 * 96 * 8, n3 = 3 * 4 * 32 * 8, n1 = 2 * 2 * 32 * 8;
+    const int64_t per = n2 + n3 + n1 + kF_N;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < per * n_layers;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int l = (int)(i / per);
@@ -754,14 +830,19 @@ __global__ void repack_bf16_kernel(const float* __restrict__ canon, int64_t cstr
             const int t = live ? d * 9 + dyi * 3 + dxi : 0;
             const float v = live ? W3[((int64_t)j * kC + kg * 8 + e) * kT + t] : 0.f;
             reinterpret_cast<__nv_bfloat16*>(blk + kW2Bytes)[r3] = __float2bfloat16_rn(v);
+        } else if (r < n2 + n3 + n1) {
+            const int r1 = (int)(r - n2 - n3);
+            const int e = r1 & 7, o = (r1 >> 3) & 31, kg = (r1 >> 8) & 1, need = r1 >> 9;
+            const int t = tap_of(need, kg * 8 + e);
+            const float v = t < 0 ? 0.f : W1[(int64_t)o * kT + t];
+            reinterpret_cast<__nv_bfloat16*>(blk + kW2Bytes + kW3Bytes)[r1] = __float2bfloat16_rn(v);
         } else {
-            const int f = (int)(r - n2 - n3);
+            const int f = (int)(r - n2 - n3 - n1);
             float v = 0.f;
-            if (f < kF_b1) v = W1[(f % kC) * kT + f / kC];
-            else if (f < kF_b2) v = b1[f - kF_b1];
+            if (f < kF_b2) v = b1[f - kF_b1];
             else if (f < kF_b3) v = b2[f - kF_b2];
             else if (f < kF_b3 + 2) v = b3[f - kF_b3];
-            reinterpret_cast<float*>(blk + kW2Bytes + kW3Bytes)[f] = v;
+            reinterpret_cast<float*>(blk + kW2Bytes + kW3Bytes + kW1Bytes)[f] = v;
         }
     }
 }
@@ -781,7 +862,7 @@ gf_status bf16_configure(gf_flow* f) {
 }
 
 gf_status repack_bf16(gf_flow* f, cudaStream_t stream) {
-    const int64_t total = (int64_t)(9 * 4 * 96 * 8 + 3 * 4 * 32 * 8 + kF_N) * f->shape.n_layers;
+    const int64_t total = (int64_t)(9 * 4 * 96 * 8 + 3 * 4 * 32 * 8 + 2 * 2 * 32 * 8 + kF_N) * f->shape.n_layers;
     const int grid = (int)std::min<int64_t>((total + 255) / 256, 4096);
     if (total == 0) return GF_OK;
     repack_bf16_kernel<<<grid, 256, 0, stream>>>(f->d_canon, f->canon_stride, f->shape.n_layers,

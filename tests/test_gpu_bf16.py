@@ -1,8 +1,8 @@
 """GPU parity of the BF16 tensor-core variant (3D L=16, hidden 32).
 
-The kernel rounds h1 (after LeakyReLU), the conv2 weights and h2 (after
-LeakyReLU) to bf16 and accumulates conv2 in FP32 on the tensor cores; all sums
-over the lattice are FP64.  It is compared with the oracle in the matching
+The kernel rounds conv1's input (the masked field) and all conv weights, h1
+(after LeakyReLU) and h2 (after LeakyReLU) to bf16 and accumulates every
+convolution in FP32 on the tensor cores; all sums over the lattice are FP64.  It is compared with the oracle in the matching
 BF16-emulation mode (same rounding points, FP64 elsewhere), and its error against the pure FP64 oracle is reported (max and p99 per result).
 
 Tolerances against the BF16-emulated oracle: two bf16 ulps (2^-7) relative per
@@ -20,7 +20,7 @@ import gf_inputs as gi
 from gpu_util import assert_logw_close, assert_sites_close, require_gpu
 
 pytestmark = pytest.mark.gpu
-BF16_MODE = 1 | 2 | 4 | 8 | 32      # H1 | W2 | H2 | W3 | FP32 prior
+BF16_MODE = 1 | 2 | 4 | 8 | 16 | 32 | 64   # H1 | W2 | H2 | W3 | W1 | FP32 prior | conv1 input
 RTOL = 2.0**-7                      # per site
 LW_RTOL = 1e-3                      # per log-weight
 
