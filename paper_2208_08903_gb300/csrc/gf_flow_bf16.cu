@@ -27,15 +27,15 @@
 // Warp-specialised pipeline within a layer (mbarriers only, no CTA barrier):
 // eight conv1 worker warps gather each slice's conv1 operand (the field at the
 // live taps, BF16) two slices ahead and turn the conv1 accumulators into h1
-// (four h1 slots); one thread of warp 0 queues conv1, conv2 of M-tile 0 and,
-// once h2[u-1] exists, one conv3 batch with every contribution of h2[u-1] (the
-// three dz parts stacked along N, so each h2 tile is read from shared memory
-// three times instead of nine; three TMEM batch regions); one thread of warp 17
-// queues conv2 of M-tile 1 (one TMEM buffer per M-tile); eight epilogue warps
-// turn conv2 accumulators into h2 (three slots) and, from three batch regions,
-// the conv3 result into the affine update of x.  A single issuing thread that
-// shares its sub-partition with busy warps cannot keep the tensor cores fed,
-// hence two issuers on separate sub-partitions.  conv1 reads only fixed sites
+// (four h1 slots); four single threads, one per sub-partition, queue the
+// tensor-core work: conv2 of M-tile 0, conv2 of M-tile 1 (one TMEM buffer per
+// M-tile), the conv3 batches (once h2[u] exists, one batch with every
+// contribution of h2[u]: the three dz parts stacked along N, so each h2 tile is
+// read from shared memory three times instead of nine; three TMEM batch
+// regions) and conv1; eight epilogue warps turn conv2 accumulators into h2
+// (three slots) and, from three batch regions, the conv3 result into the affine
+// update of x.  An issuing thread stalls behind its own queued MMAs, so each
+// kind of work has its own issuer and none waits for another's backlog.  conv1 reads only fixed sites
 // of x and the update writes only the other parity, so x needs no ordering
 // within a layer; the CTA meets at a barrier between layers.
 #include <algorithm>
@@ -49,7 +49,7 @@ namespace gf {
 
 namespace {
 
-constexpr int kThreads = 20 * 32;                      // 2 MMA-issuing, 8 epilogue, 8 conv1, 2 spare warps
+constexpr int kThreads = 20 * 32;                      // 4 MMA-issuing, 8 epilogue, 8 conv1 warps
 constexpr int kL = 16, kC = 32, kT = 27;
 constexpr int kHaloSites = 18 * 16;                    // y = -1 .. 16
 constexpr int kCgStride = kHaloSites * 16;             // bytes between channel groups
@@ -61,8 +61,12 @@ constexpr int kSlotBytes = 4 * kCgStride;              // [cg][site][8] bf16 = 1
 // 15, 22..31 zero), layout [dy3][kg][n][8] bf16.
 constexpr int kW2Bytes = 9 * 4 * 96 * 16;              // 55296
 constexpr int kW3Bytes = 3 * 4 * 32 * 16;              // 6144
-// The field x in shared memory, [z][y][x] (rows of 16 floats).
+// The field x in shared memory, [z][y][x] (rows of 16 floats).  Column x of row y
+// is stored at x ^ xswz(y): a warp of conv1 gathers reads four consecutive rows at
+// one column parity each, and the swizzle puts those rows in four distinct
+// (bank half, parity) classes, so the gathers are free of bank conflicts.
 constexpr int kXRow = 16, kXSlice = 16 * kXRow, kXFloats = 16 * kXSlice;
+__device__ __forceinline__ int xswz(int y) { return (y >> 1) & 1; }
 // conv1 B operands: for each tap set (NEED = 0, 1: the 13 or 14 taps that reach
 // fixed sites from a site of one parity, in tap order, padded to K = 16 with
 // zeros), W1 as [need][kg][32 rows][8] bf16.
@@ -82,16 +86,18 @@ constexpr int kIm2colBufBytes = 2 * 2 * 128 * 16, kIm2colBytes = 2 * kIm2colBufB
 constexpr int kTmemCols = 512;
 constexpr long long kWaitLimit = 1ll << 22;             // bounded mbarrier wait (iterations)
 // Warp w runs on sub-partition w % 4 and may read TMEM lane quarter w % 4.
-// One lane of warp 0 issues conv1, conv2 of M-tile 0 and the conv3 batches; one
-// lane of warp 17 (another sub-partition) issues conv2 of M-tile 1, which
-// doubles the MMA issue rate; warps 1..8 are the conv2/conv3 epilogue
-// (e = w - 1); warps 9..16 are the conv1 workers (tile = (w - 9) >> 2, TMEM
-// lane quarter w & 3), which build conv1's A operand and turn its accumulator
-// into h1; warps 18 and 19 have no role inside a layer.
-constexpr int kMmaWarp = 0;
+// One lane each of warps 0, 17, 18 and 19 (sub-partitions 0..3) issues conv2 of
+// M-tile 0, conv2 of M-tile 1, the conv3 batches and conv1; warps 1..8 are the
+// conv2/conv3 epilogue (e = w - 1); warps 9..16 are the conv1 workers (tile =
+// (w - 9) >> 2, TMEM lane quarter w & 3), which build conv1's A operand and
+// turn its accumulator into h1.
+constexpr int kMmaWarp = 0;                                     // conv2 of M-tile 0; owns TMEM
 constexpr int kEpiWarps = 8, kEpiThreads = kEpiWarps * 32;      // warps 1..8
 constexpr int kC1Warp0 = 9, kProdThreads = 8 * 32;              // warps 9..16
-constexpr int kMma2Warp = 17;                                   // issues conv2 of M-tile 1
+constexpr int kMma2Warp = 17;                                   // conv2 of M-tile 1
+constexpr int kMma3Warp = 18;                                   // conv3 batches
+constexpr int kMma1Warp = 19;                                   // conv1
+constexpr int kIssuers = 4;
 
 // ---------------------------------------------------------------- PTX wrappers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -122,14 +128,6 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
     asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-                 " selp.u32 %0, 1, 0, p;\n}\n"
-                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
-    return ok != 0;
-}
-// Non-blocking test of an mbarrier phase (try_wait may suspend the thread).
-__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile("{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
                  " selp.u32 %0, 1, 0, p;\n}\n"
                  : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
     return ok != 0;
@@ -243,17 +241,25 @@ __host__ __device__ constexpr int tap_of(int need, int k) {
     return -1;
 }
 
+// conv1's bias rides in the last two K columns (A = 1, B = b1 split into a BF16
+// head and a BF16 remainder, so the FP32 accumulator adds b1 to about 2^-17);
+// every tap set has at most 14 live taps.
+constexpr int kBiasK = 14;
+static_assert(tap_of(0, kBiasK) < 0 && tap_of(1, kBiasK) < 0, "conv1 bias columns must be padding");
+
 // conv1 A operand row of one site: the masked field at its 13 or 14 live taps
-// (BF16), zero-padded to K = 16, stored as the row's two 16-byte core-matrix
-// pieces.
+// (BF16), zero-padded, then the two bias columns (1.0), stored as the row's two
+// 16-byte core-matrix pieces.  yr[dy] = row offset, ys[dy] = that row's column
+// swizzle, xc[dx] = column.
 template <int NEED>
 __device__ __forceinline__ void im2col_row(unsigned char* a_tile, int r, const float* x, const int (&zr)[3],
-                                           const int (&yr)[3], const int (&xc)[3]) {
+                                           const int (&yr)[3], const int (&ys)[3], const int (&xc)[3]) {
     float v[16];
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
         const int t = tap_of(NEED, k);
-        v[k] = t < 0 ? 0.f : x[zr[t / 9] + yr[(t / 3) % 3] + xc[t % 3]];
+        v[k] = k >= kBiasK ? 1.f
+                           : (t < 0 ? 0.f : x[zr[t / 9] + yr[(t / 3) % 3] + (xc[t % 3] ^ ys[(t / 3) % 3])]);
     }
 #pragma unroll
     for (int kg = 0; kg < 2; ++kg) {
@@ -364,7 +370,7 @@ __device__ __forceinline__ void conv3_epi_finish(const float (&p)[3][8], int z, 
     const float tt = st[3] + __shfl_sync(0xffffffffu, st[1], src_m) + __shfl_sync(0xffffffffu, st[5], src_p) + b3t;
     if (((z + y + xx) & 1) != frozen) {
         const float s = use_tanh ? tanhf(spre) : spre;
-        float& xv = x[(z * 16 + y) * kXRow + xx];
+        float& xv = x[(z * 16 + y) * kXRow + (xx ^ xswz(y))];
         if (!inverse) xv = fmaf(xv, expf(s), tt);
         else xv = (xv - tt) * expf(-s);
         logdet += (double)s;
@@ -402,16 +408,16 @@ __device__ __forceinline__ uint64_t mbar_arrive(uint64_t* bar) {
 //   h1 slot: bar_h1[c % 4], completion c / 4;
 //   conv2 of tile t: bar_m2[2 t + (g2 & 1)] completion g2 >> 1; its TMEM drained:
 //   bar_t2[t] completion g2; h2 written: bar_h2[g2 % 3], completion g2 / 3;
-//   conv3 batch gb: bar_m3[gb & 1], completion gb >> 1; its region gb & 3
-//   released: bar_t3[gb & 3], completion gb >> 2.
+//   conv3 batch gb: bar_m3[gb & 1], completion gb >> 1; its region gb % 3
+//   released: bar_t3[gb % 3], completion gb / 3.
 constexpr int kConv1PerLayer = 20, kConv2PerLayer = 18;
 
-// Warp roles: one lane of warp 0 issues every tcgen05.mma; warps 1..8 run the
+// Warp roles: four issuing threads (warps 0, 17, 18, 19); warps 1..8 run the
 // conv2 and conv3 epilogues (e = w - 1: M-tile or channel half e >> 2, TMEM lane
-// quarter w & 3); eight warps on sub-partitions 1..3 compute conv1 (packed FFMA)
-// into the h1 slots; warps 12, 16 and 19 have no role inside a layer.  They synchronise through mbarriers only,
-// so the tensor cores, the FMA pipes and the epilogues overlap; the CTA meets
-// at a barrier only between layers.
+// quarter w & 3); warps 9..16 build conv1's operands and turn its accumulators
+// into the h1 slots.  They synchronise through mbarriers only, so the tensor
+// cores and the epilogues overlap; the CTA meets at a barrier only between
+// layers.
 template <bool INVERSE>
 __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a) {
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -455,7 +461,7 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
             mbar_init(bar_b1 + i, kProdThreads);
             mbar_init(bar_c1 + i, 1);
         }
-        mbar_init(bar_fin, 2);                                 // one commit per issuing thread
+        mbar_init(bar_fin, kIssuers);                          // one commit per issuing thread
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -465,7 +471,7 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
     const uint32_t tmem = *tmem_slot;
     const auto t2tile = [tmem](int t) { return tmem + (uint32_t)(t * 96); };
     const auto t3reg = [tmem](int r) { return tmem + (uint32_t)(kTmemC3 + (r % 3) * 64); };
-    const auto xi = [](int n) { return (n >> 4) * kXRow + (n & 15); };   // site -> padded x index
+    const auto xi = [](int n) { return (n >> 4) * kXRow + ((n & 15) ^ xswz(n >> 4)); };   // site -> x index
 
     // A descriptors of every h1 / h2 slot (LBO = channel-group stride, SBO = 8 sites);
     // B: conv2 LBO = 96 rows x 16 B between K groups, conv3 LBO = 32 rows x 16 B, SBO = 128.
@@ -527,80 +533,11 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
             __syncthreads();
             const int c0 = seq * kConv1PerLayer, g20 = seq * kConv2PerLayer;
 
-            if (warp == kMmaWarp) {
-                // ---------------- tensor-core issue (one thread)
+            if (warp == kMmaWarp || warp == kMma2Warp) {
+                // ---------------- conv2 of M-tile t (one thread): slice u needs h1 of u-1..u+1
+                // and the tile's TMEM buffer drained by the epilogue of u-1
                 if (lane == 0) {
-                    auto wait_h1 = [&](int v) {
-                        const int c = c0 + v + 2;
-                        return wait_n(bar_h1 + (c & 3), c >> 2, abort_flag, a.status);
-                    };
-                    // conv3 batch ub: every contribution of h2[ub] (needs h2[ub] written and
-                    // the batch region free: batch ub-4's readers drained)
-                    auto batch = [&](int ub) {
-                        const int gh = g20 + ub + 1;
-                        if (!wait_n(bar_h2 + gh % 3, gh / 3, abort_flag, a.status)) return false;
-                        if (gh >= 3 && !wait_n(bar_t3 + gh % 3, (gh - 3) / 3, abort_flag, a.status))
-                            return false;
-                        fence_after_sync();
-                        issue_conv3_batch(a2(h2_slot(ub)), b3d, t3reg(gh));
-                        mma_commit(bar_m3 + (gh & 1));
-                        return true;
-                    };
-                    // conv1 of virtual slice v: one MMA (K = 16) per parity tile, B = the tile's
-                    // tap set, into buffer b = c & 1 (c = c0 + v + 2) of the A operand and of
-                    // the accumulator.  Issued as soon as the workers have built the A operand
-                    // (they build slice v only after draining conv1 of slice v-2).
-                    int next1 = -2;
-                    auto issue1 = [&]() {
-                        const int b = (c0 + next1 + 2) & 1;
-                        fence_after_sync();
-#pragma unroll
-                        for (int pc = 0; pc < 2; ++pc)
-                            mma_bf16(tmem + (uint32_t)(kTmemC1 + 64 * b + 32 * pc),
-                                     desc_add(a1c, (uint32_t)((b * kIm2colBufBytes + pc * 4096) >> 4)),
-                                     desc_add(b1d, (uint32_t)(((frozen ^ pc) & 1) * 64)), kIdesc32, 0u);
-                        mma_commit(bar_c1 + b);
-                        ++next1;
-                    };
-                    auto pump1 = [&]() {                 // non-blocking
-                        while (next1 <= kL + 1) {
-                            const int c = c0 + next1 + 2;
-                            if (!mbar_test_wait(bar_b1 + (c & 1), (uint32_t)(c >> 1) & 1u)) break;
-                            issue1();
-                        }
-                    };
-                    auto need1 = [&](int v) {            // blocking, up to conv1 of slice v
-                        while (next1 <= v) {
-                            const int c = c0 + next1 + 2;
-                            if (!wait_n(bar_b1 + (c & 1), c >> 1, abort_flag, a.status)) return false;
-                            issue1();
-                        }
-                        return true;
-                    };
-                    for (int u = -1; u <= kL && !*abort_flag; ++u) {
-                        pump1();
-                        if (u == -1) {
-                            if (!need1(0) || !wait_h1(-2) || !wait_h1(-1) || !wait_h1(0)) break;
-                        } else if (!need1(u + 1) || !wait_h1(u + 1)) {
-                            break;
-                        }
-                        const int g2 = g20 + u + 1;
-                        const uint64_t as[3] = {a1(h1_slot(u - 1)), a1(h1_slot(u)), a1(h1_slot(u + 1))};
-                        // M-tile 0 (tile 1 is issued by the second MMA thread); its buffer is
-                        // drained by epi2 of u-1
-                        if (g2 >= 1 && !wait_n(bar_t2, g2 - 1, abort_flag, a.status)) break;
-                        fence_after_sync();
-                        issue_conv2_tile(as, b2d, t2tile(0), 0);
-                        mma_commit(bar_m2 + (g2 & 1));
-                        pump1();
-                        if (u >= 0 && !batch(u - 1)) break;
-                    }
-                    if (!*abort_flag) batch(kL);
-                }
-                __syncwarp();
-            } else if (warp == kMma2Warp) {
-                // ---------------- second tensor-core issue thread: conv2 of M-tile 1
-                if (lane == 0) {
+                    const int t = warp == kMma2Warp;
                     for (int u = -1; u <= kL && !*abort_flag; ++u) {
                         bool ok = true;
                         for (int v = (u == -1 ? -2 : u + 1); v <= u + 1 && ok; ++v) {
@@ -608,36 +545,73 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
                             ok = wait_n(bar_h1 + (c & 3), c >> 2, abort_flag, a.status);
                         }
                         const int g2 = g20 + u + 1;
-                        if (!ok || (g2 >= 1 && !wait_n(bar_t2 + 1, g2 - 1, abort_flag, a.status))) break;
+                        if (!ok || (g2 >= 1 && !wait_n(bar_t2 + t, g2 - 1, abort_flag, a.status))) break;
                         fence_after_sync();
                         const uint64_t as[3] = {a1(h1_slot(u - 1)), a1(h1_slot(u)), a1(h1_slot(u + 1))};
-                        issue_conv2_tile(as, b2d, t2tile(1), 1);
-                        mma_commit(bar_m2 + 2 + (g2 & 1));
+                        issue_conv2_tile(as, b2d, t2tile(t), t);
+                        mma_commit(bar_m2 + 2 * t + (g2 & 1));
+                    }
+                }
+                __syncwarp();
+            } else if (warp == kMma3Warp) {
+                // ---------------- conv3 batch ub (one thread): every contribution of h2[ub]; needs
+                // h2[ub] written and its batch region free (batch ub-3's readers drained)
+                if (lane == 0) {
+                    for (int ub = -1; ub <= kL && !*abort_flag; ++ub) {
+                        const int gh = g20 + ub + 1;
+                        if (!wait_n(bar_h2 + gh % 3, gh / 3, abort_flag, a.status)) break;
+                        if (gh >= 3 && !wait_n(bar_t3 + gh % 3, (gh - 3) / 3, abort_flag, a.status)) break;
+                        fence_after_sync();
+                        issue_conv3_batch(a2(h2_slot(ub)), b3d, t3reg(gh));
+                        mma_commit(bar_m3 + (gh & 1));
+                    }
+                }
+                __syncwarp();
+            } else if (warp == kMma1Warp) {
+                // ---------------- conv1 of virtual slice v (one thread): one MMA (K = 16) per
+                // parity tile, B = the tile's tap set, into buffer b = c & 1 of the A operand
+                // and of the accumulator, once the workers have built the A operand (they
+                // build slice v only after draining conv1 of slice v-2)
+                if (lane == 0) {
+                    for (int v = -2; v <= kL + 1 && !*abort_flag; ++v) {
+                        const int c = c0 + v + 2, b = c & 1;
+                        if (!wait_n(bar_b1 + b, c >> 1, abort_flag, a.status)) break;
+                        fence_after_sync();
+#pragma unroll
+                        for (int pc = 0; pc < 2; ++pc)
+                            mma_bf16(tmem + (uint32_t)(kTmemC1 + 64 * b + 32 * pc),
+                                     desc_add(a1c, (uint32_t)((b * kIm2colBufBytes + pc * 4096) >> 4)),
+                                     desc_add(b1d, (uint32_t)(((frozen ^ pc) & 1) * 64)), kIdesc32, 0u);
+                        mma_commit(bar_c1 + b);
                     }
                 }
                 __syncwarp();
             } else if (warp >= kC1Warp0 && warp < kC1Warp0 + 8) {
                 // ---------------- conv1 workers: thread = row r of parity tile pc.  Two A
                 // operand buffers and two accumulators (b = c & 1): the A operand of slice
-                // v+2 is built as soon as conv1 of slice v has been drained.
+                // v+2 is built as soon as conv1 of slice v has been drained.  Row r holds
+                // site (y, 2 xh + parity) with lanes 0-3 / 4-7 on rows 2j / 2j+1 (opposite
+                // parities), so each 8-lane phase of the 16-byte h1 stores covers 8
+                // distinct bank groups.
                 const int pc = (warp - kC1Warp0) >> 2, r = ((warp & 3) << 5) | lane;
-                const int y = r >> 3, xh = r & 7;
+                const int y = ((r >> 4) << 1) | ((r >> 2) & 1), xh = (((r >> 3) & 1) << 2) | (r & 3);
                 const int need = (frozen ^ pc) & 1;
                 const uint32_t t1lane = (uint32_t)((warp & 3) * 32) << 16;
                 auto build = [&](int v) {                // A operand of slice v, then signal it
                     const int c = c0 + v + 2;
                     const int z = slice_of(v);
                     const int xs = 2 * xh + ((pc ^ z ^ y) & 1);
-                    int zr[3], yr[3], xc[3];
+                    int zr[3], yr[3], ys[3], xc[3];
 #pragma unroll
                     for (int d = 0; d < 3; ++d) {
                         zr[d] = wrap16(z + d - 1) * kXSlice;
                         yr[d] = wrap16(y + d - 1) * kXRow;
+                        ys[d] = xswz(wrap16(y + d - 1));
                         xc[d] = wrap16(xs + d - 1);
                     }
                     unsigned char* a_tile = im2col + (c & 1) * kIm2colBufBytes + pc * 4096;
-                    if (need) im2col_row<1>(a_tile, r, x, zr, yr, xc);
-                    else im2col_row<0>(a_tile, r, x, zr, yr, xc);
+                    if (need) im2col_row<1>(a_tile, r, x, zr, yr, ys, xc);
+                    else im2col_row<0>(a_tile, r, x, zr, yr, ys, xc);
                     fence_proxy_async();
                     mbar_arrive(bar_b1 + (c & 1));
                 };
@@ -669,7 +643,7 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
                         float o[8];
 #pragma unroll
                         for (int i = 0; i < 8; ++i) {
-                            const float hv = d[cg * 8 + i] + wf[kF_b1 + cg * 8 + i];
+                            const float hv = d[cg * 8 + i];             // b1 is in the MMA
                             o[i] = hv > 0.f ? hv : a.slope * hv;
                         }
                         store8(slot, cg, y, xs, o);
@@ -777,9 +751,9 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
         }
         __syncthreads();
     }
-    // after an abort some MMAs may still be queued: both issuing threads commit,
+    // after an abort some MMAs may still be queued: every issuing thread commits,
     // and TMEM is freed only once all their tensor-core work is done (bounded wait)
-    if (warp == kMma2Warp && lane == 0) mma_commit(bar_fin);
+    if ((warp == kMma2Warp || warp == kMma3Warp || warp == kMma1Warp) && lane == 0) mma_commit(bar_fin);
     if (warp == kMmaWarp && lane == 0) {
         mma_commit(bar_fin);
         for (long long spins = 0; !mbar_try_wait(bar_fin, 0u) && spins < kWaitLimit; ++spins) {}
@@ -799,8 +773,8 @@ static_assert(kSmemBytes <= 227 * 1024, "shared memory budget");
 // canonical FP32 -> per-layer block: W2 [tap9][kg][dxi*32 + o][8] bf16,
 // W3 [dy3][kg][d*8 + dxi*2 + j][8] bf16 (tap (d, dy, dxi); j = 0: s, 1: t; rows
 // with (row & 7) >= 6 or row >= 24 zero),
-// then W1 as the two conv1 B operands [need][kg][o][8] bf16 (tap_of order), then
-// FP32 b1, b2, b3.
+// then W1 as the two conv1 B operands [need][kg][o][8] bf16 (tap_of order; K
+// columns 14 and 15 hold b1's BF16 head and remainder), then FP32 b1, b2, b3.
 __global__ void repack_bf16_kernel(const float* __restrict__ canon, int64_t cstride, int n_layers,
                                    unsigned char* __restrict__ out) {
     constexpr int n2 = 9 * 4 * 96 * 8, n3 = 3 * 4 * 32 * 8, n1 = 2 * 2 * 32 * 8;
@@ -833,8 +807,9 @@ __global__ void repack_bf16_kernel(const float* __restrict__ canon, int64_t cstr
         } else if (r < n2 + n3 + n1) {
             const int r1 = (int)(r - n2 - n3);
             const int e = r1 & 7, o = (r1 >> 3) & 31, kg = (r1 >> 8) & 1, need = r1 >> 9;
-            const int t = tap_of(need, kg * 8 + e);
-            const float v = t < 0 ? 0.f : W1[(int64_t)o * kT + t];
+            const int k = kg * 8 + e, t = tap_of(need, k);
+            const float bh = __bfloat162float(__float2bfloat16_rn(b1[o]));
+            const float v = k == kBiasK ? b1[o] : k == kBiasK + 1 ? b1[o] - bh : t < 0 ? 0.f : W1[(int64_t)o * kT + t];
             reinterpret_cast<__nv_bfloat16*>(blk + kW2Bytes + kW3Bytes)[r1] = __float2bfloat16_rn(v);
         } else {
             const int f = (int)(r - n2 - n3 - n1);
