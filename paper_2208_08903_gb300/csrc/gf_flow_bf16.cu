@@ -24,7 +24,7 @@
 // address.  The periodic x-shift is not gathered: the epilogues form
 // out(x) = sum_dx P_dx(x + dx) with width-16 shuffles (one x-row = one
 // half-warp = 16 TMEM lanes).
-// Warp-specialised pipeline within a layer (mbarriers only, no CTA barrier):
+// Warp-specialised pipeline (mbarriers only, no CTA barrier):
 // eight conv1 worker warps gather each slice's conv1 operand (the field at the
 // live taps, BF16) two slices ahead and turn the conv1 accumulators into h1
 // (four h1 slots); four single threads, one per sub-partition, queue the
@@ -37,7 +37,12 @@
 // update of x.  An issuing thread stalls behind its own queued MMAs, so each
 // kind of work has its own issuer and none waits for another's backlog.  conv1 reads only fixed sites
 // of x and the update writes only the other parity, so x needs no ordering
-// within a layer; the CTA meets at a barrier between layers.
+// within a layer.  Layers follow one another without a CTA barrier: each layer
+// walks the slices from a start rotated by 4, so its first conv1 slices read
+// field slices that the previous layer finished early; four checkpoint barriers
+// per layer tell the conv1 workers which slices the previous layer has updated,
+// and the workers stage the next layer's weights (bulk copies for W2 and W3) as
+// soon as the previous layer's last conv2 / conv3 has finished.
 #include <algorithm>
 #include <cstring>
 
@@ -222,9 +227,10 @@ __device__ __forceinline__ void store8(unsigned char* slot, int cg, int y, int x
     if (y == 15) *reinterpret_cast<uint4*>(base + hsite(-1, x) * 16) = w;
 }
 
-// Virtual slice v (may lie outside 0..L-1 by the wrap-around recomputation)
-// -> lattice slice v mod L; h1 slot v mod 4, h2 slot v mod 3.
-__device__ __forceinline__ int slice_of(int v) { return v & 15; }
+// Virtual slice v of a layer (may lie outside 0..L-1 by the wrap-around
+// recomputation) is lattice slice (v + R) mod L for the layer's rotation R; its
+// h1 slot is v mod 4, its h2 slot v mod 3 (the same in every layer, as a layer
+// has 20 conv1 and 18 conv2 slices).
 __device__ __forceinline__ int h1_slot(int v) { return (v + 16) & 3; }
 __device__ __forceinline__ int h2_slot(int v) { return (v + 15) % 3; }
 
@@ -391,6 +397,16 @@ __device__ __forceinline__ bool wait_n(uint64_t* bar, int n, volatile int* abort
     }
     return true;
 }
+// Arrival that also announces `bytes` of bulk-copy data for the current phase.
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// Bulk copy global -> shared (16-byte aligned, size a multiple of 16), completing on bar.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
 __device__ __forceinline__ uint64_t mbar_arrive(uint64_t* bar) {
     uint64_t state;
     asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(state) : "r"(smem_u32(bar)) : "memory");
@@ -409,7 +425,9 @@ __device__ __forceinline__ uint64_t mbar_arrive(uint64_t* bar) {
 //   conv2 of tile t: bar_m2[2 t + (g2 & 1)] completion g2 >> 1; its TMEM drained:
 //   bar_t2[t] completion g2; h2 written: bar_h2[g2 % 3], completion g2 / 3;
 //   conv3 batch gb: bar_m3[gb & 1], completion gb >> 1; its region gb % 3
-//   released: bar_t3[gb % 3], completion gb / 3.
+//   released: bar_t3[gb % 3], completion gb / 3;
+//   once per layer (completion seq): W2 and biases staged bar_w2, W3 staged
+//   bar_w3, field slices <= 5 / 9 / 13 / 15 updated bar_x[0..3].
 constexpr int kConv1PerLayer = 20, kConv2PerLayer = 18;
 
 // Warp roles: four issuing threads (warps 0, 17, 18, 19); warps 1..8 run the
@@ -417,7 +435,7 @@ constexpr int kConv1PerLayer = 20, kConv2PerLayer = 18;
 // quarter w & 3); warps 9..16 build conv1's operands and turn its accumulators
 // into the h1 slots.  They synchronise through mbarriers only, so the tensor
 // cores and the epilogues overlap; the CTA meets at a barrier only between
-// layers.
+// configurations.
 template <bool INVERSE>
 __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a) {
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -439,7 +457,10 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
     uint64_t* bar_b1 = bar_t3 + 3;                             // 2: conv1 A operand built (workers)
     uint64_t* bar_c1 = bar_b1 + 2;                             // 2: conv1 MMAs done (commit)
     uint64_t* bar_fin = bar_c1 + 2;                            // 1: every queued MMA done (exit)
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar_fin + 1);
+    uint64_t* bar_w2 = bar_fin + 1;                            // 1: a layer's W2 and biases staged
+    uint64_t* bar_w3 = bar_w2 + 1;                             // 1: a layer's W3 staged
+    uint64_t* bar_x = bar_w3 + 1;                              // 4: a layer's field slices <= 5, 9, 13, 15 updated
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar_x + 4);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -462,6 +483,9 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
             mbar_init(bar_c1 + i, 1);
         }
         mbar_init(bar_fin, kIssuers);                          // one commit per issuing thread
+        mbar_init(bar_w2, 1);                                  // expect_tx by the staging thread
+        mbar_init(bar_w3, 1);
+        for (int i = 0; i < 4; ++i) mbar_init(bar_x + i, kEpiThreads);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -513,69 +537,72 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
         __syncthreads();
 
         double logdet = 0.0;
-        for (int li = 0; li < a.n_layers; ++li, ++seq) {
-            const int l = INVERSE ? a.n_layers - 1 - li : li;
-            const int frozen = l & 1;
-            {   // stage this layer's weights (W2, W3 already in the MMA operand layouts)
-                // all of a thread's loads are issued before its stores (L2 latency once)
-                const uint4* src = reinterpret_cast<const uint4*>(a.Wl + (size_t)l * kLayerBytes);
-                uint4* dst = reinterpret_cast<uint4*>(smem);
-                constexpr int kN16 = kLayerBytes / 16, kPer = (kN16 + kThreads - 1) / kThreads;
-                uint4 tmp[kPer];
-#pragma unroll
-                for (int j = 0; j < kPer; ++j)
-                    if (tid + j * kThreads < kN16) tmp[j] = __ldg(src + tid + j * kThreads);
-#pragma unroll
-                for (int j = 0; j < kPer; ++j)
-                    if (tid + j * kThreads < kN16) dst[tid + j * kThreads] = tmp[j];
-            }
-            fence_proxy_async();
-            __syncthreads();
-            const int c0 = seq * kConv1PerLayer, g20 = seq * kConv2PerLayer;
-
-            if (warp == kMmaWarp || warp == kMma2Warp) {
-                // ---------------- conv2 of M-tile t (one thread): slice u needs h1 of u-1..u+1
-                // and the tile's TMEM buffer drained by the epilogue of u-1
-                if (lane == 0) {
-                    const int t = warp == kMma2Warp;
-                    for (int u = -1; u <= kL && !*abort_flag; ++u) {
-                        bool ok = true;
+        const int seq0 = seq, nl = a.n_layers;
+        // Layers are pipelined into one another (no CTA barrier between them): layer li
+        // (global number s = seq0 + li) walks the lattice slices in the order R + v with
+        // R = 4 li (mod 16), so the first slices of layer li need only field slices that
+        // layer li-1 finished early, and its conv1 overlaps layer li-1's last conv2 and
+        // conv3 work.  The conv1 workers stage each layer's weights: the conv1 B operand
+        // after their last drain of layer li-1, W2 and the FP32 biases once layer li-1's
+        // last conv2 is done (bar_w2), W3 once its last conv3 batch is done (bar_w3).
+        const auto lay = [&](int li) { return INVERSE ? nl - 1 - li : li; };
+        const auto rot = [](int li) { return (4 * li) & 15; };
+        if (warp == kMmaWarp || warp == kMma2Warp) {
+            // ---------------- conv2 of M-tile t (one thread): slice u needs h1 of u-1..u+1
+            // and the tile's TMEM buffer drained by the epilogue of u-1
+            if (lane == 0) {
+                const int t = warp == kMma2Warp;
+                bool ok = true;
+                for (int li = 0; li < nl && ok; ++li) {
+                    const int s = seq0 + li, c0 = s * kConv1PerLayer, g20 = s * kConv2PerLayer;
+                    ok = wait_n(bar_w2, s, abort_flag, a.status);          // this layer's W2 staged
+                    for (int u = -1; u <= kL && ok; ++u) {
                         for (int v = (u == -1 ? -2 : u + 1); v <= u + 1 && ok; ++v) {
                             const int c = c0 + v + 2;
                             ok = wait_n(bar_h1 + (c & 3), c >> 2, abort_flag, a.status);
                         }
                         const int g2 = g20 + u + 1;
-                        if (!ok || (g2 >= 1 && !wait_n(bar_t2 + t, g2 - 1, abort_flag, a.status))) break;
+                        if (!ok || (g2 >= 1 && !(ok = wait_n(bar_t2 + t, g2 - 1, abort_flag, a.status)))) break;
                         fence_after_sync();
                         const uint64_t as[3] = {a1(h1_slot(u - 1)), a1(h1_slot(u)), a1(h1_slot(u + 1))};
                         issue_conv2_tile(as, b2d, t2tile(t), t);
                         mma_commit(bar_m2 + 2 * t + (g2 & 1));
                     }
                 }
-                __syncwarp();
-            } else if (warp == kMma3Warp) {
-                // ---------------- conv3 batch ub (one thread): every contribution of h2[ub]; needs
-                // h2[ub] written and its batch region free (batch ub-3's readers drained)
-                if (lane == 0) {
-                    for (int ub = -1; ub <= kL && !*abort_flag; ++ub) {
+            }
+            __syncwarp();
+        } else if (warp == kMma3Warp) {
+            // ---------------- conv3 batch ub (one thread): every contribution of h2[ub]; needs
+            // h2[ub] written and its batch region free (batch ub-3's readers drained)
+            if (lane == 0) {
+                bool ok = true;
+                for (int li = 0; li < nl && ok; ++li) {
+                    const int s = seq0 + li, g20 = s * kConv2PerLayer;
+                    ok = wait_n(bar_w3, s, abort_flag, a.status);          // this layer's W3 staged
+                    for (int ub = -1; ub <= kL && ok; ++ub) {
                         const int gh = g20 + ub + 1;
-                        if (!wait_n(bar_h2 + gh % 3, gh / 3, abort_flag, a.status)) break;
-                        if (gh >= 3 && !wait_n(bar_t3 + gh % 3, (gh - 3) / 3, abort_flag, a.status)) break;
+                        ok = wait_n(bar_h2 + gh % 3, gh / 3, abort_flag, a.status) &&
+                             (gh < 3 || wait_n(bar_t3 + gh % 3, (gh - 3) / 3, abort_flag, a.status));
+                        if (!ok) break;
                         fence_after_sync();
                         issue_conv3_batch(a2(h2_slot(ub)), b3d, t3reg(gh));
                         mma_commit(bar_m3 + (gh & 1));
                     }
                 }
-                __syncwarp();
-            } else if (warp == kMma1Warp) {
-                // ---------------- conv1 of virtual slice v (one thread): one MMA (K = 16) per
-                // parity tile, B = the tile's tap set, into buffer b = c & 1 of the A operand
-                // and of the accumulator, once the workers have built the A operand (they
-                // build slice v only after draining conv1 of slice v-2)
-                if (lane == 0) {
-                    for (int v = -2; v <= kL + 1 && !*abort_flag; ++v) {
+            }
+            __syncwarp();
+        } else if (warp == kMma1Warp) {
+            // ---------------- conv1 of virtual slice v (one thread): one MMA (K = 16) per
+            // parity tile, B = the tile's tap set, into buffer b = c & 1 of the A operand
+            // and of the accumulator, once the workers have built the A operand (they
+            // build slice v only after draining conv1 of slice v-2)
+            if (lane == 0) {
+                bool ok = true;
+                for (int li = 0; li < nl && ok; ++li) {
+                    const int s = seq0 + li, c0 = s * kConv1PerLayer, frozen = lay(li) & 1;
+                    for (int v = -2; v <= kL + 1; ++v) {
                         const int c = c0 + v + 2, b = c & 1;
-                        if (!wait_n(bar_b1 + b, c >> 1, abort_flag, a.status)) break;
+                        if (!(ok = wait_n(bar_b1 + b, c >> 1, abort_flag, a.status))) break;
                         fence_after_sync();
 #pragma unroll
                         for (int pc = 0; pc < 2; ++pc)
@@ -585,21 +612,61 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
                         mma_commit(bar_c1 + b);
                     }
                 }
-                __syncwarp();
-            } else if (warp >= kC1Warp0 && warp < kC1Warp0 + 8) {
-                // ---------------- conv1 workers: thread = row r of parity tile pc.  Two A
-                // operand buffers and two accumulators (b = c & 1): the A operand of slice
-                // v+2 is built as soon as conv1 of slice v has been drained.  Row r holds
-                // site (y, 2 xh + parity) with lanes 0-3 / 4-7 on rows 2j / 2j+1 (opposite
-                // parities), so each 8-lane phase of the 16-byte h1 stores covers 8
-                // distinct bank groups.
-                const int pc = (warp - kC1Warp0) >> 2, r = ((warp & 3) << 5) | lane;
-                const int y = ((r >> 4) << 1) | ((r >> 2) & 1), xh = (((r >> 3) & 1) << 2) | (r & 3);
-                const int need = (frozen ^ pc) & 1;
-                const uint32_t t1lane = (uint32_t)((warp & 3) * 32) << 16;
-                auto build = [&](int v) {                // A operand of slice v, then signal it
+            }
+            __syncwarp();
+        } else if (warp >= kC1Warp0 && warp < kC1Warp0 + 8) {
+            // ---------------- conv1 workers: thread = row r of parity tile pc.  Two A
+            // operand buffers and two accumulators (b = c & 1): the A operand of slice
+            // v+2 is built as soon as conv1 of slice v has been drained.  Row r holds
+            // site (y, 2 xh + parity) with lanes 0-3 / 4-7 on rows 2j / 2j+1 (opposite
+            // parities), so each 8-lane phase of the 16-byte h1 stores covers 8
+            // distinct bank groups.
+            const int wt = tid - kC1Warp0 * 32;                   // 0..255
+            const int pc = (warp - kC1Warp0) >> 2, r = ((warp & 3) << 5) | lane;
+            const int y = ((r >> 4) << 1) | ((r >> 2) & 1), xh = (((r >> 3) & 1) << 2) | (r & 3);
+            const uint32_t t1lane = (uint32_t)((warp & 3) * 32) << 16;
+            // layer l's block: W2 with the FP32 biases and W3 arrive by bulk copies issued by
+            // one thread (completion on bar_w2 / bar_w3 by byte count); the conv1 B operand
+            // (2 KB) by one 16-byte copy per thread of the first 128
+            const auto stage_w2 = [&](int l) {
+                const unsigned char* blk = a.Wl + (size_t)l * kLayerBytes;
+                mbar_expect_tx(bar_w2, (uint32_t)(kW2Bytes + kF_N * 4));
+                bulk_g2s(w2s, blk, (uint32_t)kW2Bytes, bar_w2);
+                bulk_g2s(wf, blk + kW2Bytes + kW3Bytes + kW1Bytes, (uint32_t)(kF_N * 4), bar_w2);
+            };
+            const auto stage_w3 = [&](int l) {
+                mbar_expect_tx(bar_w3, (uint32_t)kW3Bytes);
+                bulk_g2s(w3s, a.Wl + (size_t)l * kLayerBytes + kW2Bytes, (uint32_t)kW3Bytes, bar_w3);
+            };
+            const auto stage_w1 = [&](int l) {
+                if (wt < kW1Bytes / 16)
+                    reinterpret_cast<uint4*>(w1s)[wt] =
+                        __ldg(reinterpret_cast<const uint4*>(a.Wl + (size_t)l * kLayerBytes + kW2Bytes + kW3Bytes) + wt);
+            };
+            int xseen = 0, kx = 0;                                 // slices of layer li-1 known updated
+            bool ok = true;
+            for (int li = 0; li < nl && ok; ++li) {
+                const int s = seq0 + li, c0 = s * kConv1PerLayer, g20 = s * kConv2PerLayer, l = lay(li);
+                const int need = ((l & 1) ^ pc) & 1, R = rot(li);
+                if (li == 0 && wt == 0) {                          // the first layer's W2 and W3
+                    stage_w2(l);
+                    stage_w3(l);
+                }
+                stage_w1(l);                                       // (conv1 of layer li-1 drained)
+                xseen = li == 0 ? kL : 0;
+                kx = 0;
+                auto build = [&](int v) {                          // A operand of slice v, then signal it
                     const int c = c0 + v + 2;
-                    const int z = slice_of(v);
+                    // slices R+v-1 .. R+v+1 were slices v+3 .. v+5 (mod 16) of layer li-1
+                    // (v >= 10 reaches its last two): wait until its epilogue has updated them,
+                    // at four checkpoints per layer (slices 5, 9, 13, 15; the last one, which
+                    // comes after layer li's first conv2, is first needed at v = 9)
+                    while (xseen <= (v + 5 < kL - 1 ? v + 5 : kL - 1) && ok) {
+                        ok = wait_n(bar_x + kx, s - 1, abort_flag, a.status);
+                        xseen = (kx == 3 ? kL - 1 : 5 + 4 * kx) + 1;
+                        ++kx;
+                    }
+                    const int z = (v + R) & 15;
                     const int xs = 2 * xh + ((pc ^ z ^ y) & 1);
                     int zr[3], yr[3], ys[3], xc[3];
 #pragma unroll
@@ -617,9 +684,9 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
                 };
                 build(-2);
                 build(-1);
-                for (int v = -2; v <= kL + 1 && !*abort_flag; ++v) {
+                for (int v = -2; v <= kL + 1 && ok; ++v) {
                     const int c = c0 + v + 2;
-                    if (!wait_n(bar_c1 + (c & 1), c >> 1, abort_flag, a.status)) break;
+                    if (!(ok = wait_n(bar_c1 + (c & 1), c >> 1, abort_flag, a.status))) break;
                     fence_after_sync();
                     float d[32];
                     const uint32_t acc = tmem + (uint32_t)(kTmemC1 + 64 * (c & 1) + 32 * pc) + t1lane;
@@ -629,13 +696,14 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
                     fence_before_sync();
                     // its arrival also says this accumulator (and A buffer) may be reused
                     if (v + 2 <= kL + 1) build(v + 2);
-                    if (v >= 2) {                        // slot of h1[v-4] is free once conv2 of slice v-3 is done
-                        const int g2 = g20 + v - 2;
-                        if (!wait_n(bar_m2 + (g2 & 1), g2 >> 1, abort_flag, a.status) ||
-                            !wait_n(bar_m2 + 2 + (g2 & 1), g2 >> 1, abort_flag, a.status))
-                            break;
-                    }
-                    const int z = slice_of(v);
+                    if (!ok) break;
+                    // the h1 slot of v last held h1 of v-4 (or of slice v+16 of the previous
+                    // layer): wait until the last conv2 that read it is done (both tiles)
+                    const int g2 = v >= 2 ? g20 + v - 2 : (li > 0 ? g20 - kConv2PerLayer + (v + 17 < 16 ? v + 17 : 16) + 1 : -1);
+                    if (g2 >= 0 && !(ok = wait_n(bar_m2 + (g2 & 1), g2 >> 1, abort_flag, a.status) &&
+                                          wait_n(bar_m2 + 2 + (g2 & 1), g2 >> 1, abort_flag, a.status)))
+                        break;
+                    const int z = (v + R) & 15;
                     const int xs = 2 * xh + ((pc ^ z ^ y) & 1);
                     unsigned char* slot = h1 + (size_t)h1_slot(v) * kSlotBytes;
 #pragma unroll
@@ -650,42 +718,64 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
                     }
                     fence_proxy_async();
                     mbar_arrive(bar_h1 + (c & 3));
-                }
-            } else if (warp >= 1 && warp <= kEpiWarps) {
-                // ---------------- epilogues.  conv2: lane quarter q, channel half hf of each
-                // tile in turn; conv3: tile mt, lane quarter q.
-                const int e = warp - 1;                  // 0..7: quarters 1, 2, 3, 0, 1, 2, 3, 0
-                const int q = warp & 3, hf = e >> 2, mt = e >> 2;
-                float b2[16];                            // this thread's conv2 biases and the conv3 biases
-#pragma unroll
-                for (int c = 0; c < 16; ++c) b2[c] = wf[kF_b2 + hf * 16 + c];
-                const float b3s = wf[kF_b3], b3t = wf[kF_b3 + 1];
-                auto wait_batch = [&](int ub) {
-                    const int gb = g20 + ub + 1;
-                    return wait_n(bar_m3 + (gb & 1), gb >> 1, abort_flag, a.status);
-                };
-                auto release = [&](int ub) { mbar_arrive(bar_t3 + (g20 + ub + 1) % 3); };
-                auto epi3 = [&](int w) {                 // batches w-1, w, w+1 are complete
-                    float p[3][8];
-                    conv3_epi_load(p, t3reg(g20 + w), t3reg(g20 + w + 1), t3reg(g20 + w + 2), mt, q);
-                    fence_before_sync();
-                    release(w - 1);                      // slice w is the last reader of batch w-1
-                    if (w == kL - 1) { release(kL - 1); release(kL); }
-                    conv3_epi_finish(p, slice_of(w), b3s, b3t, x, frozen, a.use_tanh, INVERSE, logdet, mt, q, lane);
-                };
-                for (int u = -1; u <= kL && !*abort_flag; ++u) {
-                    const int g2 = g20 + u + 1;
-                    // batch u-2 done: slice u-3 is complete and the h2 slot of u (last read by
-                    // batch u-3) is free.  Draining slice u-3 first keeps the epilogue two
-                    // batches behind the tensor cores, so they never wait for it.
-                    if (u >= 2) {
-                        if (!wait_batch(u - 2)) break;
-                        fence_after_sync();
-                        if (u >= 3) epi3(u - 3);
+                    if (li > 0 && v == -1 && wt == 0) {
+                        stage_w2(l);                     // layer li-1's last conv2 is done (waited above)
+                    } else if (li > 0 && v == 2 && wt == 0) {
+                        const int gb = g20 - 1;          // layer li-1's last conv3 batch
+                        if (!(ok = wait_n(bar_m3 + (gb & 1), gb >> 1, abort_flag, a.status))) break;
+                        stage_w3(l);
                     }
-                    bool ok = true;
+                }
+            }
+        } else if (warp >= 1 && warp <= kEpiWarps) {
+            // ---------------- epilogues.  conv2: lane quarter q, channel half hf of each
+            // tile in turn; conv3: tile mt, lane quarter q.  Iteration u of layer li first
+            // finishes the conv3 slice two batches behind (u-3 of layer li, or the last two
+            // slices of layer li-1 at u = -1, 0), then turns conv2 of slice u into h2.
+            // After the last layer, two more iterations finish its last two slices.
+            const int e = warp - 1;                  // 0..7: quarters 1, 2, 3, 0, 1, 2, 3, 0
+            const int q = warp & 3, hf = e >> 2, mt = e >> 2;
+            float b2[16];                            // this thread's conv2 biases, conv3 biases
+            float b3s = 0.f, b3t = 0.f, b3s_p = 0.f, b3t_p = 0.f;   // of layer li and of li-1
+            bool ok = true;
+            for (int li = 0; li <= nl && ok; ++li) {
+                const int s = seq0 + li, g20 = s * kConv2PerLayer;
+                for (int u = -1; u <= (li < nl ? kL : 0) && ok; ++u) {
+                    const int g2 = g20 + u + 1;
+                    // batch g2-2 done: the conv3 slice below is complete and the h2 slot of u
+                    // (last read by batch g2-3) is free
+                    const bool tail = u <= 0 && li > 0, own = u >= 3;
+                    if (li > 0 || u >= 1) {
+                        const int gb = g2 - 2;
+                        if (!(ok = wait_n(bar_m3 + (gb & 1), gb >> 1, abort_flag, a.status))) break;
+                        fence_after_sync();
+                    }
+                    if (tail || own) {
+                        // slice w of layer lj (global conv3 numbers gw = g20 of lj + w + 1)
+                        const int lj = tail ? li - 1 : li, w = tail ? kL - 1 + u : u - 3;
+                        const int gj = (seq0 + lj) * kConv2PerLayer + w + 1;
+                        float p[3][8];
+                        conv3_epi_load(p, t3reg(gj - 1), t3reg(gj), t3reg(gj + 1), mt, q);
+                        fence_before_sync();
+                        mbar_arrive(bar_t3 + (gj - 1) % 3);   // slice w is the last reader of batch w-1
+                        if (w == kL - 1) { mbar_arrive(bar_t3 + gj % 3); mbar_arrive(bar_t3 + (gj + 1) % 3); }
+                        // layer li's biases replace li-1's at u = -1, after its slice 14
+                        const bool prev = u == 0 && li < nl;
+                        conv3_epi_finish(p, (w + rot(lj)) & 15, prev ? b3s_p : b3s, prev ? b3t_p : b3t, x,
+                                         lay(lj) & 1, a.use_tanh, INVERSE, logdet, mt, q, lane);
+                        if (w == kL - 1 || (w >= 5 && (w & 3) == 1))   // checkpoint: slices <= w updated
+                            mbar_arrive(bar_x + (w == kL - 1 ? 3 : (w - 5) >> 2));
+                    }
+                    if (li == nl) continue;
+                    if (u == -1) {                                 // this layer's biases (W2 staged)
+                        if (!(ok = wait_n(bar_w2, s, abort_flag, a.status))) break;
+                        b3s_p = b3s; b3t_p = b3t;
+#pragma unroll
+                        for (int c = 0; c < 16; ++c) b2[c] = wf[kF_b2 + hf * 16 + c];
+                        b3s = wf[kF_b3]; b3t = wf[kF_b3 + 1];
+                    }
                     for (int t = 0; t < 2; ++t) {
-                        if (!wait_n(bar_m2 + 2 * t + (g2 & 1), g2 >> 1, abort_flag, a.status)) { ok = false; break; }
+                        if (!(ok = wait_n(bar_m2 + 2 * t + (g2 & 1), g2 >> 1, abort_flag, a.status))) break;
                         fence_after_sync();
                         Conv2Parts P;
                         conv2_epi_load(P, t2tile(t), q, hf);
@@ -697,21 +787,12 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
                     fence_proxy_async();
                     mbar_arrive(bar_h2 + g2 % 3);
                 }
-                // slices L-2 and L-1 complete with batches L-1 and L
-                if (!*abort_flag && wait_batch(kL - 1)) {
-                    fence_after_sync();
-                    epi3(kL - 2);
-                    if (wait_batch(kL)) {
-                        fence_after_sync();
-                        epi3(kL - 1);
-                    }
-                }
             }
-            fence_before_sync();
-            __syncthreads();
-            fence_after_sync();
-            if (*abort_flag) break;
         }
+        seq = seq0 + nl;
+        fence_before_sync();
+        __syncthreads();
+        fence_after_sync();
         if (*abort_flag) break;
 
         if (INVERSE) {
@@ -767,7 +848,7 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
 }
 
 constexpr size_t kSmemBytes = (size_t)kLayerBytes + 7 * (size_t)kSlotBytes + (size_t)kXFloats * 4 + kIm2colBytes +
-                              32 * 8 + 24 * 8 + 4 + 4;
+                              32 * 8 + 32 * 8 + 4 + 4;
 static_assert(kSmemBytes <= 227 * 1024, "shared memory budget");
 
 // canonical FP32 -> per-layer block: W2 [tap9][kg][dxi*32 + o][8] bf16,
