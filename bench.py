@@ -450,21 +450,28 @@ def bench_extra(args, dev, flush, pk):
                           "bytes_per_launch": B * V * 4 + B * 8, "ms": float(np.mean(t))}
 
     # chain observables: M and C(t) per configuration (HBM-bound read of the
-    # fields), then the autocorrelation / tau_int of a 100k-step series and the ESS
-    M = torch.empty(B, device=dev, dtype=torch.float64)
-    Cc = torch.empty(B, shape.L, device=dev, dtype=torch.float64)
+    # fields), then the autocorrelation / tau_int of a 100k-step series and the ESS.
+    # The fields here are larger than L2 (4 x the batch, 268 MB) and are read in
+    # turn without a flush: a flush that writes L2 full leaves dirty lines whose
+    # write-back would double the traffic of this read-only kernel.
     lib = P._abi.load()
     stream = torch.cuda.current_stream().cuda_stream
+    Bo = 4 * B
+    phi_o = torch.randn(Bo, V, device=dev)
+    M = torch.empty(Bo, device=dev, dtype=torch.float64)
+    Cc = torch.empty(Bo, shape.L, device=dev, dtype=torch.float64)
 
     def obs(i):
-        P._abi.check("gf_observables", lib.gf_observables(shape.nd, shape.L, B, phi32.data_ptr(), M.data_ptr(),
+        P._abi.check("gf_observables", lib.gf_observables(shape.nd, shape.L, Bo, phi_o.data_ptr(), M.data_ptr(),
                                                           Cc.data_ptr(), stream))
-    t = _time_steps(obs, 10, 3, flush)
-    ob_bytes = B * V * 4 + B * (shape.L + 1) * 8
+    t = _time_steps(obs, 10, 3, None)
+    ob_bytes = Bo * V * 4 + Bo * (shape.L + 1) * 8
     gbs = ob_bytes / (float(np.mean(t)) / 1e3) / 1e9
     out["observables"] = {"GB_per_s": gbs, "frac_of_hbm": gbs / pk.get("hbm_gbs", 6800.0),
                           "bytes_per_launch": ob_bytes, "ms": float(np.mean(t)),
-                          "workload": f"M and C(t) of {B} configurations of {shape.nd}D L={shape.L}"}
+                          "workload": f"M and C(t) of {Bo} configurations of {shape.nd}D L={shape.L}",
+                          "l2": "inputs 4x L2 size, read in turn, no flush"}
+    del phi_o
     y = torch.randn(100000, device=dev, dtype=torch.float64)
     t = _time_steps(lambda i: P.autocorr(y, 1000), 5, 2, None)
     out["autocorr"] = {"ms": float(np.mean(t)), "n": 100000, "t_max": 1000}

@@ -7,8 +7,9 @@
 //  - per configuration: M = mean of phi and C(t) = (1/V) sum_tau Phi(tau)
 //    Phi(tau + t), Phi(tau) = sum of phi over the slice at outermost
 //    coordinate tau.  A slice is V/L contiguous sites, so one warp sums one
-//    slice with coalesced 16-byte loads (FP64 accumulation); the kernel reads
-//    each field once and is HBM-bound.
+//    slice with coalesced 16-byte loads; lanes and the warp accumulate in FP32
+//    pairs (error-free transformations), so the kernel reads each field once
+//    with little FP64 work.
 //  - chain gather: the chain's series O[chain_idx[k]] of a per-proposal
 //    observable.
 //  - Gamma(t) of a series (one CTA per lag, fixed-order FP64 reduction), then
@@ -26,10 +27,55 @@ namespace {
 constexpr int kObsThreads = 256;
 constexpr int kRedThreads = 1024;
 
-// One CTA per configuration (grid-stride).  Dynamic shared memory: L doubles.
-__global__ void __launch_bounds__(kObsThreads) obs_kernel(int L, int64_t V, int64_t B, const float* __restrict__ phi,
-                                                         double* __restrict__ M, double* __restrict__ C) {
-    extern __shared__ double Phi[];
+// Sum of FP32 values kept as an unevaluated pair hi + lo of FP32 numbers
+// (Knuth's TwoSum for the rounding error of each addition, renormalised with
+// Dekker's Fast2Sum), so each lane's partial slice sum is accurate to about
+// n 2^-48 relative without FP64 arithmetic, which is slow on this GPU; the
+// pair is widened to FP64 once per lane.
+struct FF { float hi, lo; };
+__device__ __forceinline__ void ff_add(FF& a, float b) {
+    const float s = a.hi + b;
+    const float bp = s - a.hi;
+    const float e = (a.hi - (s - bp)) + (b - bp);   // s + e == a.hi + b exactly
+    const float lo = a.lo + e;
+    a.hi = s + lo;
+    a.lo = lo - (a.hi - s);
+}
+__device__ __forceinline__ void ff_add(FF& a, const FF& b) {
+    const float s = a.hi + b.hi;
+    const float bp = s - a.hi;
+    const float e = (a.hi - (s - bp)) + (b.hi - bp);
+    const float lo = e + (a.lo + b.lo);
+    a.hi = s + lo;
+    a.lo = lo - (a.hi - s);
+}
+// Butterfly sum of the lanes' pairs (fixed order).
+__device__ __forceinline__ FF warp_sum_ff(FF a) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const FF b{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+        ff_add(a, b);
+    }
+    return a;
+}
+// acc += x * y for pairs: the head product exactly (FMA residual), the cross
+// terms in FP32 (their rounding is about 2^-48 of the product).
+__device__ __forceinline__ void ff_fma(FF& acc, const FF& x, const FF& y) {
+    const float p = x.hi * y.hi;
+    const float e = fmaf(x.hi, y.hi, -p) + (x.hi * y.lo + x.lo * y.hi);
+    ff_add(acc, FF{p, e});
+}
+__device__ __forceinline__ double ff_to_double(const FF& a) { return (double)a.hi + (double)a.lo; }
+
+// One CTA per configuration (grid-stride).  Dynamic shared memory: L pairs.
+// Each warp sums whole slices: every lane first issues up to four 16-byte loads,
+// then adds them into its FP32 pair; the warp reduces the pairs the same way.
+// M and C(t) are formed from the slice pairs in pair arithmetic too and widened
+// to FP64 once per output, so FP64 instructions are a few per configuration.
+__global__ void __launch_bounds__(kObsThreads) obs_kernel(int L, int64_t V, int64_t B, double inv_v,
+                                                         const float* __restrict__ phi, double* __restrict__ M,
+                                                         double* __restrict__ C) {
+    extern __shared__ FF Phi[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int64_t S = V / L;
     for (int64_t b = blockIdx.x; b < B; b += gridDim.x) {
@@ -37,33 +83,102 @@ __global__ void __launch_bounds__(kObsThreads) obs_kernel(int L, int64_t V, int6
         const bool vec = (S % 4 == 0) && ((reinterpret_cast<uintptr_t>(p) & 15) == 0);
         for (int tau = wid; tau < L; tau += nw) {
             const float* q = p + (int64_t)tau * S;
-            double acc = 0.0;
+            FF acc{0.f, 0.f};
             if (vec) {
                 const float4* q4 = reinterpret_cast<const float4*>(q);
-                for (int64_t i = lane; i < S / 4; i += 32) {
-                    const float4 v = __ldg(q4 + i);
-                    acc += ((double)v.x + (double)v.y) + ((double)v.z + (double)v.w);
+                const int64_t S4 = S / 4;
+                for (int64_t i0 = lane; i0 < S4; i0 += 4 * 32) {
+                    float4 v[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        if (i0 + 32 * k < S4) v[k] = __ldg(q4 + i0 + 32 * k);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        if (i0 + 32 * k < S4) {
+                            ff_add(acc, v[k].x);
+                            ff_add(acc, v[k].y);
+                            ff_add(acc, v[k].z);
+                            ff_add(acc, v[k].w);
+                        }
                 }
             } else {
-                for (int64_t i = lane; i < S; i += 32) acc += (double)__ldg(q + i);
+                for (int64_t i = lane; i < S; i += 32) ff_add(acc, __ldg(q + i));
             }
-            acc = warp_sum(acc);
+            acc = warp_sum_ff(acc);
             if (lane == 0) Phi[tau] = acc;
         }
         __syncthreads();
         if (M && threadIdx.x == 0) {
-            double m = 0.0;
-            for (int tau = 0; tau < L; ++tau) m += Phi[tau];
-            M[b] = m / (double)V;
+            FF m{0.f, 0.f};
+            for (int tau = 0; tau < L; ++tau) ff_add(m, Phi[tau]);
+            M[b] = ff_to_double(m) * inv_v;
         }
         if (C) {
             for (int t = threadIdx.x; t < L; t += blockDim.x) {
-                double acc = 0.0;
-                for (int tau = 0, u = t; tau < L; ++tau, u = (u + 1 == L) ? 0 : u + 1) acc += Phi[tau] * Phi[u];
-                C[b * L + t] = acc / (double)V;
+                FF acc{0.f, 0.f};
+                for (int tau = 0, u = t; tau < L; ++tau, u = (u + 1 == L) ? 0 : u + 1) ff_fma(acc, Phi[tau], Phi[u]);
+                C[b * L + t] = ff_to_double(acc) * inv_v;
             }
         }
         __syncthreads();
+    }
+}
+
+// One warp per configuration (grid-stride over configurations), for slices of
+// a multiple of 128 sites and L <= kObsWarpMaxL: lane l reads 16-byte pieces
+// l, l + 32, ... of the field in batches of eight loads, so every lane sees the
+// same slice at the same step; at each slice end the warp reduces its pairs, and
+// the L slice sums (pairs, per-warp shared memory) give M and C(t) without any
+// CTA barrier.  FP64 is slow on this GPU even for one instruction per warp, so
+// 1/V comes from the host (a division per thread was most of the run time).
+constexpr int kObsWarpMaxL = 64;
+__global__ void __launch_bounds__(kObsThreads) obs_warp_kernel(int L, int64_t V, int64_t B, double inv_v,
+                                                              const float* __restrict__ phi,
+                                                              double* __restrict__ M, double* __restrict__ C) {
+    __shared__ FF sums[kObsThreads / 32][kObsWarpMaxL];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t S4 = V / L / 4;                 // 16-byte pieces per slice, a multiple of 32
+    const int per = (int)(S4 / 32);               // batches of 32 pieces per slice
+    const int nk = L * per;                       // pieces per lane
+    FF* ps = sums[wid];
+    for (int64_t b = (int64_t)blockIdx.x * (kObsThreads / 32) + wid; b < B;
+         b += (int64_t)gridDim.x * (kObsThreads / 32)) {
+        const float4* q4 = reinterpret_cast<const float4*>(phi + b * V) + lane;
+        FF acc{0.f, 0.f};
+        for (int k0 = 0; k0 < nk; k0 += 8) {
+            float4 v[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (k0 + j < nk) v[j] = __ldg(q4 + (int64_t)32 * (k0 + j));
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                if (k0 + j < nk) {
+                    ff_add(acc, v[j].x);
+                    ff_add(acc, v[j].y);
+                    ff_add(acc, v[j].z);
+                    ff_add(acc, v[j].w);
+                    if ((k0 + j + 1) % per == 0) {             // end of slice (k0 + j) / per
+                        const FF t = warp_sum_ff(acc);
+                        if (lane == 0) ps[(k0 + j) / per] = t;
+                        acc = FF{0.f, 0.f};
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        if (M && lane == 0) {
+            FF m{0.f, 0.f};
+            for (int tau = 0; tau < L; ++tau) ff_add(m, ps[tau]);
+            M[b] = ff_to_double(m) * inv_v;
+        }
+        if (C) {
+            for (int t = lane; t < L; t += 32) {
+                FF a{0.f, 0.f};
+                for (int tau = 0, u = t; tau < L; ++tau, u = (u + 1 == L) ? 0 : u + 1) ff_fma(a, ps[tau], ps[u]);
+                C[b * L + t] = ff_to_double(a) * inv_v;
+            }
+        }
+        __syncwarp();
     }
 }
 
@@ -193,9 +308,16 @@ gf_status gf_observables(int32_t nd, int32_t L, int64_t B, const float* d_phi, d
     if (B > 0 && (!d_phi || (!d_M_out && !d_C_out))) return GF_EINVAL;
     if (B == 0) return GF_OK;
     const int64_t V = ipow(L, nd);
-    const size_t smem = sizeof(double) * (size_t)L;
-    const unsigned grid = (unsigned)std::min<int64_t>(B, (int64_t)num_sms() * 8);
-    obs_kernel<<<grid, kObsThreads, smem, stream>>>(L, V, B, d_phi, d_M_out, d_C_out);
+    const int64_t S = V / L;
+    if (S % 128 == 0 && L <= kObsWarpMaxL && (reinterpret_cast<uintptr_t>(d_phi) & 15) == 0) {
+        constexpr int wpb = kObsThreads / 32;
+        const unsigned grid = (unsigned)std::min<int64_t>((B + wpb - 1) / wpb, (int64_t)num_sms() * 8);
+        obs_warp_kernel<<<grid, kObsThreads, 0, stream>>>(L, V, B, 1.0 / (double)V, d_phi, d_M_out, d_C_out);
+    } else {
+        const size_t smem = sizeof(FF) * (size_t)L;
+        const unsigned grid = (unsigned)std::min<int64_t>(B, (int64_t)num_sms() * 8);
+        obs_kernel<<<grid, kObsThreads, smem, stream>>>(L, V, B, 1.0 / (double)V, d_phi, d_M_out, d_C_out);
+    }
     GF_CHECK_LAUNCH();
     return GF_OK;
 }
