@@ -1,8 +1,9 @@
 """GPU parity of the chain observables against the FP64 oracle.
 
 Per-configuration M and C(t), the autocorrelation function and the ESS are
-FP64 sums in a different order on the two sides: 1e-12 relative (to the
-larger of the value and the configuration's scale).  The chain gather is exact.
+sums in a different order on the two sides (the GPU sums each slice in FP32
+pairs, about 2^-48 relative per addition, the rest in FP64): 1e-12 relative (to
+the larger of the value and the configuration's scale).  The chain gather is exact.
 The window W of tau_int is an integer decided in FP64 on both sides from those
 sums; the AR(1) series used here have no near tie at the window, so W must be
 equal.
