@@ -94,6 +94,49 @@ __device__ __forceinline__ double block_sum(double v, double* scratch) {
     return r;
 }
 
+// Unevaluated sum hi + lo of two FP32 numbers ("double-float"): Knuth's
+// TwoSum gives the exact rounding error of an addition, Dekker's Fast2Sum
+// renormalises the pair and an FMA gives the exact error of a product, so sums
+// and products keep about 2^-48 relative accuracy with FP32 instructions only.
+// FP64 instructions are slow on this GPU (about one lane per SM clock).
+struct FF { float hi, lo; };
+__device__ __forceinline__ void ff_add(FF& a, float b) {
+    const float s = a.hi + b;
+    const float bp = s - a.hi;
+    const float e = (a.hi - (s - bp)) + (b - bp);   // s + e == a.hi + b exactly
+    const float lo = a.lo + e;
+    a.hi = s + lo;
+    a.lo = lo - (a.hi - s);
+}
+__device__ __forceinline__ void ff_add(FF& a, const FF& b) {
+    const float s = a.hi + b.hi;
+    const float bp = s - a.hi;
+    const float e = (a.hi - (s - bp)) + (b.hi - bp);
+    const float lo = e + (a.lo + b.lo);
+    a.hi = s + lo;
+    a.lo = lo - (a.hi - s);
+}
+// x * y for pairs: the head product exactly (FMA residual), the cross terms in
+// FP32 (their rounding is about 2^-48 of the product).
+__device__ __forceinline__ FF ff_mul(const FF& x, const FF& y) {
+    const float p = x.hi * y.hi;
+    const float e = fmaf(x.hi, y.hi, -p) + (x.hi * y.lo + x.lo * y.hi);
+    const float s = p + e;
+    return FF{s, e - (s - p)};
+}
+// acc += x * y
+__device__ __forceinline__ void ff_fma(FF& acc, const FF& x, const FF& y) {
+    const float p = x.hi * y.hi;
+    const float e = fmaf(x.hi, y.hi, -p) + (x.hi * y.lo + x.lo * y.hi);
+    ff_add(acc, FF{p, e});
+}
+__device__ __forceinline__ double ff_to_double(const FF& a) { return (double)a.hi + (double)a.lo; }
+// Host: the pair nearest a double (hi = nearest float, lo = nearest float of the rest).
+inline void ff_split(double d, float* hi, float* lo) {
+    *hi = (float)d;
+    *lo = (float)(d - (double)*hi);
+}
+
 constexpr double LOG_2PI = 1.8378770664093454835606594728112;
 
 // ---------------------------------------------------------------------------

@@ -5,8 +5,9 @@
 // Paper arXiv:2208.08903 Sec. 1 (affine coupling layers, Jacobian, model
 // density, action); precision split of this variant: the convolutions read
 // BF16 operands (the masked field, h1, h2 and the weights) and accumulate in
-// FP32; the field x and the affine update stay FP32; log-det, sum z^2, S,
-// log q and log w are FP64.
+// FP32; the field x and the affine update stay FP32; each thread sums its
+// log-det terms, z^2 and action terms in FP32 pairs (about 2^-48 relative, with
+// no FP64 instruction per site), and the block sums, log q and log w are FP64.
 //
 // Per CTA one configuration at a time (persistent).  Within a layer the
 // lattice is walked along z one 256-site slice at a time:
@@ -202,6 +203,7 @@ struct Bf16Args {
     float slope;
     int use_tanh, has_phi4;
     double m2, lam;
+    float c2d_hi, c2d_lo, lam_hi, lam_lo;   // 2d + m2 and lam as FP32 pairs
     int64_t B;
     uint64_t seed, counter0;
     const float* z_in; float* z_out; const float* phi_in; float* phi_out;
@@ -363,7 +365,7 @@ __device__ __forceinline__ void conv3_epi_load(float (&p)[3][8], uint32_t rm, ui
     tmem_ld_wait();
 }
 __device__ __forceinline__ void conv3_epi_finish(const float (&p)[3][8], int z, float b3s, float b3t, float* x,
-                                                 int frozen, int use_tanh, bool inverse, double& logdet, int mt,
+                                                 int frozen, int use_tanh, bool inverse, FF& logdet, int mt,
                                                  int q, int lane) {
     const int y = mt * 8 + q * 2 + (lane >> 4), xx = lane & 15;
     float st[6];
@@ -379,7 +381,7 @@ __device__ __forceinline__ void conv3_epi_finish(const float (&p)[3][8], int z, 
         float& xv = x[(z * 16 + y) * kXRow + (xx ^ xswz(y))];
         if (!inverse) xv = fmaf(xv, expf(s), tt);
         else xv = (xv - tt) * expf(-s);
-        logdet += (double)s;
+        ff_add(logdet, s);
     }
 }
 
@@ -510,13 +512,14 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
 
     int seq = 0;                                   // layers processed by this CTA so far
     for (int64_t b = blockIdx.x; b < a.B; b += gridDim.x) {
-        double sumz2 = 0.0;
+        FF sumz2{0.f, 0.f};                        // sum z^2: each square exactly as a pair
         if (!INVERSE) {
             if (a.z_in) {
                 for (int n = tid; n < V; n += kThreads) {
                     const float v = __ldg(a.z_in + b * V + n);
                     x[xi(n)] = v;
-                    sumz2 += (double)v * v;
+                    const float p = v * v;
+                    ff_add(sumz2, FF{p, fmaf(v, v, -p)});
                 }
             } else {
                 for (int j = tid; 4 * j < V; j += kThreads) {
@@ -525,7 +528,11 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
                     float zz[4];
                     normals4_f32(w, zz);
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) { x[xi(4 * j + q)] = zz[q]; sumz2 += (double)zz[q] * zz[q]; }
+                    for (int q = 0; q < 4; ++q) {
+                        x[xi(4 * j + q)] = zz[q];
+                        const float p = zz[q] * zz[q];
+                        ff_add(sumz2, FF{p, fmaf(zz[q], zz[q], -p)});
+                    }
                 }
             }
             __syncthreads();
@@ -536,7 +543,7 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
         }
         __syncthreads();
 
-        double logdet = 0.0;
+        FF logdet{0.f, 0.f};                       // this thread's sum of s over its updated sites
         const int seq0 = seq, nl = a.n_layers;
         // Layers are pipelined into one another (no CTA barrier between them): layer li
         // (global number s = seq0 + li) walks the lattice slices in the order R + v with
@@ -798,28 +805,37 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
         if (INVERSE) {
             for (int n = tid; n < V; n += kThreads) {
                 const float v = x[xi(n)];
-                sumz2 += (double)v * v;
+                const float p = v * v;
+                ff_add(sumz2, FF{p, fmaf(v, v, -p)});
                 if (a.z_out) a.z_out[b * V + n] = v;
             }
         } else {
             for (int n = tid; n < V; n += kThreads) a.phi_out[b * V + n] = x[xi(n)];
         }
-        const double ld = block_sum(logdet, red);
-        const double z2 = block_sum(sumz2, red);
+        const double ld = block_sum(ff_to_double(logdet), red);
+        const double z2 = block_sum(ff_to_double(sumz2), red);
         double S = 0.0;
         if (!INVERSE && a.has_phi4) {
-            // forward-hop arrangement of the action: (2d + m2) phi^2 + lam phi^4 - 2 phi sum_mu phi(n + mu)
-            const double c2d = 6.0 + a.m2;
-            double acc = 0.0;
+            // forward-hop arrangement of the action, per site
+            // phi^2 (c2d + lam phi^2) - 2 phi sum_mu phi(n + mu), c2d = 2d + m2, in FP32 pairs
+            // (phi^2 exact, products and sums to about 2^-48), widened to FP64 per thread
+            const FF c2d{a.c2d_hi, a.c2d_lo}, lam{a.lam_hi, a.lam_lo};
+            FF acc{0.f, 0.f};
             for (int n = tid; n < V; n += kThreads) {
                 const int xc = n & 15, yc = (n >> 4) & 15, zc = n >> 8;
-                const double hop = (double)x[xi((n & ~15) | wrap16(xc + 1))] +
-                                   (double)x[xi((zc << 8) | (wrap16(yc + 1) << 4) | xc)] +
-                                   (double)x[xi((wrap16(zc + 1) << 8) | (yc << 4) | xc)];
-                const double c = x[xi(n)], qq = c * c;
-                acc += fma(qq, fma(a.lam, qq, c2d), -2.0 * c * hop);
+                FF hop{x[xi((n & ~15) | wrap16(xc + 1))], 0.f};
+                ff_add(hop, x[xi((zc << 8) | (wrap16(yc + 1) << 4) | xc)]);
+                ff_add(hop, x[xi((wrap16(zc + 1) << 8) | (yc << 4) | xc)]);
+                const float c = x[xi(n)], cp = c * c;
+                const FF qq{cp, fmaf(c, c, -cp)};
+                FF inner = ff_mul(lam, qq);
+                ff_add(inner, c2d);
+                const FF pot = ff_mul(qq, inner);
+                const FF kin = ff_mul(FF{-2.f * c, 0.f}, hop);
+                ff_add(acc, pot);
+                ff_add(acc, kin);
             }
-            S = block_sum(acc, red);
+            S = block_sum(ff_to_double(acc), red);
         }
         if (tid == 0) {
             const double logr = -0.5 * z2 - 0.5 * (double)V * LOG_2PI;
@@ -940,6 +956,8 @@ gf_status launch_flow_bf16(const gf_flow* f, bool inverse, const gf_phi4* phi4, 
     a.has_phi4 = phi4 != nullptr;
     a.m2 = phi4 ? phi4->m2 : 0.0;
     a.lam = phi4 ? phi4->lam : 0.0;
+    ff_split(6.0 + a.m2, &a.c2d_hi, &a.c2d_lo);
+    ff_split(a.lam, &a.lam_hi, &a.lam_lo);
     a.B = B; a.seed = seed; a.counter0 = counter0;
     a.z_in = z_in; a.z_out = z_out; a.phi_in = phi_in; a.phi_out = phi_out;
     a.logq_out = logq_out; a.S_out = S_out; a.logw_out = logw_out;

@@ -27,28 +27,6 @@ namespace {
 constexpr int kObsThreads = 256;
 constexpr int kRedThreads = 1024;
 
-// Sum of FP32 values kept as an unevaluated pair hi + lo of FP32 numbers
-// (Knuth's TwoSum for the rounding error of each addition, renormalised with
-// Dekker's Fast2Sum), so each lane's partial slice sum is accurate to about
-// n 2^-48 relative without FP64 arithmetic, which is slow on this GPU; the
-// pair is widened to FP64 once per lane.
-struct FF { float hi, lo; };
-__device__ __forceinline__ void ff_add(FF& a, float b) {
-    const float s = a.hi + b;
-    const float bp = s - a.hi;
-    const float e = (a.hi - (s - bp)) + (b - bp);   // s + e == a.hi + b exactly
-    const float lo = a.lo + e;
-    a.hi = s + lo;
-    a.lo = lo - (a.hi - s);
-}
-__device__ __forceinline__ void ff_add(FF& a, const FF& b) {
-    const float s = a.hi + b.hi;
-    const float bp = s - a.hi;
-    const float e = (a.hi - (s - bp)) + (b.hi - bp);
-    const float lo = e + (a.lo + b.lo);
-    a.hi = s + lo;
-    a.lo = lo - (a.hi - s);
-}
 // Butterfly sum of the lanes' pairs (fixed order).
 __device__ __forceinline__ FF warp_sum_ff(FF a) {
 #pragma unroll
@@ -58,15 +36,6 @@ __device__ __forceinline__ FF warp_sum_ff(FF a) {
     }
     return a;
 }
-// acc += x * y for pairs: the head product exactly (FMA residual), the cross
-// terms in FP32 (their rounding is about 2^-48 of the product).
-__device__ __forceinline__ void ff_fma(FF& acc, const FF& x, const FF& y) {
-    const float p = x.hi * y.hi;
-    const float e = fmaf(x.hi, y.hi, -p) + (x.hi * y.lo + x.lo * y.hi);
-    ff_add(acc, FF{p, e});
-}
-__device__ __forceinline__ double ff_to_double(const FF& a) { return (double)a.hi + (double)a.lo; }
-
 // One CTA per configuration (grid-stride).  Dynamic shared memory: L pairs.
 // Each warp sums whole slices: every lane first issues up to four 16-byte loads,
 // then adds them into its FP32 pair; the warp reduces the pairs the same way.
