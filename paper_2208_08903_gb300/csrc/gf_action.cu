@@ -3,10 +3,12 @@
 // lattice Laplacian).
 //
 // Each CTA stages one configuration at a time in shared memory with 16-byte
-// loads (grid-stride over configurations), evaluates the site terms in FP64
-// from shared memory and reduces them in a fixed order.  On GB300 the FP64
-// issue rate (about 1/64 of FP32), not HBM, bounds it: the site terms must be
-// FP64 because S enters the Metropolis-Hastings log weights.
+// loads (grid-stride over configurations), evaluates the site terms from shared
+// memory and reduces them in a fixed order.  S enters the Metropolis-Hastings
+// log weights, so it needs FP64 accuracy; for FP32 fields the site terms and the
+// per-thread sums are formed in FP32 pairs (about 2^-48 relative), because FP64
+// instructions are slow on GB300 (the FP64 form was FP64-bound at 2 % of HBM);
+// FP64 fields keep FP64 arithmetic.
 #include <algorithm>
 
 #include "gf_common.cuh"
@@ -62,20 +64,46 @@ __device__ __forceinline__ double site_term_fwd(const T* p, int n, int nd, int L
     return fma(q, fma(lam, q, c2d), -2.0 * c * hop);
 }
 
+// The same site term for an FP32 field in FP32 pairs, added to acc: phi^2
+// exactly (FMA residual), the products and sums to about 2^-48.
+__device__ __forceinline__ void site_term_ff(FF& acc, const float* p, int n, int nd, int L, const FF& c2d,
+                                             const FF& lam) {
+    const int xc = n % L, yc = (n / L) % L;
+    FF hop{p[n - xc + wrapi(xc + 1, L)], 0.f};
+    ff_add(hop, p[n + (wrapi(yc + 1, L) - yc) * L]);
+    if (nd == 3) {
+        const int zc = n / (L * L);
+        ff_add(hop, p[n + (wrapi(zc + 1, L) - zc) * L * L]);
+    }
+    const float c = p[n], cp = c * c;
+    const FF qq{cp, fmaf(c, c, -cp)};
+    FF inner = ff_mul(lam, qq);
+    ff_add(inner, c2d);
+    ff_add(acc, ff_mul(qq, inner));
+    ff_add(acc, ff_mul(FF{-2.f * c, 0.f}, hop));
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kActThreads) action_kernel(int nd, int L, int V, double m2, double lam,
-                                                             int64_t B, const T* __restrict__ phi,
-                                                             double* __restrict__ S_out) {
+                                                             FF c2d_ff, FF lam_ff, int64_t B,
+                                                             const T* __restrict__ phi, double* __restrict__ S_out) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* p = reinterpret_cast<T*>(smem_raw);
     double* red = reinterpret_cast<double*>(smem_raw + (((size_t)V * sizeof(T) + 15) & ~size_t(15)));
-    const double c2d = 2.0 * nd + m2;
     for (int64_t b = blockIdx.x; b < B; b += gridDim.x) {
         stage(phi + b * V, p, V);
         __syncthreads();
-        double acc = 0.0;
-        for (int n = threadIdx.x; n < V; n += blockDim.x) acc += site_term_fwd(p, n, nd, L, c2d, lam);
-        const double S = block_sum(acc, red);
+        double S;
+        if constexpr (sizeof(T) == 4) {
+            FF a{0.f, 0.f};
+            for (int n = threadIdx.x; n < V; n += blockDim.x) site_term_ff(a, p, n, nd, L, c2d_ff, lam_ff);
+            S = block_sum_ff(a, reinterpret_cast<FF*>(red));
+        } else {
+            const double c2d = 2.0 * nd + m2;
+            double acc = 0.0;
+            for (int n = threadIdx.x; n < V; n += blockDim.x) acc += site_term_fwd(p, n, nd, L, c2d, lam);
+            S = block_sum(acc, red);
+        }
         if (threadIdx.x == 0) S_out[b] = S;
         __syncthreads();
     }
@@ -151,19 +179,22 @@ gf_status gf_phi4_action(int32_t nd, int32_t L, const gf_phi4* phi4, int64_t B,
     int V = 1;
     for (int i = 0; i < nd; ++i) V *= L;
     const size_t esz = phi_is_fp64 ? 8 : 4;
+    FF c2d_ff, lam_ff;
+    ff_split(2.0 * nd + phi4->m2, &c2d_ff.hi, &c2d_ff.lo);
+    ff_split(phi4->lam, &lam_ff.hi, &lam_ff.lo);
     const size_t smem = (((size_t)V * esz + 15) & ~size_t(15)) + 32 * sizeof(double);
     if (phi_is_fp64) {
         auto k = action_kernel<double>;
         if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
             return GF_ECUDA;
         k<<<(unsigned)grid_for(k, smem, B), kActThreads, smem, stream>>>(
-            nd, L, V, phi4->m2, phi4->lam, B, static_cast<const double*>(d_phi), d_S_out);
+            nd, L, V, phi4->m2, phi4->lam, c2d_ff, lam_ff, B, static_cast<const double*>(d_phi), d_S_out);
     } else {
         auto k = action_kernel<float>;
         if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
             return GF_ECUDA;
         k<<<(unsigned)grid_for(k, smem, B), kActThreads, smem, stream>>>(
-            nd, L, V, phi4->m2, phi4->lam, B, static_cast<const float*>(d_phi), d_S_out);
+            nd, L, V, phi4->m2, phi4->lam, c2d_ff, lam_ff, B, static_cast<const float*>(d_phi), d_S_out);
     }
     GF_CHECK_LAUNCH();
     return GF_OK;

@@ -131,6 +131,27 @@ __device__ __forceinline__ void ff_fma(FF& acc, const FF& x, const FF& y) {
     ff_add(acc, FF{p, e});
 }
 __device__ __forceinline__ double ff_to_double(const FF& a) { return (double)a.hi + (double)a.lo; }
+// Butterfly sum of the lanes' pairs (fixed order).
+__device__ __forceinline__ FF warp_sum_ff(FF a) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const FF b{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+        ff_add(a, b);
+    }
+    return a;
+}
+// Block sum of the threads' pairs in a fixed order, widened to FP64 (valid in
+// every thread); scratch holds 32 pairs.
+__device__ __forceinline__ double block_sum_ff(FF v, FF* scratch) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    v = warp_sum_ff(v);
+    if (lane == 0) scratch[wid] = v;
+    __syncthreads();
+    FF r = lane < nw ? scratch[lane] : FF{0.f, 0.f};
+    r = warp_sum_ff(r);
+    __syncthreads();
+    return ff_to_double(r);
+}
 // Host: the pair nearest a double (hi = nearest float, lo = nearest float of the rest).
 inline void ff_split(double d, float* hi, float* lo) {
     *hi = (float)d;

@@ -812,8 +812,9 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
         } else {
             for (int n = tid; n < V; n += kThreads) a.phi_out[b * V + n] = x[xi(n)];
         }
-        const double ld = block_sum(ff_to_double(logdet), red);
-        const double z2 = block_sum(ff_to_double(sumz2), red);
+        FF* red_ff = reinterpret_cast<FF*>(red);
+        const double ld = block_sum_ff(logdet, red_ff);
+        const double z2 = block_sum_ff(sumz2, red_ff);
         double S = 0.0;
         if (!INVERSE && a.has_phi4) {
             // forward-hop arrangement of the action, per site
@@ -835,7 +836,7 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
                 ff_add(acc, pot);
                 ff_add(acc, kin);
             }
-            S = block_sum(ff_to_double(acc), red);
+            S = block_sum_ff(acc, red_ff);
         }
         if (tid == 0) {
             const double logr = -0.5 * z2 - 0.5 * (double)V * LOG_2PI;

@@ -27,15 +27,6 @@ namespace {
 constexpr int kObsThreads = 256;
 constexpr int kRedThreads = 1024;
 
-// Butterfly sum of the lanes' pairs (fixed order).
-__device__ __forceinline__ FF warp_sum_ff(FF a) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const FF b{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
-        ff_add(a, b);
-    }
-    return a;
-}
 // One CTA per configuration (grid-stride).  Dynamic shared memory: L pairs.
 // Each warp sums whole slices: every lane first issues up to four 16-byte loads,
 // then adds them into its FP32 pair; the warp reduces the pairs the same way.
