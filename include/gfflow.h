@@ -40,8 +40,10 @@ typedef enum {
 
 typedef enum {
     GF_PREC_FP32 = 0,             /* FP32 convolutions, FP64 sums                  */
-    GF_PREC_BF16CONV_FP64RED = 1  /* BF16 tensor-core conv2, FP32 accumulate,
-                                     FP64 sums (3D, C=32 only)                    */
+    GF_PREC_BF16CONV_FP64RED = 1  /* BF16 tensor-core conv1/conv2/conv3, FP32
+                                     accumulate; log-det, z^2 and action sums to
+                                     FP64 accuracy (FP32 pairs per thread, FP64
+                                     across the block) (3D, L=16, C=32 only)     */
 } gf_precision;
 
 /* Flow shape (paper Sec. 3, model parameters: n_layers, hidden_sizes,
