@@ -8,7 +8,8 @@
 // One CTA owns one configuration at a time (persistent grid-stride loop):
 // the field x stays in shared memory through every layer, the hidden
 // activations h1/h2 live in a slot cache of slices (see gf_flow.cuh), the
-// log-det, sum z^2 and action are reduced in FP64.  Nothing but the inputs
+// log-det, sum z^2 and action are summed to FP64 accuracy (FP32 pairs per
+// thread, see gf_common.cuh, then across the block).  Nothing but the inputs
 // and the per-configuration results touches global memory: weights are read
 // through the read-only path (L1/L2), or, when every layer's packed weights
 // fit beside the activations (small flows such as the paper's 2D L=8 example),
@@ -35,6 +36,7 @@ struct FlowArgs {
     int use_tanh;
     int has_phi4;
     double m2, lam;
+    FF c2d_ff, lam_ff;       // 2 nd + m2 and lam as FP32 pairs
     int64_t B;
     uint64_t seed, counter0;
     const float* z_in;
@@ -217,7 +219,7 @@ __device__ void phase_h2(const FlowArgs& a, const float* __restrict__ Wl, const 
 // C2/tps channels, combined with xor-shuffles.
 template <int ND, bool INVERSE, bool WS>
 __device__ void phase_c3(const FlowArgs& a, const float* __restrict__ Wl, const Phase& ph,
-                         const float* h2, float* x, int frozen, double& logdet) {
+                         const float* h2, float* x, int frozen, FF& logdet) {
     const int L = a.L, S = a.S, C2 = a.C2, T = (ND == 3) ? 27 : 9;
     const int half = S >> 1, nact = ph.n * half;
     int tps = 1;
@@ -272,26 +274,29 @@ __device__ void phase_c3(const FlowArgs& a, const float* __restrict__ Wl, const 
             float& xv = x[sl * S + j];
             if (!INVERSE) xv = fmaf(xv, expf(s), tt);
             else xv = (xv - tt) * expf(-s);
-            logdet += (double)s;
+            ff_add(logdet, s);
         }
     }
 }
 
-// phi^4 site term in FP64 (paper Sec. 1): sum_mu phi (2 phi - phi(n+mu) - phi(n-mu)) + m2 phi^2 + lam phi^4
+// phi^4 action of the configuration in shared memory (paper Sec. 1), this
+// thread's sites, in the forward-hop arrangement (equal to the two-neighbour
+// form summed over the lattice): phi^2 (c2d + lam phi^2) - 2 phi sum_mu phi(n + mu),
+// c2d = 2 nd + m2, in FP32 pairs (phi^2 exact, products and sums to about 2^-48).
 template <int ND>
-__device__ double action_part(const float* x, int L, int V, double m2, double lam) {
-    double acc = 0.0;
+__device__ FF action_part(const float* x, int L, int V, const FF& c2d, const FF& lam) {
+    FF acc{0.f, 0.f};
     for (int n = threadIdx.x; n < V; n += blockDim.x) {
         const int xc = n % L, yc = (n / L) % L, zc = n / (L * L);
-        const double p = x[n];
-        double k = 0.0;
-        k += 2.0 * p - (double)x[n - xc + wrap(xc + 1, L)] - (double)x[n - xc + wrap(xc - 1, L)];
-        k += 2.0 * p - (double)x[n + (wrap(yc + 1, L) - yc) * L] - (double)x[n + (wrap(yc - 1, L) - yc) * L];
-        if (ND == 3)
-            k += 2.0 * p - (double)x[n + (wrap(zc + 1, L) - zc) * L * L] -
-                 (double)x[n + (wrap(zc - 1, L) - zc) * L * L];
-        const double p2 = p * p;
-        acc += p * k + m2 * p2 + lam * p2 * p2;
+        FF hop{x[n - xc + wrap(xc + 1, L)], 0.f};
+        ff_add(hop, x[n + (wrap(yc + 1, L) - yc) * L]);
+        if (ND == 3) ff_add(hop, x[n + (wrap(zc + 1, L) - zc) * L * L]);
+        const float c = x[n], cp = c * c;
+        const FF qq{cp, fmaf(c, c, -cp)};
+        FF inner = ff_mul(lam, qq);
+        ff_add(inner, c2d);
+        ff_add(acc, ff_mul(qq, inner));
+        ff_add(acc, ff_mul(FF{-2.f * c, 0.f}, hop));
     }
     return acc;
 }
@@ -318,13 +323,14 @@ __global__ void __launch_bounds__(kThreads) flow_fp32_kernel(const FlowArgs a) {
     const float* Wbase = WS ? wsm : a.W;
 
     for (int64_t b = blockIdx.x; b < a.B; b += gridDim.x) {
-        double sumz2 = 0.0;
+        FF sumz2{0.f, 0.f};                        // sum z^2: each square exactly as a pair
         if (!INVERSE) {
             if (a.z_in) {
                 for (int n = threadIdx.x; n < V; n += blockDim.x) {
                     const float v = __ldg(a.z_in + b * V + n);
                     x[n] = v;
-                    sumz2 += (double)v * v;
+                    const float p = v * v;
+                    ff_add(sumz2, FF{p, fmaf(v, v, -p)});
                 }
             } else {
                 for (int j = threadIdx.x; 4 * j < V; j += blockDim.x) {
@@ -336,7 +342,8 @@ __global__ void __launch_bounds__(kThreads) flow_fp32_kernel(const FlowArgs a) {
                     for (int q = 0; q < 4; ++q) {
                         if (4 * j + q < V) {
                             x[4 * j + q] = zz[q];
-                            sumz2 += (double)zz[q] * zz[q];
+                            const float p = zz[q] * zz[q];
+                            ff_add(sumz2, FF{p, fmaf(zz[q], zz[q], -p)});
                         }
                     }
                 }
@@ -349,7 +356,7 @@ __global__ void __launch_bounds__(kThreads) flow_fp32_kernel(const FlowArgs a) {
         }
         __syncthreads();
 
-        double logdet = 0.0;
+        FF logdet{0.f, 0.f};
         for (int li = 0; li < a.n_layers; ++li) {
             const int l = INVERSE ? a.n_layers - 1 - li : li;
             const int frozen = l & 1;
@@ -369,16 +376,18 @@ __global__ void __launch_bounds__(kThreads) flow_fp32_kernel(const FlowArgs a) {
         if (INVERSE) {
             for (int n = threadIdx.x; n < V; n += blockDim.x) {
                 const float v = x[n];
-                sumz2 += (double)v * v;
+                const float p = v * v;
+                ff_add(sumz2, FF{p, fmaf(v, v, -p)});
                 if (a.z_out) a.z_out[b * V + n] = v;
             }
         } else {
             for (int n = threadIdx.x; n < V; n += blockDim.x) a.phi_out[b * V + n] = x[n];
         }
-        const double ld = block_sum(logdet, red);
-        const double z2 = block_sum(sumz2, red);
+        FF* red_ff = reinterpret_cast<FF*>(red);
+        const double ld = block_sum_ff(logdet, red_ff);
+        const double z2 = block_sum_ff(sumz2, red_ff);
         double S = 0.0;
-        if (!INVERSE && a.has_phi4) S = block_sum(action_part<ND>(x, a.L, V, a.m2, a.lam), red);
+        if (!INVERSE && a.has_phi4) S = block_sum_ff(action_part<ND>(x, a.L, V, a.c2d_ff, a.lam_ff), red_ff);
         if (threadIdx.x == 0) {
             const double logr = -0.5 * z2 - 0.5 * (double)V * LOG_2PI;
             const double logq = logr - ld;
@@ -455,6 +464,8 @@ gf_status launch_flow_fp32(const gf_flow* f, bool inverse, const gf_phi4* phi4, 
     a.has_phi4 = phi4 != nullptr;
     a.m2 = phi4 ? phi4->m2 : 0.0;
     a.lam = phi4 ? phi4->lam : 0.0;
+    ff_split(2.0 * f->shape.nd + a.m2, &a.c2d_ff.hi, &a.c2d_ff.lo);
+    ff_split(a.lam, &a.lam_ff.hi, &a.lam_ff.lo);
     a.B = B; a.seed = seed; a.counter0 = counter0;
     a.z_in = z_in; a.z_out = z_out; a.phi_in = phi_in; a.phi_out = phi_out;
     a.logq_out = logq_out; a.S_out = S_out; a.logw_out = logw_out;
