@@ -66,8 +66,12 @@ __device__ __forceinline__ double site_term_fwd(const T* p, int n, int nd, int L
 
 // The same site term for an FP32 field in FP32 pairs, added to acc: phi^2
 // exactly (FMA residual), the products and sums to about 2^-48.
-__device__ __forceinline__ void site_term_ff(FF& acc, const float* p, int n, int nd, int L, const FF& c2d,
+// LC > 0: the lattice size as a compile-time constant (the index arithmetic,
+// which otherwise dominates, becomes shifts and masks for powers of two).
+template <int LC>
+__device__ __forceinline__ void site_term_ff(FF& acc, const float* p, int n, int nd, int L_rt, const FF& c2d,
                                              const FF& lam) {
+    const int L = LC > 0 ? LC : L_rt;
     const int xc = n % L, yc = (n / L) % L;
     FF hop{p[n - xc + wrapi(xc + 1, L)], 0.f};
     ff_add(hop, p[n + (wrapi(yc + 1, L) - yc) * L]);
@@ -83,7 +87,7 @@ __device__ __forceinline__ void site_term_ff(FF& acc, const float* p, int n, int
     ff_add(acc, ff_mul(FF{-2.f * c, 0.f}, hop));
 }
 
-template <typename T>
+template <typename T, int LC = 0>
 __global__ void __launch_bounds__(kActThreads) action_kernel(int nd, int L, int V, double m2, double lam,
                                                              FF c2d_ff, FF lam_ff, int64_t B,
                                                              const T* __restrict__ phi, double* __restrict__ S_out) {
@@ -96,7 +100,7 @@ __global__ void __launch_bounds__(kActThreads) action_kernel(int nd, int L, int 
         double S;
         if constexpr (sizeof(T) == 4) {
             FF a{0.f, 0.f};
-            for (int n = threadIdx.x; n < V; n += blockDim.x) site_term_ff(a, p, n, nd, L, c2d_ff, lam_ff);
+            for (int n = threadIdx.x; n < V; n += blockDim.x) site_term_ff<LC>(a, p, n, nd, L, c2d_ff, lam_ff);
             S = block_sum_ff(a, reinterpret_cast<FF*>(red));
         } else {
             const double c2d = 2.0 * nd + m2;
@@ -190,7 +194,7 @@ gf_status gf_phi4_action(int32_t nd, int32_t L, const gf_phi4* phi4, int64_t B,
         k<<<(unsigned)grid_for(k, smem, B), kActThreads, smem, stream>>>(
             nd, L, V, phi4->m2, phi4->lam, c2d_ff, lam_ff, B, static_cast<const double*>(d_phi), d_S_out);
     } else {
-        auto k = action_kernel<float>;
+        auto k = (nd == 3 && L == 16) ? action_kernel<float, 16> : action_kernel<float>;
         if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
             return GF_ECUDA;
         k<<<(unsigned)grid_for(k, smem, B), kActThreads, smem, stream>>>(
