@@ -51,7 +51,7 @@ class Flow:
 
     shape: any object with nd, L, n_layers, c1, c2, use_final_tanh, leaky_slope.
     weights: FP64 numpy array (or CPU tensor) in canonical layout.
-    precision: "fp32" or "bf16" (BF16 tensor-core conv2, FP64 sums).
+    precision: "fp32" or "bf16" (BF16 tensor-core convolutions, sums to FP64 accuracy).
     """
 
     def __init__(self, shape, weights, precision: str = "fp32"):

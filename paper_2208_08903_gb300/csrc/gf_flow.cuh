@@ -53,7 +53,7 @@ struct gf_flow {
     size_t smem_bytes;
     bool wsmem;             // FP32 kernel keeps all packed weights in shared memory
     // BF16 tensor-core path (3D, C=32)
-    void* d_bf16;           // packed bf16 conv2 weights and FP32 head weights
+    void* d_bf16;           // per layer: bf16 conv2 / conv3 / conv1 (+ bias) B operands, FP32 biases
     size_t smem_bytes_bf16;
 };
 
