@@ -24,6 +24,8 @@ _OUT = os.path.join(_HERE, "_build", "libgforacle.so")
 _lib = None
 
 BF16_H1, BF16_W2, BF16_H2, BF16_W3, BF16_W1, F32_IO, BF16_X1 = 1, 2, 4, 8, 16, 32, 64
+F32_ACC = 128        # FP32-accumulating model (tolerance experiment only)
+BF16_MODE = BF16_H1 | BF16_W2 | BF16_H2 | BF16_W3 | BF16_W1 | F32_IO | BF16_X1
 
 
 def build(force: bool = False) -> str:

@@ -202,22 +202,36 @@ static layer_w layer_ptrs(const gfo_shape* sh, const double* w, int layer) {
 
 static double lrelu(double v, double a) { return v > 0.0 ? v : a * v; }
 
-/* Periodic cross-correlation: in [V][Cin] -> out [V][Cout], W [Cout][Cin][T]. */
+/* Periodic cross-correlation: in [V][Cin] -> out [V][Cout], W [Cout][Cin][T].
+ * f32acc: the sum is carried in FP32 (GFO_F32_ACC), else in FP64. */
 static void conv(int64_t V, int T, const int64_t* nbr, int Cin, int Cout,
-                 const double* W, const double* b, int round_w, const double* in, double* out) {
+                 const double* W, const double* b, int round_w, int f32acc,
+                 const double* in, double* out) {
+    /* bf16 weights: every weight rounded once up front (the same values the
+     * products below would see if each were rounded where it is read) */
+    const int64_t nw = (int64_t)Cout * Cin * T;
+    double* Wr = NULL;
+    if (round_w) {
+        Wr = (double*)malloc(sizeof(double) * (nw > 0 ? nw : 1));
+        for (int64_t k = 0; k < nw; ++k) Wr[k] = bf16_round(W[k]);
+        W = Wr;
+    }
     for (int64_t n = 0; n < V; ++n) {
         for (int o = 0; o < Cout; ++o) {
             double acc = b[o];
+            float facc = (float)b[o];
             for (int i = 0; i < Cin; ++i) {
                 for (int t = 0; t < T; ++t) {
-                    double wv = W[((int64_t)o * Cin + i) * T + t];
-                    if (round_w) wv = bf16_round(wv);
-                    acc += wv * in[nbr[n * T + t] * Cin + i];
+                    const double wv = W[((int64_t)o * Cin + i) * T + t];
+                    const double prod = wv * in[nbr[n * T + t] * Cin + i];
+                    if (f32acc) facc = facc + (float)prod;
+                    else acc += prod;
                 }
             }
-            out[n * Cout + o] = acc;
+            out[n * Cout + o] = f32acc ? (double)facc : acc;
         }
     }
+    free(Wr);
 }
 
 /* Network intermediates of one layer on one configuration. */
@@ -249,17 +263,18 @@ static void net_forward(const gfo_shape* sh, layer_w lw, int32_t bf16, int64_t V
         for (int64_t n = 0; n < V; ++n) nb->yin[n] = bf16_round(y[n]);
         y = nb->yin;
     }
-    conv(V, T, nbr, 1, sh->c1, lw.W1, lw.b1, bf16 & GFO_BF16_W1, y, nb->h1pre);
+    const int f32acc = (bf16 & GFO_F32_ACC) != 0;
+    conv(V, T, nbr, 1, sh->c1, lw.W1, lw.b1, bf16 & GFO_BF16_W1, f32acc, y, nb->h1pre);
     for (int64_t k = 0; k < V * sh->c1; ++k) {
         nb->h1[k] = lrelu(nb->h1pre[k], sh->leaky_slope);
         if (bf16 & GFO_BF16_H1) nb->h1[k] = bf16_round(nb->h1[k]);
     }
-    conv(V, T, nbr, sh->c1, sh->c2, lw.W2, lw.b2, bf16 & GFO_BF16_W2, nb->h1, nb->h2pre);
+    conv(V, T, nbr, sh->c1, sh->c2, lw.W2, lw.b2, bf16 & GFO_BF16_W2, f32acc, nb->h1, nb->h2pre);
     for (int64_t k = 0; k < V * sh->c2; ++k) {
         nb->h2[k] = lrelu(nb->h2pre[k], sh->leaky_slope);
         if (bf16 & GFO_BF16_H2) nb->h2[k] = bf16_round(nb->h2[k]);
     }
-    conv(V, T, nbr, sh->c2, 2, lw.W3, lw.b3, bf16 & GFO_BF16_W3, nb->h2, nb->spre);
+    conv(V, T, nbr, sh->c2, 2, lw.W3, lw.b3, bf16 & GFO_BF16_W3, f32acc, nb->h2, nb->spre);
     for (int64_t n = 0; n < V; ++n) {
         nb->s[n] = sh->use_final_tanh ? tanh(nb->spre[2 * n]) : nb->spre[2 * n];
         nb->t[n] = nb->spre[2 * n + 1];
@@ -301,6 +316,7 @@ static void sample_one(const gfo_shape* sh, const double* w, int32_t bf16, int64
         for (int64_t n = 0; n < V; ++n) {
             if (par[n] != frozen) {
                 x[n] = x[n] * exp(nb->s[n]) + nb->t[n];
+                if (bf16 & GFO_F32_ACC) x[n] = (double)(float)x[n];
                 logdet += nb->s[n];
             }
         }

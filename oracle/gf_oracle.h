@@ -63,7 +63,14 @@ enum {
     GFO_BF16_W3 = 8,   /* round conv3 weights to bf16 */
     GFO_BF16_W1 = 16,  /* round conv1 weights to bf16 */
     GFO_F32_IO  = 32,  /* round the prior sample z to fp32 (the paper's Float32 prior) */
-    GFO_BF16_X1 = 64   /* round conv1's input (the masked field) to bf16 */
+    GFO_BF16_X1 = 64,  /* round conv1's input (the masked field) to bf16 */
+    /* Model of an FP32-accumulating device, used only to measure how far two
+     * computations that differ at the FP32 level drift apart through the bf16
+     * roundings: every convolution is summed in FP32 (sequentially, bias
+     * first, each product rounded to FP32 before it is added) and the field
+     * is rounded to FP32 after every affine update.  Sums over the lattice
+     * (log-det, z^2, action) stay FP64. */
+    GFO_F32_ACC = 128
 };
 
 typedef struct {

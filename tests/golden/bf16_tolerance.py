@@ -1,0 +1,100 @@
+"""Derives the parity tolerances of the BF16 tensor-core path from the oracle alone.
+
+The BF16 kernel rounds conv1's input, the conv weights, h1 and h2 to bf16 at
+the same points as the oracle's BF16-emulation mode, but it forms every
+convolution sum in FP32 on the tensor cores where the oracle sums in FP64.
+So the two reach each bf16 rounding with values that differ at the FP32
+level, and a value that sits within that difference of a rounding boundary
+rounds the other way on one side.  Such a flip moves s and t of the nearby
+updated sites by part of a bf16 ulp, and the later coupling layers carry it on.
+
+This script measures that drift with the oracle only: it runs the
+BF16-emulation mode twice on the same inputs, once with FP64 sums (the mode
+the GPU tests compare against) and once with every convolution summed in FP32
+and the field kept in FP32 (GFO_F32_ACC, a model of an FP32-accumulating
+device).  The difference between the two runs is the size of error that
+FP32-level differences produce through the bf16 roundings; the GPU tolerance
+is its maximum over the sample times a stated margin, per number of coupling
+layers.  It also reports the BF16-emulated results' error against the pure
+FP64 oracle.
+
+Inputs: 3D L=16, hidden 32, m2=-6, lam=5 (the 3D workload's theory),
+Kaiming-uniform weights from seed 0, the FP32 prior from seed 77 (not the
+seeds of the GPU tests), 64 configurations per layer count.
+
+    python tests/golden/bf16_tolerance.py          # writes bf16_tolerance.json
+"""
+from __future__ import annotations
+
+import json
+import os
+import sys
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+sys.path.insert(0, ROOT)
+
+import gf_inputs as gi  # noqa: E402
+import oracle  # noqa: E402
+
+OUT = os.path.join(HERE, "bf16_tolerance.json")
+MARGIN = 2.0
+SEED = 77
+LAYERS = (2, 16)
+
+
+def site_err(a, ref):
+    rms = np.sqrt((ref ** 2).mean(1, keepdims=True))
+    return np.abs(a - ref) / np.maximum(np.abs(ref), rms)
+
+
+def scalar_err(a, ref):
+    return np.abs(a - ref) / np.maximum(np.abs(ref), 1.0)
+
+
+def stats(e):
+    e = np.asarray(e, np.float64).ravel()
+    return {"max": float(e.max()), "p99": float(np.percentile(e, 99)), "mean": float(e.mean())}
+
+
+def drift(n_layers: int, B: int, seed: int = SEED, counter0: int = 0, nthreads=None) -> dict:
+    """Per-result error statistics of the FP32-accumulating model against the
+    FP64-summing BF16 emulation, and of the latter against pure FP64."""
+    shape = gi.FlowShape(3, 16, n_layers, 32, 32)
+    w = gi.init_weights(shape, seed=0)
+    m2, lam = -6.0, 5.0
+    kw = dict(seed=seed, counter0=counter0, nthreads=nthreads)
+    ref = oracle.flow_sample(shape, w, m2, lam, B, bf16_mask=oracle.BF16_MODE, **kw)
+    f32 = oracle.flow_sample(shape, w, m2, lam, B, bf16_mask=oracle.BF16_MODE | oracle.F32_ACC, **kw)
+    f64 = oracle.flow_sample(shape, w, m2, lam, B, bf16_mask=oracle.F32_IO, **kw)
+    out = {"n_layers": n_layers, "configurations": B,
+           "fp32_model_vs_emulated": {"phi": stats(site_err(f32["phi"], ref["phi"]))},
+           "emulated_vs_fp64": {"phi": stats(site_err(ref["phi"], f64["phi"]))}}
+    for k in ("logq", "S", "logw"):
+        out["fp32_model_vs_emulated"][k] = stats(scalar_err(f32[k], ref[k]))
+        out["emulated_vs_fp64"][k] = stats(scalar_err(ref[k], f64[k]))
+    d = out["fp32_model_vs_emulated"]
+    out["site_rtol"] = MARGIN * d["phi"]["max"]
+    out["scalar_rtol"] = MARGIN * max(d[k]["max"] for k in ("logq", "S", "logw"))
+    return out
+
+
+def main():
+    oracle.build()
+    res = {"what": "BF16 path parity tolerances per coupling-layer count, derived from the oracle "
+                   "(FP32-accumulating model vs the FP64-summing BF16 emulation)",
+           "margin": MARGIN, "shape": "3D L=16, hidden 32, m2=-6, lam=5, weights seed 0",
+           "prior_seed": SEED, "command": "python tests/golden/bf16_tolerance.py", "by_layers": {}}
+    for n in LAYERS:
+        r = drift(n, 64)
+        res["by_layers"][str(n)] = r
+        print(json.dumps(r), flush=True)
+    with open(OUT, "w") as f:
+        json.dump(res, f, indent=1)
+    print("wrote", OUT)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,10 +1,51 @@
 """Helpers shared by the GPU parity tests: tolerance checks against the oracle."""
+import json
+import os
+
 import numpy as np
 import pytest
 
 # Plain FP32 path: 1e-5 relative per site, 1e-4 relative per log-weight.
 SITE_RTOL = 1e-5
 LOGW_RTOL = 1e-4
+
+# BF16 tensor-core path: compared with the oracle's BF16-emulation mode (conv1
+# input and weights, h1, W2, h2, W3 rounded to bf16 where the kernel rounds
+# them; FP32 prior).  Its tolerances come from a CPU experiment on the oracle
+# alone (tests/golden/bf16_tolerance.py): the drift that FP32-level
+# differences before the bf16 roundings produce, maximum over 64
+# configurations times a margin, per number of coupling layers.
+BF16_MODE = 1 | 2 | 4 | 8 | 16 | 32 | 64
+_BF16_TOL = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "bf16_tolerance.json")
+
+
+def bf16_tolerances(n_layers: int):
+    """(per-site rtol, per-result rtol for log q / S / log w) for a flow of
+    n_layers coupling layers: the bound measured for the smallest layer count
+    in the experiment that is >= n_layers (the drift grows with depth)."""
+    with open(_BF16_TOL) as f:
+        by = json.load(f)["by_layers"]
+    counts = sorted(int(k) for k in by)
+    pick = next((c for c in counts if c >= n_layers), None)
+    if pick is None:
+        raise ValueError(f"no BF16 tolerance measured for {n_layers} coupling layers (have {counts})")
+    e = by[str(pick)]
+    return float(e["site_rtol"]), float(e["scalar_rtol"])
+
+
+def bf16_site_rtol(n_layers: int) -> float:
+    return bf16_tolerances(n_layers)[0]
+
+
+def bf16_logw_rtol(n_layers: int) -> float:
+    return bf16_tolerances(n_layers)[1]
+
+
+def bf16_drift_model(n_layers: int) -> dict:
+    """The experiment's error statistics (max / p99 / mean per result) of the
+    FP32-accumulating model against the FP64-summing emulation."""
+    with open(_BF16_TOL) as f:
+        return json.load(f)["by_layers"][str(n_layers)]["fp32_model_vs_emulated"]
 
 
 def require_gpu():
