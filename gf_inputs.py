@@ -6,15 +6,19 @@ oracle (``oracle/``) and the CUDA library receive the arrays produced here as
 plain data, so neither depends on the other.
 
 Canonical weight layout (FP64, flat, one block per coupling layer ``l`` in the
-order the layers are applied to the prior sample):
+order the layers are applied to the prior sample): for each convolution
+j = 0 .. n_hidden of the layer's s/t network
 
-    W1[c1][1][T]  b1[c1]  W2[c2][c1][T]  b2[c2]  W3[2][c2][T]  b3[2]
+    W{j+1}[c_out][c_in][T]  b{j+1}[c_out]
 
-with ``T = 3**nd`` taps ordered (kz, ky, kx) in 3D and (ky, kx) in 2D, offset
-``k - 1`` along each axis.  Output channel 0 of conv3 is s, channel 1 is t.
-The s/t network shape (three 3^d convolutions, hidden sizes [c1, c2], one
-input channel, two output channels) is the paper's model section (Sec. 3,
-the example parameter file: n_layers, hidden_sizes, kernel_size, inC, outC).
+with c_in = 1 for the first and c_out = 2 for the last (the head), the hidden
+widths in between, ``T = k**nd`` taps ordered (kz, ky, kx) in 3D and (ky, kx)
+in 2D, offset ``t - (k-1)/2`` along each axis.  Output channel 0 of the head is
+s, channel 1 is t.  With the paper's example network (hidden_sizes [c1, c2],
+kernel_size 3) this is W1[c1][1][T] b1 W2[c2][c1][T] b2 W3[2][c2][T] b3.  The
+s/t network shape (n_layers, hidden_sizes, kernel_size, one input channel, two
+output channels) is the paper's model section (Sec. 3, the example parameter
+file).
 
 Initialisation: Kaiming-uniform with negative slope sqrt(5) (the default of
 PyTorch convolution layers, which the paper's software mirrors), i.e.
@@ -34,10 +38,21 @@ class FlowShape:
     nd: int                 # lattice dimension, 2 or 3
     L: int                  # sites per axis (periodic)
     n_layers: int           # affine coupling layers
-    c1: int = 8             # hidden width after conv1
-    c2: int = 8             # hidden width after conv2
+    c1: int = 8             # hidden widths of the paper's two-hidden-layer net
+    c2: int = 8
     use_final_tanh: bool = True
     leaky_slope: float = 0.01
+    hidden_sizes: tuple | None = None   # any hidden_sizes list (overrides c1, c2)
+    ksize: int = 3          # kernel_size (odd), circular padding (ksize-1)/2
+
+    @property
+    def hidden(self) -> tuple:
+        return tuple(self.hidden_sizes) if self.hidden_sizes is not None else (self.c1, self.c2)
+
+    @property
+    def is_default_net(self) -> bool:
+        """The paper's example network form: two hidden convolutions, 3 taps per axis."""
+        return len(self.hidden) == 2 and self.ksize == 3
 
     @property
     def V(self) -> int:
@@ -45,22 +60,32 @@ class FlowShape:
 
     @property
     def taps(self) -> int:
-        return 3 ** self.nd
+        return self.ksize ** self.nd
+
+    def conv_channels(self):
+        """(c_in, c_out) of convolution j = 0 .. n_hidden."""
+        chans = (1,) + self.hidden + (2,)
+        return [(chans[j], chans[j + 1]) for j in range(len(chans) - 1)]
 
     def layer_params(self) -> int:
         T = self.taps
-        return (self.c1 * T + self.c1 + self.c2 * self.c1 * T + self.c2
-                + 2 * self.c2 * T + 2)
+        return sum(ci * co * T + co for ci, co in self.conv_channels())
 
     def n_params(self) -> int:
         return self.n_layers * self.layer_params()
 
+    @property
+    def head(self) -> int:
+        """1-based index of the head convolution (W{head}, b{head})."""
+        return len(self.hidden) + 1
+
     def layer_blocks(self):
-        """(name, shape) of the six tensors of one layer, in layout order."""
+        """(name, shape) of the tensors of one layer, in layout order."""
         T = self.taps
-        return [("W1", (self.c1, 1, T)), ("b1", (self.c1,)),
-                ("W2", (self.c2, self.c1, T)), ("b2", (self.c2,)),
-                ("W3", (2, self.c2, T)), ("b3", (2,))]
+        out = []
+        for j, (ci, co) in enumerate(self.conv_channels()):
+            out += [(f"W{j + 1}", (co, ci, T)), (f"b{j + 1}", (co,))]
+        return out
 
 
 @dataclasses.dataclass(frozen=True)
@@ -73,8 +98,9 @@ def init_weights(shape: FlowShape, seed: int = 0) -> np.ndarray:
     """Flat FP64 weights in the canonical layout, Kaiming-uniform from ``seed``."""
     gen = np.random.Generator(np.random.Philox(key=seed))
     T = shape.taps
-    fan_in = {"W1": T, "b1": T, "W2": shape.c1 * T, "b2": shape.c1 * T,
-              "W3": shape.c2 * T, "b3": shape.c2 * T}
+    fan_in = {}
+    for j, (ci, _) in enumerate(shape.conv_channels()):
+        fan_in[f"W{j + 1}"] = fan_in[f"b{j + 1}"] = ci * T
     out = []
     for _ in range(shape.n_layers):
         for name, shp in shape.layer_blocks():
@@ -98,22 +124,22 @@ def split_layer(shape: FlowShape, w: np.ndarray, layer: int) -> dict:
 
 
 def zero_head(shape: FlowShape, w: np.ndarray) -> np.ndarray:
-    """Copy of ``w`` with every conv3 weight and bias set to zero (s = t = 0)."""
+    """Copy of ``w`` with every head weight and bias set to zero (s = t = 0)."""
     w = w.copy()
     for l in range(shape.n_layers):
         d = split_layer(shape, w, l)
-        d["W3"][...] = 0.0
-        d["b3"][...] = 0.0
+        d[f"W{shape.head}"][...] = 0.0
+        d[f"b{shape.head}"][...] = 0.0
     return w
 
 
 def scale_head(shape: FlowShape, w: np.ndarray, factor: float) -> np.ndarray:
-    """Copy of ``w`` with conv3 weights and bias multiplied by ``factor``."""
+    """Copy of ``w`` with the head's weights and bias multiplied by ``factor``."""
     w = w.copy()
     for l in range(shape.n_layers):
         d = split_layer(shape, w, l)
-        d["W3"][...] *= factor
-        d["b3"][...] *= factor
+        d[f"W{shape.head}"][...] *= factor
+        d[f"b{shape.head}"][...] *= factor
     return w
 
 

@@ -25,6 +25,7 @@ _lib = None
 
 BF16_H1, BF16_W2, BF16_H2, BF16_W3, BF16_W1, F32_IO, BF16_X1 = 1, 2, 4, 8, 16, 32, 64
 F32_ACC = 128        # FP32-accumulating model (tolerance experiment only)
+Z_JITTER = 256       # prior perturbed within its FP32 test bound (tolerance experiment only)
 BF16_MODE = BF16_H1 | BF16_W2 | BF16_H2 | BF16_W3 | BF16_W1 | F32_IO | BF16_X1
 
 
@@ -45,10 +46,13 @@ def build(force: bool = False) -> str:
     return _OUT
 
 
+MAX_HIDDEN = 8
+
+
 class Shape(C.Structure):
     _fields_ = [("nd", C.c_int32), ("L", C.c_int32), ("n_layers", C.c_int32),
-                ("c1", C.c_int32), ("c2", C.c_int32), ("use_final_tanh", C.c_int32),
-                ("leaky_slope", C.c_double)]
+                ("n_hidden", C.c_int32), ("hidden", C.c_int32 * MAX_HIDDEN), ("ksize", C.c_int32),
+                ("use_final_tanh", C.c_int32), ("leaky_slope", C.c_double)]
 
 
 class MHState(C.Structure):
@@ -112,7 +116,13 @@ def default_threads() -> int:
 
 
 def shape_struct(shape) -> Shape:
-    return Shape(shape.nd, shape.L, shape.n_layers, shape.c1, shape.c2,
+    """gfo_shape of any object with nd, L, n_layers, use_final_tanh, leaky_slope
+    and either `hidden` (+ `ksize`) or c1, c2 (two hidden layers, 3 taps per axis)."""
+    hidden = tuple(getattr(shape, "hidden", (shape.c1, shape.c2)))
+    if len(hidden) > MAX_HIDDEN:
+        raise ValueError(f"at most {MAX_HIDDEN} hidden convolutions")
+    h = (C.c_int32 * MAX_HIDDEN)(*(list(hidden) + [0] * (MAX_HIDDEN - len(hidden))))
+    return Shape(shape.nd, shape.L, shape.n_layers, len(hidden), h, int(getattr(shape, "ksize", 3)),
                  1 if shape.use_final_tanh else 0, shape.leaky_slope)
 
 

@@ -44,7 +44,7 @@ void gfo_philox4x64_10(const uint64_t key[2], const uint64_t ctr[4], uint64_t ou
 
 /* Stream tags in the last counter word (reading: the paper does not specify
  * its generator; each random purpose gets its own counter sub-space). */
-enum { TAG_PRIOR = 1, TAG_MH = 2, TAG_HMC_P = 3, TAG_HMC_U = 4 };
+enum { TAG_PRIOR = 1, TAG_MH = 2, TAG_HMC_P = 3, TAG_HMC_U = 4, TAG_Z_JITTER = 5 };
 
 /* Uniform in (0,1) with 23 random bits: (2k+1) * 2^-24, exact in fp32. */
 static double u24(uint64_t w) { return (double)(2 * (w >> 41) + 1) * 0x1p-24; }
@@ -105,17 +105,18 @@ static int parity(int nd, int L, int64_t n) {
     int c[3]; coords(nd, L, n, c);
     return (c[0] + c[1] + c[2]) & 1;
 }
-/* nbr[n*T + t] = index of n + delta(t); taps ordered (kz,ky,kx) / (ky,kx),
- * delta = k - 1 along each axis. */
-static int64_t* make_nbr(int nd, int L) {
-    int64_t V = ipow(L, nd); int T = (int)ipow(3, nd);
+/* nbr[n*T + t] = index of n + delta(t) for a K^nd-tap stencil; taps ordered
+ * (kz,ky,kx) / (ky,kx) with kx fastest, delta = k - (K-1)/2 along each axis. */
+static int64_t* make_nbr(int nd, int L, int K) {
+    int64_t V = ipow(L, nd); int T = (int)ipow(K, nd);
+    const int h = (K - 1) / 2;
     int64_t* nbr = (int64_t*)malloc(sizeof(int64_t) * V * T);
     for (int64_t n = 0; n < V; ++n) {
         int c[3]; coords(nd, L, n, c);
         for (int t = 0; t < T; ++t) {
             int k[3] = {0, 0, 0}; int tt = t;
-            for (int a = 0; a < nd; ++a) { k[a] = tt % 3; tt /= 3; } /* k[0]=kx (fastest) */
-            int d[3] = {c[0] + k[0] - 1, c[1] + k[1] - 1, c[2] + k[2] - 1};
+            for (int a = 0; a < nd; ++a) { k[a] = tt % K; tt /= K; } /* k[0]=kx (fastest) */
+            int d[3] = {c[0] + k[0] - h, c[1] + k[1] - h, c[2] + k[2] - h};
             nbr[n * T + t] = site(nd, L, d);
         }
     }
@@ -167,8 +168,10 @@ void gfo_force(int32_t nd, int32_t L, double m2, double lam, int64_t B, const do
 }
 
 /* ------------------------------------------------------------------------ */
-/* Coupling network: conv(1->c1) LReLU conv(c1->c2) LReLU conv(c2->2),       */
-/* periodic 3^d cross-correlation out[n][o] = b[o] + sum_{i,t} W[o][i][t] in[nbr(n,t)][i]. */
+/* Coupling network (Sec. 1: s, t are the output of a convolutional network */
+/* of the fixed sites; Sec. 3: hidden_sizes, kernel_size, inC = 1, outC = 2): */
+/* conv 0 .. conv n_hidden, periodic K^nd cross-correlation                  */
+/* out[n][o] = b[o] + sum_{i,t} W[o][i][t] in[nbr(n,t)][i].                  */
 /* ------------------------------------------------------------------------ */
 static double bf16_round(double x) {
     /* Round to the nearest value with 8 significant bits, ties to even. */
@@ -178,29 +181,36 @@ static double bf16_round(double x) {
     return ldexp(r, e - 8);
 }
 
+static double lrelu(double v, double a) { return v > 0.0 ? v : a * v; }
+
+static int n_taps(const gfo_shape* sh) { return (int)ipow(sh->ksize, sh->nd); }
+/* input / output channels of convolution j (0 .. n_hidden) */
+static int conv_cin(const gfo_shape* sh, int j) { return j == 0 ? 1 : sh->hidden[j - 1]; }
+static int conv_cout(const gfo_shape* sh, int j) { return j == sh->n_hidden ? 2 : sh->hidden[j]; }
+
+/* Canonical per-layer block: for j = 0..n_hidden, W_j[cout][cin][T] then b_j[cout]. */
 typedef struct {
-    const double *W1, *b1, *W2, *b2, *W3, *b3;
+    const double* W[GFO_MAX_HIDDEN + 1];
+    const double* b[GFO_MAX_HIDDEN + 1];
 } layer_w;
 
 static int64_t layer_size(const gfo_shape* sh) {
-    int64_t T = ipow(3, sh->nd);
-    return sh->c1 * T + sh->c1 + (int64_t)sh->c2 * sh->c1 * T + sh->c2 + 2 * sh->c2 * T + 2;
+    int64_t T = n_taps(sh), n = 0;
+    for (int j = 0; j <= sh->n_hidden; ++j)
+        n += (int64_t)conv_cout(sh, j) * conv_cin(sh, j) * T + conv_cout(sh, j);
+    return n;
 }
 
 static layer_w layer_ptrs(const gfo_shape* sh, const double* w, int layer) {
-    int64_t T = ipow(3, sh->nd);
+    int64_t T = n_taps(sh);
     const double* p = w + layer * layer_size(sh);
     layer_w lw;
-    lw.W1 = p; p += sh->c1 * T;
-    lw.b1 = p; p += sh->c1;
-    lw.W2 = p; p += (int64_t)sh->c2 * sh->c1 * T;
-    lw.b2 = p; p += sh->c2;
-    lw.W3 = p; p += 2 * sh->c2 * T;
-    lw.b3 = p;
+    for (int j = 0; j <= sh->n_hidden; ++j) {
+        lw.W[j] = p; p += (int64_t)conv_cout(sh, j) * conv_cin(sh, j) * T;
+        lw.b[j] = p; p += conv_cout(sh, j);
+    }
     return lw;
 }
-
-static double lrelu(double v, double a) { return v > 0.0 ? v : a * v; }
 
 /* Periodic cross-correlation: in [V][Cin] -> out [V][Cout], W [Cout][Cin][T].
  * f32acc: the sum is carried in FP32 (GFO_F32_ACC), else in FP64. */
@@ -234,29 +244,34 @@ static void conv(int64_t V, int T, const int64_t* nbr, int Cin, int Cout,
     free(Wr);
 }
 
-/* Network intermediates of one layer on one configuration. */
-typedef struct { double *yin, *h1pre, *h1, *h2pre, *h2, *spre, *s, *t; } net_buf;
+/* Network intermediates of one layer on one configuration: for hidden
+ * convolution j, pre[j] = its output before the activation, post[j] = after. */
+typedef struct {
+    double *yin, *spre, *s, *t;
+    double *pre[GFO_MAX_HIDDEN], *post[GFO_MAX_HIDDEN];
+} net_buf;
 
 static net_buf net_alloc(const gfo_shape* sh, int64_t V) {
     net_buf nb;
     nb.yin = (double*)malloc(sizeof(double) * V);
-    nb.h1pre = (double*)malloc(sizeof(double) * V * sh->c1);
-    nb.h1 = (double*)malloc(sizeof(double) * V * sh->c1);
-    nb.h2pre = (double*)malloc(sizeof(double) * V * sh->c2);
-    nb.h2 = (double*)malloc(sizeof(double) * V * sh->c2);
+    for (int j = 0; j < sh->n_hidden; ++j) {
+        nb.pre[j] = (double*)malloc(sizeof(double) * V * sh->hidden[j]);
+        nb.post[j] = (double*)malloc(sizeof(double) * V * sh->hidden[j]);
+    }
     nb.spre = (double*)malloc(sizeof(double) * V * 2);
     nb.s = (double*)malloc(sizeof(double) * V);
     nb.t = (double*)malloc(sizeof(double) * V);
     return nb;
 }
-static void net_free(net_buf* nb) {
-    free(nb->yin); free(nb->h1pre); free(nb->h1); free(nb->h2pre); free(nb->h2);
+static void net_free(const gfo_shape* sh, net_buf* nb) {
+    free(nb->yin);
+    for (int j = 0; j < sh->n_hidden; ++j) { free(nb->pre[j]); free(nb->post[j]); }
     free(nb->spre); free(nb->s); free(nb->t);
 }
 
 /* s, t = net(y) where y is the layer input with its updated (active) sites zeroed.
- * Readings: LeakyReLU after conv1 and conv2, none after conv3; tanh on channel 0
- * (s) only when use_final_tanh; channel 1 is t. */
+ * Readings: LeakyReLU after every hidden convolution, none after the head;
+ * tanh on channel 0 (s) only when use_final_tanh; channel 1 is t. */
 static void net_forward(const gfo_shape* sh, layer_w lw, int32_t bf16, int64_t V, int T,
                         const int64_t* nbr, const double* y, net_buf* nb) {
     if (bf16 & GFO_BF16_X1) {          /* the BF16 variant's conv1 reads the field in bf16 */
@@ -264,17 +279,22 @@ static void net_forward(const gfo_shape* sh, layer_w lw, int32_t bf16, int64_t V
         y = nb->yin;
     }
     const int f32acc = (bf16 & GFO_F32_ACC) != 0;
-    conv(V, T, nbr, 1, sh->c1, lw.W1, lw.b1, bf16 & GFO_BF16_W1, f32acc, y, nb->h1pre);
-    for (int64_t k = 0; k < V * sh->c1; ++k) {
-        nb->h1[k] = lrelu(nb->h1pre[k], sh->leaky_slope);
-        if (bf16 & GFO_BF16_H1) nb->h1[k] = bf16_round(nb->h1[k]);
+    const double* in = y;
+    for (int j = 0; j <= sh->n_hidden; ++j) {
+        const int cin = conv_cin(sh, j), cout = conv_cout(sh, j);
+        const int head = j == sh->n_hidden;
+        const int round_w = head ? (bf16 & GFO_BF16_W3)
+                          : j == 0 ? (bf16 & GFO_BF16_W1) : (bf16 & GFO_BF16_W2);
+        double* out = head ? nb->spre : nb->pre[j];
+        conv(V, T, nbr, cin, cout, lw.W[j], lw.b[j], round_w, f32acc, in, out);
+        if (head) break;
+        const int round_h = j == 0 ? (bf16 & GFO_BF16_H1) : (bf16 & GFO_BF16_H2);
+        for (int64_t k = 0; k < V * cout; ++k) {
+            nb->post[j][k] = lrelu(nb->pre[j][k], sh->leaky_slope);
+            if (round_h) nb->post[j][k] = bf16_round(nb->post[j][k]);
+        }
+        in = nb->post[j];
     }
-    conv(V, T, nbr, sh->c1, sh->c2, lw.W2, lw.b2, bf16 & GFO_BF16_W2, f32acc, nb->h1, nb->h2pre);
-    for (int64_t k = 0; k < V * sh->c2; ++k) {
-        nb->h2[k] = lrelu(nb->h2pre[k], sh->leaky_slope);
-        if (bf16 & GFO_BF16_H2) nb->h2[k] = bf16_round(nb->h2[k]);
-    }
-    conv(V, T, nbr, sh->c2, 2, lw.W3, lw.b3, bf16 & GFO_BF16_W3, f32acc, nb->h2, nb->spre);
     for (int64_t n = 0; n < V; ++n) {
         nb->s[n] = sh->use_final_tanh ? tanh(nb->spre[2 * n]) : nb->spre[2 * n];
         nb->t[n] = nb->spre[2 * n + 1];
@@ -282,20 +302,23 @@ static void net_forward(const gfo_shape* sh, layer_w lw, int32_t bf16, int64_t V
 }
 
 static int shape_ok(const gfo_shape* sh) {
-    return sh && (sh->nd == 2 || sh->nd == 3) && sh->L >= 1 && sh->n_layers >= 0 &&
-           sh->c1 >= 1 && sh->c2 >= 1;
+    if (!sh || (sh->nd != 2 && sh->nd != 3) || sh->L < 1 || sh->n_layers < 0) return 0;
+    if (sh->n_hidden < 0 || sh->n_hidden > GFO_MAX_HIDDEN) return 0;
+    if (sh->ksize < 1 || (sh->ksize & 1) == 0) return 0;
+    for (int j = 0; j < sh->n_hidden; ++j) if (sh->hidden[j] < 1) return 0;
+    return 1;
 }
 
 int gfo_coupling_net(const gfo_shape* sh, const double* w, int32_t layer, int32_t bf16_mask,
                      const double* y, double* s, double* t) {
     if (!shape_ok(sh) || layer < 0 || layer >= sh->n_layers) return -1;
-    int64_t V = ipow(sh->L, sh->nd); int T = (int)ipow(3, sh->nd);
-    int64_t* nbr = make_nbr(sh->nd, sh->L);
+    int64_t V = ipow(sh->L, sh->nd); int T = n_taps(sh);
+    int64_t* nbr = make_nbr(sh->nd, sh->L, sh->ksize);
     net_buf nb = net_alloc(sh, V);
     net_forward(sh, layer_ptrs(sh, w, layer), bf16_mask, V, T, nbr, y, &nb);
     memcpy(s, nb.s, sizeof(double) * V);
     memcpy(t, nb.t, sizeof(double) * V);
-    net_free(&nb); free(nbr);
+    net_free(sh, &nb); free(nbr);
     return 0;
 }
 
@@ -329,13 +352,28 @@ int gfo_flow_sample(const gfo_shape* sh, const double* w, int32_t bf16_mask, dou
                     double* z_out, double* phi_out, double* logq_out, double* S_out,
                     double* logw_out, int32_t nthreads) {
     if (!shape_ok(sh) || B < 0 || !phi_out || !logq_out) return -1;
-    int64_t V = ipow(sh->L, sh->nd); int T = (int)ipow(3, sh->nd);
-    int64_t* nbr = make_nbr(sh->nd, sh->L);
+    int64_t V = ipow(sh->L, sh->nd); int T = n_taps(sh);
+    int64_t* nbr = make_nbr(sh->nd, sh->L, sh->ksize);
     int* par = (int*)malloc(sizeof(int) * V);
     for (int64_t n = 0; n < V; ++n) par[n] = parity(sh->nd, sh->L, n);
     double* zall = (double*)malloc(sizeof(double) * (B > 0 ? B : 1) * V);
     if (z_in) memcpy(zall, z_in, sizeof(double) * B * V);
-    else gfo_prior(V, B, seed, counter0, (bf16_mask & GFO_F32_IO) ? 1 : 0, zall);
+    else {
+        gfo_prior(V, B, seed, counter0, 0, zall);
+        if (bf16_mask & GFO_Z_JITTER) {         /* tolerance experiment only (see header) */
+            for (int64_t b = 0; b < B; ++b)
+                for (int64_t n = 0; n < V; ++n) {
+                    uint64_t key[2] = {seed, 1};
+                    uint64_t ctr[4] = {counter0 + (uint64_t)b, (uint64_t)n, 0, TAG_Z_JITTER};
+                    uint64_t w[4];
+                    gfo_philox4x64_10(key, ctr, w);
+                    const double e = (2.0 * u53(w[0]) - 1.0) * 0x1p-20;
+                    zall[b * V + n] *= 1.0 + e;
+                }
+        }
+        if (bf16_mask & GFO_F32_IO)
+            for (int64_t k = 0; k < B * V; ++k) zall[k] = (double)(float)zall[k];
+    }
     if (nthreads < 1) nthreads = 1;
 #pragma omp parallel num_threads(nthreads)
     {
@@ -353,7 +391,7 @@ int gfo_flow_sample(const gfo_shape* sh, const double* w, int32_t bf16_mask, dou
             if (S_out) S_out[b] = S;
             if (logw_out) logw_out[b] = -S - logq_out[b]; /* log p - log q, p = exp(-S) unnormalised */
         }
-        net_free(&nb); free(y);
+        net_free(sh, &nb); free(y);
     }
     if (z_out) memcpy(z_out, zall, sizeof(double) * B * V);
     free(zall); free(par); free(nbr);
@@ -363,8 +401,8 @@ int gfo_flow_sample(const gfo_shape* sh, const double* w, int32_t bf16_mask, dou
 int gfo_flow_logq(const gfo_shape* sh, const double* w, int32_t bf16_mask, int64_t B,
                   const double* phi, double* z_out, double* logq_out, int32_t nthreads) {
     if (!shape_ok(sh) || B < 0 || !phi || !logq_out) return -1;
-    int64_t V = ipow(sh->L, sh->nd); int T = (int)ipow(3, sh->nd);
-    int64_t* nbr = make_nbr(sh->nd, sh->L);
+    int64_t V = ipow(sh->L, sh->nd); int T = n_taps(sh);
+    int64_t* nbr = make_nbr(sh->nd, sh->L, sh->ksize);
     int* par = (int*)malloc(sizeof(int) * V);
     for (int64_t n = 0; n < V; ++n) par[n] = parity(sh->nd, sh->L, n);
     if (nthreads < 1) nthreads = 1;
@@ -394,7 +432,7 @@ int gfo_flow_logq(const gfo_shape* sh, const double* w, int32_t bf16_mask, int64
             logq_out[b] = logr - logdet;
             if (z_out) memcpy(z_out + b * V, x, sizeof(double) * V);
         }
-        net_free(&nb); free(y); free(x);
+        net_free(sh, &nb); free(y); free(x);
     }
     free(par); free(nbr);
     return 0;
@@ -549,9 +587,9 @@ static void conv_backward(int64_t V, int T, const int64_t* nbr, int Cin, int Cou
 int gfo_flow_loss_grad(const gfo_shape* sh, const double* w, double m2, double lam, int64_t B,
                        const double* z, double* loss_out, double* grad_out, int32_t nthreads) {
     if (!shape_ok(sh) || B <= 0 || !z || !loss_out || !grad_out) return -1;
-    int64_t V = ipow(sh->L, sh->nd); int T = (int)ipow(3, sh->nd);
+    int64_t V = ipow(sh->L, sh->nd); int T = n_taps(sh);
     int64_t P = layer_size(sh) * sh->n_layers;
-    int64_t* nbr = make_nbr(sh->nd, sh->L);
+    int64_t* nbr = make_nbr(sh->nd, sh->L, sh->ksize);
     int* par = (int*)malloc(sizeof(int) * V);
     for (int64_t n = 0; n < V; ++n) par[n] = parity(sh->nd, sh->L, n);
     double* loss_b = (double*)malloc(sizeof(double) * B);
@@ -570,8 +608,10 @@ int gfo_flow_loss_grad(const gfo_shape* sh, const double* w, double m2, double l
         double* gx = (double*)malloc(sizeof(double) * V);
         double* gy = (double*)malloc(sizeof(double) * V);
         double* g3 = (double*)malloc(sizeof(double) * V * 2);
-        double* gh2 = (double*)malloc(sizeof(double) * V * sh->c2);
-        double* gh1 = (double*)malloc(sizeof(double) * V * sh->c1);
+        int cmax = 1;
+        for (int j = 0; j < sh->n_hidden; ++j) if (sh->hidden[j] > cmax) cmax = sh->hidden[j];
+        double* gA = (double*)malloc(sizeof(double) * V * cmax);   /* adjoint of a hidden activation */
+        double* gB = (double*)malloc(sizeof(double) * V * cmax);
 #pragma omp for schedule(dynamic, 1)
         for (int64_t b = 0; b < B; ++b) {
             /* forward, keeping each layer input x_l */
@@ -598,13 +638,16 @@ int gfo_flow_loss_grad(const gfo_shape* sh, const double* w, double m2, double l
             for (int l = sh->n_layers - 1; l >= 0; --l) {
                 const double* xi = xs + (int64_t)l * V;
                 layer_w lw = layer_ptrs(sh, w, l);
-                double* Gl = G + (int64_t)l * layer_size(sh);
-                double* gW1 = Gl;
-                double* gb1 = gW1 + sh->c1 * T;
-                double* gW2 = gb1 + sh->c1;
-                double* gb2 = gW2 + (int64_t)sh->c2 * sh->c1 * T;
-                double* gW3 = gb2 + sh->c2;
-                double* gb3 = gW3 + 2 * sh->c2 * T;
+                /* gradient blocks of this layer, in the canonical layout */
+                double* gW[GFO_MAX_HIDDEN + 1];
+                double* gb[GFO_MAX_HIDDEN + 1];
+                {
+                    double* q = G + (int64_t)l * layer_size(sh);
+                    for (int j = 0; j <= sh->n_hidden; ++j) {
+                        gW[j] = q; q += (int64_t)conv_cout(sh, j) * conv_cin(sh, j) * T;
+                        gb[j] = q; q += conv_cout(sh, j);
+                    }
+                }
                 int frozen = l & 1;
                 for (int64_t n = 0; n < V; ++n) y[n] = (par[n] == frozen) ? xi[n] : 0.0;
                 net_forward(sh, lw, 0, V, T, nbr, y, &nb);
@@ -620,21 +663,25 @@ int gfo_flow_loss_grad(const gfo_shape* sh, const double* w, double m2, double l
                         g3[2 * n] = 0.0; g3[2 * n + 1] = 0.0;
                     }
                 }
-                memset(gh2, 0, sizeof(double) * V * sh->c2);
-                conv_backward(V, T, nbr, sh->c2, 2, lw.W3, nb.h2, g3, gh2, gW3, gb3);
-                for (int64_t k = 0; k < V * sh->c2; ++k)
-                    gh2[k] *= (nb.h2pre[k] > 0.0) ? 1.0 : sh->leaky_slope;
-                memset(gh1, 0, sizeof(double) * V * sh->c1);
-                conv_backward(V, T, nbr, sh->c1, sh->c2, lw.W2, nb.h1, gh2, gh1, gW2, gb2);
-                for (int64_t k = 0; k < V * sh->c1; ++k)
-                    gh1[k] *= (nb.h1pre[k] > 0.0) ? 1.0 : sh->leaky_slope;
-                memset(gy, 0, sizeof(double) * V);
-                conv_backward(V, T, nbr, 1, sh->c1, lw.W1, y, gh1, gy, gW1, gb1);
+                /* back through the convolutions, head first: gout is the adjoint of
+                 * convolution j's output (pre-activation), gin that of its input */
+                const double* gout = g3;
+                for (int j = sh->n_hidden; j >= 0; --j) {
+                    const int cin = conv_cin(sh, j), cout = conv_cout(sh, j);
+                    const double* in = j == 0 ? y : nb.post[j - 1];
+                    double* gin = j == 0 ? gy : (gout == gA ? gB : gA);
+                    memset(gin, 0, sizeof(double) * V * cin);
+                    conv_backward(V, T, nbr, cin, cout, lw.W[j], in, gout, gin, gW[j], gb[j]);
+                    if (j > 0)               /* through the LeakyReLU of hidden j-1 */
+                        for (int64_t k = 0; k < V * cin; ++k)
+                            gin[k] *= (nb.pre[j - 1][k] > 0.0) ? 1.0 : sh->leaky_slope;
+                    gout = gin;
+                }
                 for (int64_t n = 0; n < V; ++n)
                     if (par[n] == frozen) gx[n] += gy[n];          /* y = x on fixed sites only */
             }
         }
-        net_free(&nb); free(xs); free(y); free(gx); free(gy); free(g3); free(gh2); free(gh1);
+        net_free(sh, &nb); free(xs); free(y); free(gx); free(gy); free(g3); free(gA); free(gB);
     }
     double loss = 0.0;
     for (int64_t b = 0; b < B; ++b) loss += loss_b[b];

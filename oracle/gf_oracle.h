@@ -45,22 +45,33 @@
 extern "C" {
 #endif
 
-/* Flow shape.  k = 3 taps per axis, circular padding 1. */
+/* Flow shape (Sec. 3, model parameters n_layers, hidden_sizes, kernel_size,
+ * inC = 1, outC = 2, use_final_tanh).  Each coupling layer's net is the chain
+ * conv(1 -> hidden[0]) LReLU ... conv(hidden[n_hidden-2] -> hidden[n_hidden-1])
+ * LReLU conv(hidden[n_hidden-1] -> 2), every convolution periodic with
+ * ksize^nd taps (ksize odd, circular padding (ksize-1)/2).  n_hidden = 0 is a
+ * single conv(1 -> 2). */
+#define GFO_MAX_HIDDEN 8
 typedef struct {
     int32_t nd;            /* 2 or 3 */
     int32_t L;             /* sites per axis */
     int32_t n_layers;
-    int32_t c1, c2;        /* hidden widths */
+    int32_t n_hidden;      /* number of hidden convolutions, 0..GFO_MAX_HIDDEN */
+    int32_t hidden[GFO_MAX_HIDDEN];   /* their output widths */
+    int32_t ksize;         /* taps per axis, odd */
     int32_t use_final_tanh;
-    double  leaky_slope;   /* LeakyReLU slope after conv1 and conv2 */
+    double  leaky_slope;   /* LeakyReLU slope after every hidden convolution */
 } gfo_shape;
 
-/* Rounding points for the BF16-emulation mode (bit flags, 0 = pure FP64). */
+/* Rounding points for the BF16-emulation mode (bit flags, 0 = pure FP64).
+ * "conv1" is the first convolution, "conv3" the head (the last), "conv2"
+ * every convolution in between; h1 is the first hidden activation, h2 every
+ * later one (the names of the two-hidden-layer net). */
 enum {
     GFO_BF16_H1 = 1,   /* round h1 (after LeakyReLU) to bf16 */
     GFO_BF16_W2 = 2,   /* round conv2 weights to bf16 */
     GFO_BF16_H2 = 4,   /* round h2 (after LeakyReLU) to bf16 */
-    GFO_BF16_W3 = 8,   /* round conv3 weights to bf16 */
+    GFO_BF16_W3 = 8,   /* round conv3 (head) weights to bf16 */
     GFO_BF16_W1 = 16,  /* round conv1 weights to bf16 */
     GFO_F32_IO  = 32,  /* round the prior sample z to fp32 (the paper's Float32 prior) */
     GFO_BF16_X1 = 64,  /* round conv1's input (the masked field) to bf16 */
@@ -70,7 +81,13 @@ enum {
      * first, each product rounded to FP32 before it is added) and the field
      * is rounded to FP32 after every affine update.  Sums over the lattice
      * (log-det, z^2, action) stay FP64. */
-    GFO_F32_ACC = 128
+    GFO_F32_ACC = 128,
+    /* With GFO_F32_ACC, for the same experiment: each prior sample drawn in
+     * the sampler (not a given z) is multiplied by (1 + e), e uniform in
+     * +-2^-20 (the relative bound to which an FP32 Box-Muller prior is tested
+     * against this oracle's), from philox(key=(seed, 1), ctr=(counter0+b, n,
+     * 0, 5)) word 0, before the FP32 rounding. */
+    GFO_Z_JITTER = 256
 };
 
 typedef struct {

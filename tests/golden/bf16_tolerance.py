@@ -8,11 +8,16 @@ level, and a value that sits within that difference of a rounding boundary
 rounds the other way on one side.  Such a flip moves s and t of the nearby
 updated sites by part of a bf16 ulp, and the later coupling layers carry it on.
 
-This script measures that drift with the oracle only: it runs the
+The kernel's prior sample also differs from the oracle's at the FP32 level:
+it evaluates Box-Muller in FP32 (tested against the oracle to 1e-6 relative),
+the oracle in FP64 before rounding to FP32.
+
+This script measures the drift with the oracle only: it runs the
 BF16-emulation mode twice on the same inputs, once with FP64 sums (the mode
-the GPU tests compare against) and once with every convolution summed in FP32
-and the field kept in FP32 (GFO_F32_ACC, a model of an FP32-accumulating
-device).  The difference between the two runs is the size of error that
+the GPU tests compare against) and once as a model of an FP32 device: every
+convolution summed in FP32, the field kept in FP32 (GFO_F32_ACC), and each
+prior sample perturbed by a relative amount uniform in +-2^-20, the prior's
+tested bound (GFO_Z_JITTER).  The difference between the two runs is the size of error that
 FP32-level differences produce through the bf16 roundings; the GPU tolerance
 is its maximum over the sample times a stated margin, per number of coupling
 layers.  It also reports the BF16-emulated results' error against the pure
@@ -67,7 +72,8 @@ def drift(n_layers: int, B: int, seed: int = SEED, counter0: int = 0, nthreads=N
     m2, lam = -6.0, 5.0
     kw = dict(seed=seed, counter0=counter0, nthreads=nthreads)
     ref = oracle.flow_sample(shape, w, m2, lam, B, bf16_mask=oracle.BF16_MODE, **kw)
-    f32 = oracle.flow_sample(shape, w, m2, lam, B, bf16_mask=oracle.BF16_MODE | oracle.F32_ACC, **kw)
+    f32 = oracle.flow_sample(shape, w, m2, lam, B,
+                             bf16_mask=oracle.BF16_MODE | oracle.F32_ACC | oracle.Z_JITTER, **kw)
     f64 = oracle.flow_sample(shape, w, m2, lam, B, bf16_mask=oracle.F32_IO, **kw)
     out = {"n_layers": n_layers, "configurations": B,
            "fp32_model_vs_emulated": {"phi": stats(site_err(f32["phi"], ref["phi"]))},
