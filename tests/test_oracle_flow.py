@@ -24,11 +24,14 @@ def lrelu(v, a):
 
 
 def scipy_net(shape, w, layer, y, round_fn=None, flags=0):
-    """s, t of one coupling network with scipy's periodic correlate."""
+    """s, t of one coupling network (any hidden_sizes, odd kernel size) with
+    scipy's periodic correlate.  flags: the oracle's bf16 rounding points (1 h1,
+    2 middle weights, 4 later hidden activations, 8 head weights, 16 first
+    weights, 64 the network input)."""
     d = gi.split_layer(shape, w, layer)
-    nd, L = shape.nd, shape.L
+    nd, L, k = shape.nd, shape.L, shape.ksize
     grid = [L] * nd
-    ker = lambda W: W.reshape(W.shape[0], W.shape[1], *([3] * nd))
+    ker = lambda W: W.reshape(W.shape[0], W.shape[1], *([k] * nd))
     rw = (lambda a: a) if round_fn is None else round_fn
 
     def conv(inp, W, b):
@@ -41,20 +44,22 @@ def scipy_net(shape, w, layer, y, round_fn=None, flags=0):
             out[o] = acc
         return out
 
-    W1 = rw(d["W1"]) if flags & 16 else d["W1"]
     if flags & 64:
         y = rw(y)
-    W2 = rw(d["W2"]) if flags & 2 else d["W2"]
-    W3 = rw(d["W3"]) if flags & 8 else d["W3"]
-    h1 = lrelu(conv(y.reshape([1] + grid), W1, d["b1"]), shape.leaky_slope)
-    if flags & 1:
-        h1 = rw(h1)
-    h2 = lrelu(conv(h1, W2, d["b2"]), shape.leaky_slope)
-    if flags & 4:
-        h2 = rw(h2)
-    st = conv(h2, W3, d["b3"])
-    s = np.tanh(st[0]) if shape.use_final_tanh else st[0]
-    return s.ravel(), st[1].ravel()
+    h = y.reshape([1] + grid)
+    nh = len(shape.hidden)
+    for j in range(nh + 1):
+        W = d[f"W{j + 1}"]
+        wflag = 8 if j == nh else (16 if j == 0 else 2)
+        if flags & wflag:
+            W = rw(W)
+        h = conv(h, W, d[f"b{j + 1}"])
+        if j < nh:
+            h = lrelu(h, shape.leaky_slope)
+            if flags & (1 if j == 0 else 4):
+                h = rw(h)
+    s = np.tanh(h[0]) if shape.use_final_tanh else h[0]
+    return s.ravel(), h[1].ravel()
 
 
 def parity(nd, L):
@@ -78,9 +83,17 @@ def numpy_flow(shape, w, z):
 SHAPES = [gi.FlowShape(2, 4, 3, 4, 5), gi.FlowShape(2, 3, 2, 3, 2),
           gi.FlowShape(3, 3, 2, 2, 3), gi.FlowShape(2, 5, 4, 8, 8, use_final_tanh=False),
           gi.FlowShape(3, 2, 3, 4, 4)]
+# the model section's other network shapes: hidden_sizes lists of other
+# lengths (three hidden layers, one, none) and kernel_size 5 / 7
+VARIANTS = [gi.FlowShape(2, 6, 3, hidden_sizes=(4, 3, 5), ksize=5),
+            gi.FlowShape(2, 5, 2, hidden_sizes=(3, 3, 3), ksize=3),
+            gi.FlowShape(3, 5, 2, hidden_sizes=(3,), ksize=5),
+            gi.FlowShape(2, 4, 2, hidden_sizes=(), ksize=3),
+            gi.FlowShape(2, 8, 2, hidden_sizes=(2, 4), ksize=7, use_final_tanh=False),
+            gi.FlowShape(3, 4, 2, hidden_sizes=(2, 2, 2, 2), ksize=3)]
 
 
-@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("shape", SHAPES + VARIANTS)
 def test_coupling_net_vs_scipy(orc, shape):
     w = gi.init_weights(shape, seed=3)
     y = gi.random_field(shape.nd, shape.L, 1, seed=4)[0]
@@ -89,6 +102,17 @@ def test_coupling_net_vs_scipy(orc, shape):
         rs, rt = scipy_net(shape, w, layer, y)
         assert np.allclose(s, rs, rtol=1e-12, atol=1e-13)
         assert np.allclose(t, rt, rtol=1e-12, atol=1e-13)
+
+
+def test_variant_weight_layout_and_default_net_unchanged():
+    """hidden_sizes (c1, c2) with kernel 3 is the original layout; a variant's
+    parameter count is the sum over its convolutions."""
+    a, b = gi.FlowShape(3, 4, 2, 8, 16), gi.FlowShape(3, 4, 2, hidden_sizes=(8, 16), ksize=3)
+    assert np.array_equal(gi.init_weights(a, seed=1), gi.init_weights(b, seed=1))
+    v = gi.FlowShape(2, 4, 3, hidden_sizes=(4, 3, 5), ksize=5)
+    T = 25
+    assert v.layer_params() == (4 * T + 4) + (3 * 4 * T + 3) + (5 * 3 * T + 5) + (2 * 5 * T + 2)
+    assert [n for n, _ in v.layer_blocks()] == ["W1", "b1", "W2", "b2", "W3", "b3", "W4", "b4"]
 
 
 def test_bf16_rounding_points_vs_torch(orc):
@@ -112,7 +136,7 @@ def test_bf16_rounding_points_vs_torch(orc):
     assert not np.allclose(s0, s1, rtol=1e-6)
 
 
-@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("shape", SHAPES + VARIANTS)
 def test_flow_vs_bruteforce_composition(orc, shape):
     w = gi.init_weights(shape, seed=5)
     B = 3
@@ -130,7 +154,9 @@ def test_flow_vs_bruteforce_composition(orc, shape):
 
 
 @pytest.mark.parametrize("shape", [gi.FlowShape(2, 2, 4, 4, 4), gi.FlowShape(2, 3, 3, 4, 4),
-                                   gi.FlowShape(3, 2, 4, 3, 3), gi.FlowShape(3, 3, 2, 2, 2)])
+                                   gi.FlowShape(3, 2, 4, 3, 3), gi.FlowShape(3, 3, 2, 2, 2),
+                                   gi.FlowShape(2, 3, 3, hidden_sizes=(3, 2, 3), ksize=5),
+                                   gi.FlowShape(3, 2, 2, hidden_sizes=(2,), ksize=5)])
 def test_logdet_vs_bruteforce_jacobian(orc, shape):
     """log|det dphi/dz| by central differences + LU must equal log r(z) - log q."""
     w = gi.init_weights(shape, seed=2)
@@ -152,7 +178,7 @@ def test_logdet_vs_bruteforce_jacobian(orc, shape):
     assert logabsdet == pytest.approx(logdet, rel=1e-7, abs=1e-7)
 
 
-@pytest.mark.parametrize("shape", SHAPES + [gi.WORKLOADS["c1"]["shape"]])
+@pytest.mark.parametrize("shape", SHAPES + VARIANTS + [gi.WORKLOADS["c1"]["shape"]])
 def test_invertibility(orc, shape):
     w = gi.init_weights(shape, seed=0)
     o = orc.flow_sample(shape, w, -4.0, 8.0, 5, seed=9, counter0=3)

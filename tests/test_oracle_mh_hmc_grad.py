@@ -167,7 +167,10 @@ def test_hmc_rejection_restores_field(orc):
 
 
 GSHAPES = [gi.FlowShape(2, 4, 4, 4, 4), gi.FlowShape(3, 2, 3, 3, 2),
-           gi.FlowShape(2, 3, 2, 3, 3, use_final_tanh=False)]
+           gi.FlowShape(2, 3, 2, 3, 3, use_final_tanh=False),
+           gi.FlowShape(2, 4, 2, hidden_sizes=(3, 2, 3), ksize=5),
+           gi.FlowShape(2, 3, 3, hidden_sizes=(), ksize=3),
+           gi.FlowShape(3, 3, 2, hidden_sizes=(2,), ksize=5)]
 
 
 @pytest.mark.parametrize("shape", GSHAPES)
@@ -181,7 +184,7 @@ def test_loss_gradient_finite_differences(orc, shape):
     rng = np.random.default_rng(0)
     idx = rng.choice(w.size, 20, replace=False)
     idx[:6] = [0, shape.layer_params() - 1, shape.layer_params() - 2,
-               shape.c1 * shape.taps, w.size - 1, w.size // 2]
+               shape.conv_channels()[0][1] * shape.taps, w.size - 1, w.size // 2]
     eps = 1e-6
     for i in idx:
         wp, wm = w.copy(), w.copy()
