@@ -46,14 +46,41 @@ typedef enum {
                                      across the block) (3D, L=16, C=32 only)     */
 } gf_precision;
 
-/* Flow shape (paper Sec. 3, model parameters: n_layers, hidden_sizes,
- * kernel_size, inC=1, outC=2, use_final_tanh, use_bn=false).
- * Supported: nd in {2,3}; c_hidden1 == c_hidden2 in {8,16,32}; ksize == 3;
- * 2 <= L with L^nd <= 65536 and L even (checkerboard is a bipartition). */
+/* Flow shape (paper Sec. 3, model parameters: n_layers, hidden_sizes =
+ * [c_hidden1, c_hidden2], kernel_size, inC=1, outC=2, use_final_tanh,
+ * use_bn=false).  The same network as gf_flow_shape_ex with n_hidden = 2 (see
+ * there for what is supported); L even (the checkerboard is a bipartition). */
 typedef struct {
     int32_t nd, L, n_layers, c_hidden1, c_hidden2, ksize, use_final_tanh;
     double leaky_slope;   /* LeakyReLU slope after conv1 and conv2 */
 } gf_flow_shape;
+
+/* The general s/t network of the paper's model section (Sec. 3, model
+ * parameters hidden_sizes and kernel_size): n_hidden convolutions of widths
+ * hidden[0..n_hidden-1], each followed by LeakyReLU, then the head conv(-> 2)
+ * (channel 0 = s, tanh when use_final_tanh; channel 1 = t).  Every
+ * convolution is periodic with ksize^nd taps (ksize odd, circular padding
+ * (ksize-1)/2), taps ordered (kz,ky,kx) resp. (ky,kx), kx fastest, offset
+ * k - (ksize-1)/2.  Canonical weights per layer: for each convolution j =
+ * 0..n_hidden, W_j[c_out][c_in][T] then b_j[c_out] (c_in of the first is 1,
+ * c_out of the head 2).  n_hidden = 2, ksize = 3 is the layout of
+ * gf_flow_shape.
+ * Supported: nd in {2,3}; L even, L^nd <= 65536; 0 <= n_hidden <=
+ * GF_MAX_HIDDEN; widths 1..256; ksize in {1,3,5,7}.  Two equal hidden widths in
+ * {8,16,32} with ksize 3 run on the slice-cached kernels (both precisions);
+ * every other network runs on a whole-lattice FP32 kernel that needs
+ * 4 (V + 2 V Cp) bytes of shared memory per block, Cp = the widest hidden
+ * layer rounded up to odd, at most 227 KB (else GF_EUNSUPPORTED); those flows
+ * support sampling and log q only (training and the unfused form return
+ * GF_EUNSUPPORTED). */
+#define GF_MAX_HIDDEN 8
+typedef struct {
+    int32_t nd, L, n_layers;
+    int32_t n_hidden;
+    int32_t hidden[GF_MAX_HIDDEN];
+    int32_t ksize, use_final_tanh;
+    double leaky_slope;   /* LeakyReLU slope after every hidden convolution */
+} gf_flow_shape_ex;
 
 /* phi^4 couplings (paper Sec. 1, action S[phi] and potential V[phi]):
  * S = sum_n [ sum_mu phi(n)(2 phi(n) - phi(n+mu) - phi(n-mu)) + m2 phi^2 + lam phi^4 ]. */
@@ -77,13 +104,18 @@ typedef struct {
 /* ---------------------------------------------------------------------- */
 
 /* Copies host FP64 weights (canonical layout, one block per layer in the
- * order the layers act on the prior sample: W1[c1][1][T] b1[c1]
+ * order the layers act on the prior sample; for gf_flow_shape: W1[c1][1][T] b1[c1]
  * W2[c2][c1][T] b2[c2] W3[2][c2][T] b3[2], T = 3^nd taps ordered
  * (kz,ky,kx) resp. (ky,kx), offset k-1; conv3 channel 0 is s, 1 is t) to the
  * device in the kernels' layouts.  Synchronises `stream` before returning.
  * *out is set only on GF_OK; release with gf_flow_destroy. */
 gf_status gf_flow_create(const gf_flow_shape* shape, const double* weights_host,
                          gf_precision prec, cudaStream_t stream, gf_flow** out);
+/* The same for the general network (any hidden_sizes list, odd kernel size;
+ * canonical weights as described at gf_flow_shape_ex).  GF_PREC_BF16CONV_FP64RED
+ * is supported only where gf_flow_create supports it. */
+gf_status gf_flow_create_ex(const gf_flow_shape_ex* shape, const double* weights_host,
+                            gf_precision prec, cudaStream_t stream, gf_flow** out);
 gf_status gf_flow_destroy(gf_flow* flow);
 /* Number of canonical parameters. */
 int64_t   gf_flow_n_params(const gf_flow* flow);

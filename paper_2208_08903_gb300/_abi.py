@@ -15,8 +15,10 @@ GF_PREC_FP32, GF_PREC_BF16CONV_FP64RED = 0, 1
 GF_OBS_MAX_L = 4096
 GF_MH_NOALLOC_MAX_N = 131072     # include/gfflow.h
 
+GF_MAX_HIDDEN = 8
+
 EXPORTED = [
-    "gf_flow_create", "gf_flow_destroy", "gf_flow_n_params", "gf_flow_set_weights_device",
+    "gf_flow_create", "gf_flow_create_ex", "gf_flow_destroy", "gf_flow_n_params", "gf_flow_set_weights_device",
     "gf_flow_get_weights_device", "gf_flow_sample", "gf_flow_logq", "gf_phi4_action",
     "gf_unfused_workspace_bytes", "gf_flow_sample_unfused",
     "gf_phi4_force", "gf_mh_chain_workspace_bytes", "gf_mh_chain", "gf_mh_chain_noalloc",
@@ -31,6 +33,12 @@ class FlowShapeC(C.Structure):
     _fields_ = [("nd", C.c_int32), ("L", C.c_int32), ("n_layers", C.c_int32),
                 ("c_hidden1", C.c_int32), ("c_hidden2", C.c_int32), ("ksize", C.c_int32),
                 ("use_final_tanh", C.c_int32), ("leaky_slope", C.c_double)]
+
+
+class FlowShapeExC(C.Structure):
+    _fields_ = [("nd", C.c_int32), ("L", C.c_int32), ("n_layers", C.c_int32),
+                ("n_hidden", C.c_int32), ("hidden", C.c_int32 * GF_MAX_HIDDEN),
+                ("ksize", C.c_int32), ("use_final_tanh", C.c_int32), ("leaky_slope", C.c_double)]
 
 
 class Phi4C(C.Structure):
@@ -70,6 +78,7 @@ def load():
     L = C.CDLL(path)
     sig = {
         "gf_flow_create": ([C.POINTER(FlowShapeC), _VP, _I32, _VP, C.POINTER(_VP)], _I32),
+        "gf_flow_create_ex": ([C.POINTER(FlowShapeExC), _VP, _I32, _VP, C.POINTER(_VP)], _I32),
         "gf_flow_destroy": ([_VP], _I32),
         "gf_flow_n_params": ([_VP], _I64),
         "gf_flow_set_weights_device": ([_VP, _VP, _VP], _I32),

@@ -49,7 +49,9 @@ class SampleResult:
 class Flow:
     """A RealNVP coupling stack resident on the current CUDA device.
 
-    shape: any object with nd, L, n_layers, c1, c2, use_final_tanh, leaky_slope.
+    shape: any object with nd, L, n_layers, use_final_tanh, leaky_slope and
+    either `hidden` (the hidden_sizes list) with `ksize`, or c1, c2 (two hidden
+    convolutions, kernel size 3).
     weights: FP64 numpy array (or CPU tensor) in canonical layout.
     precision: "fp32" or "bf16" (BF16 tensor-core convolutions, sums to FP64 accuracy).
     """
@@ -58,14 +60,19 @@ class Flow:
         lib = _abi.load()
         self.shape = shape
         self.V = shape.L ** shape.nd
-        sh = _abi.FlowShapeC(shape.nd, shape.L, shape.n_layers, shape.c1, shape.c2, 3,
-                             1 if shape.use_final_tanh else 0, float(shape.leaky_slope))
+        hidden = tuple(getattr(shape, "hidden", (shape.c1, shape.c2)))
+        if len(hidden) > _abi.GF_MAX_HIDDEN:
+            raise ValueError(f"at most {_abi.GF_MAX_HIDDEN} hidden convolutions")
+        hid = (C.c_int32 * _abi.GF_MAX_HIDDEN)(*(list(hidden) + [0] * (_abi.GF_MAX_HIDDEN - len(hidden))))
+        sh = _abi.FlowShapeExC(shape.nd, shape.L, shape.n_layers, len(hidden), hid,
+                               int(getattr(shape, "ksize", 3)), 1 if shape.use_final_tanh else 0,
+                               float(shape.leaky_slope))
         w = torch.as_tensor(weights, dtype=torch.float64).contiguous().cpu()
         prec = {"fp32": _abi.GF_PREC_FP32, "bf16": _abi.GF_PREC_BF16CONV_FP64RED}[precision]
         self.precision = precision
         h = C.c_void_p()
-        _abi.check("gf_flow_create", lib.gf_flow_create(C.byref(sh), w.data_ptr(), prec,
-                                                         _stream(), C.byref(h)))
+        _abi.check("gf_flow_create_ex", lib.gf_flow_create_ex(C.byref(sh), w.data_ptr(), prec,
+                                                               _stream(), C.byref(h)))
         self._h = h
         self._lib = lib
         self.weights_version = 0      # bumped whenever the resident weights change

@@ -199,24 +199,33 @@ using namespace gf;
 
 namespace {
 
-bool shape_valid(const gf_flow_shape* s) {
+bool shape_ex_valid(const gf_flow_shape_ex* s) {
     if (!s) return false;
     if (s->nd != 2 && s->nd != 3) return false;
-    if (s->ksize != 3) return false;
+    if (s->ksize < 1 || s->ksize > 7 || (s->ksize & 1) == 0) return false;
     if (s->L < 2 || (s->L & 1)) return false;
     int64_t V = 1;
     for (int i = 0; i < s->nd; ++i) V *= s->L;
     if (V > 65536) return false;
     if (s->n_layers < 0 || s->n_layers > 4096) return false;
-    if (s->c_hidden1 != s->c_hidden2) return false;
-    const int c = s->c_hidden1;
-    if (c != 8 && c != 16 && c != 32) return false;
+    if (s->n_hidden < 0 || s->n_hidden > GF_MAX_HIDDEN) return false;
+    for (int j = 0; j < s->n_hidden; ++j)
+        if (s->hidden[j] < 1 || s->hidden[j] > 256) return false;
     if (!(s->leaky_slope == s->leaky_slope)) return false;
     return true;
 }
 
+// The paper's example network form on the slice-cached kernels: two equal
+// hidden widths in {8, 16, 32}, 3 taps per axis.
+bool default_net(const gf_flow_shape_ex* s) {
+    if (s->n_hidden != 2 || s->ksize != 3 || s->hidden[0] != s->hidden[1]) return false;
+    const int c = s->hidden[0];
+    return c == 8 || c == 16 || c == 32;
+}
+
 void free_flow(gf_flow* f) {
     if (!f) return;
+    cudaFree(f->d_vpacked);
     cudaFree(f->d_canon);
     cudaFree(f->d_packed);
     cudaFree(f->d_sched);
@@ -243,26 +252,91 @@ const char* gf_status_string(int32_t s) {
 
 gf_status gf_flow_create(const gf_flow_shape* shape, const double* weights_host,
                          gf_precision prec, cudaStream_t stream, gf_flow** out) {
-    if (!out || !weights_host || !shape_valid(shape)) return GF_EINVAL;
+    if (!shape) return GF_EINVAL;
+    gf_flow_shape_ex ex;
+    std::memset(&ex, 0, sizeof(ex));
+    ex.nd = shape->nd;
+    ex.L = shape->L;
+    ex.n_layers = shape->n_layers;
+    ex.n_hidden = 2;
+    ex.hidden[0] = shape->c_hidden1;
+    ex.hidden[1] = shape->c_hidden2;
+    ex.ksize = shape->ksize;
+    ex.use_final_tanh = shape->use_final_tanh;
+    ex.leaky_slope = shape->leaky_slope;
+    return gf_flow_create_ex(&ex, weights_host, prec, stream, out);
+}
+
+gf_status gf_flow_create_ex(const gf_flow_shape_ex* shape, const double* weights_host,
+                            gf_precision prec, cudaStream_t stream, gf_flow** out) {
+    if (!out || !weights_host || !shape_ex_valid(shape)) return GF_EINVAL;
     if (prec != GF_PREC_FP32 && prec != GF_PREC_BF16CONV_FP64RED) return GF_EINVAL;
-    if (prec == GF_PREC_BF16CONV_FP64RED && !bf16_supported(shape)) return GF_EUNSUPPORTED;
+    const bool dflt = default_net(shape);
+    gf_flow_shape legacy;
+    std::memset(&legacy, 0, sizeof(legacy));
+    legacy.nd = shape->nd;
+    legacy.L = shape->L;
+    legacy.n_layers = shape->n_layers;
+    legacy.c_hidden1 = shape->n_hidden > 0 ? shape->hidden[0] : 0;
+    legacy.c_hidden2 = shape->n_hidden > 1 ? shape->hidden[1] : 0;
+    legacy.ksize = shape->ksize;
+    legacy.use_final_tanh = shape->use_final_tanh;
+    legacy.leaky_slope = shape->leaky_slope;
+    if (prec == GF_PREC_BF16CONV_FP64RED && (!dflt || !bf16_supported(&legacy))) return GF_EUNSUPPORTED;
+
     gf_flow* f = new gf_flow;
     std::memset(f, 0, sizeof(*f));
-    f->shape = *shape;
+    f->shape = legacy;
     f->prec = prec;
     cudaGetDevice(&f->device);
     f->V = 1;
     for (int i = 0; i < shape->nd; ++i) f->V *= shape->L;
     f->S = f->V / shape->L;
-    f->T = shape->nd == 3 ? 27 : 9;
-    f->C1 = shape->c_hidden1;
-    f->C2 = shape->c_hidden2;
+    f->K = shape->ksize;
+    f->T = 1;
+    for (int i = 0; i < shape->nd; ++i) f->T *= f->K;
+    f->n_hidden = shape->n_hidden;
+    for (int j = 0; j < shape->n_hidden; ++j) f->hidden[j] = shape->hidden[j];
+    f->variant = !dflt;
+    gf_status st;
+    if (f->variant) {
+        f->canon_stride = 0;
+        for (int j = 0; j <= f->n_hidden; ++j) {
+            const int64_t ci = j == 0 ? 1 : f->hidden[j - 1], co = j == f->n_hidden ? 2 : f->hidden[j];
+            f->canon_stride += co * ci * f->T + co;
+        }
+        f->n_params = f->canon_stride * shape->n_layers;
+        st = variant_configure(f);
+        if (st != GF_OK) { free_flow(f); return st; }
+        std::vector<float> w32((size_t)std::max<int64_t>(f->n_params, 1));
+        for (int64_t i = 0; i < f->n_params; ++i) w32[i] = (float)weights_host[i];
+        const size_t pbytes = sizeof(float) * (size_t)std::max<int64_t>(1, f->vstride * shape->n_layers);
+        if (cudaMalloc(&f->d_canon, sizeof(float) * w32.size()) != cudaSuccess ||
+            cudaMalloc(&f->d_vpacked, pbytes) != cudaSuccess) {
+            free_flow(f);
+            return GF_ENOMEM;
+        }
+        if (cudaMemcpyAsync(f->d_canon, w32.data(), sizeof(float) * w32.size(), cudaMemcpyHostToDevice,
+                            stream) != cudaSuccess ||
+            cudaMemsetAsync(f->d_vpacked, 0, pbytes, stream) != cudaSuccess) {
+            free_flow(f);
+            return GF_ECUDA;
+        }
+        st = repack_variant(f, stream);
+        if (st != GF_OK) { free_flow(f); return st; }
+        if (cudaStreamSynchronize(stream) != cudaSuccess) { free_flow(f); return GF_ECUDA; }
+        *out = f;
+        return GF_OK;
+    }
+
+    f->C1 = shape->hidden[0];
+    f->C2 = shape->hidden[1];
     f->canon_stride = (int64_t)f->C1 * f->T + f->C1 + (int64_t)f->C2 * f->C1 * f->T + f->C2 +
                       2LL * f->C2 * f->T + 2;
     f->n_params = f->canon_stride * shape->n_layers;
     f->packed_stride = packed_offsets(f->T, f->C1, f->C2).stride;
 
-    gf_status st = flow_fp32_configure(f);
+    st = flow_fp32_configure(f);
     if (st != GF_OK) { free_flow(f); return st; }
     if (prec == GF_PREC_BF16CONV_FP64RED) {
         st = bf16_configure(f);
@@ -312,6 +386,7 @@ gf_status gf_flow_set_weights_device(gf_flow* flow, const float* d_weights, cuda
     if (cudaMemcpyAsync(flow->d_canon, d_weights, sizeof(float) * flow->n_params,
                         cudaMemcpyDeviceToDevice, stream) != cudaSuccess)
         return GF_ECUDA;
+    if (flow->variant) return repack_variant(flow, stream);
     return repack_weights(flow, stream);
 }
 
@@ -331,6 +406,9 @@ gf_status gf_flow_sample(const gf_flow* flow, const gf_phi4* phi4, int64_t B,
     if (!flow || B < 0 || (B > 0 && (!d_phi_out || !d_logq_out))) return GF_EINVAL;
     if (!phi4 && (d_S_out || d_logw_out)) return GF_EINVAL;
     if (B == 0) return GF_OK;
+    if (flow->variant)
+        return launch_flow_variant(flow, false, phi4, B, seed, counter0, d_z_in, d_z_out, nullptr,
+                                   d_phi_out, d_logq_out, d_S_out, d_logw_out, stream);
     if (flow->prec == GF_PREC_BF16CONV_FP64RED)
         return launch_flow_bf16(flow, false, phi4, B, seed, counter0, d_z_in, d_z_out, nullptr,
                                 d_phi_out, d_logq_out, d_S_out, d_logw_out, stream);
@@ -342,6 +420,9 @@ gf_status gf_flow_logq(const gf_flow* flow, int64_t B, const float* d_phi_in,
                        float* d_z_out, double* d_logq_out, cudaStream_t stream) {
     if (!flow || B < 0 || (B > 0 && (!d_phi_in || !d_logq_out))) return GF_EINVAL;
     if (B == 0) return GF_OK;
+    if (flow->variant)
+        return launch_flow_variant(flow, true, nullptr, B, 0, 0, nullptr, d_z_out, d_phi_in, nullptr,
+                                   d_logq_out, nullptr, nullptr, stream);
     if (flow->prec == GF_PREC_BF16CONV_FP64RED)
         return launch_flow_bf16(flow, true, nullptr, B, 0, 0, nullptr, d_z_out, d_phi_in, nullptr,
                                 d_logq_out, nullptr, nullptr, stream);

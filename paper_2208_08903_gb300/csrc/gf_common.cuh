@@ -160,6 +160,30 @@ inline void ff_split(double d, float* hi, float* lo) {
 
 constexpr double LOG_2PI = 1.8378770664093454835606594728112;
 
+// phi^4 action (paper Sec. 1) of one configuration held in shared memory,
+// this thread's share of the sites (n = threadIdx.x, += blockDim.x), in the
+// forward-hop arrangement (equal to the two-neighbour form summed over the
+// periodic lattice): phi^2 (c2d + lam phi^2) - 2 phi sum_mu phi(n + mu),
+// c2d = 2 nd + m2, in FP32 pairs (phi^2 exact, products and sums to about
+// 2^-48).  Used by the fused coupling-stack kernels' epilogues.
+template <int ND>
+__device__ FF action_part(const float* x, int L, int V, const FF& c2d, const FF& lam) {
+    FF acc{0.f, 0.f};
+    for (int n = threadIdx.x; n < V; n += blockDim.x) {
+        const int xc = n % L, yc = (n / L) % L, zc = n / (L * L);
+        FF hop{x[n - xc + (xc + 1 == L ? 0 : xc + 1)], 0.f};
+        ff_add(hop, x[n + ((yc + 1 == L ? 0 : yc + 1) - yc) * L]);
+        if (ND == 3) ff_add(hop, x[n + ((zc + 1 == L ? 0 : zc + 1) - zc) * L * L]);
+        const float c = x[n], cp = c * c;
+        const FF qq{cp, fmaf(c, c, -cp)};
+        FF inner = ff_mul(lam, qq);
+        ff_add(inner, c2d);
+        ff_add(acc, ff_mul(qq, inner));
+        ff_add(acc, ff_mul(FF{-2.f * c, 0.f}, hop));
+    }
+    return acc;
+}
+
 // ---------------------------------------------------------------------------
 // Host helpers
 // ---------------------------------------------------------------------------

@@ -55,6 +55,19 @@ struct gf_flow {
     // BF16 tensor-core path (3D, C=32)
     void* d_bf16;           // per layer: bf16 conv2 / conv3 / conv1 (+ bias) B operands, FP32 biases
     size_t smem_bytes_bf16;
+    // General s/t network (gf_flow_create_ex with hidden_sizes other than two
+    // equal widths in {8,16,32}, or a kernel size other than 3): whole-lattice
+    // FP32 kernel of gf_flow_variant.cu
+    bool variant;
+    int n_hidden;
+    int hidden[GF_MAX_HIDDEN];
+    int K;                  // taps per axis
+    float* d_vpacked;       // per layer: conv j weights [t][cin][cop], bias [cop]
+    int64_t vstride;        // packed floats per layer
+    int32_t vwoff[GF_MAX_HIDDEN + 1], vboff[GF_MAX_HIDDEN + 1];
+    int32_t vcin[GF_MAX_HIDDEN + 1], vcout[GF_MAX_HIDDEN + 1], vcop[GF_MAX_HIDDEN + 1];
+    int Cp;                 // shared-memory row width of the hidden activations (odd)
+    int vthreads;
 };
 
 namespace gf {
@@ -72,5 +85,13 @@ gf_status launch_flow_fp32(const gf_flow* f, bool inverse, const gf_phi4* phi4, 
                            const float* phi_in, float* phi_out, double* logq_out,
                            double* S_out, double* logw_out, cudaStream_t stream);
 gf_status flow_fp32_configure(gf_flow* f);   // chooses FULL/RING, G, smem
+
+// General network (gf_flow_variant.cu)
+gf_status variant_configure(gf_flow* f);     // packed offsets, smem, threads (host only)
+gf_status repack_variant(gf_flow* f, cudaStream_t stream);
+gf_status launch_flow_variant(const gf_flow* f, bool inverse, const gf_phi4* phi4, int64_t B,
+                              uint64_t seed, uint64_t counter0, const float* z_in, float* z_out,
+                              const float* phi_in, float* phi_out, double* logq_out,
+                              double* S_out, double* logw_out, cudaStream_t stream);
 
 }  // namespace gf

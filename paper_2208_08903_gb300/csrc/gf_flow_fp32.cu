@@ -279,28 +279,6 @@ __device__ void phase_c3(const FlowArgs& a, const float* __restrict__ Wl, const 
     }
 }
 
-// phi^4 action of the configuration in shared memory (paper Sec. 1), this
-// thread's sites, in the forward-hop arrangement (equal to the two-neighbour
-// form summed over the lattice): phi^2 (c2d + lam phi^2) - 2 phi sum_mu phi(n + mu),
-// c2d = 2 nd + m2, in FP32 pairs (phi^2 exact, products and sums to about 2^-48).
-template <int ND>
-__device__ FF action_part(const float* x, int L, int V, const FF& c2d, const FF& lam) {
-    FF acc{0.f, 0.f};
-    for (int n = threadIdx.x; n < V; n += blockDim.x) {
-        const int xc = n % L, yc = (n / L) % L, zc = n / (L * L);
-        FF hop{x[n - xc + wrap(xc + 1, L)], 0.f};
-        ff_add(hop, x[n + (wrap(yc + 1, L) - yc) * L]);
-        if (ND == 3) ff_add(hop, x[n + (wrap(zc + 1, L) - zc) * L * L]);
-        const float c = x[n], cp = c * c;
-        const FF qq{cp, fmaf(c, c, -cp)};
-        FF inner = ff_mul(lam, qq);
-        ff_add(inner, c2d);
-        ff_add(acc, ff_mul(qq, inner));
-        ff_add(acc, ff_mul(FF{-2.f * c, 0.f}, hop));
-    }
-    return acc;
-}
-
 template <int ND, bool INVERSE, bool WS>
 __global__ void __launch_bounds__(kThreads) flow_fp32_kernel(const FlowArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];

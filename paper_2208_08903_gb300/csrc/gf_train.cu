@@ -903,7 +903,7 @@ using namespace gf;
 extern "C" {
 
 size_t gf_train_workspace_bytes(const gf_flow* flow, int64_t B) {
-    if (!flow || B < 0) return 0;
+    if (!flow || B < 0 || flow->variant) return 0;
     return carve(flow, B, nullptr).bytes;
 }
 
@@ -914,6 +914,7 @@ gf_status gf_flow_train_step(gf_flow* flow, const gf_phi4* phi4, int64_t B, uint
                              int64_t adam_t, void* d_workspace, size_t workspace_bytes,
                              cudaStream_t stream) {
     if (!flow || !phi4 || B <= 0 || !d_loss_out) return GF_EINVAL;
+    if (flow->variant) return GF_EUNSUPPORTED;
     if (!(lr >= 0.f)) return GF_EINVAL;
     if (lr > 0.f && (!d_adam_m || !d_adam_v || adam_t < 1)) return GF_EINVAL;
     const TrainWs w = carve(flow, B, static_cast<char*>(d_workspace));
@@ -930,6 +931,7 @@ gf_status gf_flow_forward_train(const gf_flow* flow, int64_t B, uint64_t seed, u
                                 const float* d_z_in, float* d_phi_out, double* d_logq_out, void* d_workspace,
                                 size_t workspace_bytes, cudaStream_t stream) {
     if (!flow || B <= 0 || !d_phi_out || !d_logq_out) return GF_EINVAL;
+    if (flow->variant) return GF_EUNSUPPORTED;
     const TrainWs w = carve(flow, B, static_cast<char*>(d_workspace));
     if (!d_workspace || workspace_bytes < w.bytes) return GF_EINVAL;
     if ((reinterpret_cast<uintptr_t>(d_workspace) & 255) != 0) return GF_EINVAL;
@@ -941,6 +943,7 @@ gf_status gf_flow_forward_train(const gf_flow* flow, int64_t B, uint64_t seed, u
 gf_status gf_flow_backward(const gf_flow* flow, int64_t B, const float* d_gphi, const double* d_glogq,
                            float* d_grad_out, void* d_workspace, size_t workspace_bytes, cudaStream_t stream) {
     if (!flow || B <= 0 || !d_grad_out) return GF_EINVAL;
+    if (flow->variant) return GF_EUNSUPPORTED;
     const TrainWs w = carve(flow, B, static_cast<char*>(d_workspace));
     if (!d_workspace || workspace_bytes < w.bytes) return GF_EINVAL;
     if ((reinterpret_cast<uintptr_t>(d_workspace) & 255) != 0) return GF_EINVAL;
@@ -949,7 +952,7 @@ gf_status gf_flow_backward(const gf_flow* flow, int64_t B, const float* d_gphi, 
 }
 
 size_t gf_unfused_workspace_bytes(const gf_flow* flow, int64_t B) {
-    if (!flow || B < 0) return 0;
+    if (!flow || B < 0 || flow->variant) return 0;
     return carve_plain(flow, B, nullptr).bytes;
 }
 
@@ -959,6 +962,7 @@ gf_status gf_flow_sample_unfused(const gf_flow* flow, const gf_phi4* phi4, int64
                                  size_t workspace_bytes, cudaStream_t stream) {
     if (!flow || B < 0 || (B > 0 && (!d_phi_out || !d_logq_out))) return GF_EINVAL;
     if (!phi4 && (d_S_out || d_logw_out)) return GF_EINVAL;
+    if (flow->variant) return GF_EUNSUPPORTED;
     if (B == 0) return GF_OK;
     const PlainWs w = carve_plain(flow, B, static_cast<char*>(d_workspace));
     if (!d_workspace || workspace_bytes < w.bytes) return GF_EINVAL;

@@ -43,13 +43,30 @@ def test_argument_errors_without_gpu(lib):
     bad = [
         _abi.FlowShapeC(2, 7, 2, 8, 8, 3, 1, 0.01),     # odd L
         _abi.FlowShapeC(4, 8, 2, 8, 8, 3, 1, 0.01),     # nd = 4
-        _abi.FlowShapeC(2, 8, 2, 8, 16, 3, 1, 0.01),    # c1 != c2
-        _abi.FlowShapeC(2, 8, 2, 12, 12, 3, 1, 0.01),   # width not in {8,16,32}
-        _abi.FlowShapeC(2, 8, 2, 8, 8, 5, 1, 0.01),     # ksize 5
+        _abi.FlowShapeC(2, 8, 2, 0, 16, 3, 1, 0.01),    # zero width
+        _abi.FlowShapeC(2, 8, 2, 300, 8, 3, 1, 0.01),   # width > 256
+        _abi.FlowShapeC(2, 8, 2, 8, 8, 4, 1, 0.01),     # even ksize
+        _abi.FlowShapeC(2, 8, 2, 8, 8, 9, 1, 0.01),     # ksize > 7
         _abi.FlowShapeC(3, 64, 2, 8, 8, 3, 1, 0.01),    # V > 65536
     ]
     for sh in bad:
         assert lib.gf_flow_create(C.byref(sh), w, 0, None, C.byref(h)) == _abi.GF_EINVAL
+
+    def ex(nd, L, n_layers, hidden, k, tanh=1):
+        hid = (C.c_int32 * _abi.GF_MAX_HIDDEN)(*(list(hidden) + [0] * (_abi.GF_MAX_HIDDEN - len(hidden))))
+        return _abi.FlowShapeExC(nd, L, n_layers, len(hidden), hid, k, tanh, 0.01)
+    sh9 = ex(2, 8, 2, [8] * 8, 3)
+    sh9.n_hidden = 9                                   # more than GF_MAX_HIDDEN hidden layers
+    assert lib.gf_flow_create_ex(C.byref(sh9), w, 0, None, C.byref(h)) == _abi.GF_EINVAL
+    assert lib.gf_flow_create_ex(C.byref(ex(2, 8, 2, [8, 8, 8], 6)), w, 0, None, C.byref(h)) == _abi.GF_EINVAL
+    # the general network does not fit shared memory whole (2D L=64, two hidden layers of 32)
+    big = ex(2, 64, 2, [32, 16], 5)
+    assert lib.gf_flow_create_ex(C.byref(big), w, 0, None, C.byref(h)) == _abi.GF_EUNSUPPORTED
+    # BF16 only for the slice-cached network form
+    assert lib.gf_flow_create_ex(C.byref(ex(3, 16, 2, [32, 32, 32], 3)), w, 1, None, C.byref(h)) == \
+        _abi.GF_EUNSUPPORTED
+    assert lib.gf_flow_create(C.byref(_abi.FlowShapeC(3, 16, 2, 32, 16, 3, 1, 0.01)), w, 1, None,
+                              C.byref(h)) == _abi.GF_EUNSUPPORTED
     good = _abi.FlowShapeC(2, 8, 2, 8, 8, 3, 1, 0.01)
     assert lib.gf_flow_create(C.byref(good), None, 0, None, C.byref(h)) == _abi.GF_EINVAL
     assert lib.gf_flow_create(C.byref(good), w, 7, None, C.byref(h)) == _abi.GF_EINVAL

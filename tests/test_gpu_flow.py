@@ -104,8 +104,12 @@ def test_empty_batch_and_errors():
     assert out.phi.numel() == 0
     with pytest.raises(P._abi.GFError):
         P.Flow(gi.FlowShape(2, 7, 2, 8, 8), gi.init_weights(gi.FlowShape(2, 7, 2, 8, 8)))
-    with pytest.raises(P._abi.GFError):
-        P.Flow(gi.FlowShape(2, 8, 2, 12, 12), gi.init_weights(gi.FlowShape(2, 8, 2, 12, 12)))
+    with pytest.raises(P._abi.GFError):          # even kernel size
+        P.Flow(gi.FlowShape(2, 8, 2, ksize=4), np.zeros(1000))
+    # widths outside {8, 16, 32} are valid: they run on the general-network kernel
+    w12 = gi.init_weights(gi.FlowShape(2, 8, 2, 12, 12))
+    f12 = P.Flow(gi.FlowShape(2, 8, 2, 12, 12), w12)
+    assert f12.sample(0, phi4=(-4.0, 8.0)).phi.numel() == 0
 
 
 @pytest.mark.parametrize("key", ["c1", "c3"])
