@@ -267,6 +267,17 @@ gf_status gf_flow_train_step(gf_flow* flow, const gf_phi4* phi4, int64_t B, uint
                              int64_t adam_t, void* d_workspace, size_t workspace_bytes,
                              cudaStream_t stream);
 
+/* One Adam step (Kingma & Ba; bias-corrected, 1-based step adam_t) on the
+ * flow's weights with a gradient supplied by the caller: d_grad [n_params]
+ * FP32 in canonical order (for example the average over data-parallel ranks
+ * of gf_flow_train_step's gradients, or gf_flow_backward's), moments
+ * d_adam_m, d_adam_v [n_params] FP32 updated in place.  The same update
+ * gf_flow_train_step applies when lr > 0 (Sec. 3: opt = Adam).  Any flow,
+ * including general networks. */
+gf_status gf_flow_adam_step(gf_flow* flow, const float* d_grad, float lr, float beta1, float beta2,
+                            float adam_eps, float* d_adam_m, float* d_adam_v, int64_t adam_t,
+                            cudaStream_t stream);
+
 /* The training step in two halves, for a loss assembled by the caller
  * (e.g. through torch.autograd).  Both take the workspace of
  * gf_train_workspace_bytes(flow, B).

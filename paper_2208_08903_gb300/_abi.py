@@ -23,7 +23,8 @@ EXPORTED = [
     "gf_unfused_workspace_bytes", "gf_flow_sample_unfused",
     "gf_phi4_force", "gf_mh_chain_workspace_bytes", "gf_mh_chain", "gf_mh_chain_noalloc",
     "gf_hmc_trajectory",
-    "gf_train_workspace_bytes", "gf_flow_train_step", "gf_flow_forward_train", "gf_flow_backward",
+    "gf_train_workspace_bytes", "gf_flow_train_step", "gf_flow_adam_step", "gf_flow_forward_train",
+    "gf_flow_backward",
     "gf_phi4_action_vjp", "gf_observables", "gf_chain_gather", "gf_autocorr", "gf_ess",
     "gf_device_status", "gf_status_string",
 ]
@@ -99,6 +100,7 @@ def load():
         "gf_train_workspace_bytes": ([_VP, _I64], _SZ),
         "gf_flow_train_step": ([_VP, C.POINTER(Phi4C), _I64, _U64, _U64, _VP, _VP, _VP, _F32,
                                 _F32, _F32, _F32, _VP, _VP, _I64, _VP, _SZ, _VP], _I32),
+        "gf_flow_adam_step": ([_VP, _VP, _F32, _F32, _F32, _F32, _VP, _VP, _I64, _VP], _I32),
         "gf_flow_forward_train": ([_VP, _I64, _U64, _U64, _VP, _VP, _VP, _VP, _SZ, _VP], _I32),
         "gf_flow_backward": ([_VP, _I64, _VP, _VP, _VP, _VP, _SZ, _VP], _I32),
         "gf_phi4_action_vjp": ([_I32, _I32, C.POINTER(Phi4C), _I64, _VP, _VP, _VP, _VP], _I32),

@@ -194,6 +194,16 @@ class Flow:
         return loss, g
 
 
+    def adam_step(self, grad: torch.Tensor, lr: float, adam_m: torch.Tensor, adam_v: torch.Tensor,
+                  adam_t: int, beta1=0.9, beta2=0.999, adam_eps=1e-8):
+        """gf_flow_adam_step: one Adam update of the resident weights with `grad`."""
+        for t, name in ((grad, "grad"), (adam_m, "adam_m"), (adam_v, "adam_v")):
+            _need(t, torch.float32, name, self.n_params)
+        _abi.check("gf_flow_adam_step", self._lib.gf_flow_adam_step(
+            self._h, _ptr(grad), float(lr), float(beta1), float(beta2), float(adam_eps), _ptr(adam_m),
+            _ptr(adam_v), int(adam_t), _stream()))
+        self.weights_version += 1
+
     def forward_train(self, B: int, seed: int = 0, counter0: int = 0, z=None,
                       workspace: torch.Tensor | None = None):
         """Forward half of training: (phi [B][V] FP32, log q [B] FP64, workspace).

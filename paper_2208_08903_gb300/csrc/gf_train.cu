@@ -951,6 +951,20 @@ gf_status gf_flow_backward(const gf_flow* flow, int64_t B, const float* d_gphi, 
     return backward<2>(flow, B, d_gphi, d_glogq, d_grad_out, w, stream);
 }
 
+gf_status gf_flow_adam_step(gf_flow* flow, const float* d_grad, float lr, float beta1, float beta2,
+                            float adam_eps, float* d_adam_m, float* d_adam_v, int64_t adam_t,
+                            cudaStream_t stream) {
+    if (!flow || !d_grad || !d_adam_m || !d_adam_v || adam_t < 1 || !(lr >= 0.f)) return GF_EINVAL;
+    if (flow->n_params == 0) return GF_OK;
+    const float c1 = 1.f - powf(beta1, (float)adam_t), c2 = 1.f - powf(beta2, (float)adam_t);
+    k_adam<<<(unsigned)grid1d(flow->n_params), kThreads, 0, stream>>>(flow->n_params, flow->d_canon, d_grad,
+                                                                       d_adam_m, d_adam_v, lr, beta1, beta2,
+                                                                       adam_eps, c1, c2);
+    GF_CHECK_LAUNCH();
+    if (flow->variant) return repack_variant(flow, stream);
+    return repack_weights(flow, stream);
+}
+
 size_t gf_unfused_workspace_bytes(const gf_flow* flow, int64_t B) {
     if (!flow || B < 0 || flow->variant) return 0;
     return carve_plain(flow, B, nullptr).bytes;

@@ -20,6 +20,7 @@ from __future__ import annotations
 import argparse
 import dataclasses
 import json
+import math
 import time
 
 import numpy as np
@@ -96,14 +97,18 @@ def load_checkpoint(path: str, flow: api.Flow) -> tuple[TrainState, dict]:
 
 
 def evaluate(flow: api.Flow, phi4, n_proposals: int, batch: int, seed: int, counter0: int = 0,
-             mh_seed: int = 1, sampler: str = "fused") -> dict:
+             mh_seed: int = 1, sampler: str = "fused", keep_logw: bool = False) -> dict:
     """Acceptance of an MH independence chain over n_proposals flow samples,
     the ESS fraction of their importance weights and the chain average of
     |M| with its integrated autocorrelation time (all on the device).
-    sampler: "fused" (gf_flow_sample) or "unfused" (one kernel per conv)."""
+    sampler: "fused" (gf_flow_sample of `flow`, whatever its precision) or
+    "unfused" (one kernel per conv).  The proposals are fixed by (seed,
+    counter0): two flows evaluated with the same arguments see the same prior
+    samples and the same MH uniforms."""
     st = api.new_mh_state(mh_seed)
     lws, Ms, idxs = [], [], []
     ws = None
+    t0 = time.perf_counter()
     for i in range(0, n_proposals, batch):
         b = min(batch, n_proposals - i)
         if sampler == "fused":
@@ -123,16 +128,31 @@ def evaluate(flow: api.Flow, phi4, n_proposals: int, batch: int, seed: int, coun
     _, summ = api.autocorr(series, t_max)
     ess = api.ess(logw)
     s = api.read_mh_state(st)
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
     summ = summ.cpu().tolist()
-    return {"acceptance": s.n_acc / max(1, s.step - 1), "ess": float(ess.item()),
-            "abs_M": summ[3], "tau_int_abs_M": summ[0], "window": int(summ[1]),
-            "proposals": n_proposals}
+    n = max(1, s.step - 1)
+    acc = s.n_acc / n
+    out = {"acceptance": acc, "acceptance_binomial_err": math.sqrt(max(acc * (1 - acc), 0.0) / n),
+           "ess": float(ess.item()), "abs_M": summ[3], "tau_int_abs_M": summ[0],
+           "tau_int_err": summ[2], "window": int(summ[1]), "proposals": n_proposals,
+           "seconds": secs, "precision": getattr(flow, "precision", "fp32"), "sampler": sampler}
+    if keep_logw:
+        out["logw"] = logw
+        out["chain_idx"] = torch.cat(idxs)
+    return out
+
+
+def decision_agreement(a: dict, b: dict) -> float:
+    """Fraction of proposals on which two evaluations (kept with keep_logw)
+    left their chains in the same state."""
+    return float((a["chain_idx"] == b["chain_idx"]).double().mean().item())
 
 
 def main(argv=None):
     import gf_inputs as gi
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
-    ap.add_argument("--workload", default="c1", choices=["c1", "c2"])
+    ap.add_argument("--workload", default="c1", choices=["c1", "c2", "c3"])
     ap.add_argument("--epochs", type=int, default=200)
     ap.add_argument("--iterations", type=int, default=100)
     ap.add_argument("--batch", type=int, default=0)
@@ -143,10 +163,19 @@ def main(argv=None):
     ap.add_argument("--resume", default="")
     ap.add_argument("--eval-proposals", type=int, default=16384)
     ap.add_argument("--eval-every", type=int, default=20)
+    ap.add_argument("--n-layers", type=int, default=0, help="override the workload's coupling-layer count")
+    ap.add_argument("--m2", type=float, default=None)
+    ap.add_argument("--lam", type=float, default=None)
+    ap.add_argument("--compare-proposals", type=int, default=0,
+                    help="proposals for the final sampler comparison (default: --eval-proposals)")
     args = ap.parse_args(argv)
     W = gi.WORKLOADS[args.workload]
     shape, phi4 = W["shape"], W["phi4"]
-    batch = args.batch or W["batch"]
+    if args.n_layers:
+        shape = dataclasses.replace(shape, n_layers=args.n_layers)
+    if args.m2 is not None or args.lam is not None:
+        phi4 = gi.Phi4(args.m2 if args.m2 is not None else phi4.m2, args.lam if args.lam is not None else phi4.lam)
+    batch = args.batch or (64 if args.workload == "c3" else W["batch"])
     flow = api.Flow(shape, gi.init_weights(shape, seed=args.model_seed))
     state = None
     if args.resume:
@@ -162,13 +191,22 @@ def main(argv=None):
             if args.checkpoint:
                 save_checkpoint(args.checkpoint, flow, state, workload=args.workload, seed=args.seed,
                                 batch=batch, lr=args.lr)
-    # the fused and the plain (one kernel per convolution) samplers on the same
-    # proposals: the MH decisions, hence the acceptance, must agree
-    same = {}
-    for kind in ("fused", "unfused"):
-        same[kind] = evaluate(flow, phi4, args.eval_proposals, 4096, seed=args.seed + 2, sampler=kind)
-    print(json.dumps({"final": True, "step": state.step, "fused": same["fused"], "unfused": same["unfused"]}),
-          flush=True)
+    # the fused and the plain (one kernel per convolution) FP32 samplers, and the
+    # BF16 tensor-core sampler where the shape has one, on the same proposals
+    n_cmp = args.compare_proposals or args.eval_proposals
+    arms = {"fused": (flow, "fused"), "unfused": (flow, "unfused")}
+    if (shape.nd, shape.L, shape.c1, shape.c2) == (3, 16, 32, 32) and shape.is_default_net:
+        wt = flow.get_weights().double().cpu().numpy()
+        arms["bf16"] = (api.Flow(shape, wt, precision="bf16"), "fused")
+    same = {k: evaluate(f, phi4, n_cmp, 4096, seed=args.seed + 2, sampler=kind, keep_logw=True)
+            for k, (f, kind) in arms.items()}
+    line = {"final": True, "step": state.step, "theory": [phi4.m2, phi4.lam], "n_layers": shape.n_layers}
+    for k, ev in same.items():
+        line[k] = {kk: v for kk, v in ev.items() if kk not in ("logw", "chain_idx")}
+        line[k]["configs_per_s"] = n_cmp / ev["seconds"]
+        if k != "fused":
+            line[k]["decisions_same_as_fused"] = decision_agreement(ev, same["fused"])
+    print(json.dumps(line), flush=True)
 
 
 if __name__ == "__main__":

@@ -142,3 +142,24 @@ def test_lr_schedule_and_evaluation():
         assert 0.0 <= e["acceptance"] <= 1.0 and 0.0 < e["ess"] <= 1.0 and e["abs_M"] >= 0.0
     # same proposals through the fused and the plain sampler: same chain up to near ties
     assert abs(ev["fused"]["acceptance"] - ev["unfused"]["acceptance"]) <= 2 / 999
+
+
+def test_data_parallel_step_on_one_rank_equals_fused_step():
+    """distributed.dp_train_step without a process group (one rank): the
+    gradient of gf_flow_train_step (lr = 0) applied by gf_flow_adam_step gives
+    bit for bit the weights of gf_flow_train_step with lr > 0."""
+    torch, P = require_gpu()
+    from paper_2208_08903_gb300 import distributed as D
+    shape = gi.FlowShape(2, 8, 4, 8, 8)
+    w = gi.init_weights(shape, seed=7)
+    fa, fb = P.Flow(shape, w), P.Flow(shape, w)
+    ma, va = torch.zeros(fa.n_params, device="cuda"), torch.zeros(fa.n_params, device="cuda")
+    mb, vb = torch.zeros(fb.n_params, device="cuda"), torch.zeros(fb.n_params, device="cuda")
+    for t in (1, 2, 3):
+        la, _ = fa.train_step(96, (-4.0, 8.0), seed=3, counter0=96 * t, lr=1e-3, adam_m=ma, adam_v=va, adam_t=t,
+                              grad=False)
+        lb = D.dp_train_step(fb, (-4.0, 8.0), 96, seed=3, counter0=96 * t, lr=1e-3, adam_m=mb, adam_v=vb, adam_t=t)
+        assert float(la.item()) == float(lb.item())
+    assert torch.equal(fa.get_weights(), fb.get_weights())
+    assert torch.equal(ma, mb) and torch.equal(va, vb)
+    assert P.device_status() == 0
