@@ -616,9 +616,9 @@ def bench_serving(dev, n_requests=120, rate=200.0, n_models=16, seed=5):
     arr = serving.poisson_arrivals(n_requests, rate, seed)
     reqs = [serving.Request(i, name, m2, lam, b, sd, arrival=float(arr[i]))
             for i, (name, m2, lam, b, sd) in enumerate(gi.serving_requests(n_requests, list(models), seed))]
-    srv = serving.Server(models, hbm_budget_bytes=16 << 30, max_active=16, chunk=2048, device=dev)
-    srv.run(reqs[:4], keep_results=False, realtime=False)          # warm-up (kernel attributes, streams)
-    _, stats = srv.run(reqs, keep_results=False, realtime=True)
+    with serving.Server(models, hbm_budget_bytes=16 << 30, max_active=16, chunk=2048, device=dev) as srv:
+        srv.run(reqs[:4], keep_results=False, realtime=False)      # warm-up (kernel attributes, streams)
+        _, stats = srv.run(reqs, keep_results=False, realtime=True)
     stats.update({"offered_rate_req_per_s": rate, "models": n_models,
                   "mix": "2D L in {8,16,32,64}, 3D L in {8,12,16}, 12-24 couplings, hidden {8,16,32}, "
                          "batch 64-8192 log-uniform, BF16 conv2 for 3D L=16 hidden 32, FP32 otherwise"})

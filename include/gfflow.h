@@ -344,9 +344,36 @@ gf_status gf_ess(int64_t n, const double* d_logw, double* d_ess_out, cudaStream_
 /* Status                                                                  */
 /* ---------------------------------------------------------------------- */
 
-/* Synchronises `stream`, returns the device status word (0 = no error,
- * else a negative gf_status) and clears it. */
+/* Test hook for the failure path of the BF16 tensor-core kernel (the
+ * bounded mbarrier waits between its roles).  spins > 0: in launches made
+ * after the call (process-wide), each block's first conv2 issuer, before its
+ * first MMA, waits up to `spins` polls for a barrier completion that never
+ * comes; the wait then gives up as any pipeline wait does when its limit runs
+ * out: it records GF_ETIMEOUT in the device status word and raises the
+ * block's abort flag; every other role leaves its loops, the block waits for
+ * its queued tensor-core work and weight copies, frees its tensor memory and
+ * returns.  The outputs of such a launch are undefined.  spins = 0 turns the
+ * hook off; spins < 0 or above 2^21 returns GF_EINVAL.  Not for production
+ * use. */
+gf_status gf_set_bf16_stall_test(int64_t spins);
+
+/* Returns in *status_out the status word that kernels launched on `stream`
+ * record errors in (0 = no error, else a negative gf_status) and clears it:
+ * after the work already queued on `stream`, one atomic exchange on the device
+ * reads and zeroes it, then the call waits for `stream`.  Without a slot set
+ * for `stream` (gf_set_stream_status_slot) the word is process-wide: it holds
+ * the first error of any kernel of this library on any stream since it was
+ * last cleared, so with work in flight on several streams an error cannot be
+ * attributed to one of them (use per-stream slots for that). */
 gf_status gf_device_status(cudaStream_t stream, int32_t* status_out);
+/* Per-stream error attribution (for example one stream per request in a
+ * serving loop): kernels launched on `stream` after this call record their
+ * device-detected errors (first error wins) in *d_slot -- 4 bytes of device
+ * memory owned by the caller, zeroed by the caller, alive while associated --
+ * instead of the process-wide word, and gf_device_status(stream) reads and
+ * clears that slot.  d_slot = NULL removes the association.  Host-side only;
+ * thread-safe. */
+gf_status gf_set_stream_status_slot(cudaStream_t stream, int32_t* d_slot);
 /* Human-readable name of a status code (static string). */
 const char* gf_status_string(int32_t status);
 

@@ -26,7 +26,8 @@ EXPORTED = [
     "gf_train_workspace_bytes", "gf_flow_train_step", "gf_flow_adam_step", "gf_flow_forward_train",
     "gf_flow_backward",
     "gf_phi4_action_vjp", "gf_observables", "gf_chain_gather", "gf_autocorr", "gf_ess",
-    "gf_device_status", "gf_status_string",
+    "gf_device_status", "gf_status_string", "gf_set_bf16_stall_test",
+    "gf_set_stream_status_slot",
 ]
 
 
@@ -109,6 +110,8 @@ def load():
         "gf_autocorr": ([_I64, _VP, _I32, _F64, _VP, _VP, _VP], _I32),
         "gf_ess": ([_I64, _VP, _VP, _VP], _I32),
         "gf_device_status": ([_VP, C.POINTER(_I32)], _I32),
+        "gf_set_bf16_stall_test": ([_I64], _I32),
+        "gf_set_stream_status_slot": ([_VP, _VP], _I32),
         "gf_status_string": ([_I32], C.c_char_p),
     }
     for name, (args, res) in sig.items():

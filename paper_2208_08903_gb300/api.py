@@ -381,6 +381,19 @@ def ess(logw: torch.Tensor) -> torch.Tensor:
 
 
 def device_status(stream=None) -> int:
+    """gf_device_status: the status word of `stream` (its slot, else the
+    process-wide word), read and cleared; 0 = no device-detected error."""
     v = C.c_int32(0)
     _abi.check("gf_device_status", _abi.load().gf_device_status(_stream(stream), C.byref(v)))
     return v.value
+
+
+def set_stream_status_slot(stream, slot: torch.Tensor | None):
+    """gf_set_stream_status_slot: kernels launched on `stream` record their
+    errors in `slot` (one zeroed int32 CUDA element) instead of the
+    process-wide word; None removes the association.  Keep `slot` alive while
+    it is associated."""
+    if slot is not None:
+        _need(slot, torch.int32, "slot", 1)
+    _abi.check("gf_set_stream_status_slot",
+               _abi.load().gf_set_stream_status_slot(_stream(stream), _ptr(slot)))

@@ -33,20 +33,6 @@ __device__ __forceinline__ void stage(const T* __restrict__ g, T* s, int V) {
     }
 }
 
-// Sum over mu of (2 phi(n) - phi(n+mu) - phi(n-mu)) in FP64.
-template <typename T>
-__device__ __forceinline__ double lap_minus(const T* p, int n, int nd, int L) {
-    const int xc = n % L, yc = (n / L) % L;
-    const double c = (double)p[n];
-    double k = 2.0 * c - (double)p[n - xc + wrapi(xc + 1, L)] - (double)p[n - xc + wrapi(xc - 1, L)];
-    k += 2.0 * c - (double)p[n + (wrapi(yc + 1, L) - yc) * L] - (double)p[n + (wrapi(yc - 1, L) - yc) * L];
-    if (nd == 3) {
-        const int zc = n / (L * L), LL = L * L;
-        k += 2.0 * c - (double)p[n + (wrapi(zc + 1, L) - zc) * LL] - (double)p[n + (wrapi(zc - 1, L) - zc) * LL];
-    }
-    return k;
-}
-
 // Site term in the forward-hop arrangement (equal to the two-neighbour form of
 // the action summed over the lattice): (2d + m2) phi^2 + lam phi^4
 // - 2 phi(n) sum_mu phi(n + mu).  It needs d neighbour reads and about half the
@@ -121,10 +107,7 @@ __global__ void __launch_bounds__(kActThreads) force_kernel(int nd, int L, int V
     for (int64_t b = blockIdx.x; b < B; b += gridDim.x) {
         stage(phi + b * V, p, V);
         __syncthreads();
-        for (int n = threadIdx.x; n < V; n += blockDim.x) {
-            const double c = p[n];
-            F[b * V + n] = 2.0 * lap_minus(p, n, nd, L) + 2.0 * m2 * c + 4.0 * lam * c * c * c;
-        }
+        for (int n = threadIdx.x; n < V; n += blockDim.x) F[b * V + n] = phi4_force_site(p, n, nd, L, m2, lam);
         __syncthreads();
     }
 }
@@ -141,11 +124,8 @@ __global__ void __launch_bounds__(kActThreads) action_vjp_kernel(int nd, int L, 
         stage(phi + b * V, p, V);
         __syncthreads();
         const double g = gS[b];
-        for (int n = threadIdx.x; n < V; n += blockDim.x) {
-            const double c = p[n];
-            const double F = 2.0 * lap_minus(p, n, nd, L) + 2.0 * m2 * c + 4.0 * lam * c * c * c;
-            gphi[b * V + n] = (float)(g * F);
-        }
+        for (int n = threadIdx.x; n < V; n += blockDim.x)
+            gphi[b * V + n] = (float)(g * phi4_force_site(p, n, nd, L, m2, lam));
         __syncthreads();
     }
 }

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cstring>
 #include <mutex>
+#include <unordered_map>
 #include <vector>
 
 #include "gf_flow.cuh"
@@ -12,12 +13,30 @@ namespace gf {
 
 namespace {
 __device__ int32_t g_status = 0;
+__device__ int32_t g_status_read = 0;     // gf_device_status's copy of the exchanged word
+
+std::mutex g_slot_mu;
+std::unordered_map<cudaStream_t, int32_t*> g_stream_slot;   // gf_set_stream_status_slot
+std::mutex g_read_mu;                                        // one gf_device_status at a time
+
+__global__ void status_exchange_kernel(int32_t* word, int32_t* out) {
+    *out = atomicExch(reinterpret_cast<int*>(word), 0);
 }
+}  // namespace
 
 int32_t* status_word() {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_status) != cudaSuccess) return nullptr;
     return static_cast<int32_t*>(p);
+}
+
+int32_t* status_word(cudaStream_t stream) {
+    {
+        std::lock_guard<std::mutex> lk(g_slot_mu);
+        auto it = g_stream_slot.find(stream);
+        if (it != g_stream_slot.end()) return it->second;
+    }
+    return status_word();
 }
 
 int num_sms() {
@@ -432,11 +451,25 @@ gf_status gf_flow_logq(const gf_flow* flow, int64_t B, const float* d_phi_in,
 
 gf_status gf_device_status(cudaStream_t stream, int32_t* status_out) {
     if (!status_out) return GF_EINVAL;
-    if (cudaStreamSynchronize(stream) != cudaSuccess) return GF_ECUDA;
-    int32_t v = 0, zero = 0;
-    if (cudaMemcpyFromSymbol(&v, g_status, sizeof(v)) != cudaSuccess) return GF_ECUDA;
-    if (cudaMemcpyToSymbol(g_status, &zero, sizeof(zero)) != cudaSuccess) return GF_ECUDA;
+    std::lock_guard<std::mutex> lk(g_read_mu);
+    int32_t* word = status_word(stream);
+    void* outp = nullptr;
+    if (!word || cudaGetSymbolAddress(&outp, g_status_read) != cudaSuccess) return GF_ECUDA;
+    // read and clear in one atomic exchange on the device, after the stream's work
+    status_exchange_kernel<<<1, 1, 0, stream>>>(word, static_cast<int32_t*>(outp));
+    if (cudaGetLastError() != cudaSuccess) return GF_ECUDA;
+    int32_t v = 0;
+    if (cudaMemcpyAsync(&v, outp, sizeof(v), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+        cudaStreamSynchronize(stream) != cudaSuccess)
+        return GF_ECUDA;
     *status_out = v;
+    return GF_OK;
+}
+
+gf_status gf_set_stream_status_slot(cudaStream_t stream, int32_t* d_slot) {
+    std::lock_guard<std::mutex> lk(g_slot_mu);
+    if (d_slot) g_stream_slot[stream] = d_slot;
+    else g_stream_slot.erase(stream);
     return GF_OK;
 }
 

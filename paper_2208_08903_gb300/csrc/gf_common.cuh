@@ -19,7 +19,10 @@ namespace gf {
 __device__ __forceinline__ void set_status(int32_t* word, int32_t code) {
     atomicCAS(reinterpret_cast<int*>(word), 0, code);
 }
-int32_t* status_word();   // host: device address of the status word
+int32_t* status_word();   // host: device address of the process-wide status word
+// host: where kernels launched on `stream` record errors (the stream's slot
+// from gf_set_stream_status_slot, else the process-wide word)
+int32_t* status_word(cudaStream_t stream);
 
 // ---------------------------------------------------------------------------
 // Philox4x64-10: ten rounds of two 64x64->128 multiplies with a Weyl key
@@ -159,6 +162,35 @@ inline void ff_split(double d, float* hi, float* lo) {
 }
 
 constexpr double LOG_2PI = 1.8378770664093454835606594728112;
+
+// Periodic neighbour wrap for |offset| <= L.
+__device__ __forceinline__ int wrap_site(int v, int L) { return v < 0 ? v + L : (v >= L ? v - L : v); }
+
+// Sum over mu of (2 phi(n) - phi(n+mu) - phi(n-mu)), i.e. minus the lattice
+// Laplacian of the paper's action (Sec. 1), in FP64 on a periodic lattice,
+// site n = x + L (y + L z); fields of any element type (widened exactly).
+template <typename T>
+__device__ __forceinline__ double lap_minus(const T* p, int n, int nd, int L) {
+    const int xc = n % L, yc = (n / L) % L;
+    const double c = (double)p[n];
+    double k = 2.0 * c - (double)p[n - xc + wrap_site(xc + 1, L)] - (double)p[n - xc + wrap_site(xc - 1, L)];
+    k += 2.0 * c - (double)p[n + (wrap_site(yc + 1, L) - yc) * L] - (double)p[n + (wrap_site(yc - 1, L) - yc) * L];
+    if (nd == 3) {
+        const int zc = n / (L * L), LL = L * L;
+        k += 2.0 * c - (double)p[n + (wrap_site(zc + 1, L) - zc) * LL] -
+             (double)p[n + (wrap_site(zc - 1, L) - zc) * LL];
+    }
+    return k;
+}
+
+// The force dS/dphi(n) = 2 sum_mu (2 phi - phi(n+mu) - phi(n-mu)) + 2 m2 phi
+// + 4 lam phi^3 in FP64: the one definition used by gf_phi4_force, the action
+// VJP, the HMC kicks and the training reverse pass's seed.
+template <typename T>
+__device__ __forceinline__ double phi4_force_site(const T* p, int n, int nd, int L, double m2, double lam) {
+    const double c = (double)p[n];
+    return 2.0 * lap_minus(p, n, nd, L) + 2.0 * m2 * c + 4.0 * lam * c * c * c;
+}
 
 // phi^4 action (paper Sec. 1) of one configuration held in shared memory,
 // this thread's share of the sites (n = threadIdx.x, += blockDim.x), in the

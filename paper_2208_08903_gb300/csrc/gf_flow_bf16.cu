@@ -45,6 +45,7 @@
 // and the workers stage the next layer's weights (bulk copies for W2 and W3) as
 // soon as the previous layer's last conv2 / conv3 has finished.
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 
 #include <cuda_bf16.h>
@@ -91,6 +92,8 @@ constexpr int kTmemC1 = 384;
 constexpr int kIm2colBufBytes = 2 * 2 * 128 * 16, kIm2colBytes = 2 * kIm2colBufBytes;
 constexpr int kTmemCols = 512;
 constexpr long long kWaitLimit = 1ll << 22;             // bounded mbarrier wait (iterations)
+// Failure-path test of the next launches (gf_set_bf16_stall_test): 0 = off.
+std::atomic<long long> g_stall_spins{0};
 // Warp w runs on sub-partition w % 4 and may read TMEM lane quarter w % 4.
 // One lane each of warps 0, 17, 18 and 19 (sub-partitions 0..3) issues conv2 of
 // M-tile 0, conv2 of M-tile 1, the conv3 batches and conv1; warps 1..8 are the
@@ -209,6 +212,7 @@ struct Bf16Args {
     const float* z_in; float* z_out; const float* phi_in; float* phi_out;
     double* logq_out; double* S_out; double* logw_out;
     int32_t* status;
+    long long stall_spins;     // > 0: failure-path test (see gf_set_bf16_stall_test)
 };
 
 __device__ __forceinline__ int wrap16(int v) { return v & 15; }
@@ -399,6 +403,11 @@ __device__ __forceinline__ bool wait_n(uint64_t* bar, int n, volatile int* abort
     }
     return true;
 }
+// Bounded wait that ignores the abort flag (teardown: work already issued must
+// finish before its shared memory or TMEM is released).
+__device__ __forceinline__ void drain_wait(uint64_t* bar, int n) {
+    for (long long spins = 0; !mbar_try_wait(bar, (uint32_t)n & 1u) && spins < kWaitLimit; ++spins) {}
+}
 // Arrival that also announces `bytes` of bulk-copy data for the current phase.
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(smem_u32(bar)), "r"(bytes)
@@ -462,7 +471,8 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
     uint64_t* bar_w2 = bar_fin + 1;                            // 1: a layer's W2 and biases staged
     uint64_t* bar_w3 = bar_w2 + 1;                             // 1: a layer's W3 staged
     uint64_t* bar_x = bar_w3 + 1;                              // 4: a layer's field slices <= 5, 9, 13, 15 updated
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar_x + 4);
+    uint64_t* bar_stall = bar_x + 4;                           // 1: never completed (failure-path test)
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar_stall + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -488,6 +498,7 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
         mbar_init(bar_w2, 1);                                  // expect_tx by the staging thread
         mbar_init(bar_w3, 1);
         for (int i = 0; i < 4; ++i) mbar_init(bar_x + i, kEpiThreads);
+        mbar_init(bar_stall, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -511,6 +522,7 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
     const uint64_t a1c = smem_desc(smem_u32(im2col), 128 * 16, 128);           // + (buffer, tile)
 
     int seq = 0;                                   // layers processed by this CTA so far
+    int last_w2 = -1, last_w3 = -1;                // staging thread: completions its last copies bring
     for (int64_t b = blockIdx.x; b < a.B; b += gridDim.x) {
         FF sumz2{0.f, 0.f};                        // sum z^2: each square exactly as a pair
         if (!INVERSE) {
@@ -560,6 +572,17 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
             if (lane == 0) {
                 const int t = warp == kMma2Warp;
                 bool ok = true;
+                if (a.stall_spins > 0 && seq0 == 0 && t == 0) {
+                    // failure-path test: a wait for a completion that never comes runs
+                    // out long after every MMA issued so far has finished
+                    for (long long spins = 0; !mbar_try_wait(bar_stall, 0u); ++spins)
+                        if (spins > a.stall_spins) {
+                            *abort_flag = 1;
+                            set_status(a.status, GF_ETIMEOUT);
+                            ok = false;
+                            break;
+                        }
+                }
                 for (int li = 0; li < nl && ok; ++li) {
                     const int s = seq0 + li, c0 = s * kConv1PerLayer, g20 = s * kConv2PerLayer;
                     ok = wait_n(bar_w2, s, abort_flag, a.status);          // this layer's W2 staged
@@ -637,11 +660,13 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
             // (2 KB) by one 16-byte copy per thread of the first 128
             const auto stage_w2 = [&](int l) {
                 const unsigned char* blk = a.Wl + (size_t)l * kLayerBytes;
+                ++last_w2;                                // bar_w2 completes once per staged layer
                 mbar_expect_tx(bar_w2, (uint32_t)(kW2Bytes + kF_N * 4));
                 bulk_g2s(w2s, blk, (uint32_t)kW2Bytes, bar_w2);
                 bulk_g2s(wf, blk + kW2Bytes + kW3Bytes + kW1Bytes, (uint32_t)(kF_N * 4), bar_w2);
             };
             const auto stage_w3 = [&](int l) {
+                ++last_w3;
                 mbar_expect_tx(bar_w3, (uint32_t)kW3Bytes);
                 bulk_g2s(w3s, a.Wl + (size_t)l * kLayerBytes + kW2Bytes, (uint32_t)kW3Bytes, bar_w3);
             };
@@ -849,12 +874,18 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
         }
         __syncthreads();
     }
-    // after an abort some MMAs may still be queued: every issuing thread commits,
-    // and TMEM is freed only once all their tensor-core work is done (bounded wait)
+    // after an abort some MMAs may still be queued and a weight copy may still be
+    // writing shared memory: every issuing thread commits, and TMEM is freed only
+    // once all their tensor-core work is done; the staging thread waits for the
+    // completions its last W2 / W3 copies bring (bounded waits, abort flag ignored)
     if ((warp == kMma2Warp || warp == kMma3Warp || warp == kMma1Warp) && lane == 0) mma_commit(bar_fin);
     if (warp == kMmaWarp && lane == 0) {
         mma_commit(bar_fin);
-        for (long long spins = 0; !mbar_try_wait(bar_fin, 0u) && spins < kWaitLimit; ++spins) {}
+        drain_wait(bar_fin, 0);
+    }
+    if (warp == kC1Warp0 && lane == 0) {           // the staging thread (worker wt == 0)
+        if (last_w2 >= 0) drain_wait(bar_w2, last_w2);
+        if (last_w3 >= 0) drain_wait(bar_w3, last_w3);
     }
     fence_before_sync();
     __syncthreads();
@@ -962,7 +993,8 @@ gf_status launch_flow_bf16(const gf_flow* f, bool inverse, const gf_phi4* phi4, 
     a.B = B; a.seed = seed; a.counter0 = counter0;
     a.z_in = z_in; a.z_out = z_out; a.phi_in = phi_in; a.phi_out = phi_out;
     a.logq_out = logq_out; a.S_out = S_out; a.logw_out = logw_out;
-    a.status = status_word();
+    a.status = status_word(stream);
+    a.stall_spins = g_stall_spins.load(std::memory_order_relaxed);
     if (!a.status) return GF_ECUDA;
     auto kern = inverse ? flow_bf16_kernel<true> : flow_bf16_kernel<false>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes) != cudaSuccess)
@@ -974,3 +1006,9 @@ gf_status launch_flow_bf16(const gf_flow* f, bool inverse, const gf_phi4* phi4, 
 }
 
 }  // namespace gf
+
+extern "C" gf_status gf_set_bf16_stall_test(int64_t spins) {
+    if (spins < 0 || spins > gf::kWaitLimit / 2) return GF_EINVAL;
+    gf::g_stall_spins.store((long long)spins, std::memory_order_relaxed);
+    return GF_OK;
+}

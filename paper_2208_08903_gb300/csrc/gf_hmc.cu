@@ -15,21 +15,6 @@ namespace {
 constexpr int kHmcThreads = 256;
 constexpr int kMaxSitesPerThread = 16;    // V <= 4096
 
-__device__ __forceinline__ int wrapi(int v, int L) { return v < 0 ? v + L : (v >= L ? v - L : v); }
-
-// sum_mu (2 phi(n) - phi(n+mu) - phi(n-mu))
-__device__ __forceinline__ double kin_term(const double* p, int n, int nd, int L) {
-    const int xc = n % L, yc = (n / L) % L;
-    const double c = p[n];
-    double k = 2.0 * c - p[n - xc + wrapi(xc + 1, L)] - p[n - xc + wrapi(xc - 1, L)];
-    k += 2.0 * c - p[n + (wrapi(yc + 1, L) - yc) * L] - p[n + (wrapi(yc - 1, L) - yc) * L];
-    if (nd == 3) {
-        const int zc = n / (L * L), LL = L * L;
-        k += 2.0 * c - p[n + (wrapi(zc + 1, L) - zc) * LL] - p[n + (wrapi(zc - 1, L) - zc) * LL];
-    }
-    return k;
-}
-
 __global__ void __launch_bounds__(kHmcThreads) hmc_kernel(int nd, int L, int V, double m2, double lam,
                                                           int64_t n_chains, double* __restrict__ phi_g,
                                                           int n_steps, double eps, uint64_t seed,
@@ -63,7 +48,7 @@ __global__ void __launch_bounds__(kHmcThreads) hmc_kernel(int nd, int L, int V, 
                 const int n = threadIdx.x + k * blockDim.x;
                 if (k < nper && n < V) {
                     const double f = p[n], f2 = f * f;
-                    h += 0.5 * pi[k] * pi[k] + f * kin_term(p, n, nd, L) + m2 * f2 + lam * f2 * f2;
+                    h += 0.5 * pi[k] * pi[k] + f * lap_minus(p, n, nd, L) + m2 * f2 + lam * f2 * f2;
                 }
             }
             return block_sum(h, red);
@@ -72,10 +57,7 @@ __global__ void __launch_bounds__(kHmcThreads) hmc_kernel(int nd, int L, int V, 
 #pragma unroll
             for (int k = 0; k < kMaxSitesPerThread; ++k) {
                 const int n = threadIdx.x + k * blockDim.x;
-                if (k < nper && n < V) {
-                    const double f = p[n];
-                    pi[k] -= h * (2.0 * kin_term(p, n, nd, L) + 2.0 * m2 * f + 4.0 * lam * f * f * f);
-                }
+                if (k < nper && n < V) pi[k] -= h * phi4_force_site(p, n, nd, L, m2, lam);
             }
         };
         const double H0 = energy();

@@ -289,7 +289,7 @@ gf_status gf_chain_gather(int64_t n, const int64_t* d_chain_idx, int64_t idx0, i
     if (n == 0) return GF_OK;
     const int64_t total = n * width;
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, num_sms() * 16LL));
-    gather_kernel<<<grid, 256, 0, stream>>>(n, d_chain_idx, idx0, n_values, d_values, width, d_out, status_word());
+    gather_kernel<<<grid, 256, 0, stream>>>(n, d_chain_idx, idx0, n_values, d_values, width, d_out, status_word(stream));
     GF_CHECK_LAUNCH();
     return GF_OK;
 }

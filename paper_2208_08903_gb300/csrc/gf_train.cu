@@ -486,14 +486,8 @@ __global__ void __launch_bounds__(kThreads) k_loss_force(const float* __restrict
         double acc = 0.0, z2 = 0.0;
         for (int n = threadIdx.x; n < V; n += blockDim.x) {
             const double c = p[n];
-            double k = 0.0;
-            for (int mu = 0; mu < ND; ++mu) {
-                const int t_plus = (mu == 0) ? (ND == 3 ? 14 : 5) : (mu == 1) ? (ND == 3 ? 16 : 7) : 22;
-                const int t_minus = (ND == 3 ? 26 : 8) - t_plus;
-                k += 2.0 * c - (double)p[nbr<ND>(n, t_plus, L)] - (double)p[nbr<ND>(n, t_minus, L)];
-            }
-            acc += c * k + m2 * c * c + lam * c * c * c * c;
-            gx[b * V + n] = (float)(2.0 * k + 2.0 * m2 * c + 4.0 * lam * c * c * c);
+            acc += c * lap_minus(p, n, ND, L) + m2 * c * c + lam * c * c * c * c;
+            gx[b * V + n] = (float)phi4_force_site(p, n, ND, L, m2, lam);
             const double zz = z[b * V + n];
             z2 += zz * zz;
         }

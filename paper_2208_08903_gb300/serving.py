@@ -12,7 +12,12 @@ with their own (m2, lam), seed and Metropolis-Hastings chain.  The loop:
     request's chain consumes its proposals in order while chunks of different
     requests overlap on the GPU;
   * retires a request when its last chunk's event completes, frees its slot
-    and budget, and records its latency (completion - arrival).
+    and budget, and records its latency (completion - arrival);
+  * attributes device-detected errors (a bounded wait of a kernel that ran
+    out) to the request that caused them: each stream has its own status slot
+    (gf_set_stream_status_slot), read and cleared when a request on it
+    retires; a request whose slot is non-zero is reported failed (Result.error)
+    and its outputs must not be used.
 
 Results do not depend on what else is running: every random number is keyed
 by the request's seed and the configuration's index inside the request, and
@@ -67,6 +72,7 @@ class Result:
     arrival: float
     admitted: float
     done: float
+    error: int = 0              # 0, or the gf_status a kernel of this request recorded
 
     @property
     def latency(self) -> float:
@@ -130,6 +136,36 @@ class Server:
         self.chunk = int(chunk)
         self.device = device or torch.device("cuda", torch.cuda.current_device())
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(self.max_active)]
+        # one device status slot per stream: errors are attributed to the request on it
+        self.slots = torch.zeros(self.max_active, dtype=torch.int32, device=self.device)
+        for i, st in enumerate(self.streams):
+            api.set_stream_status_slot(st, self.slots[i:i + 1])
+
+    def close(self):
+        """Removes the streams' status-slot associations (also done when the
+        server is garbage collected).  The association belongs to the stream
+        handle, and torch hands out pooled streams, so a server should be
+        closed before another one is created on the same device."""
+        for st in getattr(self, "streams", []) or []:
+            if st is not None and getattr(self, "slots", None) is not None:
+                api.set_stream_status_slot(st, None)
+        self.slots = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _take_error(self, si: int) -> int:
+        """Reads and clears stream si's status slot (its work has completed)."""
+        return api.device_status(self.streams[si])
 
     def run(self, requests, keep_results: bool = True, realtime: bool = True, poll_s: float = 50e-6):
         """Serves `requests` (arrival times relative to the start) and returns
@@ -174,12 +210,13 @@ class Server:
                 elif st.finished():
                     done = now()
                     r = st.req
+                    err = self._take_error(si)
                     if keep_results:
                         results[rid] = Result(rid, st.phi, st.logq, st.S, st.logw, st.idx, st.acc, st.state,
-                                              r.arrival if realtime else 0.0, admitted_at[rid], done)
+                                              r.arrival if realtime else 0.0, admitted_at[rid], done, err)
                     else:
                         results[rid] = Result(rid, None, None, None, None, None, None, None,
-                                              r.arrival if realtime else 0.0, admitted_at[rid], done)
+                                              r.arrival if realtime else 0.0, admitted_at[rid], done, err)
                     del active[rid]
                     free_streams.append(si)
                     used -= need
@@ -203,6 +240,7 @@ class Server:
             "p99_latency_ms": float(np.percentile(lat, 99) * 1e3) if lat.size else None,
             "max_concurrent_requests": max_concurrent,
             "peak_budget_bytes": peak_used,
+            "failed_requests": int(sum(1 for r in results.values() if r.error)),
         }
         return results, stats
 

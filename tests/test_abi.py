@@ -97,3 +97,19 @@ def test_product_path_has_no_oracle_dependency():
                 src = open(os.path.join(dirpath, fn)).read()
                 assert "oracle" not in src.lower(), fn
                 assert "gf_oracle" not in src and "gfo_" not in src, fn
+
+
+def test_force_is_defined_once():
+    """dS/dphi has one device definition (gf_common.cuh: phi4_force_site),
+    used by gf_phi4_force, the action VJP, the HMC kicks and the training
+    reverse pass; no kernel file writes the force formula itself."""
+    csrc = os.path.join(ROOT, "paper_2208_08903_gb300", "csrc")
+    users = 0
+    for fn in os.listdir(csrc):
+        src = open(os.path.join(csrc, fn)).read()
+        if fn == "gf_common.cuh":
+            assert src.count("4.0 * lam * c * c * c") == 1
+            continue
+        assert "4.0 * lam" not in src, fn
+        users += "phi4_force_site(" in src
+    assert users >= 3

@@ -16,6 +16,13 @@ waits, arrivals and commits, under many random schedules, and checks:
 * conv1 reads each field slice only after the previous layer has updated it, and
   a layer updates a slice only after the previous layer's conv1 reads of it.
 
+It also replays the failure path: one role's wait runs out at a random point
+(the kernel then records GF_ETIMEOUT and raises the CTA's abort flag; every
+other wait gives up once it sees the flag), and checks that every role leaves
+its loops, that the tensor-core work still queued is complete before TMEM is
+freed (the issuers' final commit to bar_fin) and that no bulk weight copy is
+still writing shared memory when the CTA exits.
+
 Several workers or epilogue warps act as one agent here (their per-thread
 arrivals are one arrival); the model checks the protocol, not the arithmetic.
 Planted mistakes (a skipped wait, weights staged early, no slice rotation) are
@@ -99,21 +106,36 @@ def rot(li):
     return (4 * li) & 15
 
 
-def run(n_configs, n_layers, seed, mutation=None):
+def run(n_configs, n_layers, seed, mutation=None, abort_at=None):
     """Replays the kernel's loops; `mutation` plants one protocol mistake (for the
-    tests that show the model catches it)."""
+    tests that show the model catches it).  abort_at = (agent, k): the first wait
+    of that agent from its k-th on that is not already satisfied runs out.
+    Returns the status word (None or "GF_ETIMEOUT")."""
     m = Model(n_configs, n_layers, seed)
     B = m.B
     nl = n_layers
+    m.abort = False
+    m.status = None
+    n_waits = {}
 
     waiting = {}
     current = [None]
 
     def wait(name, n, who=None):
+        """True once completion n of `name` is seen; False when this wait runs
+        out (abort_at) or gives up because another thread aborted."""
+        me = current[0]
+        n_waits[me] = n_waits.get(me, 0) + 1
         while True:
             if m.check_wait(name, n):
-                return
-            waiting[current[0]] = (name, n, B[name].done)
+                return True
+            if m.abort:                      # the flag is polled while the wait spins
+                return False
+            if abort_at is not None and abort_at[0] == me and n_waits[me] >= abort_at[1]:
+                m.abort = True
+                m.status = "GF_ETIMEOUT"
+                return False
+            waiting[me] = (name, n, B[name].done)
             yield
 
     def issue(queue, group):
@@ -127,16 +149,19 @@ def run(n_configs, n_layers, seed, mutation=None):
         for li in range(nl):
             s = cfg * nl + li
             c0, g20 = s * C1_PER_LAYER, s * C2_PER_LAYER
-            yield from wait("w2", s)
+            if not (yield from wait("w2", s)):
+                return
             if m.w["W2"] != s:
                 raise Violation("conv2 issued before its W2")
             for u in range(-1, L + 1):
                 for v in (range(-2, 1) if u == -1 else [u + 1]):
                     c = c0 + v + 2
-                    yield from wait(f"h1{c & 3}", c >> 2)
+                    if not (yield from wait(f"h1{c & 3}", c >> 2)):
+                        return
                 g2 = g20 + u + 1
                 if g2 >= 1 and mutation != "no_t2_wait":
-                    yield from wait(f"t2{t}", g2 - 1)
+                    if not (yield from wait(f"t2{t}", g2 - 1)):
+                        return
                 reads = [c0 + v + 2 for v in (u - 1, u, u + 1)]
                 for c in reads:
                     if m.h1[c & 3] != c:
@@ -151,14 +176,17 @@ def run(n_configs, n_layers, seed, mutation=None):
         for li in range(nl):
             s = cfg * nl + li
             g20 = s * C2_PER_LAYER
-            yield from wait("w3", s)
+            if not (yield from wait("w3", s)):
+                return
             if m.w["W3"] != s:
                 raise Violation("conv3 issued before its W3")
             for ub in range(-1, L + 1):
                 gh = g20 + ub + 1
-                yield from wait(f"h2{gh % 3}", gh // 3)
+                if not (yield from wait(f"h2{gh % 3}", gh // 3)):
+                    return
                 if gh >= 3 and mutation != "no_t3_wait":
-                    yield from wait(f"t3{gh % 3}", (gh - 3) // 3)
+                    if not (yield from wait(f"t3{gh % 3}", (gh - 3) // 3)):
+                        return
                 if m.h2[gh % 3] != gh:
                     raise Violation(f"batch {gh} reads h2 slot holding {m.h2[gh % 3]}")
                 if m.c3_left.get(gh - 3, 0) > 0:
@@ -176,7 +204,8 @@ def run(n_configs, n_layers, seed, mutation=None):
             for v in range(-2, L + 2):
                 c = c0 + v + 2
                 b = c & 1
-                yield from wait(f"b1{b}", c >> 1)
+                if not (yield from wait(f"b1{b}", c >> 1)):
+                    return
                 if m.im2col[b] != c or m.w["W1"] != s:
                     raise Violation(f"conv1 {c} reads operand {m.im2col[b]} / W1 {m.w['W1']}")
                 if m.tm_c1[b] is not None:
@@ -189,6 +218,7 @@ def run(n_configs, n_layers, seed, mutation=None):
         if m.pending_reads(pred_readers):
             raise Violation(f"bulk copy of {resource} {version} while a queued MMA still reads the old one")
         m.queues["copy"].append(dict(kind="copy", res=resource, ver=version, commit=barrier))
+        m.last_copy[barrier] = B[barrier].done     # the completion this copy will bring
         B[barrier].arrive()          # expect_tx arrival
 
     def workers(cfg):
@@ -207,17 +237,21 @@ def run(n_configs, n_layers, seed, mutation=None):
             xseen = L if li == 0 else 0
             kx = 0
 
+            ok = [True]
+
             def build(v):
+                # as the kernel: the checkpoint waits stop at an abort, the operand is
+                # still built and signalled (its buffer was drained before)
                 nonlocal xseen, kx
                 c = c0 + v + 2
-                while xseen <= min(v + 5, L - 1):
-                    yield from wait(f"x{kx}", s - 1)
+                while xseen <= min(v + 5, L - 1) and ok[0]:
+                    ok[0] = yield from wait(f"x{kx}", s - 1)
                     xseen = (L - 1 if kx == 3 else 5 + 4 * kx) + 1
                     kx += 1
                 for d in (-1, 0, 1):
                     z = (v + R + d) & 15
                     want = s - 1 if li > 0 else ("prior", cfg)
-                    if m.x.get((z, fr)) != want:
+                    if ok[0] and m.x.get((z, fr)) != want:
                         raise Violation(f"conv1 of layer {s} reads slice {z} written by {m.x.get((z, fr))}")
                     m.x_reads.setdefault((z, fr), set()).add(s)
                 b = c & 1
@@ -228,8 +262,11 @@ def run(n_configs, n_layers, seed, mutation=None):
             yield from build(-2)
             yield from build(-1)
             for v in range(-2, L + 2):
+                if not ok[0]:
+                    return
                 c = c0 + v + 2
-                yield from wait(f"c1{c & 1}", c >> 1)
+                if not (yield from wait(f"c1{c & 1}", c >> 1)):
+                    return
                 if m.tm_c1[c & 1] != c:
                     raise Violation("conv1 drain of the wrong accumulator")
                 m.tm_c1[c & 1] = None
@@ -238,6 +275,8 @@ def run(n_configs, n_layers, seed, mutation=None):
                         m.x_reads[key].discard(s)
                 if v + 2 <= L + 1:
                     yield from build(v + 2)
+                if not ok[0]:
+                    return
                 if v >= 2:
                     g2 = g20 + v - 2
                 elif li > 0:
@@ -245,8 +284,9 @@ def run(n_configs, n_layers, seed, mutation=None):
                 else:
                     g2 = -1
                 if g2 >= 0 and mutation != "no_slot_wait":
-                    yield from wait(f"m2{g2 & 1}", g2 >> 1)
-                    yield from wait(f"m2{2 + (g2 & 1)}", g2 >> 1)
+                    if not ((yield from wait(f"m2{g2 & 1}", g2 >> 1)) and
+                            (yield from wait(f"m2{2 + (g2 & 1)}", g2 >> 1))):
+                        return
                 old = m.h1[c & 3]
                 if old is not None and m.pending_reads(lambda g: g["kind"] == "conv2" and old in g["h1"]):
                     raise Violation(f"h1 {c} overwrites {old} still read by a queued conv2")
@@ -258,7 +298,8 @@ def run(n_configs, n_layers, seed, mutation=None):
                         raise Violation("biases restaged before the epilogue read the previous ones")
                 elif li > 0 and v == 2:
                     gb = g20 - 1
-                    yield from wait(f"m3{gb & 1}", gb >> 1)
+                    if not (yield from wait(f"m3{gb & 1}", gb >> 1)):
+                        return
                     copy("W3", s, "w3", lambda g: g["kind"] == "conv3")
                 yield
 
@@ -273,7 +314,8 @@ def run(n_configs, n_layers, seed, mutation=None):
                 tail, own = (u <= 0 and li > 0), u >= 3
                 if (li > 0 or u >= 1) and not (mutation == "no_batch_wait" and not (tail or own)):
                     gb = g2 - 2
-                    yield from wait(f"m3{gb & 1}", gb >> 1)
+                    if not (yield from wait(f"m3{gb & 1}", gb >> 1)):
+                        return
                 if tail or own:
                     lj = li - 1 if tail else li
                     w = L - 1 + u if tail else u - 3
@@ -299,11 +341,13 @@ def run(n_configs, n_layers, seed, mutation=None):
                 if li == nl:
                     continue
                 if u == -1:
-                    yield from wait("w2", s)
+                    if not (yield from wait("w2", s)):
+                        return
                     if m.w["wf"] != s:
                         raise Violation("epilogue reads biases of another layer")
                 for t in (0, 1):
-                    yield from wait(f"m2{2 * t + (g2 & 1)}", g2 >> 1)
+                    if not (yield from wait(f"m2{2 * t + (g2 & 1)}", g2 >> 1)):
+                        return
                     if m.tm_c2[t] != g2:
                         raise Violation(f"drain of tile {t} finds {m.tm_c2[t]}, wants {g2}")
                     m.tm_c2[t] = None
@@ -328,7 +372,10 @@ def run(n_configs, n_layers, seed, mutation=None):
             m.pending.remove(g)
         B[g["commit"]].arrive()
 
+    m.last_copy = {}                   # barrier -> completion its last issued copy brings
     for cfg in range(n_configs):
+        if m.abort:
+            break
         # the prior (all threads, then a CTA barrier)
         for z in range(L):
             for p in (0, 1):
@@ -355,9 +402,37 @@ def run(n_configs, n_layers, seed, mutation=None):
                 complete_one(k)
             if not agents and not any(m.queues.values()):
                 break
+            if m.abort and not agents:
+                break                  # every role has left its loops; queued work may remain
             # deadlock: every live agent blocked and nothing queued
-        # the CTA barrier at the end of the configuration needs every queued MMA done
-        assert not m.pending
+        if not m.abort:
+            # the CTA barrier at the end of the configuration needs every queued MMA done
+            assert not m.pending
+
+    # teardown (after the loop over configurations, normal or aborted): the four
+    # issuers commit to bar_fin and one thread waits for it, i.e. for every
+    # tensor-core group they queued; the staging thread waits for the
+    # completions its last W2 / W3 copies bring.  Meanwhile queued copies and MMAs
+    # keep completing in any order.
+    def drain(until):
+        guard = 0
+        while not until():
+            live = [q for q, v in m.queues.items() if v]
+            if not live:
+                raise Violation("teardown waits for work that was never queued")
+            complete_one(m.rng.choice(live))
+            guard += 1
+            if guard > 100_000:
+                raise Violation("teardown does not finish")
+    drain(lambda: not any(m.queues[q] for q in ("qA", "qB", "qC", "qD")))
+    if mutation != "no_copy_drain":
+        drain(lambda: all(B[b].done > n for b, n in m.last_copy.items()))
+    # TMEM is freed and the CTA exits: nothing may still use either
+    if m.pending:
+        raise Violation("TMEM freed while tensor-core work is queued")
+    if m.queues["copy"]:
+        raise Violation("CTA exits while a bulk weight copy still writes shared memory")
+    return m.status
 
 
 @pytest.mark.parametrize("seed", range(24))
@@ -375,3 +450,42 @@ def test_model_catches_planted_mistakes(mutation):
         except Violation:
             return
     raise AssertionError(f"{mutation} went unnoticed")
+
+
+AGENTS = ["A", "Bt", "C", "D", "W", "E"]
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_abort_at_a_random_wait(seed):
+    """A random role's wait runs out at a random point: every role leaves its
+    loops, the status word says GF_ETIMEOUT, queued tensor-core work is done
+    before TMEM is freed and no copy is in flight when the CTA exits."""
+    rng = random.Random(1000 + seed)
+    who, k = rng.choice(AGENTS), rng.randint(1, 400)
+    st = run(n_configs=2, n_layers=3, seed=seed, abort_at=(who, k))
+    # a wait that is never blocked from its k-th on cannot run out: then no abort
+    assert st in (None, "GF_ETIMEOUT")
+
+
+def test_abort_happens_in_most_draws():
+    """The abort schedules are not vacuous: most draws do abort."""
+    hits = 0
+    for seed in range(30):
+        rng = random.Random(5000 + seed)
+        if run(n_configs=1, n_layers=3, seed=seed, abort_at=(rng.choice(AGENTS), rng.randint(1, 200))):
+            hits += 1
+    assert hits >= 15, hits
+
+
+def test_missing_copy_drain_is_caught():
+    """Without the staging thread's wait for its last copies, some abort leaves
+    a bulk copy writing shared memory after the CTA exits."""
+    for seed in range(200):
+        rng = random.Random(9000 + seed)
+        try:
+            run(n_configs=1, n_layers=3, seed=seed, abort_at=(rng.choice(["A", "Bt", "C", "E"]), rng.randint(1, 3)),
+                mutation="no_copy_drain")
+        except Violation as e:
+            assert "bulk weight copy" in str(e)
+            return
+    raise AssertionError("a copy in flight at exit went unnoticed")

@@ -146,3 +146,66 @@ def test_bf16_64_configurations_error_report(orc):
     model = bf16_drift_model(shape.n_layers)["phi"]
     assert np.percentile(e, 99) <= 2 * model["p99"], (np.percentile(e, 99), model)
     assert e.mean() <= 2 * model["mean"], (e.mean(), model)
+
+
+def test_bf16_wait_that_runs_out_reports_timeout_and_recovers(orc):
+    """Failure path of the BF16 kernel's bounded waits, without a GPU fault:
+    with the stall hook on, each block's first conv2 issuer waits for a barrier
+    completion that never comes (65,536 polls, long after every MMA issued so
+    far has finished); that wait gives up, the other roles leave their loops,
+    the block drains its queued tensor-core work and weight copies, frees its
+    tensor memory and returns.  The host sees GF_ETIMEOUT, and the next launch
+    (hook off) is correct."""
+    torch, P = require_gpu()
+    lib = P._abi.load()
+    shape = gi.FlowShape(3, 16, 2, 32, 32)
+    w = gi.init_weights(shape, seed=0)
+    flow = P.Flow(shape, w, precision="bf16")
+    assert P.device_status() == 0
+    assert lib.gf_set_bf16_stall_test(-1) == P._abi.GF_EINVAL
+    try:
+        assert lib.gf_set_bf16_stall_test(1 << 16) == P._abi.GF_OK
+        flow.sample(304, seed=3, counter0=0, phi4=(-6.0, 5.0))
+        torch.cuda.synchronize()
+        st = P.device_status()
+    finally:
+        lib.gf_set_bf16_stall_test(0)
+    assert st == P._abi.GF_ETIMEOUT
+    out = flow.sample(4, seed=11, counter0=0, phi4=(-6.0, 5.0))
+    torch.cuda.synchronize()
+    assert P.device_status() == 0
+    RTOL, LW_RTOL = bf16_tolerances(shape.n_layers)
+    ref = orc.flow_sample(shape, w, -6.0, 5.0, 4, seed=11, counter0=0, bf16_mask=BF16_MODE)
+    assert_sites_close(out.phi.cpu().numpy(), ref["phi"], rtol=RTOL)
+    assert_logw_close(out.logw.cpu().numpy(), ref["logw"], rtol=LW_RTOL)
+
+
+def test_stream_status_slots_attribute_errors_to_their_stream():
+    """gf_set_stream_status_slot: a timeout in a launch on stream 1 lands in
+    stream 1's slot only; stream 2's slot and the process-wide word stay 0."""
+    torch, P = require_gpu()
+    lib = P._abi.load()
+    shape = gi.FlowShape(3, 16, 2, 32, 32)
+    flow = P.Flow(shape, gi.init_weights(shape), precision="bf16")
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    slots = torch.zeros(2, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    assert P.device_status() == 0
+    P.set_stream_status_slot(s1, slots[0:1])
+    P.set_stream_status_slot(s2, slots[1:2])
+    try:
+        lib.gf_set_bf16_stall_test(1 << 16)
+        with torch.cuda.stream(s1):
+            flow.sample(304, seed=1, counter0=0, phi4=(-6.0, 5.0))
+        lib.gf_set_bf16_stall_test(0)
+        with torch.cuda.stream(s2):
+            flow.sample(304, seed=2, counter0=0, phi4=(-6.0, 5.0))
+        torch.cuda.synchronize()
+        assert P.device_status(s1) == P._abi.GF_ETIMEOUT
+        assert P.device_status(s1) == 0              # read and cleared
+        assert P.device_status(s2) == 0
+        assert P.device_status() == 0
+    finally:
+        lib.gf_set_bf16_stall_test(0)
+        P.set_stream_status_slot(s1, None)
+        P.set_stream_status_slot(s2, None)

@@ -35,13 +35,15 @@ def test_results_same_alone_and_in_mix(orc):
     reqs = [serving.Request(i, names[i % 4], float(rng.uniform(-6, -2)), float(rng.uniform(1, 10)),
                             int(rng.integers(5, 300)), 900 + i, arrival=0.0) for i in range(14)]
     budget = 6 << 20
-    srv = serving.Server(models, hbm_budget_bytes=budget, max_active=4, chunk=64)
-    mix, stats = srv.run(reqs, realtime=False)
+    with serving.Server(models, hbm_budget_bytes=budget, max_active=4, chunk=64) as srv:
+        mix, stats = srv.run(reqs, realtime=False)
     assert stats["requests"] == len(reqs)
+    assert stats["failed_requests"] == 0
     assert stats["max_concurrent_requests"] > 1
     assert stats["peak_budget_bytes"] <= budget
     for r in reqs:
-        alone, _ = serving.Server(models, hbm_budget_bytes=budget, max_active=1, chunk=64).run([r], realtime=False)
+        with serving.Server(models, hbm_budget_bytes=budget, max_active=1, chunk=64) as srv1:
+            alone, _ = srv1.run([r], realtime=False)
         a, m = alone[r.rid], mix[r.rid]
         for k in ("phi", "logq", "S", "logw", "chain_idx", "accepted", "mh_state"):
             assert torch.equal(getattr(a, k), getattr(m, k)), (r.rid, k)
@@ -64,7 +66,8 @@ def test_realtime_poisson_loop_reports_latency():
     names = list(models)
     reqs = [serving.Request(i, names[int(rng.integers(4))], -4.0, 5.0, int(rng.integers(64, 512)), i,
                             arrival=float(arr[i])) for i in range(40)]
-    res, stats = serving.Server(models, hbm_budget_bytes=64 << 20, max_active=8, chunk=256).run(reqs)
-    assert stats["requests"] == 40
+    with serving.Server(models, hbm_budget_bytes=64 << 20, max_active=8, chunk=256) as srv:
+        res, stats = srv.run(reqs)
+    assert stats["requests"] == 40 and stats["failed_requests"] == 0
     assert 0 < stats["p50_latency_ms"] <= stats["p99_latency_ms"]
     assert all(r.done >= r.arrival for r in res.values())

@@ -50,6 +50,7 @@ def server(monkeypatch):
         srv.budget, srv.max_active, srv.chunk = budget, max_active, chunk
         srv.device = "cpu"
         srv.streams = [None] * max_active
+        srv._take_error = lambda si: 0            # no device: no kernel errors
         return srv
     return make
 
@@ -93,3 +94,30 @@ def test_bytes_needed_counts_outputs_chain_and_workspace():
     # phi FP32 [B][V] + log q, S, log w, chain index (8 B each) + accept flag (1 B)
     # + 8 B per proposal of one chunk's workspace + the chain state
     assert SV._Active.bytes_needed(r, SV.Model("m", shape, None), 64) == 100 * 64 * 4 + 100 * 33 + 8 * 64 + 48
+
+
+def test_device_error_marks_only_its_request_failed(server):
+    """The status slot read when a request retires belongs to that request's
+    stream: a non-zero slot fails that request alone."""
+    srv = server(budget=1 << 40, max_active=3)
+    on_stream = {}
+
+    def take_error(si):
+        return on_stream.pop(si, 0)
+    srv._take_error = take_error
+    reqs = requests(6)
+    orig_launch = FakeActive.launch_next
+
+    def launch(self):
+        orig_launch(self)
+        if self.req.rid == 4:                 # a kernel of request 4 records GF_ETIMEOUT (-5)
+            on_stream[srv.streams.index(self.stream)] = -5
+    FakeActive.launch_next = launch
+    srv.streams = [f"s{i}" for i in range(3)]
+    try:
+        res, stats = srv.run(reqs, realtime=False)
+    finally:
+        FakeActive.launch_next = orig_launch
+    assert res[4].error == -5
+    assert all(res[i].error == 0 for i in res if i != 4)
+    assert stats["failed_requests"] == 1
