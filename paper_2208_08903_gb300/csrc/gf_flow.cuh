@@ -86,6 +86,13 @@ gf_status launch_flow_fp32(const gf_flow* f, bool inverse, const gf_phi4* phi4, 
                            double* S_out, double* logw_out, cudaStream_t stream);
 gf_status flow_fp32_configure(gf_flow* f);   // chooses FULL/RING, G, smem
 
+// 3D L=16, hidden 32, FP32 (gf_flow_fp32_c32.cu)
+bool fp32_c32_supported(const gf_flow* f);
+gf_status launch_flow_fp32_c32(const gf_flow* f, bool inverse, const gf_phi4* phi4, int64_t B, uint64_t seed,
+                               uint64_t counter0, const float* z_in, float* z_out, const float* phi_in,
+                               float* phi_out, double* logq_out, double* S_out, double* logw_out,
+                               cudaStream_t stream);
+
 // General network (gf_flow_variant.cu)
 gf_status variant_configure(gf_flow* f);     // packed offsets, smem, threads (host only)
 gf_status repack_variant(gf_flow* f, cudaStream_t stream);

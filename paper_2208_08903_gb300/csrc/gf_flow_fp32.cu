@@ -428,6 +428,9 @@ gf_status launch_flow_fp32(const gf_flow* f, bool inverse, const gf_phi4* phi4, 
                            uint64_t seed, uint64_t counter0, const float* z_in, float* z_out,
                            const float* phi_in, float* phi_out, double* logq_out,
                            double* S_out, double* logw_out, cudaStream_t stream) {
+    if (fp32_c32_supported(f))
+        return launch_flow_fp32_c32(f, inverse, phi4, B, seed, counter0, z_in, z_out, phi_in, phi_out, logq_out,
+                                    S_out, logw_out, stream);
     FlowArgs a;
     std::memset(&a, 0, sizeof(a));
     a.W = f->d_packed;

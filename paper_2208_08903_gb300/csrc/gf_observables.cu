@@ -87,24 +87,27 @@ __global__ void __launch_bounds__(kObsThreads) obs_kernel(int L, int64_t V, int6
 // One warp per configuration (grid-stride over configurations), for slices of
 // a multiple of 128 sites and L <= kObsWarpMaxL: lane l reads 16-byte pieces
 // l, l + 32, ... of the field in batches of eight loads, so every lane sees the
-// same slice at the same step; at each slice end the warp reduces its pairs, and
-// the L slice sums (pairs, per-warp shared memory) give M and C(t) without any
-// CTA barrier.  FP64 is slow on this GPU even for one instruction per warp, so
-// 1/V comes from the host (a division per thread was most of the run time).
+// same slice at the same step.  Each lane sums its part of a slice with a
+// compensated sum (Knuth's TwoSum into hi, the exact rounding errors added
+// into lo: seven FP32 operations per site) and, at the slice's end, leaves the
+// pair in the warp's table (dynamic shared memory, [L][32] pairs, lane index
+// xor-swizzled by the slice so stores and the column reads below are free of
+// bank conflicts).  Lane tau then adds up the 32 pairs of slice tau in pair
+// arithmetic; M and C(t) follow from the L slice sums, as pairs, widened to
+// FP64 once per output.  No CTA barrier is needed.  1/V comes from the host.
 constexpr int kObsWarpMaxL = 64;
 __global__ void __launch_bounds__(kObsThreads) obs_warp_kernel(int L, int64_t V, int64_t B, double inv_v,
                                                               const float* __restrict__ phi,
                                                               double* __restrict__ M, double* __restrict__ C) {
-    __shared__ FF sums[kObsThreads / 32][kObsWarpMaxL];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    extern __shared__ FF tab_all[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    FF* tab = tab_all + (size_t)wid * L * 32;
     const int64_t S4 = V / L / 4;                 // 16-byte pieces per slice, a multiple of 32
     const int per = (int)(S4 / 32);               // batches of 32 pieces per slice
     const int nk = L * per;                       // pieces per lane
-    FF* ps = sums[wid];
-    for (int64_t b = (int64_t)blockIdx.x * (kObsThreads / 32) + wid; b < B;
-         b += (int64_t)gridDim.x * (kObsThreads / 32)) {
+    for (int64_t b = (int64_t)blockIdx.x * wpb + wid; b < B; b += (int64_t)gridDim.x * wpb) {
         const float4* q4 = reinterpret_cast<const float4*>(phi + b * V) + lane;
-        FF acc{0.f, 0.f};
+        float hi = 0.f, lo = 0.f;
         for (int k0 = 0; k0 < nk; k0 += 8) {
             float4 v[8];
 #pragma unroll
@@ -113,28 +116,40 @@ __global__ void __launch_bounds__(kObsThreads) obs_warp_kernel(int L, int64_t V,
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 if (k0 + j < nk) {
-                    ff_add(acc, v[j].x);
-                    ff_add(acc, v[j].y);
-                    ff_add(acc, v[j].z);
-                    ff_add(acc, v[j].w);
+                    const float c[4] = {v[j].x, v[j].y, v[j].z, v[j].w};
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float s = hi + c[q];
+                        const float bp = s - hi;
+                        lo += (hi - (s - bp)) + (c[q] - bp);
+                        hi = s;
+                    }
                     if ((k0 + j + 1) % per == 0) {             // end of slice (k0 + j) / per
-                        const FF t = warp_sum_ff(acc);
-                        if (lane == 0) ps[(k0 + j) / per] = t;
-                        acc = FF{0.f, 0.f};
+                        const int tau = (k0 + j) / per;
+                        tab[tau * 32 + ((lane ^ tau) & 31)] = FF{hi, lo};
+                        hi = 0.f;
+                        lo = 0.f;
                     }
                 }
             }
         }
         __syncwarp();
+        for (int tau = lane; tau < L; tau += 32) {
+            FF acc{0.f, 0.f};
+            for (int i = 0; i < 32; ++i) ff_add(acc, tab[tau * 32 + ((i ^ tau) & 31)]);
+            tab[tau * 32 + ((0 ^ tau) & 31)] = acc;     // the slice sum, in lane 0's entry
+        }
+        __syncwarp();
+        const auto slice = [&](int tau) -> FF { return tab[tau * 32 + (tau & 31)]; };
         if (M && lane == 0) {
             FF m{0.f, 0.f};
-            for (int tau = 0; tau < L; ++tau) ff_add(m, ps[tau]);
+            for (int tau = 0; tau < L; ++tau) ff_add(m, slice(tau));
             M[b] = ff_to_double(m) * inv_v;
         }
         if (C) {
             for (int t = lane; t < L; t += 32) {
                 FF a{0.f, 0.f};
-                for (int tau = 0, u = t; tau < L; ++tau, u = (u + 1 == L) ? 0 : u + 1) ff_fma(a, ps[tau], ps[u]);
+                for (int tau = 0, u = t; tau < L; ++tau, u = (u + 1 == L) ? 0 : u + 1) ff_fma(a, slice(tau), slice(u));
                 C[b * L + t] = ff_to_double(a) * inv_v;
             }
         }
@@ -270,9 +285,11 @@ gf_status gf_observables(int32_t nd, int32_t L, int64_t B, const float* d_phi, d
     const int64_t V = ipow(L, nd);
     const int64_t S = V / L;
     if (S % 128 == 0 && L <= kObsWarpMaxL && (reinterpret_cast<uintptr_t>(d_phi) & 15) == 0) {
-        constexpr int wpb = kObsThreads / 32;
-        const unsigned grid = (unsigned)std::min<int64_t>((B + wpb - 1) / wpb, (int64_t)num_sms() * 8);
-        obs_warp_kernel<<<grid, kObsThreads, 0, stream>>>(L, V, B, 1.0 / (double)V, d_phi, d_M_out, d_C_out);
+        // warps per block: each warp's table is L x 32 pairs; at most 48 KB per block
+        const int wpb = (int)std::max<int64_t>(1, std::min<int64_t>(kObsThreads / 32, 49152 / (256 * (int64_t)L)));
+        const size_t smem = (size_t)wpb * L * 32 * sizeof(FF);
+        const unsigned grid = (unsigned)std::min<int64_t>((B + wpb - 1) / wpb, (int64_t)num_sms() * 16);
+        obs_warp_kernel<<<grid, 32 * wpb, smem, stream>>>(L, V, B, 1.0 / (double)V, d_phi, d_M_out, d_C_out);
     } else {
         const size_t smem = sizeof(FF) * (size_t)L;
         const unsigned grid = (unsigned)std::min<int64_t>(B, (int64_t)num_sms() * 8);

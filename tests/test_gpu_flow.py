@@ -22,7 +22,8 @@ CASES = [
     (gi.FlowShape(3, 2, 4, 8, 8), -6.0, 5.0, 5),                     # smallest 3D lattice
     (gi.FlowShape(3, 4, 6, 16, 16, use_final_tanh=False), -6.0, 5.0, 6),
     (gi.FlowShape(2, 32, 24, 32, 32), -4.0, 8.0, 6),                 # c2 shape, RING
-    (gi.FlowShape(3, 16, 16, 32, 32), -6.0, 5.0, 3),                 # c3 shape, RING
+    (gi.FlowShape(3, 16, 16, 32, 32), -6.0, 5.0, 3),                 # c3 shape (3D L=16 C=32 kernel)
+    (gi.FlowShape(3, 16, 3, 32, 32, use_final_tanh=False), -2.0, 1.0, 5),   # odd layer count, no tanh
     (gi.FlowShape(2, 64, 12, 16, 16), -3.0, 4.0, 2),                 # large 2D, RING
 ]
 
