@@ -40,10 +40,15 @@ typedef enum {
 
 typedef enum {
     GF_PREC_FP32 = 0,             /* FP32 convolutions, FP64 sums                  */
-    GF_PREC_BF16CONV_FP64RED = 1  /* BF16 tensor-core conv1/conv2/conv3, FP32
-                                     accumulate; log-det, z^2 and action sums to
-                                     FP64 accuracy (FP32 pairs per thread, FP64
-                                     across the block) (3D, L=16, C=32 only)     */
+    GF_PREC_BF16CONV_FP64RED = 1  /* tensor-core convolutions with FP32
+                                     accumulation: conv2 (the dominant one) with
+                                     BF16 operands (h1, W2), conv1 and conv3 with
+                                     FP16 operands (the masked field, W1; h2, W3),
+                                     so |field| and |h2| must stay below 65504 (a
+                                     non-finite s or t records GF_EDEVICE);
+                                     log-det, z^2 and action sums to FP64
+                                     accuracy (FP32 pairs per thread, FP64 across
+                                     the block) (3D, L=16, C=32 only)             */
 } gf_precision;
 
 /* Flow shape (paper Sec. 3, model parameters: n_layers, hidden_sizes =

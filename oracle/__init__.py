@@ -26,7 +26,11 @@ _lib = None
 BF16_H1, BF16_W2, BF16_H2, BF16_W3, BF16_W1, F32_IO, BF16_X1 = 1, 2, 4, 8, 16, 32, 64
 F32_ACC = 128        # FP32-accumulating model (tolerance experiment only)
 Z_JITTER = 256       # prior perturbed within its FP32 test bound (tolerance experiment only)
-BF16_MODE = BF16_H1 | BF16_W2 | BF16_H2 | BF16_W3 | BF16_W1 | F32_IO | BF16_X1
+F16_X1, F16_W1, F16_H2, F16_W3 = 512, 1024, 2048, 4096
+# the tensor-core precision mode: bf16 for conv2's operands (h1, W2), FP16 for
+# conv1's input and weights and for conv3's operands (h2, W3), FP32 prior
+BF16_MODE = BF16_H1 | BF16_W2 | F16_H2 | F16_W3 | F16_W1 | F32_IO | F16_X1
+ALL_BF16_MODE = BF16_H1 | BF16_W2 | BF16_H2 | BF16_W3 | BF16_W1 | F32_IO | BF16_X1
 
 
 def build(force: bool = False) -> str:

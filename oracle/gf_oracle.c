@@ -181,6 +181,18 @@ static double bf16_round(double x) {
     return ldexp(r, e - 8);
 }
 
+/* Round to the nearest IEEE binary16 value, ties to even: 11 significant bits
+ * for |x| >= 2^-14, multiples of 2^-24 below (subnormals), infinity from
+ * 65520 (half-way between the largest finite value 65504 and 2^16) up. */
+static double f16_round(double x) {
+    if (x == 0.0 || !isfinite(x)) return x;
+    if (fabs(x) >= 65520.0) return copysign(INFINITY, x);
+    int e; frexp(x, &e);                          /* |x| in [2^(e-1), 2^e) */
+    int q = e - 11;                               /* quantum of 11 significant bits */
+    if (q < -24) q = -24;
+    return ldexp(nearbyint(ldexp(x, -q)), q);     /* default mode: ties to even */
+}
+
 static double lrelu(double v, double a) { return v > 0.0 ? v : a * v; }
 
 static int n_taps(const gfo_shape* sh) { return (int)ipow(sh->ksize, sh->nd); }
@@ -221,9 +233,9 @@ static void conv(int64_t V, int T, const int64_t* nbr, int Cin, int Cout,
      * products below would see if each were rounded where it is read) */
     const int64_t nw = (int64_t)Cout * Cin * T;
     double* Wr = NULL;
-    if (round_w) {
+    if (round_w) {                    /* 1: bf16, 2: FP16 */
         Wr = (double*)malloc(sizeof(double) * (nw > 0 ? nw : 1));
-        for (int64_t k = 0; k < nw; ++k) Wr[k] = bf16_round(W[k]);
+        for (int64_t k = 0; k < nw; ++k) Wr[k] = round_w == 2 ? f16_round(W[k]) : bf16_round(W[k]);
         W = Wr;
     }
     for (int64_t n = 0; n < V; ++n) {
@@ -274,8 +286,8 @@ static void net_free(const gfo_shape* sh, net_buf* nb) {
  * tanh on channel 0 (s) only when use_final_tanh; channel 1 is t. */
 static void net_forward(const gfo_shape* sh, layer_w lw, int32_t bf16, int64_t V, int T,
                         const int64_t* nbr, const double* y, net_buf* nb) {
-    if (bf16 & GFO_BF16_X1) {          /* the BF16 variant's conv1 reads the field in bf16 */
-        for (int64_t n = 0; n < V; ++n) nb->yin[n] = bf16_round(y[n]);
+    if (bf16 & (GFO_BF16_X1 | GFO_F16_X1)) {  /* the tensor-core mode's conv1 reads a rounded field */
+        for (int64_t n = 0; n < V; ++n) nb->yin[n] = (bf16 & GFO_F16_X1) ? f16_round(y[n]) : bf16_round(y[n]);
         y = nb->yin;
     }
     const int f32acc = (bf16 & GFO_F32_ACC) != 0;
@@ -283,15 +295,18 @@ static void net_forward(const gfo_shape* sh, layer_w lw, int32_t bf16, int64_t V
     for (int j = 0; j <= sh->n_hidden; ++j) {
         const int cin = conv_cin(sh, j), cout = conv_cout(sh, j);
         const int head = j == sh->n_hidden;
-        const int round_w = head ? (bf16 & GFO_BF16_W3)
-                          : j == 0 ? (bf16 & GFO_BF16_W1) : (bf16 & GFO_BF16_W2);
+        const int round_w = head ? ((bf16 & GFO_F16_W3) ? 2 : (bf16 & GFO_BF16_W3) ? 1 : 0)
+                          : j == 0 ? ((bf16 & GFO_F16_W1) ? 2 : (bf16 & GFO_BF16_W1) ? 1 : 0)
+                                   : ((bf16 & GFO_BF16_W2) ? 1 : 0);
         double* out = head ? nb->spre : nb->pre[j];
         conv(V, T, nbr, cin, cout, lw.W[j], lw.b[j], round_w, f32acc, in, out);
         if (head) break;
-        const int round_h = j == 0 ? (bf16 & GFO_BF16_H1) : (bf16 & GFO_BF16_H2);
+        const int round_h = j == 0 ? ((bf16 & GFO_BF16_H1) ? 1 : 0)
+                                   : ((bf16 & GFO_F16_H2) ? 2 : (bf16 & GFO_BF16_H2) ? 1 : 0);
         for (int64_t k = 0; k < V * cout; ++k) {
             nb->post[j][k] = lrelu(nb->pre[j][k], sh->leaky_slope);
-            if (round_h) nb->post[j][k] = bf16_round(nb->post[j][k]);
+            if (round_h == 1) nb->post[j][k] = bf16_round(nb->post[j][k]);
+            else if (round_h == 2) nb->post[j][k] = f16_round(nb->post[j][k]);
         }
         in = nb->post[j];
     }

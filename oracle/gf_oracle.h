@@ -87,7 +87,16 @@ enum {
      * +-2^-20 (the relative bound to which an FP32 Box-Muller prior is tested
      * against this oracle's), from philox(key=(seed, 1), ctr=(counter0+b, n,
      * 0, 5)) word 0, before the FP32 rounding. */
-    GFO_Z_JITTER = 256
+    GFO_Z_JITTER = 256,
+    /* FP16 (IEEE binary16, round to nearest even, subnormals kept, overflow to
+     * infinity) instead of bf16 at four rounding points: conv1's input and
+     * weights, the later hidden activations (h2) and the head's weights (the
+     * tensor-core precision mode rounds those to FP16, the dominant
+     * convolution's operands h1 and W2 to bf16). */
+    GFO_F16_X1 = 512,
+    GFO_F16_W1 = 1024,
+    GFO_F16_H2 = 2048,
+    GFO_F16_W3 = 4096
 };
 
 typedef struct {

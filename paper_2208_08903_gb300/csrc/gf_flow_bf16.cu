@@ -1,11 +1,14 @@
 // gf_flow_bf16.cu -- fused coupling stack with conv1, conv2 and conv3 on the
-// 5th-generation tensor cores (tcgen05, BF16 operands, FP32 accumulation in
+// 5th-generation tensor cores (tcgen05, 16-bit operands, FP32 accumulation in
 // TMEM), for 3D lattices with L = 16 and hidden width 32.
 //
 // Paper arXiv:2208.08903 Sec. 1 (affine coupling layers, Jacobian, model
-// density, action); precision split of this variant: the convolutions read
-// BF16 operands (the masked field, h1, h2 and the weights) and accumulate in
-// FP32; the field x and the affine update stay FP32; each thread sums its
+// density, action); precision split of this variant: conv2 (95 % of the
+// FLOPs) reads BF16 operands (h1 and W2); conv1 and conv3 read FP16 operands
+// (the masked field and W1; h2 and W3) at the same tensor-core rate, because
+// the BF16 rounding of those weights moved log w the most (on a trained 3D
+// flow it cost a fifth of the MH acceptance); every convolution accumulates
+// in FP32; the field x and the affine update stay FP32; each thread sums its
 // log-det terms, z^2 and action terms in FP32 pairs (about 2^-48 relative, with
 // no FP64 instruction per site), and the block sums, log q and log w are FP64.
 //
@@ -13,7 +16,7 @@
 // lattice is walked along z one 256-site slice at a time:
 //   conv1: per parity tile (M = 128 sites of one parity, K = the 13 or 14 taps
 //   that reach fixed sites, padded to 16, N = 32) -> h1 slice (BF16)
-//   conv2 as an implicit GEMM -> h2 slice (BF16)
+//   conv2 as an implicit GEMM -> h2 slice (FP16)
 //   conv3 as an implicit GEMM (rows s and t) -> affine update of x
 // Implicit GEMM: per z-slice two M = 128 tiles (8 y-rows x 16 x); K = the 9
 // (dz,dy) taps x 32 channels in steps of 16; the three dx weight sets are
@@ -27,7 +30,7 @@
 // half-warp = 16 TMEM lanes).
 // Warp-specialised pipeline (mbarriers only, no CTA barrier):
 // eight conv1 worker warps gather each slice's conv1 operand (the field at the
-// live taps, BF16) two slices ahead and turn the conv1 accumulators into h1
+// live taps, FP16) two slices ahead and turn the conv1 accumulators into h1
 // (four h1 slots); four single threads, one per sub-partition, queue the
 // tensor-core work: conv2 of M-tile 0, conv2 of M-tile 1 (one TMEM buffer per
 // M-tile), the conv3 batches (once h2[u] exists, one batch with every
@@ -49,6 +52,7 @@
 #include <cstring>
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "gf_flow.cuh"
 
@@ -199,6 +203,8 @@ __device__ __forceinline__ uint64_t desc_add(uint64_t d, uint32_t off) {
 // Instruction descriptors: D = F32, A = B = BF16, both K-major, M = 128, N = 96 / 32.
 constexpr uint32_t kIdesc96 = (1u << 4) | (1u << 7) | (1u << 10) | ((96u >> 3) << 17) | ((128u >> 4) << 24);
 constexpr uint32_t kIdesc32 = (1u << 4) | (1u << 7) | (1u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+// D = F32, A = B = FP16 (conv1 and conv3), K-major, M = 128, N = 32.
+constexpr uint32_t kIdesc32h = (1u << 4) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
 
 struct Bf16Args {
     const unsigned char* Wl;   // per-layer blocks of kLayerBytes
@@ -220,13 +226,23 @@ __device__ __forceinline__ int wrap16(int v) { return v & 15; }
 // halo-row site index of interior (y, x), y in -1..16
 __device__ __forceinline__ int hsite(int y, int x) { return (y + 1) * 16 + x; }
 
-// Stores 8 channels (one channel group) of a site in BF16, plus the periodic
-// halo copy when the row is y = 0 or y = 15.
+// Stores 8 channels (one channel group) of a site in BF16 (h1, conv2's A
+// operand) or FP16 (h2, conv3's A operand), plus the periodic halo copy when
+// the row is y = 0 or y = 15.
+template <bool F16>
 __device__ __forceinline__ void store8(unsigned char* slot, int cg, int y, int x, const float* v) {
-    __align__(16) __nv_bfloat162 p[4];
+    uint4 w;
+    if (F16) {
+        __align__(16) __half2 p[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) p[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
-    const uint4 w = *reinterpret_cast<const uint4*>(p);
+        for (int i = 0; i < 4; ++i) p[i] = __floats2half2_rn(v[2 * i], v[2 * i + 1]);
+        w = *reinterpret_cast<const uint4*>(p);
+    } else {
+        __align__(16) __nv_bfloat162 p[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) p[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+        w = *reinterpret_cast<const uint4*>(p);
+    }
     unsigned char* base = slot + (size_t)cg * kCgStride;
     *reinterpret_cast<uint4*>(base + hsite(y, x) * 16) = w;
     if (y == 0) *reinterpret_cast<uint4*>(base + hsite(16, x) * 16) = w;
@@ -253,14 +269,14 @@ __host__ __device__ constexpr int tap_of(int need, int k) {
     return -1;
 }
 
-// conv1's bias rides in the last two K columns (A = 1, B = b1 split into a BF16
-// head and a BF16 remainder, so the FP32 accumulator adds b1 to about 2^-17);
+// conv1's bias rides in the last two K columns (A = 1, B = b1 split into an FP16
+// head and an FP16 remainder, so the FP32 accumulator adds b1 to about 2^-22);
 // every tap set has at most 14 live taps.
 constexpr int kBiasK = 14;
 static_assert(tap_of(0, kBiasK) < 0 && tap_of(1, kBiasK) < 0, "conv1 bias columns must be padding");
 
 // conv1 A operand row of one site: the masked field at its 13 or 14 live taps
-// (BF16), zero-padded, then the two bias columns (1.0), stored as the row's two
+// (FP16), zero-padded, then the two bias columns (1.0), stored as the row's two
 // 16-byte core-matrix pieces.  yr[dy] = row offset, ys[dy] = that row's column
 // swizzle, xc[dx] = column.
 template <int NEED>
@@ -275,9 +291,9 @@ __device__ __forceinline__ void im2col_row(unsigned char* a_tile, int r, const f
     }
 #pragma unroll
     for (int kg = 0; kg < 2; ++kg) {
-        __align__(16) __nv_bfloat162 p[4];
+        __align__(16) __half2 p[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) p[i] = __floats2bfloat162_rn(v[kg * 8 + 2 * i], v[kg * 8 + 2 * i + 1]);
+        for (int i = 0; i < 4; ++i) p[i] = __floats2half2_rn(v[kg * 8 + 2 * i], v[kg * 8 + 2 * i + 1]);
         *reinterpret_cast<uint4*>(a_tile + kg * 2048 + r * 16) = *reinterpret_cast<const uint4*>(p);
     }
 }
@@ -317,7 +333,7 @@ __device__ __forceinline__ void issue_conv3_batch(uint64_t a, uint64_t b0, uint3
             for (int mt = 0; mt < 2; ++mt) {
                 const uint64_t ad = desc_add(a, (uint32_t)((2 * k * kCgStride + (mt * 8 + dyi) * 256) >> 4));
                 const uint64_t bd = desc_add(b0, (uint32_t)(dyi * b_tap + k * b_k));
-                mma_bf16(region + (uint32_t)mt * 32, ad, bd, kIdesc32, (dyi | k) ? 1u : 0u);
+                mma_bf16(region + (uint32_t)mt * 32, ad, bd, kIdesc32h, (dyi | k) ? 1u : 0u);
             }
         }
     }
@@ -350,7 +366,7 @@ __device__ __forceinline__ void conv2_epi_store(const Conv2Parts& P, unsigned ch
                             __shfl_sync(0xffffffffu, P.pp[ch], src_p) + b2[ch];
             o[c] = s > 0.f ? s : slope * s;
         }
-        store8(slot, hf * 2 + g, y, xx, o);
+        store8<true>(slot, hf * 2 + g, y, xx, o);
     }
 }
 
@@ -370,7 +386,7 @@ __device__ __forceinline__ void conv3_epi_load(float (&p)[3][8], uint32_t rm, ui
 }
 __device__ __forceinline__ void conv3_epi_finish(const float (&p)[3][8], int z, float b3s, float b3t, float* x,
                                                  int frozen, int use_tanh, bool inverse, FF& logdet, int mt,
-                                                 int q, int lane) {
+                                                 int q, int lane, int32_t* status) {
     const int y = mt * 8 + q * 2 + (lane >> 4), xx = lane & 15;
     float st[6];
 #pragma unroll
@@ -381,6 +397,9 @@ __device__ __forceinline__ void conv3_epi_finish(const float (&p)[3][8], int z, 
                        b3s;
     const float tt = st[3] + __shfl_sync(0xffffffffu, st[1], src_m) + __shfl_sync(0xffffffffu, st[5], src_p) + b3t;
     if (((z + y + xx) & 1) != frozen) {
+        // FP16 operands of conv1 / conv3 overflow beyond 65504: a non-finite
+        // s or t (from a field or h2 value out of that range) is reported
+        if (!isfinite(spre) || !isfinite(tt)) set_status(status, GF_EDEVICE);
         const float s = use_tanh ? tanhf(spre) : spre;
         float& xv = x[(z * 16 + y) * kXRow + (xx ^ xswz(y))];
         if (!inverse) xv = fmaf(xv, expf(s), tt);
@@ -638,7 +657,7 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
                         for (int pc = 0; pc < 2; ++pc)
                             mma_bf16(tmem + (uint32_t)(kTmemC1 + 64 * b + 32 * pc),
                                      desc_add(a1c, (uint32_t)((b * kIm2colBufBytes + pc * 4096) >> 4)),
-                                     desc_add(b1d, (uint32_t)(((frozen ^ pc) & 1) * 64)), kIdesc32, 0u);
+                                     desc_add(b1d, (uint32_t)(((frozen ^ pc) & 1) * 64)), kIdesc32h, 0u);
                         mma_commit(bar_c1 + b);
                     }
                 }
@@ -746,7 +765,7 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
                             const float hv = d[cg * 8 + i];             // b1 is in the MMA
                             o[i] = hv > 0.f ? hv : a.slope * hv;
                         }
-                        store8(slot, cg, y, xs, o);
+                        store8<false>(slot, cg, y, xs, o);
                     }
                     fence_proxy_async();
                     mbar_arrive(bar_h1 + (c & 3));
@@ -794,7 +813,7 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
                         // layer li's biases replace li-1's at u = -1, after its slice 14
                         const bool prev = u == 0 && li < nl;
                         conv3_epi_finish(p, (w + rot(lj)) & 15, prev ? b3s_p : b3s, prev ? b3t_p : b3t, x,
-                                         lay(lj) & 1, a.use_tanh, INVERSE, logdet, mt, q, lane);
+                                         lay(lj) & 1, a.use_tanh, INVERSE, logdet, mt, q, lane, a.status);
                         if (w == kL - 1 || (w >= 5 && (w & 3) == 1))   // checkpoint: slices <= w updated
                             mbar_arrive(bar_x + (w == kL - 1 ? 3 : (w - 5) >> 2));
                     }
@@ -900,10 +919,10 @@ constexpr size_t kSmemBytes = (size_t)kLayerBytes + 7 * (size_t)kSlotBytes + (si
 static_assert(kSmemBytes <= 227 * 1024, "shared memory budget");
 
 // canonical FP32 -> per-layer block: W2 [tap9][kg][dxi*32 + o][8] bf16,
-// W3 [dy3][kg][d*8 + dxi*2 + j][8] bf16 (tap (d, dy, dxi); j = 0: s, 1: t; rows
+// W3 [dy3][kg][d*8 + dxi*2 + j][8] fp16 (tap (d, dy, dxi); j = 0: s, 1: t; rows
 // with (row & 7) >= 6 or row >= 24 zero),
-// then W1 as the two conv1 B operands [need][kg][o][8] bf16 (tap_of order; K
-// columns 14 and 15 hold b1's BF16 head and remainder), then FP32 b1, b2, b3.
+// then W1 as the two conv1 B operands [need][kg][o][8] fp16 (tap_of order; K
+// columns 14 and 15 hold b1's FP16 head and remainder), then FP32 b1, b2, b3.
 __global__ void repack_bf16_kernel(const float* __restrict__ canon, int64_t cstride, int n_layers,
                                    unsigned char* __restrict__ out) {
     constexpr int n2 = 9 * 4 * 96 * 8, n3 = 3 * 4 * 32 * 8, n1 = 2 * 2 * 32 * 8;
@@ -932,14 +951,14 @@ __global__ void repack_bf16_kernel(const float* __restrict__ canon, int64_t cstr
             const bool live = d < 3 && rr < 6;
             const int t = live ? d * 9 + dyi * 3 + dxi : 0;
             const float v = live ? W3[((int64_t)j * kC + kg * 8 + e) * kT + t] : 0.f;
-            reinterpret_cast<__nv_bfloat16*>(blk + kW2Bytes)[r3] = __float2bfloat16_rn(v);
+            reinterpret_cast<__half*>(blk + kW2Bytes)[r3] = __float2half_rn(v);
         } else if (r < n2 + n3 + n1) {
             const int r1 = (int)(r - n2 - n3);
             const int e = r1 & 7, o = (r1 >> 3) & 31, kg = (r1 >> 8) & 1, need = r1 >> 9;
             const int k = kg * 8 + e, t = tap_of(need, k);
-            const float bh = __bfloat162float(__float2bfloat16_rn(b1[o]));
+            const float bh = __half2float(__float2half_rn(b1[o]));
             const float v = k == kBiasK ? b1[o] : k == kBiasK + 1 ? b1[o] - bh : t < 0 ? 0.f : W1[(int64_t)o * kT + t];
-            reinterpret_cast<__nv_bfloat16*>(blk + kW2Bytes + kW3Bytes)[r1] = __float2bfloat16_rn(v);
+            reinterpret_cast<__half*>(blk + kW2Bytes + kW3Bytes)[r1] = __float2half_rn(v);
         } else {
             const int f = (int)(r - n2 - n3 - n1);
             float v = 0.f;

@@ -96,6 +96,21 @@ def load_checkpoint(path: str, flow: api.Flow) -> tuple[TrainState, dict]:
     return st, json.loads(str(z["meta"]))
 
 
+CHECKPOINT_DIR = __import__("os").path.join(__import__("os").path.dirname(__file__), "checkpoints")
+
+
+def load_weights(path: str, shape=None):
+    """FP64 canonical weights of a weights-only checkpoint (the `weights`,
+    `shape`, `leaky_slope` entries of an .npz written by save_checkpoint or
+    shipped in checkpoints/); checks the stored shape against `shape`."""
+    z = np.load(path)
+    if shape is not None:
+        want = [shape.nd, shape.L, shape.n_layers, shape.c1, shape.c2, int(bool(shape.use_final_tanh))]
+        if z["shape"].tolist() != want or float(z["leaky_slope"]) != float(shape.leaky_slope):
+            raise ValueError(f"checkpoint shape {z['shape'].tolist()} does not match {want}")
+    return z["weights"].astype(np.float64)
+
+
 def evaluate(flow: api.Flow, phi4, n_proposals: int, batch: int, seed: int, counter0: int = 0,
              mh_seed: int = 1, sampler: str = "fused", keep_logw: bool = False) -> dict:
     """Acceptance of an MH independence chain over n_proposals flow samples,

@@ -1,11 +1,11 @@
-"""Derives the parity tolerances of the BF16 tensor-core path from the oracle alone.
+"""Derives the parity tolerances of the tensor-core path from the oracle alone.
 
-The BF16 kernel rounds conv1's input, the conv weights, h1 and h2 to bf16 at
-the same points as the oracle's BF16-emulation mode, but it forms every
-convolution sum in FP32 on the tensor cores where the oracle sums in FP64.
-So the two reach each bf16 rounding with values that differ at the FP32
-level, and a value that sits within that difference of a rounding boundary
-rounds the other way on one side.  Such a flip moves s and t of the nearby
+The tensor-core kernel rounds h1 and W2 to bf16 and conv1's input and
+weights, h2 and W3 to FP16, at the same points as the oracle's emulation mode
+(oracle.BF16_MODE), but it forms every convolution sum in FP32 on the tensor
+cores where the oracle sums in FP64.  So the two reach each rounding with
+values that differ at the FP32 level, and a value that sits within that
+difference of a rounding boundary rounds the other way on one side.  Such a flip moves s and t of the nearby
 updated sites by part of a bf16 ulp, and the later coupling layers carry it on.
 
 The kernel's prior sample also differs from the oracle's at the FP32 level:

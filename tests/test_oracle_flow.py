@@ -23,11 +23,13 @@ def lrelu(v, a):
     return np.where(v > 0, v, a * v)
 
 
-def scipy_net(shape, w, layer, y, round_fn=None, flags=0):
+def scipy_net(shape, w, layer, y, round_fn=None, flags=0, round16=None):
     """s, t of one coupling network (any hidden_sizes, odd kernel size) with
     scipy's periodic correlate.  flags: the oracle's bf16 rounding points (1 h1,
     2 middle weights, 4 later hidden activations, 8 head weights, 16 first
-    weights, 64 the network input)."""
+    weights, 64 the network input) and FP16 ones (512 the network input, 1024
+    first weights, 2048 later hidden activations, 4096 head weights), applied
+    with round_fn (bf16) and round16 (FP16)."""
     d = gi.split_layer(shape, w, layer)
     nd, L, k = shape.nd, shape.L, shape.ksize
     grid = [L] * nd
@@ -44,19 +46,27 @@ def scipy_net(shape, w, layer, y, round_fn=None, flags=0):
             out[o] = acc
         return out
 
-    if flags & 64:
+    r16 = (lambda a: a) if round16 is None else round16
+    if flags & 512:
+        y = r16(y)
+    elif flags & 64:
         y = rw(y)
     h = y.reshape([1] + grid)
     nh = len(shape.hidden)
     for j in range(nh + 1):
         W = d[f"W{j + 1}"]
         wflag = 8 if j == nh else (16 if j == 0 else 2)
-        if flags & wflag:
+        f16flag = 4096 if j == nh else (1024 if j == 0 else 0)
+        if flags & f16flag:
+            W = r16(W)
+        elif flags & wflag:
             W = rw(W)
         h = conv(h, W, d[f"b{j + 1}"])
         if j < nh:
             h = lrelu(h, shape.leaky_slope)
-            if flags & (1 if j == 0 else 4):
+            if j > 0 and flags & 2048:
+                h = r16(h)
+            elif flags & (1 if j == 0 else 4):
                 h = rw(h)
     s = np.tanh(h[0]) if shape.use_final_tanh else h[0]
     return s.ravel(), h[1].ravel()
@@ -113,6 +123,38 @@ def test_variant_weight_layout_and_default_net_unchanged():
     T = 25
     assert v.layer_params() == (4 * T + 4) + (3 * 4 * T + 3) + (5 * 3 * T + 5) + (2 * 5 * T + 2)
     assert [n for n, _ in v.layer_blocks()] == ["W1", "b1", "W2", "b2", "W3", "b3", "W4", "b4"]
+
+
+def test_fp16_rounding_points_vs_numpy(orc):
+    """The FP16 rounding points (conv1 input and weights, h2, head weights)
+    against numpy's float16 conversion (round to nearest even, subnormals,
+    overflow to infinity), alone and in the tensor-core mode's combination."""
+    def r16(a):
+        with np.errstate(over="ignore"):
+            return np.asarray(a, np.float64).astype(np.float16).astype(np.float64)
+
+    def rbf(a):
+        torch = pytest.importorskip("torch")
+        a = np.asarray(a)
+        return torch.from_numpy(a.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy().reshape(a.shape)
+
+    shape = gi.FlowShape(3, 3, 1, 8, 8)
+    w = gi.init_weights(shape, seed=8)
+    y = gi.random_field(3, 3, 1, seed=2)[0]
+    for flags in (512, 1024, 2048, 4096, orc.BF16_MODE & ~32):
+        s, t = orc.coupling_net(shape, w, 0, y, bf16_mask=flags)
+        rs, rt = scipy_net(shape, w, 0, y, round_fn=rbf, flags=flags, round16=r16)
+        assert np.allclose(s, rs, rtol=1e-9, atol=1e-10), flags
+        assert np.allclose(t, rt, rtol=1e-9, atol=1e-10), flags
+    # overflow, subnormals and ties through the input rounding point (a net whose
+    # conv1 is the identity on the centre tap)
+    shape1 = gi.FlowShape(2, 3, 1, hidden_sizes=(), ksize=1, use_final_tanh=False)
+    w1 = np.array([1.0, 0.0, 0.0, 0.0])               # W1 [2][1][1] = (1, 0), b1 = (0, 0)
+    for v in (70000.0, 65519.0, 65520.0, 3e-7, 1e-8, 1.0 + 2.0**-11, 1.0 + 3 * 2.0**-11, 2049.0):
+        yv = np.zeros(9)
+        yv[0] = v
+        s, _ = orc.coupling_net(shape1, w1, 0, yv, bf16_mask=512)
+        assert s[0] == r16(v) or (np.isinf(s[0]) and np.isinf(r16(v))), v
 
 
 def test_bf16_rounding_points_vs_torch(orc):
