@@ -435,6 +435,12 @@ def bench_extra(args, dev, flush, pk):
     out["fused_fp32"] = sampling_rate("fused")
     torch.cuda.empty_cache()
 
+    # equal acceptance on the trained 3D flow shipped in checkpoints/: the
+    # tensor-core, fused FP32 and plain FP32 samplers on the same proposals
+    if args.workload == "c3":
+        out["trained_c3_equal_acceptance"] = trained_acceptance(shape, phi4, n=args.acceptance_proposals)
+        torch.cuda.empty_cache()
+
     # reverse-KL training step, 2D L=32, 24 couplings, hidden 32, batch 1024, Adam
     W2 = gi.WORKLOADS["c2"]
     f2 = P.Flow(W2["shape"], gi.init_weights(W2["shape"]))
@@ -548,6 +554,33 @@ def bench_extra(args, dev, flush, pk):
         sweep[str(Bs)] = Bs / (float(np.mean(t)) / 1e3)
     out["c1_batch_sweep_configs_per_s"] = sweep
     return out
+
+
+def trained_acceptance(shape, phi4, n=32768):
+    """MH acceptance (binomial error), ESS, tau_int(|M|) and configs/s of the
+    three samplers on the trained 3D flow, all on the same n proposals."""
+    import paper_2208_08903_gb300 as P
+    from paper_2208_08903_gb300 import train as T
+    w = T.load_weights(os.path.join(T.CHECKPOINT_DIR, "c3_L16_16layers_15k.npz"), shape)
+    f32 = P.Flow(shape, w)
+    arms = {"tensor_core": (P.Flow(shape, w, precision="bf16"), "fused"), "fused_fp32": (f32, "fused"),
+            "plain_fp32": (f32, "unfused")}
+    ev = {k: T.evaluate(f, phi4, n, 4096, seed=12347, sampler=kind, keep_logw=True) for k, (f, kind) in arms.items()}
+    res = {"checkpoint": "checkpoints/c3_L16_16layers_15k.npz (15,000 reverse-KL Adam steps, batch 64)",
+           "proposals": n}
+    for k, e in ev.items():
+        res[k] = {kk: e[kk] for kk in ("acceptance", "acceptance_binomial_err", "ess", "abs_M", "tau_int_abs_M",
+                                       "tau_int_err")}
+        res[k]["configs_per_s"] = n / e["seconds"]
+    res["tensor_core"]["decisions_same_as_fp32"] = T.decision_agreement(ev["tensor_core"], ev["fused_fp32"])
+    res["plain_fp32"]["decisions_same_as_fused"] = T.decision_agreement(ev["plain_fp32"], ev["fused_fp32"])
+    d = res["tensor_core"]["acceptance"] - res["fused_fp32"]["acceptance"]
+    se = math.hypot(res["tensor_core"]["acceptance_binomial_err"], res["fused_fp32"]["acceptance_binomial_err"])
+    res["acceptance_difference_sigma"] = d / se if se > 0 else None
+    res["speedup_tensor_core_vs_plain_fp32"] = res["tensor_core"]["configs_per_s"] / res["plain_fp32"]["configs_per_s"]
+    res["speedup_tensor_core_vs_plain_fp32_per_independent_sample"] = (
+        res["speedup_tensor_core_vs_plain_fp32"] * res["plain_fp32"]["tau_int_abs_M"] / res["tensor_core"]["tau_int_abs_M"])
+    return res
 
 
 def torch_eager_flow(shape, phi4, w, dev):
@@ -705,6 +738,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the secondary measurements")
     ap.add_argument("--serving-requests", type=int, default=120)
+    ap.add_argument("--acceptance-proposals", type=int, default=32768)
     args = ap.parse_args()
     if args.impl == "reference":
         # The oracle runs on the host cores of rank 0 only: no process group, no GPU.
