@@ -522,7 +522,7 @@ def bench_extra(args, dev, flush, pk):
     t = _time_steps(lambda i: P.mh_chain(st, lw, workspace=wsm), 5, 2, None)
     out["mh_chain"] = {"ns_per_proposal": float(np.mean(t)) * 1e6 / n, "proposals": n}
 
-    # serving mix: resident random-init models, Poisson arrivals at 200 req/s
+    # serving mix: resident random-init models; capacity, then a Poisson load sweep
     out["serving_c5"] = bench_serving(dev, n_requests=args.serving_requests)
     torch.cuda.empty_cache()
 
@@ -637,7 +637,10 @@ def torch_eager_rate(shape, phi4, w, B, dev, flush):
 
 
 def bench_serving(dev, n_requests=120, rate=200.0, n_models=16, seed=5):
-    """Continuous-batching loop on the serving mix; returns latency / throughput."""
+    """Continuous-batching loop on the serving mix: the capacity (every
+    request admitted at t=0), then p50/p99 latency, throughput and the overlap
+    of requests' kernels at Poisson loads of 25 %, 50 %, 75 % and 90 % of that
+    capacity and at the mix's nominal 200 req/s."""
     import torch
     import paper_2208_08903_gb300 as P
     from paper_2208_08903_gb300 import serving
@@ -646,16 +649,35 @@ def bench_serving(dev, n_requests=120, rate=200.0, n_models=16, seed=5):
     for name, shape, s in specs:
         prec = "bf16" if (shape.nd == 3 and shape.L == 16 and shape.c1 == 32 and shape.c2 == 32) else "fp32"
         models[name] = serving.Model(name, shape, P.Flow(shape, gi.init_weights(shape, seed=s), precision=prec))
-    arr = serving.poisson_arrivals(n_requests, rate, seed)
-    reqs = [serving.Request(i, name, m2, lam, b, sd, arrival=float(arr[i]))
-            for i, (name, m2, lam, b, sd) in enumerate(gi.serving_requests(n_requests, list(models), seed))]
+    mix = gi.serving_requests(n_requests, list(models), seed)
+
+    def requests(rate_req_s):
+        arr = serving.poisson_arrivals(n_requests, rate_req_s, seed) if rate_req_s else np.zeros(n_requests)
+        return [serving.Request(i, name, m2, lam, b, sd, arrival=float(arr[i]))
+                for i, (name, m2, lam, b, sd) in enumerate(mix)]
+
+    out = {"mix": "2D L in {8,16,32,64}, 3D L in {8,12,16}, 12-24 couplings, hidden {8,16,24,32}, "
+                  "batch 64-8192 log-uniform; tensor-core kernel for 3D L=16 hidden 32, FP32 otherwise",
+           "models": n_models, "requests_per_load": n_requests,
+           "mean_configs_per_request": float(np.mean([m[3] for m in mix]))}
     with serving.Server(models, hbm_budget_bytes=16 << 30, max_active=16, chunk=2048, device=dev) as srv:
-        srv.run(reqs[:4], keep_results=False, realtime=False)      # warm-up (kernel attributes, streams)
-        _, stats = srv.run(reqs, keep_results=False, realtime=True)
-    stats.update({"offered_rate_req_per_s": rate, "models": n_models,
-                  "mix": "2D L in {8,16,32,64}, 3D L in {8,12,16}, 12-24 couplings, hidden {8,16,32}, "
-                         "batch 64-8192 log-uniform, BF16 conv2 for 3D L=16 hidden 32, FP32 otherwise"})
-    return stats
+        srv.run(requests(0)[:4], keep_results=False, realtime=False)      # warm-up
+        _, cap = srv.run(requests(0), keep_results=False, realtime=False, timeline=True)
+        cap_req_s = n_requests / cap["wall_s"]
+        out["capacity"] = {"configs_per_s": cap["configs_per_s"], "requests_per_s": cap_req_s,
+                           "overlapped_fraction": cap.get("overlapped_fraction"),
+                           "max_requests_in_flight": cap.get("max_requests_in_flight")}
+        loads = []
+        for frac in (0.25, 0.5, 0.75, 0.9, None):
+            r = rate if frac is None else frac * cap_req_s
+            _, st = srv.run(requests(r), keep_results=False, realtime=True, timeline=True)
+            loads.append({"offered_req_per_s": r, "fraction_of_capacity": r / cap_req_s,
+                          "p50_latency_ms": st["p50_latency_ms"], "p99_latency_ms": st["p99_latency_ms"],
+                          "configs_per_s": st["configs_per_s"], "failed_requests": st["failed_requests"],
+                          "overlapped_fraction": st.get("overlapped_fraction"),
+                          "max_requests_in_flight": st.get("max_requests_in_flight")})
+        out["loads"] = loads
+    return out
 
 
 # --------------------------------------------------------------------------- CPU oracle
@@ -737,7 +759,7 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=120.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the secondary measurements")
-    ap.add_argument("--serving-requests", type=int, default=120)
+    ap.add_argument("--serving-requests", type=int, default=60)
     ap.add_argument("--acceptance-proposals", type=int, default=32768)
     args = ap.parse_args()
     if args.impl == "reference":

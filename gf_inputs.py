@@ -168,7 +168,7 @@ WORKLOADS = {
 
 # ---------------------------------------------------------------------------
 # Serving mix: resident models drawn from 2D L in {8,16,32,64} and 3D L in
-# {8,12,16}, 12-24 couplings, hidden width in {8,16,32}; requests pick a model
+# {8,12,16}, 12-24 couplings, hidden width in {8,16,24,32}; requests pick a model
 # uniformly, (m2, lam) uniform in [-6,-2] x [1,10], batch log-uniform in
 # [64, 8192], Poisson arrivals.
 # ---------------------------------------------------------------------------
@@ -179,7 +179,7 @@ def serving_models(n_models: int, seed: int):
     out = []
     for i in range(n_models):
         nd, L = lattices[int(rng.integers(len(lattices)))]
-        c = int(rng.choice([8, 16, 32]))
+        c = int(rng.choice([8, 16, 24, 32]))
         n_layers = int(rng.integers(12, 25))
         out.append((f"m{i}", FlowShape(nd, L, n_layers, c, c), 1000 + i))
     return out

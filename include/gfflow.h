@@ -72,7 +72,8 @@ typedef struct {
  * gf_flow_shape.
  * Supported: nd in {2,3}; L even, L^nd <= 65536; 0 <= n_hidden <=
  * GF_MAX_HIDDEN; widths 1..256; ksize in {1,3,5,7}.  Two equal hidden widths in
- * {8,16,32} with ksize 3 run on the slice-cached kernels (both precisions);
+ * {8,16,24,32} with ksize 3 run on the slice-cached kernels (the tensor-core
+ * precision for 3D L=16 with width 32 only);
  * every other network runs on a whole-lattice FP32 kernel that needs
  * 4 (V + 2 V Cp) bytes of shared memory per block, Cp = the widest hidden
  * layer rounded up to odd, at most 227 KB (else GF_EUNSUPPORTED); those flows

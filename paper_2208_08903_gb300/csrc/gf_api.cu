@@ -235,11 +235,11 @@ bool shape_ex_valid(const gf_flow_shape_ex* s) {
 }
 
 // The paper's example network form on the slice-cached kernels: two equal
-// hidden widths in {8, 16, 32}, 3 taps per axis.
+// hidden widths in {8, 16, 24, 32}, 3 taps per axis.
 bool default_net(const gf_flow_shape_ex* s) {
     if (s->n_hidden != 2 || s->ksize != 3 || s->hidden[0] != s->hidden[1]) return false;
     const int c = s->hidden[0];
-    return c == 8 || c == 16 || c == 32;
+    return c == 8 || c == 16 || c == 24 || c == 32;
 }
 
 void free_flow(gf_flow* f) {

@@ -73,8 +73,12 @@ __device__ __forceinline__ int coord_sum_in_slice(int j, int L) {
 }
 
 // Swizzled float4 chunk of a site row of C floats (conflict-free LDS.128
-// when consecutive lanes read consecutive sites).
-__device__ __forceinline__ int swz(int chunk, int j, int C) { return chunk ^ (j & ((C >> 2) - 1)); }
+// when consecutive lanes read consecutive sites): xor with the site index for
+// a power-of-two number of chunks, a rotation otherwise (C = 24).
+__device__ __forceinline__ int swz(int chunk, int j, int C) {
+    const int n = C >> 2;
+    return (n & (n - 1)) == 0 ? chunk ^ (j & (n - 1)) : (chunk + j) % n;
+}
 
 __device__ __forceinline__ float lrelu(float v, float a) { return v > 0.f ? v : a * v; }
 
@@ -176,14 +180,14 @@ __device__ void phase_h2(const FlowArgs& a, const float* __restrict__ Wl, const 
             for (int k = 0; k < 4; ++k) {
                 const int j2 = shift_in_slice<ND>(jj[k], dy, dx, L);
                 row[k] = h1 + ph.in[rr[k] + 1 + ds] * slot_sz + (size_t)j2 * C1;
-                key[k] = j2 & ((C1 >> 2) - 1);
+                key[k] = j2;
             }
             const float* Wt = W2 + (size_t)t * C1 * C2 + co;
             for (int c4 = 0; c4 < (C1 >> 2); ++c4) {
                 float4 hv[4];
 #pragma unroll
                 for (int k = 0; k < 4; ++k)
-                    hv[k] = *reinterpret_cast<const float4*>(row[k] + ((c4 ^ key[k]) << 2));
+                    hv[k] = *reinterpret_cast<const float4*>(row[k] + (swz(c4, key[k], C1) << 2));
 #pragma unroll
                 for (int cc = 0; cc < 4; ++cc) {
                     const float* wp = Wt + (size_t)(4 * c4 + cc) * C2;
@@ -223,7 +227,7 @@ __device__ void phase_c3(const FlowArgs& a, const float* __restrict__ Wl, const 
     const int L = a.L, S = a.S, C2 = a.C2, T = (ND == 3) ? 27 : 9;
     const int half = S >> 1, nact = ph.n * half;
     int tps = 1;
-    while (tps * 2 <= (C2 >> 2) && nact * tps * 2 <= (int)blockDim.x) tps *= 2;
+    while (tps * 2 <= (C2 >> 2) && (C2 >> 2) % (tps * 2) == 0 && nact * tps * 2 <= (int)blockDim.x) tps *= 2;
     const int nchunk = (C2 >> 2) / tps;
     const int total = nact * tps;
     const float* W3 = Wl + a.off.W3;
@@ -250,11 +254,11 @@ __device__ void phase_c3(const FlowArgs& a, const float* __restrict__ Wl, const 
                 tap_delta<ND>(t, ds, dy, dx);
                 const int j2 = shift_in_slice<ND>(j, dy, dx, L);
                 const float* row = h2 + ph.in[r + 1 + ds] * slot_sz + (size_t)j2 * C2;
-                const int key = j2 & ((C2 >> 2) - 1);
+
                 const float* Wt = W3 + (size_t)t * C2 * 2;
                 for (int c = 0; c < nchunk; ++c) {
                     const int c4 = rk * nchunk + c;
-                    const float4 hv = *reinterpret_cast<const float4*>(row + ((c4 ^ key) << 2));
+                    const float4 hv = *reinterpret_cast<const float4*>(row + (swz(c4, j2, C2) << 2));
                     const float4 w01 = ldw4<WS>(Wt + 8 * c4);
                     const float4 w23 = ldw4<WS>(Wt + 8 * c4 + 4);
                     ps = fmaf(hv.x, w01.x, ps); pt = fmaf(hv.x, w01.y, pt);

@@ -103,19 +103,24 @@ class _Active:
         B, V = req.batch, model.V
         return B * V * 4 + B * (8 * 4 + 1) + 8 * chunk + 48
 
-    def launch_next(self):
+    def launch_next(self, timeline=None):
         req, B = self.req, self.req.batch
         a = self.next
         b = min(B, a + self.chunk)
         phi4 = (req.m2, req.lam)
         with torch.cuda.stream(self.stream):
+            if timeline is not None:
+                t0 = torch.cuda.Event(enable_timing=True)
+                t0.record(self.stream)
             out = api.SampleResult(phi=self.phi[a:b], logq=self.logq[a:b], S=self.S[a:b],
                                    logw=self.logw[a:b])
             self.model.flow.sample(b - a, seed=req.seed, counter0=a, phi4=phi4, out=out)
             api.mh_chain(self.state, self.logw[a:b], workspace=self.ws, chain_idx=self.idx[a:b],
                          acc=self.acc[a:b])
-            self.event = torch.cuda.Event()
+            self.event = torch.cuda.Event(enable_timing=timeline is not None)
             self.event.record(self.stream)
+            if timeline is not None:
+                timeline.append((self.req.rid, t0, self.event))
         self.next = b
 
     def finished(self) -> bool:
@@ -167,9 +172,18 @@ class Server:
         """Reads and clears stream si's status slot (its work has completed)."""
         return api.device_status(self.streams[si])
 
-    def run(self, requests, keep_results: bool = True, realtime: bool = True, poll_s: float = 50e-6):
+    def run(self, requests, keep_results: bool = True, realtime: bool = True, poll_s: float = 50e-6,
+            timeline: bool = False):
         """Serves `requests` (arrival times relative to the start) and returns
-        (results by rid, stats).  realtime=False admits every request at t=0."""
+        (results by rid, stats).  realtime=False admits every request at t=0.
+        timeline=True records a CUDA event pair around every chunk (sample +
+        MH chain on the request's stream) and adds to the stats how much of the
+        GPU-busy time had chunks of two or more requests in flight at once."""
+        chunks = [] if timeline else None
+        ref = None
+        if timeline:
+            ref = torch.cuda.Event(enable_timing=True)
+            ref.record(torch.cuda.current_stream(self.device))
         pending = sorted(requests, key=lambda r: (r.arrival, r.rid))
         pi = 0
         free_streams = list(range(self.max_active))
@@ -205,7 +219,10 @@ class Server:
             progressed = False
             for rid, (st, si, need) in list(active.items()):
                 if st.ready():
-                    st.launch_next()
+                    if chunks is not None:
+                        st.launch_next(chunks)
+                    else:
+                        st.launch_next()
                     progressed = True
                 elif st.finished():
                     done = now()
@@ -242,7 +259,38 @@ class Server:
             "peak_budget_bytes": peak_used,
             "failed_requests": int(sum(1 for r in results.values() if r.error)),
         }
+        if chunks:
+            iv = [(rid, ref.elapsed_time(a), ref.elapsed_time(b)) for rid, a, b in chunks]
+            stats.update(overlap_stats(iv))
         return results, stats
+
+
+def overlap_stats(intervals):
+    """From (request id, start ms, end ms) of every chunk: the GPU-busy time
+    (union of the intervals), the part of it during which chunks of at least
+    two different requests were in flight, and the most requests in flight at
+    once."""
+    ev = []
+    for rid, a, b in intervals:
+        ev.append((a, 1, rid))
+        ev.append((b, -1, rid))
+    ev.sort(key=lambda e: (e[0], e[1]))
+    live = {}
+    busy = multi = 0.0
+    peak = 0
+    last = None
+    for t, d, rid in ev:
+        if last is not None:
+            n_req = sum(1 for v in live.values() if v > 0)
+            if n_req >= 1:
+                busy += t - last
+            if n_req >= 2:
+                multi += t - last
+        live[rid] = live.get(rid, 0) + d
+        peak = max(peak, sum(1 for v in live.values() if v > 0))
+        last = t
+    return {"gpu_busy_ms": busy, "overlapped_ms": multi,
+            "overlapped_fraction": multi / busy if busy > 0 else 0.0, "max_requests_in_flight": peak}
 
 
 def poisson_arrivals(n: int, rate_per_s: float, seed: int) -> np.ndarray:

@@ -25,6 +25,8 @@ CASES = [
     (gi.FlowShape(3, 16, 16, 32, 32), -6.0, 5.0, 3),                 # c3 shape (3D L=16 C=32 kernel)
     (gi.FlowShape(3, 16, 3, 32, 32, use_final_tanh=False), -2.0, 1.0, 5),   # odd layer count, no tanh
     (gi.FlowShape(2, 64, 12, 16, 16), -3.0, 4.0, 2),                 # large 2D, RING
+    (gi.FlowShape(2, 16, 5, 24, 24), -2.0, 3.0, 4),                  # hidden width 24: rotated chunks
+    (gi.FlowShape(3, 12, 4, 24, 24, use_final_tanh=False), -5.0, 2.0, 3),   # 3D L=12, width 24, RING
 ]
 
 

@@ -19,6 +19,7 @@ CASES = [
     (gi.FlowShape(2, 4, 4, 8, 8, use_final_tanh=False), 0.5, 1.0, 3),
     (gi.FlowShape(2, 32, 24, 32, 32), -4.0, 8.0, 3),          # c2 shape, small batch
     (gi.FlowShape(3, 8, 4, 32, 32), -6.0, 5.0, 2),            # 3D, C=32
+    (gi.FlowShape(2, 8, 3, 24, 24), -4.0, 8.0, 4),            # hidden width 24 (serving mix)
 ]
 
 

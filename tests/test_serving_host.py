@@ -121,3 +121,15 @@ def test_device_error_marks_only_its_request_failed(server):
     assert res[4].error == -5
     assert all(res[i].error == 0 for i in res if i != 4)
     assert stats["failed_requests"] == 1
+
+
+def test_overlap_statistics():
+    """Busy time is the union of the chunks' intervals; overlapped time counts
+    only moments with chunks of two or more different requests in flight."""
+    iv = [(1, 0.0, 10.0), (2, 5.0, 15.0), (3, 20.0, 30.0), (1, 25.0, 26.0), (1, 26.0, 27.0)]
+    st = SV.overlap_stats(iv)
+    assert st["gpu_busy_ms"] == 25.0
+    assert st["overlapped_ms"] == 7.0
+    assert st["max_requests_in_flight"] == 2
+    one = SV.overlap_stats([(4, 0.0, 3.0), (4, 3.0, 5.0), (4, 4.0, 6.0)])   # one request's own chunks
+    assert one["overlapped_ms"] == 0.0 and one["gpu_busy_ms"] == 6.0
