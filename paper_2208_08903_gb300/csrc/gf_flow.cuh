@@ -88,10 +88,13 @@ gf_status flow_fp32_configure(gf_flow* f);   // chooses FULL/RING, G, smem
 
 // 3D L=16, hidden 32, FP32 (gf_flow_fp32_c32.cu)
 bool fp32_c32_supported(const gf_flow* f);
+// xs_out / logdet_out (training forward pass, nullable): the field after
+// layers 1..N-1 at xs_out + layer * xs_stride + b * V, and the log-det.
 gf_status launch_flow_fp32_c32(const gf_flow* f, bool inverse, const gf_phi4* phi4, int64_t B, uint64_t seed,
                                uint64_t counter0, const float* z_in, float* z_out, const float* phi_in,
                                float* phi_out, double* logq_out, double* S_out, double* logw_out,
-                               cudaStream_t stream);
+                               cudaStream_t stream, float* xs_out = nullptr, int64_t xs_stride = 0,
+                               double* logdet_out = nullptr);
 
 // General network (gf_flow_variant.cu)
 gf_status variant_configure(gf_flow* f);     // packed offsets, smem, threads (host only)

@@ -68,6 +68,11 @@ struct C32Args {
     double* logq_out;
     double* S_out;
     double* logw_out;
+    // training forward pass (nullable): the field after layers 1 .. N-1 of
+    // configuration b at xs_out + layer * xs_stride + b * V, and its log-det
+    float* xs_out;
+    int64_t xs_stride;
+    double* logdet_out;
 };
 
 __device__ __forceinline__ float lrelu(float v, float a) { return v > 0.f ? v : a * v; }
@@ -302,6 +307,8 @@ __global__ void __launch_bounds__(kThr, 1) flow_fp32_c32_kernel(const C32Args a)
             const int l = INVERSE ? a.n_layers - 1 - li : li;
             const int frozen = l & 1;
             __syncthreads();                          // previous layer done with the weights and st
+            if (a.xs_out && li > 0)                   // the field after li layers (training)
+                for (int n = tid; n < kV; n += kThr) a.xs_out[li * a.xs_stride + b * kV + n] = x[n];
             const float4* src = reinterpret_cast<const float4*>(a.W + (size_t)l * a.stride);
             float4* dst = reinterpret_cast<float4*>(Wl);
             for (int i = tid; i < nstage; i += kThr) dst[i] = __ldg(src + i);
@@ -357,6 +364,7 @@ __global__ void __launch_bounds__(kThr, 1) flow_fp32_c32_kernel(const C32Args a)
         double S = 0.0;
         if (!INVERSE && a.has_phi4) S = block_sum_ff(action_part<3>(x, kL, kV, a.c2d_ff, a.lam_ff), red);
         if (tid == 0) {
+            if (a.logdet_out) a.logdet_out[b] = ld;
             const double logr = -0.5 * z2 - 0.5 * (double)kV * LOG_2PI;
             const double logq = logr - ld;
             a.logq_out[b] = logq;
@@ -430,6 +438,8 @@ __global__ void __launch_bounds__(kThr, 1) flow_fp32_c32_2d_kernel(const C32Args
             const int l = INVERSE ? a.n_layers - 1 - li : li;
             const int frozen = l & 1, pa = frozen ^ 1;
             __syncthreads();
+            if (a.xs_out && li > 0)                   // the field after li layers (training)
+                for (int n = tid; n < d2::V; n += kThr) a.xs_out[li * a.xs_stride + b * d2::V + n] = x[n];
             const float4* src = reinterpret_cast<const float4*>(a.W + (size_t)l * a.stride);
             float4* dst = reinterpret_cast<float4*>(Wl);
             for (int i = tid; i < nstage; i += kThr) dst[i] = __ldg(src + i);
@@ -563,6 +573,7 @@ __global__ void __launch_bounds__(kThr, 1) flow_fp32_c32_2d_kernel(const C32Args
         double S = 0.0;
         if (!INVERSE && a.has_phi4) S = block_sum_ff(action_part<2>(x, d2::L, d2::V, a.c2d_ff, a.lam_ff), red);
         if (tid == 0) {
+            if (a.logdet_out) a.logdet_out[b] = ld;
             const double logr = -0.5 * z2 - 0.5 * (double)d2::V * LOG_2PI;
             const double logq = logr - ld;
             a.logq_out[b] = logq;
@@ -589,7 +600,7 @@ size_t fp32_c32_smem(const gf_flow* f) {
 gf_status launch_flow_fp32_c32(const gf_flow* f, bool inverse, const gf_phi4* phi4, int64_t B, uint64_t seed,
                                uint64_t counter0, const float* z_in, float* z_out, const float* phi_in,
                                float* phi_out, double* logq_out, double* S_out, double* logw_out,
-                               cudaStream_t stream) {
+                               cudaStream_t stream, float* xs_out, int64_t xs_stride, double* logdet_out) {
     C32Args a;
     std::memset(&a, 0, sizeof(a));
     a.W = f->d_packed;
@@ -604,6 +615,7 @@ gf_status launch_flow_fp32_c32(const gf_flow* f, bool inverse, const gf_phi4* ph
     a.B = B; a.seed = seed; a.counter0 = counter0;
     a.z_in = z_in; a.z_out = z_out; a.phi_in = phi_in; a.phi_out = phi_out;
     a.logq_out = logq_out; a.S_out = S_out; a.logw_out = logw_out;
+    a.xs_out = xs_out; a.xs_stride = xs_stride; a.logdet_out = logdet_out;
     const size_t smem = fp32_c32_smem(f);
     auto kern = f->shape.nd == 3 ? (inverse ? flow_fp32_c32_kernel<true> : flow_fp32_c32_kernel<false>)
                                  : (inverse ? flow_fp32_c32_2d_kernel<true> : flow_fp32_c32_2d_kernel<false>);

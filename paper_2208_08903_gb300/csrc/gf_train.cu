@@ -460,16 +460,283 @@ __global__ void __launch_bounds__(1024) k_wgrad_tiled(const WgArgs a, int G) {
     }
 }
 
+// Weight gradient of the two thin convolutions, tiled through shared memory:
+// conv3 (C -> 2, unmasked input) and conv1 (1 -> C, input masked to the fixed
+// sites).  A work unit is G consecutive slices of one configuration; its gout
+// rows and its input rows plus one halo slice on each side are staged in
+// shared memory (input [site][Cin], gout [site][Cout]).  conv3: thread = input
+// channel ci and row group; conv1: thread = output channel and row group.  A
+// thread walks its rows (an x-row of a slice) along x with a sliding window of
+// the 3 (2D) or 9 (3D) input rows' values at x-1, x, x+1, so every input value
+// is loaded once per row and feeds all taps: per site 1 (2D) or 3 (3D) input
+// loads and one gout load feed 18 / 54 (conv3) or 9 / 27 (conv1) FMAs.  The
+// row groups' sums are combined in a fixed order in shared memory (the bias is
+// tap T); per-CTA partials as k_wgrad.
+template <int ND>
+__global__ void __launch_bounds__(512) k_wgrad_thin(const WgArgs a, int G) {
+    extern __shared__ __align__(16) float sm[];
+    constexpr int T = ND == 3 ? 27 : 9, NR = ND == 3 ? 9 : 3;   // taps, input rows per output row
+    const int L = a.L, V = a.V, CI = a.Cin, CO = a.Cout;
+    const int S = V / L;
+    const bool conv3 = CO == 2;                           // else conv1 (CI == 1)
+    const int nch = conv3 ? CI : CO;                      // channels one row group covers
+    const int ngrp = blockDim.x / nch;
+    const int ch = threadIdx.x % nch, grp = threadIdx.x / nch;
+    const bool active = grp < ngrp;
+    // row pitches: 4 extra floats for 16-byte chunked rows, so the staging
+    // stores of consecutive sites fall in distinct bank groups
+    const int PI = CI % 4 == 0 ? CI + 4 : CI, PO = CO % 4 == 0 ? CO + 4 : CO;
+    float* g_s = sm;                                       // [G*S][PO]
+    float* x_s = g_s + (size_t)G * S * PO;                 // [(G+2)*S][PI]
+    float* red = sm;                                       // [ngrp][nch][(T+1)*2], after the units
+    constexpr int NA = (T + 1) * 2;
+    float acc[NA];
+#pragma unroll
+    for (int i = 0; i < NA; ++i) acc[i] = 0.f;
+    const int rows_per_slice = ND == 3 ? L : 1;
+    const int units_per_cfg = L / G;
+    const int64_t units = a.B * units_per_cfg;
+    for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
+        const int64_t b = u / units_per_cfg;
+        const int s0 = (int)(u % units_per_cfg) * G;
+        __syncthreads();
+        // staging: 16-byte chunk loads (4 channels of one site) where the
+        // channel count allows, consecutive threads on consecutive sites
+        if (CO % 4 == 0) {
+            const int nc = CO / 4;
+            for (int e = threadIdx.x; e < G * S * nc; e += blockDim.x) {
+                const int c4 = e / (G * S), site = e % (G * S);
+                const float4 v = __ldg(reinterpret_cast<const float4*>(a.gout + chunk_at(b, s0 * S + site, 4 * c4, CO, V)));
+                *reinterpret_cast<float4*>(g_s + (size_t)site * PO + 4 * c4) = v;
+            }
+        } else {
+            for (int e = threadIdx.x; e < G * S * CO; e += blockDim.x) {
+                const int site = e / CO, c = e % CO, w = CO < 4 ? CO : 4;
+                g_s[(size_t)site * PO + c] = __ldg(a.gout + chunk_at(b, s0 * S + site, c - c % w, CO, V) + c % w);
+            }
+        }
+        if (CI % 4 == 0) {
+            const int nc = CI / 4, nsite = (G + 2) * S;
+            for (int e = threadIdx.x; e < nsite * nc; e += blockDim.x) {
+                const int c4 = e / nsite, site = e % nsite;
+                const int sl = s0 - 1 + site / S;
+                const int n = ((sl % L + L) % L) * S + site % S;
+                const float4 v = __ldg(reinterpret_cast<const float4*>(a.in + chunk_at(b, n, 4 * c4, CI, V)));
+                *reinterpret_cast<float4*>(x_s + (size_t)site * PI + 4 * c4) = v;     // (inputs with CI > 1 are unmasked)
+            }
+        } else {
+            for (int e = threadIdx.x; e < (G + 2) * S * CI; e += blockDim.x) {
+                const int site = e / CI, c = e % CI, w = CI < 4 ? CI : 4;
+                const int sl = s0 - 1 + site / S;
+                const int n = ((sl % L + L) % L) * S + site % S;
+                float v = __ldg(a.in + chunk_at(b, n, c - c % w, CI, V) + c % w);
+                if (a.mask >= 0 && parity<ND>(n, L) != a.mask) v = 0.f;
+                x_s[(size_t)site * PI + c] = v;
+            }
+        }
+        __syncthreads();
+        if (!active) continue;
+        const int cin = conv3 ? ch : 0;
+        for (int row = grp; row < G * rows_per_slice; row += ngrp) {
+            const int rs = row / rows_per_slice, y = row % rows_per_slice;
+            // input row k = (ds, dy) of output row (rs, y): slice rs + 1 + ds, row y + dy
+            int base[NR];
+#pragma unroll
+            for (int k = 0; k < NR; ++k) {
+                const int ds = (ND == 3 ? k / 3 : k) - 1, dy = ND == 3 ? k % 3 - 1 : 0;
+                base[k] = (rs + 1 + ds) * S + (ND == 3 ? wrapi(y + dy, L) * L : 0);
+            }
+            const int gbase = rs * S + (ND == 3 ? y * L : 0);
+            float wm[NR], w0[NR], wp[NR];                  // window at x-1, x, x+1
+#pragma unroll
+            for (int k = 0; k < NR; ++k) {
+                wm[k] = x_s[(size_t)(base[k] + L - 1) * PI + cin];
+                w0[k] = x_s[(size_t)base[k] * PI + cin];
+            }
+            for (int x = 0; x < L; ++x) {
+                const int xp = x + 1 == L ? 0 : x + 1;
+#pragma unroll
+                for (int k = 0; k < NR; ++k) wp[k] = x_s[(size_t)(base[k] + xp) * PI + cin];
+                float g0, g1 = 0.f;
+                if (conv3) {
+                    const float2 gg = *reinterpret_cast<const float2*>(g_s + (size_t)(gbase + x) * PO);
+                    g0 = gg.x;
+                    g1 = gg.y;
+                } else {
+                    g0 = g_s[(size_t)(gbase + x) * PO + ch];
+                }
+#pragma unroll
+                for (int k = 0; k < NR; ++k) {
+                    // taps (k, dx = -1, 0, +1) = tap index 3k + dxi
+                    acc[(3 * k + 0) * 2] = fmaf(wm[k], g0, acc[(3 * k + 0) * 2]);
+                    acc[(3 * k + 1) * 2] = fmaf(w0[k], g0, acc[(3 * k + 1) * 2]);
+                    acc[(3 * k + 2) * 2] = fmaf(wp[k], g0, acc[(3 * k + 2) * 2]);
+                    if (conv3) {
+                        acc[(3 * k + 0) * 2 + 1] = fmaf(wm[k], g1, acc[(3 * k + 0) * 2 + 1]);
+                        acc[(3 * k + 1) * 2 + 1] = fmaf(w0[k], g1, acc[(3 * k + 1) * 2 + 1]);
+                        acc[(3 * k + 2) * 2 + 1] = fmaf(wp[k], g1, acc[(3 * k + 2) * 2 + 1]);
+                    }
+                    wm[k] = w0[k];
+                    w0[k] = wp[k];
+                }
+                acc[T * 2] += g0;                          // bias
+                acc[T * 2 + 1] += g1;
+            }
+        }
+    }
+    // combine the row groups in a fixed order, then one partial per CTA
+    __syncthreads();
+    if (active)
+#pragma unroll
+        for (int i = 0; i < NA; ++i) red[((size_t)grp * nch + ch) * NA + i] = acc[i];
+    __syncthreads();
+    float* P = a.partial + (int64_t)blockIdx.x * (T + 1) * CI * CO;
+    for (int e = threadIdx.x; e < nch * NA; e += blockDim.x) {
+        const int c = e / NA, i = e % NA;
+        float sum = 0.f;
+        for (int g = 0; g < ngrp; ++g) sum += red[((size_t)g * nch + c) * NA + i];
+        const int t = i >> 1, o = i & 1;
+        if (conv3) P[((int64_t)t * CI + c) * 2 + o] = (t == T && c != 0) ? 0.f : sum;
+        else if (o == 0) P[(int64_t)t * CO + c] = sum;
+    }
+}
+
+// Weight gradient of the C -> C convolution (conv2) for C = 32 as a GEMM over
+// the sites: dW[(t, i)][o] = sum_n x(n + delta(t))[i] g(n)[o].  A work unit is G
+// slices of one configuration, staged in shared memory with a row pitch of 36
+// floats (input slices with one halo slice on each side, gout slices); each
+// thread owns an 8 x 8 tile (8 input channels of one tap x 8 output channels),
+// so per site two 16-byte input loads and two 16-byte gout loads (both shared
+// by the lanes of the same tap / channel group) feed 64 FMAs.  In 2D the CTA's
+// two thread halves take alternate sites of a unit and are added in a fixed
+// order at the end.  The bias gradient rides on the threads of tap 0, input
+// group 0.  Per-CTA partials in k_wgrad's layout (tap T = bias).
+template <int ND>
+__global__ void __launch_bounds__(ND == 3 ? 448 : 288, ND == 3 ? 1 : 2) k_wgrad_c32(const WgArgs a, int G) {
+    extern __shared__ __align__(16) float sm[];
+    constexpr int T = ND == 3 ? 27 : 9, C = 32, P = 36;
+    constexpr int TILES = T * 4 * 4;                  // (tap, input group) x output group
+    constexpr int HALVES = ND == 3 ? 1 : 2;
+    const int L = a.L, V = a.V, S = V / L;
+    const int half = threadIdx.x / TILES, r = threadIdx.x % TILES;
+    const bool active = half < HALVES;
+    const int ar = r >> 2, og = r & 3;               // A row group (tap, input group), output group
+    const int t = ar >> 2, ig = ar & 3;
+    int ds, dy, dx;
+    tap_delta<ND>(t, ds, dy, dx);
+    float* x_s = sm;                                   // [(G+2)*S][P]
+    float* g_s = sm + (size_t)(G + 2) * S * P;         // [G*S][P]
+    float acc[8][8], accb[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        accb[i] = 0.f;
+#pragma unroll
+        for (int o = 0; o < 8; ++o) acc[i][o] = 0.f;
+    }
+    const bool does_bias = ar == 0;
+    const int units_per_cfg = L / G;
+    const int64_t units = a.B * units_per_cfg;
+    for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
+        const int64_t b = u / units_per_cfg;
+        const int s0 = (int)(u % units_per_cfg) * G;
+        __syncthreads();
+        const int nsx = (G + 2) * S;
+        for (int e = threadIdx.x; e < nsx * 8; e += blockDim.x) {
+            const int c4 = e / nsx, site = e % nsx;
+            const int sl = s0 - 1 + site / S;
+            const int n = ((sl % L + L) % L) * S + site % S;
+            *reinterpret_cast<float4*>(x_s + (size_t)site * P + 4 * c4) =
+                __ldg(reinterpret_cast<const float4*>(a.in + chunk_at(b, n, 4 * c4, C, V)));
+        }
+        const int nsg = G * S;
+        for (int e = threadIdx.x; e < nsg * 8; e += blockDim.x) {
+            const int c4 = e / nsg, site = e % nsg;
+            *reinterpret_cast<float4*>(g_s + (size_t)site * P + 4 * c4) =
+                __ldg(reinterpret_cast<const float4*>(a.gout + chunk_at(b, s0 * S + site, 4 * c4, C, V)));
+        }
+        __syncthreads();
+        if (!active) continue;
+        for (int q = half; q < nsg; q += HALVES) {
+            const int rs = q / S, j = q - rs * S;
+            int j2;
+            if (ND == 3) {
+                const int y = j / L, x = j - y * L;
+                j2 = wrapi(y + dy, L) * L + wrapi(x + dx, L);
+            } else {
+                j2 = wrapi(j + dx, L);
+            }
+            const float* ap = x_s + (size_t)((rs + 1 + ds) * S + j2) * P + ig * 8;
+            const float* bp = g_s + (size_t)q * P + og * 8;
+            const float4 a0 = *reinterpret_cast<const float4*>(ap);
+            const float4 a1 = *reinterpret_cast<const float4*>(ap + 4);
+            const float4 b0 = *reinterpret_cast<const float4*>(bp);
+            const float4 b1 = *reinterpret_cast<const float4*>(bp + 4);
+            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int o = 0; o < 8; ++o) acc[i][o] = fmaf(av[i], bv[o], acc[i][o]);
+            if (does_bias)
+#pragma unroll
+                for (int o = 0; o < 8; ++o) accb[o] += bv[o];
+        }
+    }
+    // combine the halves (2D) in a fixed order through shared memory, then write
+    __syncthreads();
+    float* Pt = a.partial + (int64_t)blockIdx.x * (T + 1) * C * C;
+    if (HALVES == 2) {
+        float* red = sm;                               // [TILES][72]
+        if (active && half == 1) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int o = 0; o < 8; ++o) red[(size_t)r * 72 + i * 8 + o] = acc[i][o];
+#pragma unroll
+            for (int o = 0; o < 8; ++o) red[(size_t)r * 72 + 64 + o] = accb[o];
+        }
+        __syncthreads();
+        if (active && half == 0) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int o = 0; o < 8; ++o) acc[i][o] += red[(size_t)r * 72 + i * 8 + o];
+#pragma unroll
+            for (int o = 0; o < 8; ++o) accb[o] += red[(size_t)r * 72 + 64 + o];
+        }
+    }
+    if (active && half == 0) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int o = 0; o < 8; ++o) Pt[((int64_t)t * C + ig * 8 + i) * C + og * 8 + o] = acc[i][o];
+        if (does_bias)
+#pragma unroll
+            for (int o = 0; o < 8; ++o) Pt[((int64_t)T * C + 0) * C + og * 8 + o] = accb[o];
+    }
+}
+
 // grad (canonical, for one conv of one layer): W[o][i][t] and b[o], scaled by 1/B.
-__global__ void k_wgrad_reduce(const float* __restrict__ partial, int nparts, int T, int Cin, int Cout,
-                               float scale, float* __restrict__ gW, float* __restrict__ gb) {
+__global__ void __launch_bounds__(256) k_wgrad_reduce(const float* __restrict__ partial, int nparts, int T, int Cin,
+                                                      int Cout, float scale, float* __restrict__ gW,
+                                                      float* __restrict__ gb) {
+    // block = 32 outputs (lane); its 8 warps sum interleaved eighths of the
+    // partials, combined in warp order (fixed: deterministic)
+    __shared__ float part[8][32];
     const int per = (T + 1) * Cin * Cout;
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < per; p += gridDim.x * blockDim.x) {
-        float s = 0.f;
-        for (int k = 0; k < nparts; ++k) s += partial[(int64_t)k * per + p];
-        const int o = p % Cout, i = (p / Cout) % Cin, t = p / (Cout * Cin);
-        if (t < T) gW[((int64_t)o * Cin + i) * T + t] = s * scale;
-        else if (i == 0) gb[o] = s * scale;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int p = blockIdx.x * 32 + lane;
+    float s = 0.f;
+    if (p < per)
+        for (int k = wid; k < nparts; k += 8) s += partial[(int64_t)k * per + p];
+    part[wid][lane] = s;
+    __syncthreads();
+    if (wid == 0 && p < per) {
+        float t = 0.f;
+        for (int w = 0; w < 8; ++w) t += part[w][lane];
+        const int o = p % Cout, i = (p / Cout) % Cin, tt = p / (Cout * Cin);
+        if (tt < T) gW[((int64_t)o * Cin + i) * T + tt] = t * scale;
+        else if (i == 0) gb[o] = t * scale;
     }
 }
 
@@ -672,12 +939,43 @@ gf_status wgrad(const WgArgs& a, float* gW, float* gbias, float scale, cudaStrea
         const int threads = (tasks * nsplit + 31) / 32 * 32;
         kern<<<grid, threads, 0, st>>>(a, nsplit);
     };
-    if (a.Cin == 1) launch(k_wgrad<ND, 1, 8>, (T + 1) * (a.Cout / 8));
-    else if (a.Cout == 2) launch(k_wgrad<ND, 4, 2>, (T + 1) * (a.Cin / 4));
-    else {
+    if (a.Cin == 1 || a.Cout == 2) {
+        // thin convolutions: shared-memory tiled, one thread per (tap, channel);
+        // G = the largest divisor of L whose staged rows fit in 96 KB
+        const int S = a.V / a.L;
+        const int nch = a.Cout == 2 ? a.Cin : a.Cout;
+        const int ngrp = std::max(1, 512 / nch);
+        const size_t red = (size_t)ngrp * nch * (T + 1) * 2 * sizeof(float);
+        int G = a.L;
+        const int PI = a.Cin % 4 == 0 ? a.Cin + 4 : a.Cin, PO = a.Cout % 4 == 0 ? a.Cout + 4 : a.Cout;
+        auto staged = [&](int g) { return (size_t)(g * S * PO + (g + 2) * S * PI) * sizeof(float); };
+        while (G > 1 && (staged(G) > 112 * 1024 || a.L % G != 0)) --G;
+        auto bytes = [&](int g) { return std::max(staged(g), red); };   // the group sums reuse the staging area
+        if (cudaFuncSetAttribute(k_wgrad_thin<ND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)bytes(G)) != cudaSuccess)
+            return GF_ECUDA;
+        k_wgrad_thin<ND><<<grid, ngrp * nch, bytes(G), st>>>(a, G);
+    } else {
         // C -> C (unmasked input): shared-memory tiled; G = the largest divisor of
         // L whose staged rows fit in 96 KB, else 1
         if (a.mask >= 0) return GF_EINVAL;
+        if (a.Cin == 32 && a.Cout == 32) {
+            const int S = a.V / a.L;
+            auto bytes = [&](int g) { return (size_t)((g + 2) * S + g * S) * 36 * sizeof(float); };
+            int G = a.L;
+            while (G > 1 && (bytes(G) > 100 * 1024 || a.L % G != 0)) --G;
+            const size_t smem = std::max(bytes(G), (size_t)(T * 16) * 72 * sizeof(float));
+            const int threads = ND == 3 ? 448 : 288;
+            if (cudaFuncSetAttribute(k_wgrad_c32<ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+                cudaSuccess)
+                return GF_ECUDA;
+            k_wgrad_c32<ND><<<grid, threads, smem, st>>>(a, G);
+            GF_CHECK_LAUNCH();
+            const int per = (T + 1) * a.Cin * a.Cout;
+            k_wgrad_reduce<<<(per + 31) / 32, 256, 0, st>>>(a.partial, grid, T, a.Cin, a.Cout, scale, gW, gbias);
+            GF_CHECK_LAUNCH();
+            return GF_OK;
+        }
         const int S = a.V / a.L;
         int G = a.L;
         auto bytes = [&](int g) { return (size_t)(g * S * a.Cout + (g + 2) * S * a.Cin) * sizeof(float); };
@@ -690,7 +988,7 @@ gf_status wgrad(const WgArgs& a, float* gW, float* gbias, float scale, cudaStrea
     }
     GF_CHECK_LAUNCH();
     const int per = (T + 1) * a.Cin * a.Cout;
-    k_wgrad_reduce<<<(per + 255) / 256, 256, 0, st>>>(a.partial, grid, T, a.Cin, a.Cout, scale, gW, gbias);
+    k_wgrad_reduce<<<(per + 31) / 32, 256, 0, st>>>(a.partial, grid, T, a.Cin, a.Cout, scale, gW, gbias);
     GF_CHECK_LAUNCH();
     return GF_OK;
 }
@@ -705,6 +1003,12 @@ gf_status forward_pass(const gf_flow* f, int64_t B, uint64_t seed, uint64_t coun
     const int64_t BV = B * (int64_t)V;
     const float slope = (float)f->shape.leaky_slope;
     const PackedOffsets po = packed_offsets(T, C1, C2);
+    if (fp32_c32_supported(f)) {
+        // one fused launch: z (or the prior) -> every layer's input x_l and the
+        // log-det, with the FP32 weights (log q goes to a scratch buffer)
+        return launch_flow_fp32_c32(f, false, nullptr, B, seed, counter0, z_in, w.xs, nullptr,
+                                    w.xs + (int64_t)N * BV, w.loss_b, nullptr, nullptr, st, w.xs, BV, w.logdet);
+    }
     k_prior<<<(unsigned)grid1d(BV / 4 + 1), kThreads, 0, st>>>(V, B, seed, counter0, z_in, w.xs);
     GF_CHECK_LAUNCH();
     if (cudaMemsetAsync(w.logdet, 0, sizeof(double) * B, st) != cudaSuccess) return GF_ECUDA;

@@ -20,6 +20,7 @@ CASES = [
     (gi.FlowShape(2, 32, 24, 32, 32), -4.0, 8.0, 3),          # c2 shape, small batch
     (gi.FlowShape(3, 8, 4, 32, 32), -6.0, 5.0, 2),            # 3D, C=32
     (gi.FlowShape(2, 8, 3, 24, 24), -4.0, 8.0, 4),            # hidden width 24 (serving mix)
+    (gi.FlowShape(3, 16, 3, 32, 32), -6.0, 5.0, 2),           # 3D L=16 C=32: fused forward pass
 ]
 
 
