@@ -96,6 +96,12 @@ gf_status launch_flow_fp32_c32(const gf_flow* f, bool inverse, const gf_phi4* ph
                                cudaStream_t stream, float* xs_out = nullptr, int64_t xs_stride = 0,
                                double* logdet_out = nullptr);
 
+// The training reverse pass's recompute of one layer's network (2D L=32,
+// width 32): h1, h2 (chunk-major workspace layout) and s from x_l.
+bool fp32_c32_recompute_supported(const gf_flow* f);
+gf_status launch_c32_recompute(const gf_flow* f, int layer, int64_t B, const float* xl, float* h1_out, float* h2_out,
+                               float* s_out, cudaStream_t stream);
+
 // General network (gf_flow_variant.cu)
 gf_status variant_configure(gf_flow* f);     // packed offsets, smem, threads (host only)
 gf_status repack_variant(gf_flow* f, cudaStream_t stream);

@@ -586,7 +586,185 @@ __global__ void __launch_bounds__(kThr, 1) flow_fp32_c32_2d_kernel(const C32Args
     }
 }
 
+// One coupling layer's network recomputed for the training reverse pass (2D
+// L=32, width 32): from the layer input x_l of each configuration, h1 and h2
+// (after LeakyReLU) in the channel-chunk-major activation layout of the
+// training workspace ([b][c/4][V][4]) and s at the updated sites (after the
+// tanh; 0 at the fixed sites), with the same slab plan as the sampler.
+__global__ void __launch_bounds__(kThr, 1) c32_2d_recompute_kernel(const C32Args a, int layer, const float* __restrict__ xl,
+                                                                  float* __restrict__ h1_out, float* __restrict__ h2_out,
+                                                                  float* __restrict__ s_out) {
+    extern __shared__ __align__(16) float sm[];
+    float* x = sm + d2::kOffX;
+    float* h1 = sm + d2::kOffH1;
+    float* h2 = sm + d2::kOffH2;
+    float* st = sm + d2::kOffST;
+    float* Wl = sm + d2::kOffW;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int co8 = (warp & 3) * 8, half = warp >> 2;
+    const int frozen = layer & 1, pa = frozen ^ 1;
+    constexpr int V = d2::V, L = d2::L;
+    {
+        const float4* src = reinterpret_cast<const float4*>(a.W + (size_t)layer * a.stride);
+        float4* dst = reinterpret_cast<float4*>(Wl);
+        for (int i = tid; i < (int)(a.stride / 4); i += kThr) dst[i] = __ldg(src + i);
+    }
+    const float* W1 = Wl + a.off.W1;
+    const float* b1 = Wl + a.off.b1;
+    const float* W2 = Wl + a.off.W2;
+    const float* b2 = Wl + a.off.b2;
+    const float* W3 = Wl + a.off.W3;
+    // chunk-major activation layout: element (b, n, c) at ((b*8 + c/4)*V + n)*4 + c%4
+    const auto chunk = [](int64_t b, int n, int c4) { return ((b * 8 + c4) * (int64_t)V + n) * 4; };
+    for (int64_t b = blockIdx.x; b < a.B; b += gridDim.x) {
+        __syncthreads();
+        for (int n = tid; n < V; n += kThr) x[n] = __ldg(xl + b * V + n);
+        for (int i = tid; i < L * 16 * 2; i += kThr) st[i] = 0.f;
+        __syncthreads();
+        for (int slab = 0; slab < 2; ++slab) {
+            const int r0 = slab * d2::ROWS;
+            for (int i = tid; i < d2::HROWS * L; i += kThr) {
+                const int hr = i >> 5, xc = i & 31, y = (r0 - 1 + hr) & 31;
+                float acc[kC];
+#pragma unroll
+                for (int c = 0; c < kC; c += 4) {
+                    const float4 bb = *reinterpret_cast<const float4*>(b1 + c);
+                    acc[c] = bb.x; acc[c + 1] = bb.y; acc[c + 2] = bb.z; acc[c + 3] = bb.w;
+                }
+#pragma unroll 1
+                for (int t = 0; t < d2::T; ++t) {
+                    const int yy = (y + t / 3 - 1) & 31, xx = (xc + t % 3 - 1) & 31;
+                    const float xv = (((xx + yy) & 1) == frozen) ? x[(yy << 5) | xx] : 0.f;
+#pragma unroll
+                    for (int c = 0; c < kC; c += 4) {
+                        const float4 wv = *reinterpret_cast<const float4*>(W1 + t * kC + c);
+                        acc[c] = fmaf(xv, wv.x, acc[c]);
+                        acc[c + 1] = fmaf(xv, wv.y, acc[c + 1]);
+                        acc[c + 2] = fmaf(xv, wv.z, acc[c + 2]);
+                        acc[c + 3] = fmaf(xv, wv.w, acc[c + 3]);
+                    }
+                }
+                float* row = h1 + i * kCP;
+#pragma unroll
+                for (int c = 0; c < kC; ++c) row[c] = lrelu(acc[c], a.slope);
+            }
+            __syncthreads();
+            // h1 of the slab's 16 rows to the workspace
+            for (int e = tid; e < d2::ROWS * L * 8; e += kThr) {
+                const int c4 = e / (d2::ROWS * L), site = e % (d2::ROWS * L);
+                const float* rw = h1 + (L + site) * kCP + 4 * c4;
+                *reinterpret_cast<float4*>(h1_out + chunk(b, (r0 << 5) + site, c4)) = make_float4(rw[0], rw[1], rw[2], rw[3]);
+            }
+            {
+                float acc[8][8];
+                {
+                    const float4 u = *reinterpret_cast<const float4*>(b2 + co8);
+                    const float4 v = *reinterpret_cast<const float4*>(b2 + co8 + 4);
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        acc[k][0] = u.x; acc[k][1] = u.y; acc[k][2] = u.z; acc[k][3] = u.w;
+                        acc[k][4] = v.x; acc[k][5] = v.y; acc[k][6] = v.z; acc[k][7] = v.w;
+                    }
+                }
+#pragma unroll 1
+                for (int t = 0; t < d2::T; ++t) {
+                    const int dy = t / 3 - 1, dx = t % 3 - 1;
+                    const int xs = (lane + dx) & 31;
+                    const float* hb = h1 + ((8 * half + dy + 1) * L + xs) * kCP;
+                    const float* wt = W2 + (size_t)t * kC * kC + co8;
+#pragma unroll 4
+                    for (int ci = 0; ci < kC; ++ci) {
+                        const float4 u = *reinterpret_cast<const float4*>(wt + ci * kC);
+                        const float4 v = *reinterpret_cast<const float4*>(wt + ci * kC + 4);
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) {
+                            const float h = hb[k * L * kCP + ci];
+                            acc[k][0] = fmaf(h, u.x, acc[k][0]); acc[k][1] = fmaf(h, u.y, acc[k][1]);
+                            acc[k][2] = fmaf(h, u.z, acc[k][2]); acc[k][3] = fmaf(h, u.w, acc[k][3]);
+                            acc[k][4] = fmaf(h, v.x, acc[k][4]); acc[k][5] = fmaf(h, v.y, acc[k][5]);
+                            acc[k][6] = fmaf(h, v.z, acc[k][6]); acc[k][7] = fmaf(h, v.w, acc[k][7]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    float o[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) o[j] = lrelu(acc[k][j], a.slope);
+                    float* row = h2 + ((8 * half + k) * L + lane) * kCP + co8;
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) row[j] = o[j];
+                    const int n = ((r0 + 8 * half + k) << 5) | lane;
+                    *reinterpret_cast<float4*>(h2_out + chunk(b, n, co8 / 4)) = make_float4(o[0], o[1], o[2], o[3]);
+                    *reinterpret_cast<float4*>(h2_out + chunk(b, n, co8 / 4 + 1)) = make_float4(o[4], o[5], o[6], o[7]);
+                }
+            }
+            __syncthreads();
+            for (int it = tid; it < d2::HROWS * 16; it += kThr) {
+                const int tr = it >> 4, kx = it & 15;
+                const int y = (r0 - 1 + tr) & 31;
+                const int xc = 2 * kx + ((pa ^ y) & 1);
+                float ps = 0.f, pt = 0.f;
+                for (int dy = -1; dy <= 1; ++dy) {
+                    const int hr = tr - 1 + dy;
+                    if (hr < 0 || hr >= d2::ROWS) continue;
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        const float* row = h2 + (hr * L + ((xc + dx) & 31)) * kCP;
+                        const float* w = W3 + (size_t)((dy + 1) * 3 + dx + 1) * kC * 2;
+#pragma unroll 8
+                        for (int ci = 0; ci < kC; ++ci) {
+                            const float2 wv = *reinterpret_cast<const float2*>(w + 2 * ci);
+                            ps = fmaf(row[ci], wv.x, ps);
+                            pt = fmaf(row[ci], wv.y, pt);
+                        }
+                    }
+                }
+                float* o = st + ((y << 4) | kx) * 2;
+                o[0] += ps;
+                o[1] += pt;
+            }
+            __syncthreads();
+        }
+        const float bs = Wl[a.off.b3];
+        for (int n = tid; n < V; n += kThr) {
+            const int y = n >> 5, xc = n & 31;
+            float sv = 0.f;
+            if (((xc + y) & 1) == pa) {
+                const float spre = st[((y << 4) | (xc >> 1)) * 2] + bs;
+                sv = a.use_tanh ? tanhf(spre) : spre;
+            }
+            s_out[b * V + n] = sv;
+        }
+    }
+}
+
 }  // namespace
+
+bool fp32_c32_recompute_supported(const gf_flow* f) {
+    return !f->variant && f->C1 == kC && f->C2 == kC && f->shape.nd == 2 && f->shape.L == d2::L && f->T == d2::T;
+}
+
+gf_status launch_c32_recompute(const gf_flow* f, int layer, int64_t B, const float* xl, float* h1_out, float* h2_out,
+                               float* s_out, cudaStream_t stream) {
+    C32Args a;
+    std::memset(&a, 0, sizeof(a));
+    a.W = f->d_packed;
+    a.stride = f->packed_stride;
+    a.off = packed_offsets(f->T, f->C1, f->C2);
+    a.n_layers = f->shape.n_layers;
+    a.slope = (float)f->shape.leaky_slope;
+    a.use_tanh = f->shape.use_final_tanh;
+    a.B = B;
+    const size_t smem = (size_t)(d2::kOffW + f->packed_stride) * 4;
+    if (cudaFuncSetAttribute(c32_2d_recompute_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return GF_ECUDA;
+    const int64_t grid = std::min<int64_t>(B, (int64_t)num_sms());
+    if (grid <= 0) return GF_OK;
+    c32_2d_recompute_kernel<<<(unsigned)grid, kThr, smem, stream>>>(a, layer, xl, h1_out, h2_out, s_out);
+    GF_CHECK_LAUNCH();
+    return GF_OK;
+}
 
 bool fp32_c32_supported(const gf_flow* f) {
     if (f->variant || f->C1 != kC || f->C2 != kC) return false;

@@ -656,17 +656,17 @@ __global__ void __launch_bounds__(ND == 3 ? 448 : 288, ND == 3 ? 1 : 2) k_wgrad_
         }
         __syncthreads();
         if (!active) continue;
-        for (int q = half; q < nsg; q += HALVES) {
-            const int rs = q / S, j = q - rs * S;
-            int j2;
-            if (ND == 3) {
-                const int y = j / L, x = j - y * L;
-                j2 = wrapi(y + dy, L) * L + wrapi(x + dx, L);
-            } else {
-                j2 = wrapi(j + dx, L);
-            }
-            const float* ap = x_s + (size_t)((rs + 1 + ds) * S + j2) * P + ig * 8;
-            const float* bp = g_s + (size_t)q * P + og * 8;
+        // sites of the unit as (slice rs, row y, column x); the 2D halves take
+        // alternate columns, the tap's shifted column is a wrap of x + dx
+        const int rows = ND == 3 ? L : 1;
+        for (int rr = 0; rr < G * rows; ++rr) {
+            const int rs = ND == 3 ? rr / L : rr, y = ND == 3 ? rr - rs * L : 0;
+            const int in_row = (rs + 1 + ds) * S + (ND == 3 ? wrapi(y + dy, L) * L : 0);
+            const int g_row = rs * S + y * L;
+            for (int x = half; x < L; x += HALVES) {
+            const int j2 = wrapi(x + dx, L);
+            const float* ap = x_s + (size_t)(in_row + j2) * P + ig * 8;
+            const float* bp = g_s + (size_t)(g_row + x) * P + og * 8;
             const float4 a0 = *reinterpret_cast<const float4*>(ap);
             const float4 a1 = *reinterpret_cast<const float4*>(ap + 4);
             const float4 b0 = *reinterpret_cast<const float4*>(bp);
@@ -680,6 +680,7 @@ __global__ void __launch_bounds__(ND == 3 ? 448 : 288, ND == 3 ? 1 : 2) k_wgrad_
             if (does_bias)
 #pragma unroll
                 for (int o = 0; o < 8; ++o) accb[o] += bv[o];
+            }
         }
     }
     // combine the halves (2D) in a fixed order through shared memory, then write
@@ -1056,11 +1057,15 @@ gf_status reverse_pass(const gf_flow* f, int64_t B, const double* glq, float glq
         float* gb2 = gW2 + (int64_t)C2 * C1 * T;
         float* gW3 = gb2 + C2;
         float* gb3 = gW3 + 2LL * C2 * T;
-        gf_status s = net_fwd<ND>(f, l, xl, B, w, st);               // recompute h1, h2
-        if (s != GF_OK) return s;
-        k_couple_fwd<ND><<<cfg_grid, kThreads, 0, st>>>(w.h2, C2, P + po.W3, P + po.b3, use_tanh, l & 1, L, V, B,
-                                                       xl, w.g3 /* scratch for x_out */, w.s, nullptr);
-        GF_CHECK_LAUNCH();
+        gf_status s;
+        if (fp32_c32_recompute_supported(f)) {                          // h1, h2, s in one launch
+            if ((s = launch_c32_recompute(f, l, B, xl, w.h1, w.h2, w.s, st)) != GF_OK) return s;
+        } else {
+            if ((s = net_fwd<ND>(f, l, xl, B, w, st)) != GF_OK) return s;   // recompute h1, h2
+            k_couple_fwd<ND><<<cfg_grid, kThreads, 0, st>>>(w.h2, C2, P + po.W3, P + po.b3, use_tanh, l & 1, L, V,
+                                                           B, xl, w.g3 /* scratch for x_out */, w.s, nullptr);
+            GF_CHECK_LAUNCH();
+        }
         k_couple_bwd<ND><<<(unsigned)grid1d(BV), kThreads, 0, st>>>(l & 1, use_tanh, L, V, B, xl, w.s, glq,
                                                                    glq_const, w.gx, w.g3);
         GF_CHECK_LAUNCH();
