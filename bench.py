@@ -89,6 +89,28 @@ def fp32_alu_peak_tflops(n_sm: int, mhz: float) -> float:
     return n_sm * 128 * 2 * mhz * 1e6 / 1e12
 
 
+_ALU_PEAK = {}
+
+
+def alu_peak(n_sm: int, mhz: float, fp64: bool = False):
+    """(TFLOP/s, description): the FFMA (DFMA) rate measured on this device by
+    the library's multiply-add probe, taken once per process; the derived
+    lane-count figure when the probe fails."""
+    if fp64 not in _ALU_PEAK:
+        try:
+            import paper_2208_08903_gb300 as P
+            v = max(P.api.alu_peak(fp64=fp64, iters=1 << 17) for _ in range(3)) / 1e12
+            _ALU_PEAK[fp64] = (v, f"{'DFMA' if fp64 else 'FFMA'} measured by gf_alu_peak (best of 3 launches)")
+        except Exception as e:  # noqa: BLE001
+            if fp64:
+                _ALU_PEAK[fp64] = (None, f"probe failed: {e}")
+            else:
+                _ALU_PEAK[fp64] = (fp32_alu_peak_tflops(n_sm, mhz),
+                                   f"FP32 FFMA: {n_sm} SM x 128 lanes x 2 FLOP x {mhz:.0f} MHz (derived; probe "
+                                   f"failed: {e})")
+    return _ALU_PEAK[fp64]
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle sampling during the timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -215,7 +237,7 @@ def bench_train(args, rank, world, local):
     fl = 4 * flops_per_config(shape) * B
     pk, pk_kind = peaks()
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak = fp32_alu_peak_tflops(n_sm, pk.get("sm_max_mhz", 2070.0))
+    peak, peak_kind = alu_peak(n_sm, pk.get("sm_max_mhz", 2070.0))
     ach = fl / (float(np.mean(t)) / 1e3) / 1e12
     return {"metric": "train steps/s (reverse-KL step: forward + backward + Adam)",
             "value": world * args.steps / (total_ms / 1e3), "unit": "steps/s", "n_gpus": world,
@@ -230,8 +252,10 @@ def bench_train(args, rank, world, local):
             # 13 per layer backward, Adam + repack
             "gpu_launches": args.steps * (16 * shape.n_layers + 6),
             "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                         "traffic": None, "note": "algorithmic FLOP = 4 x forward (forward, recompute, "
-                                                  "data and weight gradients)"},
+                         "traffic": None, "peak_kind": peak_kind,
+                         "peak_derived": fp32_alu_peak_tflops(n_sm, pk.get("sm_max_mhz", 2070.0)),
+                         "note": "algorithmic FLOP = 4 x forward (forward, recompute, "
+                                 "data and weight gradients)"},
             "clocks": clk, "loss": float(loss.item())}
 
 
@@ -337,10 +361,10 @@ def bench_gpu(args, rank, world, local):
                 "frac_of_sustained": achieved / pk.get("bf16_tflops_sustained", 1700.0)}
     else:
         mhz = pk.get("sm_max_mhz", 2070.0)
-        peak = fp32_alu_peak_tflops(n_sm, mhz)
+        peak, peak_kind = alu_peak(n_sm, mhz)
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
-                "peak_kind": f"FP32 FFMA: {n_sm} SM x 128 lanes x 2 FLOP x {mhz:.0f} MHz (derived)"}
+                "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                "peak_derived": fp32_alu_peak_tflops(n_sm, mhz)}
     roof["kernel"] = "flow_fp32_kernel" if prec == "fp32" else "flow_bf16_kernel"
     roof["traffic"] = measured_traffic(roof["kernel"], B)
     pipe = measured_counter(roof["kernel"], "tensor_pipe_active_pct")
@@ -463,10 +487,23 @@ def bench_extra(args, dev, flush, pk):
     t = _time_steps(lambda i: P.hmc_trajectory(3, W4["L"], W4["phi4"], phi, W4["n_steps"], W4["eps"], 7, i),
                     20, 3, None)
     traj_ms = float(np.mean(t))
+    # FP64 FLOP per site and leapfrog step: force 20 (three directions of
+    # 2 phi - two neighbours, 2 x lap + 2 m2 phi + 4 lam phi^3), kick 2, drift 2
+    hmc_fl = 24.0 * W4["chains"] * W4["L"] ** 3 * W4["n_steps"]
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    dfma, dfma_kind = alu_peak(n_sm, pk.get("sm_max_mhz", 2070.0), fp64=True)
+    ffma, ffma_kind = alu_peak(n_sm, pk.get("sm_max_mhz", 2070.0), fp64=False)
+    hmc_tf = hmc_fl / (traj_ms / 1e3) / 1e12
     out["hmc_c4"] = {"trajectories_per_s": 1e3 / traj_ms, "ms_per_trajectory_all_chains": traj_ms,
                      "chain_trajectories_per_s": W4["chains"] * 1e3 / traj_ms,
                      "seconds_for_1000_trajectories": traj_ms,
+                     "fp64_tflops": hmc_tf, "dfma_peak_tflops": dfma,
+                     "frac_of_dfma": hmc_tf / dfma if dfma else None, "peak_kind": dfma_kind,
+                     "flop_per_site_step": 24,
                      "workload": "3D L=16, 512 chains, 20 steps, eps=0.05, FP64"}
+    out["alu_peaks_measured"] = {"ffma_tflops": ffma, "dfma_tflops": dfma, "ffma_kind": ffma_kind,
+                                 "dfma_kind": dfma_kind,
+                                 "ffma_derived_tflops": fp32_alu_peak_tflops(n_sm, pk.get("sm_max_mhz", 2070.0))}
 
     # standalone action of FP32 fields: fields larger than L2 (4 x the batch,
     # 268 MB) read in turn without a flush, as for the observables below

@@ -347,6 +347,18 @@ gf_status gf_autocorr(int64_t n, const double* d_y, int32_t t_max, double c_wind
 gf_status gf_ess(int64_t n, const double* d_logw, double* d_ess_out, cudaStream_t stream);
 
 /* ---------------------------------------------------------------------- */
+/* Measurement (no counterpart in the paper: the roofline denominators of   */
+/* this library's FP32 and FP64 kernels)                                   */
+/* ---------------------------------------------------------------------- */
+
+/* Measured multiply-add throughput of the current device: FP32 FFMA
+ * (fp64 = 0) or FP64 DFMA (fp64 = 1), 2 FLOP per FMA, from eight independent
+ * chains per thread on 4 x 256 threads per SM for `iters` iterations, timed
+ * with CUDA events on `stream` (synchronises it).  *flops_per_s_out in FLOP/s.
+ * iters < 8 returns GF_EINVAL. */
+gf_status gf_alu_peak(int32_t fp64, int64_t iters, double* flops_per_s_out, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------- */
 /* Status                                                                  */
 /* ---------------------------------------------------------------------- */
 

@@ -27,7 +27,7 @@ EXPORTED = [
     "gf_flow_backward",
     "gf_phi4_action_vjp", "gf_observables", "gf_chain_gather", "gf_autocorr", "gf_ess",
     "gf_device_status", "gf_status_string", "gf_set_bf16_stall_test",
-    "gf_set_stream_status_slot",
+    "gf_set_stream_status_slot", "gf_alu_peak",
 ]
 
 
@@ -112,6 +112,7 @@ def load():
         "gf_device_status": ([_VP, C.POINTER(_I32)], _I32),
         "gf_set_bf16_stall_test": ([_I64], _I32),
         "gf_set_stream_status_slot": ([_VP, _VP], _I32),
+        "gf_alu_peak": ([_I32, _I64, C.POINTER(_F64), _VP], _I32),
         "gf_status_string": ([_I32], C.c_char_p),
     }
     for name, (args, res) in sig.items():

@@ -1,0 +1,60 @@
+// gf_peaks.cu -- measured FP32 FFMA and FP64 DFMA throughput of the current
+// device, the denominators of the roofline fractions of the FP32 sampler and
+// training kernels and of the FP64 HMC kernel (the BF16 tensor-core and HBM
+// denominators are measured outside this library).
+//
+// Every thread runs eight independent multiply-add chains (enough to cover the
+// pipeline latency at full occupancy) for `iters` iterations; the operands
+// keep the values bounded and the results are folded into one store so the
+// compiler keeps every FMA.  The grid is 4 blocks of 256 threads per SM.
+#include <algorithm>
+
+#include "gf_common.cuh"
+
+namespace gf {
+namespace {
+
+template <typename T>
+__global__ void __launch_bounds__(256) fma_probe_kernel(int64_t iters, T a, T b, T* out) {
+    T x0 = (T)threadIdx.x * (T)1e-3, x1 = x0 + (T)1, x2 = x0 + (T)2, x3 = x0 + (T)3;
+    T x4 = x0 + (T)4, x5 = x0 + (T)5, x6 = x0 + (T)6, x7 = x0 + (T)7;
+    for (int64_t i = 0; i < iters; ++i) {
+        x0 = fma(x0, a, b); x1 = fma(x1, a, b); x2 = fma(x2, a, b); x3 = fma(x3, a, b);
+        x4 = fma(x4, a, b); x5 = fma(x5, a, b); x6 = fma(x6, a, b); x7 = fma(x7, a, b);
+    }
+    const T r = ((x0 + x1) + (x2 + x3)) + ((x4 + x5) + (x6 + x7));
+    if (r == (T)-1.2345) *out = r;                // never true: keeps the chains live
+}
+
+template <typename T>
+gf_status probe(int64_t iters, double* flops_per_s, cudaStream_t stream) {
+    T* sink = nullptr;
+    const int blocks = num_sms() * 4, threads = 256;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return GF_ECUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return GF_ECUDA; }
+    // a = 1 - 2^-20 keeps every chain contracting towards b / (1 - a)
+    const T a = (T)1 - (T)9.5367431640625e-07, b = (T)1e-3;
+    fma_probe_kernel<T><<<blocks, threads, 0, stream>>>(iters / 8, a, b, sink);   // warm-up
+    cudaEventRecord(e0, stream);
+    fma_probe_kernel<T><<<blocks, threads, 0, stream>>>(iters, a, b, sink);
+    cudaEventRecord(e1, stream);
+    gf_status st = GF_OK;
+    float ms = 0.f;
+    if (cudaGetLastError() != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess || ms <= 0.f)
+        st = GF_ECUDA;
+    else
+        *flops_per_s = 2.0 * 8.0 * (double)iters * blocks * threads / (ms * 1e-3);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return st;
+}
+
+}  // namespace
+}  // namespace gf
+
+extern "C" gf_status gf_alu_peak(int32_t fp64, int64_t iters, double* flops_per_s_out, cudaStream_t stream) {
+    if (!flops_per_s_out || iters < 8 || (fp64 != 0 && fp64 != 1)) return GF_EINVAL;
+    return fp64 ? gf::probe<double>(iters, flops_per_s_out, stream) : gf::probe<float>(iters, flops_per_s_out, stream);
+}

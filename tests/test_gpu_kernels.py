@@ -116,3 +116,18 @@ def test_hmc_matches_oracle(orc, nd, L, nc):
         assert np.allclose(t.cpu().numpy(), phi_ref, rtol=1e-10, atol=1e-10)
         phi0 = phi_ref
     assert P.device_status() == 0
+
+
+def test_alu_peak_probe_is_plausible():
+    """The FFMA/DFMA probe's rate sits below the lane-count bound at the
+    device's maximum clock (128 FP32 FMA lanes per SM) and well above a tenth
+    of it; FP64 runs slower than FP32."""
+    require_gpu()
+    import torch
+    from paper_2208_08903_gb300 import api
+    prop = torch.cuda.get_device_properties(0)
+    f32 = api.alu_peak(fp64=False, iters=1 << 15)
+    f64 = api.alu_peak(fp64=True, iters=1 << 12)
+    bound = prop.multi_processor_count * 128 * 2 * 2.2e9      # above every Blackwell boost clock
+    assert 0.1 * bound < f32 < bound
+    assert 0 < f64 < f32
