@@ -351,12 +351,13 @@ gf_status gf_ess(int64_t n, const double* d_logw, double* d_ess_out, cudaStream_
 /* this library's FP32 and FP64 kernels)                                   */
 /* ---------------------------------------------------------------------- */
 
-/* Measured multiply-add throughput of the current device: FP32 FFMA
- * (fp64 = 0) or FP64 DFMA (fp64 = 1), 2 FLOP per FMA, from eight independent
- * chains per thread on 4 x 256 threads per SM for `iters` iterations, timed
- * with CUDA events on `stream` (synchronises it).  *flops_per_s_out in FLOP/s.
- * iters < 8 returns GF_EINVAL. */
-gf_status gf_alu_peak(int32_t fp64, int64_t iters, double* flops_per_s_out, cudaStream_t stream);
+/* Measured multiply-add throughput of the current device: kind 0 = FP32
+ * FFMA, 1 = FP64 DFMA, 2 = packed FP32x2 FMA (fma.rn.f32x2), 2 FLOP per
+ * FP32/FP64 multiply-add, from eight independent multiply-add chains per
+ * thread on 4 x 256 threads per SM for `iters` iterations, timed with CUDA
+ * events on `stream` (synchronises it).  *flops_per_s_out in FLOP/s.
+ * iters < 8 or another kind returns GF_EINVAL. */
+gf_status gf_alu_peak(int32_t kind, int64_t iters, double* flops_per_s_out, cudaStream_t stream);
 
 /* ---------------------------------------------------------------------- */
 /* Status                                                                  */

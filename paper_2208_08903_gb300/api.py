@@ -399,8 +399,10 @@ def set_stream_status_slot(stream, slot: torch.Tensor | None):
                _abi.load().gf_set_stream_status_slot(_stream(stream), _ptr(slot)))
 
 
-def alu_peak(fp64: bool = False, iters: int = 1 << 16) -> float:
-    """gf_alu_peak: measured FP32 FFMA (or FP64 DFMA) throughput in FLOP/s."""
+def alu_peak(fp64: bool = False, iters: int = 1 << 16, packed: bool = False) -> float:
+    """gf_alu_peak: measured FP32 FFMA, FP64 DFMA (fp64) or packed FP32x2 FMA
+    (packed) throughput in FLOP/s."""
     v = C.c_double(0.0)
-    _abi.check("gf_alu_peak", _abi.load().gf_alu_peak(1 if fp64 else 0, int(iters), C.byref(v), _stream()))
+    kind = 1 if fp64 else (2 if packed else 0)
+    _abi.check("gf_alu_peak", _abi.load().gf_alu_peak(kind, int(iters), C.byref(v), _stream()))
     return v.value

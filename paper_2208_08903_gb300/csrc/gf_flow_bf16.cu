@@ -54,6 +54,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include "gf_async.cuh"
 #include "gf_flow.cuh"
 
 namespace gf {
@@ -113,9 +114,6 @@ constexpr int kMma1Warp = 19;                                   // conv1
 constexpr int kIssuers = 4;
 
 // ---------------------------------------------------------------- PTX wrappers
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
 __device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                  :: "r"(smem_u32(dst)), "r"(ncols) : "memory");
@@ -131,19 +129,6 @@ __device__ __forceinline__ void fence_before_sync() {
 }
 __device__ __forceinline__ void fence_after_sync() {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void fence_proxy_async() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-                 " selp.u32 %0, 1, 0, p;\n}\n"
-                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
-    return ok != 0;
 }
 // D[tmem] (+)= A[smem] * B[smem]^T, kind::f16 (BF16 in, FP32 accumulate).
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
@@ -427,21 +412,6 @@ __device__ __forceinline__ bool wait_n(uint64_t* bar, int n, volatile int* abort
 __device__ __forceinline__ void drain_wait(uint64_t* bar, int n) {
     for (long long spins = 0; !mbar_try_wait(bar, (uint32_t)n & 1u) && spins < kWaitLimit; ++spins) {}
 }
-// Arrival that also announces `bytes` of bulk-copy data for the current phase.
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-// Bulk copy global -> shared (16-byte aligned, size a multiple of 16), completing on bar.
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                 :: "r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ uint64_t mbar_arrive(uint64_t* bar) {
-    uint64_t state;
-    asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(state) : "r"(smem_u32(bar)) : "memory");
-    return state;
-}
 
 // Per layer and CTA: 20 conv1 slices (virtual v = -2..17), 18 conv2 slices
 // (u = -1..16), 18 conv3 batches and 16 conv3 slices (w = 0..15).  Batch u is
@@ -519,7 +489,7 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
         for (int i = 0; i < 4; ++i) mbar_init(bar_x + i, kEpiThreads);
         mbar_init(bar_stall, 1);
         *abort_flag = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fence_mbar_init();
     }
     fence_before_sync();
     __syncthreads();

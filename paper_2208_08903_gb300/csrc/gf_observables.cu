@@ -6,10 +6,11 @@
 //
 //  - per configuration: M = mean of phi and C(t) = (1/V) sum_tau Phi(tau)
 //    Phi(tau + t), Phi(tau) = sum of phi over the slice at outermost
-//    coordinate tau.  A slice is V/L contiguous sites, so one warp sums one
-//    slice with coalesced 16-byte loads; lanes and the warp accumulate in FP32
-//    pairs (error-free transformations), so the kernel reads each field once
-//    with little FP64 work.
+//    coordinate tau (V/L contiguous sites).  Threads accumulate in FP32 pairs
+//    (error-free transformations), so the kernel reads each field once with
+//    little FP64 work.  FP32 fields of 2D L = 16, 32, 64 and 3D L = 8, 16 are
+//    streamed through shared memory by bulk copies; other shapes read global
+//    memory directly (a warp per configuration or a block per configuration).
 //  - chain gather: the chain's series O[chain_idx[k]] of a per-proposal
 //    observable.
 //  - Gamma(t) of a series (one CTA per lag, fixed-order FP64 reduction), then
@@ -19,6 +20,7 @@
 #include <algorithm>
 #include <cmath>
 
+#include "gf_async.cuh"
 #include "gf_common.cuh"
 
 namespace gf {
@@ -157,6 +159,121 @@ __global__ void __launch_bounds__(kObsThreads) obs_warp_kernel(int L, int64_t V,
     }
 }
 
+// Streaming form: a block of 128 threads owns a ring of shared-memory buffers
+// that bulk copies fill with whole configurations (BulkRing), so the next
+// configurations arrive while the current one is summed.  The TPS = 128 / L
+// consecutive threads of slice tau each sum every TPS-th 4-site chunk of it
+// with a compensated sum (TwoSum into hi, the exact rounding errors into lo:
+// seven FP32 operations per site), combine their pairs by shuffles and leave
+// Phi(tau) in shared memory; after one block barrier threads t < L form C(t)
+// and thread L forms M, in pair arithmetic widened to FP64 once per output.
+// Phi is double-buffered, so one barrier per configuration suffices.
+constexpr int kOsThreads = 128;
+constexpr long long kOsWaitLimit = 1ll << 24;     // bounded wait for a configuration's bulk copy
+
+template <int ND, int L>
+__global__ void __launch_bounds__(kOsThreads) obs_stream_kernel(int64_t B, double inv_v,
+                                                                const float* __restrict__ phi,
+                                                                double* __restrict__ M_out,
+                                                                double* __restrict__ C_out,
+                                                                int32_t* __restrict__ status) {
+    constexpr int V = ND == 3 ? L * L * L : L * L;
+    constexpr int NBUF = ring_depth<V * 4>();
+    constexpr int CPS = V / L / 4;                          // chunks per slice
+    constexpr int TPS = kOsThreads / L;                     // threads per slice
+    constexpr int PER = CPS >= TPS ? CPS / TPS : 1;         // chunks per thread
+    static_assert((L & (L - 1)) == 0 && L >= 8 && L <= 64 && TPS <= 32, "streaming lattice");
+    static_assert(CPS % TPS == 0 || TPS % CPS == 0, "slice split");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + NBUF * V * 4);  // [NBUF]
+    FF* Phi = reinterpret_cast<FF*>(full + NBUF);                          // [2][L]
+    int* abort_s = reinterpret_cast<int*>(Phi + 2 * L);
+    const int tid = threadIdx.x, tau = tid / TPS, sub = tid % TPS;
+    const BulkRing<NBUF> ring(smem_raw, full, phi, V * 4, B);
+    if (tid == 0) {
+        *abort_s = 0;
+        ring.start();
+    }
+    __syncthreads();
+    int64_t k = 0;
+    for (; k < ring.count; ++k) {
+        const int64_t b = blockIdx.x + k * gridDim.x;
+        const float4* p4 = static_cast<const float4*>(ring.data(k));
+        float hi = 0.f, lo = 0.f;
+        if (!ring.wait(k, kOsWaitLimit)) {
+            set_status(status, GF_ETIMEOUT);
+            *abort_s = 1;
+        } else if (CPS >= TPS || sub < CPS) {
+#pragma unroll
+            for (int j = 0; j < PER; ++j) {
+                const float4 v = p4[tau * CPS + sub + TPS * j];
+                const float c[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float s = hi + c[q], bp = s - hi;
+                    lo += (hi - (s - bp)) + (c[q] - bp);
+                    hi = s;
+                }
+            }
+        }
+        FF a{hi, lo};
+#pragma unroll
+        for (int o = TPS / 2; o > 0; o >>= 1)
+            ff_add(a, FF{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)});
+        FF* ph = Phi + (k & 1) * L;
+        if (sub == 0) ph[tau] = a;
+        __syncthreads();
+        if (*abort_s) break;                    // block-uniform
+        if (tid == 0) ring.refill(k);           // every thread has read this buffer
+        if (tid < L) {
+            if (C_out) {
+                FF c{0.f, 0.f};
+#pragma unroll 4
+                for (int u = 0; u < L; ++u) ff_fma(c, ph[u], ph[(u + tid) & (L - 1)]);
+                C_out[b * L + tid] = ff_to_double(c) * inv_v;
+            }
+        } else if (tid == L && M_out) {
+            FF m{0.f, 0.f};
+#pragma unroll 4
+            for (int u = 0; u < L; ++u) ff_add(m, ph[u]);
+            M_out[b] = ff_to_double(m) * inv_v;
+        }
+    }
+    if (tid == 0) ring.drain(k, kOsWaitLimit);
+}
+
+template <int ND, int L>
+void launch_obs_stream(int64_t B, double inv_v, const float* phi, double* M, double* C, cudaStream_t stream,
+                       bool* ok) {
+    constexpr int V = ND == 3 ? L * L * L : L * L;
+    constexpr int NBUF = ring_depth<V * 4>();
+    const size_t smem = (size_t)NBUF * V * 4 + NBUF * 8 + 2 * L * sizeof(FF) + 16;
+    auto kern = obs_stream_kernel<ND, L>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kOsThreads, smem) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    const int64_t grid = std::min<int64_t>(B, (int64_t)num_sms() * per_sm);
+    kern<<<(unsigned)grid, kOsThreads, smem, stream>>>(B, inv_v, phi, M, C, status_word(stream));
+    *ok = true;
+}
+
+// The streaming kernel for FP32 fields of 2D L = 16, 32, 64 and 3D L = 8, 16
+// that start on a 16-byte boundary; false when the shape or the alignment does
+// not qualify.
+bool launch_obs_stream_if(int nd, int L, int64_t B, double inv_v, const float* phi, double* M, double* C,
+                          cudaStream_t stream) {
+    if ((reinterpret_cast<uintptr_t>(phi) & 15) != 0) return false;
+    bool ok = false;
+    if (nd == 2 && L == 16) launch_obs_stream<2, 16>(B, inv_v, phi, M, C, stream, &ok);
+    else if (nd == 2 && L == 32) launch_obs_stream<2, 32>(B, inv_v, phi, M, C, stream, &ok);
+    else if (nd == 2 && L == 64) launch_obs_stream<2, 64>(B, inv_v, phi, M, C, stream, &ok);
+    else if (nd == 3 && L == 8) launch_obs_stream<3, 8>(B, inv_v, phi, M, C, stream, &ok);
+    else if (nd == 3 && L == 16) launch_obs_stream<3, 16>(B, inv_v, phi, M, C, stream, &ok);
+    return ok;
+}
+
 // out[k][j] = values[(chain_idx[k] - idx0) * width + j]; an index outside
 // [0, n_values) writes NaN and records GF_EINVAL in the status word.
 __global__ void gather_kernel(int64_t n, const int64_t* __restrict__ chain_idx, int64_t idx0, int64_t n_values,
@@ -284,7 +401,9 @@ gf_status gf_observables(int32_t nd, int32_t L, int64_t B, const float* d_phi, d
     if (B == 0) return GF_OK;
     const int64_t V = ipow(L, nd);
     const int64_t S = V / L;
-    if (S % 128 == 0 && L <= kObsWarpMaxL && (reinterpret_cast<uintptr_t>(d_phi) & 15) == 0) {
+    if (launch_obs_stream_if(nd, L, B, 1.0 / (double)V, d_phi, d_M_out, d_C_out, stream)) {
+        // streaming kernel launched
+    } else if (S % 128 == 0 && L <= kObsWarpMaxL && (reinterpret_cast<uintptr_t>(d_phi) & 15) == 0) {
         // warps per block: each warp's table is L x 32 pairs; at most 48 KB per block
         const int wpb = (int)std::max<int64_t>(1, std::min<int64_t>(kObsThreads / 32, 49152 / (256 * (int64_t)L)));
         const size_t smem = (size_t)wpb * L * 32 * sizeof(FF);

@@ -1,7 +1,8 @@
-// gf_peaks.cu -- measured FP32 FFMA and FP64 DFMA throughput of the current
-// device, the denominators of the roofline fractions of the FP32 sampler and
-// training kernels and of the FP64 HMC kernel (the BF16 tensor-core and HBM
-// denominators are measured outside this library).
+// gf_peaks.cu -- measured FP32 FFMA, FP64 DFMA and packed FP32x2 FMA
+// throughput of the current device, the denominators of the roofline
+// fractions of the FP32 sampler and training kernels and of the FP64 HMC
+// kernel (the BF16 tensor-core and HBM denominators are measured outside this
+// library).
 //
 // Every thread runs eight independent multiply-add chains (enough to cover the
 // pipeline latency at full occupancy) for `iters` iterations; the operands
@@ -26,7 +27,29 @@ __global__ void __launch_bounds__(256) fma_probe_kernel(int64_t iters, T a, T b,
     if (r == (T)-1.2345) *out = r;                // never true: keeps the chains live
 }
 
-template <typename T>
+// Packed form: four 64-bit registers, each holding two FP32 lanes, through
+// fma.rn.f32x2 (eight FP32 multiply-adds per iteration, as above).
+__global__ void __launch_bounds__(256) fma_probe_f32x2_kernel(int64_t iters, float a, float b, float* out) {
+    unsigned long long x0, x1, x2, x3, av, bv;
+    const float t = (float)threadIdx.x * 1e-3f;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(x0) : "f"(t), "f"(t + 1.f));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(x1) : "f"(t + 2.f), "f"(t + 3.f));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(x2) : "f"(t + 4.f), "f"(t + 5.f));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(x3) : "f"(t + 6.f), "f"(t + 7.f));
+    asm("mov.b64 %0, {%1, %1};" : "=l"(av) : "f"(a));
+    asm("mov.b64 %0, {%1, %1};" : "=l"(bv) : "f"(b));
+    for (int64_t i = 0; i < iters; ++i) {
+        asm volatile("fma.rn.f32x2 %0, %0, %1, %2;" : "+l"(x0) : "l"(av), "l"(bv));
+        asm volatile("fma.rn.f32x2 %0, %0, %1, %2;" : "+l"(x1) : "l"(av), "l"(bv));
+        asm volatile("fma.rn.f32x2 %0, %0, %1, %2;" : "+l"(x2) : "l"(av), "l"(bv));
+        asm volatile("fma.rn.f32x2 %0, %0, %1, %2;" : "+l"(x3) : "l"(av), "l"(bv));
+    }
+    float r0, r1;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r0), "=f"(r1) : "l"(x0 ^ x1 ^ x2 ^ x3));
+    if (r0 + r1 == -1.2345f) *out = r0;           // never true: keeps the chains live
+}
+
+template <typename T, bool PACKED = false>
 gf_status probe(int64_t iters, double* flops_per_s, cudaStream_t stream) {
     T* sink = nullptr;
     const int blocks = num_sms() * 4, threads = 256;
@@ -35,9 +58,15 @@ gf_status probe(int64_t iters, double* flops_per_s, cudaStream_t stream) {
     if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return GF_ECUDA; }
     // a = 1 - 2^-20 keeps every chain contracting towards b / (1 - a)
     const T a = (T)1 - (T)9.5367431640625e-07, b = (T)1e-3;
-    fma_probe_kernel<T><<<blocks, threads, 0, stream>>>(iters / 8, a, b, sink);   // warm-up
+    auto launch = [&](int64_t n) {
+        if constexpr (PACKED)
+            fma_probe_f32x2_kernel<<<blocks, threads, 0, stream>>>(n, (float)a, (float)b, (float*)sink);
+        else
+            fma_probe_kernel<T><<<blocks, threads, 0, stream>>>(n, a, b, sink);
+    };
+    launch(iters / 8);                            // warm-up
     cudaEventRecord(e0, stream);
-    fma_probe_kernel<T><<<blocks, threads, 0, stream>>>(iters, a, b, sink);
+    launch(iters);
     cudaEventRecord(e1, stream);
     gf_status st = GF_OK;
     float ms = 0.f;
@@ -54,7 +83,9 @@ gf_status probe(int64_t iters, double* flops_per_s, cudaStream_t stream) {
 }  // namespace
 }  // namespace gf
 
-extern "C" gf_status gf_alu_peak(int32_t fp64, int64_t iters, double* flops_per_s_out, cudaStream_t stream) {
-    if (!flops_per_s_out || iters < 8 || (fp64 != 0 && fp64 != 1)) return GF_EINVAL;
-    return fp64 ? gf::probe<double>(iters, flops_per_s_out, stream) : gf::probe<float>(iters, flops_per_s_out, stream);
+extern "C" gf_status gf_alu_peak(int32_t kind, int64_t iters, double* flops_per_s_out, cudaStream_t stream) {
+    if (!flops_per_s_out || iters < 8 || kind < 0 || kind > 2) return GF_EINVAL;
+    if (kind == 1) return gf::probe<double>(iters, flops_per_s_out, stream);
+    if (kind == 2) return gf::probe<float, true>(iters, flops_per_s_out, stream);
+    return gf::probe<float>(iters, flops_per_s_out, stream);
 }

@@ -80,7 +80,7 @@ def test_argument_errors_without_gpu(lib):
     assert lib.gf_mh_chain_workspace_bytes(10) == 80
     fl = C.c_double()
     assert lib.gf_alu_peak(0, 4, C.byref(fl), None) == _abi.GF_EINVAL       # iters < 8
-    assert lib.gf_alu_peak(2, 1024, C.byref(fl), None) == _abi.GF_EINVAL    # neither FP32 nor FP64
+    assert lib.gf_alu_peak(3, 1024, C.byref(fl), None) == _abi.GF_EINVAL    # no such kind
     assert lib.gf_alu_peak(0, 1024, None, None) == _abi.GF_EINVAL
     assert lib.gf_mh_chain_workspace_bytes(0) == 0
     assert lib.gf_hmc_trajectory(2, 8, C.byref(p), 4, None, 0, 0.1, 0, 0, None, None, None) == _abi.GF_EINVAL

@@ -31,6 +31,25 @@ def test_observables_match_oracle(orc, nd, L, B):
     assert_sites_close(Cc.cpu().numpy(), rC, rtol=RTOL, what="C(t)")
 
 
+@pytest.mark.parametrize("nd,L,B", [(2, 16, 3001), (2, 32, 1201), (2, 64, 917), (3, 8, 2500), (3, 16, 1000)])
+def test_observables_streaming_lattices(orc, nd, L, B):
+    """The bulk-copy streaming kernel's lattices with more configurations than
+    one wave of blocks holds, so every block cycles through its buffer ring."""
+    torch, P = require_gpu()
+    V = L**nd
+    phi = (orc.prior(V, B, seed=5 + L, counter0=0, f32=True) * 0.7 - 0.2).astype(np.float32).astype(np.float64)
+    t = torch.tensor(phi, dtype=torch.float32, device="cuda")
+    M, Cc = P.observables(nd, L, t)
+    rM, rC = orc.observables(nd, L, phi)
+    assert_sites_close(M.cpu().numpy()[:, None], rM[:, None], rtol=RTOL, what="M")
+    assert_sites_close(Cc.cpu().numpy(), rC, rtol=RTOL, what="C(t)")
+    # either output alone
+    M1, none_c = P.observables(nd, L, t, two_point=False)
+    none_m, C1 = P.observables(nd, L, t, magnetisation=False)
+    assert none_c is None and none_m is None
+    assert torch.equal(M1, M) and torch.equal(C1, Cc)
+
+
 def test_observables_at_bench_size_sampled(orc):
     torch, P = require_gpu()
     nd, L, B = 3, 16, 4096
