@@ -249,6 +249,10 @@ void free_flow(gf_flow* f) {
     cudaFree(f->d_packed);
     cudaFree(f->d_sched);
     cudaFree(f->d_bf16);
+    for (cudaEvent_t e : f->ev_fork)
+        if (e) cudaEventDestroy(e);
+    if (f->ev_join) cudaEventDestroy(f->ev_join);
+    if (f->side) cudaStreamDestroy(f->side);
     delete f;
 }
 
@@ -317,6 +321,10 @@ gf_status gf_flow_create_ex(const gf_flow_shape_ex* shape, const double* weights
     f->n_hidden = shape->n_hidden;
     for (int j = 0; j < shape->n_hidden; ++j) f->hidden[j] = shape->hidden[j];
     f->variant = !dflt;
+    if (cudaStreamCreateWithFlags(&f->side, cudaStreamNonBlocking) != cudaSuccess) { free_flow(f); return GF_ECUDA; }
+    for (cudaEvent_t& e : f->ev_fork)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) { free_flow(f); return GF_ECUDA; }
+    if (cudaEventCreateWithFlags(&f->ev_join, cudaEventDisableTiming) != cudaSuccess) { free_flow(f); return GF_ECUDA; }
     gf_status st;
     if (f->variant) {
         f->canon_stride = 0;

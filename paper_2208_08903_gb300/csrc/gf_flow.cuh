@@ -68,6 +68,10 @@ struct gf_flow {
     int32_t vcin[GF_MAX_HIDDEN + 1], vcout[GF_MAX_HIDDEN + 1], vcop[GF_MAX_HIDDEN + 1];
     int Cp;                 // shared-memory row width of the hidden activations (odd)
     int vthreads;
+    // reverse pass: the weight gradients of a layer run on `side`, forked from
+    // and joined back into the caller's stream with these events
+    cudaStream_t side;
+    cudaEvent_t ev_fork[3], ev_join;
 };
 
 namespace gf {

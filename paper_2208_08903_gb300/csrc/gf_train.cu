@@ -96,7 +96,7 @@ struct ConvArgs {
     int L, V; int64_t B;
 };
 
-template <int ND, int VEC>
+template <int ND, int VEC, bool MASKED>
 __global__ void __launch_bounds__(kThreads) k_conv(const ConvArgs a) {
     extern __shared__ __align__(16) float wsm[];
     const int T = ND == 3 ? 27 : 9;
@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(kThreads) k_conv(const ConvArgs a) {
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 m[k] = nbr<ND>(n[k], t, a.L);
-                msk[k] = (a.mask < 0 || parity<ND>(m[k], a.L) == a.mask) ? 1.f : 0.f;
+                msk[k] = (!MASKED || parity<ND>(m[k], a.L) == a.mask) ? 1.f : 0.f;
             }
             const float* Wt = wsm + t * a.Cin * a.Cout + co;
             for (int c0 = 0; c0 < a.Cin; c0 += VEC) {
@@ -156,8 +156,10 @@ __global__ void __launch_bounds__(kThreads) k_conv(const ConvArgs a) {
                     } else {
                         hv[k][0] = __ldg(p);
                     }
+                    if constexpr (MASKED) {
 #pragma unroll
-                    for (int q = 0; q < VEC; ++q) hv[k][q] *= msk[k];
+                        for (int q = 0; q < VEC; ++q) hv[k][q] *= msk[k];
+                    }
                 }
 #pragma unroll
                 for (int q = 0; q < VEC; ++q) {
@@ -908,9 +910,15 @@ gf_status conv(const ConvArgs& a, cudaStream_t st) {
         return true;
     };
     bool ok;
-    if (a.Cin % 4 == 0) ok = go(k_conv<ND, 4>);
-    else if (a.Cin % 2 == 0) ok = go(k_conv<ND, 2>);
-    else ok = go(k_conv<ND, 1>);
+    if (a.mask >= 0) {      // masked input (conv1 of a coupling): parity test per neighbour
+        if (a.Cin % 4 == 0) ok = go(k_conv<ND, 4, true>);
+        else if (a.Cin % 2 == 0) ok = go(k_conv<ND, 2, true>);
+        else ok = go(k_conv<ND, 1, true>);
+    } else {
+        if (a.Cin % 4 == 0) ok = go(k_conv<ND, 4, false>);
+        else if (a.Cin % 2 == 0) ok = go(k_conv<ND, 2, false>);
+        else ok = go(k_conv<ND, 1, false>);
+    }
     if (!ok) return GF_ECUDA;
     GF_CHECK_LAUNCH();
     return GF_OK;
@@ -1069,18 +1077,31 @@ gf_status reverse_pass(const gf_flow* f, int64_t B, const double* glq, float glq
         k_couple_bwd<ND><<<(unsigned)grid1d(BV), kThreads, 0, st>>>(l & 1, use_tanh, L, V, B, xl, w.s, glq,
                                                                    glq_const, w.gx, w.g3);
         GF_CHECK_LAUNCH();
+        // The data gradients (gh2, gh1, gx) stay on `st`; each weight gradient
+        // runs on the flow's side stream as soon as its inputs exist and
+        // overlaps the next data gradient.  The side stream only reads
+        // activations and writes G and the partial sums; the next layer (which
+        // rewrites the activations) and the caller wait for it.
+        if (cudaEventRecord(f->ev_fork[0], st) != cudaSuccess || cudaStreamWaitEvent(f->side, f->ev_fork[0], 0) != cudaSuccess)
+            return GF_ECUDA;
         WgArgs a3{w.h2, C2, -1, w.g3, 2, w.partial, L, V, B};
-        if ((s = wgrad<ND>(a3, gW3, gb3, scale, st)) != GF_OK) return s;
+        if ((s = wgrad<ND>(a3, gW3, gb3, scale, f->side)) != GF_OK) return s;
         ConvArgs d3{w.g3, 2, -1, Wb + (int64_t)T * C1 + (int64_t)T * C2 * C1, nullptr, C2, w.gh2, w.h2, 1, slope, L, V, B};
         if ((s = conv<ND>(d3, st)) != GF_OK) return s;                // gh2 * LReLU'
+        if (cudaEventRecord(f->ev_fork[1], st) != cudaSuccess || cudaStreamWaitEvent(f->side, f->ev_fork[1], 0) != cudaSuccess)
+            return GF_ECUDA;
         WgArgs a2{w.h1, C1, -1, w.gh2, C2, w.partial, L, V, B};
-        if ((s = wgrad<ND>(a2, gW2, gb2, scale, st)) != GF_OK) return s;
+        if ((s = wgrad<ND>(a2, gW2, gb2, scale, f->side)) != GF_OK) return s;
         ConvArgs d2{w.gh2, C2, -1, Wb + (int64_t)T * C1, nullptr, C1, w.gh1, w.h1, 1, slope, L, V, B};
         if ((s = conv<ND>(d2, st)) != GF_OK) return s;                // gh1 * LReLU'
+        if (cudaEventRecord(f->ev_fork[2], st) != cudaSuccess || cudaStreamWaitEvent(f->side, f->ev_fork[2], 0) != cudaSuccess)
+            return GF_ECUDA;
         WgArgs a1{xl, 1, l & 1, w.gh1, C1, w.partial, L, V, B};
-        if ((s = wgrad<ND>(a1, gW1, gb1, scale, st)) != GF_OK) return s;
+        if ((s = wgrad<ND>(a1, gW1, gb1, scale, f->side)) != GF_OK) return s;
         k_conv1_bwd<ND><<<(unsigned)grid1d(BV), kThreads, 0, st>>>(w.gh1, C1, Wb, l & 1, L, V, B, w.gx);
         GF_CHECK_LAUNCH();
+        if (cudaEventRecord(f->ev_join, f->side) != cudaSuccess || cudaStreamWaitEvent(st, f->ev_join, 0) != cudaSuccess)
+            return GF_ECUDA;
     }
     return GF_OK;
 }
