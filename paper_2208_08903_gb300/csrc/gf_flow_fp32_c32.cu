@@ -21,18 +21,20 @@
 // the updated sites of slices k-3, k-2, k-1 are added at once; after step 17
 // every s, t is complete and the affine update runs.  Per conv2 weight/input
 // read: 4 h1 loads (one per site) and 2 broadcast 16-byte weight loads per
-// tap plane feed 32 FMAs per plane.
+// tap plane feed 32 FMAs per plane, issued as 16 packed FP32-pair FMAs
+// (fma.rn.f32x2: same rounding, half the issue slots).
 //
 // 2D L=32 with hidden width 32 (the 2D training workload's flow) uses the same
 // plan with slabs of 16 rows instead of z-slices: per layer two steps, each
 // computing h1 of the slab's 16 rows plus one halo row on each side (18 rows,
 // 12.5 % extra conv1 work), conv2 of the 16 rows from that buffer (a thread
 // holds 8 sites x 8 channels: 8 h1 loads and 2 broadcast weight loads feed 64
-// FMAs), h2 of the slab, and its conv3 contributions to the s, t accumulators
-// of rows -1 .. 16 of the slab.
+// FMAs, issued as 32 packed FP32-pair FMAs), h2 of the slab, and its conv3
+// contributions to the s, t accumulators of rows -1 .. 16 of the slab.
 #include <algorithm>
 #include <cstring>
 
+#include "gf_f32x2.cuh"
 #include "gf_flow.cuh"
 
 namespace gf {
@@ -115,11 +117,27 @@ __device__ __forceinline__ void conv1_slice(const float* __restrict__ x, const f
     for (int c = 0; c < kC; ++c) row[c] = lrelu(acc[c], slope);
 }
 
-// Accumulator ring: acc[r][k][j] = channel co8 + j of site k of the output
-// slice held in ring slot r.
+// Accumulator ring: a[r][k][p] = channels co8 + 2p, co8 + 2p + 1 of site k of
+// the output slice held in ring slot r, as a packed FP32 pair: conv2 runs as
+// fma.rn.f32x2 (two output channels per instruction, the same rounding as two
+// fmaf), which halves the issue slots of the FMA stream.
 struct Ring {
-    float a[3][4][8];
+    f32x2 a[3][4][4];
 };
+
+// one input channel of one tap plane: a[R][k][.] += h[k] * (w[co8 .. co8 + 7])
+template <int R>
+__device__ __forceinline__ void ring_fma(Ring& g, const f32x2 (&hh)[4], const float* __restrict__ w) {
+    const ulonglong2 u = *reinterpret_cast<const ulonglong2*>(w);
+    const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(w + 4);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        g.a[R][k][0] = f2_fma(hh[k], u.x, g.a[R][k][0]);
+        g.a[R][k][1] = f2_fma(hh[k], u.y, g.a[R][k][1]);
+        g.a[R][k][2] = f2_fma(hh[k], v.x, g.a[R][k][2]);
+        g.a[R][k][3] = f2_fma(hh[k], v.y, g.a[R][k][3]);
+    }
+}
 
 // conv2 contributions of h1 slice zs to the output slices in ring slots RM
 // (tap plane dz = -1), R0 (dz = 0) and RP (dz = +1); PM / P0 / PP say which of
@@ -139,54 +157,23 @@ __device__ __forceinline__ void conv2_step(Ring& g, const float* __restrict__ h1
         const float* wp = W2 + (size_t)(2 * 9 + tp) * kC * kC + co8;
 #pragma unroll 4
         for (int ci = 0; ci < kC; ++ci) {
-            float h[4];
+            f32x2 hh[4];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) h[k] = h1[base[k] + ci];
-            if (PM) {
-                const float4 u = *reinterpret_cast<const float4*>(wm + ci * kC);
-                const float4 v = *reinterpret_cast<const float4*>(wm + ci * kC + 4);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    g.a[RM][k][0] = fmaf(h[k], u.x, g.a[RM][k][0]); g.a[RM][k][1] = fmaf(h[k], u.y, g.a[RM][k][1]);
-                    g.a[RM][k][2] = fmaf(h[k], u.z, g.a[RM][k][2]); g.a[RM][k][3] = fmaf(h[k], u.w, g.a[RM][k][3]);
-                    g.a[RM][k][4] = fmaf(h[k], v.x, g.a[RM][k][4]); g.a[RM][k][5] = fmaf(h[k], v.y, g.a[RM][k][5]);
-                    g.a[RM][k][6] = fmaf(h[k], v.z, g.a[RM][k][6]); g.a[RM][k][7] = fmaf(h[k], v.w, g.a[RM][k][7]);
-                }
-            }
-            if (P0) {
-                const float4 u = *reinterpret_cast<const float4*>(w0 + ci * kC);
-                const float4 v = *reinterpret_cast<const float4*>(w0 + ci * kC + 4);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    g.a[R0][k][0] = fmaf(h[k], u.x, g.a[R0][k][0]); g.a[R0][k][1] = fmaf(h[k], u.y, g.a[R0][k][1]);
-                    g.a[R0][k][2] = fmaf(h[k], u.z, g.a[R0][k][2]); g.a[R0][k][3] = fmaf(h[k], u.w, g.a[R0][k][3]);
-                    g.a[R0][k][4] = fmaf(h[k], v.x, g.a[R0][k][4]); g.a[R0][k][5] = fmaf(h[k], v.y, g.a[R0][k][5]);
-                    g.a[R0][k][6] = fmaf(h[k], v.z, g.a[R0][k][6]); g.a[R0][k][7] = fmaf(h[k], v.w, g.a[R0][k][7]);
-                }
-            }
-            if (PP) {
-                const float4 u = *reinterpret_cast<const float4*>(wp + ci * kC);
-                const float4 v = *reinterpret_cast<const float4*>(wp + ci * kC + 4);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    g.a[RP][k][0] = fmaf(h[k], u.x, g.a[RP][k][0]); g.a[RP][k][1] = fmaf(h[k], u.y, g.a[RP][k][1]);
-                    g.a[RP][k][2] = fmaf(h[k], u.z, g.a[RP][k][2]); g.a[RP][k][3] = fmaf(h[k], u.w, g.a[RP][k][3]);
-                    g.a[RP][k][4] = fmaf(h[k], v.x, g.a[RP][k][4]); g.a[RP][k][5] = fmaf(h[k], v.y, g.a[RP][k][5]);
-                    g.a[RP][k][6] = fmaf(h[k], v.z, g.a[RP][k][6]); g.a[RP][k][7] = fmaf(h[k], v.w, g.a[RP][k][7]);
-                }
-            }
+            for (int k = 0; k < 4; ++k) hh[k] = f2_splat(h1[base[k] + ci]);
+            if (PM) ring_fma<RM>(g, hh, wm + ci * kC);
+            if (P0) ring_fma<R0>(g, hh, w0 + ci * kC);
+            if (PP) ring_fma<RP>(g, hh, wp + ci * kC);
         }
     }
 }
 
 template <int R>
 __device__ __forceinline__ void ring_init(Ring& g, const float* __restrict__ b2, int co8) {
-    const float4 u = *reinterpret_cast<const float4*>(b2 + co8);
-    const float4 v = *reinterpret_cast<const float4*>(b2 + co8 + 4);
+    const ulonglong2 u = *reinterpret_cast<const ulonglong2*>(b2 + co8);
+    const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(b2 + co8 + 4);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        g.a[R][k][0] = u.x; g.a[R][k][1] = u.y; g.a[R][k][2] = u.z; g.a[R][k][3] = u.w;
-        g.a[R][k][4] = v.x; g.a[R][k][5] = v.y; g.a[R][k][6] = v.z; g.a[R][k][7] = v.w;
+        g.a[R][k][0] = u.x; g.a[R][k][1] = u.y; g.a[R][k][2] = v.x; g.a[R][k][3] = v.y;
     }
 }
 
@@ -198,7 +185,10 @@ __device__ __forceinline__ void ring_store(const Ring& g, float* __restrict__ h2
     for (int k = 0; k < 4; ++k) {
         float* row = h2 + ss[k] * kCP + co8;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) row[j] = lrelu(g.a[R][k][j], slope);
+        for (int p = 0; p < 4; ++p) {
+            row[2 * p] = lrelu(f2_lo(g.a[R][k][p]), slope);
+            row[2 * p + 1] = lrelu(f2_hi(g.a[R][k][p]), slope);
+        }
     }
 }
 
@@ -378,6 +368,37 @@ __global__ void __launch_bounds__(kThr, 1) flow_fp32_c32_kernel(const C32Args a)
 }
 
 // ------------------------------------------------------------------ 2D L=32, C=32
+// 2D slab conv2 (packed FP32 pairs as in the 3D ring): acc[k][p] holds
+// channels co8 + 2p, co8 + 2p + 1 of site k; init from the bias, then one tap:
+// sites k at hb + k * kstride (h1 rows of pitch kCP), weights wt[ci * 32 + co8 ..].
+__device__ __forceinline__ void slab_init(f32x2 (&acc)[8][4], const float* __restrict__ b2, int co8) {
+    const ulonglong2 u = *reinterpret_cast<const ulonglong2*>(b2 + co8);
+    const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(b2 + co8 + 4);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        acc[k][0] = u.x; acc[k][1] = u.y; acc[k][2] = v.x; acc[k][3] = v.y;
+    }
+}
+__device__ __forceinline__ void slab_tap(f32x2 (&acc)[8][4], const float* __restrict__ hb, int kstride,
+                                         const float* __restrict__ wt) {
+#pragma unroll 4
+    for (int ci = 0; ci < kC; ++ci) {
+        const ulonglong2 u = *reinterpret_cast<const ulonglong2*>(wt + ci * kC);
+        const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(wt + ci * kC + 4);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const f32x2 hh = f2_splat(hb[k * kstride + ci]);
+            acc[k][0] = f2_fma(hh, u.x, acc[k][0]);
+            acc[k][1] = f2_fma(hh, u.y, acc[k][1]);
+            acc[k][2] = f2_fma(hh, v.x, acc[k][2]);
+            acc[k][3] = f2_fma(hh, v.y, acc[k][3]);
+        }
+    }
+}
+__device__ __forceinline__ float slab_out(const f32x2 (&acc)[8][4], int k, int j) {
+    return (j & 1) ? f2_hi(acc[k][j >> 1]) : f2_lo(acc[k][j >> 1]);
+}
+
 namespace d2 {
 constexpr int L = 32, V = 1024, T = 9, ROWS = 16, HROWS = ROWS + 2;
 constexpr int kOffX = 0;
@@ -481,41 +502,20 @@ __global__ void __launch_bounds__(kThr, 1) flow_fp32_c32_2d_kernel(const C32Args
                 __syncthreads();
                 // conv2 of the 16 rows: sites 256 half + lane + 32 k (row = k + 8 half), channels co8..co8+7
                 {
-                    float acc[8][8];
-                    {
-                        const float4 u = *reinterpret_cast<const float4*>(b2 + co8);
-                        const float4 v = *reinterpret_cast<const float4*>(b2 + co8 + 4);
-#pragma unroll
-                        for (int k = 0; k < 8; ++k) {
-                            acc[k][0] = u.x; acc[k][1] = u.y; acc[k][2] = u.z; acc[k][3] = u.w;
-                            acc[k][4] = v.x; acc[k][5] = v.y; acc[k][6] = v.z; acc[k][7] = v.w;
-                        }
-                    }
+                    f32x2 acc[8][4];
+                    slab_init(acc, b2, co8);
 #pragma unroll 1
                     for (int t = 0; t < d2::T; ++t) {
                         const int dy = t / 3 - 1, dx = t % 3 - 1;
                         const int xs = (lane + dx) & 31;
                         const float* hb = h1 + ((8 * half + dy + 1) * d2::L + xs) * kCP;   // row k: + k * d2::L * kCP
-                        const float* wt = W2 + (size_t)t * kC * kC + co8;
-#pragma unroll 4
-                        for (int ci = 0; ci < kC; ++ci) {
-                            const float4 u = *reinterpret_cast<const float4*>(wt + ci * kC);
-                            const float4 v = *reinterpret_cast<const float4*>(wt + ci * kC + 4);
-#pragma unroll
-                            for (int k = 0; k < 8; ++k) {
-                                const float h = hb[k * d2::L * kCP + ci];
-                                acc[k][0] = fmaf(h, u.x, acc[k][0]); acc[k][1] = fmaf(h, u.y, acc[k][1]);
-                                acc[k][2] = fmaf(h, u.z, acc[k][2]); acc[k][3] = fmaf(h, u.w, acc[k][3]);
-                                acc[k][4] = fmaf(h, v.x, acc[k][4]); acc[k][5] = fmaf(h, v.y, acc[k][5]);
-                                acc[k][6] = fmaf(h, v.z, acc[k][6]); acc[k][7] = fmaf(h, v.w, acc[k][7]);
-                            }
-                        }
+                        slab_tap(acc, hb, d2::L * kCP, W2 + (size_t)t * kC * kC + co8);
                     }
 #pragma unroll
                     for (int k = 0; k < 8; ++k) {
                         float* row = h2 + ((8 * half + k) * d2::L + lane) * kCP + co8;
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) row[j] = lrelu(acc[k][j], a.slope);
+                        for (int j = 0; j < 8; ++j) row[j] = lrelu(slab_out(acc, k, j), a.slope);
                     }
                 }
                 __syncthreads();
@@ -656,41 +656,20 @@ __global__ void __launch_bounds__(kThr, 1) c32_2d_recompute_kernel(const C32Args
                 *reinterpret_cast<float4*>(h1_out + chunk(b, (r0 << 5) + site, c4)) = make_float4(rw[0], rw[1], rw[2], rw[3]);
             }
             {
-                float acc[8][8];
-                {
-                    const float4 u = *reinterpret_cast<const float4*>(b2 + co8);
-                    const float4 v = *reinterpret_cast<const float4*>(b2 + co8 + 4);
-#pragma unroll
-                    for (int k = 0; k < 8; ++k) {
-                        acc[k][0] = u.x; acc[k][1] = u.y; acc[k][2] = u.z; acc[k][3] = u.w;
-                        acc[k][4] = v.x; acc[k][5] = v.y; acc[k][6] = v.z; acc[k][7] = v.w;
-                    }
-                }
+                f32x2 acc[8][4];
+                slab_init(acc, b2, co8);
 #pragma unroll 1
                 for (int t = 0; t < d2::T; ++t) {
                     const int dy = t / 3 - 1, dx = t % 3 - 1;
                     const int xs = (lane + dx) & 31;
                     const float* hb = h1 + ((8 * half + dy + 1) * L + xs) * kCP;
-                    const float* wt = W2 + (size_t)t * kC * kC + co8;
-#pragma unroll 4
-                    for (int ci = 0; ci < kC; ++ci) {
-                        const float4 u = *reinterpret_cast<const float4*>(wt + ci * kC);
-                        const float4 v = *reinterpret_cast<const float4*>(wt + ci * kC + 4);
-#pragma unroll
-                        for (int k = 0; k < 8; ++k) {
-                            const float h = hb[k * L * kCP + ci];
-                            acc[k][0] = fmaf(h, u.x, acc[k][0]); acc[k][1] = fmaf(h, u.y, acc[k][1]);
-                            acc[k][2] = fmaf(h, u.z, acc[k][2]); acc[k][3] = fmaf(h, u.w, acc[k][3]);
-                            acc[k][4] = fmaf(h, v.x, acc[k][4]); acc[k][5] = fmaf(h, v.y, acc[k][5]);
-                            acc[k][6] = fmaf(h, v.z, acc[k][6]); acc[k][7] = fmaf(h, v.w, acc[k][7]);
-                        }
-                    }
+                    slab_tap(acc, hb, L * kCP, W2 + (size_t)t * kC * kC + co8);
                 }
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
                     float o[8];
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) o[j] = lrelu(acc[k][j], a.slope);
+                    for (int j = 0; j < 8; ++j) o[j] = lrelu(slab_out(acc, k, j), a.slope);
                     float* row = h2 + ((8 * half + k) * L + lane) * kCP + co8;
 #pragma unroll
                     for (int j = 0; j < 8; ++j) row[j] = o[j];
