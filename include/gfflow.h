@@ -226,9 +226,11 @@ gf_status gf_mh_chain(gf_mh_state* d_state, int64_t n, const double* d_logw,
  * device array inside the library (GF_MH_NOALLOC_MAX_N entries = 1 MiB,
  * held on every device that loads the library until the process exits).  The caller still passes the state,
  * log weights and outputs (same meaning as for gf_mh_chain).  No memory is
- * allocated.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  n > GF_MH_NOALLOC_MAX_N returns GF_EINVAL.
+ * allocated.  Every call made outside stream capture looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current, so a device
+ * reset or a new primary context is followed; a call being captured into a
+ * graph reuses the last address, so make one call on the device before
+ * capturing.  n > GF_MH_NOALLOC_MAX_N returns GF_EINVAL.
  * Every call on a device shares the one array and leaves its contents
  * behind; each call writes every entry it reads before reading it, so
  * nothing needs clearing, but calls that overlap on the GPU (different

@@ -116,7 +116,10 @@ gf_status mh_launch(gf_mh_state* d_state, int64_t n, const double* d_logw, int64
 // ---------------------------------------------------------------------------
 // Allocation-free variant: log u goes to a fixed device array owned by the
 // library instead of caller workspace.  Host code cannot use the array's
-// name as a device address, so its address is looked up once per device.
+// name as a device address, so its address is looked up on every call made
+// outside stream capture (a device reset or a new primary context can move
+// it) and cached per device; a call being captured into a graph uses the
+// cached address (looked up first if there is none).
 // ---------------------------------------------------------------------------
 static __device__ __align__(256) int64_t g_mh_noalloc_keys[GF_MH_NOALLOC_MAX_N];
 
@@ -125,12 +128,14 @@ constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 int64_t* g_noalloc_ptr[kMaxDevices] = {};
 
-gf_status noalloc_scratch(int64_t** out) {
+gf_status noalloc_scratch(cudaStream_t stream, int64_t** out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return GF_ECUDA;
     if (dev < 0 || dev >= kMaxDevices) return GF_EUNSUPPORTED;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(stream, &cs) != cudaSuccess) return GF_ECUDA;
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (g_noalloc_ptr[dev] == nullptr) {
+    if (g_noalloc_ptr[dev] == nullptr || cs == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_mh_noalloc_keys) != cudaSuccess || p == nullptr) return GF_ECUDA;
         g_noalloc_ptr[dev] = static_cast<int64_t*>(p);
@@ -168,7 +173,7 @@ gf_status gf_mh_chain_noalloc(gf_mh_state* d_state, int64_t n, const double* d_l
     if (n == 0) return GF_OK;
     if (!d_logw) return GF_EINVAL;
     int64_t* scratch = nullptr;
-    const gf_status st = noalloc_scratch(&scratch);
+    const gf_status st = noalloc_scratch(stream, &scratch);
     if (st != GF_OK) return st;
     return mh_launch(d_state, n, d_logw, d_chain_idx_out, d_acc_out, scratch, stream);
 }
