@@ -321,10 +321,6 @@ gf_status gf_flow_create_ex(const gf_flow_shape_ex* shape, const double* weights
     f->n_hidden = shape->n_hidden;
     for (int j = 0; j < shape->n_hidden; ++j) f->hidden[j] = shape->hidden[j];
     f->variant = !dflt;
-    if (cudaStreamCreateWithFlags(&f->side, cudaStreamNonBlocking) != cudaSuccess) { free_flow(f); return GF_ECUDA; }
-    for (cudaEvent_t& e : f->ev_fork)
-        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) { free_flow(f); return GF_ECUDA; }
-    if (cudaEventCreateWithFlags(&f->ev_join, cudaEventDisableTiming) != cudaSuccess) { free_flow(f); return GF_ECUDA; }
     gf_status st;
     if (f->variant) {
         f->canon_stride = 0;
@@ -375,6 +371,11 @@ gf_status gf_flow_create_ex(const gf_flow_shape_ex* shape, const double* weights
     std::vector<float> w32((size_t)std::max<int64_t>(f->n_params, 1));
     for (int64_t i = 0; i < f->n_params; ++i) w32[i] = (float)weights_host[i];
 
+    // side stream and events of the training reverse pass
+    if (cudaStreamCreateWithFlags(&f->side, cudaStreamNonBlocking) != cudaSuccess) { free_flow(f); return GF_ECUDA; }
+    for (cudaEvent_t& e : f->ev_fork)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) { free_flow(f); return GF_ECUDA; }
+    if (cudaEventCreateWithFlags(&f->ev_join, cudaEventDisableTiming) != cudaSuccess) { free_flow(f); return GF_ECUDA; }
     if (cudaMalloc(&f->d_canon, sizeof(float) * w32.size()) != cudaSuccess ||
         cudaMalloc(&f->d_packed, sizeof(float) * std::max<int64_t>(1, f->packed_stride * shape->n_layers)) != cudaSuccess ||
         cudaMalloc(&f->d_sched, sizeof(Phase) * sched.size()) != cudaSuccess) {
