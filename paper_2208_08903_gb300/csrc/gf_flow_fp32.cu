@@ -74,10 +74,13 @@ __device__ __forceinline__ int coord_sum_in_slice(int j, int L) {
 
 // Swizzled float4 chunk of a site row of C floats (conflict-free LDS.128
 // when consecutive lanes read consecutive sites): xor with the site index for
-// a power-of-two number of chunks, a rotation otherwise (C = 24).
+// a power-of-two number of chunks, a rotation otherwise (ROT: C = 24).  ROT is
+// a template parameter so the power-of-two kernels carry no division.
+template <bool ROT>
 __device__ __forceinline__ int swz(int chunk, int j, int C) {
     const int n = C >> 2;
-    return (n & (n - 1)) == 0 ? chunk ^ (j & (n - 1)) : (chunk + j) % n;
+    if constexpr (ROT) return (chunk + j) % n;
+    else return chunk ^ (j & (n - 1));
 }
 
 __device__ __forceinline__ float lrelu(float v, float a) { return v > 0.f ? v : a * v; }
@@ -96,7 +99,7 @@ __device__ __forceinline__ float ldw(const float* p) {
 }
 
 // ---------------------------------------------------------------- conv1
-template <int ND, bool WS>
+template <int ND, bool WS, bool ROT>
 __device__ void phase_h1(const FlowArgs& a, const float* __restrict__ Wl, const Phase& ph,
                          const float* x, float* h1, int frozen) {
     const int L = a.L, S = a.S, C1 = a.C1, T = (ND == 3) ? 27 : 9;
@@ -132,15 +135,15 @@ __device__ void phase_h1(const FlowArgs& a, const float* __restrict__ Wl, const 
                                       lrelu(acc[2], a.slope), lrelu(acc[3], a.slope));
         const float4 o1 = make_float4(lrelu(acc[4], a.slope), lrelu(acc[5], a.slope),
                                       lrelu(acc[6], a.slope), lrelu(acc[7], a.slope));
-        *reinterpret_cast<float4*>(row + (swz(co >> 2, j, C1) << 2)) = o0;
-        *reinterpret_cast<float4*>(row + (swz((co >> 2) + 1, j, C1) << 2)) = o1;
+        *reinterpret_cast<float4*>(row + (swz<ROT>(co >> 2, j, C1) << 2)) = o0;
+        *reinterpret_cast<float4*>(row + (swz<ROT>((co >> 2) + 1, j, C1) << 2)) = o1;
     }
 }
 
 // ---------------------------------------------------------------- conv2
 // Warp task = 128 consecutive chunk sites x 8 output channels; lane i owns
 // sites i, i+32, i+64, i+96 (register tile 4 x 8), weights are warp-uniform.
-template <int ND, bool WS>
+template <int ND, bool WS, bool ROT>
 __device__ void phase_h2(const FlowArgs& a, const float* __restrict__ Wl, const Phase& ph,
                          const float* h1, float* h2) {
     const int L = a.L, S = a.S, C1 = a.C1, C2 = a.C2, T = (ND == 3) ? 27 : 9;
@@ -187,7 +190,7 @@ __device__ void phase_h2(const FlowArgs& a, const float* __restrict__ Wl, const 
                 float4 hv[4];
 #pragma unroll
                 for (int k = 0; k < 4; ++k)
-                    hv[k] = *reinterpret_cast<const float4*>(row[k] + (swz(c4, key[k], C1) << 2));
+                    hv[k] = *reinterpret_cast<const float4*>(row[k] + (swz<ROT>(c4, key[k], C1) << 2));
 #pragma unroll
                 for (int cc = 0; cc < 4; ++cc) {
                     const float* wp = Wt + (size_t)(4 * c4 + cc) * C2;
@@ -212,8 +215,8 @@ __device__ void phase_h2(const FlowArgs& a, const float* __restrict__ Wl, const 
                                           lrelu(acc[k][2], a.slope), lrelu(acc[k][3], a.slope));
             const float4 o1 = make_float4(lrelu(acc[k][4], a.slope), lrelu(acc[k][5], a.slope),
                                           lrelu(acc[k][6], a.slope), lrelu(acc[k][7], a.slope));
-            *reinterpret_cast<float4*>(orow + (swz(co >> 2, jj[k], C2) << 2)) = o0;
-            *reinterpret_cast<float4*>(orow + (swz((co >> 2) + 1, jj[k], C2) << 2)) = o1;
+            *reinterpret_cast<float4*>(orow + (swz<ROT>(co >> 2, jj[k], C2) << 2)) = o0;
+            *reinterpret_cast<float4*>(orow + (swz<ROT>((co >> 2) + 1, jj[k], C2) << 2)) = o1;
         }
     }
 }
@@ -221,7 +224,7 @@ __device__ void phase_h2(const FlowArgs& a, const float* __restrict__ Wl, const 
 // ---------------------------------------------------------------- conv3 + affine update
 // (s, t) at the updated sites only; `tps` lanes share a site, each summing
 // C2/tps channels, combined with xor-shuffles.
-template <int ND, bool INVERSE, bool WS>
+template <int ND, bool INVERSE, bool WS, bool ROT>
 __device__ void phase_c3(const FlowArgs& a, const float* __restrict__ Wl, const Phase& ph,
                          const float* h2, float* x, int frozen, FF& logdet) {
     const int L = a.L, S = a.S, C2 = a.C2, T = (ND == 3) ? 27 : 9;
@@ -258,7 +261,7 @@ __device__ void phase_c3(const FlowArgs& a, const float* __restrict__ Wl, const 
                 const float* Wt = W3 + (size_t)t * C2 * 2;
                 for (int c = 0; c < nchunk; ++c) {
                     const int c4 = rk * nchunk + c;
-                    const float4 hv = *reinterpret_cast<const float4*>(row + (swz(c4, j2, C2) << 2));
+                    const float4 hv = *reinterpret_cast<const float4*>(row + (swz<ROT>(c4, j2, C2) << 2));
                     const float4 w01 = ldw4<WS>(Wt + 8 * c4);
                     const float4 w23 = ldw4<WS>(Wt + 8 * c4 + 4);
                     ps = fmaf(hv.x, w01.x, ps); pt = fmaf(hv.x, w01.y, pt);
@@ -283,7 +286,7 @@ __device__ void phase_c3(const FlowArgs& a, const float* __restrict__ Wl, const 
     }
 }
 
-template <int ND, bool INVERSE, bool WS>
+template <int ND, bool INVERSE, bool WS, bool ROT>
 __global__ void __launch_bounds__(kThreads) flow_fp32_kernel(const FlowArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int V = a.V;
@@ -348,9 +351,9 @@ __global__ void __launch_bounds__(kThreads) flow_fp32_kernel(const FlowArgs a) {
                     reinterpret_cast<uint32_t*>(ph)[threadIdx.x] =
                         __ldg(reinterpret_cast<const uint32_t*>(a.sched + p) + threadIdx.x);
                 __syncthreads();
-                if (ph->type == PH_H1) phase_h1<ND, WS>(a, Wl, *ph, x, h1, frozen);
-                else if (ph->type == PH_H2) phase_h2<ND, WS>(a, Wl, *ph, h1, h2);
-                else phase_c3<ND, INVERSE, WS>(a, Wl, *ph, h2, x, frozen, logdet);
+                if (ph->type == PH_H1) phase_h1<ND, WS, ROT>(a, Wl, *ph, x, h1, frozen);
+                else if (ph->type == PH_H2) phase_h2<ND, WS, ROT>(a, Wl, *ph, h1, h2);
+                else phase_c3<ND, INVERSE, WS, ROT>(a, Wl, *ph, h2, x, frozen, logdet);
                 __syncthreads();
             }
         }
@@ -385,7 +388,9 @@ __global__ void __launch_bounds__(kThreads) flow_fp32_kernel(const FlowArgs a) {
 
 template <int ND, bool INV, bool WS>
 gf_status launch_t(const gf_flow* f, const FlowArgs& a, cudaStream_t stream) {
-    auto kern = flow_fp32_kernel<ND, INV, WS>;
+    const int n1 = f->C1 >> 2, n2 = f->C2 >> 2;      // float4 chunks per row (C1 == C2 here)
+    const bool rot = (n1 & (n1 - 1)) != 0 || (n2 & (n2 - 1)) != 0;
+    auto kern = rot ? flow_fp32_kernel<ND, INV, WS, true> : flow_fp32_kernel<ND, INV, WS, false>;
     static int configured_bytes[2] = {0, 0};   // per-instantiation attribute cache
     (void)configured_bytes;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -81,8 +81,9 @@ def test_requests_kernels_overlap_on_the_device():
     from paper_2208_08903_gb300 import serving
     specs = [("p", gi.FlowShape(2, 8, 6, 8, 8), 1), ("q", gi.FlowShape(2, 16, 4, 16, 16), 2)]
     models = {n: serving.Model(n, sh, P.Flow(sh, gi.init_weights(sh, seed=s))) for n, sh, s in specs}
-    reqs = [serving.Request(i, "pq"[i % 2], -4.0, 5.0, 256, 70 + i, arrival=0.0) for i in range(12)]
-    with serving.Server(models, hbm_budget_bytes=64 << 20, max_active=6, chunk=32) as srv:
+    # chunks long enough (256 configurations) that the host loop keeps several in flight
+    reqs = [serving.Request(i, "pq"[i % 2], -4.0, 5.0, 1024, 70 + i, arrival=0.0) for i in range(12)]
+    with serving.Server(models, hbm_budget_bytes=256 << 20, max_active=6, chunk=256) as srv:
         srv.run(reqs[:2], realtime=False)                   # warm-up
         res, stats = srv.run(reqs, realtime=False, timeline=True)
     print({k: stats[k] for k in ("gpu_busy_ms", "overlapped_fraction", "max_requests_in_flight")})
