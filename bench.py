@@ -406,8 +406,9 @@ def bench_gpu(args, rank, world, local):
     if world == 1 and not args.no_extra:
         flush2 = torch.empty(2 * L2_BYTES // 4, device=dev, dtype=torch.float32)
         res["extra"] = bench_extra(args, dev, flush2, pk)
-        pl = res["extra"]["plain_fp32_unfused"]["configs_per_s"]
-        res["extra"]["speedup_vs_plain_fp32"] = value / pl
+        if "plain_fp32_unfused" in res["extra"]:
+            pl = res["extra"]["plain_fp32_unfused"]["configs_per_s"]
+            res["extra"]["speedup_vs_plain_fp32"] = value / pl
     return res
 
 
@@ -441,6 +442,10 @@ def bench_extra(args, dev, flush, pk):
     shape, phi4, B = W["shape"], W["phi4"], args.batch or W["batch"]
     w = gi.init_weights(shape, seed=0)
     V = shape.V
+    only = [x for x in (args.only_extra or "").split(",") if x]
+
+    def want(name):
+        return not only or name in only
 
     def sampling_rate(kind, steps=3):
         flow = P.Flow(shape, w, precision="fp32")
@@ -463,146 +468,156 @@ def bench_extra(args, dev, flush, pk):
         return {"configs_per_s": B * len(t) / (sum(t) / 1e3), "ms_per_step": float(np.mean(t)),
                 "acceptance": s.n_acc / max(1, s.step - 1)}
 
-    out["plain_fp32_unfused"] = sampling_rate("unfused")
-    out["fused_fp32"] = sampling_rate("fused")
-    torch.cuda.empty_cache()
-
-    # equal acceptance on the trained 3D flow shipped in checkpoints/: the
-    # tensor-core, fused FP32 and plain FP32 samplers on the same proposals
-    if args.workload == "c3":
-        out["trained_c3_equal_acceptance"] = trained_acceptance(shape, phi4, n=args.acceptance_proposals)
+    if want("sampling"):
+        out["plain_fp32_unfused"] = sampling_rate("unfused")
+        out["fused_fp32"] = sampling_rate("fused")
         torch.cuda.empty_cache()
 
-    # reverse-KL training step, 2D L=32, 24 couplings, hidden 32, batch 1024, Adam
-    W2 = gi.WORKLOADS["c2"]
-    f2 = P.Flow(W2["shape"], gi.init_weights(W2["shape"]))
-    m = torch.zeros(f2.n_params, device=dev)
-    v = torch.zeros(f2.n_params, device=dev)
-    ws2 = torch.empty(f2.train_workspace_bytes(W2["batch"]), device=dev, dtype=torch.uint8)
-    t = _time_steps(lambda i: f2.train_step(W2["batch"], W2["phi4"], seed=12345, counter0=i * W2["batch"],
-                                            lr=1e-3, adam_m=m, adam_v=v, adam_t=i + 1, workspace=ws2,
-                                            grad=False), 3, 2, flush)
-    fl = 4 * flops_per_config(W2["shape"]) * W2["batch"]
-    out["train_c2"] = {"steps_per_s": 1e3 / float(np.mean(t)), "ms_per_step": float(np.mean(t)),
-                       "approx_tflops": fl / (float(np.mean(t)) / 1e3) / 1e12,
-                       "workload": "2D L=32, 24 couplings, hidden 32, batch 1024, forward+backward+Adam"}
-    del ws2, f2
-    torch.cuda.empty_cache()
+    if want("trained"):
+        # equal acceptance on the trained 3D flow shipped in checkpoints/: the
+        # tensor-core, fused FP32 and plain FP32 samplers on the same proposals
+        if args.workload == "c3":
+            out["trained_c3_equal_acceptance"] = trained_acceptance(shape, phi4, n=args.acceptance_proposals)
+            torch.cuda.empty_cache()
 
-    # HMC, 3D L=16, 512 chains, 20 leapfrog steps, eps 0.05, FP64
-    W4 = gi.WORKLOADS["c4"]
-    phi = torch.zeros(W4["chains"], W4["L"] ** 3, device=dev, dtype=torch.float64)
-    t = _time_steps(lambda i: P.hmc_trajectory(3, W4["L"], W4["phi4"], phi, W4["n_steps"], W4["eps"], 7, i),
-                    20, 3, None)
-    traj_ms = float(np.mean(t))
-    # FP64 FLOP per site and leapfrog step: force 20 (three directions of
-    # 2 phi - two neighbours, 2 x lap + 2 m2 phi + 4 lam phi^3), kick 2, drift 2
-    hmc_fl = 24.0 * W4["chains"] * W4["L"] ** 3 * W4["n_steps"]
-    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-    dfma, dfma_kind = alu_peak(n_sm, pk.get("sm_max_mhz", 2070.0), fp64=True)
-    ffma, ffma_kind = alu_peak(n_sm, pk.get("sm_max_mhz", 2070.0), fp64=False)
-    hmc_tf = hmc_fl / (traj_ms / 1e3) / 1e12
-    out["hmc_c4"] = {"trajectories_per_s": 1e3 / traj_ms, "ms_per_trajectory_all_chains": traj_ms,
-                     "chain_trajectories_per_s": W4["chains"] * 1e3 / traj_ms,
-                     "seconds_for_1000_trajectories": traj_ms,
-                     "fp64_tflops": hmc_tf, "dfma_peak_tflops": dfma,
-                     "frac_of_dfma": hmc_tf / dfma if dfma else None, "peak_kind": dfma_kind,
-                     "flop_per_site_step": 24,
-                     "workload": "3D L=16, 512 chains, 20 steps, eps=0.05, FP64"}
-    try:
-        f2 = max(P.api.alu_peak(packed=True, iters=1 << 17) for _ in range(3)) / 1e12
-    except Exception:  # noqa: BLE001
-        f2 = None
-    out["alu_peaks_measured"] = {"ffma_tflops": ffma, "dfma_tflops": dfma, "ffma2_packed_tflops": f2,
-                                 "ffma_kind": ffma_kind,
-                                 "dfma_kind": dfma_kind,
-                                 "ffma_derived_tflops": fp32_alu_peak_tflops(n_sm, pk.get("sm_max_mhz", 2070.0))}
+    if want("train"):
+        # reverse-KL training step, 2D L=32, 24 couplings, hidden 32, batch 1024, Adam
+        W2 = gi.WORKLOADS["c2"]
+        f2 = P.Flow(W2["shape"], gi.init_weights(W2["shape"]))
+        m = torch.zeros(f2.n_params, device=dev)
+        v = torch.zeros(f2.n_params, device=dev)
+        ws2 = torch.empty(f2.train_workspace_bytes(W2["batch"]), device=dev, dtype=torch.uint8)
+        t = _time_steps(lambda i: f2.train_step(W2["batch"], W2["phi4"], seed=12345, counter0=i * W2["batch"],
+                                                lr=1e-3, adam_m=m, adam_v=v, adam_t=i + 1, workspace=ws2,
+                                                grad=False), 3, 2, flush)
+        fl = 4 * flops_per_config(W2["shape"]) * W2["batch"]
+        out["train_c2"] = {"steps_per_s": 1e3 / float(np.mean(t)), "ms_per_step": float(np.mean(t)),
+                           "approx_tflops": fl / (float(np.mean(t)) / 1e3) / 1e12,
+                           "workload": "2D L=32, 24 couplings, hidden 32, batch 1024, forward+backward+Adam"}
+        del ws2, f2
+        torch.cuda.empty_cache()
 
-    # standalone action of FP32 fields: fields larger than L2 (4 x the batch,
-    # 268 MB) read in turn without a flush, as for the observables below
-    Ba = 4 * B
-    phi32 = torch.randn(Ba, V, device=dev)
-    S = torch.empty(Ba, device=dev, dtype=torch.float64)
-    t = _time_steps(lambda i: P.phi4_action(shape.nd, shape.L, phi4, phi32, out=S), 10, 3, None)
-    gbs = (Ba * V * 4 + Ba * 8) / (float(np.mean(t)) / 1e3) / 1e9
-    out["action_fp32"] = {"GB_per_s": gbs, "frac_of_hbm": gbs / pk.get("hbm_gbs", 6800.0),
-                          "bytes_per_launch": Ba * V * 4 + Ba * 8, "ms": float(np.mean(t)),
-                          "workload": f"{Ba} configurations of {shape.nd}D L={shape.L}",
-                          "l2": "inputs 4x L2 size, read in turn, no flush"}
-    del phi32
+    if want("hmc"):
+        # HMC, 3D L=16, 512 chains, 20 leapfrog steps, eps 0.05, FP64
+        W4 = gi.WORKLOADS["c4"]
+        phi = torch.zeros(W4["chains"], W4["L"] ** 3, device=dev, dtype=torch.float64)
+        t = _time_steps(lambda i: P.hmc_trajectory(3, W4["L"], W4["phi4"], phi, W4["n_steps"], W4["eps"], 7, i),
+                        20, 3, None)
+        traj_ms = float(np.mean(t))
+        # FP64 FLOP per site and leapfrog step: force 20 (three directions of
+        # 2 phi - two neighbours, 2 x lap + 2 m2 phi + 4 lam phi^3), kick 2, drift 2
+        hmc_fl = 24.0 * W4["chains"] * W4["L"] ** 3 * W4["n_steps"]
+        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        dfma, dfma_kind = alu_peak(n_sm, pk.get("sm_max_mhz", 2070.0), fp64=True)
+        ffma, ffma_kind = alu_peak(n_sm, pk.get("sm_max_mhz", 2070.0), fp64=False)
+        hmc_tf = hmc_fl / (traj_ms / 1e3) / 1e12
+        out["hmc_c4"] = {"trajectories_per_s": 1e3 / traj_ms, "ms_per_trajectory_all_chains": traj_ms,
+                         "chain_trajectories_per_s": W4["chains"] * 1e3 / traj_ms,
+                         "seconds_for_1000_trajectories": traj_ms,
+                         "fp64_tflops": hmc_tf, "dfma_peak_tflops": dfma,
+                         "frac_of_dfma": hmc_tf / dfma if dfma else None, "peak_kind": dfma_kind,
+                         "flop_per_site_step": 24,
+                         "workload": "3D L=16, 512 chains, 20 steps, eps=0.05, FP64"}
+        try:
+            f2 = max(P.api.alu_peak(packed=True, iters=1 << 17) for _ in range(3)) / 1e12
+        except Exception:  # noqa: BLE001
+            f2 = None
+        out["alu_peaks_measured"] = {"ffma_tflops": ffma, "dfma_tflops": dfma, "ffma2_packed_tflops": f2,
+                                     "ffma_kind": ffma_kind,
+                                     "dfma_kind": dfma_kind,
+                                     "ffma_derived_tflops": fp32_alu_peak_tflops(n_sm, pk.get("sm_max_mhz", 2070.0))}
 
-    # chain observables: M and C(t) per configuration (HBM-bound read of the
-    # fields), then the autocorrelation / tau_int of a 100k-step series and the ESS.
-    # The fields here are larger than L2 (4 x the batch, 268 MB) and are read in
-    # turn without a flush: a flush that writes L2 full leaves dirty lines whose
-    # write-back would double the traffic of this read-only kernel.
-    lib = P._abi.load()
-    stream = torch.cuda.current_stream().cuda_stream
-    Bo = 4 * B
-    phi_o = torch.randn(Bo, V, device=dev)
-    M = torch.empty(Bo, device=dev, dtype=torch.float64)
-    Cc = torch.empty(Bo, shape.L, device=dev, dtype=torch.float64)
+    if want("action"):
+        # standalone action of FP32 fields: fields larger than L2 (4 x the batch,
+        # 268 MB) read in turn without a flush, as for the observables below
+        Ba = 4 * B
+        phi32 = torch.randn(Ba, V, device=dev)
+        S = torch.empty(Ba, device=dev, dtype=torch.float64)
+        t = _time_steps(lambda i: P.phi4_action(shape.nd, shape.L, phi4, phi32, out=S), 10, 3, None)
+        gbs = (Ba * V * 4 + Ba * 8) / (float(np.mean(t)) / 1e3) / 1e9
+        out["action_fp32"] = {"GB_per_s": gbs, "frac_of_hbm": gbs / pk.get("hbm_gbs", 6800.0),
+                              "bytes_per_launch": Ba * V * 4 + Ba * 8, "ms": float(np.mean(t)),
+                              "workload": f"{Ba} configurations of {shape.nd}D L={shape.L}",
+                              "l2": "inputs 4x L2 size, read in turn, no flush"}
+        del phi32
 
-    def obs(i):
-        P._abi.check("gf_observables", lib.gf_observables(shape.nd, shape.L, Bo, phi_o.data_ptr(), M.data_ptr(),
-                                                          Cc.data_ptr(), stream))
-    t = _time_steps(obs, 10, 3, None)
-    ob_bytes = Bo * V * 4 + Bo * (shape.L + 1) * 8
-    gbs = ob_bytes / (float(np.mean(t)) / 1e3) / 1e9
-    out["observables"] = {"GB_per_s": gbs, "frac_of_hbm": gbs / pk.get("hbm_gbs", 6800.0),
-                          "bytes_per_launch": ob_bytes, "ms": float(np.mean(t)),
-                          "workload": f"M and C(t) of {Bo} configurations of {shape.nd}D L={shape.L}",
-                          "l2": "inputs 4x L2 size, read in turn, no flush"}
-    del phi_o
-    y = torch.randn(100000, device=dev, dtype=torch.float64)
-    t = _time_steps(lambda i: P.autocorr(y, 1000), 5, 2, None)
-    out["autocorr"] = {"ms": float(np.mean(t)), "n": 100000, "t_max": 1000}
-    t = _time_steps(lambda i: P.ess(y), 5, 2, None)
-    out["ess"] = {"ms": float(np.mean(t)), "n": 100000}
+    if want("observables"):
+        # chain observables: M and C(t) per configuration (HBM-bound read of the
+        # fields), then the autocorrelation / tau_int of a 100k-step series and the ESS.
+        # The fields here are larger than L2 (4 x the batch, 268 MB) and are read in
+        # turn without a flush: a flush that writes L2 full leaves dirty lines whose
+        # write-back would double the traffic of this read-only kernel.
+        lib = P._abi.load()
+        stream = torch.cuda.current_stream().cuda_stream
+        Bo = 4 * B
+        phi_o = torch.randn(Bo, V, device=dev)
+        M = torch.empty(Bo, device=dev, dtype=torch.float64)
+        Cc = torch.empty(Bo, shape.L, device=dev, dtype=torch.float64)
 
-    # context: the same flow in eager PyTorch (cuDNN FP32 convolutions, TF32 off)
-    out["torch_eager_fp32_context"] = torch_eager_rate(shape, phi4, w, min(B, 1024), dev, flush)
-    torch.cuda.empty_cache()
+        def obs(i):
+            P._abi.check("gf_observables", lib.gf_observables(shape.nd, shape.L, Bo, phi_o.data_ptr(), M.data_ptr(),
+                                                              Cc.data_ptr(), stream))
+        t = _time_steps(obs, 10, 3, None)
+        ob_bytes = Bo * V * 4 + Bo * (shape.L + 1) * 8
+        gbs = ob_bytes / (float(np.mean(t)) / 1e3) / 1e9
+        out["observables"] = {"GB_per_s": gbs, "frac_of_hbm": gbs / pk.get("hbm_gbs", 6800.0),
+                              "bytes_per_launch": ob_bytes, "ms": float(np.mean(t)),
+                              "workload": f"M and C(t) of {Bo} configurations of {shape.nd}D L={shape.L}",
+                              "l2": "inputs 4x L2 size, read in turn, no flush"}
+        del phi_o
+        y = torch.randn(100000, device=dev, dtype=torch.float64)
+        t = _time_steps(lambda i: P.autocorr(y, 1000), 5, 2, None)
+        out["autocorr"] = {"ms": float(np.mean(t)), "n": 100000, "t_max": 1000}
+        t = _time_steps(lambda i: P.ess(y), 5, 2, None)
+        out["ess"] = {"ms": float(np.mean(t)), "n": 100000}
 
-    # MH chain alone, 100k proposals
-    n = 100000
-    lw = torch.randn(n, device=dev, dtype=torch.float64) * 2 - 50
-    st = P.new_mh_state(seed=1, device=dev)
-    wsm = torch.empty(n, device=dev, dtype=torch.float64)
-    t = _time_steps(lambda i: P.mh_chain(st, lw, workspace=wsm), 5, 2, None)
-    out["mh_chain"] = {"ns_per_proposal": float(np.mean(t)) * 1e6 / n, "proposals": n}
+    if want("eager"):
+        # context: the same flow in eager PyTorch (cuDNN FP32 convolutions, TF32 off)
+        out["torch_eager_fp32_context"] = torch_eager_rate(shape, phi4, w, min(B, 1024), dev, flush)
+        torch.cuda.empty_cache()
 
-    # serving mix: resident random-init models; capacity, then a Poisson load sweep
-    out["serving_c5"] = bench_serving(dev, n_requests=args.serving_requests)
-    torch.cuda.empty_cache()
+    if want("mh"):
+        # MH chain alone, 100k proposals
+        n = 100000
+        lw = torch.randn(n, device=dev, dtype=torch.float64) * 2 - 50
+        st = P.new_mh_state(seed=1, device=dev)
+        wsm = torch.empty(n, device=dev, dtype=torch.float64)
+        t = _time_steps(lambda i: P.mh_chain(st, lw, workspace=wsm), 5, 2, None)
+        out["mh_chain"] = {"ns_per_proposal": float(np.mean(t)) * 1e6 / n, "proposals": n}
 
-    # the paper's example workload (2D L=8, 16 couplings, hidden 8, batch 64)
-    W1 = gi.WORKLOADS["c1"]
-    f1 = P.Flow(W1["shape"], gi.init_weights(W1["shape"]))
-    r1 = P.SampleResult(phi=torch.empty(64, 64, device=dev), logq=torch.empty(64, device=dev, dtype=torch.float64),
-                        S=torch.empty(64, device=dev, dtype=torch.float64),
-                        logw=torch.empty(64, device=dev, dtype=torch.float64))
-    st1 = P.new_mh_state(seed=2, device=dev)
+    if want("serving"):
+        # serving mix: resident random-init models; capacity, then a Poisson load sweep
+        out["serving_c5"] = bench_serving(dev, n_requests=args.serving_requests)
+        torch.cuda.empty_cache()
 
-    def c1step(i):
-        f1.sample(64, seed=3, counter0=64 * i, phi4=W1["phi4"], out=r1)
-        P.mh_chain(st1, r1.logw)
-    t = _time_steps(c1step, 50, 5, None)
-    out["c1_sampling"] = {"configs_per_s": 64 / (float(np.mean(t)) / 1e3), "ms_per_step": float(np.mean(t))}
-    # batch sweep of the c1 flow (fused FP32 sampler + MH): 64 configurations cannot fill 152 SMs
-    sweep = {}
-    for Bs in (64, 1024, 16384, 65536):
-        rs = P.SampleResult(phi=torch.empty(Bs, 64, device=dev), logq=torch.empty(Bs, device=dev, dtype=torch.float64),
-                            S=torch.empty(Bs, device=dev, dtype=torch.float64),
-                            logw=torch.empty(Bs, device=dev, dtype=torch.float64))
-        sts = P.new_mh_state(seed=3, device=dev)
+    if want("c1"):
+        # the paper's example workload (2D L=8, 16 couplings, hidden 8, batch 64)
+        W1 = gi.WORKLOADS["c1"]
+        f1 = P.Flow(W1["shape"], gi.init_weights(W1["shape"]))
+        r1 = P.SampleResult(phi=torch.empty(64, 64, device=dev), logq=torch.empty(64, device=dev, dtype=torch.float64),
+                            S=torch.empty(64, device=dev, dtype=torch.float64),
+                            logw=torch.empty(64, device=dev, dtype=torch.float64))
+        st1 = P.new_mh_state(seed=2, device=dev)
 
-        def sstep(i, Bs=Bs, rs=rs, sts=sts):
-            f1.sample(Bs, seed=4, counter0=Bs * i, phi4=W1["phi4"], out=rs)
-            P.mh_chain(sts, rs.logw)
-        t = _time_steps(sstep, 10, 3, None)
-        sweep[str(Bs)] = Bs / (float(np.mean(t)) / 1e3)
-    out["c1_batch_sweep_configs_per_s"] = sweep
+        def c1step(i):
+            f1.sample(64, seed=3, counter0=64 * i, phi4=W1["phi4"], out=r1)
+            P.mh_chain(st1, r1.logw)
+        t = _time_steps(c1step, 50, 5, None)
+        out["c1_sampling"] = {"configs_per_s": 64 / (float(np.mean(t)) / 1e3), "ms_per_step": float(np.mean(t))}
+        # batch sweep of the c1 flow (fused FP32 sampler + MH): 64 configurations cannot fill 152 SMs
+        sweep = {}
+        for Bs in (64, 1024, 16384, 65536):
+            rs = P.SampleResult(phi=torch.empty(Bs, 64, device=dev), logq=torch.empty(Bs, device=dev, dtype=torch.float64),
+                                S=torch.empty(Bs, device=dev, dtype=torch.float64),
+                                logw=torch.empty(Bs, device=dev, dtype=torch.float64))
+            sts = P.new_mh_state(seed=3, device=dev)
+
+            def sstep(i, Bs=Bs, rs=rs, sts=sts):
+                f1.sample(Bs, seed=4, counter0=Bs * i, phi4=W1["phi4"], out=rs)
+                P.mh_chain(sts, rs.logw)
+            t = _time_steps(sstep, 10, 3, None)
+            sweep[str(Bs)] = Bs / (float(np.mean(t)) / 1e3)
+        out["c1_batch_sweep_configs_per_s"] = sweep
     return out
 
 
@@ -809,6 +824,9 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=120.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the secondary measurements")
+    ap.add_argument("--only-extra", default="",
+                    help="comma list of secondary measurements to run (sampling, trained, train, hmc, action, "
+                         "observables, eager, mh, serving, c1); default all")
     ap.add_argument("--serving-requests", type=int, default=60)
     ap.add_argument("--acceptance-proposals", type=int, default=32768)
     args = ap.parse_args()
