@@ -185,9 +185,8 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
 __device__ __forceinline__ uint64_t desc_add(uint64_t d, uint32_t off) {
     return ((d >> 32) << 32) | (uint32_t)((uint32_t)d + off);
 }
-// Instruction descriptors: D = F32, A = B = BF16, both K-major, M = 128, N = 96 / 32.
+// Instruction descriptors: D = F32, A = B = BF16 (conv2), both K-major, M = 128, N = 96.
 constexpr uint32_t kIdesc96 = (1u << 4) | (1u << 7) | (1u << 10) | ((96u >> 3) << 17) | ((128u >> 4) << 24);
-constexpr uint32_t kIdesc32 = (1u << 4) | (1u << 7) | (1u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
 // D = F32, A = B = FP16 (conv1 and conv3), K-major, M = 128, N = 32.
 constexpr uint32_t kIdesc32h = (1u << 4) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
 
@@ -371,7 +370,7 @@ __device__ __forceinline__ void conv3_epi_load(float (&p)[3][8], uint32_t rm, ui
 }
 __device__ __forceinline__ void conv3_epi_finish(const float (&p)[3][8], int z, float b3s, float b3t, float* x,
                                                  int frozen, int use_tanh, bool inverse, FF& logdet, int mt,
-                                                 int q, int lane, int32_t* status) {
+                                                 int q, int lane, float& chk) {
     const int y = mt * 8 + q * 2 + (lane >> 4), xx = lane & 15;
     float st[6];
 #pragma unroll
@@ -382,9 +381,10 @@ __device__ __forceinline__ void conv3_epi_finish(const float (&p)[3][8], int z, 
                        b3s;
     const float tt = st[3] + __shfl_sync(0xffffffffu, st[1], src_m) + __shfl_sync(0xffffffffu, st[5], src_p) + b3t;
     if (((z + y + xx) & 1) != frozen) {
-        // FP16 operands of conv1 / conv3 overflow beyond 65504: a non-finite
-        // s or t (from a field or h2 value out of that range) is reported
-        if (!isfinite(spre) || !isfinite(tt)) set_status(status, GF_EDEVICE);
+        // FP16 operands of conv1 / conv3 overflow beyond 65504: a non-finite s
+        // or t (from a field or h2 value out of that range) turns chk into NaN
+        // (0 * inf and 0 * NaN are NaN); it is reported once per configuration
+        chk = fmaf(spre, 0.f, fmaf(tt, 0.f, chk));
         const float s = use_tanh ? tanhf(spre) : spre;
         float& xv = x[(z * 16 + y) * kXRow + (xx ^ xswz(y))];
         if (!inverse) xv = fmaf(xv, expf(s), tt);
@@ -545,6 +545,7 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
         __syncthreads();
 
         FF logdet{0.f, 0.f};                       // this thread's sum of s over its updated sites
+        float chk = 0.f;                           // NaN once a non-finite s or t was seen
         const int seq0 = seq, nl = a.n_layers;
         // Layers are pipelined into one another (no CTA barrier between them): layer li
         // (global number s = seq0 + li) walks the lattice slices in the order R + v with
@@ -783,7 +784,7 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
                         // layer li's biases replace li-1's at u = -1, after its slice 14
                         const bool prev = u == 0 && li < nl;
                         conv3_epi_finish(p, (w + rot(lj)) & 15, prev ? b3s_p : b3s, prev ? b3t_p : b3t, x,
-                                         lay(lj) & 1, a.use_tanh, INVERSE, logdet, mt, q, lane, a.status);
+                                         lay(lj) & 1, a.use_tanh, INVERSE, logdet, mt, q, lane, chk);
                         if (w == kL - 1 || (w >= 5 && (w & 3) == 1))   // checkpoint: slices <= w updated
                             mbar_arrive(bar_x + (w == kL - 1 ? 3 : (w - 5) >> 2));
                     }
@@ -827,6 +828,7 @@ __global__ void __launch_bounds__(kThreads, 1) flow_bf16_kernel(const Bf16Args a
             for (int n = tid; n < V; n += kThreads) a.phi_out[b * V + n] = x[xi(n)];
         }
         FF* red_ff = reinterpret_cast<FF*>(red);
+        if (chk != chk) set_status(a.status, GF_EDEVICE);
         const double ld = block_sum_ff(logdet, red_ff);
         const double z2 = block_sum_ff(sumz2, red_ff);
         double S = 0.0;
