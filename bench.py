@@ -590,6 +590,10 @@ def bench_extra(args, dev, flush, pk):
         out["serving_c5"] = bench_serving(dev, n_requests=args.serving_requests)
         torch.cuda.empty_cache()
 
+    if want("tc"):
+        out["tensor_core_other_shapes"] = bench_tc_shapes(dev, flush, pk)
+        torch.cuda.empty_cache()
+
     if want("c1"):
         # the paper's example workload (2D L=8, 16 couplings, hidden 8, batch 64)
         W1 = gi.WORKLOADS["c1"]
@@ -619,6 +623,43 @@ def bench_extra(args, dev, flush, pk):
             sweep[str(Bs)] = Bs / (float(np.mean(t)) / 1e3)
         out["c1_batch_sweep_configs_per_s"] = sweep
     return out
+
+
+def bench_tc_shapes(dev, flush, pk):
+    """The tensor-core kernel for the lattice shapes other than 3D L=16 C=32
+    (gf_flow_tc.cu) next to the fused FP32 kernel on the same flows: per-launch
+    CUDA-event time of gf_flow_sample (prior, coupling stack, log q, S, log w)
+    with L2 flushed between launches, configs/s, algorithmic TFLOP/s and the
+    fraction of the measured BF16 burst peak (each launch timed alone)."""
+    import torch
+    import paper_2208_08903_gb300 as P
+    cases = [("2D L=32, 24 couplings, hidden 32", gi.FlowShape(2, 32, 24, 32, 32), 8192),
+             ("2D L=64, 16 couplings, hidden 16", gi.FlowShape(2, 64, 16, 16, 16), 4096),
+             ("2D L=16, 16 couplings, hidden 24", gi.FlowShape(2, 16, 16, 24, 24), 16384),
+             ("3D L=8, 16 couplings, hidden 32", gi.FlowShape(3, 8, 16, 32, 32), 8192),
+             ("3D L=12, 16 couplings, hidden 16", gi.FlowShape(3, 12, 16, 16, 16), 4096)]
+    phi4 = (-4.0, 6.0)
+    res = {"theory": "m2=-4, lam=6, random-init weights seed 0", "peak_tflops": pk["bf16_tflops"]}
+    for name, shape, B in cases:
+        w = gi.init_weights(shape, seed=0)
+        line = {"batch": B, "flops_per_config": flops_per_config(shape)}
+        for prec in ("bf16", "fp32"):
+            flow = P.Flow(shape, w, precision=prec)
+            r = P.SampleResult(phi=torch.empty(B, shape.V, device=dev),
+                               logq=torch.empty(B, device=dev, dtype=torch.float64),
+                               S=torch.empty(B, device=dev, dtype=torch.float64),
+                               logw=torch.empty(B, device=dev, dtype=torch.float64))
+            t = _time_steps(lambda i: flow.sample(B, seed=5, counter0=i * B, phi4=phi4, out=r),
+                            5 if prec == "bf16" else 2, 2, flush)
+            ms = float(np.mean(t))
+            line[prec] = {"configs_per_s": B / (ms / 1e3), "ms_per_launch": ms,
+                          "tflops": flops_per_config(shape) * B / (ms / 1e3) / 1e12}
+            del flow, r
+        line["bf16"]["frac_of_bf16_burst"] = line["bf16"]["tflops"] / pk["bf16_tflops"]
+        line["speedup_vs_fused_fp32"] = line["bf16"]["configs_per_s"] / line["fp32"]["configs_per_s"]
+        res[name] = line
+    assert P.device_status() == 0
+    return res
 
 
 def trained_acceptance(shape, phi4, n=32768):
@@ -826,7 +867,7 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the secondary measurements")
     ap.add_argument("--only-extra", default="",
                     help="comma list of secondary measurements to run (sampling, trained, train, hmc, action, "
-                         "observables, eager, mh, serving, c1); default all")
+                         "observables, eager, mh, serving, tc, c1); default all")
     ap.add_argument("--serving-requests", type=int, default=60)
     ap.add_argument("--acceptance-proposals", type=int, default=32768)
     args = ap.parse_args()

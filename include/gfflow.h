@@ -41,14 +41,20 @@ typedef enum {
 typedef enum {
     GF_PREC_FP32 = 0,             /* FP32 convolutions, FP64 sums                  */
     GF_PREC_BF16CONV_FP64RED = 1  /* tensor-core convolutions with FP32
-                                     accumulation: conv2 (the dominant one) with
-                                     BF16 operands (h1, W2), conv1 and conv3 with
-                                     FP16 operands (the masked field, W1; h2, W3),
-                                     so |field| and |h2| must stay below 65504 (a
-                                     non-finite s or t records GF_EDEVICE);
-                                     log-det, z^2 and action sums to FP64
-                                     accuracy (FP32 pairs per thread, FP64 across
-                                     the block) (3D, L=16, C=32 only)             */
+                                     accumulation; log-det, z^2 and action sums
+                                     to FP64 accuracy (FP32 pairs per thread,
+                                     FP64 across the block).  Two kernels:
+                                     3D, L=16, C=32: conv2 (the dominant one)
+                                     with BF16 operands (h1, W2), conv1 and
+                                     conv3 on the tensor cores with FP16
+                                     operands (the masked field, W1; h2, W3),
+                                     so |field| and |h2| must stay below 65504
+                                     (a non-finite s or t records GF_EDEVICE);
+                                     other shapes (see gf_flow_tensor_core_
+                                     supported): conv2 with BF16 operands (h1,
+                                     W2) on the tensor cores, conv1 and conv3 in
+                                     FP32 from the FP32 field and weights and
+                                     the BF16 h2                                  */
 } gf_precision;
 
 /* Flow shape (paper Sec. 3, model parameters: n_layers, hidden_sizes =
@@ -73,7 +79,7 @@ typedef struct {
  * Supported: nd in {2,3}; L even, L^nd <= 65536; 0 <= n_hidden <=
  * GF_MAX_HIDDEN; widths 1..256; ksize in {1,3,5,7}.  Two equal hidden widths in
  * {8,16,24,32} with ksize 3 run on the slice-cached kernels (the tensor-core
- * precision for 3D L=16 with width 32 only);
+ * precision for the shapes gf_flow_tensor_core_supported accepts);
  * every other network runs on a whole-lattice FP32 kernel that needs
  * 4 (V + 2 V Cp) bytes of shared memory per block, Cp = the widest hidden
  * layer rounded up to odd, at most 227 KB (else GF_EUNSUPPORTED); those flows
@@ -122,6 +128,18 @@ gf_status gf_flow_create(const gf_flow_shape* shape, const double* weights_host,
  * is supported only where gf_flow_create supports it. */
 gf_status gf_flow_create_ex(const gf_flow_shape_ex* shape, const double* weights_host,
                             gf_precision prec, cudaStream_t stream, gf_flow** out);
+/* 1 when gf_flow_create_ex accepts GF_PREC_BF16CONV_FP64RED for `shape`, else 0
+ * (host only, no device work; a null or invalid shape gives 0).  Convolutions
+ * go on the tensor cores where the hidden width makes conv2 a dense
+ * contraction (paper Sec. 1, the coupling layers' convolutional networks):
+ * two equal hidden widths of 16, 24 or 32 (24 padded to 32 with zeros),
+ * ksize 3, and either 3D L=16 with width 32 (its own kernel) or a lattice whose
+ * activations fit one block's shared memory: 2 (P^nd + 2 (1 + P (+P^2)) +
+ * 128) x Cp bytes (about; P = L + 2, Cp = 16 or 32) plus W2 and the field,
+ * at most 227 KB, e.g. 2D L <= 32 with any of the widths, 2D L = 64 and 3D
+ * L = 12 with width 16, 3D L = 8 with any.  Hidden width 8 stays on the FP32
+ * kernels: there conv2 is too thin for the tensor cores. */
+int32_t gf_flow_tensor_core_supported(const gf_flow_shape_ex* shape);
 gf_status gf_flow_destroy(gf_flow* flow);
 /* Number of canonical parameters. */
 int64_t   gf_flow_n_params(const gf_flow* flow);

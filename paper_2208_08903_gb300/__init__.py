@@ -10,5 +10,5 @@ from .api import (Flow, SampleResult, autocorr, chain_gather, device_status, ess
                   hmc_trajectory, mh_chain, observables,
                   mh_chain_noalloc,
                   mh_chain_workspace_bytes, new_mh_state, phi4_action, phi4_action_vjp,
-                  phi4_force, read_mh_state, set_stream_status_slot)
+                  phi4_force, read_mh_state, set_stream_status_slot, tensor_core_supported)
 from . import autograd  # noqa: F401

@@ -18,7 +18,8 @@ GF_MH_NOALLOC_MAX_N = 131072     # include/gfflow.h
 GF_MAX_HIDDEN = 8
 
 EXPORTED = [
-    "gf_flow_create", "gf_flow_create_ex", "gf_flow_destroy", "gf_flow_n_params", "gf_flow_set_weights_device",
+    "gf_flow_create", "gf_flow_create_ex", "gf_flow_tensor_core_supported", "gf_flow_destroy", "gf_flow_n_params",
+    "gf_flow_set_weights_device",
     "gf_flow_get_weights_device", "gf_flow_sample", "gf_flow_logq", "gf_phi4_action",
     "gf_unfused_workspace_bytes", "gf_flow_sample_unfused",
     "gf_phi4_force", "gf_mh_chain_workspace_bytes", "gf_mh_chain", "gf_mh_chain_noalloc",
@@ -81,6 +82,7 @@ def load():
     sig = {
         "gf_flow_create": ([C.POINTER(FlowShapeC), _VP, _I32, _VP, C.POINTER(_VP)], _I32),
         "gf_flow_create_ex": ([C.POINTER(FlowShapeExC), _VP, _I32, _VP, C.POINTER(_VP)], _I32),
+        "gf_flow_tensor_core_supported": ([C.POINTER(FlowShapeExC)], _I32),
         "gf_flow_destroy": ([_VP], _I32),
         "gf_flow_n_params": ([_VP], _I64),
         "gf_flow_set_weights_device": ([_VP, _VP, _VP], _I32),

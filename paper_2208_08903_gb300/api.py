@@ -46,6 +46,22 @@ class SampleResult:
     z: torch.Tensor | None = None
 
 
+def _shape_ex(shape) -> _abi.FlowShapeExC:
+    hidden = tuple(getattr(shape, "hidden", (shape.c1, shape.c2)))
+    if len(hidden) > _abi.GF_MAX_HIDDEN:
+        raise ValueError(f"at most {_abi.GF_MAX_HIDDEN} hidden convolutions")
+    hid = (C.c_int32 * _abi.GF_MAX_HIDDEN)(*(list(hidden) + [0] * (_abi.GF_MAX_HIDDEN - len(hidden))))
+    return _abi.FlowShapeExC(shape.nd, shape.L, shape.n_layers, len(hidden), hid,
+                             int(getattr(shape, "ksize", 3)), 1 if shape.use_final_tanh else 0,
+                             float(shape.leaky_slope))
+
+
+def tensor_core_supported(shape) -> bool:
+    """Whether Flow(shape, w, precision="bf16") has a tensor-core kernel
+    (gf_flow_tensor_core_supported; host only)."""
+    return bool(_abi.load().gf_flow_tensor_core_supported(C.byref(_shape_ex(shape))))
+
+
 class Flow:
     """A RealNVP coupling stack resident on the current CUDA device.
 
@@ -60,13 +76,7 @@ class Flow:
         lib = _abi.load()
         self.shape = shape
         self.V = shape.L ** shape.nd
-        hidden = tuple(getattr(shape, "hidden", (shape.c1, shape.c2)))
-        if len(hidden) > _abi.GF_MAX_HIDDEN:
-            raise ValueError(f"at most {_abi.GF_MAX_HIDDEN} hidden convolutions")
-        hid = (C.c_int32 * _abi.GF_MAX_HIDDEN)(*(list(hidden) + [0] * (_abi.GF_MAX_HIDDEN - len(hidden))))
-        sh = _abi.FlowShapeExC(shape.nd, shape.L, shape.n_layers, len(hidden), hid,
-                               int(getattr(shape, "ksize", 3)), 1 if shape.use_final_tanh else 0,
-                               float(shape.leaky_slope))
+        sh = _shape_ex(shape)
         w = torch.as_tensor(weights, dtype=torch.float64).contiguous().cpu()
         prec = {"fp32": _abi.GF_PREC_FP32, "bf16": _abi.GF_PREC_BF16CONV_FP64RED}[precision]
         self.precision = precision

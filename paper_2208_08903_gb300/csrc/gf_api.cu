@@ -201,7 +201,7 @@ gf_status repack_weights(gf_flow* f, cudaStream_t stream) {
     repack_kernel<<<grid, 256, 0, stream>>>(f->d_canon, f->d_packed, f->shape.n_layers, f->T,
                                             f->C1, f->C2, f->canon_stride, o);
     GF_CHECK_LAUNCH();
-    if (f->prec == GF_PREC_BF16CONV_FP64RED) return repack_bf16(f, stream);
+    if (f->prec == GF_PREC_BF16CONV_FP64RED) return f->tc ? repack_tc(f, stream) : repack_bf16(f, stream);
     return GF_OK;
 }
 
@@ -305,7 +305,8 @@ gf_status gf_flow_create_ex(const gf_flow_shape_ex* shape, const double* weights
     legacy.ksize = shape->ksize;
     legacy.use_final_tanh = shape->use_final_tanh;
     legacy.leaky_slope = shape->leaky_slope;
-    if (prec == GF_PREC_BF16CONV_FP64RED && (!dflt || !bf16_supported(&legacy))) return GF_EUNSUPPORTED;
+    if (prec == GF_PREC_BF16CONV_FP64RED && (!dflt || !(bf16_supported(&legacy) || tc_supported(&legacy))))
+        return GF_EUNSUPPORTED;
 
     gf_flow* f = new gf_flow;
     std::memset(f, 0, sizeof(*f));
@@ -362,7 +363,7 @@ gf_status gf_flow_create_ex(const gf_flow_shape_ex* shape, const double* weights
     st = flow_fp32_configure(f);
     if (st != GF_OK) { free_flow(f); return st; }
     if (prec == GF_PREC_BF16CONV_FP64RED) {
-        st = bf16_configure(f);
+        st = bf16_supported(&f->shape) ? bf16_configure(f) : tc_configure(f);
         if (st != GF_OK) { free_flow(f); return st; }
     }
     std::vector<Phase> sched = build_schedule(shape->L, f->G, f->full);
@@ -398,6 +399,21 @@ gf_status gf_flow_create_ex(const gf_flow_shape_ex* shape, const double* weights
     if (cudaStreamSynchronize(stream) != cudaSuccess) { free_flow(f); return GF_ECUDA; }
     *out = f;
     return GF_OK;
+}
+
+int32_t gf_flow_tensor_core_supported(const gf_flow_shape_ex* shape) {
+    if (!shape_ex_valid(shape) || !default_net(shape)) return 0;
+    gf_flow_shape s;
+    std::memset(&s, 0, sizeof(s));
+    s.nd = shape->nd;
+    s.L = shape->L;
+    s.n_layers = shape->n_layers;
+    s.c_hidden1 = shape->hidden[0];
+    s.c_hidden2 = shape->hidden[1];
+    s.ksize = shape->ksize;
+    s.use_final_tanh = shape->use_final_tanh;
+    s.leaky_slope = shape->leaky_slope;
+    return (bf16_supported(&s) || tc_supported(&s)) ? 1 : 0;
 }
 
 gf_status gf_flow_destroy(gf_flow* flow) {
@@ -437,6 +453,9 @@ gf_status gf_flow_sample(const gf_flow* flow, const gf_phi4* phi4, int64_t B,
     if (flow->variant)
         return launch_flow_variant(flow, false, phi4, B, seed, counter0, d_z_in, d_z_out, nullptr,
                                    d_phi_out, d_logq_out, d_S_out, d_logw_out, stream);
+    if (flow->prec == GF_PREC_BF16CONV_FP64RED && flow->tc)
+        return launch_flow_tc(flow, false, phi4, B, seed, counter0, d_z_in, d_z_out, nullptr,
+                              d_phi_out, d_logq_out, d_S_out, d_logw_out, stream);
     if (flow->prec == GF_PREC_BF16CONV_FP64RED)
         return launch_flow_bf16(flow, false, phi4, B, seed, counter0, d_z_in, d_z_out, nullptr,
                                 d_phi_out, d_logq_out, d_S_out, d_logw_out, stream);
@@ -451,6 +470,9 @@ gf_status gf_flow_logq(const gf_flow* flow, int64_t B, const float* d_phi_in,
     if (flow->variant)
         return launch_flow_variant(flow, true, nullptr, B, 0, 0, nullptr, d_z_out, d_phi_in, nullptr,
                                    d_logq_out, nullptr, nullptr, stream);
+    if (flow->prec == GF_PREC_BF16CONV_FP64RED && flow->tc)
+        return launch_flow_tc(flow, true, nullptr, B, 0, 0, nullptr, d_z_out, d_phi_in, nullptr,
+                              d_logq_out, nullptr, nullptr, stream);
     if (flow->prec == GF_PREC_BF16CONV_FP64RED)
         return launch_flow_bf16(flow, true, nullptr, B, 0, 0, nullptr, d_z_out, d_phi_in, nullptr,
                                 d_logq_out, nullptr, nullptr, stream);

@@ -52,9 +52,11 @@ struct gf_flow {
     bool full;
     size_t smem_bytes;
     bool wsmem;             // FP32 kernel keeps all packed weights in shared memory
-    // BF16 tensor-core path (3D, C=32)
-    void* d_bf16;           // per layer: bf16 conv2 / conv3 / conv1 (+ bias) B operands, FP32 biases
+    // BF16 tensor-core path: the 3D L=16, C=32 kernel (gf_flow_bf16.cu) or,
+    // when tc is set, the kernel for other shapes (gf_flow_tc.cu)
+    void* d_bf16;           // per-layer weight blocks of the tensor-core kernel
     size_t smem_bytes_bf16;
+    bool tc;
     // General s/t network (gf_flow_create_ex with hidden_sizes other than two
     // equal widths in {8,16,32}, or a kernel size other than 3): whole-lattice
     // FP32 kernel of gf_flow_variant.cu
@@ -105,6 +107,15 @@ gf_status launch_flow_fp32_c32(const gf_flow* f, bool inverse, const gf_phi4* ph
 bool fp32_c32_recompute_supported(const gf_flow* f);
 gf_status launch_c32_recompute(const gf_flow* f, int layer, int64_t B, const float* xl, float* h1_out, float* h2_out,
                                float* s_out, cudaStream_t stream);
+
+// Tensor-core kernel for the shapes other than 3D L=16, C=32 (gf_flow_tc.cu)
+bool tc_supported(const gf_flow_shape* s);
+gf_status tc_configure(gf_flow* f);          // allocates the weight blocks
+gf_status repack_tc(gf_flow* f, cudaStream_t stream);
+gf_status launch_flow_tc(const gf_flow* f, bool inverse, const gf_phi4* phi4, int64_t B,
+                         uint64_t seed, uint64_t counter0, const float* z_in, float* z_out,
+                         const float* phi_in, float* phi_out, double* logq_out,
+                         double* S_out, double* logw_out, cudaStream_t stream);
 
 // General network (gf_flow_variant.cu)
 gf_status variant_configure(gf_flow* f);     // packed offsets, smem, threads (host only)

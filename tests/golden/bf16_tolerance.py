@@ -28,6 +28,7 @@ Kaiming-uniform weights from seed 0, the FP32 prior from seed 77 (not the
 seeds of the GPU tests), 64 configurations per layer count.
 
     python tests/golden/bf16_tolerance.py          # writes bf16_tolerance.json
+    python tests/golden/bf16_tolerance.py --tc     # writes tc_tolerance.json (second kernel)
 """
 from __future__ import annotations
 
@@ -87,8 +88,64 @@ def drift(n_layers: int, B: int, seed: int = SEED, counter0: int = 0, nthreads=N
     return out
 
 
+# The tensor-core kernel for the other lattice shapes (2D L = 8..64, 3D L = 8,
+# 12; hidden 16, 24 or 32) rounds h1, W2 and h2 to bf16 and keeps conv1 and
+# conv3 in FP32; its bounds take the maximum drift over these shapes (serving
+# flows have 12 to 24 coupling layers).
+TC_MODE = oracle.BF16_H1 | oracle.BF16_W2 | oracle.BF16_H2 | oracle.F32_IO
+TC_SHAPES = ((2, 16, 24), (2, 32, 32), (2, 64, 16), (3, 8, 32), (3, 12, 16))
+TC_LAYERS = (2, 8, 24)
+TC_OUT = os.path.join(HERE, "tc_tolerance.json")
+
+
+def drift_tc(n_layers: int, B: int, seed: int = SEED, nthreads=None) -> dict:
+    """drift() for the second tensor-core kernel's rounding points, per shape
+    of TC_SHAPES (m2 = -4, lam = 6), and the bounds over all of them."""
+    out = {"n_layers": n_layers, "configurations_per_shape": B, "by_shape": {}}
+    worst_site = worst_scalar = 0.0
+    for nd, L, c in TC_SHAPES:
+        shape = gi.FlowShape(nd, L, n_layers, c, c)
+        w = gi.init_weights(shape, seed=0)
+        kw = dict(seed=seed, counter0=0, nthreads=nthreads)
+        ref = oracle.flow_sample(shape, w, -4.0, 6.0, B, bf16_mask=TC_MODE, **kw)
+        f32 = oracle.flow_sample(shape, w, -4.0, 6.0, B,
+                                 bf16_mask=TC_MODE | oracle.F32_ACC | oracle.Z_JITTER, **kw)
+        f64 = oracle.flow_sample(shape, w, -4.0, 6.0, B, bf16_mask=oracle.F32_IO, **kw)
+        r = {"fp32_model_vs_emulated": {"phi": stats(site_err(f32["phi"], ref["phi"]))},
+             "emulated_vs_fp64": {"phi": stats(site_err(ref["phi"], f64["phi"]))}}
+        for k in ("logq", "S", "logw"):
+            r["fp32_model_vs_emulated"][k] = stats(scalar_err(f32[k], ref[k]))
+            r["emulated_vs_fp64"][k] = stats(scalar_err(ref[k], f64[k]))
+        d = r["fp32_model_vs_emulated"]
+        worst_site = max(worst_site, d["phi"]["max"])
+        worst_scalar = max(worst_scalar, max(d[k]["max"] for k in ("logq", "S", "logw")))
+        out["by_shape"][f"{nd}D L={L} C={c}"] = r
+    out["site_rtol"] = MARGIN * worst_site
+    out["scalar_rtol"] = MARGIN * worst_scalar
+    return out
+
+
+def main_tc():
+    res = {"what": "parity tolerances of the tensor-core kernel for the lattice shapes other than "
+                   "3D L=16 C=32, per coupling-layer count (FP32-accumulating model vs the FP64-summing "
+                   "emulation of its rounding points: h1, W2, h2 in bf16)",
+           "mode": TC_MODE, "margin": MARGIN, "shapes": [list(s) for s in TC_SHAPES],
+           "theory": "m2=-4, lam=6, weights seed 0", "prior_seed": SEED,
+           "command": "python tests/golden/bf16_tolerance.py --tc", "by_layers": {}}
+    for n in TC_LAYERS:
+        r = drift_tc(n, 64)
+        res["by_layers"][str(n)] = r
+        print(n, r["site_rtol"], r["scalar_rtol"], flush=True)
+    with open(TC_OUT, "w") as f:
+        json.dump(res, f, indent=1)
+    print("wrote", TC_OUT)
+
+
 def main():
     oracle.build()
+    if "--tc" in sys.argv[1:]:
+        main_tc()
+        return
     res = {"what": "BF16 path parity tolerances per coupling-layer count, derived from the oracle "
                    "(FP32-accumulating model vs the FP64-summing BF16 emulation)",
            "margin": MARGIN, "shape": "3D L=16, hidden 32, m2=-6, lam=5, weights seed 0",

@@ -17,20 +17,35 @@ LOGW_RTOL = 1e-4
 # margin, per number of coupling layers.
 BF16_MODE = 1 | 2 | 2048 | 4096 | 1024 | 32 | 512
 _BF16_TOL = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "bf16_tolerance.json")
+# The tensor-core kernel for the other lattice shapes rounds h1, W2 and h2 to
+# bf16 (conv1 and conv3 stay FP32); its bounds come from the same experiment
+# over 2D and 3D shapes of the serving mix (tests/golden/tc_tolerance.json).
+TC_MODE = 1 | 2 | 4 | 32
+_TC_TOL = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "tc_tolerance.json")
+
+
+def _pick_tolerance(path, n_layers):
+    with open(path) as f:
+        by = json.load(f)["by_layers"]
+    counts = sorted(int(k) for k in by)
+    pick = next((c for c in counts if c >= n_layers), None)
+    if pick is None:
+        raise ValueError(f"no tolerance measured for {n_layers} coupling layers in {path} (have {counts})")
+    e = by[str(pick)]
+    return float(e["site_rtol"]), float(e["scalar_rtol"])
+
+
+def tc_tolerances(n_layers: int):
+    """(per-site rtol, per-result rtol) of the second tensor-core kernel for a
+    flow of n_layers coupling layers (the smallest measured count >= n_layers)."""
+    return _pick_tolerance(_TC_TOL, n_layers)
 
 
 def bf16_tolerances(n_layers: int):
     """(per-site rtol, per-result rtol for log q / S / log w) for a flow of
     n_layers coupling layers: the bound measured for the smallest layer count
     in the experiment that is >= n_layers (the drift grows with depth)."""
-    with open(_BF16_TOL) as f:
-        by = json.load(f)["by_layers"]
-    counts = sorted(int(k) for k in by)
-    pick = next((c for c in counts if c >= n_layers), None)
-    if pick is None:
-        raise ValueError(f"no BF16 tolerance measured for {n_layers} coupling layers (have {counts})")
-    e = by[str(pick)]
-    return float(e["site_rtol"]), float(e["scalar_rtol"])
+    return _pick_tolerance(_BF16_TOL, n_layers)
 
 
 def bf16_site_rtol(n_layers: int) -> float:

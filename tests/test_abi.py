@@ -117,3 +117,26 @@ def test_force_is_defined_once():
         assert "4.0 * lam" not in src, fn
         users += "phi4_force_site(" in src
     assert users >= 3
+
+
+def test_tensor_core_support_query(lib):
+    """gf_flow_tensor_core_supported (host only): the shapes with a tensor-core
+    kernel are the two-equal-width networks of width 16, 24 or 32 with kernel
+    size 3 whose activations fit one block (or 3D L=16 with width 32); width 8,
+    other networks and invalid shapes answer 0."""
+    from paper_2208_08903_gb300 import _abi
+
+    def ex(nd, L, hidden, k=3):
+        hid = (C.c_int32 * _abi.GF_MAX_HIDDEN)(*(list(hidden) + [0] * (_abi.GF_MAX_HIDDEN - len(hidden))))
+        return _abi.FlowShapeExC(nd, L, 12, len(hidden), hid, k, 1, 0.01)
+
+    yes = [(2, 8, [16, 16]), (2, 16, [24, 24]), (2, 32, [32, 32]), (2, 64, [16, 16]), (3, 8, [32, 32]),
+           (3, 12, [16, 16]), (3, 16, [32, 32]), (3, 16, [16, 16])]
+    no = [(2, 32, [8, 8]), (2, 64, [32, 32]), (3, 12, [32, 32]), (3, 16, [24, 24]), (2, 32, [16, 32]),
+          (2, 32, [16, 16, 16]), (2, 7, [16, 16])]
+    for nd, L, h in yes:
+        assert lib.gf_flow_tensor_core_supported(C.byref(ex(nd, L, h))) == 1, (nd, L, h)
+    for nd, L, h in no:
+        assert lib.gf_flow_tensor_core_supported(C.byref(ex(nd, L, h))) == 0, (nd, L, h)
+    assert lib.gf_flow_tensor_core_supported(C.byref(ex(2, 32, [16, 16], k=5))) == 0
+    assert lib.gf_flow_tensor_core_supported(None) == 0

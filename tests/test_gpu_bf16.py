@@ -112,10 +112,13 @@ def test_bf16_full_batch_sampled(orc):
 
 
 def test_bf16_rejects_other_shapes():
+    """Hidden width 8 (no dense contraction) and lattices whose activations do
+    not fit one block (2D L=64 with width 32) have no tensor-core kernel."""
     torch, P = require_gpu()
-    shape = gi.FlowShape(3, 8, 2, 32, 32)
-    with pytest.raises(P._abi.GFError):
-        P.Flow(shape, gi.init_weights(shape), precision="bf16")
+    for shape in (gi.FlowShape(3, 8, 2, 8, 8), gi.FlowShape(2, 64, 2, 32, 32)):
+        assert not P.tensor_core_supported(shape)
+        with pytest.raises(P._abi.GFError):
+            P.Flow(shape, gi.init_weights(shape), precision="bf16")
 
 
 def test_bf16_64_configurations_error_report(orc):
