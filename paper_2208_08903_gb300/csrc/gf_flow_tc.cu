@@ -1,48 +1,57 @@
-// gf_flow_tc.cu -- fused coupling stack with conv2 on the tensor cores
-// (tcgen05, BF16 operands, FP32 accumulation in TMEM) for the lattice shapes
-// other than 3D L=16 with hidden width 32 (which has its own kernel): 2D and
-// 3D, even L, two equal hidden widths of 16, 24 or 32 channels (24 padded to
-// 32 with zero weights), kernel size 3, while the lattice's activations fit in
-// shared memory.
+// gf_flow_tc.cu -- fused coupling stack with conv2 and the conv3 head on the
+// tensor cores (tcgen05, 16-bit operands, FP32 accumulation in TMEM) for the
+// lattice shapes other than 3D L=16 with hidden width 32 (which has its own
+// kernel): 2D and 3D, even L, two equal hidden widths of 16, 24 or 32 channels
+// (24 padded to 32 with zero weights), kernel size 3, while the lattice's
+// activations fit in shared memory.
 //
 // Paper arXiv:2208.08903 Sec. 1 (checkerboard affine coupling layers, their
 // Jacobian, the model density and the action).  Precision: conv2, the dense
-// contraction (C x C x 3^d per site), reads BF16 h1 and W2 and accumulates in
-// FP32; conv1 (one input channel) and the conv3 head (two outputs, evaluated
-// at the updated sites only) are thin and run on the FP32 pipe from the FP32
-// field, FP32 weights and the BF16 h2; the affine update is FP32; log-det and
-// z^2 are summed per thread in FP32 pairs (about 2^-48 relative) and across
-// the block in FP64, as are log q, the action and log w.
+// contraction (C x C x 3^d per site), reads BF16 h1 and W2; the conv3 head
+// reads FP16 h2 and W3 (FP16 keeps three more mantissa bits of the small head
+// weights, whose BF16 rounding moved log w the most in the 3D kernel's
+// experiments); both accumulate in FP32.  conv1 (one input channel, about half
+// of its taps live) runs on the FP32 pipe from the FP32 field and weights; the
+// affine update is FP32; log-det and z^2 are summed per thread in FP32 pairs
+// (about 2^-48 relative) and across the block in FP64, as are log q, the
+// action and log w.  |h2| must stay below 65504: a non-finite s or t records
+// GF_EDEVICE.
 //
 // Per CTA one configuration at a time (persistent grid).  The activations
 // live in a zero-padded copy of the lattice, one halo layer per axis holding
 // the periodic images: P = L + 2 positions per axis, x fastest, stored
 // channel-group major [Cp/8][position][8 channels] so that 8 consecutive
 // positions of one channel group are one 128-byte core matrix of the
-// K-major canonical layout.  conv2 is then an implicit GEMM whose A operand
-// for tap (dz,dy,dx) is the same array started (dx-1) + (dy-1) P + (dz-1) P^2
-// positions later: M = 128 consecutive padded positions per tile (the rows
-// that fall on halo positions are computed and dropped), N = Cp output
-// channels, K = 3^d taps x Cp channels in steps of 16.  Per layer:
-//   conv1 (all warps): h1 = LReLU(W1 * masked x + b1) at every site, written
-//     in BF16 to its padded position and to its periodic images;
+// K-major canonical layout.  A convolution is then an implicit GEMM whose A
+// operand for tap (dz,dy,dx) is the same array started (dx-1) + (dy-1) P +
+// (dz-1) P^2 positions later: M = 128 consecutive padded positions per tile
+// (rows on halo positions are computed and dropped), K = 3^d taps x Cp
+// channels in steps of 16; N = Cp output channels for conv2, N = 16 for the
+// head (rows s and t, the rest zero).  Per layer, with a CTA barrier between
+// the phases:
+//   conv1 (all warps): h1 = LReLU(W1 * masked x + b1) at every site, BF16, at
+//     its padded position and at its periodic images;
 //   conv2 (one issuing thread): the tiles in order into a ring of TMEM
-//     accumulators; four epilogue warps (one per TMEM lane quarter) turn a
-//     tile into h2 = LReLU(acc + b2) in BF16, written over h1 in place once
-//     every tile that reads those positions (up to ceil(p0 / 128) tiles on,
-//     p0 = 1 + P (+ P^2) the largest tap offset) has completed;
-//   conv3 + update (all warps): (s, t) at the updated sites from the BF16 h2
-//     and FP32 W3, s = tanh(s), x <- x e^s + t (or the inverse), log-det += s.
+//     accumulators; two groups of four epilogue warps (one warp per TMEM lane
+//     quarter) take alternate tiles and turn them into h2 = LReLU(acc + b2) in
+//     FP16, written over h1 in place once every tile that reads those
+//     positions (up to ceil(p0 / 128) tiles on, p0 = 1 + P (+ P^2) the largest
+//     tap offset) has completed;
+//   halo (all warps): the periodic images of h2;
+//   conv3 (the issuing thread, the epilogue groups): (s, t) for every tile;
+//     at the updated sites s = tanh(s + b_s), x <- x e^s + t (or the
+//     inverse), log-det += s.
 // Each layer's weights arrive by bulk copies (cp.async.bulk): W2 for the next
-// layer as soon as this layer's conv2 has completed, the FP32 part (W1, b1,
-// b2, W3, b3) one layer ahead into a second buffer.  Every wait on an
-// mbarrier is bounded: a wait that runs out records GF_ETIMEOUT, raises the
-// CTA's abort flag, and the CTA leaves after draining its queued MMAs and
+// layer once this layer's conv2 has completed, W3 once its conv3 has, the
+// FP32 part (W1, b1, b2, b3) one layer ahead into a second buffer.  Every wait
+// on an mbarrier is bounded: a wait that runs out records GF_ETIMEOUT, raises
+// the CTA's abort flag, and the CTA leaves after draining its queued MMAs and
 // copies.
 #include <algorithm>
 #include <cstring>
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "gf_async.cuh"
 #include "gf_flow.cuh"
@@ -52,29 +61,48 @@ namespace gf {
 
 namespace {
 
-constexpr int kTcThreads = 256;           // warp 0: MMA issue and TMEM owner; warps 4..7: conv2 epilogue
-constexpr int kTcM = 128;                 // positions per conv2 tile (TMEM lanes)
-constexpr int kTcMaxBuf = 32;             // TMEM accumulator ring: at most 512 / 16 buffers
+constexpr int kTcThreads = 384;           // warp 0: MMA issue and TMEM owner; warps 4..11: two epilogue groups
+constexpr int kTcM = 128;                 // positions per tile (TMEM lanes)
+constexpr int kTcMaxBuf = 32;             // TMEM accumulator rings: at most 512 / 16 buffers
 constexpr long long kTcWaitLimit = 1ll << 22;
 constexpr int kSmemPerSM = 233472;        // 228 KB of shared memory per SM
 constexpr int kSmemPerCTA = 232448;       // 227 KB opt-in maximum per CTA
 constexpr int kSmemReserve = 1024;        // reserved per resident CTA
 
+// n / d as (n * m) >> k, exact for 0 <= n < 2^24 and 1 <= d < 2^12
+// (m = ceil(2^k / d) with k = 24 + ceil(log2 d): the round-up reciprocal of
+// Granlund and Montgomery, which fits 32 bits here).
+struct FastDiv {
+    uint32_t m;
+    int k;
+};
+FastDiv make_fastdiv(uint32_t d) {
+    int s = 0;
+    while ((1u << s) < d) ++s;
+    const int k = 24 + s;
+    return FastDiv{(uint32_t)(((1ull << k) + d - 1) / d), k};
+}
+__device__ __forceinline__ int fdiv(int n, const FastDiv& f) {
+    return (int)(((uint64_t)(uint32_t)n * f.m) >> f.k);
+}
+
 struct TcGeom {
     int nd, L, V, P, C, Cp, T;
     int p_first;          // padded position of site (0, ..., 0) = 1 + P (+ P^2); also the largest tap offset
-    int n_tiles;          // conv2 tiles covering the positions p_first .. L p_first
+    int n_tiles;          // tiles covering the positions p_first .. L p_first
     int npos;             // positions held per channel group (multiple of 8)
     int r_lag;            // tiles after a tile that read its positions: ceil(p_first / 128)
-    int nbuf, tmem_cols;  // TMEM accumulator ring (set at launch)
-    uint32_t w2_bytes, wf_bytes, layer_bytes;
-    int wf_W1, wf_b1, wf_b2, wf_W3, wf_b3;   // float offsets in the FP32 part of a layer block
-    uint32_t off_act, off_w2, off_wf, off_x, off_red, off_bar, smem_need;
+    int npad;             // P^nd: positions of the padded lattice
+    int nbuf2, nbuf3, tmem_cols;   // TMEM accumulator rings of conv2 (Cp columns) and conv3 (16); set at launch
+    FastDiv fd_half, fd_Lh, fd_L, fd_P, fd_PP;
+    uint32_t w2_bytes, w3_bytes, wf_bytes, layer_bytes;   // layer block: W2 | W3 | FP32 part
+    int wf_W1, wf_b1, wf_b2, wf_b3;                        // float offsets in the FP32 part
+    uint32_t off_act, off_w2, off_w3, off_wf, off_x, off_red, off_bar, smem_need;
 };
 
 struct TcArgs {
     TcGeom g;
-    const unsigned char* Wl;   // per-layer blocks: W2 [tap][kg][n][8] bf16, then the FP32 part
+    const unsigned char* Wl;   // per-layer blocks (layer_bytes each)
     int n_layers;
     float slope;
     int use_tanh, has_phi4;
@@ -90,9 +118,9 @@ __device__ __forceinline__ int wrapc(int v, int L) { return v < 0 ? v + L : (v >
 __device__ __forceinline__ float lrelu_tc(float v, float a) { return v > 0.f ? v : a * v; }
 
 // Bounded wait for completion number n (0-based) of an mbarrier (phase parity
-// n & 1; every waiter is at most one completion behind).  False when the
-// limit ran out (the CTA's abort flag is raised and GF_ETIMEOUT recorded) or
-// another thread already gave up.
+// n & 1; every waiter has seen completion n - 1 already, so the parity names
+// completion n).  False when the limit ran out (the CTA's abort flag is raised
+// and GF_ETIMEOUT recorded) or another thread already gave up.
 __device__ __forceinline__ bool tc_wait(uint64_t* bar, int64_t n, volatile int* abort_flag, int32_t* status) {
     long long spins = 0;
     while (!mbar_try_wait(bar, (uint32_t)(n & 1))) {
@@ -112,30 +140,30 @@ __device__ __forceinline__ void tc_drain(uint64_t* bar, int64_t n) {
     for (long long spins = 0; !mbar_try_wait(bar, (uint32_t)(n & 1)) && spins < kTcWaitLimit; ++spins) {}
 }
 
-// Site number j of the V/2 sites of parity q (rows y + L z in order, x fastest
-// within a row): x = 2 (j mod L/2) + ((q + y + z) mod 2).
-template <int ND>
-__device__ __forceinline__ void parity_site(int j, int q, int L, int& xc, int& yc, int& zc) {
-    const int Lh = L >> 1;
-    const int xh = j % Lh, r = j / Lh;
-    yc = r % L;
-    zc = ND == 3 ? r / L : 0;
-    xc = 2 * xh + ((q ^ yc ^ zc) & 1);
-}
-
 __device__ __forceinline__ uint4 pack_bf16x8(const float* v) {
     __align__(16) __nv_bfloat162 p[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) p[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
     return *reinterpret_cast<const uint4*>(p);
 }
-__device__ __forceinline__ void unpack_bf16x8(const uint4& w, float* v) {
-    const uint32_t u[4] = {w.x, w.y, w.z, w.w};
+__device__ __forceinline__ uint4 pack_f16x8(const float* v) {
+    __align__(16) __half2 p[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        v[2 * i] = __uint_as_float(u[i] << 16);
-        v[2 * i + 1] = __uint_as_float(u[i] & 0xFFFF0000u);
+    for (int i = 0; i < 4; ++i) p[i] = __floats2half2_rn(v[2 * i], v[2 * i + 1]);
+    return *reinterpret_cast<const uint4*>(p);
+}
+
+// Padded coordinates (px, py, pz) of position p; pz = 1 in 2D.
+template <int ND>
+__device__ __forceinline__ void pos_xyz(const TcGeom& g, int p, int& px, int& py, int& pz) {
+    int rem = p;
+    pz = 1;
+    if (ND == 3) {
+        pz = fdiv(p, g.fd_PP);
+        rem = p - pz * g.P * g.P;
     }
+    py = fdiv(rem, g.fd_P);
+    px = rem - py * g.P;
 }
 
 // conv1: h1 = LReLU(W1 * (x at the frozen sites) + b1) for every site and
@@ -143,18 +171,21 @@ __device__ __forceinline__ void unpack_bf16x8(const uint4& w, float* v) {
 // Work items are ordered (channel group, site parity, site), so a warp holds
 // one channel group (its weight loads are broadcasts) and one site parity (the
 // live taps, those that reach frozen sites, are the same for the whole warp).
+// Site j of parity q (rows y + L z in order, x fastest in a row): x = 2 (j mod
+// L/2) + ((q + y + z) mod 2).
 template <int ND, int CP>
 __device__ void tc_conv1(const TcGeom& g, const float* wf, const float* x, int frozen, float slope,
                          unsigned char* act) {
     constexpr int NKG = CP / 8;
-    const int L = g.L, half = g.V >> 1, P = g.P, npos = g.npos;
+    const int L = g.L, half = g.V >> 1, Lh = L >> 1, P = g.P, npos = g.npos;
     const float* W1 = wf + g.wf_W1;
     const float* b1 = wf + g.wf_b1;
     for (int it = threadIdx.x; it < half * 2 * NKG; it += blockDim.x) {
-        const int grp = it / half, j = it - grp * half;
+        const int grp = fdiv(it, g.fd_half), j = it - grp * half;
         const int kg = grp >> 1, q = grp & 1;
-        int xc, yc, zc;
-        parity_site<ND>(j, q, L, xc, yc, zc);
+        const int r = fdiv(j, g.fd_Lh), xh = j - r * Lh;
+        const int zc = ND == 3 ? fdiv(r, g.fd_L) : 0, yc = r - zc * L;
+        const int xc = 2 * xh + ((q ^ yc ^ zc) & 1);
         float acc[8];
         {
             const float4 lo = *reinterpret_cast<const float4*>(b1 + kg * 8);
@@ -212,69 +243,51 @@ __device__ void tc_conv1(const TcGeom& g, const float* wf, const float* x, int f
     }
 }
 
-// conv3 head at the updated sites and the affine update (paper Sec. 1):
-// s, t = W3 * h2 + b3 (s through tanh when use_final_tanh), x <- x e^s + t in
-// the sampling direction, (x - t) e^-s inverting; log-det += s.  Work items
-// (site, channel group) with the channel groups in adjacent lanes; their
-// partial sums meet by a fixed butterfly, so every result is independent of
-// where the configuration runs.
-template <int ND, int CP, bool INVERSE>
-__device__ void tc_conv3(const TcGeom& g, const float* wf, const unsigned char* act, float* x, int frozen,
-                         int use_tanh, FF& logdet) {
+// The periodic images of h2: every halo position of the padded lattice gets
+// the channel groups of its interior source site.
+template <int ND, int CP>
+__device__ void tc_halo(const TcGeom& g, unsigned char* act) {
     constexpr int NKG = CP / 8;
-    const int L = g.L, half = g.V >> 1, P = g.P, npos = g.npos;
-    const int pa = frozen ^ 1;
-    const float* W3 = wf + g.wf_W3;
-    const float bs = wf[g.wf_b3], bt = wf[g.wf_b3 + 1];
-    for (int it = threadIdx.x; it < half * NKG; it += blockDim.x) {
-        const int kg = it % NKG, j = it / NKG;
-        int xc, yc, zc;
-        parity_site<ND>(j, pa, L, xc, yc, zc);
-        const int xs[3] = {wrapc(xc - 1, L) + 1, xc + 1, wrapc(xc + 1, L) + 1};
-        const int ys[3] = {(wrapc(yc - 1, L) + 1) * P, (yc + 1) * P, (wrapc(yc + 1, L) + 1) * P};
-        int zs[3] = {0, 0, 0};
-        if (ND == 3) {
-            zs[0] = (wrapc(zc - 1, L) + 1) * P * P;
-            zs[1] = (zc + 1) * P * P;
-            zs[2] = (wrapc(zc + 1, L) + 1) * P * P;
-        }
-        const unsigned char* base = act + (size_t)kg * npos * 16;
-        float ps = 0.f, pt = 0.f;
+    const int L = g.L, P = g.P, npos = g.npos;
+    for (int p = threadIdx.x; p < g.npad; p += blockDim.x) {
+        int px, py, pz;
+        pos_xyz<ND>(g, p, px, py, pz);
+        if (px >= 1 && px <= L && py >= 1 && py <= L && pz >= 1 && pz <= L) continue;
+        const int sx = px == 0 ? L : (px == L + 1 ? 1 : px);
+        const int sy = py == 0 ? L : (py == L + 1 ? 1 : py);
+        const int sz = ND == 3 ? (pz == 0 ? L : (pz == L + 1 ? 1 : pz)) : 0;
+        const int src = sx + sy * P + sz * P * P;
 #pragma unroll
-        for (int dz = 0; dz < (ND == 3 ? 3 : 1); ++dz) {
+        for (int kg = 0; kg < NKG; ++kg)
+            *reinterpret_cast<uint4*>(act + ((size_t)kg * npos + p) * 16) =
+                *reinterpret_cast<const uint4*>(act + ((size_t)kg * npos + src) * 16);
+    }
+}
+
+// One issuing thread: a convolution's tile t as an implicit GEMM, all taps
+// and K-steps of 16 channels, into TMEM columns d, completion on `full`.
+// a0 / b0: descriptors of the activations and of tap 0, K-step 0 of the
+// weights; b_tap, b_ks: the weights' descriptor steps (16-byte units).
+template <int ND, int CP>
+__device__ __forceinline__ void issue_tile(const TcGeom& g, int t, uint32_t d, uint64_t a0, uint64_t b0,
+                                           uint32_t b_tap, uint32_t b_ks, uint32_t idesc, uint64_t* full) {
+    int tap = 0;
+    for (int dz = 0; dz < (ND == 3 ? 3 : 1); ++dz) {
+        for (int dy = 0; dy < 3; ++dy) {
+            const int row0 = g.p_first + kTcM * t + (dy - 1) * g.P + (ND == 3 ? (dz - 1) * g.P * g.P : 0);
 #pragma unroll
-            for (int dy = 0; dy < 3; ++dy) {
+            for (int dx = 0; dx < 3; ++dx, ++tap) {
+                const uint32_t aoff = (uint32_t)(row0 + dx - 1);   // positions = 16-byte units
 #pragma unroll
-                for (int dx = 0; dx < 3; ++dx) {
-                    const int t = ND == 3 ? (dz * 3 + dy) * 3 + dx : dy * 3 + dx;
-                    float h[8];
-                    unpack_bf16x8(*reinterpret_cast<const uint4*>(base + (size_t)(zs[dz] + ys[dy] + xs[dx]) * 16), h);
-                    const float4* w = reinterpret_cast<const float4*>(W3 + (t * CP + kg * 8) * 2);
-#pragma unroll
-                    for (int c4 = 0; c4 < 4; ++c4) {
-                        const float4 ww = w[c4];             // (s, t) weights of channels 2 c4, 2 c4 + 1
-                        ps = fmaf(h[2 * c4], ww.x, ps);
-                        pt = fmaf(h[2 * c4], ww.y, pt);
-                        ps = fmaf(h[2 * c4 + 1], ww.z, ps);
-                        pt = fmaf(h[2 * c4 + 1], ww.w, pt);
-                    }
+                for (int ks = 0; ks < CP / 16; ++ks) {
+                    const uint64_t ad = desc_add(a0, aoff + (uint32_t)(2 * ks * g.npos));
+                    const uint64_t bd = desc_add(b0, (uint32_t)tap * b_tap + (uint32_t)ks * b_ks);
+                    mma_bf16(d, ad, bd, idesc, (tap | ks) ? 1u : 0u);
                 }
             }
         }
-#pragma unroll
-        for (int o = 1; o < NKG; o <<= 1) {
-            ps += __shfl_xor_sync(0xffffffffu, ps, o);
-            pt += __shfl_xor_sync(0xffffffffu, pt, o);
-        }
-        if (kg == 0) {
-            const float s = use_tanh ? tanhf(ps + bs) : ps + bs;
-            const float tt = pt + bt;
-            float& xv = x[(zc * L + yc) * L + xc];
-            if (!INVERSE) xv = fmaf(xv, expf(s), tt);
-            else xv = (xv - tt) * expf(-s);
-            ff_add(logdet, s);
-        }
     }
+    mma_commit(full);
 }
 
 template <int ND, int CP, bool INVERSE>
@@ -284,39 +297,44 @@ __global__ void __launch_bounds__(kTcThreads) flow_tc_kernel(const TcArgs a) {
     const TcGeom& g = a.g;
     unsigned char* act = smem + g.off_act;
     unsigned char* w2s = smem + g.off_w2;
+    unsigned char* w3s = smem + g.off_w3;
     float* wfs = reinterpret_cast<float*>(smem + g.off_wf);
     float* x = reinterpret_cast<float*>(smem + g.off_x);
     FF* red = reinterpret_cast<FF*>(smem + g.off_red);
-    uint64_t* bar_full = reinterpret_cast<uint64_t*>(smem + g.off_bar);   // nbuf: a tile's MMAs done (commit)
-    uint64_t* bar_empty = bar_full + kTcMaxBuf;                             // nbuf: a tile's TMEM drained (128)
-    uint64_t* bar_w2 = bar_empty + kTcMaxBuf;                               // a layer's W2 staged
-    uint64_t* bar_wf = bar_w2 + 1;                                          // 2: a layer's FP32 part staged
-    uint64_t* bar_fin = bar_wf + 2;                                         // every queued MMA done (exit)
+    uint64_t* full2 = reinterpret_cast<uint64_t*>(smem + g.off_bar);   // conv2 tile's MMAs done (commit)
+    uint64_t* empty2 = full2 + kTcMaxBuf;                                // its accumulator drained (128)
+    uint64_t* full3 = empty2 + kTcMaxBuf;                                // conv3 tile's MMAs done
+    uint64_t* empty3 = full3 + kTcMaxBuf;                                // its accumulator drained
+    uint64_t* bar_w2 = empty3 + kTcMaxBuf;                               // a layer's W2 staged
+    uint64_t* bar_w3 = bar_w2 + 1;                                       // a layer's W3 staged
+    uint64_t* bar_wf = bar_w3 + 1;                                       // 2: a layer's FP32 part staged
+    uint64_t* bar_fin = bar_wf + 2;                                      // every queued MMA done (exit)
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar_fin + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int V = g.V, npos = g.npos;
+    const int V = g.V, L = g.L, npos = g.npos, nt = g.n_tiles;
     const int wf_floats = (int)(g.wf_bytes >> 2);
     const int64_t n_cfg = a.B > (int64_t)blockIdx.x ? (a.B - 1 - (int64_t)blockIdx.x) / gridDim.x + 1 : 0;
     const int64_t total_steps = n_cfg * a.n_layers;   // this CTA's layer applications
-    int64_t w2_issued = -1, wf_issued = -1;           // thread 0: the last staged steps
+    int64_t w2_issued = -1, w3_issued = -1, wf_issued = -1;   // thread 0: the last staged steps
+    // epilogue warps: group eg (0: warps 4..7, 1: warps 8..11) takes the tiles
+    // t = eg (mod 2); warp w reads TMEM lane quarter q = w mod 4
+    const int eg = warp >= 4 ? (warp - 4) >> 2 : -1, q = warp & 3;
 
     const auto block_of = [&](int64_t step) {
         const int li = (int)(step % a.n_layers);
         return a.Wl + (size_t)(INVERSE ? a.n_layers - 1 - li : li) * g.layer_bytes;
     };
-    const auto stage_w2 = [&](int64_t step) {
+    const auto stage = [&](int64_t step, void* dst, uint32_t off, uint32_t bytes, uint64_t* bar) {
         fence_proxy_async();
-        mbar_expect_tx(bar_w2, g.w2_bytes);
-        bulk_g2s(w2s, block_of(step), g.w2_bytes, bar_w2);
-        w2_issued = step;
+        mbar_expect_tx(bar, bytes);
+        bulk_g2s(dst, block_of(step) + off, bytes, bar);
     };
+    const auto stage_w2 = [&](int64_t step) { stage(step, w2s, 0, g.w2_bytes, bar_w2); w2_issued = step; };
+    const auto stage_w3 = [&](int64_t step) { stage(step, w3s, g.w2_bytes, g.w3_bytes, bar_w3); w3_issued = step; };
     const auto stage_wf = [&](int64_t step) {
-        const int sel = (int)(step & 1);
-        fence_proxy_async();
-        mbar_expect_tx(bar_wf + sel, g.wf_bytes);
-        bulk_g2s(wfs + sel * wf_floats, block_of(step) + g.w2_bytes, g.wf_bytes, bar_wf + sel);
+        stage(step, wfs + (int)(step & 1) * wf_floats, g.w2_bytes + g.w3_bytes, g.wf_bytes, bar_wf + (step & 1));
         wf_issued = step;
     };
 
@@ -325,19 +343,22 @@ __global__ void __launch_bounds__(kTcThreads) flow_tc_kernel(const TcArgs a) {
         tmem_relinquish();
     }
     if (tid == 0) {
-        for (int i = 0; i < g.nbuf; ++i) {
-            mbar_init(bar_full + i, 1);
-            mbar_init(bar_empty + i, 4 * 32);
+        for (int i = 0; i < kTcMaxBuf; ++i) {
+            mbar_init(full2 + i, 1);
+            mbar_init(empty2 + i, 4 * 32);
+            mbar_init(full3 + i, 1);
+            mbar_init(empty3 + i, 4 * 32);
         }
         mbar_init(bar_w2, 1);
+        mbar_init(bar_w3, 1);
         mbar_init(bar_wf, 1);
         mbar_init(bar_wf + 1, 1);
         mbar_init(bar_fin, 1);
         *abort_flag = 0;
         fence_mbar_init();
     }
-    // positions past the lattice feed only dropped rows of the last tiles; zero
-    // them once so every MMA reads finite numbers
+    // positions past the padded lattice feed only dropped rows of the last
+    // tiles; zero them once so every MMA reads finite numbers
     for (int i = tid; i < NKG * npos; i += blockDim.x)
         reinterpret_cast<uint4*>(act)[i] = make_uint4(0u, 0u, 0u, 0u);
     fence_proxy_async();
@@ -346,15 +367,19 @@ __global__ void __launch_bounds__(kTcThreads) flow_tc_kernel(const TcArgs a) {
     fence_after_sync();
     if (tid == 0 && total_steps > 0) {
         stage_w2(0);
+        stage_w3(0);
         stage_wf(0);
     }
     const uint32_t tmem = *tmem_slot;
-    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(CP >> 3) << 17) |
-                           ((uint32_t)(kTcM >> 4) << 24);   // D F32, A = B = BF16, K-major, M = 128, N = CP
-    const uint64_t adesc0 = smem_desc(smem_u32(act), (uint32_t)npos * 16u, 128u);
-    const uint64_t bdesc0 = smem_desc(smem_u32(w2s), (uint32_t)CP * 16u, 128u);
+    // D = F32, K-major A and B, M = 128: conv2 BF16 with N = CP, conv3 FP16 with N = 16
+    const uint32_t idesc2 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(CP >> 3) << 17) |
+                            ((uint32_t)(kTcM >> 4) << 24);
+    const uint32_t idesc3 = (1u << 4) | ((16u >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
+    const uint64_t a0 = smem_desc(smem_u32(act), (uint32_t)npos * 16u, 128u);
+    const uint64_t b2d = smem_desc(smem_u32(w2s), (uint32_t)CP * 16u, 128u);   // [tap][kg][n < CP][8] bf16
+    const uint64_t b3d = smem_desc(smem_u32(w3s), 16u * 16u, 128u);           // [tap][kg][n < 16][8] fp16
 
-    int64_t step = 0, tile_seq = 0;
+    int64_t step = 0, seq2 = 0, seq3 = 0;   // layer steps and tiles of each convolution so far
     for (int64_t b = blockIdx.x; b < a.B; b += gridDim.x) {
         // prior sample (sampling) or the given field (inverting)
         FF sumz2{0.f, 0.f};
@@ -373,10 +398,10 @@ __global__ void __launch_bounds__(kTcThreads) flow_tc_kernel(const TcArgs a) {
                     float zz[4];
                     normals4_f32(w, zz);
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        x[4 * jq + q] = zz[q];
-                        const float p = zz[q] * zz[q];
-                        ff_add(sumz2, FF{p, fmaf(zz[q], zz[q], -p)});
+                    for (int k = 0; k < 4; ++k) {
+                        x[4 * jq + k] = zz[k];
+                        const float p = zz[k] * zz[k];
+                        ff_add(sumz2, FF{p, fmaf(zz[k], zz[k], -p)});
                     }
                 }
             }
@@ -393,7 +418,8 @@ __global__ void __launch_bounds__(kTcThreads) flow_tc_kernel(const TcArgs a) {
             const int l = INVERSE ? a.n_layers - 1 - li : li;
             const int frozen = l & 1;
             const float* wf = wfs + (int)(step & 1) * wf_floats;
-            // conv1 -> h1 (BF16, padded, with periodic images)
+
+            // ---- conv1 -> h1 (BF16, padded, with periodic images)
             if (tc_wait(bar_wf + (step & 1), step >> 1, abort_flag, a.status)) {
                 if (tid == 0 && step + 1 < total_steps) stage_wf(step + 1);
                 tc_conv1<ND, CP>(g, wf, x, frozen, a.slope, act);
@@ -402,55 +428,35 @@ __global__ void __launch_bounds__(kTcThreads) flow_tc_kernel(const TcArgs a) {
             __syncthreads();
             if (*abort_flag) break;
 
-            // conv2 on the tensor cores; the epilogue writes h2 over h1 in place
-            if (warp == 0) {
-                if (lane == 0 && tc_wait(bar_w2, step, abort_flag, a.status)) {
-                    for (int t = 0; t < g.n_tiles; ++t) {
-                        const int64_t s = tile_seq + t;
-                        const int buf = (int)(s % g.nbuf);
-                        const int64_t k = s / g.nbuf;
-                        if (k >= 1 && !tc_wait(bar_empty + buf, k - 1, abort_flag, a.status)) break;
+            // ---- conv2 on the tensor cores; the epilogue writes h2 (FP16) over h1 in place
+            if (tid == 0) {
+                if (tc_wait(bar_w2, step, abort_flag, a.status)) {
+                    for (int t = 0; t < nt; ++t) {
+                        const int64_t s = seq2 + t;
+                        const int buf = (int)(s % g.nbuf2);
+                        const int64_t k = s / g.nbuf2;
+                        if (k >= 1 && !tc_wait(empty2 + buf, k - 1, abort_flag, a.status)) break;
                         fence_after_sync();
-                        const uint32_t d = tmem + (uint32_t)(buf * CP);
-                        // tap (dz, dy, dx) reads the positions shifted by (dx-1) + (dy-1) P + (dz-1) P^2
-                        int tap = 0;
-                        for (int dz = 0; dz < (ND == 3 ? 3 : 1); ++dz) {
-                            for (int dy = 0; dy < 3; ++dy) {
-                                const int row0 = g.p_first + kTcM * t + (dy - 1) * g.P +
-                                                 (ND == 3 ? (dz - 1) * g.P * g.P : 0);
-#pragma unroll
-                                for (int dx = 0; dx < 3; ++dx, ++tap) {
-                                    const uint32_t aoff = (uint32_t)(row0 + dx - 1);   // 16-byte units
-#pragma unroll
-                                    for (int ks = 0; ks < CP / 16; ++ks) {
-                                        const uint64_t ad = desc_add(adesc0, aoff + (uint32_t)(2 * ks * npos));
-                                        const uint64_t bd = desc_add(bdesc0, (uint32_t)((tap * NKG + 2 * ks) * CP));
-                                        mma_bf16(d, ad, bd, idesc, (tap | ks) ? 1u : 0u);
-                                    }
-                                }
-                            }
-                        }
-                        mma_commit(bar_full + buf);
+                        issue_tile<ND, CP>(g, t, tmem + (uint32_t)(buf * CP), a0, b2d, (uint32_t)(NKG * CP),
+                                           (uint32_t)(2 * CP), idesc2, full2 + buf);
                     }
                 }
-                __syncwarp();
-            } else if (warp >= 4) {
-                const int q = warp & 3;
+            } else if (eg >= 0) {
                 const float* b2 = wf + g.wf_b2;
-                int64_t waited = tile_seq;     // next tile whose completion is still to be awaited
+                int64_t waited = seq2;     // completions are awaited in tile order (both groups)
                 bool ok = true;
-                for (int t = 0; t < g.n_tiles && ok; ++t) {
+                for (int t = eg; t < nt && ok; t += 2) {
                     // h2 of tile t may overwrite h1 once tiles t .. t + r_lag are done
-                    const int64_t need = tile_seq + (t + g.r_lag < g.n_tiles ? t + g.r_lag : g.n_tiles - 1);
+                    const int64_t need = seq2 + (t + g.r_lag < nt ? t + g.r_lag : nt - 1);
                     while (ok && waited <= need) {
-                        ok = tc_wait(bar_full + (int)(waited % g.nbuf), waited / g.nbuf, abort_flag, a.status);
+                        ok = tc_wait(full2 + (int)(waited % g.nbuf2), waited / g.nbuf2, abort_flag, a.status);
                         ++waited;
                     }
                     if (!ok) break;
                     fence_after_sync();
-                    const int buf = (int)((tile_seq + t) % g.nbuf);
-                    float v[32];
+                    const int buf = (int)((seq2 + t) % g.nbuf2);
                     const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * CP);
+                    float v[CP];
                     {
                         float v16[16];
                         tmem_ld16(taddr, v16);
@@ -464,32 +470,88 @@ __global__ void __launch_bounds__(kTcThreads) flow_tc_kernel(const TcArgs a) {
                         tmem_ld_wait();
                     }
                     fence_before_sync();
-                    mbar_arrive(bar_empty + buf);
+                    mbar_arrive(empty2 + buf);
                     const int p = g.p_first + kTcM * t + 32 * q + lane;
-                    const int P = g.P;
-                    const int px = p % P, py = (p / P) % P, pz = ND == 3 ? p / (P * P) : 1;
-                    if (px >= 1 && px <= g.L && py >= 1 && py <= g.L && pz >= 1 && pz <= g.L) {
+                    int px, py, pz;
+                    pos_xyz<ND>(g, p, px, py, pz);
+                    if (px >= 1 && px <= L && py >= 1 && py <= L && pz >= 1 && pz <= L) {
 #pragma unroll
                         for (int kg = 0; kg < NKG; ++kg) {
                             float h[8];
 #pragma unroll
                             for (int c = 0; c < 8; ++c) h[c] = lrelu_tc(v[kg * 8 + c] + b2[kg * 8 + c], a.slope);
-                            *reinterpret_cast<uint4*>(act + ((size_t)kg * npos + p) * 16) = pack_bf16x8(h);
+                            *reinterpret_cast<uint4*>(act + ((size_t)kg * npos + p) * 16) = pack_f16x8(h);
                         }
                     }
                 }
             }
-            tile_seq += g.n_tiles;
+            seq2 += nt;
             fence_before_sync();
             __syncthreads();
             if (*abort_flag) break;
             fence_after_sync();
-            // every MMA of this layer has completed: the next layer's W2 may land
+            // every conv2 MMA of this layer has completed: the next layer's W2 may land
             if (tid == 0 && step + 1 < total_steps) stage_w2(step + 1);
 
-            // conv3 and the affine update of the other parity
-            tc_conv3<ND, CP, INVERSE>(g, wf, act, x, frozen, a.use_tanh, logdet);
+            // ---- periodic images of h2
+            tc_halo<ND, CP>(g, act);
+            fence_proxy_async();
             __syncthreads();
+
+            // ---- conv3 (s, t) on the tensor cores; the epilogue updates the other parity
+            if (tid == 0) {
+                if (tc_wait(bar_w3, step, abort_flag, a.status)) {
+                    for (int t = 0; t < nt; ++t) {
+                        const int64_t s = seq3 + t;
+                        const int buf = (int)(s % g.nbuf3);
+                        const int64_t k = s / g.nbuf3;
+                        if (k >= 1 && !tc_wait(empty3 + buf, k - 1, abort_flag, a.status)) break;
+                        fence_after_sync();
+                        issue_tile<ND, CP>(g, t, tmem + (uint32_t)(buf * 16), a0, b3d, (uint32_t)(NKG * 16),
+                                           (uint32_t)(2 * 16), idesc3, full3 + buf);
+                    }
+                }
+            } else if (eg >= 0) {
+                const float bs = wf[g.wf_b3], bt = wf[g.wf_b3 + 1];
+                const int pa = frozen ^ 1;
+                int64_t waited = seq3;
+                bool ok = true;
+                for (int t = eg; t < nt && ok; t += 2) {
+                    while (ok && waited <= seq3 + t) {
+                        ok = tc_wait(full3 + (int)(waited % g.nbuf3), waited / g.nbuf3, abort_flag, a.status);
+                        ++waited;
+                    }
+                    if (!ok) break;
+                    fence_after_sync();
+                    const int buf = (int)((seq3 + t) % g.nbuf3);
+                    float st[2];
+                    tmem_ld2(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 16), st);
+                    tmem_ld_wait();
+                    fence_before_sync();
+                    mbar_arrive(empty3 + buf);
+                    const int p = g.p_first + kTcM * t + 32 * q + lane;
+                    int px, py, pz;
+                    pos_xyz<ND>(g, p, px, py, pz);
+                    // parity of the site (px - 1, py - 1, pz - 1)
+                    const int par = ND == 3 ? ((px + py + pz + 1) & 1) : ((px + py) & 1);
+                    if (px >= 1 && px <= L && py >= 1 && py <= L && pz >= 1 && pz <= L && par == pa) {
+                        const float s = a.use_tanh ? tanhf(st[0] + bs) : st[0] + bs;
+                        const float tt = st[1] + bt;
+                        if (!isfinite(s) || !isfinite(tt)) set_status(a.status, GF_EDEVICE);
+                        float& xv = x[((ND == 3 ? (pz - 1) * L : 0) + (py - 1)) * L + (px - 1)];
+                        if (!INVERSE) xv = fmaf(xv, expf(s), tt);
+                        else xv = (xv - tt) * expf(-s);
+                        ff_add(logdet, s);
+                    }
+                }
+            }
+            seq3 += nt;
+            fence_before_sync();
+            __syncthreads();
+            if (*abort_flag) break;
+            fence_after_sync();
+            // every conv3 MMA of this layer has completed: the next layer's W3 may land
+            if (tid == 0 && step + 1 < total_steps) stage_w3(step + 1);
         }
         if (*abort_flag) break;
 
@@ -506,7 +568,7 @@ __global__ void __launch_bounds__(kTcThreads) flow_tc_kernel(const TcArgs a) {
         const double ld = block_sum_ff(logdet, red);
         const double z2 = block_sum_ff(sumz2, red);
         double S = 0.0;
-        if (!INVERSE && a.has_phi4) S = block_sum_ff(action_part<ND>(x, g.L, V, a.c2d_ff, a.lam_ff), red);
+        if (!INVERSE && a.has_phi4) S = block_sum_ff(action_part<ND>(x, L, V, a.c2d_ff, a.lam_ff), red);
         if (tid == 0) {
             const double logr = -0.5 * z2 - 0.5 * (double)V * LOG_2PI;
             const double logq = logr - ld;
@@ -522,9 +584,8 @@ __global__ void __launch_bounds__(kTcThreads) flow_tc_kernel(const TcArgs a) {
     // abort) finish before their shared memory and TMEM are released
     if (tid == 0) {
         if (w2_issued >= 0) tc_drain(bar_w2, w2_issued);
+        if (w3_issued >= 0) tc_drain(bar_w3, w3_issued);
         if (wf_issued >= 0) tc_drain(bar_wf + (wf_issued & 1), wf_issued >> 1);
-    }
-    if (tid == 0) {
         mma_commit(bar_fin);
         tc_drain(bar_fin, 0);
     }
@@ -537,12 +598,13 @@ __global__ void __launch_bounds__(kTcThreads) flow_tc_kernel(const TcArgs a) {
 }
 
 // canonical FP32 -> per-layer block: W2 as [tap][kg][n][8] bf16 (K-major core
-// matrices; rows n >= C and channels >= C zero), then FP32 W1 [tap][Cp],
-// b1 [Cp], b2 [Cp], W3 [tap][Cp][2] (s, t), b3 [2], zero padding.
+// matrices; rows n >= C and channels >= C zero), W3 as [tap][kg][n][8] fp16
+// with n = 0: s, 1: t, rows 2..15 zero, then FP32 W1 [tap][Cp], b1 [Cp],
+// b2 [Cp], b3 [2], zero padding.
 __global__ void repack_tc_kernel(const float* __restrict__ canon, int64_t cstride, int n_layers, TcGeom g,
                                  unsigned char* __restrict__ out) {
     const int T = g.T, C = g.C, CP = g.Cp, NKG = CP / 8;
-    const int64_t n2 = g.w2_bytes / 2, nf = g.wf_bytes / 4, per = n2 + nf;
+    const int64_t n2 = g.w2_bytes / 2, n3 = g.w3_bytes / 2, nf = g.wf_bytes / 4, per = n2 + n3 + nf;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < per * n_layers;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int l = (int)(i / per);
@@ -559,8 +621,13 @@ __global__ void repack_tc_kernel(const float* __restrict__ canon, int64_t cstrid
             const int t = (int)(r / (8 * CP * NKG)), ic = kg * 8 + e;
             const float v = (n < C && ic < C) ? W2[((int64_t)n * C + ic) * T + t] : 0.f;
             reinterpret_cast<__nv_bfloat16*>(blk)[r] = __float2bfloat16_rn(v);
+        } else if (r < n2 + n3) {
+            const int r3 = (int)(r - n2);
+            const int e = r3 & 7, n = (r3 >> 3) & 15, kg = (r3 >> 7) % NKG, t = r3 / (128 * NKG), ic = kg * 8 + e;
+            const float v = (n < 2 && ic < C) ? W3[((int64_t)n * C + ic) * T + t] : 0.f;
+            reinterpret_cast<__half*>(blk + g.w2_bytes)[r3] = __float2half_rn(v);
         } else {
-            const int f = (int)(r - n2);
+            const int f = (int)(r - n2 - n3);
             float v = 0.f;
             if (f < g.wf_b1) {
                 const int t = f / CP, c = f % CP;
@@ -568,22 +635,19 @@ __global__ void repack_tc_kernel(const float* __restrict__ canon, int64_t cstrid
             } else if (f < g.wf_b2) {
                 const int c = f - g.wf_b1;
                 if (c < C) v = b1[c];
-            } else if (f < g.wf_W3) {
+            } else if (f < g.wf_b3) {
                 const int c = f - g.wf_b2;
                 if (c < C) v = b2[c];
-            } else if (f < g.wf_b3) {
-                const int r3 = f - g.wf_W3, t = r3 / (2 * CP), c = (r3 >> 1) % CP, j = r3 & 1;
-                if (c < C) v = W3[((int64_t)j * C + c) * T + t];
             } else if (f < g.wf_b3 + 2) {
                 v = b3[f - g.wf_b3];
             }
-            reinterpret_cast<float*>(blk + g.w2_bytes)[f] = v;
+            reinterpret_cast<float*>(blk + g.w2_bytes + g.w3_bytes)[f] = v;
         }
     }
 }
 
 // Geometry and shared-memory plan of a shape; false when this kernel does not
-// take it (the TMEM ring is chosen at launch).
+// take it (the TMEM rings are chosen at launch).
 bool tc_plan(const gf_flow_shape& s, TcGeom& g) {
     std::memset(&g, 0, sizeof(g));
     if (s.nd != 2 && s.nd != 3) return false;
@@ -601,28 +665,36 @@ bool tc_plan(const gf_flow_shape& s, TcGeom& g) {
     if (g.V % 64 != 0 || g.V > 65536) return false;        // V/2 a multiple of 32: parity-uniform warps
     g.P = s.L + 2;
     g.T = s.nd == 3 ? 27 : 9;
+    g.npad = s.nd == 3 ? g.P * g.P * g.P : g.P * g.P;
     g.p_first = s.nd == 3 ? 1 + g.P + g.P * g.P : 1 + g.P;
     const int p_last = g.p_first * s.L;
     g.n_tiles = (p_last - g.p_first + 1 + kTcM - 1) / kTcM;
     g.npos = (2 * g.p_first + g.n_tiles * kTcM + 7) & ~7;
     if (g.npos > 16383) return false;                      // descriptor LBO field (16-byte units)
     g.r_lag = (g.p_first + kTcM - 1) / kTcM;
+    g.fd_half = make_fastdiv((uint32_t)(g.V / 2));
+    g.fd_Lh = make_fastdiv((uint32_t)(s.L / 2));
+    g.fd_L = make_fastdiv((uint32_t)s.L);
+    g.fd_P = make_fastdiv((uint32_t)g.P);
+    g.fd_PP = make_fastdiv((uint32_t)(g.P * g.P));
+    if (g.V / 2 >= 4096 || g.npos * 4 >= (1 << 24)) return false;   // FastDiv ranges
     const int NKG = g.Cp / 8;
     g.w2_bytes = (uint32_t)(g.T * NKG * g.Cp * 16);
+    g.w3_bytes = (uint32_t)(g.T * NKG * 16 * 16);
     g.wf_W1 = 0;
     g.wf_b1 = g.T * g.Cp;
     g.wf_b2 = g.wf_b1 + g.Cp;
-    g.wf_W3 = g.wf_b2 + g.Cp;
-    g.wf_b3 = g.wf_W3 + 2 * g.T * g.Cp;
+    g.wf_b3 = g.wf_b2 + g.Cp;
     g.wf_bytes = (uint32_t)(((g.wf_b3 + 2 + 3) & ~3) * 4);
-    g.layer_bytes = g.w2_bytes + g.wf_bytes;
+    g.layer_bytes = g.w2_bytes + g.w3_bytes + g.wf_bytes;
     g.off_act = 0;
     g.off_w2 = (uint32_t)NKG * g.npos * 16;
-    g.off_wf = g.off_w2 + g.w2_bytes;
+    g.off_w3 = g.off_w2 + g.w2_bytes;
+    g.off_wf = g.off_w3 + g.w3_bytes;
     g.off_x = g.off_wf + 2 * g.wf_bytes;
     g.off_red = g.off_x + (uint32_t)((g.V * 4 + 15) & ~15);
     g.off_bar = g.off_red + 32 * 8;
-    g.smem_need = g.off_bar + (2 * kTcMaxBuf + 4) * 8 + 16;
+    g.smem_need = g.off_bar + (4 * kTcMaxBuf + 5) * 8 + 16;
     return g.smem_need <= (uint32_t)kSmemPerCTA;
 }
 
@@ -637,14 +709,15 @@ gf_status launch_tc(TcArgs& a, cudaStream_t stream) {
         per_sm < 1)
         return GF_ECUDA;
     // TMEM: CTAs resident on one SM share its 512 columns; keep at least
-    // r_lag + 2 accumulators per CTA, and pad shared memory so that no more
-    // CTAs than planned share an SM
-    const auto cols_for = [](int k) { int c = 256; while (c * k > 512) c >>= 1; return c; };
+    // r_lag + 2 conv2 accumulators per CTA, and pad shared memory so that no
+    // more CTAs than planned share an SM
+    const auto cols_for = [](int k) { int c = 512; while (c * k > 512) c >>= 1; return c; };
     int k = std::min(per_sm, 16);
     while (k > 1 && cols_for(k) / CP < g.r_lag + 2) --k;
     g.tmem_cols = cols_for(k);
-    g.nbuf = std::min(kTcMaxBuf, g.tmem_cols / CP);
-    if (g.nbuf < g.r_lag + 2) return GF_EUNSUPPORTED;
+    g.nbuf2 = std::min(kTcMaxBuf, g.tmem_cols / CP);
+    g.nbuf3 = std::min(kTcMaxBuf, g.tmem_cols / 16);
+    if (g.nbuf2 < g.r_lag + 2 || g.nbuf3 < 2) return GF_EUNSUPPORTED;
     size_t smem = g.smem_need;
     if (k < per_sm) smem = std::max<size_t>(smem, (size_t)(kSmemPerSM / (k + 1) - kSmemReserve + 128));
     smem = (smem + 127) & ~size_t(127);
@@ -679,7 +752,7 @@ gf_status tc_configure(gf_flow* f) {
 gf_status repack_tc(gf_flow* f, cudaStream_t stream) {
     TcGeom g;
     if (!tc_plan(f->shape, g)) return GF_EUNSUPPORTED;
-    const int64_t total = (int64_t)(g.w2_bytes / 2 + g.wf_bytes / 4) * f->shape.n_layers;
+    const int64_t total = (int64_t)(g.w2_bytes / 2 + g.w3_bytes / 2 + g.wf_bytes / 4) * f->shape.n_layers;
     if (total == 0) return GF_OK;
     const int grid = (int)std::min<int64_t>((total + 255) / 256, 4096);
     repack_tc_kernel<<<grid, 256, 0, stream>>>(f->d_canon, f->canon_stride, f->shape.n_layers, g,

@@ -89,10 +89,10 @@ def drift(n_layers: int, B: int, seed: int = SEED, counter0: int = 0, nthreads=N
 
 
 # The tensor-core kernel for the other lattice shapes (2D L = 8..64, 3D L = 8,
-# 12; hidden 16, 24 or 32) rounds h1, W2 and h2 to bf16 and keeps conv1 and
-# conv3 in FP32; its bounds take the maximum drift over these shapes (serving
-# flows have 12 to 24 coupling layers).
-TC_MODE = oracle.BF16_H1 | oracle.BF16_W2 | oracle.BF16_H2 | oracle.F32_IO
+# 12; hidden 16, 24 or 32) rounds h1 and W2 to bf16 and h2 and W3 to FP16 and
+# keeps conv1 in FP32; its bounds take the maximum drift over these shapes
+# (serving flows have 12 to 24 coupling layers).
+TC_MODE = oracle.BF16_H1 | oracle.BF16_W2 | oracle.F16_H2 | oracle.F16_W3 | oracle.F32_IO
 TC_SHAPES = ((2, 16, 24), (2, 32, 32), (2, 64, 16), (3, 8, 32), (3, 12, 16))
 TC_LAYERS = (2, 8, 24)
 TC_OUT = os.path.join(HERE, "tc_tolerance.json")
@@ -128,7 +128,7 @@ def drift_tc(n_layers: int, B: int, seed: int = SEED, nthreads=None) -> dict:
 def main_tc():
     res = {"what": "parity tolerances of the tensor-core kernel for the lattice shapes other than "
                    "3D L=16 C=32, per coupling-layer count (FP32-accumulating model vs the FP64-summing "
-                   "emulation of its rounding points: h1, W2, h2 in bf16)",
+                   "emulation of its rounding points: h1, W2 in bf16, h2, W3 in fp16)",
            "mode": TC_MODE, "margin": MARGIN, "shapes": [list(s) for s in TC_SHAPES],
            "theory": "m2=-4, lam=6, weights seed 0", "prior_seed": SEED,
            "command": "python tests/golden/bf16_tolerance.py --tc", "by_layers": {}}

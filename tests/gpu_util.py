@@ -17,10 +17,11 @@ LOGW_RTOL = 1e-4
 # margin, per number of coupling layers.
 BF16_MODE = 1 | 2 | 2048 | 4096 | 1024 | 32 | 512
 _BF16_TOL = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "bf16_tolerance.json")
-# The tensor-core kernel for the other lattice shapes rounds h1, W2 and h2 to
-# bf16 (conv1 and conv3 stay FP32); its bounds come from the same experiment
-# over 2D and 3D shapes of the serving mix (tests/golden/tc_tolerance.json).
-TC_MODE = 1 | 2 | 4 | 32
+# The tensor-core kernel for the other lattice shapes rounds h1 and W2 to bf16
+# and h2 and W3 to FP16 (conv1 stays FP32); its bounds come from the same
+# experiment over 2D and 3D shapes of the serving mix
+# (tests/golden/tc_tolerance.json).
+TC_MODE = 1 | 2 | 2048 | 4096 | 32
 _TC_TOL = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "tc_tolerance.json")
 
 

@@ -4,13 +4,15 @@ Requests of different lattice sizes, dimensions and couplings are admitted as
 slots and HBM budget free up; their chunks overlap on the GPU on separate
 streams.  Every request's phi, log q, S, log w, chain indices, accept flags and
 final chain state must be bit-identical to the same request served alone, and
-one request is checked against the FP64 oracle.
+one FP32 request is checked against the FP64 oracle and one request on the
+2D tensor-core kernel against the oracle's emulation of its rounding points.
 """
 import numpy as np
 import pytest
 
 import gf_inputs as gi
-from gpu_util import assert_logw_close, assert_sites_close, require_gpu
+from gpu_util import (LOGW_RTOL, SITE_RTOL, TC_MODE, assert_logw_close, assert_sites_close, require_gpu,
+                      tc_tolerances)
 
 pytestmark = pytest.mark.gpu
 
@@ -21,7 +23,9 @@ def _models(P):
     from paper_2208_08903_gb300 import serving
     models = {}
     for name, shape, s in specs:
-        prec = "bf16" if (shape.nd == 3 and shape.L == 16 and shape.c1 == 32) else "fp32"
+        # the tensor-core kernels where the hidden width allows (b, c: gf_flow_tc.cu;
+        # d: the 3D L=16 kernel), FP32 for width 8 (a)
+        prec = "bf16" if P.tensor_core_supported(shape) else "fp32"
         models[name] = serving.Model(name, shape, P.Flow(shape, gi.init_weights(shape, seed=s), precision=prec))
     return models, {n: (sh, s) for n, sh, s in specs}
 
@@ -47,13 +51,19 @@ def test_results_same_alone_and_in_mix(orc):
         a, m = alone[r.rid], mix[r.rid]
         for k in ("phi", "logq", "S", "logw", "chain_idx", "accepted", "mh_state"):
             assert torch.equal(getattr(a, k), getattr(m, k)), (r.rid, k)
-    # one request against the oracle
-    r = reqs[2]
-    shape, s = specs[r.model]
-    w = gi.init_weights(shape, seed=s)
-    ref = orc.flow_sample(shape, w, r.m2, r.lam, r.batch, seed=r.seed, counter0=0)
-    assert_sites_close(mix[r.rid].phi.cpu().numpy(), ref["phi"])
-    assert_logw_close(mix[r.rid].logw.cpu().numpy(), ref["logw"])
+    # an FP32 request against the oracle, a tensor-core 2D request against its emulation
+    assert models["c"].flow.precision == "bf16" and models["a"].flow.precision == "fp32"
+    for r in (reqs[0], reqs[2]):
+        shape, s = specs[r.model]
+        w = gi.init_weights(shape, seed=s)
+        if r.model == "c":
+            rtol, lw_rtol = tc_tolerances(shape.n_layers)
+            ref = orc.flow_sample(shape, w, r.m2, r.lam, r.batch, seed=r.seed, counter0=0, bf16_mask=TC_MODE)
+        else:
+            rtol, lw_rtol = SITE_RTOL, LOGW_RTOL
+            ref = orc.flow_sample(shape, w, r.m2, r.lam, r.batch, seed=r.seed, counter0=0)
+        assert_sites_close(mix[r.rid].phi.cpu().numpy(), ref["phi"], rtol=rtol)
+        assert_logw_close(mix[r.rid].logw.cpu().numpy(), ref["logw"], rtol=lw_rtol)
     assert P.device_status() == 0
 
 
