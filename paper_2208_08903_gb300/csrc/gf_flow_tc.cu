@@ -153,17 +153,18 @@ __device__ __forceinline__ uint4 pack_f16x8(const float* v) {
     return *reinterpret_cast<const uint4*>(p);
 }
 
-// Padded coordinates (px, py, pz) of position p; pz = 1 in 2D.
+// Padded coordinates (px, py, pz) of position p (row stride P, plane stride
+// PP); pz = 1 in 2D.
 template <int ND>
-__device__ __forceinline__ void pos_xyz(const TcGeom& g, int p, int& px, int& py, int& pz) {
+__device__ __forceinline__ void pos_xyz(int p, int P, int PP, FastDiv fdP, FastDiv fdPP, int& px, int& py, int& pz) {
     int rem = p;
     pz = 1;
     if (ND == 3) {
-        pz = fdiv(p, g.fd_PP);
-        rem = p - pz * g.P * g.P;
+        pz = fdiv(p, fdPP);
+        rem = p - pz * PP;
     }
-    py = fdiv(rem, g.fd_P);
-    px = rem - py * g.P;
+    py = fdiv(rem, fdP);
+    px = rem - py * P;
 }
 
 // conv1: h1 = LReLU(W1 * (x at the frozen sites) + b1) for every site and
@@ -251,7 +252,7 @@ __device__ void tc_halo(const TcGeom& g, unsigned char* act) {
     const int L = g.L, P = g.P, npos = g.npos;
     for (int p = threadIdx.x; p < g.npad; p += blockDim.x) {
         int px, py, pz;
-        pos_xyz<ND>(g, p, px, py, pz);
+        pos_xyz<ND>(p, P, P * P, g.fd_P, g.fd_PP, px, py, pz);
         if (px >= 1 && px <= L && py >= 1 && py <= L && pz >= 1 && pz <= L) continue;
         const int sx = px == 0 ? L : (px == L + 1 ? 1 : px);
         const int sy = py == 0 ? L : (py == L + 1 ? 1 : py);
@@ -264,23 +265,28 @@ __device__ void tc_halo(const TcGeom& g, unsigned char* act) {
     }
 }
 
-// One issuing thread: a convolution's tile t as an implicit GEMM, all taps
-// and K-steps of 16 channels, into TMEM columns d, completion on `full`.
-// a0 / b0: descriptors of the activations and of tap 0, K-step 0 of the
-// weights; b_tap, b_ks: the weights' descriptor steps (16-byte units).
+// One issuing thread: a convolution's tile as an implicit GEMM, all taps and
+// K-steps of 16 channels, into TMEM columns d, completion on `full`.  a0 / b0:
+// descriptors of the activations and of tap 0, K-step 0 of the weights; row:
+// the tile's first position; P, PP: the padded row and plane strides; a_ks,
+// b_tap, b_ks: descriptor steps (16-byte units).  Everything arrives by value
+// (registers): the issuing thread is latency-bound, and values read from the
+// kernel's parameters would be read again after every tcgen05 statement.
 template <int ND, int CP>
-__device__ __forceinline__ void issue_tile(const TcGeom& g, int t, uint32_t d, uint64_t a0, uint64_t b0,
-                                           uint32_t b_tap, uint32_t b_ks, uint32_t idesc, uint64_t* full) {
-    int tap = 0;
-    for (int dz = 0; dz < (ND == 3 ? 3 : 1); ++dz) {
-        for (int dy = 0; dy < 3; ++dy) {
-            const int row0 = g.p_first + kTcM * t + (dy - 1) * g.P + (ND == 3 ? (dz - 1) * g.P * g.P : 0);
+__device__ __forceinline__ void issue_tile(int row, int P, int PP, uint32_t d, uint64_t a0, uint64_t b0,
+                                           uint32_t a_ks, uint32_t b_tap, uint32_t b_ks, uint32_t idesc,
+                                           uint64_t* full) {
 #pragma unroll
-            for (int dx = 0; dx < 3; ++dx, ++tap) {
-                const uint32_t aoff = (uint32_t)(row0 + dx - 1);   // positions = 16-byte units
+    for (int dz = 0; dz < (ND == 3 ? 3 : 1); ++dz) {
+#pragma unroll
+        for (int dy = 0; dy < 3; ++dy) {
+            const uint64_t arow = desc_add(a0, (uint32_t)(row + (dy - 1) * P + (ND == 3 ? (dz - 1) * PP : 0)));
+#pragma unroll
+            for (int dx = 0; dx < 3; ++dx) {
+                const int tap = (ND == 3 ? dz * 9 : 0) + dy * 3 + dx;
 #pragma unroll
                 for (int ks = 0; ks < CP / 16; ++ks) {
-                    const uint64_t ad = desc_add(a0, aoff + (uint32_t)(2 * ks * g.npos));
+                    const uint64_t ad = desc_add(arow, (uint32_t)(dx - 1) + (uint32_t)ks * a_ks);
                     const uint64_t bd = desc_add(b0, (uint32_t)tap * b_tap + (uint32_t)ks * b_ks);
                     mma_bf16(d, ad, bd, idesc, (tap | ks) ? 1u : 0u);
                 }
@@ -291,7 +297,7 @@ __device__ __forceinline__ void issue_tile(const TcGeom& g, int t, uint32_t d, u
 }
 
 template <int ND, int CP, bool INVERSE>
-__global__ void __launch_bounds__(kTcThreads) flow_tc_kernel(const TcArgs a) {
+__global__ void __launch_bounds__(kTcThreads, ND == 3 ? 1 : 2) flow_tc_kernel(const TcArgs a) {
     constexpr int NKG = CP / 8;
     extern __shared__ __align__(1024) unsigned char smem[];
     const TcGeom& g = a.g;
@@ -313,7 +319,12 @@ __global__ void __launch_bounds__(kTcThreads) flow_tc_kernel(const TcArgs a) {
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int V = g.V, L = g.L, npos = g.npos, nt = g.n_tiles;
+    // geometry in registers (the tcgen05 statements' memory clobbers would
+    // otherwise make every use read the kernel parameters again)
+    const int V = g.V, L = g.L, npos = g.npos, nt = g.n_tiles, P = g.P, PP = g.P * g.P, p_first = g.p_first;
+    const int nbuf2 = g.nbuf2, nbuf3 = g.nbuf3, r_lag = g.r_lag;
+    const FastDiv fdP = g.fd_P, fdPP = g.fd_PP;
+    const uint32_t a_ks = 2u * (uint32_t)npos;
     const int wf_floats = (int)(g.wf_bytes >> 2);
     const int64_t n_cfg = a.B > (int64_t)blockIdx.x ? (a.B - 1 - (int64_t)blockIdx.x) / gridDim.x + 1 : 0;
     const int64_t total_steps = n_cfg * a.n_layers;   // this CTA's layer applications
@@ -431,14 +442,14 @@ __global__ void __launch_bounds__(kTcThreads) flow_tc_kernel(const TcArgs a) {
             // ---- conv2 on the tensor cores; the epilogue writes h2 (FP16) over h1 in place
             if (tid == 0) {
                 if (tc_wait(bar_w2, step, abort_flag, a.status)) {
+                    int buf = (int)(seq2 % nbuf2);
+                    int64_t k = seq2 / nbuf2;
                     for (int t = 0; t < nt; ++t) {
-                        const int64_t s = seq2 + t;
-                        const int buf = (int)(s % g.nbuf2);
-                        const int64_t k = s / g.nbuf2;
                         if (k >= 1 && !tc_wait(empty2 + buf, k - 1, abort_flag, a.status)) break;
                         fence_after_sync();
-                        issue_tile<ND, CP>(g, t, tmem + (uint32_t)(buf * CP), a0, b2d, (uint32_t)(NKG * CP),
-                                           (uint32_t)(2 * CP), idesc2, full2 + buf);
+                        issue_tile<ND, CP>(p_first + kTcM * t, P, PP, tmem + (uint32_t)(buf * CP), a0, b2d, a_ks,
+                                           (uint32_t)(NKG * CP), (uint32_t)(2 * CP), idesc2, full2 + buf);
+                        if (++buf == nbuf2) { buf = 0; ++k; }
                     }
                 }
             } else if (eg >= 0) {
@@ -447,14 +458,14 @@ __global__ void __launch_bounds__(kTcThreads) flow_tc_kernel(const TcArgs a) {
                 bool ok = true;
                 for (int t = eg; t < nt && ok; t += 2) {
                     // h2 of tile t may overwrite h1 once tiles t .. t + r_lag are done
-                    const int64_t need = seq2 + (t + g.r_lag < nt ? t + g.r_lag : nt - 1);
+                    const int64_t need = seq2 + (t + r_lag < nt ? t + r_lag : nt - 1);
                     while (ok && waited <= need) {
-                        ok = tc_wait(full2 + (int)(waited % g.nbuf2), waited / g.nbuf2, abort_flag, a.status);
+                        ok = tc_wait(full2 + (int)(waited % nbuf2), waited / nbuf2, abort_flag, a.status);
                         ++waited;
                     }
                     if (!ok) break;
                     fence_after_sync();
-                    const int buf = (int)((seq2 + t) % g.nbuf2);
+                    const int buf = (int)((seq2 + t) % nbuf2);
                     const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * CP);
                     float v[CP];
                     {
@@ -471,9 +482,9 @@ __global__ void __launch_bounds__(kTcThreads) flow_tc_kernel(const TcArgs a) {
                     }
                     fence_before_sync();
                     mbar_arrive(empty2 + buf);
-                    const int p = g.p_first + kTcM * t + 32 * q + lane;
+                    const int p = p_first + kTcM * t + 32 * q + lane;
                     int px, py, pz;
-                    pos_xyz<ND>(g, p, px, py, pz);
+                    pos_xyz<ND>(p, P, PP, fdP, fdPP, px, py, pz);
                     if (px >= 1 && px <= L && py >= 1 && py <= L && pz >= 1 && pz <= L) {
 #pragma unroll
                         for (int kg = 0; kg < NKG; ++kg) {
@@ -501,14 +512,14 @@ __global__ void __launch_bounds__(kTcThreads) flow_tc_kernel(const TcArgs a) {
             // ---- conv3 (s, t) on the tensor cores; the epilogue updates the other parity
             if (tid == 0) {
                 if (tc_wait(bar_w3, step, abort_flag, a.status)) {
+                    int buf = (int)(seq3 % nbuf3);
+                    int64_t k = seq3 / nbuf3;
                     for (int t = 0; t < nt; ++t) {
-                        const int64_t s = seq3 + t;
-                        const int buf = (int)(s % g.nbuf3);
-                        const int64_t k = s / g.nbuf3;
                         if (k >= 1 && !tc_wait(empty3 + buf, k - 1, abort_flag, a.status)) break;
                         fence_after_sync();
-                        issue_tile<ND, CP>(g, t, tmem + (uint32_t)(buf * 16), a0, b3d, (uint32_t)(NKG * 16),
-                                           (uint32_t)(2 * 16), idesc3, full3 + buf);
+                        issue_tile<ND, CP>(p_first + kTcM * t, P, PP, tmem + (uint32_t)(buf * 16), a0, b3d, a_ks,
+                                           (uint32_t)(NKG * 16), (uint32_t)(2 * 16), idesc3, full3 + buf);
+                        if (++buf == nbuf3) { buf = 0; ++k; }
                     }
                 }
             } else if (eg >= 0) {
@@ -518,20 +529,20 @@ __global__ void __launch_bounds__(kTcThreads) flow_tc_kernel(const TcArgs a) {
                 bool ok = true;
                 for (int t = eg; t < nt && ok; t += 2) {
                     while (ok && waited <= seq3 + t) {
-                        ok = tc_wait(full3 + (int)(waited % g.nbuf3), waited / g.nbuf3, abort_flag, a.status);
+                        ok = tc_wait(full3 + (int)(waited % nbuf3), waited / nbuf3, abort_flag, a.status);
                         ++waited;
                     }
                     if (!ok) break;
                     fence_after_sync();
-                    const int buf = (int)((seq3 + t) % g.nbuf3);
+                    const int buf = (int)((seq3 + t) % nbuf3);
                     float st[2];
                     tmem_ld2(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 16), st);
                     tmem_ld_wait();
                     fence_before_sync();
                     mbar_arrive(empty3 + buf);
-                    const int p = g.p_first + kTcM * t + 32 * q + lane;
+                    const int p = p_first + kTcM * t + 32 * q + lane;
                     int px, py, pz;
-                    pos_xyz<ND>(g, p, px, py, pz);
+                    pos_xyz<ND>(p, P, PP, fdP, fdPP, px, py, pz);
                     // parity of the site (px - 1, py - 1, pz - 1)
                     const int par = ND == 3 ? ((px + py + pz + 1) & 1) : ((px + py) & 1);
                     if (px >= 1 && px <= L && py >= 1 && py <= L && pz >= 1 && pz <= L && par == pa) {
