@@ -23,22 +23,29 @@
 // channel-group major [Cp/8][position][8 channels] so that 8 consecutive
 // positions of one channel group are one 128-byte core matrix of the
 // K-major canonical layout.  A convolution is then an implicit GEMM whose A
-// operand for tap (dz,dy,dx) is the same array started (dx-1) + (dy-1) P +
-// (dz-1) P^2 positions later: M = 128 consecutive padded positions per tile
-// (rows on halo positions are computed and dropped), K = 3^d taps x Cp
-// channels in steps of 16; N = Cp output channels for conv2, N = 16 for the
-// head (rows s and t, the rest zero).  Per layer, with a CTA barrier between
+// operand for taps (dz,dy,*) is the same array started (dy-1) P + (dz-1) P^2
+// positions later, K = the 3^(d-1) (dz,dy) pairs x Cp channels in steps of
+// 16, and whose three x-taps are stacked along N (conv2: N = 3 Cp; head:
+// N = 16, columns 2 dx + (s, t)): each row's column block dx is the partial
+// sum of tap dx at the row's own position, and the epilogue adds block 0 of
+// the row to the left, block 1 and block 2 of the row to the right.  The 128
+// rows of a tile are 16 core matrices of 8 consecutive positions, each 6
+// positions after the previous one, so rows 1..6 of every 8 are outputs (96
+// per tile, positions on the halo dropped) whose x-neighbours are in the same
+// 8 TMEM lanes (width-8 shuffles).  Per layer, with a CTA barrier between
 // the phases:
 //   conv1 (all warps): h1 = LReLU(W1 * masked x + b1) at every site, BF16, at
 //     its padded position and at its periodic images;
-//   conv2 (one issuing thread): the tiles in order into a ring of TMEM
-//     accumulators; two groups of four epilogue warps (one warp per TMEM lane
-//     quarter) take alternate tiles and turn them into h2 = LReLU(acc + b2) in
-//     FP16, written over h1 in place once every tile that reads those
-//     positions (up to ceil(p0 / 128) tiles on, p0 = 1 + P (+ P^2) the largest
-//     tap offset) has completed;
+//   conv2 (two issuing threads on different sub-partitions, alternate tiles):
+//     two groups of four epilogue warps (one warp per TMEM lane quarter) take
+//     the same alternate tiles, each through its own ring of TMEM
+//     accumulators, and turn them into
+//     h2 = LReLU(acc + b2) in FP16, released from TMEM at once and written
+//     over h1 in place once every tile that reads those positions (up to
+//     ceil(p0 / 96) tiles on, p0 = 1 + P (+ P^2) the largest tap offset) has
+//     completed;
 //   halo (all warps): the periodic images of h2;
-//   conv3 (the issuing thread, the epilogue groups): (s, t) for every tile;
+//   conv3 (the issuing threads, the epilogue groups): (s, t) for every tile;
 //     at the updated sites s = tanh(s + b_s), x <- x e^s + t (or the
 //     inverse), log-det += s.
 // Each layer's weights arrive by bulk copies (cp.async.bulk): W2 for the next
@@ -61,9 +68,11 @@ namespace gf {
 
 namespace {
 
-constexpr int kTcThreads = 384;           // warp 0: MMA issue and TMEM owner; warps 4..11: two epilogue groups
-constexpr int kTcM = 128;                 // positions per tile (TMEM lanes)
-constexpr int kTcMaxBuf = 32;             // TMEM accumulator rings: at most 512 / 16 buffers
+constexpr int kTcThreads = 384;           // warps 0, 1: MMA issue (warp 0 owns TMEM); warps 4..11: two epilogue groups
+constexpr int kTcM = 128;                 // rows per tile (TMEM lanes)
+constexpr int kTcOut = 96;                // output positions per tile (6 of every 8 rows)
+constexpr int kTcRing = 8;                // TMEM accumulators per epilogue group (at most)
+constexpr int kTcMaxTiles = 64;           // tiles per layer (one completion barrier each)
 constexpr long long kTcWaitLimit = 1ll << 22;
 constexpr int kSmemPerSM = 233472;        // 228 KB of shared memory per SM
 constexpr int kSmemPerCTA = 232448;       // 227 KB opt-in maximum per CTA
@@ -89,11 +98,11 @@ __device__ __forceinline__ int fdiv(int n, const FastDiv& f) {
 struct TcGeom {
     int nd, L, V, P, C, Cp, T;
     int p_first;          // padded position of site (0, ..., 0) = 1 + P (+ P^2); also the largest tap offset
-    int n_tiles;          // tiles covering the positions p_first .. L p_first
+    int n_tiles;          // tiles covering the positions p_first .. L p_first, 96 each
     int npos;             // positions held per channel group (multiple of 8)
-    int r_lag;            // tiles after a tile that read its positions: ceil(p_first / 128)
+    int r_lag;            // tiles after a tile that read its outputs' positions: ceil(p_first / 96)
     int npad;             // P^nd: positions of the padded lattice
-    int nbuf2, nbuf3, tmem_cols;   // TMEM accumulator rings of conv2 (Cp columns) and conv3 (16); set at launch
+    int nbuf2, nbuf3, tmem_cols;   // TMEM accumulators per epilogue group: conv2 (3 Cp columns), conv3 (16); set at launch
     FastDiv fd_half, fd_Lh, fd_L, fd_P, fd_PP;
     uint32_t w2_bytes, w3_bytes, wf_bytes, layer_bytes;   // layer block: W2 | W3 | FP32 part
     int wf_W1, wf_b1, wf_b2, wf_b3;                        // float offsets in the FP32 part
@@ -265,35 +274,35 @@ __device__ void tc_halo(const TcGeom& g, unsigned char* act) {
     }
 }
 
-// One issuing thread: a convolution's tile as an implicit GEMM, all taps and
-// K-steps of 16 channels, into TMEM columns d, completion on `full`.  a0 / b0:
-// descriptors of the activations and of tap 0, K-step 0 of the weights; row:
-// the tile's first position; P, PP: the padded row and plane strides; a_ks,
-// b_tap, b_ks: descriptor steps (16-byte units).  Everything arrives by value
-// (registers): the issuing thread is latency-bound, and values read from the
-// kernel's parameters would be read again after every tcgen05 statement.
+// One issuing thread: a convolution's tile as an implicit GEMM with the three
+// x-taps stacked along N: for each (dz, dy) and K-step of 16 channels one MMA
+// whose column block dx holds the partial sum of tap (dz, dy, dx) at the row's
+// own position; the epilogue adds block dx of the row one position to the
+// left / right.  Rows: 16 core matrices of 8 positions, each 6 positions after
+// the previous one (SBO = 96 bytes), so row 8 g + r is position
+// first + 6 g + r and every row with r in 1..6 finds both x-neighbours in its
+// own 8 rows.  a0 / b0: descriptors of the activations and of the weights'
+// first block; P, PP: the padded row and plane strides; a_ks, b_tap, b_ks:
+// descriptor steps (16-byte units).  Everything arrives by value (registers):
+// the issuing thread is latency-bound, and values read from the kernel's
+// parameters would be read again after every tcgen05 statement.
 template <int ND, int CP>
-__device__ __forceinline__ void issue_tile(int row, int P, int PP, uint32_t d, uint64_t a0, uint64_t b0,
-                                           uint32_t a_ks, uint32_t b_tap, uint32_t b_ks, uint32_t idesc,
-                                           uint64_t* full) {
+__device__ __forceinline__ void issue_tile(int first, int P, int PP, uint32_t d, uint64_t a0, uint64_t b0,
+                                           uint32_t a_ks, uint32_t b_tap, uint32_t b_ks, uint32_t idesc) {
 #pragma unroll
     for (int dz = 0; dz < (ND == 3 ? 3 : 1); ++dz) {
 #pragma unroll
         for (int dy = 0; dy < 3; ++dy) {
-            const uint64_t arow = desc_add(a0, (uint32_t)(row + (dy - 1) * P + (ND == 3 ? (dz - 1) * PP : 0)));
+            const int tp = (ND == 3 ? dz * 3 : 0) + dy;
+            const uint64_t arow = desc_add(a0, (uint32_t)(first + (dy - 1) * P + (ND == 3 ? (dz - 1) * PP : 0)));
 #pragma unroll
-            for (int dx = 0; dx < 3; ++dx) {
-                const int tap = (ND == 3 ? dz * 9 : 0) + dy * 3 + dx;
-#pragma unroll
-                for (int ks = 0; ks < CP / 16; ++ks) {
-                    const uint64_t ad = desc_add(arow, (uint32_t)(dx - 1) + (uint32_t)ks * a_ks);
-                    const uint64_t bd = desc_add(b0, (uint32_t)tap * b_tap + (uint32_t)ks * b_ks);
-                    mma_bf16(d, ad, bd, idesc, (tap | ks) ? 1u : 0u);
-                }
+            for (int ks = 0; ks < CP / 16; ++ks) {
+                const uint64_t ad = desc_add(arow, (uint32_t)ks * a_ks);
+                const uint64_t bd = desc_add(b0, (uint32_t)tp * b_tap + (uint32_t)ks * b_ks);
+                mma_bf16(d, ad, bd, idesc, (tp | ks) ? 1u : 0u);
             }
         }
     }
-    mma_commit(full);
 }
 
 template <int ND, int CP, bool INVERSE>
@@ -307,11 +316,14 @@ __global__ void __launch_bounds__(kTcThreads, ND == 3 ? 1 : 2) flow_tc_kernel(co
     float* wfs = reinterpret_cast<float*>(smem + g.off_wf);
     float* x = reinterpret_cast<float*>(smem + g.off_x);
     FF* red = reinterpret_cast<FF*>(smem + g.off_red);
-    uint64_t* full2 = reinterpret_cast<uint64_t*>(smem + g.off_bar);   // conv2 tile's MMAs done (commit)
-    uint64_t* empty2 = full2 + kTcMaxBuf;                                // its accumulator drained (128)
-    uint64_t* full3 = empty2 + kTcMaxBuf;                                // conv3 tile's MMAs done
-    uint64_t* empty3 = full3 + kTcMaxBuf;                                // its accumulator drained
-    uint64_t* bar_w2 = empty3 + kTcMaxBuf;                               // a layer's W2 staged
+    // TMEM accumulator rings, one per epilogue group: full = the tile's MMAs
+    // done (commit), empty = its accumulator drained (the group's 128 threads)
+    uint64_t* full2 = reinterpret_cast<uint64_t*>(smem + g.off_bar);   // [2][kTcRing]
+    uint64_t* empty2 = full2 + 2 * kTcRing;
+    uint64_t* full3 = empty2 + 2 * kTcRing;
+    uint64_t* empty3 = full3 + 2 * kTcRing;
+    uint64_t* done2 = empty3 + 2 * kTcRing;                              // [kTcMaxTiles]: conv2 tile done, once a layer
+    uint64_t* bar_w2 = done2 + kTcMaxTiles;                              // a layer's W2 staged
     uint64_t* bar_w3 = bar_w2 + 1;                                       // a layer's W3 staged
     uint64_t* bar_wf = bar_w3 + 1;                                       // 2: a layer's FP32 part staged
     uint64_t* bar_fin = bar_wf + 2;                                      // every queued MMA done (exit)
@@ -322,7 +334,7 @@ __global__ void __launch_bounds__(kTcThreads, ND == 3 ? 1 : 2) flow_tc_kernel(co
     // geometry in registers (the tcgen05 statements' memory clobbers would
     // otherwise make every use read the kernel parameters again)
     const int V = g.V, L = g.L, npos = g.npos, nt = g.n_tiles, P = g.P, PP = g.P * g.P, p_first = g.p_first;
-    const int nbuf2 = g.nbuf2, nbuf3 = g.nbuf3, r_lag = g.r_lag;
+    const int nb2 = g.nbuf2, nb3 = g.nbuf3, r_lag = g.r_lag;
     const FastDiv fdP = g.fd_P, fdPP = g.fd_PP;
     const uint32_t a_ks = 2u * (uint32_t)npos;
     const int wf_floats = (int)(g.wf_bytes >> 2);
@@ -330,7 +342,7 @@ __global__ void __launch_bounds__(kTcThreads, ND == 3 ? 1 : 2) flow_tc_kernel(co
     const int64_t total_steps = n_cfg * a.n_layers;   // this CTA's layer applications
     int64_t w2_issued = -1, w3_issued = -1, wf_issued = -1;   // thread 0: the last staged steps
     // epilogue warps: group eg (0: warps 4..7, 1: warps 8..11) takes the tiles
-    // t = eg (mod 2); warp w reads TMEM lane quarter q = w mod 4
+    // t = eg (mod 2) through its own TMEM ring; warp w reads lane quarter w mod 4
     const int eg = warp >= 4 ? (warp - 4) >> 2 : -1, q = warp & 3;
 
     const auto block_of = [&](int64_t step) {
@@ -354,17 +366,18 @@ __global__ void __launch_bounds__(kTcThreads, ND == 3 ? 1 : 2) flow_tc_kernel(co
         tmem_relinquish();
     }
     if (tid == 0) {
-        for (int i = 0; i < kTcMaxBuf; ++i) {
+        for (int i = 0; i < 2 * kTcRing; ++i) {
             mbar_init(full2 + i, 1);
             mbar_init(empty2 + i, 4 * 32);
             mbar_init(full3 + i, 1);
             mbar_init(empty3 + i, 4 * 32);
         }
+        for (int i = 0; i < kTcMaxTiles; ++i) mbar_init(done2 + i, 1);
         mbar_init(bar_w2, 1);
         mbar_init(bar_w3, 1);
         mbar_init(bar_wf, 1);
         mbar_init(bar_wf + 1, 1);
-        mbar_init(bar_fin, 1);
+        mbar_init(bar_fin, 2);                 // one commit per issuing thread
         *abort_flag = 0;
         fence_mbar_init();
     }
@@ -382,15 +395,23 @@ __global__ void __launch_bounds__(kTcThreads, ND == 3 ? 1 : 2) flow_tc_kernel(co
         stage_wf(0);
     }
     const uint32_t tmem = *tmem_slot;
-    // D = F32, K-major A and B, M = 128: conv2 BF16 with N = CP, conv3 FP16 with N = 16
-    const uint32_t idesc2 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(CP >> 3) << 17) |
+    // D = F32, K-major A and B, M = 128: conv2 BF16 with N = 3 CP, conv3 FP16 with N = 16
+    const uint32_t idesc2 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(3 * CP >> 3) << 17) |
                             ((uint32_t)(kTcM >> 4) << 24);
     const uint32_t idesc3 = (1u << 4) | ((16u >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
-    const uint64_t a0 = smem_desc(smem_u32(act), (uint32_t)npos * 16u, 128u);
-    const uint64_t b2d = smem_desc(smem_u32(w2s), (uint32_t)CP * 16u, 128u);   // [tap][kg][n < CP][8] bf16
-    const uint64_t b3d = smem_desc(smem_u32(w3s), 16u * 16u, 128u);           // [tap][kg][n < 16][8] fp16
+    const uint64_t a0 = smem_desc(smem_u32(act), (uint32_t)npos * 16u, 6u * 16u);
+    const uint64_t b2d = smem_desc(smem_u32(w2s), 3u * CP * 16u, 128u);   // [tp][kg][dx CP + c][8] bf16
+    const uint64_t b3d = smem_desc(smem_u32(w3s), 16u * 16u, 128u);       // [tp][kg][2 dx + j][8] fp16
+    // this thread's row of a tile: position first + 6 (row >> 3) + (row & 7),
+    // an output when row & 7 is in 1..6
+    const int row = 32 * q + lane, roff = 6 * (row >> 3) + (row & 7);
+    const bool rvalid = (row & 7) >= 1 && (row & 7) <= 6;
 
-    int64_t step = 0, seq2 = 0, seq3 = 0;   // layer steps and tiles of each convolution so far
+    int64_t step = 0;
+    // the next accumulator of this thread's ring (issuing thread r: ring r;
+    // epilogue group g: ring g) and how often it has been filled before
+    int i2 = 0, i3 = 0;
+    int64_t k2 = 0, k3 = 0;
     for (int64_t b = blockIdx.x; b < a.B; b += gridDim.x) {
         // prior sample (sampling) or the given field (inverting)
         FF sumz2{0.f, 0.f};
@@ -440,63 +461,65 @@ __global__ void __launch_bounds__(kTcThreads, ND == 3 ? 1 : 2) flow_tc_kernel(co
             if (*abort_flag) break;
 
             // ---- conv2 on the tensor cores; the epilogue writes h2 (FP16) over h1 in place
-            if (tid == 0) {
-                if (tc_wait(bar_w2, step, abort_flag, a.status)) {
-                    int buf = (int)(seq2 % nbuf2);
-                    int64_t k = seq2 / nbuf2;
-                    for (int t = 0; t < nt; ++t) {
-                        if (k >= 1 && !tc_wait(empty2 + buf, k - 1, abort_flag, a.status)) break;
+            if (warp < 2) {
+                // issuing thread r (lane 0 of warp r, sub-partition r): tiles t = r (mod 2) into ring r
+                if (lane == 0 && tc_wait(bar_w2, step, abort_flag, a.status)) {
+                    for (int t = warp; t < nt; t += 2) {
+                        if (k2 >= 1 && !tc_wait(empty2 + warp * kTcRing + i2, k2 - 1, abort_flag, a.status)) break;
                         fence_after_sync();
-                        issue_tile<ND, CP>(p_first + kTcM * t, P, PP, tmem + (uint32_t)(buf * CP), a0, b2d, a_ks,
-                                           (uint32_t)(NKG * CP), (uint32_t)(2 * CP), idesc2, full2 + buf);
-                        if (++buf == nbuf2) { buf = 0; ++k; }
+                        issue_tile<ND, CP>(p_first - 1 + kTcOut * t, P, PP,
+                                           tmem + (uint32_t)((warp * nb2 + i2) * 3 * CP), a0, b2d, a_ks,
+                                           (uint32_t)(NKG * 3 * CP), (uint32_t)(2 * 3 * CP), idesc2);
+                        mma_commit(full2 + warp * kTcRing + i2);
+                        mma_commit(done2 + t);
+                        if (++i2 == nb2) { i2 = 0; ++k2; }
                     }
                 }
+                __syncwarp();
             } else if (eg >= 0) {
                 const float* b2 = wf + g.wf_b2;
-                int64_t waited = seq2;     // completions are awaited in tile order (both groups)
+                int dwaited = 0;           // tiles whose completion this thread has seen (done2)
                 bool ok = true;
                 for (int t = eg; t < nt && ok; t += 2) {
-                    // h2 of tile t may overwrite h1 once tiles t .. t + r_lag are done
-                    const int64_t need = seq2 + (t + r_lag < nt ? t + r_lag : nt - 1);
-                    while (ok && waited <= need) {
-                        ok = tc_wait(full2 + (int)(waited % nbuf2), waited / nbuf2, abort_flag, a.status);
-                        ++waited;
-                    }
-                    if (!ok) break;
+                    if (!(ok = tc_wait(full2 + eg * kTcRing + i2, k2, abort_flag, a.status))) break;
                     fence_after_sync();
-                    const int buf = (int)((seq2 + t) % nbuf2);
-                    const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * CP);
-                    float v[CP];
-                    {
-                        float v16[16];
-                        tmem_ld16(taddr, v16);
+                    // out = D_0(left) + D_1 + D_2(right) + b2, 16 channels at a time, LeakyReLU
+                    const uint32_t tcol = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((eg * nb2 + i2) * 3 * CP);
+                    float out[CP];
 #pragma unroll
-                        for (int c = 0; c < 16; ++c) v[c] = v16[c];
-                        if constexpr (CP == 32) {
-                            tmem_ld16(taddr + 16, v16);
-#pragma unroll
-                            for (int c = 0; c < 16; ++c) v[16 + c] = v16[c];
-                        }
+                    for (int h = 0; h < CP / 16; ++h) {
+                        float v0[16], v1[16], v2[16];
+                        tmem_ld16(tcol + h * 16, v0);
+                        tmem_ld16(tcol + CP + h * 16, v1);
+                        tmem_ld16(tcol + 2 * CP + h * 16, v2);
                         tmem_ld_wait();
+#pragma unroll
+                        for (int c = 0; c < 16; ++c) {
+                            const float left = __shfl_up_sync(0xffffffffu, v0[c], 1, 8);
+                            const float right = __shfl_down_sync(0xffffffffu, v2[c], 1, 8);
+                            out[h * 16 + c] = lrelu_tc(left + v1[c] + right + b2[h * 16 + c], a.slope);
+                        }
                     }
                     fence_before_sync();
-                    mbar_arrive(empty2 + buf);
-                    const int p = p_first + kTcM * t + 32 * q + lane;
+                    mbar_arrive(empty2 + eg * kTcRing + i2);
+                    if (++i2 == nb2) { i2 = 0; ++k2; }
+                    // h2 of tile t may overwrite h1 once tiles t .. t + r_lag are done
+                    const int need = t + r_lag < nt ? t + r_lag : nt - 1;
+                    while (ok && dwaited <= need) {
+                        ok = tc_wait(done2 + dwaited, step, abort_flag, a.status);
+                        ++dwaited;
+                    }
+                    if (!ok) break;
+                    const int p = p_first - 1 + kTcOut * t + roff;
                     int px, py, pz;
                     pos_xyz<ND>(p, P, PP, fdP, fdPP, px, py, pz);
-                    if (px >= 1 && px <= L && py >= 1 && py <= L && pz >= 1 && pz <= L) {
+                    if (rvalid && px >= 1 && px <= L && py >= 1 && py <= L && pz >= 1 && pz <= L) {
 #pragma unroll
-                        for (int kg = 0; kg < NKG; ++kg) {
-                            float h[8];
-#pragma unroll
-                            for (int c = 0; c < 8; ++c) h[c] = lrelu_tc(v[kg * 8 + c] + b2[kg * 8 + c], a.slope);
-                            *reinterpret_cast<uint4*>(act + ((size_t)kg * npos + p) * 16) = pack_f16x8(h);
-                        }
+                        for (int kg = 0; kg < NKG; ++kg)
+                            *reinterpret_cast<uint4*>(act + ((size_t)kg * npos + p) * 16) = pack_f16x8(out + kg * 8);
                     }
                 }
             }
-            seq2 += nt;
             fence_before_sync();
             __syncthreads();
             if (*abort_flag) break;
@@ -510,44 +533,45 @@ __global__ void __launch_bounds__(kTcThreads, ND == 3 ? 1 : 2) flow_tc_kernel(co
             __syncthreads();
 
             // ---- conv3 (s, t) on the tensor cores; the epilogue updates the other parity
-            if (tid == 0) {
-                if (tc_wait(bar_w3, step, abort_flag, a.status)) {
-                    int buf = (int)(seq3 % nbuf3);
-                    int64_t k = seq3 / nbuf3;
-                    for (int t = 0; t < nt; ++t) {
-                        if (k >= 1 && !tc_wait(empty3 + buf, k - 1, abort_flag, a.status)) break;
+            if (warp < 2) {
+                if (lane == 0 && tc_wait(bar_w3, step, abort_flag, a.status)) {
+                    for (int t = warp; t < nt; t += 2) {
+                        if (k3 >= 1 && !tc_wait(empty3 + warp * kTcRing + i3, k3 - 1, abort_flag, a.status)) break;
                         fence_after_sync();
-                        issue_tile<ND, CP>(p_first + kTcM * t, P, PP, tmem + (uint32_t)(buf * 16), a0, b3d, a_ks,
-                                           (uint32_t)(NKG * 16), (uint32_t)(2 * 16), idesc3, full3 + buf);
-                        if (++buf == nbuf3) { buf = 0; ++k; }
+                        issue_tile<ND, CP>(p_first - 1 + kTcOut * t, P, PP, tmem + (uint32_t)((warp * nb3 + i3) * 16),
+                                           a0, b3d, a_ks, (uint32_t)(NKG * 16), (uint32_t)(2 * 16), idesc3);
+                        mma_commit(full3 + warp * kTcRing + i3);
+                        if (++i3 == nb3) { i3 = 0; ++k3; }
                     }
                 }
+                __syncwarp();
             } else if (eg >= 0) {
                 const float bs = wf[g.wf_b3], bt = wf[g.wf_b3 + 1];
                 const int pa = frozen ^ 1;
-                int64_t waited = seq3;
                 bool ok = true;
                 for (int t = eg; t < nt && ok; t += 2) {
-                    while (ok && waited <= seq3 + t) {
-                        ok = tc_wait(full3 + (int)(waited % nbuf3), waited / nbuf3, abort_flag, a.status);
-                        ++waited;
-                    }
-                    if (!ok) break;
+                    if (!(ok = tc_wait(full3 + eg * kTcRing + i3, k3, abort_flag, a.status))) break;
                     fence_after_sync();
-                    const int buf = (int)((seq3 + t) % nbuf3);
-                    float st[2];
-                    tmem_ld2(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 16), st);
+                    float v[8];
+                    tmem_ld8(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((eg * nb3 + i3) * 16), v);
                     tmem_ld_wait();
                     fence_before_sync();
-                    mbar_arrive(empty3 + buf);
-                    const int p = p_first + kTcM * t + 32 * q + lane;
+                    mbar_arrive(empty3 + eg * kTcRing + i3);
+                    if (++i3 == nb3) { i3 = 0; ++k3; }
+                    // columns 2 dx + j: j = 0 s, 1 t of tap dx at the row's own position
+                    const float sl = __shfl_up_sync(0xffffffffu, v[0], 1, 8);
+                    const float tl = __shfl_up_sync(0xffffffffu, v[1], 1, 8);
+                    const float sr = __shfl_down_sync(0xffffffffu, v[4], 1, 8);
+                    const float tr = __shfl_down_sync(0xffffffffu, v[5], 1, 8);
+                    const int p = p_first - 1 + kTcOut * t + roff;
                     int px, py, pz;
                     pos_xyz<ND>(p, P, PP, fdP, fdPP, px, py, pz);
                     // parity of the site (px - 1, py - 1, pz - 1)
                     const int par = ND == 3 ? ((px + py + pz + 1) & 1) : ((px + py) & 1);
-                    if (px >= 1 && px <= L && py >= 1 && py <= L && pz >= 1 && pz <= L && par == pa) {
-                        const float s = a.use_tanh ? tanhf(st[0] + bs) : st[0] + bs;
-                        const float tt = st[1] + bt;
+                    if (rvalid && px >= 1 && px <= L && py >= 1 && py <= L && pz >= 1 && pz <= L && par == pa) {
+                        const float s0 = sl + v[2] + sr + bs;
+                        const float s = a.use_tanh ? tanhf(s0) : s0;
+                        const float tt = tl + v[3] + tr + bt;
                         if (!isfinite(s) || !isfinite(tt)) set_status(a.status, GF_EDEVICE);
                         float& xv = x[((ND == 3 ? (pz - 1) * L : 0) + (py - 1)) * L + (px - 1)];
                         if (!INVERSE) xv = fmaf(xv, expf(s), tt);
@@ -556,7 +580,6 @@ __global__ void __launch_bounds__(kTcThreads, ND == 3 ? 1 : 2) flow_tc_kernel(co
                     }
                 }
             }
-            seq3 += nt;
             fence_before_sync();
             __syncthreads();
             if (*abort_flag) break;
@@ -593,11 +616,11 @@ __global__ void __launch_bounds__(kTcThreads, ND == 3 ? 1 : 2) flow_tc_kernel(co
     }
     // teardown: copies still landing and MMAs still queued (only after an
     // abort) finish before their shared memory and TMEM are released
+    if (warp < 2 && lane == 0) mma_commit(bar_fin);
     if (tid == 0) {
         if (w2_issued >= 0) tc_drain(bar_w2, w2_issued);
         if (w3_issued >= 0) tc_drain(bar_w3, w3_issued);
         if (wf_issued >= 0) tc_drain(bar_wf + (wf_issued & 1), wf_issued >> 1);
-        mma_commit(bar_fin);
         tc_drain(bar_fin, 0);
     }
     fence_before_sync();
@@ -608,13 +631,13 @@ __global__ void __launch_bounds__(kTcThreads, ND == 3 ? 1 : 2) flow_tc_kernel(co
     }
 }
 
-// canonical FP32 -> per-layer block: W2 as [tap][kg][n][8] bf16 (K-major core
-// matrices; rows n >= C and channels >= C zero), W3 as [tap][kg][n][8] fp16
-// with n = 0: s, 1: t, rows 2..15 zero, then FP32 W1 [tap][Cp], b1 [Cp],
-// b2 [Cp], b3 [2], zero padding.
+// canonical FP32 -> per-layer block: W2 as [tp][kg][dx CP + c][8] bf16 (tap
+// (tp, dx) with tp = (dz, dy); K-major core matrices; channels >= C zero), W3
+// as [tp][kg][2 dx + j][8] fp16 (j = 0: s, 1: t; rows 6..15 zero), then FP32
+// W1 [tap][Cp], b1 [Cp], b2 [Cp], b3 [2], zero padding.
 __global__ void repack_tc_kernel(const float* __restrict__ canon, int64_t cstride, int n_layers, TcGeom g,
                                  unsigned char* __restrict__ out) {
-    const int T = g.T, C = g.C, CP = g.Cp, NKG = CP / 8;
+    const int T = g.T, C = g.C, CP = g.Cp, NKG = CP / 8, N2 = 3 * CP;
     const int64_t n2 = g.w2_bytes / 2, n3 = g.w3_bytes / 2, nf = g.wf_bytes / 4, per = n2 + n3 + nf;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < per * n_layers;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -628,14 +651,16 @@ __global__ void repack_tc_kernel(const float* __restrict__ canon, int64_t cstrid
         const float* b3 = W3 + 2LL * C * T;
         unsigned char* blk = out + (size_t)l * g.layer_bytes;
         if (r < n2) {
-            const int e = (int)(r & 7), n = (int)((r >> 3) % CP), kg = (int)((r / (8 * CP)) % NKG);
-            const int t = (int)(r / (8 * CP * NKG)), ic = kg * 8 + e;
-            const float v = (n < C && ic < C) ? W2[((int64_t)n * C + ic) * T + t] : 0.f;
+            const int e = (int)(r & 7), n = (int)((r >> 3) % N2), kg = (int)((r / (8 * N2)) % NKG);
+            const int tp = (int)(r / (8 * N2 * NKG)), dx = n / CP, c = n % CP, ic = kg * 8 + e;
+            const int t = tp * 3 + dx;
+            const float v = (c < C && ic < C) ? W2[((int64_t)c * C + ic) * T + t] : 0.f;
             reinterpret_cast<__nv_bfloat16*>(blk)[r] = __float2bfloat16_rn(v);
         } else if (r < n2 + n3) {
             const int r3 = (int)(r - n2);
-            const int e = r3 & 7, n = (r3 >> 3) & 15, kg = (r3 >> 7) % NKG, t = r3 / (128 * NKG), ic = kg * 8 + e;
-            const float v = (n < 2 && ic < C) ? W3[((int64_t)n * C + ic) * T + t] : 0.f;
+            const int e = r3 & 7, n = (r3 >> 3) & 15, kg = (r3 >> 7) % NKG, tp = r3 / (128 * NKG), ic = kg * 8 + e;
+            const int dx = n >> 1, j = n & 1, t = tp * 3 + dx;
+            const float v = (n < 6 && ic < C) ? W3[((int64_t)j * C + ic) * T + t] : 0.f;
             reinterpret_cast<__half*>(blk + g.w2_bytes)[r3] = __float2half_rn(v);
         } else {
             const int f = (int)(r - n2 - n3);
@@ -679,10 +704,12 @@ bool tc_plan(const gf_flow_shape& s, TcGeom& g) {
     g.npad = s.nd == 3 ? g.P * g.P * g.P : g.P * g.P;
     g.p_first = s.nd == 3 ? 1 + g.P + g.P * g.P : 1 + g.P;
     const int p_last = g.p_first * s.L;
-    g.n_tiles = (p_last - g.p_first + 1 + kTcM - 1) / kTcM;
-    g.npos = (2 * g.p_first + g.n_tiles * kTcM + 7) & ~7;
+    g.n_tiles = (p_last - g.p_first + 1 + kTcOut - 1) / kTcOut;
+    if (g.n_tiles > kTcMaxTiles) return false;
+    // tile t reads positions 96 t .. 96 t + 96 + 2 p_first - 1 (rows first .. first + 97, taps +-(p_first - 1))
+    g.npos = (2 * g.p_first + g.n_tiles * kTcOut + 7) & ~7;
     if (g.npos > 16383) return false;                      // descriptor LBO field (16-byte units)
-    g.r_lag = (g.p_first + kTcM - 1) / kTcM;
+    g.r_lag = (g.p_first + kTcOut - 1) / kTcOut;
     g.fd_half = make_fastdiv((uint32_t)(g.V / 2));
     g.fd_Lh = make_fastdiv((uint32_t)(s.L / 2));
     g.fd_L = make_fastdiv((uint32_t)s.L);
@@ -690,8 +717,8 @@ bool tc_plan(const gf_flow_shape& s, TcGeom& g) {
     g.fd_PP = make_fastdiv((uint32_t)(g.P * g.P));
     if (g.V / 2 >= 4096 || g.npos * 4 >= (1 << 24)) return false;   // FastDiv ranges
     const int NKG = g.Cp / 8;
-    g.w2_bytes = (uint32_t)(g.T * NKG * g.Cp * 16);
-    g.w3_bytes = (uint32_t)(g.T * NKG * 16 * 16);
+    g.w2_bytes = (uint32_t)(g.T / 3 * NKG * 3 * g.Cp * 16);
+    g.w3_bytes = (uint32_t)(g.T / 3 * NKG * 16 * 16);
     g.wf_W1 = 0;
     g.wf_b1 = g.T * g.Cp;
     g.wf_b2 = g.wf_b1 + g.Cp;
@@ -705,7 +732,7 @@ bool tc_plan(const gf_flow_shape& s, TcGeom& g) {
     g.off_x = g.off_wf + 2 * g.wf_bytes;
     g.off_red = g.off_x + (uint32_t)((g.V * 4 + 15) & ~15);
     g.off_bar = g.off_red + 32 * 8;
-    g.smem_need = g.off_bar + (4 * kTcMaxBuf + 5) * 8 + 16;
+    g.smem_need = g.off_bar + (8 * kTcRing + kTcMaxTiles + 5) * 8 + 16;
     return g.smem_need <= (uint32_t)kSmemPerCTA;
 }
 
@@ -719,16 +746,16 @@ gf_status launch_tc(TcArgs& a, cudaStream_t stream) {
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTcThreads, g.smem_need) != cudaSuccess ||
         per_sm < 1)
         return GF_ECUDA;
-    // TMEM: CTAs resident on one SM share its 512 columns; keep at least
-    // r_lag + 2 conv2 accumulators per CTA, and pad shared memory so that no
-    // more CTAs than planned share an SM
+    // TMEM: CTAs resident on one SM share its 512 columns; each CTA needs two
+    // conv2 accumulators of 3 Cp columns (one per epilogue group); pad shared
+    // memory so that no more CTAs than planned share an SM
     const auto cols_for = [](int k) { int c = 512; while (c * k > 512) c >>= 1; return c; };
     int k = std::min(per_sm, 16);
-    while (k > 1 && cols_for(k) / CP < g.r_lag + 2) --k;
+    while (k > 1 && cols_for(k) / (2 * 3 * CP) < 1) --k;
     g.tmem_cols = cols_for(k);
-    g.nbuf2 = std::min(kTcMaxBuf, g.tmem_cols / CP);
-    g.nbuf3 = std::min(kTcMaxBuf, g.tmem_cols / 16);
-    if (g.nbuf2 < g.r_lag + 2 || g.nbuf3 < 2) return GF_EUNSUPPORTED;
+    g.nbuf2 = std::min(kTcRing, g.tmem_cols / (2 * 3 * CP));
+    g.nbuf3 = std::min(kTcRing, g.tmem_cols / (2 * 16));
+    if (g.nbuf2 < 1 || g.nbuf3 < 1) return GF_EUNSUPPORTED;
     size_t smem = g.smem_need;
     if (k < per_sm) smem = std::max<size_t>(smem, (size_t)(kSmemPerSM / (k + 1) - kSmemReserve + 128));
     smem = (smem + 127) & ~size_t(127);
