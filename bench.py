@@ -278,7 +278,7 @@ def bench_gpu(args, rank, world, local):
     shape, phi4, B = W["shape"], W["phi4"], args.batch or W["batch"]
     prec = args.precision
     if prec == "auto":
-        prec = "bf16" if (shape.nd == 3 and shape.L == 16 and shape.c1 == 32 and shape.c2 == 32) else "fp32"
+        prec = "bf16" if P.tensor_core_supported(shape) else "fp32"
     flow = P.Flow(shape, gi.init_weights(shape, seed=0), precision=prec)
     V = shape.V
     out = P.SampleResult(phi=torch.empty(B, V, device=dev),
@@ -753,7 +753,7 @@ def bench_serving(dev, n_requests=120, rate=200.0, n_models=16, seed=5):
     specs = gi.serving_models(n_models, seed)
     models = {}
     for name, shape, s in specs:
-        prec = "bf16" if (shape.nd == 3 and shape.L == 16 and shape.c1 == 32 and shape.c2 == 32) else "fp32"
+        prec = "bf16" if P.tensor_core_supported(shape) else "fp32"
         models[name] = serving.Model(name, shape, P.Flow(shape, gi.init_weights(shape, seed=s), precision=prec))
     mix = gi.serving_requests(n_requests, list(models), seed)
 
@@ -763,7 +763,10 @@ def bench_serving(dev, n_requests=120, rate=200.0, n_models=16, seed=5):
                 for i, (name, m2, lam, b, sd) in enumerate(mix)]
 
     out = {"mix": "2D L in {8,16,32,64}, 3D L in {8,12,16}, 12-24 couplings, hidden {8,16,24,32}, "
-                  "batch 64-8192 log-uniform; tensor-core kernel for 3D L=16 hidden 32, FP32 otherwise",
+                  "batch 64-8192 log-uniform; tensor-core kernels where gf_flow_tensor_core_supported "
+                  "(hidden 16-32 whose activations fit a block), FP32 kernels otherwise",
+           "precision_by_model": {name: ("bf16" if P.tensor_core_supported(shape) else "fp32")
+                                  for name, shape, _ in specs},
            "models": n_models, "requests_per_load": n_requests,
            "mean_configs_per_request": float(np.mean([m[3] for m in mix]))}
     with serving.Server(models, hbm_budget_bytes=16 << 30, max_active=16, chunk=2048, device=dev) as srv:

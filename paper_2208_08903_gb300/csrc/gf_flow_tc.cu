@@ -176,13 +176,12 @@ __device__ __forceinline__ void pos_xyz(int p, int P, int PP, FastDiv fdP, FastD
     px = rem - py * P;
 }
 
-// conv1: h1 = LReLU(W1 * (x at the frozen sites) + b1) for every site and
-// channel group, BF16, at the site's padded position and its periodic images.
-// Work items are ordered (channel group, site parity, site), so a warp holds
-// one channel group (its weight loads are broadcasts) and one site parity (the
-// live taps, those that reach frozen sites, are the same for the whole warp).
-// Site j of parity q (rows y + L z in order, x fastest in a row): x = 2 (j mod
-// L/2) + ((q + y + z) mod 2).
+// conv1: h1 = LReLU(W1 * (x at the frozen sites) + b1) for every site, all
+// channels per thread, BF16, at the site's padded position and its periodic
+// images.  Sites are ordered (parity, site), so a warp holds one site parity
+// and the live taps (those that reach frozen sites) are the same for the
+// whole warp; the weight loads are broadcasts.  Site j of parity q (rows y + L z
+// in order, x fastest in a row): x = 2 (j mod L/2) + ((q + y + z) mod 2).
 template <int ND, int CP>
 __device__ void tc_conv1(const TcGeom& g, const float* wf, const float* x, int frozen, float slope,
                          unsigned char* act) {
@@ -190,18 +189,16 @@ __device__ void tc_conv1(const TcGeom& g, const float* wf, const float* x, int f
     const int L = g.L, half = g.V >> 1, Lh = L >> 1, P = g.P, npos = g.npos;
     const float* W1 = wf + g.wf_W1;
     const float* b1 = wf + g.wf_b1;
-    for (int it = threadIdx.x; it < half * 2 * NKG; it += blockDim.x) {
-        const int grp = fdiv(it, g.fd_half), j = it - grp * half;
-        const int kg = grp >> 1, q = grp & 1;
+    for (int it = threadIdx.x; it < 2 * half; it += blockDim.x) {
+        const int q = it >= half ? 1 : 0, j = it - q * half;
         const int r = fdiv(j, g.fd_Lh), xh = j - r * Lh;
         const int zc = ND == 3 ? fdiv(r, g.fd_L) : 0, yc = r - zc * L;
         const int xc = 2 * xh + ((q ^ yc ^ zc) & 1);
-        float acc[8];
-        {
-            const float4 lo = *reinterpret_cast<const float4*>(b1 + kg * 8);
-            const float4 hi = *reinterpret_cast<const float4*>(b1 + kg * 8 + 4);
-            acc[0] = lo.x; acc[1] = lo.y; acc[2] = lo.z; acc[3] = lo.w;
-            acc[4] = hi.x; acc[5] = hi.y; acc[6] = hi.z; acc[7] = hi.w;
+        float acc[CP];
+#pragma unroll
+        for (int c4 = 0; c4 < CP / 4; ++c4) {
+            const float4 b = *reinterpret_cast<const float4*>(b1 + 4 * c4);
+            acc[4 * c4] = b.x; acc[4 * c4 + 1] = b.y; acc[4 * c4 + 2] = b.z; acc[4 * c4 + 3] = b.w;
         }
         const int xs[3] = {wrapc(xc - 1, L), xc, wrapc(xc + 1, L)};
         const int ys[3] = {wrapc(yc - 1, L) * L, yc * L, wrapc(yc + 1, L) * L};
@@ -222,18 +219,20 @@ __device__ void tc_conv1(const TcGeom& g, const float* wf, const float* x, int f
                     if ((q ^ po) != frozen) continue;
                     const int t = ND == 3 ? (dz * 3 + dy) * 3 + dx : dy * 3 + dx;
                     const float v = x[zs[dz] + ys[dy] + xs[dx]];
-                    const float4 w0 = *reinterpret_cast<const float4*>(W1 + t * CP + kg * 8);
-                    const float4 w1 = *reinterpret_cast<const float4*>(W1 + t * CP + kg * 8 + 4);
-                    acc[0] = fmaf(v, w0.x, acc[0]); acc[1] = fmaf(v, w0.y, acc[1]);
-                    acc[2] = fmaf(v, w0.z, acc[2]); acc[3] = fmaf(v, w0.w, acc[3]);
-                    acc[4] = fmaf(v, w1.x, acc[4]); acc[5] = fmaf(v, w1.y, acc[5]);
-                    acc[6] = fmaf(v, w1.z, acc[6]); acc[7] = fmaf(v, w1.w, acc[7]);
+                    const float4* w = reinterpret_cast<const float4*>(W1 + t * CP);
+#pragma unroll
+                    for (int c4 = 0; c4 < CP / 4; ++c4) {
+                        const float4 ww = w[c4];
+                        acc[4 * c4] = fmaf(v, ww.x, acc[4 * c4]);
+                        acc[4 * c4 + 1] = fmaf(v, ww.y, acc[4 * c4 + 1]);
+                        acc[4 * c4 + 2] = fmaf(v, ww.z, acc[4 * c4 + 2]);
+                        acc[4 * c4 + 3] = fmaf(v, ww.w, acc[4 * c4 + 3]);
+                    }
                 }
             }
         }
 #pragma unroll
-        for (int c = 0; c < 8; ++c) acc[c] = lrelu_tc(acc[c], slope);
-        const uint4 w = pack_bf16x8(acc);
+        for (int c = 0; c < CP; ++c) acc[c] = lrelu_tc(acc[c], slope);
         // padded coordinates of the site and of its periodic images (a site on
         // the first or last row of an axis is also the halo beyond the other end)
         int xo[2], yo[2], zo[2], nx = 1, ny = 1, nz = 1;
@@ -245,11 +244,15 @@ __device__ void tc_conv1(const TcGeom& g, const float* wf, const float* x, int f
         if (ND == 3) {
             if (zc == 0) zo[nz++] = (L + 1) * P * P; else if (zc == L - 1) zo[nz++] = 0;
         }
-        unsigned char* base = act + (size_t)kg * npos * 16;
-        for (int iz = 0; iz < nz; ++iz)
-            for (int iy = 0; iy < ny; ++iy)
-                for (int ix = 0; ix < nx; ++ix)
-                    *reinterpret_cast<uint4*>(base + (size_t)(xo[ix] + yo[iy] + zo[iz]) * 16) = w;
+#pragma unroll
+        for (int kg = 0; kg < NKG; ++kg) {
+            const uint4 w = pack_bf16x8(acc + 8 * kg);
+            unsigned char* base = act + (size_t)kg * npos * 16;
+            for (int iz = 0; iz < nz; ++iz)
+                for (int iy = 0; iy < ny; ++iy)
+                    for (int ix = 0; ix < nx; ++ix)
+                        *reinterpret_cast<uint4*>(base + (size_t)(xo[ix] + yo[iy] + zo[iz]) * 16) = w;
+        }
     }
 }
 
@@ -464,9 +467,12 @@ __global__ void __launch_bounds__(kTcThreads, ND == 3 ? 1 : 2) flow_tc_kernel(co
             if (warp < 2) {
                 // issuing thread r (lane 0 of warp r, sub-partition r): tiles t = r (mod 2) into ring r
                 if (lane == 0 && tc_wait(bar_w2, step, abort_flag, a.status)) {
+                    fence_after_sync();
                     for (int t = warp; t < nt; t += 2) {
-                        if (k2 >= 1 && !tc_wait(empty2 + warp * kTcRing + i2, k2 - 1, abort_flag, a.status)) break;
-                        fence_after_sync();
+                        if (k2 >= 1) {
+                            if (!tc_wait(empty2 + warp * kTcRing + i2, k2 - 1, abort_flag, a.status)) break;
+                            fence_after_sync();
+                        }
                         issue_tile<ND, CP>(p_first - 1 + kTcOut * t, P, PP,
                                            tmem + (uint32_t)((warp * nb2 + i2) * 3 * CP), a0, b2d, a_ks,
                                            (uint32_t)(NKG * 3 * CP), (uint32_t)(2 * 3 * CP), idesc2);
@@ -535,9 +541,12 @@ __global__ void __launch_bounds__(kTcThreads, ND == 3 ? 1 : 2) flow_tc_kernel(co
             // ---- conv3 (s, t) on the tensor cores; the epilogue updates the other parity
             if (warp < 2) {
                 if (lane == 0 && tc_wait(bar_w3, step, abort_flag, a.status)) {
+                    fence_after_sync();
                     for (int t = warp; t < nt; t += 2) {
-                        if (k3 >= 1 && !tc_wait(empty3 + warp * kTcRing + i3, k3 - 1, abort_flag, a.status)) break;
-                        fence_after_sync();
+                        if (k3 >= 1) {
+                            if (!tc_wait(empty3 + warp * kTcRing + i3, k3 - 1, abort_flag, a.status)) break;
+                            fence_after_sync();
+                        }
                         issue_tile<ND, CP>(p_first - 1 + kTcOut * t, P, PP, tmem + (uint32_t)((warp * nb3 + i3) * 16),
                                            a0, b3d, a_ks, (uint32_t)(NKG * 16), (uint32_t)(2 * 16), idesc3);
                         mma_commit(full3 + warp * kTcRing + i3);
