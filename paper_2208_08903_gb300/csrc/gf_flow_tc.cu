@@ -748,7 +748,10 @@ bool tc_plan(const gf_flow_shape& s, TcGeom& g) {
 template <int ND, int CP, bool INV>
 gf_status launch_tc(TcArgs& a, cudaStream_t stream) {
     auto kern = flow_tc_kernel<ND, CP, INV>;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemPerCTA) != cudaSuccess)
+    // the largest shared-memory carveout, so that the occupancy below (and the
+    // launch) may place as many CTAs per SM as 228 KB allow
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemPerCTA) != cudaSuccess ||
+        cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess)
         return GF_ECUDA;
     TcGeom& g = a.g;
     int per_sm = 0;
@@ -757,7 +760,9 @@ gf_status launch_tc(TcArgs& a, cudaStream_t stream) {
         return GF_ECUDA;
     // TMEM: CTAs resident on one SM share its 512 columns; each CTA needs two
     // conv2 accumulators of 3 Cp columns (one per epilogue group); pad shared
-    // memory so that no more CTAs than planned share an SM
+    // memory so that no more CTAs than planned share an SM.  (The runtime
+    // places one CTA of a kernel that uses tcgen05 per SM; the split is kept
+    // for any device that places more.)
     const auto cols_for = [](int k) { int c = 512; while (c * k > 512) c >>= 1; return c; };
     int k = std::min(per_sm, 16);
     while (k > 1 && cols_for(k) / (2 * 3 * CP) < 1) --k;
