@@ -193,15 +193,17 @@ __device__ __forceinline__ double phi4_force_site(const T* p, int n, int nd, int
 }
 
 // phi^4 action (paper Sec. 1) of one configuration held in shared memory,
-// this thread's share of the sites (n = threadIdx.x, += blockDim.x), in the
+// this thread's share of the sites (n = t0, += stride; by default the
+// thread's index in the block and the block size), in the
 // forward-hop arrangement (equal to the two-neighbour form summed over the
 // periodic lattice): phi^2 (c2d + lam phi^2) - 2 phi sum_mu phi(n + mu),
 // c2d = 2 nd + m2, in FP32 pairs (phi^2 exact, products and sums to about
 // 2^-48).  Used by the fused coupling-stack kernels' epilogues.
 template <int ND>
-__device__ FF action_part(const float* x, int L, int V, const FF& c2d, const FF& lam) {
+__device__ FF action_part(const float* x, int L, int V, const FF& c2d, const FF& lam, int t0 = threadIdx.x,
+                          int stride = blockDim.x) {
     FF acc{0.f, 0.f};
-    for (int n = threadIdx.x; n < V; n += blockDim.x) {
+    for (int n = t0; n < V; n += stride) {
         const int xc = n % L, yc = (n / L) % L, zc = n / (L * L);
         FF hop{x[n - xc + (xc + 1 == L ? 0 : xc + 1)], 0.f};
         ff_add(hop, x[n + ((yc + 1 == L ? 0 : yc + 1) - yc) * L]);

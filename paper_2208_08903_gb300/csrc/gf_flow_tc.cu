@@ -107,6 +107,7 @@ struct TcGeom {
     uint32_t w2_bytes, w3_bytes, wf_bytes, layer_bytes;   // layer block: W2 | W3 | FP32 part
     int wf_W1, wf_b1, wf_b2, wf_b3;                        // float offsets in the FP32 part
     uint32_t off_act, off_w2, off_w3, off_wf, off_x, off_red, off_bar, smem_need;
+    uint32_t half_bytes;   // shared memory of one half (smem_need rounded up to 1 KB)
 };
 
 struct TcArgs {
@@ -184,12 +185,12 @@ __device__ __forceinline__ void pos_xyz(int p, int P, int PP, FastDiv fdP, FastD
 // in order, x fastest in a row): x = 2 (j mod L/2) + ((q + y + z) mod 2).
 template <int ND, int CP>
 __device__ void tc_conv1(const TcGeom& g, const float* wf, const float* x, int frozen, float slope,
-                         unsigned char* act) {
+                         unsigned char* act, int t0, int nthr) {
     constexpr int NKG = CP / 8;
     const int L = g.L, half = g.V >> 1, Lh = L >> 1, P = g.P, npos = g.npos;
     const float* W1 = wf + g.wf_W1;
     const float* b1 = wf + g.wf_b1;
-    for (int it = threadIdx.x; it < 2 * half; it += blockDim.x) {
+    for (int it = t0; it < 2 * half; it += nthr) {
         const int q = it >= half ? 1 : 0, j = it - q * half;
         const int r = fdiv(j, g.fd_Lh), xh = j - r * Lh;
         const int zc = ND == 3 ? fdiv(r, g.fd_L) : 0, yc = r - zc * L;
@@ -259,10 +260,10 @@ __device__ void tc_conv1(const TcGeom& g, const float* wf, const float* x, int f
 // The periodic images of h2: every halo position of the padded lattice gets
 // the channel groups of its interior source site.
 template <int ND, int CP>
-__device__ void tc_halo(const TcGeom& g, unsigned char* act) {
+__device__ void tc_halo(const TcGeom& g, unsigned char* act, int t0, int nthr) {
     constexpr int NKG = CP / 8;
     const int L = g.L, P = g.P, npos = g.npos;
-    for (int p = threadIdx.x; p < g.npad; p += blockDim.x) {
+    for (int p = t0; p < g.npad; p += nthr) {
         int px, py, pz;
         pos_xyz<ND>(p, P, P * P, g.fd_P, g.fd_PP, px, py, pz);
         if (px >= 1 && px <= L && py >= 1 && py <= L && pz >= 1 && pz <= L) continue;
@@ -308,11 +309,18 @@ __device__ __forceinline__ void issue_tile(int first, int P, int PP, uint32_t d,
     }
 }
 
-template <int ND, int CP, bool INVERSE>
-__global__ void __launch_bounds__(kTcThreads, ND == 3 ? 1 : 2) flow_tc_kernel(const TcArgs a) {
+// H halves of 12 warps each run one configuration at a time on their own
+// shared memory, TMEM columns and barriers (bar.sync 1 + half between
+// their phases), so that one half's CUDA-core phases overlap the other's
+// tensor-core phases: the runtime places a single CTA of a tcgen05 kernel
+// on an SM.
+template <int ND, int CP, bool INVERSE, int H>
+__global__ void __launch_bounds__(kTcThreads * H, 1) flow_tc_kernel(const TcArgs a) {
     constexpr int NKG = CP / 8;
-    extern __shared__ __align__(1024) unsigned char smem[];
+    extern __shared__ __align__(1024) unsigned char smem_all[];
     const TcGeom& g = a.g;
+    const int h = H == 1 ? 0 : (int)(threadIdx.x / kTcThreads);
+    unsigned char* smem = smem_all + (size_t)h * g.half_bytes;
     unsigned char* act = smem + g.off_act;
     unsigned char* w2s = smem + g.off_w2;
     unsigned char* w3s = smem + g.off_w3;
@@ -333,7 +341,7 @@ __global__ void __launch_bounds__(kTcThreads, ND == 3 ? 1 : 2) flow_tc_kernel(co
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar_fin + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = (int)threadIdx.x - h * kTcThreads, lane = tid & 31, warp = tid >> 5;   // within the half
     // geometry in registers (the tcgen05 statements' memory clobbers would
     // otherwise make every use read the kernel parameters again)
     const int V = g.V, L = g.L, npos = g.npos, nt = g.n_tiles, P = g.P, PP = g.P * g.P, p_first = g.p_first;
@@ -341,8 +349,9 @@ __global__ void __launch_bounds__(kTcThreads, ND == 3 ? 1 : 2) flow_tc_kernel(co
     const FastDiv fdP = g.fd_P, fdPP = g.fd_PP;
     const uint32_t a_ks = 2u * (uint32_t)npos;
     const int wf_floats = (int)(g.wf_bytes >> 2);
-    const int64_t n_cfg = a.B > (int64_t)blockIdx.x ? (a.B - 1 - (int64_t)blockIdx.x) / gridDim.x + 1 : 0;
-    const int64_t total_steps = n_cfg * a.n_layers;   // this CTA's layer applications
+    const int64_t b0 = (int64_t)blockIdx.x * H + h, bstride = (int64_t)gridDim.x * H;
+    const int64_t n_cfg = a.B > b0 ? (a.B - 1 - b0) / bstride + 1 : 0;
+    const int64_t total_steps = n_cfg * a.n_layers;   // this half's layer applications
     int64_t w2_issued = -1, w3_issued = -1, wf_issued = -1;   // thread 0: the last staged steps
     // epilogue warps: group eg (0: warps 4..7, 1: warps 8..11) takes the tiles
     // t = eg (mod 2) through its own TMEM ring; warp w reads lane quarter w mod 4
@@ -364,10 +373,27 @@ __global__ void __launch_bounds__(kTcThreads, ND == 3 ? 1 : 2) flow_tc_kernel(co
         wf_issued = step;
     };
 
-    if (warp == 0) {
-        tmem_alloc(tmem_slot, (uint32_t)g.tmem_cols);
+    // one allocation for the CTA (warp 0 of half 0); half h uses columns
+    // h * tmem_cols .. (h + 1) * tmem_cols
+    uint32_t* tmem_slot0 = reinterpret_cast<uint32_t*>(reinterpret_cast<unsigned char*>(tmem_slot) - h * g.half_bytes);
+    if (threadIdx.x < 32) {
+        tmem_alloc(tmem_slot0, (uint32_t)(g.tmem_cols * H));
         tmem_relinquish();
     }
+    const auto half_sync = [&]() {
+        if (H == 1) __syncthreads();
+        else asm volatile("bar.sync %0, %1;" :: "r"(1 + h), "r"(kTcThreads) : "memory");
+    };
+    // FP64-accurate sum over the half's threads (fixed order)
+    const auto half_sum = [&](FF v) {
+        v = warp_sum_ff(v);
+        if (lane == 0) red[warp] = v;
+        half_sync();
+        FF r = lane < kTcThreads / 32 ? red[lane] : FF{0.f, 0.f};
+        r = warp_sum_ff(r);
+        half_sync();
+        return ff_to_double(r);
+    };
     if (tid == 0) {
         for (int i = 0; i < 2 * kTcRing; ++i) {
             mbar_init(full2 + i, 1);
@@ -386,7 +412,7 @@ __global__ void __launch_bounds__(kTcThreads, ND == 3 ? 1 : 2) flow_tc_kernel(co
     }
     // positions past the padded lattice feed only dropped rows of the last
     // tiles; zero them once so every MMA reads finite numbers
-    for (int i = tid; i < NKG * npos; i += blockDim.x)
+    for (int i = tid; i < NKG * npos; i += kTcThreads)
         reinterpret_cast<uint4*>(act)[i] = make_uint4(0u, 0u, 0u, 0u);
     fence_proxy_async();
     fence_before_sync();
@@ -397,7 +423,7 @@ __global__ void __launch_bounds__(kTcThreads, ND == 3 ? 1 : 2) flow_tc_kernel(co
         stage_w3(0);
         stage_wf(0);
     }
-    const uint32_t tmem = *tmem_slot;
+    const uint32_t tmem = *tmem_slot0 + (uint32_t)(h * g.tmem_cols);
     // D = F32, K-major A and B, M = 128: conv2 BF16 with N = 3 CP, conv3 FP16 with N = 16
     const uint32_t idesc2 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(3 * CP >> 3) << 17) |
                             ((uint32_t)(kTcM >> 4) << 24);
@@ -415,19 +441,19 @@ __global__ void __launch_bounds__(kTcThreads, ND == 3 ? 1 : 2) flow_tc_kernel(co
     // epilogue group g: ring g) and how often it has been filled before
     int i2 = 0, i3 = 0;
     int64_t k2 = 0, k3 = 0;
-    for (int64_t b = blockIdx.x; b < a.B; b += gridDim.x) {
+    for (int64_t b = b0; b < a.B; b += bstride) {
         // prior sample (sampling) or the given field (inverting)
         FF sumz2{0.f, 0.f};
         if (!INVERSE) {
             if (a.z_in) {
-                for (int n = tid; n < V; n += blockDim.x) {
+                for (int n = tid; n < V; n += kTcThreads) {
                     const float v = __ldg(a.z_in + b * V + n);
                     x[n] = v;
                     const float p = v * v;
                     ff_add(sumz2, FF{p, fmaf(v, v, -p)});
                 }
             } else {
-                for (int jq = tid; 4 * jq < V; jq += blockDim.x) {
+                for (int jq = tid; 4 * jq < V; jq += kTcThreads) {
                     const u64x4 w = philox4x64_10(a.seed, 0ull,
                                                   u64x4{a.counter0 + (uint64_t)b, (uint64_t)jq, 0ull, TAG_PRIOR});
                     float zz[4];
@@ -440,13 +466,13 @@ __global__ void __launch_bounds__(kTcThreads, ND == 3 ? 1 : 2) flow_tc_kernel(co
                     }
                 }
             }
-            __syncthreads();
+            half_sync();
             if (a.z_out)
-                for (int n = tid; n < V; n += blockDim.x) a.z_out[b * V + n] = x[n];
+                for (int n = tid; n < V; n += kTcThreads) a.z_out[b * V + n] = x[n];
         } else {
-            for (int n = tid; n < V; n += blockDim.x) x[n] = __ldg(a.phi_in + b * V + n);
+            for (int n = tid; n < V; n += kTcThreads) x[n] = __ldg(a.phi_in + b * V + n);
         }
-        __syncthreads();
+        half_sync();
 
         FF logdet{0.f, 0.f};
         for (int li = 0; li < a.n_layers; ++li, ++step) {
@@ -457,10 +483,10 @@ __global__ void __launch_bounds__(kTcThreads, ND == 3 ? 1 : 2) flow_tc_kernel(co
             // ---- conv1 -> h1 (BF16, padded, with periodic images)
             if (tc_wait(bar_wf + (step & 1), step >> 1, abort_flag, a.status)) {
                 if (tid == 0 && step + 1 < total_steps) stage_wf(step + 1);
-                tc_conv1<ND, CP>(g, wf, x, frozen, a.slope, act);
+                tc_conv1<ND, CP>(g, wf, x, frozen, a.slope, act, tid, kTcThreads);
             }
             fence_proxy_async();
-            __syncthreads();
+            half_sync();
             if (*abort_flag) break;
 
             // ---- conv2 on the tensor cores; the epilogue writes h2 (FP16) over h1 in place
@@ -527,16 +553,16 @@ __global__ void __launch_bounds__(kTcThreads, ND == 3 ? 1 : 2) flow_tc_kernel(co
                 }
             }
             fence_before_sync();
-            __syncthreads();
+            half_sync();
             if (*abort_flag) break;
             fence_after_sync();
             // every conv2 MMA of this layer has completed: the next layer's W2 may land
             if (tid == 0 && step + 1 < total_steps) stage_w2(step + 1);
 
             // ---- periodic images of h2
-            tc_halo<ND, CP>(g, act);
+            tc_halo<ND, CP>(g, act, tid, kTcThreads);
             fence_proxy_async();
-            __syncthreads();
+            half_sync();
 
             // ---- conv3 (s, t) on the tensor cores; the epilogue updates the other parity
             if (warp < 2) {
@@ -590,7 +616,7 @@ __global__ void __launch_bounds__(kTcThreads, ND == 3 ? 1 : 2) flow_tc_kernel(co
                 }
             }
             fence_before_sync();
-            __syncthreads();
+            half_sync();
             if (*abort_flag) break;
             fence_after_sync();
             // every conv3 MMA of this layer has completed: the next layer's W3 may land
@@ -599,19 +625,19 @@ __global__ void __launch_bounds__(kTcThreads, ND == 3 ? 1 : 2) flow_tc_kernel(co
         if (*abort_flag) break;
 
         if (INVERSE) {
-            for (int n = tid; n < V; n += blockDim.x) {
+            for (int n = tid; n < V; n += kTcThreads) {
                 const float v = x[n];
                 const float p = v * v;
                 ff_add(sumz2, FF{p, fmaf(v, v, -p)});
                 if (a.z_out) a.z_out[b * V + n] = v;
             }
         } else {
-            for (int n = tid; n < V; n += blockDim.x) a.phi_out[b * V + n] = x[n];
+            for (int n = tid; n < V; n += kTcThreads) a.phi_out[b * V + n] = x[n];
         }
-        const double ld = block_sum_ff(logdet, red);
-        const double z2 = block_sum_ff(sumz2, red);
+        const double ld = half_sum(logdet);
+        const double z2 = half_sum(sumz2);
         double S = 0.0;
-        if (!INVERSE && a.has_phi4) S = block_sum_ff(action_part<ND>(x, L, V, a.c2d_ff, a.lam_ff), red);
+        if (!INVERSE && a.has_phi4) S = half_sum(action_part<ND>(x, L, V, a.c2d_ff, a.lam_ff, tid, kTcThreads));
         if (tid == 0) {
             const double logr = -0.5 * z2 - 0.5 * (double)V * LOG_2PI;
             const double logq = logr - ld;
@@ -621,7 +647,7 @@ __global__ void __launch_bounds__(kTcThreads, ND == 3 ? 1 : 2) flow_tc_kernel(co
                 if (a.logw_out) a.logw_out[b] = -S - logq;
             }
         }
-        __syncthreads();
+        half_sync();
     }
     // teardown: copies still landing and MMAs still queued (only after an
     // abort) finish before their shared memory and TMEM are released
@@ -633,10 +659,10 @@ __global__ void __launch_bounds__(kTcThreads, ND == 3 ? 1 : 2) flow_tc_kernel(co
         tc_drain(bar_fin, 0);
     }
     fence_before_sync();
-    __syncthreads();
-    if (warp == 0) {
+    __syncthreads();                             // both halves
+    if (threadIdx.x < 32) {
         fence_after_sync();
-        tmem_dealloc(tmem, (uint32_t)g.tmem_cols);
+        tmem_dealloc(*tmem_slot0, (uint32_t)(g.tmem_cols * H));
     }
 }
 
@@ -742,45 +768,33 @@ bool tc_plan(const gf_flow_shape& s, TcGeom& g) {
     g.off_red = g.off_x + (uint32_t)((g.V * 4 + 15) & ~15);
     g.off_bar = g.off_red + 32 * 8;
     g.smem_need = g.off_bar + (8 * kTcRing + kTcMaxTiles + 5) * 8 + 16;
+    g.half_bytes = (g.smem_need + 1023) & ~1023u;
     return g.smem_need <= (uint32_t)kSmemPerCTA;
 }
 
-template <int ND, int CP, bool INV>
+template <int ND, int CP, bool INV, int H>
 gf_status launch_tc(TcArgs& a, cudaStream_t stream) {
-    auto kern = flow_tc_kernel<ND, CP, INV>;
-    // the largest shared-memory carveout, so that the occupancy below (and the
-    // launch) may place as many CTAs per SM as 228 KB allow
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemPerCTA) != cudaSuccess ||
-        cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess)
-        return GF_ECUDA;
+    auto kern = flow_tc_kernel<ND, CP, INV, H>;
     TcGeom& g = a.g;
+    const size_t smem = (size_t)H * g.half_bytes;
+    if (smem > (size_t)kSmemPerCTA) return GF_EUNSUPPORTED;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return GF_ECUDA;
+    // TMEM: the runtime places one CTA of a tcgen05 kernel per SM; its H
+    // halves share the 512 columns, each needing two conv2 accumulators of
+    // 3 Cp columns (one per epilogue group)
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTcThreads, g.smem_need) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTcThreads * H, smem) != cudaSuccess ||
         per_sm < 1)
         return GF_ECUDA;
-    // TMEM: CTAs resident on one SM share its 512 columns; each CTA needs two
-    // conv2 accumulators of 3 Cp columns (one per epilogue group); pad shared
-    // memory so that no more CTAs than planned share an SM.  (The runtime
-    // places one CTA of a kernel that uses tcgen05 per SM; the split is kept
-    // for any device that places more.)
-    const auto cols_for = [](int k) { int c = 512; while (c * k > 512) c >>= 1; return c; };
-    int k = std::min(per_sm, 16);
-    while (k > 1 && cols_for(k) / (2 * 3 * CP) < 1) --k;
-    g.tmem_cols = cols_for(k);
+    if (per_sm > 1) return GF_EUNSUPPORTED;      // the TMEM split assumes one CTA per SM
+    g.tmem_cols = 512 / H;
     g.nbuf2 = std::min(kTcRing, g.tmem_cols / (2 * 3 * CP));
     g.nbuf3 = std::min(kTcRing, g.tmem_cols / (2 * 16));
     if (g.nbuf2 < 1 || g.nbuf3 < 1) return GF_EUNSUPPORTED;
-    size_t smem = g.smem_need;
-    if (k < per_sm) smem = std::max<size_t>(smem, (size_t)(kSmemPerSM / (k + 1) - kSmemReserve + 128));
-    smem = (smem + 127) & ~size_t(127);
-    if (smem > (size_t)kSmemPerCTA) return GF_EUNSUPPORTED;
-    int chk = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&chk, kern, kTcThreads, smem) != cudaSuccess || chk < 1 ||
-        chk > k)
-        return GF_ECUDA;
-    const int64_t grid = std::min<int64_t>(a.B, (int64_t)num_sms() * chk);
+    const int64_t grid = std::min<int64_t>((a.B + H - 1) / H, (int64_t)num_sms());
     if (grid <= 0) return GF_OK;
-    kern<<<(unsigned)grid, kTcThreads, smem, stream>>>(a);
+    kern<<<(unsigned)grid, kTcThreads * H, smem, stream>>>(a);
     GF_CHECK_LAUNCH();
     return GF_OK;
 }
@@ -836,11 +850,17 @@ gf_status launch_flow_tc(const gf_flow* f, bool inverse, const gf_phi4* phi4, in
     if (!a.status) return GF_ECUDA;
     const bool c32 = a.g.Cp == 32;
     if (f->shape.nd == 3) {
-        if (c32) return inverse ? launch_tc<3, 32, true>(a, stream) : launch_tc<3, 32, false>(a, stream);
-        return inverse ? launch_tc<3, 16, true>(a, stream) : launch_tc<3, 16, false>(a, stream);
+        if (c32) return inverse ? launch_tc<3, 32, true, 1>(a, stream) : launch_tc<3, 32, false, 1>(a, stream);
+        return inverse ? launch_tc<3, 16, true, 1>(a, stream) : launch_tc<3, 16, false, 1>(a, stream);
     }
-    if (c32) return inverse ? launch_tc<2, 32, true>(a, stream) : launch_tc<2, 32, false>(a, stream);
-    return inverse ? launch_tc<2, 16, true>(a, stream) : launch_tc<2, 16, false>(a, stream);
+    // 2D: two configurations per CTA where two halves' shared memory fits
+    const bool two = 2 * (size_t)a.g.half_bytes <= (size_t)kSmemPerCTA && B > num_sms();
+    if (c32) {
+        if (two) return inverse ? launch_tc<2, 32, true, 2>(a, stream) : launch_tc<2, 32, false, 2>(a, stream);
+        return inverse ? launch_tc<2, 32, true, 1>(a, stream) : launch_tc<2, 32, false, 1>(a, stream);
+    }
+    if (two) return inverse ? launch_tc<2, 16, true, 2>(a, stream) : launch_tc<2, 16, false, 2>(a, stream);
+    return inverse ? launch_tc<2, 16, true, 1>(a, stream) : launch_tc<2, 16, false, 1>(a, stream);
 }
 
 }  // namespace gf

@@ -87,10 +87,12 @@ def test_tc_given_z_and_inverse(orc, nd, L, c):
 
 
 def test_tc_persistent_batch_and_placement(orc):
-    """A batch several times the resident grid (each block loops over many
-    configurations, so the TMEM ring and the weight staging wrap around many
-    times): sampled configurations against the oracle, and every configuration
-    bit-identical to the same prior counter sampled in a batch of its own."""
+    """A batch several times the resident grid (each block runs two
+    configurations at a time and loops over many, so the TMEM rings and the
+    weight staging wrap around many times): sampled configurations against
+    the oracle, every configuration bit-identical to the same prior counter
+    sampled in a batch of its own (one configuration per block), and the
+    inverse pass over the whole batch."""
     torch, P = require_gpu()
     shape = gi.FlowShape(2, 16, 3, 16, 16)
     m2, lam = -4.0, 6.0
@@ -110,6 +112,14 @@ def test_tc_persistent_batch_and_placement(orc):
         assert torch.equal(one.phi[0], out.phi[b]) and torch.equal(one.logw[0], out.logw[b])
     S = P.phi4_action(2, 16, (m2, lam), out.phi)
     assert_logw_close(S.cpu().numpy(), out.S.cpu().numpy(), rtol=1e-12, what="fused vs standalone S")
+    # the inverse pass over the same large batch (two configurations per block)
+    zb, lq = flow.logq(out.phi, return_z=True)
+    torch.cuda.synchronize()
+    assert P.device_status() == 0
+    for b in (0, 2501, B - 1):
+        zr, lqr = orc.flow_logq(shape, w, out.phi[b:b + 1].cpu().numpy().astype(np.float64), bf16_mask=TC_MODE)
+        assert_sites_close(zb[b:b + 1].cpu().numpy(), zr, rtol=RTOL, what=f"z(inverse)[{b}]")
+        assert_logw_close(lq[b:b + 1].cpu().numpy(), lqr, rtol=LW_RTOL, what=f"logq(inverse)[{b}]")
 
 
 def test_tc_mh_chain_on_flow_output(orc):
