@@ -134,11 +134,11 @@ gf_status gf_flow_create_ex(const gf_flow_shape_ex* shape, const double* weights
  * contraction (paper Sec. 1, the coupling layers' convolutional networks):
  * two equal hidden widths of 16, 24 or 32 (24 padded to 32 with zeros),
  * ksize 3, and either 3D L=16 with width 32 (its own kernel) or a lattice whose
- * activations fit one block's shared memory: 2 (P^nd + 2 (1 + P (+P^2)) +
- * 128) x Cp bytes (about; P = L + 2, Cp = 16 or 32) plus W2 and the field,
- * at most 227 KB, e.g. 2D L <= 32 with any of the widths, 2D L = 64 and 3D
- * L = 12 with width 16, 3D L = 8 with any.  Hidden width 8 stays on the FP32
- * kernels: there conv2 is too thin for the tensor cores. */
+ * padded activations (about 2 Cp (L+2)^nd bytes, Cp = 16 or 32), weights and
+ * field fit one block's 227 KB of shared memory: 2D L <= 32 with any of the
+ * widths, 2D L = 64 and 3D L = 12, 16 with width 16, 3D L = 8 with any.
+ * Hidden width 8 stays on the FP32 kernels: there conv2 is too thin for the
+ * tensor cores. */
 int32_t gf_flow_tensor_core_supported(const gf_flow_shape_ex* shape);
 gf_status gf_flow_destroy(gf_flow* flow);
 /* Number of canonical parameters. */

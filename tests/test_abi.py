@@ -131,8 +131,8 @@ def test_tensor_core_support_query(lib):
         return _abi.FlowShapeExC(nd, L, 12, len(hidden), hid, k, 1, 0.01)
 
     yes = [(2, 8, [16, 16]), (2, 16, [24, 24]), (2, 32, [32, 32]), (2, 64, [16, 16]), (3, 8, [32, 32]),
-           (3, 12, [16, 16]), (3, 16, [32, 32])]
-    no = [(2, 32, [8, 8]), (2, 64, [32, 32]), (3, 12, [32, 32]), (3, 16, [24, 24]), (3, 16, [16, 16]),
+           (3, 12, [16, 16]), (3, 16, [32, 32]), (3, 16, [16, 16])]
+    no = [(2, 32, [8, 8]), (2, 64, [32, 32]), (3, 12, [32, 32]), (3, 16, [24, 24]),
           (2, 32, [16, 32]), (2, 32, [16, 16, 16]), (2, 7, [16, 16])]
     for nd, L, h in yes:
         assert lib.gf_flow_tensor_core_supported(C.byref(ex(nd, L, h))) == 1, (nd, L, h)

@@ -35,7 +35,7 @@ def _err(gpu, ref):
 # (nd, L, hidden, coupling layers, batch): one tile (2D L=8), the padded width
 # 24, every lattice of the serving mix the kernel takes, 2 to 24 layers
 CASES = [(2, 8, 16, 2, 3), (2, 16, 24, 8, 4), (2, 32, 32, 2, 3), (2, 32, 32, 24, 2), (2, 64, 16, 2, 2),
-         (3, 8, 32, 8, 3), (3, 8, 24, 2, 3), (3, 12, 16, 2, 2), (3, 4, 32, 3, 3)]
+         (3, 8, 32, 8, 3), (3, 8, 24, 2, 3), (3, 12, 16, 2, 2), (3, 4, 32, 3, 3), (3, 16, 16, 2, 2)]
 
 
 @pytest.mark.parametrize("nd,L,c,n_layers,B", CASES)
@@ -141,3 +141,25 @@ def test_tc_mh_chain_on_flow_output(orc):
     n_acc = int(acc.cpu().numpy()[1:].sum())
     assert 0 < n_acc < 2047
     compare_mh(orc, 99, 0, lw, idx.cpu().numpy(), acc.cpu().numpy(), logw_tol=1e-15)
+
+
+def test_tc_bench_launch_sampled(orc):
+    """The bench's launch configuration of the 2D workload's flow (L=32, 24
+    couplings, width 32, batch 8192, two configurations per block): sampled
+    configurations against the emulating oracle at the 24-layer bound."""
+    torch, P = require_gpu()
+    shape = gi.FlowShape(2, 32, 24, 32, 32)
+    m2, lam = -4.0, 6.0
+    w = gi.init_weights(shape, seed=0)
+    flow = P.Flow(shape, w, precision="bf16")
+    B = 8192
+    out = flow.sample(B, seed=5, counter0=0, phi4=(m2, lam))
+    torch.cuda.synchronize()
+    assert P.device_status() == 0
+    assert torch.isfinite(out.phi).all() and torch.isfinite(out.logw).all()
+    RTOL, LW_RTOL = tc_tolerances(shape.n_layers)
+    for b in (0, 4095, B - 1):
+        ref = orc.flow_sample(shape, w, m2, lam, 1, seed=5, counter0=b, bf16_mask=TC_MODE)
+        assert_sites_close(out.phi[b:b + 1].cpu().numpy(), ref["phi"], rtol=RTOL, what=f"phi[{b}]")
+        for k in ("logq", "S", "logw"):
+            assert_logw_close(getattr(out, k)[b:b + 1].cpu().numpy(), ref[k], rtol=LW_RTOL, what=f"{k}[{b}]")
