@@ -163,3 +163,34 @@ def test_tc_bench_launch_sampled(orc):
         assert_sites_close(out.phi[b:b + 1].cpu().numpy(), ref["phi"], rtol=RTOL, what=f"phi[{b}]")
         for k in ("logq", "S", "logw"):
             assert_logw_close(getattr(out, k)[b:b + 1].cpu().numpy(), ref[k], rtol=LW_RTOL, what=f"{k}[{b}]")
+
+
+def test_tc_acceptance_equals_fp32_on_trained_2d_flow():
+    """Equal MH acceptance of the tensor-core sampler and the fused FP32
+    sampler on a 2D flow trained here (Sec. 1: flow proposals corrected by
+    the MH test with the Jacobian; Sec. 3: the training loop): 2D L=8,
+    m2=-4, lam=8 (the paper's example theory), 8 coupling layers of hidden
+    width 16, 2,000 reverse-KL Adam steps at batch 64 on the GPU; then both
+    samplers on the same 65,536 proposals (same prior counters, same MH
+    uniforms).  The acceptances must agree within three binomial standard
+    errors (combined as if independent; the chains share their proposals, so
+    this is conservative), on a flow whose acceptance is far from zero."""
+    import math
+    torch, P = require_gpu()
+    from paper_2208_08903_gb300 import train as T
+    shape = gi.FlowShape(2, 8, 8, 16, 16)
+    phi4 = (-4.0, 8.0)
+    flow = P.Flow(shape, gi.init_weights(shape, seed=2021))
+    st = T.train(flow, phi4, 20, 100, 64, lr=1e-3, seed=4242)
+    assert all(math.isfinite(x) for x in st.losses)
+    tc = P.Flow(shape, flow.get_weights().double().cpu().numpy(), precision="bf16")
+    n = 65536
+    ev32 = T.evaluate(flow, phi4, n, 4096, seed=909, sampler="fused", keep_logw=True)
+    evtc = T.evaluate(tc, phi4, n, 4096, seed=909, sampler="fused", keep_logw=True)
+    a32, atc = ev32["acceptance"], evtc["acceptance"]
+    se = math.hypot(ev32["acceptance_binomial_err"], evtc["acceptance_binomial_err"])
+    print(f"trained 2D L=8 flow: acceptance FP32 {a32:.5f} tensor-core {atc:.5f} (3 sigma {3 * se:.5f}); "
+          f"ESS {ev32['ess']:.5f} {evtc['ess']:.5f}; decisions agree {T.decision_agreement(evtc, ev32):.4f}")
+    assert a32 > 0.1
+    assert abs(atc - a32) <= 3 * se
+    assert P.device_status() == 0
