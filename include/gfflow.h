@@ -383,15 +383,15 @@ gf_status gf_alu_peak(int32_t kind, int64_t iters, double* flops_per_s_out, cuda
 /* Status                                                                  */
 /* ---------------------------------------------------------------------- */
 
-/* Test hook for the failure path of the BF16 tensor-core kernel (the
- * bounded mbarrier waits between its roles).  spins > 0: in launches made
- * after the call (process-wide), each block's first conv2 issuer, before its
- * first MMA, waits up to `spins` polls for a barrier completion that never
- * comes; the wait then gives up as any pipeline wait does when its limit runs
- * out: it records GF_ETIMEOUT in the device status word and raises the
- * block's abort flag; every other role leaves its loops, the block waits for
- * its queued tensor-core work and weight copies, frees its tensor memory and
- * returns.  The outputs of such a launch are undefined.  spins = 0 turns the
+/* Test hook for the failure path of the tensor-core kernels (the bounded
+ * mbarrier waits between their roles; both GF_PREC_BF16CONV_FP64RED kernels).
+ * spins > 0: in launches made after the call (process-wide), each block's (or
+ * block half's) first conv2 issuer, before its first MMA, waits up to `spins`
+ * polls for a barrier completion that never comes; the wait then gives up as
+ * any pipeline wait does when its limit runs out: it records GF_ETIMEOUT in
+ * the device status word and raises the block's abort flag; every other role
+ * leaves its loops, the block waits for its queued tensor-core work and weight
+ * copies, frees its tensor memory and returns.  The outputs of such a launch are undefined.  spins = 0 turns the
  * hook off; spins < 0 or above 2^21 returns GF_EINVAL.  Not for production
  * use. */
 gf_status gf_set_bf16_stall_test(int64_t spins);

@@ -108,6 +108,10 @@ bool fp32_c32_recompute_supported(const gf_flow* f);
 gf_status launch_c32_recompute(const gf_flow* f, int layer, int64_t B, const float* xl, float* h1_out, float* h2_out,
                                float* s_out, cudaStream_t stream);
 
+// Polls of the failure-path test hook of the tensor-core kernels
+// (gf_set_bf16_stall_test; 0 = off).
+long long bf16_stall_spins();
+
 // Tensor-core kernel for the shapes other than 3D L=16, C=32 (gf_flow_tc.cu)
 bool tc_supported(const gf_flow_shape* s);
 gf_status tc_configure(gf_flow* f);          // allocates the weight blocks

@@ -925,6 +925,8 @@ gf_status launch_flow_bf16(const gf_flow* f, bool inverse, const gf_phi4* phi4, 
     return GF_OK;
 }
 
+long long bf16_stall_spins() { return g_stall_spins.load(std::memory_order_relaxed); }
+
 }  // namespace gf
 
 extern "C" gf_status gf_set_bf16_stall_test(int64_t spins) {

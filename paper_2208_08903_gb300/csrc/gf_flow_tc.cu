@@ -122,6 +122,7 @@ struct TcArgs {
     const float* z_in; float* z_out; const float* phi_in; float* phi_out;
     double* logq_out; double* S_out; double* logw_out;
     int32_t* status;
+    long long stall_spins;     // > 0: failure-path test (gf_set_bf16_stall_test)
 };
 
 __device__ __forceinline__ int wrapc(int v, int L) { return v < 0 ? v + L : (v >= L ? v - L : v); }
@@ -338,7 +339,8 @@ __global__ void __launch_bounds__(kTcThreads * H, 1) flow_tc_kernel(const TcArgs
     uint64_t* bar_w3 = bar_w2 + 1;                                       // a layer's W3 staged
     uint64_t* bar_wf = bar_w3 + 1;                                       // 2: a layer's FP32 part staged
     uint64_t* bar_fin = bar_wf + 2;                                      // every queued MMA done (exit)
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar_fin + 1);
+    uint64_t* bar_stall = bar_fin + 1;                                   // never completed (failure-path test)
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar_stall + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const int tid = (int)threadIdx.x - h * kTcThreads, lane = tid & 31, warp = tid >> 5;   // within the half
@@ -407,6 +409,7 @@ __global__ void __launch_bounds__(kTcThreads * H, 1) flow_tc_kernel(const TcArgs
         mbar_init(bar_wf, 1);
         mbar_init(bar_wf + 1, 1);
         mbar_init(bar_fin, 2);                 // one commit per issuing thread
+        mbar_init(bar_stall, 1);
         *abort_flag = 0;
         fence_mbar_init();
     }
@@ -492,7 +495,19 @@ __global__ void __launch_bounds__(kTcThreads * H, 1) flow_tc_kernel(const TcArgs
             // ---- conv2 on the tensor cores; the epilogue writes h2 (FP16) over h1 in place
             if (warp < 2) {
                 // issuing thread r (lane 0 of warp r, sub-partition r): tiles t = r (mod 2) into ring r
-                if (lane == 0 && tc_wait(bar_w2, step, abort_flag, a.status)) {
+                bool go = lane == 0;
+                if (go && a.stall_spins > 0 && step == 0 && warp == 0) {
+                    // failure-path test: a wait for a completion that never comes,
+                    // before this half's first MMA
+                    for (long long spins = 0; !mbar_try_wait(bar_stall, 0u); ++spins)
+                        if (spins > a.stall_spins) {
+                            *abort_flag = 1;
+                            set_status(a.status, GF_ETIMEOUT);
+                            go = false;
+                            break;
+                        }
+                }
+                if (go && tc_wait(bar_w2, step, abort_flag, a.status)) {
                     fence_after_sync();
                     for (int t = warp; t < nt; t += 2) {
                         if (k2 >= 1) {
@@ -767,7 +782,7 @@ bool tc_plan(const gf_flow_shape& s, TcGeom& g) {
     g.off_x = g.off_wf + 2 * g.wf_bytes;
     g.off_red = g.off_x + (uint32_t)((g.V * 4 + 15) & ~15);
     g.off_bar = g.off_red + 32 * 8;
-    g.smem_need = g.off_bar + (8 * kTcRing + kTcMaxTiles + 5) * 8 + 16;
+    g.smem_need = g.off_bar + (8 * kTcRing + kTcMaxTiles + 6) * 8 + 16;
     g.half_bytes = (g.smem_need + 1023) & ~1023u;
     return g.smem_need <= (uint32_t)kSmemPerCTA;
 }
@@ -847,6 +862,7 @@ gf_status launch_flow_tc(const gf_flow* f, bool inverse, const gf_phi4* phi4, in
     a.z_in = z_in; a.z_out = z_out; a.phi_in = phi_in; a.phi_out = phi_out;
     a.logq_out = logq_out; a.S_out = S_out; a.logw_out = logw_out;
     a.status = status_word(stream);
+    a.stall_spins = bf16_stall_spins();
     if (!a.status) return GF_ECUDA;
     const bool c32 = a.g.Cp == 32;
     if (f->shape.nd == 3) {

@@ -194,3 +194,35 @@ def test_tc_acceptance_equals_fp32_on_trained_2d_flow():
     assert a32 > 0.1
     assert abs(atc - a32) <= 3 * se
     assert P.device_status() == 0
+
+
+@pytest.mark.parametrize("B", [3, 1000])
+def test_tc_wait_that_runs_out_reports_timeout_and_recovers(orc, B):
+    """Failure path of the kernel's bounded waits, without a GPU fault: with
+    the stall hook on, the first conv2 issuer of each block (of each block half
+    when a block runs two configurations) waits, before its first MMA, for a
+    barrier completion that never comes (65,536 polls); that wait gives up,
+    the other roles leave their loops, the block drains its weight copies and
+    any queued tensor-core work, frees its tensor memory and returns.  The host
+    sees GF_ETIMEOUT, and the next launch (hook off) is correct."""
+    torch, P = require_gpu()
+    lib = P._abi.load()
+    shape = gi.FlowShape(2, 16, 2, 16, 16)
+    w = gi.init_weights(shape, seed=1)
+    flow = P.Flow(shape, w, precision="bf16")
+    assert P.device_status() == 0
+    try:
+        assert lib.gf_set_bf16_stall_test(1 << 16) == P._abi.GF_OK
+        flow.sample(B, seed=3, counter0=0, phi4=(-4.0, 6.0))
+        torch.cuda.synchronize()
+        st = P.device_status()
+    finally:
+        lib.gf_set_bf16_stall_test(0)
+    assert st == P._abi.GF_ETIMEOUT
+    out = flow.sample(4, seed=11, counter0=0, phi4=(-4.0, 6.0))
+    torch.cuda.synchronize()
+    assert P.device_status() == 0
+    RTOL, LW_RTOL = tc_tolerances(shape.n_layers)
+    ref = orc.flow_sample(shape, w, -4.0, 6.0, 4, seed=11, counter0=0, bf16_mask=TC_MODE)
+    assert_sites_close(out.phi.cpu().numpy(), ref["phi"], rtol=RTOL)
+    assert_logw_close(out.logw.cpu().numpy(), ref["logw"], rtol=LW_RTOL)
