@@ -658,8 +658,44 @@ def bench_tc_shapes(dev, flush, pk):
         line["bf16"]["frac_of_bf16_burst"] = line["bf16"]["tflops"] / pk["bf16_tflops"]
         line["speedup_vs_fused_fp32"] = line["bf16"]["configs_per_s"] / line["fp32"]["configs_per_s"]
         res[name] = line
+    res["trained_2d_equal_acceptance"] = trained_2d_acceptance()
     assert P.device_status() == 0
     return res
+
+
+def trained_2d_acceptance(n=65536):
+    """Equal acceptance of the second tensor-core kernel: a 2D L=16 flow
+    (12 couplings, hidden 16, m2=-4, lam=8) trained here with the reverse-KL
+    step (3,000 Adam steps at batch 64, lr 1e-3, model seed 2021), then the
+    tensor-core and fused FP32 samplers on the same n proposals (same prior
+    counters and MH uniforms): acceptance with binomial errors, ESS, tau_int
+    of |M|, decision agreement and each sampler's configs/s over the run."""
+    import torch
+    import paper_2208_08903_gb300 as P
+    from paper_2208_08903_gb300 import train as T
+    shape = gi.FlowShape(2, 16, 12, 16, 16)
+    phi4 = (-4.0, 8.0)
+    flow = P.Flow(shape, gi.init_weights(shape, seed=2021))
+    t0 = time.perf_counter()
+    st = T.train(flow, phi4, 30, 100, 64, lr=1e-3, seed=4242)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    tc = P.Flow(shape, flow.get_weights().double().cpu().numpy(), precision="bf16")
+    for f in (flow, tc):               # first launches outside the timed runs
+        T.evaluate(f, phi4, 4096, 4096, seed=1, sampler="fused")
+    ev = {k: T.evaluate(f, phi4, n, 4096, seed=909, sampler="fused", keep_logw=True)
+          for k, f in (("fp32", flow), ("tensor_core", tc))}
+    out = {"flow": "2D L=16, 12 couplings, hidden 16, m2=-4, lam=8; 3,000 reverse-KL Adam steps at batch 64 "
+                   f"({train_s:.1f} s), final loss {st.losses[-1]:.3f}",
+           "proposals": n}
+    for k, e in ev.items():
+        out[k] = {"acceptance": e["acceptance"], "acceptance_binomial_err": e["acceptance_binomial_err"],
+                  "ess": e["ess"], "tau_int_abs_M": e["tau_int_abs_M"], "tau_int_err": e["tau_int_err"],
+                  "configs_per_s_incl_mh_observables": n / e["seconds"]}
+    se = float(np.hypot(ev["fp32"]["acceptance_binomial_err"], ev["tensor_core"]["acceptance_binomial_err"]))
+    out["acceptance_difference_sigma"] = (ev["tensor_core"]["acceptance"] - ev["fp32"]["acceptance"]) / max(se, 1e-300)
+    out["decisions_same"] = T.decision_agreement(ev["tensor_core"], ev["fp32"])
+    return out
 
 
 def trained_acceptance(shape, phi4, n=32768):
@@ -671,6 +707,8 @@ def trained_acceptance(shape, phi4, n=32768):
     f32 = P.Flow(shape, w)
     arms = {"tensor_core": (P.Flow(shape, w, precision="bf16"), "fused"), "fused_fp32": (f32, "fused"),
             "plain_fp32": (f32, "unfused")}
+    for f, kind in arms.values():      # first launches (module loading, attributes) outside the timed runs
+        T.evaluate(f, phi4, 4096, 4096, seed=1, sampler=kind)
     ev = {k: T.evaluate(f, phi4, n, 4096, seed=12347, sampler=kind, keep_logw=True) for k, (f, kind) in arms.items()}
     res = {"checkpoint": "checkpoints/c3_L16_16layers_15k.npz (15,000 reverse-KL Adam steps, batch 64)",
            "proposals": n}
