@@ -182,33 +182,44 @@ __device__ __forceinline__ void pos_xyz(int p, int P, int PP, FastDiv fdP, FastD
 // channels per thread, BF16, at the site's padded position and its periodic
 // images.  Sites are ordered (parity, site), so a warp holds one site parity
 // and the live taps (those that reach frozen sites) are the same for the
-// whole warp; the weight loads are broadcasts.  Site j of parity q (rows y + L z
-// in order, x fastest in a row): x = 2 (j mod L/2) + ((q + y + z) mod 2).
-template <int ND, int CP>
+// whole warp; the weight loads are broadcasts.  A thread takes NS sites of
+// one parity (j and j + V/(2 NS)), so each weight load feeds NS sites.  Site
+// j of parity q (rows y + L z in order, x fastest in a row): x = 2 (j mod
+// L/2) + ((q + y + z) mod 2).
+template <int ND, int CP, int NS>
 __device__ void tc_conv1(const TcGeom& g, const float* wf, const float* x, int frozen, float slope,
                          unsigned char* act, int t0, int nthr) {
     constexpr int NKG = CP / 8;
-    const int L = g.L, half = g.V >> 1, Lh = L >> 1, P = g.P, npos = g.npos;
+    const int L = g.L, half = g.V >> 1, per = half / NS, Lh = L >> 1, P = g.P, npos = g.npos;
     const float* W1 = wf + g.wf_W1;
     const float* b1 = wf + g.wf_b1;
-    for (int it = t0; it < 2 * half; it += nthr) {
-        const int q = it >= half ? 1 : 0, j = it - q * half;
-        const int r = fdiv(j, g.fd_Lh), xh = j - r * Lh;
-        const int zc = ND == 3 ? fdiv(r, g.fd_L) : 0, yc = r - zc * L;
-        const int xc = 2 * xh + ((q ^ yc ^ zc) & 1);
-        float acc[CP];
+    for (int it = t0; it < 2 * per; it += nthr) {
+        const int q = it >= per ? 1 : 0, j0 = it - q * per;
+        int xc[NS], yc[NS], zc[NS], xs[NS][3], ys[NS][3], zs[NS][3];
+#pragma unroll
+        for (int n = 0; n < NS; ++n) {
+            const int j = j0 + n * per;
+            const int r = fdiv(j, g.fd_Lh), xh = j - r * Lh;
+            zc[n] = ND == 3 ? fdiv(r, g.fd_L) : 0;
+            yc[n] = r - zc[n] * L;
+            xc[n] = 2 * xh + ((q ^ yc[n] ^ zc[n]) & 1);
+            xs[n][0] = wrapc(xc[n] - 1, L); xs[n][1] = xc[n]; xs[n][2] = wrapc(xc[n] + 1, L);
+            ys[n][0] = wrapc(yc[n] - 1, L) * L; ys[n][1] = yc[n] * L; ys[n][2] = wrapc(yc[n] + 1, L) * L;
+            zs[n][0] = zs[n][1] = zs[n][2] = 0;
+            if (ND == 3) {
+                zs[n][0] = wrapc(zc[n] - 1, L) * L * L;
+                zs[n][1] = zc[n] * L * L;
+                zs[n][2] = wrapc(zc[n] + 1, L) * L * L;
+            }
+        }
+        float acc[NS][CP];
 #pragma unroll
         for (int c4 = 0; c4 < CP / 4; ++c4) {
             const float4 b = *reinterpret_cast<const float4*>(b1 + 4 * c4);
-            acc[4 * c4] = b.x; acc[4 * c4 + 1] = b.y; acc[4 * c4 + 2] = b.z; acc[4 * c4 + 3] = b.w;
-        }
-        const int xs[3] = {wrapc(xc - 1, L), xc, wrapc(xc + 1, L)};
-        const int ys[3] = {wrapc(yc - 1, L) * L, yc * L, wrapc(yc + 1, L) * L};
-        int zs[3] = {0, 0, 0};
-        if (ND == 3) {
-            zs[0] = wrapc(zc - 1, L) * L * L;
-            zs[1] = zc * L * L;
-            zs[2] = wrapc(zc + 1, L) * L * L;
+#pragma unroll
+            for (int n = 0; n < NS; ++n) {
+                acc[n][4 * c4] = b.x; acc[n][4 * c4 + 1] = b.y; acc[n][4 * c4 + 2] = b.z; acc[n][4 * c4 + 3] = b.w;
+            }
         }
 #pragma unroll
         for (int dz = 0; dz < (ND == 3 ? 3 : 1); ++dz) {
@@ -220,46 +231,52 @@ __device__ void tc_conv1(const TcGeom& g, const float* wf, const float* x, int f
                     const int po = ND == 3 ? ((dx + dy + dz + 1) & 1) : ((dx + dy) & 1);
                     if ((q ^ po) != frozen) continue;
                     const int t = ND == 3 ? (dz * 3 + dy) * 3 + dx : dy * 3 + dx;
-                    const float v = x[zs[dz] + ys[dy] + xs[dx]];
+                    float v[NS];
+#pragma unroll
+                    for (int n = 0; n < NS; ++n) v[n] = x[zs[n][dz] + ys[n][dy] + xs[n][dx]];
                     const float4* w = reinterpret_cast<const float4*>(W1 + t * CP);
 #pragma unroll
                     for (int c4 = 0; c4 < CP / 4; ++c4) {
                         const float4 ww = w[c4];
-                        acc[4 * c4] = fmaf(v, ww.x, acc[4 * c4]);
-                        acc[4 * c4 + 1] = fmaf(v, ww.y, acc[4 * c4 + 1]);
-                        acc[4 * c4 + 2] = fmaf(v, ww.z, acc[4 * c4 + 2]);
-                        acc[4 * c4 + 3] = fmaf(v, ww.w, acc[4 * c4 + 3]);
+#pragma unroll
+                        for (int n = 0; n < NS; ++n) {
+                            acc[n][4 * c4] = fmaf(v[n], ww.x, acc[n][4 * c4]);
+                            acc[n][4 * c4 + 1] = fmaf(v[n], ww.y, acc[n][4 * c4 + 1]);
+                            acc[n][4 * c4 + 2] = fmaf(v[n], ww.z, acc[n][4 * c4 + 2]);
+                            acc[n][4 * c4 + 3] = fmaf(v[n], ww.w, acc[n][4 * c4 + 3]);
+                        }
                     }
                 }
             }
         }
 #pragma unroll
-        for (int c = 0; c < CP; ++c) acc[c] = lrelu_tc(acc[c], slope);
-        // padded coordinates of the site and of its periodic images (a site on
-        // the first or last row of an axis is also the halo beyond the other end)
-        int xo[2], yo[2], zo[2], nx = 1, ny = 1, nz = 1;
-        xo[0] = xc + 1;
-        if (xc == 0) xo[nx++] = L + 1; else if (xc == L - 1) xo[nx++] = 0;
-        yo[0] = (yc + 1) * P;
-        if (yc == 0) yo[ny++] = (L + 1) * P; else if (yc == L - 1) yo[ny++] = 0;
-        zo[0] = ND == 3 ? (zc + 1) * P * P : 0;
-        if (ND == 3) {
-            if (zc == 0) zo[nz++] = (L + 1) * P * P; else if (zc == L - 1) zo[nz++] = 0;
-        }
+        for (int n = 0; n < NS; ++n) {
 #pragma unroll
-        for (int kg = 0; kg < NKG; ++kg) {
-            const uint4 w = pack_bf16x8(acc + 8 * kg);
-            unsigned char* base = act + (size_t)kg * npos * 16;
-            for (int iz = 0; iz < nz; ++iz)
-                for (int iy = 0; iy < ny; ++iy)
-                    for (int ix = 0; ix < nx; ++ix)
-                        *reinterpret_cast<uint4*>(base + (size_t)(xo[ix] + yo[iy] + zo[iz]) * 16) = w;
+            for (int c = 0; c < CP; ++c) acc[n][c] = lrelu_tc(acc[n][c], slope);
+            // padded coordinates of the site and of its periodic images (a site on
+            // the first or last row of an axis is also the halo beyond the other end)
+            int xo[2], yo[2], zo[2], nx = 1, ny = 1, nz = 1;
+            xo[0] = xc[n] + 1;
+            if (xc[n] == 0) xo[nx++] = L + 1; else if (xc[n] == L - 1) xo[nx++] = 0;
+            yo[0] = (yc[n] + 1) * P;
+            if (yc[n] == 0) yo[ny++] = (L + 1) * P; else if (yc[n] == L - 1) yo[ny++] = 0;
+            zo[0] = ND == 3 ? (zc[n] + 1) * P * P : 0;
+            if (ND == 3) {
+                if (zc[n] == 0) zo[nz++] = (L + 1) * P * P; else if (zc[n] == L - 1) zo[nz++] = 0;
+            }
+#pragma unroll
+            for (int kg = 0; kg < NKG; ++kg) {
+                const uint4 w = pack_bf16x8(acc[n] + 8 * kg);
+                unsigned char* base = act + (size_t)kg * npos * 16;
+                for (int iz = 0; iz < nz; ++iz)
+                    for (int iy = 0; iy < ny; ++iy)
+                        for (int ix = 0; ix < nx; ++ix)
+                            *reinterpret_cast<uint4*>(base + (size_t)(xo[ix] + yo[iy] + zo[iz]) * 16) = w;
+            }
         }
     }
 }
 
-// The periodic images of h2: every halo position of the padded lattice gets
-// the channel groups of its interior source site.
 template <int ND, int CP>
 __device__ void tc_halo(const TcGeom& g, unsigned char* act, int t0, int nthr) {
     constexpr int NKG = CP / 8;
@@ -486,7 +503,7 @@ __global__ void __launch_bounds__(kTcThreads * H, 1) flow_tc_kernel(const TcArgs
             // ---- conv1 -> h1 (BF16, padded, with periodic images)
             if (tc_wait(bar_wf + (step & 1), step >> 1, abort_flag, a.status)) {
                 if (tid == 0 && step + 1 < total_steps) stage_wf(step + 1);
-                tc_conv1<ND, CP>(g, wf, x, frozen, a.slope, act, tid, kTcThreads);
+                tc_conv1<ND, CP, ND == 3 ? 2 : 1>(g, wf, x, frozen, a.slope, act, tid, kTcThreads);
             }
             fence_proxy_async();
             half_sync();
