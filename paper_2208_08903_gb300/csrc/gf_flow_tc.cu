@@ -56,6 +56,7 @@
 // copies.
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -74,9 +75,7 @@ constexpr int kTcOut = 96;                // output positions per tile (6 of eve
 constexpr int kTcRing = 8;                // TMEM accumulators per epilogue group (at most)
 constexpr int kTcMaxTiles = 64;           // tiles per layer (one completion barrier each)
 constexpr long long kTcWaitLimit = 1ll << 22;
-constexpr int kSmemPerSM = 233472;        // 228 KB of shared memory per SM
 constexpr int kSmemPerCTA = 232448;       // 227 KB opt-in maximum per CTA
-constexpr int kSmemReserve = 1024;        // reserved per resident CTA
 
 // n / d as (n * m) >> k, exact for 0 <= n < 2^24 and 1 <= d < 2^12
 // (m = ceil(2^k / d) with k = 24 + ceil(log2 d): the round-up reciprocal of
@@ -810,16 +809,28 @@ gf_status launch_tc(TcArgs& a, cudaStream_t stream) {
     TcGeom& g = a.g;
     const size_t smem = (size_t)H * g.half_bytes;
     if (smem > (size_t)kSmemPerCTA) return GF_EUNSUPPORTED;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-        return GF_ECUDA;
-    // TMEM: the runtime places one CTA of a tcgen05 kernel per SM; its H
-    // halves share the 512 columns, each needing two conv2 accumulators of
-    // 3 Cp columns (one per epilogue group)
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTcThreads * H, smem) != cudaSuccess ||
-        per_sm < 1)
-        return GF_ECUDA;
-    if (per_sm > 1) return GF_EUNSUPPORTED;      // the TMEM split assumes one CTA per SM
+    // once per device and instantiation: the shared-memory limit, and the
+    // check that the runtime places one CTA of this tcgen05 kernel per SM (its
+    // H halves share the SM's 512 TMEM columns, each needing two conv2
+    // accumulators of 3 Cp columns, one per epilogue group)
+    static std::mutex mu;
+    static int checked[64] = {0};   // 0: not yet, 1: ok, -1: more than one CTA per SM
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return GF_EUNSUPPORTED;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (checked[dev] == 0) {
+            int per_sm = 0;
+            if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemPerCTA) != cudaSuccess ||
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTcThreads * H, kSmemPerCTA / 2) !=
+                    cudaSuccess ||
+                per_sm < 1)
+                return GF_ECUDA;
+            checked[dev] = per_sm > 1 ? -1 : 1;
+        }
+        if (checked[dev] < 0) return GF_EUNSUPPORTED;
+    }
     g.tmem_cols = 512 / H;
     g.nbuf2 = std::min(kTcRing, g.tmem_cols / (2 * 3 * CP));
     g.nbuf3 = std::min(kTcRing, g.tmem_cols / (2 * 16));
