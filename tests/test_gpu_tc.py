@@ -226,3 +226,25 @@ def test_tc_wait_that_runs_out_reports_timeout_and_recovers(orc, B):
     ref = orc.flow_sample(shape, w, -4.0, 6.0, 4, seed=11, counter0=0, bf16_mask=TC_MODE)
     assert_sites_close(out.phi.cpu().numpy(), ref["phi"], rtol=RTOL)
     assert_logw_close(out.logw.cpu().numpy(), ref["logw"], rtol=LW_RTOL)
+
+
+def test_tc_odd_batch(orc):
+    """An odd batch larger than the SM count: the last block's second half has
+    one configuration fewer than its first (it leaves its loop early and
+    meets the other half only at the block's exit)."""
+    torch, P = require_gpu()
+    shape = gi.FlowShape(2, 32, 2, 24, 24)
+    m2, lam = -4.0, 6.0
+    w = gi.init_weights(shape, seed=8)
+    flow = P.Flow(shape, w, precision="bf16")
+    B = 333
+    out = flow.sample(B, seed=2, counter0=0, phi4=(m2, lam))
+    torch.cuda.synchronize()
+    assert P.device_status() == 0
+    RTOL, LW_RTOL = tc_tolerances(shape.n_layers)
+    for b in (0, 165, B - 1):
+        ref = orc.flow_sample(shape, w, m2, lam, 1, seed=2, counter0=b, bf16_mask=TC_MODE)
+        assert_sites_close(out.phi[b:b + 1].cpu().numpy(), ref["phi"], rtol=RTOL, what=f"phi[{b}]")
+        assert_logw_close(out.logw[b:b + 1].cpu().numpy(), ref["logw"], rtol=LW_RTOL, what=f"logw[{b}]")
+        one = flow.sample(1, seed=2, counter0=b, phi4=(m2, lam))
+        assert torch.equal(one.phi[0], out.phi[b]) and torch.equal(one.logw[0], out.logw[b])
