@@ -502,7 +502,7 @@ __global__ void __launch_bounds__(kTcThreads * H, 1) flow_tc_kernel(const TcArgs
             // ---- conv1 -> h1 (BF16, padded, with periodic images)
             if (tc_wait(bar_wf + (step & 1), step >> 1, abort_flag, a.status)) {
                 if (tid == 0 && step + 1 < total_steps) stage_wf(step + 1);
-                tc_conv1<ND, CP, ND == 3 ? 2 : 1>(g, wf, x, frozen, a.slope, act, tid, kTcThreads);
+                tc_conv1<ND, CP, (ND == 3 || H == 1) ? 2 : 1>(g, wf, x, frozen, a.slope, act, tid, kTcThreads);
             }
             fence_proxy_async();
             half_sync();
