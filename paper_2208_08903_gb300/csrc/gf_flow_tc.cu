@@ -17,7 +17,10 @@
 // action and log w.  |h2| must stay below 65504: a non-finite s or t records
 // GF_EDEVICE.
 //
-// Per CTA one configuration at a time (persistent grid).  The activations
+// Persistent grid of one CTA per SM (the runtime places one CTA of a tcgen05
+// kernel on an SM); a CTA runs one configuration at a time, or on 2D
+// lattices two, one per half of its warps, each half with its own shared
+// memory, TMEM columns and barriers (see flow_tc_kernel).  The activations
 // live in a zero-padded copy of the lattice, one halo layer per axis holding
 // the periodic images: P = L + 2 positions per axis, x fastest, stored
 // channel-group major [Cp/8][position][8 channels] so that 8 consecutive
@@ -32,8 +35,8 @@
 // rows of a tile are 16 core matrices of 8 consecutive positions, each 6
 // positions after the previous one, so rows 1..6 of every 8 are outputs (96
 // per tile, positions on the halo dropped) whose x-neighbours are in the same
-// 8 TMEM lanes (width-8 shuffles).  Per layer, with a CTA barrier between
-// the phases:
+// 8 TMEM lanes (width-8 shuffles).  Per layer, with a barrier of the
+// configuration's warps between the phases:
 //   conv1 (all warps): h1 = LReLU(W1 * masked x + b1) at every site, BF16, at
 //     its padded position and at its periodic images;
 //   conv2 (two issuing threads on different sub-partitions, alternate tiles):
