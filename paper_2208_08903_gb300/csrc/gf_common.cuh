@@ -166,30 +166,70 @@ constexpr double LOG_2PI = 1.8378770664093454835606594728112;
 // Periodic neighbour wrap for |offset| <= L.
 __device__ __forceinline__ int wrap_site(int v, int L) { return v < 0 ? v + L : (v >= L ? v - L : v); }
 
-// Sum over mu of (2 phi(n) - phi(n+mu) - phi(n-mu)), i.e. minus the lattice
-// Laplacian of the paper's action (Sec. 1), in FP64 on a periodic lattice,
-// site n = x + L (y + L z); fields of any element type (widened exactly).
-template <typename T>
-__device__ __forceinline__ double lap_minus(const T* p, int n, int nd, int L) {
+// The 2 nd periodic neighbours of site n = x + L (y + L z) (x fastest).
+struct SiteNbrs {
+    int xp, xm, yp, ym, zp, zm;
+};
+__device__ __forceinline__ SiteNbrs site_nbrs(int n, int nd, int L) {
     const int xc = n % L, yc = (n / L) % L;
-    const double c = (double)p[n];
-    double k = 2.0 * c - (double)p[n - xc + wrap_site(xc + 1, L)] - (double)p[n - xc + wrap_site(xc - 1, L)];
-    k += 2.0 * c - (double)p[n + (wrap_site(yc + 1, L) - yc) * L] - (double)p[n + (wrap_site(yc - 1, L) - yc) * L];
+    SiteNbrs b;
+    b.xp = n - xc + wrap_site(xc + 1, L);
+    b.xm = n - xc + wrap_site(xc - 1, L);
+    b.yp = n + (wrap_site(yc + 1, L) - yc) * L;
+    b.ym = n + (wrap_site(yc - 1, L) - yc) * L;
+    b.zp = b.zm = n;
     if (nd == 3) {
         const int zc = n / (L * L), LL = L * L;
-        k += 2.0 * c - (double)p[n + (wrap_site(zc + 1, L) - zc) * LL] -
-             (double)p[n + (wrap_site(zc - 1, L) - zc) * LL];
+        b.zp = n + (wrap_site(zc + 1, L) - zc) * LL;
+        b.zm = n + (wrap_site(zc - 1, L) - zc) * LL;
     }
+    return b;
+}
+// The same for L = 2^lg with bit operations only.
+__device__ __forceinline__ SiteNbrs site_nbrs_pow2(int n, int nd, int lg) {
+    const int m = (1 << lg) - 1;
+    const int xc = n & m, yc = (n >> lg) & m;
+    SiteNbrs b;
+    b.xp = n - xc + ((xc + 1) & m);
+    b.xm = n - xc + ((xc - 1) & m);
+    b.yp = n + ((((yc + 1) & m) - yc) << lg);
+    b.ym = n + ((((yc - 1) & m) - yc) << lg);
+    b.zp = b.zm = n;
+    if (nd == 3) {
+        const int zc = n >> (2 * lg);
+        b.zp = n + ((((zc + 1) & m) - zc) << (2 * lg));
+        b.zm = n + ((((zc - 1) & m) - zc) << (2 * lg));
+    }
+    return b;
+}
+
+// Sum over mu of (2 phi(n) - phi(n+mu) - phi(n-mu)), i.e. minus the lattice
+// Laplacian of the paper's action (Sec. 1), in FP64 on a periodic lattice;
+// fields of any element type (widened exactly).
+template <typename T>
+__device__ __forceinline__ double lap_minus_at(const T* p, int n, int nd, const SiteNbrs& b) {
+    const double c = (double)p[n];
+    double k = 2.0 * c - (double)p[b.xp] - (double)p[b.xm];
+    k += 2.0 * c - (double)p[b.yp] - (double)p[b.ym];
+    if (nd == 3) k += 2.0 * c - (double)p[b.zp] - (double)p[b.zm];
     return k;
+}
+template <typename T>
+__device__ __forceinline__ double lap_minus(const T* p, int n, int nd, int L) {
+    return lap_minus_at(p, n, nd, site_nbrs(n, nd, L));
 }
 
 // The force dS/dphi(n) = 2 sum_mu (2 phi - phi(n+mu) - phi(n-mu)) + 2 m2 phi
 // + 4 lam phi^3 in FP64: the one definition used by gf_phi4_force, the action
 // VJP, the HMC kicks and the training reverse pass's seed.
 template <typename T>
-__device__ __forceinline__ double phi4_force_site(const T* p, int n, int nd, int L, double m2, double lam) {
+__device__ __forceinline__ double phi4_force_at(const T* p, int n, int nd, const SiteNbrs& b, double m2, double lam) {
     const double c = (double)p[n];
-    return 2.0 * lap_minus(p, n, nd, L) + 2.0 * m2 * c + 4.0 * lam * c * c * c;
+    return 2.0 * lap_minus_at(p, n, nd, b) + 2.0 * m2 * c + 4.0 * lam * c * c * c;
+}
+template <typename T>
+__device__ __forceinline__ double phi4_force_site(const T* p, int n, int nd, int L, double m2, double lam) {
+    return phi4_force_at(p, n, nd, site_nbrs(n, nd, L), m2, lam);
 }
 
 // phi^4 action (paper Sec. 1) of one configuration held in shared memory,

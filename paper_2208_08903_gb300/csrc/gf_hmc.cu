@@ -15,11 +15,15 @@ namespace {
 constexpr int kHmcThreads = 256;
 constexpr int kMaxSitesPerThread = 16;    // V <= 4096
 
-__global__ void __launch_bounds__(kHmcThreads) hmc_kernel(int nd, int L, int V, double m2, double lam,
+// POW2: L = 2^lg, neighbour indices by bit operations instead of runtime
+// divisions.
+template <bool POW2>
+__global__ void __launch_bounds__(kHmcThreads) hmc_kernel(int nd, int L, int lg, int V, double m2, double lam,
                                                           int64_t n_chains, double* __restrict__ phi_g,
                                                           int n_steps, double eps, uint64_t seed,
                                                           uint64_t traj, double* __restrict__ dH_out,
                                                           uint8_t* __restrict__ acc_out) {
+    const auto nbrs = [&](int n) { return POW2 ? site_nbrs_pow2(n, nd, lg) : site_nbrs(n, nd, L); };
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double* p = reinterpret_cast<double*>(smem_raw);
     double* red = p + V;
@@ -48,7 +52,7 @@ __global__ void __launch_bounds__(kHmcThreads) hmc_kernel(int nd, int L, int V, 
                 const int n = threadIdx.x + k * blockDim.x;
                 if (k < nper && n < V) {
                     const double f = p[n], f2 = f * f;
-                    h += 0.5 * pi[k] * pi[k] + f * lap_minus(p, n, nd, L) + m2 * f2 + lam * f2 * f2;
+                    h += 0.5 * pi[k] * pi[k] + f * lap_minus_at(p, n, nd, nbrs(n)) + m2 * f2 + lam * f2 * f2;
                 }
             }
             return block_sum(h, red);
@@ -57,7 +61,7 @@ __global__ void __launch_bounds__(kHmcThreads) hmc_kernel(int nd, int L, int V, 
 #pragma unroll
             for (int k = 0; k < kMaxSitesPerThread; ++k) {
                 const int n = threadIdx.x + k * blockDim.x;
-                if (k < nper && n < V) pi[k] -= h * phi4_force_site(p, n, nd, L, m2, lam);
+                if (k < nper && n < V) pi[k] -= h * phi4_force_at(p, n, nd, nbrs(n), m2, lam);
             }
         };
         const double H0 = energy();
@@ -103,16 +107,19 @@ extern "C" gf_status gf_hmc_trajectory(int32_t nd, int32_t L, const gf_phi4* phi
     if (n_chains == 0) return GF_OK;
     if (!d_phi) return GF_EINVAL;
     const size_t smem = (size_t)V * 8 + 32 * 8;
-    if (cudaFuncSetAttribute(hmc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    int lg = 0;
+    while ((1 << lg) < L) ++lg;
+    const bool pow2 = (1 << lg) == L;
+    auto kern = pow2 ? hmc_kernel<true> : hmc_kernel<false>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return GF_ECUDA;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hmc_kernel, kHmcThreads, smem) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kHmcThreads, smem) != cudaSuccess ||
         per_sm < 1)
         per_sm = 1;
     const int64_t grid = std::min<int64_t>(n_chains, (int64_t)num_sms() * per_sm);
-    hmc_kernel<<<(unsigned)grid, kHmcThreads, smem, stream>>>(nd, L, (int)V, phi4->m2, phi4->lam, n_chains,
-                                                              d_phi, n_steps, eps, seed, traj_index,
-                                                              d_dH_out, d_acc_out);
+    kern<<<(unsigned)grid, kHmcThreads, smem, stream>>>(nd, L, lg, (int)V, phi4->m2, phi4->lam, n_chains, d_phi,
+                                                        n_steps, eps, seed, traj_index, d_dH_out, d_acc_out);
     GF_CHECK_LAUNCH();
     return GF_OK;
 }

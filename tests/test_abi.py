@@ -104,9 +104,10 @@ def test_product_path_has_no_oracle_dependency():
 
 
 def test_force_is_defined_once():
-    """dS/dphi has one device definition (gf_common.cuh: phi4_force_site),
-    used by gf_phi4_force, the action VJP, the HMC kicks and the training
-    reverse pass; no kernel file writes the force formula itself."""
+    """dS/dphi has one device definition (gf_common.cuh: phi4_force_at, and
+    phi4_force_site that finds the neighbours first), used by gf_phi4_force,
+    the action VJP, the HMC kicks and the training reverse pass; no kernel file
+    writes the force formula itself."""
     csrc = os.path.join(ROOT, "paper_2208_08903_gb300", "csrc")
     users = 0
     for fn in os.listdir(csrc):
@@ -115,7 +116,7 @@ def test_force_is_defined_once():
             assert src.count("4.0 * lam * c * c * c") == 1
             continue
         assert "4.0 * lam" not in src, fn
-        users += "phi4_force_site(" in src
+        users += "phi4_force_site(" in src or "phi4_force_at(" in src
     assert users >= 3
 
 
