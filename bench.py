@@ -637,7 +637,9 @@ def bench_tc_shapes(dev, flush, pk):
              ("2D L=64, 16 couplings, hidden 16", gi.FlowShape(2, 64, 16, 16, 16), 4096),
              ("2D L=16, 16 couplings, hidden 24", gi.FlowShape(2, 16, 16, 24, 24), 16384),
              ("3D L=8, 16 couplings, hidden 32", gi.FlowShape(3, 8, 16, 32, 32), 8192),
-             ("3D L=12, 16 couplings, hidden 16", gi.FlowShape(3, 12, 16, 16, 16), 4096)]
+             ("3D L=12, 16 couplings, hidden 16", gi.FlowShape(3, 12, 16, 16, 16), 4096),
+             ("2D L=32, 16 couplings, hidden 8 (padded to 16)", gi.FlowShape(2, 32, 16, 8, 8), 8192),
+             ("3D L=16, 16 couplings, hidden 8 (padded to 16)", gi.FlowShape(3, 16, 16, 8, 8), 4096)]
     phi4 = (-4.0, 6.0)
     res = {"theory": "m2=-4, lam=6, random-init weights seed 0", "peak_tflops": pk["bf16_tflops"]}
     for name, shape, B in cases:
@@ -802,7 +804,7 @@ def bench_serving(dev, n_requests=120, rate=200.0, n_models=16, seed=5):
 
     out = {"mix": "2D L in {8,16,32,64}, 3D L in {8,12,16}, 12-24 couplings, hidden {8,16,24,32}, "
                   "batch 64-8192 log-uniform; tensor-core kernels where gf_flow_tensor_core_supported "
-                  "(hidden 16-32 whose activations fit a block), FP32 kernels otherwise",
+                  "(activations that fit a block), FP32 kernels otherwise",
            "precision_by_model": {name: ("bf16" if P.tensor_core_supported(shape) else "fp32")
                                   for name, shape, _ in specs},
            "models": n_models, "requests_per_load": n_requests,

@@ -1,9 +1,9 @@
 // gf_flow_tc.cu -- fused coupling stack with conv2 and the conv3 head on the
 // tensor cores (tcgen05, 16-bit operands, FP32 accumulation in TMEM) for the
 // lattice shapes other than 3D L=16 with hidden width 32 (which has its own
-// kernel): 2D and 3D, even L, two equal hidden widths of 16, 24 or 32 channels
-// (24 padded to 32 with zero weights), kernel size 3, while the lattice's
-// activations fit in shared memory.
+// kernel): 2D and 3D, even L, two equal hidden widths of 8, 16, 24 or 32
+// channels (8 padded to 16 and 24 to 32 with zero weights), kernel size 3,
+// while the lattice's activations fit in shared memory.
 //
 // Paper arXiv:2208.08903 Sec. 1 (checkerboard affine coupling layers, their
 // Jacobian, the model density and the action).  Precision: conv2, the dense
@@ -758,7 +758,9 @@ bool tc_plan(const gf_flow_shape& s, TcGeom& g) {
     if (s.nd != 2 && s.nd != 3) return false;
     if (s.ksize != 3 || s.c_hidden1 != s.c_hidden2) return false;
     const int C = s.c_hidden1;
-    if (C != 16 && C != 24 && C != 32) return false;
+    // widths 8 and 24 run as 16 and 32 with zero weights and biases in the
+    // padding channels, whose activations are then LReLU(0) = 0
+    if (C < 8 || C > 32 || C % 8 != 0) return false;
     if (s.nd == 3 && s.L == 16 && C == 32) return false;   // the dedicated 3D L=16 kernel
     if (s.L < 4 || (s.L & 1)) return false;
     g.nd = s.nd;

@@ -89,11 +89,11 @@ def drift(n_layers: int, B: int, seed: int = SEED, counter0: int = 0, nthreads=N
 
 
 # The tensor-core kernel for the other lattice shapes (2D L = 8..64, 3D L = 8,
-# 12; hidden 16, 24 or 32) rounds h1 and W2 to bf16 and h2 and W3 to FP16 and
-# keeps conv1 in FP32; its bounds take the maximum drift over these shapes
-# (serving flows have 12 to 24 coupling layers).
+# 12, 16; hidden 8, 16, 24 or 32) rounds h1 and W2 to bf16 and h2 and W3 to
+# FP16 and keeps conv1 in FP32; its bounds take the maximum drift over these
+# shapes (serving flows have 12 to 24 coupling layers).
 TC_MODE = oracle.BF16_H1 | oracle.BF16_W2 | oracle.F16_H2 | oracle.F16_W3 | oracle.F32_IO
-TC_SHAPES = ((2, 16, 24), (2, 32, 32), (2, 64, 16), (3, 8, 32), (3, 12, 16))
+TC_SHAPES = ((2, 16, 24), (2, 32, 32), (2, 64, 16), (3, 8, 32), (3, 12, 16), (2, 32, 8), (3, 16, 8))
 TC_LAYERS = (2, 8, 24)
 TC_OUT = os.path.join(HERE, "tc_tolerance.json")
 

@@ -122,9 +122,9 @@ def test_force_is_defined_once():
 
 def test_tensor_core_support_query(lib):
     """gf_flow_tensor_core_supported (host only): the shapes with a tensor-core
-    kernel are the two-equal-width networks of width 16, 24 or 32 with kernel
-    size 3 whose activations fit one block (or 3D L=16 with width 32); width 8,
-    other networks and invalid shapes answer 0."""
+    kernel are the two-equal-width networks of width 8, 16, 24 or 32 with
+    kernel size 3 whose activations fit one block (or 3D L=16 with width 32);
+    other widths and networks and invalid shapes answer 0."""
     from paper_2208_08903_gb300 import _abi
 
     def ex(nd, L, hidden, k=3):
@@ -132,9 +132,10 @@ def test_tensor_core_support_query(lib):
         return _abi.FlowShapeExC(nd, L, 12, len(hidden), hid, k, 1, 0.01)
 
     yes = [(2, 8, [16, 16]), (2, 16, [24, 24]), (2, 32, [32, 32]), (2, 64, [16, 16]), (3, 8, [32, 32]),
-           (3, 12, [16, 16]), (3, 16, [32, 32]), (3, 16, [16, 16])]
-    no = [(2, 32, [8, 8]), (2, 64, [32, 32]), (3, 12, [32, 32]), (3, 16, [24, 24]),
-          (2, 32, [16, 32]), (2, 32, [16, 16, 16]), (2, 7, [16, 16])]
+           (3, 12, [16, 16]), (3, 16, [32, 32]), (3, 16, [16, 16]), (2, 32, [8, 8]), (2, 64, [8, 8]),
+           (3, 16, [8, 8])]
+    no = [(2, 64, [32, 32]), (3, 12, [32, 32]), (3, 16, [24, 24]), (2, 32, [12, 12]), (2, 32, [4, 4]),
+          (2, 32, [40, 40]), (2, 32, [16, 32]), (2, 32, [16, 16, 16]), (2, 7, [16, 16])]
     for nd, L, h in yes:
         assert lib.gf_flow_tensor_core_supported(C.byref(ex(nd, L, h))) == 1, (nd, L, h)
     for nd, L, h in no:

@@ -112,10 +112,11 @@ def test_bf16_full_batch_sampled(orc):
 
 
 def test_bf16_rejects_other_shapes():
-    """Hidden width 8 (no dense contraction) and lattices whose activations do
-    not fit one block (2D L=64 with width 32) have no tensor-core kernel."""
+    """Hidden widths that are not multiples of 8 and lattices whose
+    activations do not fit one block (2D L=64, 3D L=12 with width 32) have no
+    tensor-core kernel."""
     torch, P = require_gpu()
-    for shape in (gi.FlowShape(3, 8, 2, 8, 8), gi.FlowShape(2, 64, 2, 32, 32)):
+    for shape in (gi.FlowShape(3, 8, 2, 12, 12), gi.FlowShape(2, 64, 2, 32, 32), gi.FlowShape(3, 12, 2, 32, 32)):
         assert not P.tensor_core_supported(shape)
         with pytest.raises(P._abi.GFError):
             P.Flow(shape, gi.init_weights(shape), precision="bf16")

@@ -23,9 +23,9 @@ def _models(P):
     from paper_2208_08903_gb300 import serving
     models = {}
     for name, shape, s in specs:
-        # the tensor-core kernels where the hidden width allows (b, c: gf_flow_tc.cu;
-        # d: the 3D L=16 kernel), FP32 for width 8 (a)
-        prec = "bf16" if P.tensor_core_supported(shape) else "fp32"
+        # the tensor-core kernels (b, c: gf_flow_tc.cu; d: the 3D L=16 kernel)
+        # next to one FP32 flow (a)
+        prec = "bf16" if name != "a" and P.tensor_core_supported(shape) else "fp32"
         models[name] = serving.Model(name, shape, P.Flow(shape, gi.init_weights(shape, seed=s), precision=prec))
     return models, {n: (sh, s) for n, sh, s in specs}
 
