@@ -132,13 +132,12 @@ gf_status gf_flow_create_ex(const gf_flow_shape_ex* shape, const double* weights
  * (host only, no device work; a null or invalid shape gives 0).  Convolutions
  * go on the tensor cores where the hidden width makes conv2 a dense
  * contraction (paper Sec. 1, the coupling layers' convolutional networks):
- * two equal hidden widths of 8, 16, 24 or 32 (8 padded to 16 and 24 to 32
- * with zero weights), ksize 3, and either 3D L=16 with width 32 (its own
- * kernel) or a lattice whose padded activations (about 2 Cp (L+2)^nd bytes,
- * Cp = 16 or 32), weights and field fit one block's 227 KB of shared memory:
- * 2D L <= 32 with any of the widths, 2D L = 64 and 3D L = 12, 16 with widths
- * 8 and 16, 3D L = 8 with any.  Width 8 pays for 16 channels on the tensor
- * cores, which still beats 8 on the FP32 pipe. */
+ * two equal hidden widths of 8, 16, 24 or 32 (24 padded to 32 with zero
+ * weights), ksize 3, and either 3D L=16 with width 32 (its own kernel) or a
+ * lattice whose padded activations (about 2 Cp (L+2)^nd bytes, Cp = 8, 16 or
+ * 32), weights and field fit one block's 227 KB of shared memory: 2D L <= 32
+ * with any of the widths, 2D L = 64 and 3D L = 12, 16 with widths 8 and 16,
+ * 3D L = 8 with any. */
 int32_t gf_flow_tensor_core_supported(const gf_flow_shape_ex* shape);
 gf_status gf_flow_destroy(gf_flow* flow);
 /* Number of canonical parameters. */

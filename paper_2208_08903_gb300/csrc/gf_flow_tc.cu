@@ -2,8 +2,8 @@
 // tensor cores (tcgen05, 16-bit operands, FP32 accumulation in TMEM) for the
 // lattice shapes other than 3D L=16 with hidden width 32 (which has its own
 // kernel): 2D and 3D, even L, two equal hidden widths of 8, 16, 24 or 32
-// channels (8 padded to 16 and 24 to 32 with zero weights), kernel size 3,
-// while the lattice's activations fit in shared memory.
+// channels (24 padded to 32 with zero weights), kernel size 3, while the
+// lattice's activations fit in shared memory.
 //
 // Paper arXiv:2208.08903 Sec. 1 (checkerboard affine coupling layers, their
 // Jacobian, the model density and the action).  Precision: conv2, the dense
@@ -28,8 +28,9 @@
 // K-major canonical layout.  A convolution is then an implicit GEMM whose A
 // operand for taps (dz,dy,*) is the same array started (dy-1) P + (dz-1) P^2
 // positions later, K = the 3^(d-1) (dz,dy) pairs x Cp channels in steps of
-// 16, and whose three x-taps are stacked along N (conv2: N = 3 Cp; head:
-// N = 16, columns 2 dx + (s, t)): each row's column block dx is the partial
+// 16 (width 8: two (dz,dy) pairs per step), and whose three x-taps are
+// stacked along N (conv2: N = 3 Cp, 32 for width 8; head: N = 16, columns
+// 2 dx + (s, t)): each row's column block dx is the partial
 // sum of tap dx at the row's own position, and the epilogue adds block 0 of
 // the row to the left, block 1 and block 2 of the row to the right.  The 128
 // rows of a tile are 16 core matrices of 8 consecutive positions, each 6
@@ -128,6 +129,19 @@ struct TcArgs {
 };
 
 __device__ __forceinline__ int wrapc(int v, int L) { return v < 0 ? v + L : (v >= L ? v - L : v); }
+
+// conv2's N, the TMEM columns of one accumulator: the three x-taps of CP
+// channels (width 8: 24, padded to 32, a multiple of 16)
+template <int CP>
+__host__ __device__ constexpr int tc_n2() { return CP == 8 ? 32 : 3 * CP; }
+
+// Width 8: the (dz, dy) tap (dz 3 + dy in 3D, dy in 2D) in half kh of
+// K-step k (issue_tile_c8), or -1 for the repeated tap's zero weights.
+__host__ __device__ inline int tc8_tap(int nd, int k, int kh) {
+    const int ta = nd == 3 ? (k < 4 ? 2 * k : 7) : k;
+    if (kh == 0 && ta == (nd == 3 ? 7 : 1) && k == (nd == 3 ? 4 : 1)) return -1;
+    return ta + kh;
+}
 __device__ __forceinline__ float lrelu_tc(float v, float a) { return v > 0.f ? v : a * v; }
 
 // Bounded wait for completion number n (0-based) of an mbarrier (phase parity
@@ -329,6 +343,25 @@ __device__ __forceinline__ void issue_tile(int first, int P, int PP, uint32_t d,
     }
 }
 
+// Width 8: one K-step of 16 takes the 8 channels of two (dz, dy) taps; the
+// descriptor's K-direction core-matrix stride (LBO) is the distance between
+// the two taps' positions: P within a z-plane (aP), P^2 - 2P from (dz, 2) to
+// (dz + 1, 0) (aQ).  The 3^(d-1) taps pair as (0,1) (2,3) (4,5) (6,7) (7,8)
+// in 3D and (0,1) (1,2) in 2D; the repeated tap (7, resp. 1) has zero
+// weights in the second pair that holds it (tc8_tap).
+template <int ND>
+__device__ __forceinline__ void issue_tile_c8(int first, int P, int PP, uint32_t d, uint64_t aP, uint64_t aQ,
+                                              uint64_t b0, uint32_t b_ks, uint32_t idesc) {
+    constexpr int NKS = ND == 3 ? 5 : 2;
+#pragma unroll
+    for (int k = 0; k < NKS; ++k) {
+        const int ta = ND == 3 ? (k < 4 ? 2 * k : 7) : k;   // first tap of the pair
+        const int dz = ND == 3 ? ta / 3 : 1, dy = ND == 3 ? ta % 3 : ta;
+        const uint64_t ad = desc_add((ND == 3 && k == 1) ? aQ : aP, (uint32_t)(first + (dy - 1) * P + (dz - 1) * PP));
+        mma_bf16(d, ad, desc_add(b0, (uint32_t)k * b_ks), idesc, k ? 1u : 0u);
+    }
+}
+
 // H halves of 12 warps each run one configuration at a time on their own
 // shared memory, TMEM columns and barriers (bar.sync 1 + half between
 // their phases), so that one half's CUDA-core phases overlap the other's
@@ -337,6 +370,7 @@ __device__ __forceinline__ void issue_tile(int first, int P, int PP, uint32_t d,
 template <int ND, int CP, bool INVERSE, int H>
 __global__ void __launch_bounds__(kTcThreads * H, 1) flow_tc_kernel(const TcArgs a) {
     constexpr int NKG = CP / 8;
+    constexpr int N2 = tc_n2<CP>();
     extern __shared__ __align__(1024) unsigned char smem_all[];
     const TcGeom& g = a.g;
     const int h = H == 1 ? 0 : (int)(threadIdx.x / kTcThreads);
@@ -447,12 +481,17 @@ __global__ void __launch_bounds__(kTcThreads * H, 1) flow_tc_kernel(const TcArgs
     }
     const uint32_t tmem = *tmem_slot0 + (uint32_t)(h * g.tmem_cols);
     // D = F32, K-major A and B, M = 128: conv2 BF16 with N = 3 CP, conv3 FP16 with N = 16
-    const uint32_t idesc2 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(3 * CP >> 3) << 17) |
+    const uint32_t idesc2 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N2 >> 3) << 17) |
                             ((uint32_t)(kTcM >> 4) << 24);
     const uint32_t idesc3 = (1u << 4) | ((16u >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
     const uint64_t a0 = smem_desc(smem_u32(act), (uint32_t)npos * 16u, 6u * 16u);
-    const uint64_t b2d = smem_desc(smem_u32(w2s), 3u * CP * 16u, 128u);   // [tp][kg][dx CP + c][8] bf16
-    const uint64_t b3d = smem_desc(smem_u32(w3s), 16u * 16u, 128u);       // [tp][kg][2 dx + j][8] fp16
+    // width 8: the two tap-pair strides (issue_tile_c8)
+    const uint64_t aP = smem_desc(smem_u32(act), (uint32_t)P * 16u, 6u * 16u);
+    const uint64_t aQ = smem_desc(smem_u32(act), (uint32_t)(PP - 2 * P) * 16u, 6u * 16u);
+    // [tp][kg][dx CP + c][8] bf16 (width 8: [pair][tap][dx 8 + c][8], N = 32)
+    const uint64_t b2d = smem_desc(smem_u32(w2s), (uint32_t)N2 * 16u, 128u);
+    // [tp][kg][2 dx + j][8] fp16 (width 8: [pair][tap][2 dx + j][8])
+    const uint64_t b3d = smem_desc(smem_u32(w3s), 16u * 16u, 128u);
     // this thread's row of a tile: position first + 6 (row >> 3) + (row & 7),
     // an output when row & 7 is in 1..6
     const int row = 32 * q + lane, roff = 6 * (row >> 3) + (row & 7);
@@ -533,9 +572,12 @@ __global__ void __launch_bounds__(kTcThreads * H, 1) flow_tc_kernel(const TcArgs
                             if (!tc_wait(empty2 + warp * kTcRing + i2, k2 - 1, abort_flag, a.status)) break;
                             fence_after_sync();
                         }
-                        issue_tile<ND, CP>(p_first - 1 + kTcOut * t, P, PP,
-                                           tmem + (uint32_t)((warp * nb2 + i2) * 3 * CP), a0, b2d, a_ks,
-                                           (uint32_t)(NKG * 3 * CP), (uint32_t)(2 * 3 * CP), idesc2);
+                        const uint32_t d2 = tmem + (uint32_t)((warp * nb2 + i2) * N2);
+                        if constexpr (CP == 8)
+                            issue_tile_c8<ND>(p_first - 1 + kTcOut * t, P, PP, d2, aP, aQ, b2d, 2u * N2, idesc2);
+                        else
+                            issue_tile<ND, CP>(p_first - 1 + kTcOut * t, P, PP, d2, a0, b2d, a_ks,
+                                               (uint32_t)(NKG * N2), (uint32_t)(2 * N2), idesc2);
                         mma_commit(full2 + warp * kTcRing + i2);
                         mma_commit(done2 + t);
                         if (++i2 == nb2) { i2 = 0; ++k2; }
@@ -550,8 +592,21 @@ __global__ void __launch_bounds__(kTcThreads * H, 1) flow_tc_kernel(const TcArgs
                     if (!(ok = tc_wait(full2 + eg * kTcRing + i2, k2, abort_flag, a.status))) break;
                     fence_after_sync();
                     // out = D_0(left) + D_1 + D_2(right) + b2, 16 channels at a time, LeakyReLU
-                    const uint32_t tcol = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((eg * nb2 + i2) * 3 * CP);
+                    const uint32_t tcol = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((eg * nb2 + i2) * N2);
                     float out[CP];
+                    if constexpr (CP == 8) {
+                        // columns dx 8 + c; 24..31 are the zero padding of N
+                        float v01[16], v2p[16];
+                        tmem_ld16(tcol, v01);
+                        tmem_ld16(tcol + 16, v2p);
+                        tmem_ld_wait();
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) {
+                            const float left = __shfl_up_sync(0xffffffffu, v01[c], 1, 8);
+                            const float right = __shfl_down_sync(0xffffffffu, v2p[c], 1, 8);
+                            out[c] = lrelu_tc(left + v01[8 + c] + right + b2[c], a.slope);
+                        }
+                    }
 #pragma unroll
                     for (int h = 0; h < CP / 16; ++h) {
                         float v0[16], v1[16], v2[16];
@@ -607,8 +662,12 @@ __global__ void __launch_bounds__(kTcThreads * H, 1) flow_tc_kernel(const TcArgs
                             if (!tc_wait(empty3 + warp * kTcRing + i3, k3 - 1, abort_flag, a.status)) break;
                             fence_after_sync();
                         }
-                        issue_tile<ND, CP>(p_first - 1 + kTcOut * t, P, PP, tmem + (uint32_t)((warp * nb3 + i3) * 16),
-                                           a0, b3d, a_ks, (uint32_t)(NKG * 16), (uint32_t)(2 * 16), idesc3);
+                        const uint32_t d3 = tmem + (uint32_t)((warp * nb3 + i3) * 16);
+                        if constexpr (CP == 8)
+                            issue_tile_c8<ND>(p_first - 1 + kTcOut * t, P, PP, d3, aP, aQ, b3d, 2u * 16u, idesc3);
+                        else
+                            issue_tile<ND, CP>(p_first - 1 + kTcOut * t, P, PP, d3, a0, b3d, a_ks,
+                                               (uint32_t)(NKG * 16), (uint32_t)(2 * 16), idesc3);
                         mma_commit(full3 + warp * kTcRing + i3);
                         if (++i3 == nb3) { i3 = 0; ++k3; }
                     }
@@ -703,7 +762,9 @@ __global__ void __launch_bounds__(kTcThreads * H, 1) flow_tc_kernel(const TcArgs
 // canonical FP32 -> per-layer block: W2 as [tp][kg][dx CP + c][8] bf16 (tap
 // (tp, dx) with tp = (dz, dy); K-major core matrices; channels >= C zero), W3
 // as [tp][kg][2 dx + j][8] fp16 (j = 0: s, 1: t; rows 6..15 zero), then FP32
-// W1 [tap][Cp], b1 [Cp], b2 [Cp], b3 [2], zero padding.
+// W1 [tap][Cp], b1 [Cp], b2 [Cp], b3 [2], zero padding.  Width 8: W2 as
+// [k][kh][dx 8 + c][8] (rows 24..31 zero) and W3 as [k][kh][2 dx + j][8], tp =
+// tc8_tap(k, kh) (zero weights where it is -1).
 __global__ void repack_tc_kernel(const float* __restrict__ canon, int64_t cstride, int n_layers, TcGeom g,
                                  unsigned char* __restrict__ out) {
     const int T = g.T, C = g.C, CP = g.Cp, NKG = CP / 8, N2 = 3 * CP;
@@ -719,7 +780,18 @@ __global__ void repack_tc_kernel(const float* __restrict__ canon, int64_t cstrid
         const float* W3 = b2 + C;                   // [o][i][t], o = 0: s, 1: t
         const float* b3 = W3 + 2LL * C * T;
         unsigned char* blk = out + (size_t)l * g.layer_bytes;
-        if (r < n2) {
+        if (CP == 8 && r < n2) {
+            const int e = (int)(r & 7), n = (int)((r >> 3) & 31), kh = (int)((r >> 8) & 1), k = (int)(r >> 9);
+            const int tp = tc8_tap(g.nd, k, kh), dx = n >> 3, c = n & 7;
+            const float v = (tp >= 0 && n < 24 && c < C && e < C) ? W2[((int64_t)c * C + e) * T + tp * 3 + dx] : 0.f;
+            reinterpret_cast<__nv_bfloat16*>(blk)[r] = __float2bfloat16_rn(v);
+        } else if (CP == 8 && r < n2 + n3) {
+            const int r3 = (int)(r - n2);
+            const int e = r3 & 7, n = (r3 >> 3) & 15, kh = (r3 >> 7) & 1, k = r3 >> 8;
+            const int tp = tc8_tap(g.nd, k, kh), dx = n >> 1, j = n & 1;
+            const float v = (tp >= 0 && n < 6 && e < C) ? W3[((int64_t)j * C + e) * T + tp * 3 + dx] : 0.f;
+            reinterpret_cast<__half*>(blk + g.w2_bytes)[r3] = __float2half_rn(v);
+        } else if (r < n2) {
             const int e = (int)(r & 7), n = (int)((r >> 3) % N2), kg = (int)((r / (8 * N2)) % NKG);
             const int tp = (int)(r / (8 * N2 * NKG)), dx = n / CP, c = n % CP, ic = kg * 8 + e;
             const int t = tp * 3 + dx;
@@ -758,15 +830,15 @@ bool tc_plan(const gf_flow_shape& s, TcGeom& g) {
     if (s.nd != 2 && s.nd != 3) return false;
     if (s.ksize != 3 || s.c_hidden1 != s.c_hidden2) return false;
     const int C = s.c_hidden1;
-    // widths 8 and 24 run as 16 and 32 with zero weights and biases in the
-    // padding channels, whose activations are then LReLU(0) = 0
+    // width 24 runs as 32 with zero weights and biases in the padding
+    // channels, whose activations are then LReLU(0) = 0
     if (C < 8 || C > 32 || C % 8 != 0) return false;
     if (s.nd == 3 && s.L == 16 && C == 32) return false;   // the dedicated 3D L=16 kernel
     if (s.L < 4 || (s.L & 1)) return false;
     g.nd = s.nd;
     g.L = s.L;
     g.C = C;
-    g.Cp = C <= 16 ? 16 : 32;
+    g.Cp = C == 8 ? 8 : (C <= 16 ? 16 : 32);
     g.V = 1;
     for (int i = 0; i < s.nd; ++i) g.V *= s.L;
     if (g.V % 64 != 0 || g.V > 65536) return false;        // V/2 a multiple of 32: parity-uniform warps
@@ -788,8 +860,14 @@ bool tc_plan(const gf_flow_shape& s, TcGeom& g) {
     g.fd_PP = make_fastdiv((uint32_t)(g.P * g.P));
     if (g.V / 2 >= 4096 || g.npos * 4 >= (1 << 24)) return false;   // FastDiv ranges
     const int NKG = g.Cp / 8;
-    g.w2_bytes = (uint32_t)(g.T / 3 * NKG * 3 * g.Cp * 16);
-    g.w3_bytes = (uint32_t)(g.T / 3 * NKG * 16 * 16);
+    if (g.Cp == 8) {
+        const int nks = s.nd == 3 ? 5 : 2;                 // K-steps of two taps (issue_tile_c8)
+        g.w2_bytes = (uint32_t)(nks * 2 * tc_n2<8>() * 16);
+        g.w3_bytes = (uint32_t)(nks * 2 * 16 * 16);
+    } else {
+        g.w2_bytes = (uint32_t)(g.T / 3 * NKG * 3 * g.Cp * 16);
+        g.w3_bytes = (uint32_t)(g.T / 3 * NKG * 16 * 16);
+    }
     g.wf_W1 = 0;
     g.wf_b1 = g.T * g.Cp;
     g.wf_b2 = g.wf_b1 + g.Cp;
@@ -817,7 +895,7 @@ gf_status launch_tc(TcArgs& a, cudaStream_t stream) {
     // once per device and instantiation: the shared-memory limit, and the
     // check that the runtime places one CTA of this tcgen05 kernel per SM (its
     // H halves share the SM's 512 TMEM columns, each needing two conv2
-    // accumulators of 3 Cp columns, one per epilogue group)
+    // accumulators of tc_n2 columns, one per epilogue group)
     static std::mutex mu;
     static int checked[64] = {0};   // 0: not yet, 1: ok, -1: more than one CTA per SM
     int dev = 0;
@@ -837,7 +915,7 @@ gf_status launch_tc(TcArgs& a, cudaStream_t stream) {
         if (checked[dev] < 0) return GF_EUNSUPPORTED;
     }
     g.tmem_cols = 512 / H;
-    g.nbuf2 = std::min(kTcRing, g.tmem_cols / (2 * 3 * CP));
+    g.nbuf2 = std::min(kTcRing, g.tmem_cols / (2 * tc_n2<CP>()));
     g.nbuf3 = std::min(kTcRing, g.tmem_cols / (2 * 16));
     if (g.nbuf2 < 1 || g.nbuf3 < 1) return GF_EUNSUPPORTED;
     const int64_t grid = std::min<int64_t>((a.B + H - 1) / H, (int64_t)num_sms());
@@ -897,13 +975,18 @@ gf_status launch_flow_tc(const gf_flow* f, bool inverse, const gf_phi4* phi4, in
     a.status = status_word(stream);
     a.stall_spins = bf16_stall_spins();
     if (!a.status) return GF_ECUDA;
-    const bool c32 = a.g.Cp == 32;
+    const bool c32 = a.g.Cp == 32, c8 = a.g.Cp == 8;
     if (f->shape.nd == 3) {
         if (c32) return inverse ? launch_tc<3, 32, true, 1>(a, stream) : launch_tc<3, 32, false, 1>(a, stream);
+        if (c8) return inverse ? launch_tc<3, 8, true, 1>(a, stream) : launch_tc<3, 8, false, 1>(a, stream);
         return inverse ? launch_tc<3, 16, true, 1>(a, stream) : launch_tc<3, 16, false, 1>(a, stream);
     }
     // 2D: two configurations per CTA where two halves' shared memory fits
     const bool two = 2 * (size_t)a.g.half_bytes <= (size_t)kSmemPerCTA && B > num_sms();
+    if (c8) {
+        if (two) return inverse ? launch_tc<2, 8, true, 2>(a, stream) : launch_tc<2, 8, false, 2>(a, stream);
+        return inverse ? launch_tc<2, 8, true, 1>(a, stream) : launch_tc<2, 8, false, 1>(a, stream);
+    }
     if (c32) {
         if (two) return inverse ? launch_tc<2, 32, true, 2>(a, stream) : launch_tc<2, 32, false, 2>(a, stream);
         return inverse ? launch_tc<2, 32, true, 1>(a, stream) : launch_tc<2, 32, false, 1>(a, stream);

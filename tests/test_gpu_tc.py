@@ -1,6 +1,6 @@
 """GPU parity of the tensor-core kernel for the lattice shapes other than 3D
 L=16 with hidden width 32 (gf_flow_tc.cu): 2D and 3D lattices, hidden widths
-8 (padded to 16), 16, 24 (padded to 32) and 32.
+8 (two taps per K-step), 16, 24 (padded to 32) and 32.
 
 The kernel rounds h1 (after LeakyReLU) and conv2's weights to bf16 and h2
 (after LeakyReLU) and the head's weights to FP16, accumulates conv2 and the
@@ -32,8 +32,9 @@ def _err(gpu, ref):
     return np.abs(gpu - ref) / scale
 
 
-# (nd, L, hidden, coupling layers, batch): one tile (2D L=8), the padded widths
-# 8 and 24, every lattice of the serving mix the kernel takes, 2 to 24 layers
+# (nd, L, hidden, coupling layers, batch): one tile (2D L=8), width 8 (two taps
+# per K-step) and the padded width 24, every lattice of the serving mix the
+# kernel takes, 2 to 24 layers
 CASES = [(2, 8, 16, 2, 3), (2, 16, 24, 8, 4), (2, 32, 32, 2, 3), (2, 32, 32, 24, 2), (2, 64, 16, 2, 2),
          (3, 8, 32, 8, 3), (3, 8, 24, 2, 3), (3, 12, 16, 2, 2), (3, 4, 32, 3, 3), (3, 16, 16, 2, 2),
          (2, 8, 8, 4, 3), (2, 32, 8, 8, 2), (3, 16, 8, 2, 2), (3, 16, 8, 23, 1)]
