@@ -65,7 +65,7 @@ def test_tc_sample_matches_emulated_oracle(orc, nd, L, c, n_layers, B):
         assert_logw_close(getattr(out, k).cpu().numpy(), ref[k], rtol=LW_RTOL, what=k)
 
 
-@pytest.mark.parametrize("nd,L,c", [(2, 32, 24), (3, 8, 16)])
+@pytest.mark.parametrize("nd,L,c", [(2, 32, 24), (3, 8, 16), (2, 16, 8), (3, 8, 8)])
 def test_tc_given_z_and_inverse(orc, nd, L, c):
     """Sampling from a given z without the action, then the inverse pass
     (gf_flow_logq) back to z and log q, against the emulating oracle."""
@@ -88,15 +88,17 @@ def test_tc_given_z_and_inverse(orc, nd, L, c):
     assert P.device_status() == 0
 
 
-def test_tc_persistent_batch_and_placement(orc):
+@pytest.mark.parametrize("c", [16, 8])
+def test_tc_persistent_batch_and_placement(orc, c):
     """A batch several times the resident grid (each block runs two
     configurations at a time and loops over many, so the TMEM rings and the
     weight staging wrap around many times): sampled configurations against
     the oracle, every configuration bit-identical to the same prior counter
     sampled in a batch of its own (one configuration per block), and the
-    inverse pass over the whole batch."""
+    inverse pass over the whole batch; hidden width 16 and 8 (two taps per
+    K-step)."""
     torch, P = require_gpu()
-    shape = gi.FlowShape(2, 16, 3, 16, 16)
+    shape = gi.FlowShape(2, 16, 3, c, c)
     m2, lam = -4.0, 6.0
     w = gi.init_weights(shape, seed=2)
     flow = P.Flow(shape, w, precision="bf16")
