@@ -639,7 +639,8 @@ def bench_tc_shapes(dev, flush, pk):
              ("3D L=8, 16 couplings, hidden 32", gi.FlowShape(3, 8, 16, 32, 32), 8192),
              ("3D L=12, 16 couplings, hidden 16", gi.FlowShape(3, 12, 16, 16, 16), 4096),
              ("2D L=32, 16 couplings, hidden 8", gi.FlowShape(2, 32, 16, 8, 8), 8192),
-             ("3D L=16, 16 couplings, hidden 8", gi.FlowShape(3, 16, 16, 8, 8), 4096)]
+             ("3D L=16, 16 couplings, hidden 8", gi.FlowShape(3, 16, 16, 8, 8), 4096),
+             ("3D L=8, 16 couplings, hidden 16", gi.FlowShape(3, 8, 16, 16, 16), 8192)]
     phi4 = (-4.0, 6.0)
     res = {"theory": "m2=-4, lam=6, random-init weights seed 0", "peak_tflops": pk["bf16_tflops"]}
     for name, shape, B in cases:

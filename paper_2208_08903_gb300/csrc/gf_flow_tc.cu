@@ -18,8 +18,9 @@
 // GF_EDEVICE.
 //
 // Persistent grid of one CTA per SM (the runtime places one CTA of a tcgen05
-// kernel on an SM); a CTA runs one configuration at a time, or on 2D
-// lattices two, one per half of its warps, each half with its own shared
+// kernel on an SM); a CTA runs one configuration at a time, or, where two
+// copies of the shared-memory plan fit (2D lattices up to L = 32, small 3D
+// lattices), two, one per half of its warps, each half with its own shared
 // memory, TMEM columns and barriers (see flow_tc_kernel).  The activations
 // live in a zero-padded copy of the lattice, one halo layer per axis holding
 // the periodic images: P = L + 2 positions per axis, x fastest, stored
@@ -544,7 +545,7 @@ __global__ void __launch_bounds__(kTcThreads * H, 1) flow_tc_kernel(const TcArgs
             // ---- conv1 -> h1 (BF16, padded, with periodic images)
             if (tc_wait(bar_wf + (step & 1), step >> 1, abort_flag, a.status)) {
                 if (tid == 0 && step + 1 < total_steps) stage_wf(step + 1);
-                tc_conv1<ND, CP, (ND == 3 || H == 1) ? 2 : 1>(g, wf, x, frozen, a.slope, act, tid, kTcThreads);
+                tc_conv1<ND, CP, H == 1 ? 2 : 1>(g, wf, x, frozen, a.slope, act, tid, kTcThreads);
             }
             fence_proxy_async();
             half_sync();
@@ -976,13 +977,18 @@ gf_status launch_flow_tc(const gf_flow* f, bool inverse, const gf_phi4* phi4, in
     a.stall_spins = bf16_stall_spins();
     if (!a.status) return GF_ECUDA;
     const bool c32 = a.g.Cp == 32, c8 = a.g.Cp == 8;
+    // two configurations per CTA where two halves' shared memory fits (every
+    // 2D lattice but the largest; 3D L = 8 with widths 8, 16 and L = 12 with 8)
+    const bool two = 2 * (size_t)a.g.half_bytes <= (size_t)kSmemPerCTA && B > num_sms();
     if (f->shape.nd == 3) {
         if (c32) return inverse ? launch_tc<3, 32, true, 1>(a, stream) : launch_tc<3, 32, false, 1>(a, stream);
-        if (c8) return inverse ? launch_tc<3, 8, true, 1>(a, stream) : launch_tc<3, 8, false, 1>(a, stream);
+        if (c8) {
+            if (two) return inverse ? launch_tc<3, 8, true, 2>(a, stream) : launch_tc<3, 8, false, 2>(a, stream);
+            return inverse ? launch_tc<3, 8, true, 1>(a, stream) : launch_tc<3, 8, false, 1>(a, stream);
+        }
+        if (two) return inverse ? launch_tc<3, 16, true, 2>(a, stream) : launch_tc<3, 16, false, 2>(a, stream);
         return inverse ? launch_tc<3, 16, true, 1>(a, stream) : launch_tc<3, 16, false, 1>(a, stream);
     }
-    // 2D: two configurations per CTA where two halves' shared memory fits
-    const bool two = 2 * (size_t)a.g.half_bytes <= (size_t)kSmemPerCTA && B > num_sms();
     if (c8) {
         if (two) return inverse ? launch_tc<2, 8, true, 2>(a, stream) : launch_tc<2, 8, false, 2>(a, stream);
         return inverse ? launch_tc<2, 8, true, 1>(a, stream) : launch_tc<2, 8, false, 1>(a, stream);

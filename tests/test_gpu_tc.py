@@ -88,17 +88,17 @@ def test_tc_given_z_and_inverse(orc, nd, L, c):
     assert P.device_status() == 0
 
 
-@pytest.mark.parametrize("c", [16, 8])
-def test_tc_persistent_batch_and_placement(orc, c):
+@pytest.mark.parametrize("nd,L,c", [(2, 16, 16), (2, 16, 8), (3, 8, 16), (3, 8, 8)])
+def test_tc_persistent_batch_and_placement(orc, nd, L, c):
     """A batch several times the resident grid (each block runs two
     configurations at a time and loops over many, so the TMEM rings and the
     weight staging wrap around many times): sampled configurations against
     the oracle, every configuration bit-identical to the same prior counter
     sampled in a batch of its own (one configuration per block), and the
-    inverse pass over the whole batch; hidden width 16 and 8 (two taps per
-    K-step)."""
+    inverse pass over the whole batch; 2D and 3D, hidden width 16 and 8 (two
+    taps per K-step)."""
     torch, P = require_gpu()
-    shape = gi.FlowShape(2, 16, 3, c, c)
+    shape = gi.FlowShape(nd, L, 3, c, c)
     m2, lam = -4.0, 6.0
     w = gi.init_weights(shape, seed=2)
     flow = P.Flow(shape, w, precision="bf16")
@@ -114,7 +114,7 @@ def test_tc_persistent_batch_and_placement(orc, c):
         assert_logw_close(out.logw[b:b + 1].cpu().numpy(), ref["logw"], rtol=LW_RTOL, what=f"logw[{b}]")
         one = flow.sample(1, seed=77, counter0=b, phi4=(m2, lam))
         assert torch.equal(one.phi[0], out.phi[b]) and torch.equal(one.logw[0], out.logw[b])
-    S = P.phi4_action(2, 16, (m2, lam), out.phi)
+    S = P.phi4_action(nd, L, (m2, lam), out.phi)
     assert_logw_close(S.cpu().numpy(), out.S.cpu().numpy(), rtol=1e-12, what="fused vs standalone S")
     # the inverse pass over the same large batch (two configurations per block)
     zb, lq = flow.logq(out.phi, return_z=True)
@@ -232,12 +232,13 @@ def test_tc_wait_that_runs_out_reports_timeout_and_recovers(orc, B):
     assert_logw_close(out.logw.cpu().numpy(), ref["logw"], rtol=LW_RTOL)
 
 
-def test_tc_odd_batch(orc):
+@pytest.mark.parametrize("nd,L,c", [(2, 32, 24), (3, 8, 16)])
+def test_tc_odd_batch(orc, nd, L, c):
     """An odd batch larger than the SM count: the last block's second half has
     one configuration fewer than its first (it leaves its loop early and
     meets the other half only at the block's exit)."""
     torch, P = require_gpu()
-    shape = gi.FlowShape(2, 32, 2, 24, 24)
+    shape = gi.FlowShape(nd, L, 2, c, c)
     m2, lam = -4.0, 6.0
     w = gi.init_weights(shape, seed=8)
     flow = P.Flow(shape, w, precision="bf16")
