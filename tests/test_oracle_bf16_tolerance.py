@@ -79,3 +79,50 @@ def test_fp32_accumulation_model_is_fp32_close(orc):
     rms = np.sqrt((out64["phi"] ** 2).mean(1, keepdims=True))
     e = np.abs(out32["phi"] - out64["phi"]) / np.maximum(np.abs(out64["phi"]), rms)
     assert 0.0 < e.max() < 1e-5
+
+
+TC_STORED = os.path.join(HERE, "golden", "tc_tolerance.json")
+
+
+def test_tc_stored_bounds_follow_from_stored_drift():
+    """tests/golden/tc_tolerance.json (the tensor-core kernel for the other
+    lattice shapes): per coupling-layer count, each bound is the margin times
+    the largest drift over the shapes; the shapes cover 2D and 3D and every
+    hidden width that kernel takes; the emulation mode is the one the GPU tests
+    compare against; deeper flows get wider bounds."""
+    from gpu_util import TC_MODE
+    with open(TC_STORED) as f:
+        d = json.load(f)
+    assert d["mode"] == TC_MODE
+    shapes = [tuple(s) for s in d["shapes"]]
+    assert {s[0] for s in shapes} == {2, 3} and {s[2] for s in shapes} == {8, 16, 24, 32}
+    assert set(d["by_layers"]) == {"2", "8", "24"}
+    prev = 0.0
+    for n in ("2", "8", "24"):
+        e = d["by_layers"][n]
+        assert e["configurations_per_shape"] >= 64 and e["n_layers"] == int(n)
+        assert set(e["by_shape"]) == {f"{nd}D L={L} C={c}" for nd, L, c in shapes}
+        drift = [v["fp32_model_vs_emulated"] for v in e["by_shape"].values()]
+        assert e["site_rtol"] == pytest.approx(d["margin"] * max(m["phi"]["max"] for m in drift), rel=1e-12)
+        assert e["scalar_rtol"] == pytest.approx(
+            d["margin"] * max(m[k]["max"] for m in drift for k in ("logq", "S", "logw")), rel=1e-12)
+        assert e["site_rtol"] > prev
+        prev = e["site_rtol"]
+
+
+def test_tc_fresh_subset_reproduces_stored_drift(orc):
+    """The first 2 of each shape's stored 64 configurations (2 coupling
+    layers), run afresh: every shape's drift, and the emulation's error
+    against FP64, lie within the stored maxima (the prior counter of a
+    configuration does not depend on the batch)."""
+    mod = _load_script()
+    r = mod.drift_tc(2, 2)
+    with open(TC_STORED) as f:
+        st = json.load(f)["by_layers"]["2"]["by_shape"]
+    assert set(r["by_shape"]) == set(st)
+    for name, v in r["by_shape"].items():
+        for k in ("phi", "logq", "S", "logw"):
+            got = v["fp32_model_vs_emulated"][k]["max"]
+            assert 0.0 < got <= st[name]["fp32_model_vs_emulated"][k]["max"], (name, k, got)
+            got64 = v["emulated_vs_fp64"][k]["max"]
+            assert 0.0 < got64 <= st[name]["emulated_vs_fp64"][k]["max"], (name, k, got64)
