@@ -294,14 +294,47 @@ __device__ void tc_conv1(const TcGeom& g, const float* wf, const float* x, int f
     }
 }
 
+// The periodic images: every halo position of the padded lattice (one of
+// its coordinates 0 or L + 1) takes the value of the interior position it
+// is an image of.  The halo is enumerated face by face (3D: the two z faces
+// of P^2 positions, the two y faces of L P, the two x faces of L^2; 2D: the
+// two y rows of P, the two x columns of L), so no thread visits the interior.
 template <int ND, int CP>
 __device__ void tc_halo(const TcGeom& g, unsigned char* act, int t0, int nthr) {
     constexpr int NKG = CP / 8;
-    const int L = g.L, P = g.P, npos = g.npos;
-    for (int p = t0; p < g.npad; p += nthr) {
-        int px, py, pz;
-        pos_xyz<ND>(p, P, P * P, g.fd_P, g.fd_PP, px, py, pz);
-        if (px >= 1 && px <= L && py >= 1 && py <= L && pz >= 1 && pz <= L) continue;
+    const int L = g.L, P = g.P, npos = g.npos, PP = P * P, LL = L * L, LP = L * P;
+    const int nhalo = ND == 3 ? PP * P - LL * L : PP - LL;
+    for (int i = t0; i < nhalo; i += nthr) {
+        int px, py, pz = 1;
+        if (ND == 3) {
+            if (i < 2 * PP) {                       // z faces
+                const int f = i >= PP, rem = i - f * PP;
+                pz = f ? L + 1 : 0;
+                py = fdiv(rem, g.fd_P);
+                px = rem - py * P;
+            } else if (i < 2 * PP + 2 * LP) {       // y faces, 1 <= z <= L
+                const int j = i - 2 * PP, f = j >= LP, rem = j - f * LP, t = fdiv(rem, g.fd_P);
+                py = f ? L + 1 : 0;
+                pz = 1 + t;
+                px = rem - t * P;
+            } else {                                // x faces, 1 <= y, z <= L
+                const int k = i - 2 * PP - 2 * LP, f = k >= LL, rem = k - f * LL, t = fdiv(rem, g.fd_L);
+                px = f ? L + 1 : 0;
+                pz = 1 + t;
+                py = 1 + rem - t * L;
+            }
+        } else {
+            if (i < 2 * P) {                        // y rows
+                const int f = i >= P;
+                px = i - f * P;
+                py = f ? L + 1 : 0;
+            } else {                                // x columns, 1 <= y <= L
+                const int k = i - 2 * P, f = k >= L;
+                py = 1 + k - f * L;
+                px = f ? L + 1 : 0;
+            }
+        }
+        const int p = px + py * P + (ND == 3 ? pz * PP : 0);
         const int sx = px == 0 ? L : (px == L + 1 ? 1 : px);
         const int sy = py == 0 ? L : (py == L + 1 ? 1 : py);
         const int sz = ND == 3 ? (pz == 0 ? L : (pz == L + 1 ? 1 : pz)) : 0;
