@@ -142,3 +142,10 @@ def test_tensor_core_support_query(lib):
         assert lib.gf_flow_tensor_core_supported(C.byref(ex(nd, L, h))) == 0, (nd, L, h)
     assert lib.gf_flow_tensor_core_supported(C.byref(ex(2, 32, [16, 16], k=5))) == 0
     assert lib.gf_flow_tensor_core_supported(None) == 0
+    # the header's statement of which lattices fit, over the serving mix's
+    # lattices and widths: 2D L <= 32 any width; 2D L = 64 and 3D L = 12, 16
+    # widths 8 and 16 (3D L = 16 also 32, its own kernel); 3D L = 8 any width
+    for nd, L in ((2, 8), (2, 16), (2, 32), (2, 64), (3, 8), (3, 12), (3, 16)):
+        for c in (8, 16, 24, 32):
+            want = (nd == 2 and L <= 32) or (nd == 3 and L == 8) or c <= 16 or (nd, L, c) == (3, 16, 32)
+            assert lib.gf_flow_tensor_core_supported(C.byref(ex(nd, L, [c, c]))) == int(want), (nd, L, c)
