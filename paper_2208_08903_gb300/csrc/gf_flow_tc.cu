@@ -952,6 +952,12 @@ gf_status launch_tc(TcArgs& a, cudaStream_t stream) {
     g.nbuf2 = std::min(kTcRing, g.tmem_cols / (2 * tc_n2<CP>()));
     g.nbuf3 = std::min(kTcRing, g.tmem_cols / (2 * 16));
     if (g.nbuf2 < 1 || g.nbuf3 < 1) return GF_EUNSUPPORTED;
+    // the conv2 schedule needs r_lag <= 2 nbuf2 (+ 1 when r_lag is odd): an
+    // epilogue group holding tile t's store waits for tile t + r_lag's MMAs,
+    // whose accumulator is the one tile t + r_lag - 2 nbuf2 used, drained only
+    // by a group that has reached that tile (the same group when r_lag is
+    // even, which has drained up to t; the other, up to t + 1, when odd)
+    if (g.r_lag > 2 * g.nbuf2 + (g.r_lag & 1)) return GF_EUNSUPPORTED;
     const int64_t grid = std::min<int64_t>((a.B + H - 1) / H, (int64_t)num_sms());
     if (grid <= 0) return GF_OK;
     kern<<<(unsigned)grid, kTcThreads * H, smem, stream>>>(a);

@@ -34,6 +34,10 @@ class Violation(AssertionError):
     pass
 
 
+class Deadlock(Violation):
+    pass
+
+
 class Barrier:
     def __init__(self, name, count):
         self.name, self.count, self.arrived, self.done = name, count, 0, 0
@@ -118,6 +122,7 @@ def run(nd, L, n_cfg, n_layers, nb2, nb3, seed, mutation=None, abort_at=None):
             if abort_at is not None and k >= abort_at:
                 h.abort, h.status = True, "GF_ETIMEOUT"
                 return False
+            h.blocked = True
             yield
 
     def stage(name, what, step):
@@ -138,6 +143,7 @@ def run(nd, L, n_cfg, n_layers, nb2, nb3, seed, mutation=None, abort_at=None):
             sync["abort"][g] = h.abort
             sync["gen"] += 1
         while sync["gen"] == g:
+            h.blocked = True
             yield
         return sync["abort"][g]
 
@@ -292,8 +298,10 @@ def run(nd, L, n_cfg, n_layers, nb2, nb3, seed, mutation=None, abort_at=None):
         for name, n in (("w2", w2_i), ("w3", w3_i), (f"wf{wf_i & 1}", wf_i >> 1)):
             if n >= 0:
                 while h.B[name].done < n + 1:
+                    h.blocked = True
                     yield
         while h.B["fin"].done < 1:
+            h.blocked = True
             yield
         if any(h.queues[q] for q in h.queues):
             raise Violation("TMEM freed with tensor-core work still queued")
@@ -304,6 +312,7 @@ def run(nd, L, n_cfg, n_layers, nb2, nb3, seed, mutation=None, abort_at=None):
     def tensor_core():
         while True:
             live = [q for q in (0, 1) if h.queues[q]]
+            h.blocked = not live and not h.copies
             if live:
                 q = rng.choice(live)
                 gr = h.queues[q].pop(0)
@@ -331,20 +340,22 @@ def run(nd, L, n_cfg, n_layers, nb2, nb3, seed, mutation=None, abort_at=None):
     agents = [issuer(0), issuer(1), group(0), group(1), stager()]
     tc = tensor_core()
     live = list(range(len(agents)))
+    # deadlock: a long run of scheduler steps in which every step found its
+    # agent spinning in a wait (or the tensor cores with nothing to do)
     stall = 0
     while live:
         pick = rng.choice(live + [-1, -1])
+        h.blocked = False
         if pick == -1:
             next(tc)
-            continue
-        try:
-            next(agents[pick])
-            stall = 0
-        except StopIteration:
-            live.remove(pick)
-        stall += 1
-        if stall > 200000:
-            raise Violation("deadlock")
+        else:
+            try:
+                next(agents[pick])
+            except StopIteration:
+                live.remove(pick)
+        stall = stall + 1 if h.blocked else 0
+        if stall > 20000:
+            raise Deadlock(f"deadlock: {sorted(h.done_agents)} finished")
     # the tensor cores finish whatever is left (only the final commits)
     for _ in range(1000):
         next(tc)
@@ -355,7 +366,9 @@ SHAPES = [(2, 32), (2, 64), (3, 8), (3, 12), (2, 8)]
 
 
 @pytest.mark.parametrize("nd,L", SHAPES)
-@pytest.mark.parametrize("nb2,nb3", [(1, 8), (2, 2), (5, 16)])
+# TMEM rings of the launches: width 32 (1 or 2 buffers per group with two or
+# one halves), 16 (2 / 5), 8 (4 / 8); plus small and odd sizes
+@pytest.mark.parametrize("nb2,nb3", [(1, 8), (2, 2), (5, 16), (4, 8), (8, 8)])
 def test_protocol_random_schedules(nd, L, nb2, nb3):
     for seed in range(6):
         h = run(nd, L, n_cfg=2, n_layers=3, nb2=nb2, nb3=nb3, seed=seed)
@@ -380,3 +393,54 @@ def test_protocol_catches_planted_mistakes(mutation):
             caught = True
             break
     assert caught, mutation
+
+
+def lag_fits(r, nb2):
+    """The conv2 schedule's condition: an epilogue group holding tile t's
+    store waits for tile t + r's MMAs, which need the TMEM buffer of tile
+    t + r - 2 nb2 drained; with r even that tile belongs to the same group, so
+    it must be tile t or earlier; with r odd, the other group's current tile
+    t + 1 or earlier."""
+    return r <= 2 * nb2 + (r & 1)
+
+
+@pytest.mark.parametrize("nd,L", [(2, 64), (3, 8), (3, 12), (3, 16)])
+@pytest.mark.parametrize("nb2", [1, 2, 3, 5, 8])
+def test_protocol_deadlocks_exactly_when_the_ring_is_short_for_the_lag(nd, L, nb2):
+    _, _, r = geometry(nd, L)
+    for seed in range(3):
+        if lag_fits(r, nb2):
+            run(nd, L, n_cfg=2, n_layers=2, nb2=nb2, nb3=8, seed=seed)
+        else:
+            with pytest.raises(Deadlock):
+                run(nd, L, n_cfg=2, n_layers=2, nb2=nb2, nb3=8, seed=seed)
+
+
+def test_launch_rings_fit_the_lag():
+    """Every shape the kernel takes (gf_flow_tensor_core_supported, less the
+    3D L=16 width-32 shape, which has its own kernel), with the TMEM rings its
+    launch gives it (512 columns, or 256 per half with two halves; conv2
+    accumulators of 3 Cp columns, 32 at width 8; at most 8 per group),
+    satisfies the condition; the launcher also refuses any launch that would
+    not (GF_EUNSUPPORTED)."""
+    import ctypes as C
+    from paper_2208_08903_gb300 import _abi
+    lib = _abi.load()
+
+    def ex(nd, L, c):
+        hid = (C.c_int32 * _abi.GF_MAX_HIDDEN)(*([c, c] + [0] * (_abi.GF_MAX_HIDDEN - 2)))
+        return _abi.FlowShapeExC(nd, L, 4, 2, hid, 3, 1, 0.01)
+
+    n = 0
+    for nd, Ls in ((2, range(4, 66, 2)), (3, range(4, 18, 2))):
+        for L in Ls:
+            for c in (8, 16, 24, 32):
+                if (nd, L, c) == (3, 16, 32) or not lib.gf_flow_tensor_core_supported(C.byref(ex(nd, L, c))):
+                    continue
+                n2 = 32 if c == 8 else (48 if c == 16 else 96)
+                _, _, r = geometry(nd, L)
+                for cols in (512, 256):
+                    nb2 = min(8, cols // (2 * n2))
+                    assert nb2 >= 1 and lag_fits(r, nb2), (nd, L, c, cols, r, nb2)
+                n += 1
+    assert n >= 20
